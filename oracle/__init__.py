@@ -1,0 +1,318 @@
+"""CPU oracle for the cell-centred multigrid electrostatics solver (arXiv 1410.6609).
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path (``paper_1410_6609_gb300``) never
+imports it and shares no code with it.
+
+The arithmetic lives in ``ccmg_oracle.c`` (plain scalar loops, FP64, ``-ffp-contract=off``);
+this module only compiles it with gcc, loads it with ctypes and marshals NumPy arrays.
+Arrays are C-ordered ``[nz, ny, nx]`` (x fastest), matching the C layout ``i + nx*(j + ny*k)``.
+
+Every function cites the paper passage it follows (section / equation / algorithm).
+Pins that tie the oracle to something other than itself are in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "ccmg_oracle.c"), os.path.join(_HERE, "oracle_level_ops.inc")]
+_LIB_PATH = os.path.join(_HERE, "libccmg_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DIRICHLET = 0
+NEUMANN = 1
+CG_RTOL = 1e-14
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (plain C11, no FMA contraction)."""
+    newest = max(os.path.getmtime(p) for p in _SRC)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+           "-o", tmp, _SRC[0], "-lm"]
+    subprocess.check_call(cmd, cwd=_HERE)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            F = ctypes.c_float
+            sig = {
+                "ccmg_or_levels": (I, [I, I, I, P]),
+                "ccmg_or_apply": (None, [P, P, I, I, I, D, P]),
+                "ccmg_or_apply_f": (None, [P, P, I, I, I, F, P]),
+                "ccmg_or_residual": (None, [P, P, P, I, I, I, D, P]),
+                "ccmg_or_rbgs_half": (None, [P, P, I, I, I, D, P, I]),
+                "ccmg_or_restrict": (None, [P, P, I, I, I]),
+                "ccmg_or_prolong_correct": (None, [P, P, I, I, I, D]),
+                "ccmg_or_rhs": (None, [P, P, I, I, I, D, D, P, P]),
+                "ccmg_or_rhs_adjoint": (None, [P, P, P, I, I, I, D, D, P]),
+                "ccmg_or_cg": (I, [P, P, I, I, I, D, P, D, I]),
+                "ccmg_or_vcycles": (I, [P, P, I, I, I, D, P, I, I, D, I]),
+                "ccmg_or_rel_residual": (D, [P, P, I, I, I, D, P]),
+                "ccmg_or_solve": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
+                "ccmg_or_solve_mixed": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
+                "ccmg_or_efield": (None, [P, P, I, I, I, D, P, P]),
+                "ccmg_or_sphere_density": (None, [P, I, I, I, D, I, P, P, P, I]),
+                "ccmg_or_sphere_density_adjoint": (None, [P, P, I, I, I, D, I, P, P, I]),
+                "ccmg_or_force_gather": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P]),
+                "ccmg_or_force_gather_adjoint": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P, P, P, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _bc(bc_type) -> np.ndarray:
+    a = np.ascontiguousarray(bc_type, dtype=np.int32)
+    assert a.shape == (6,)
+    return a
+
+
+def _dims(a: np.ndarray):
+    nz, ny, nx = a.shape
+    return nx, ny, nz
+
+
+# --------------------------------------------------------------------------------------------
+# Hierarchy and coefficients (Sec. 3)
+
+def levels(nx: int, ny: int, nz: int) -> list[tuple[int, int, int]]:
+    """Level dimensions: halve while every dimension is even and its half is >= 3 (Sec. 3)."""
+    buf = np.zeros(3 * 32, dtype=np.int32)
+    n = _load().ccmg_or_levels(nx, ny, nz, _p(buf))
+    return [tuple(int(v) for v in buf[3 * l:3 * l + 3]) for l in range(n)]
+
+
+def level_coeff(h: float, l: int) -> float:
+    """c_l = 1/(2^l h^2): coefficient of the Galerkin operator on level l (Sec. 3)."""
+    return 1.0 / (2.0 ** l * h * h)
+
+
+# --------------------------------------------------------------------------------------------
+# Single-level operations (Sec. 2.4 stencil, Sec. 3 transfers, Sec. 4.3 RBGS and CG)
+
+def apply(phi, c: float, bc_type) -> np.ndarray:
+    """A_l phi with the folded boundary stencil (Sec. 2.4)."""
+    phi = _f64(phi)
+    out = np.empty_like(phi)
+    _load().ccmg_or_apply(_p(phi), _p(out), *_dims(phi), c, _p(_bc(bc_type)))
+    return out
+
+
+def apply_f32(phi, c: float, bc_type) -> np.ndarray:
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    out = np.empty_like(phi)
+    _load().ccmg_or_apply_f(_p(phi), _p(out), *_dims(phi), c, _p(_bc(bc_type)))
+    return out
+
+
+def residual(phi, f, c: float, bc_type) -> np.ndarray:
+    """r = f - A_l phi (Sec. 6.3 'Resid')."""
+    phi, f = _f64(phi), _f64(f)
+    r = np.empty_like(phi)
+    _load().ccmg_or_residual(_p(phi), _p(f), _p(r), *_dims(phi), c, _p(_bc(bc_type)))
+    return r
+
+
+def rbgs_half(phi, f, c: float, bc_type, colour: int) -> np.ndarray:
+    """One red (colour 0, i+j+k even) or black (colour 1) Gauss-Seidel half-sweep (Sec. 4.3)."""
+    phi = _f64(phi).copy()
+    f = _f64(f)
+    _load().ccmg_or_rbgs_half(_p(phi), _p(f), *_dims(phi), c, _p(_bc(bc_type)), colour)
+    return phi
+
+
+def restrict(r) -> np.ndarray:
+    """Averaging restriction: coarse value = mean of the 8 children (Sec. 3)."""
+    r = _f64(r)
+    nz, ny, nx = r.shape
+    fc = np.empty((nz // 2, ny // 2, nx // 2))
+    _load().ccmg_or_restrict(_p(r), _p(fc), nx, ny, nz)
+    return fc
+
+
+def prolong_correct(phi, ec, omega: float = 2.0) -> np.ndarray:
+    """phi += omega * (constant prolongation of ec) (Sec. 3, magnified correction)."""
+    phi = _f64(phi).copy()
+    ec = _f64(ec)
+    _load().ccmg_or_prolong_correct(_p(phi), _p(ec), *_dims(phi), omega)
+    return phi
+
+
+def rhs(rho, h: float, bc_type, bc_value, eps: float = 1.0) -> np.ndarray:
+    """f = rho/eps with Dirichlet (+2g/h^2) and Neumann (+g/h) face terms (Sec. 2.4, 4.3)."""
+    rho = _f64(rho)
+    f = np.empty_like(rho)
+    _load().ccmg_or_rhs(_p(rho), _p(f), *_dims(rho), h, eps, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    return f
+
+
+def rhs_adjoint(lam, h: float, bc_type, eps: float = 1.0):
+    """Adjoint of :func:`rhs`: returns (dJ/drho, dJ/dbc_value[6]) given lam = dJ/df."""
+    lam = _f64(lam)
+    grho = np.empty_like(lam)
+    gbc = np.zeros(6)
+    _load().ccmg_or_rhs_adjoint(_p(lam), _p(grho), _p(gbc), *_dims(lam), h, eps, _p(_bc(bc_type)))
+    return grho, gbc
+
+
+def cg(b, c: float, bc_type, rtol: float = CG_RTOL, maxit: int | None = None):
+    """Unpreconditioned CG from x = 0 on A_l x = b (Sec. 4.3 coarse solver). Returns (x, iters)."""
+    b = _f64(b)
+    x = np.empty_like(b)
+    if maxit is None:
+        maxit = 2 * b.size
+    it = _load().ccmg_or_cg(_p(x), _p(b), *_dims(b), c, _p(_bc(bc_type)), rtol, maxit)
+    return x, it
+
+
+# --------------------------------------------------------------------------------------------
+# Cycles and solves (Sec. 3, Sec. 4.3, Algorithm 1)
+
+def vcycles(phi, f, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2,
+            omega: float = 2.0):
+    """ncycles V(nu1,nu2)-cycles on A_0 phi = f (f BC-adapted). Returns (phi, last CG iters)."""
+    phi = _f64(phi).copy()
+    f = _f64(f)
+    it = _load().ccmg_or_vcycles(_p(phi), _p(f), *_dims(phi), h, _p(_bc(bc_type)), nu1, nu2, omega,
+                                 ncycles)
+    return phi, it
+
+
+def rel_residual(phi, f, h: float, bc_type) -> float:
+    """||f - A_0 phi||_2 / ||f||_2 (Algorithm 1 termination quantity)."""
+    phi, f = _f64(phi), _f64(f)
+    return float(_load().ccmg_or_rel_residual(_p(phi), _p(f), *_dims(phi), h, _p(_bc(bc_type))))
+
+
+def solve(f, h: float, bc_type, tol: float = 1e-10, max_cycles: int = 100, nu1: int = 2,
+          nu2: int = 2, omega: float = 2.0, phi0=None):
+    """Algorithm 1: V-cycles while ||r||/||f|| >= tol. Returns (phi, cycles, rel_res)."""
+    f = _f64(f)
+    phi = np.zeros_like(f) if phi0 is None else _f64(phi0).copy()
+    rel = ctypes.c_double()
+    k = _load().ccmg_or_solve(_p(phi), _p(f), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega, tol,
+                              max_cycles, ctypes.byref(rel))
+    return phi, k, rel.value
+
+
+def solve_mixed(f, h: float, bc_type, tol: float = 1e-9, max_cycles: int = 100, nu1: int = 2,
+                nu2: int = 2, omega: float = 2.0, phi0=None):
+    """FP64 defect correction around single-precision V-cycles. Returns (phi, cycles, rel_res)."""
+    f = _f64(f)
+    phi = np.zeros_like(f) if phi0 is None else _f64(phi0).copy()
+    rel = ctypes.c_double()
+    k = _load().ccmg_or_solve_mixed(_p(phi), _p(f), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega,
+                                    tol, max_cycles, ctypes.byref(rel))
+    return phi, k, rel.value
+
+
+# --------------------------------------------------------------------------------------------
+# Fields and forces (Sec. 2.4: Eq. ElectrostatForce, central differences, subsampling)
+
+def efield(phi, h: float, bc_type, bc_value) -> np.ndarray:
+    """E = -grad phi by central differences with BC ghost values; returns [3, nz, ny, nx]."""
+    phi = _f64(phi)
+    E = np.empty((3,) + phi.shape)
+    _load().ccmg_or_efield(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    return E
+
+
+def _spheres(centers, radius, density):
+    c = _f64(centers).reshape(-1, 3)
+    r = _f64(radius).reshape(-1)
+    d = _f64(density).reshape(-1)
+    assert c.shape[0] == r.shape[0] == d.shape[0]
+    return c, r, d
+
+
+def sphere_density(shape, h: float, centers, radius, density, sf: int = 2) -> np.ndarray:
+    """rho(b) = sum_s density_s * (subsampled overlap fraction of sphere s with cell b)."""
+    nz, ny, nx = shape
+    c, r, d = _spheres(centers, radius, density)
+    rho = np.empty((nz, ny, nx))
+    _load().ccmg_or_sphere_density(_p(rho), nx, ny, nz, h, c.shape[0], _p(c), _p(r), _p(d), sf)
+    return rho
+
+
+def sphere_density_adjoint(gfield, h: float, centers, radius, sf: int = 2) -> np.ndarray:
+    gfield = _f64(gfield)
+    c, r, _ = _spheres(centers, radius, np.zeros(len(_f64(radius).reshape(-1))))
+    g = np.zeros(c.shape[0])
+    _load().ccmg_or_sphere_density_adjoint(_p(gfield), _p(g), *_dims(gfield), h, c.shape[0], _p(c),
+                                           _p(r), sf)
+    return g
+
+
+def force_gather(phi, h: float, bc_type, bc_value, centers, radius, density, sf: int = 2):
+    """F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce). Returns [P, 3]."""
+    phi = _f64(phi)
+    c, r, d = _spheres(centers, radius, density)
+    F = np.empty((c.shape[0], 3))
+    _load().ccmg_or_force_gather(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                 c.shape[0], _p(c), _p(r), _p(d), sf, _p(F))
+    return F
+
+
+def force_gather_adjoint(phi, h: float, bc_type, bc_value, centers, radius, density, wF,
+                         sf: int = 2):
+    """Adjoint of :func:`force_gather` for J = sum wF * F. Returns (dJ/dphi, dJ/ddensity, dJ/dbc)."""
+    phi = _f64(phi)
+    c, r, d = _spheres(centers, radius, density)
+    wF = _f64(wF).reshape(-1, 3)
+    gphi = np.zeros_like(phi)
+    gd = np.zeros(c.shape[0])
+    gbc = np.zeros(6)
+    _load().ccmg_or_force_gather_adjoint(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                         c.shape[0], _p(c), _p(r), _p(d), sf, _p(wF), _p(gphi), _p(gd),
+                                         _p(gbc))
+    return gphi, gd, gbc
+
+
+def force_objective_and_grad(shape, h: float, bc_type, bc_value, centers, radius, density, wF,
+                             sf: int = 2, eps: float = 1.0, tol: float = 1e-13, max_cycles: int = 200):
+    """J = sum wF * F(density, bc_value) and its gradient by one adjoint solve.
+
+    Chain: density -> rho field (subsampling) -> f = rhs(rho, bc) -> phi = A^-1 f -> F.
+    A is symmetric, so the adjoint solve A lam = dJ/dphi reuses the same multigrid (homogeneous
+    BCs: the BC values enter only through the RHS). Returns (J, dJ/ddensity[P], dJ/dbc[6], info).
+    """
+    rho = sphere_density(shape, h, centers, radius, density, sf)
+    f = rhs(rho, h, bc_type, bc_value, eps)
+    phi, k1, rel1 = solve(f, h, bc_type, tol=tol, max_cycles=max_cycles)
+    F = force_gather(phi, h, bc_type, bc_value, centers, radius, density, sf)
+    J = float(np.sum(_f64(wF).reshape(-1, 3) * F))
+    gphi, gdens, gbc = force_gather_adjoint(phi, h, bc_type, bc_value, centers, radius, density, wF, sf)
+    lam, k2, rel2 = solve(gphi, h, bc_type, tol=tol, max_cycles=max_cycles)
+    grho, gbc_rhs = rhs_adjoint(lam, h, bc_type, eps)
+    gdens = gdens + sphere_density_adjoint(grho, h, centers, radius, sf)
+    return J, gdens, gbc + gbc_rhs, {"phi": phi, "lam": lam, "cycles": (k1, k2), "rel": (rel1, rel2)}

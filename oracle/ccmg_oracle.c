@@ -1,0 +1,606 @@
+/* ccmg_oracle.c -- plain, slow, obviously-correct CPU oracle for the electrostatics step of
+ * Bartuschat & Ruede, "Parallel Multiphysics Simulations of Charged Particles in Microfluidic
+ * Flows" (arXiv 1410.6609).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the benchmark's CPU
+ * baseline may load this library. It shares no code with the CUDA path.
+ *
+ * Scalar FP64 loops (FP32 for the inner cycle of the mixed-precision variant), compiled with
+ * -ffp-contract=off so that every product and sum is rounded on its own. No blocking, no
+ * fusion: each step of the method is one loop nest, taken in the order the paper gives.
+ *
+ * What it computes (paper section / equation named at each function):
+ *   - RHS of the Poisson equation -lap(phi) = rho/eps with Dirichlet / Neumann BCs folded into
+ *     the RHS (Sec. 2.4, Eq. Poisson and the 1D derivation of the BC treatment);
+ *   - the cell-centred multigrid V(nu1,nu2)-cycle: red-black Gauss-Seidel, averaging
+ *     restriction, constant prolongation with a x2 magnified correction, Galerkin coarse
+ *     operators in closed form, CG on the coarsest grid (Sec. 3 and Sec. 4.3);
+ *   - termination on the L2 norm of the residual (Algorithm 1);
+ *   - the E-field by central differences and the Coulomb force on each particle
+ *     (Sec. 2.4, Eq. ElectrostatForce, D3Q7 central differences);
+ *   - the charge-density subsampling of spheres (Sec. 2.4, "Subsampling");
+ *   - adjoints of the force, the RHS and the subsampling (not in the paper; used to check
+ *     gradients of J = sum of weighted forces).
+ *
+ * Boundary convention: faces 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z; bc_type 0 = Dirichlet (value = the
+ * potential on the face), 1 = Neumann (value = the outward normal derivative on the face).
+ * Ghost values: Dirichlet 2 g - phi_1, Neumann phi_1 + h g (the paper derives both for
+ * spacing 1; they are scaled by h here).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define BC_DIRICHLET 0
+#define BC_NEUMANN 1
+
+static size_t idx3(int i, int j, int k, int nx, int ny) {
+  return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)k);
+}
+
+/* Diagonal shift of the folded stencil at cell (i,j,k): the neighbour entry on a boundary
+ * face moves to the centre with sign +1 for Dirichlet (centre beta - alpha, alpha = -1) and
+ * -1 for Neumann (centre beta + alpha). Sec. 2.4, "Boundary conditions". */
+static int face_shift(int type) { return type == BC_DIRICHLET ? 1 : -1; }
+static int diag_shift(int i, int j, int k, int nx, int ny, int nz, const int* bc) {
+  int d = 0;
+  if (i == 0) d += face_shift(bc[0]);
+  if (i == nx - 1) d += face_shift(bc[1]);
+  if (j == 0) d += face_shift(bc[2]);
+  if (j == ny - 1) d += face_shift(bc[3]);
+  if (k == 0) d += face_shift(bc[4]);
+  if (k == nz - 1) d += face_shift(bc[5]);
+  return d;
+}
+
+#define REAL double
+#define FN(name) name##_d
+#include "oracle_level_ops.inc"
+#undef REAL
+#undef FN
+#define REAL float
+#define FN(name) name##_f
+#include "oracle_level_ops.inc"
+#undef REAL
+#undef FN
+
+/* ------------------------------------------------------------------------------------------ */
+/* Level hierarchy (Sec. 3): coarsen while every dimension is even and its half is >= 3.       */
+
+#define OR_MAX_LEVELS 32
+
+int ccmg_or_levels(int nx, int ny, int nz, int* dims_out) {
+  int n = 0;
+  int d[3] = {nx, ny, nz};
+  for (;;) {
+    if (dims_out) {
+      dims_out[3 * n + 0] = d[0];
+      dims_out[3 * n + 1] = d[1];
+      dims_out[3 * n + 2] = d[2];
+    }
+    ++n;
+    if (n >= OR_MAX_LEVELS) break;
+    int ok = 1;
+    for (int a = 0; a < 3; ++a)
+      if ((d[a] % 2) != 0 || d[a] / 2 < 3) ok = 0;
+    if (!ok) break;
+    for (int a = 0; a < 3; ++a) d[a] /= 2;
+  }
+  return n;
+}
+
+/* Coefficient of level l: c_l = 1 / (2^l h^2). The Galerkin product R A_l P of the averaging
+ * restriction and the constant prolongation halves the coefficient and keeps the pattern and
+ * the boundary shifts (checked against the literal triple product by the tests). */
+static double level_coeff(double h, int l) { return 1.0 / (ldexp(1.0, l) * h * h); }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Exported single-level operations (used by per-kernel parity tests).                          */
+
+void ccmg_or_apply(const double* phi, double* out, int nx, int ny, int nz, double c, const int* bc) {
+  apply_d(phi, out, nx, ny, nz, c, bc);
+}
+void ccmg_or_residual(const double* phi, const double* f, double* r, int nx, int ny, int nz, double c,
+                      const int* bc) {
+  residual_d(phi, f, r, nx, ny, nz, c, bc);
+}
+void ccmg_or_rbgs_half(double* phi, const double* f, int nx, int ny, int nz, double c, const int* bc,
+                       int colour) {
+  rbgs_half_d(phi, f, nx, ny, nz, c, bc, colour);
+}
+void ccmg_or_restrict(const double* r, double* fc, int nx, int ny, int nz) {
+  restrict_avg_d(r, fc, nx, ny, nz);
+}
+void ccmg_or_prolong_correct(double* phi, const double* ec, int nx, int ny, int nz, double omega) {
+  prolong_correct_d(phi, ec, nx, ny, nz, omega);
+}
+void ccmg_or_apply_f(const float* phi, float* out, int nx, int ny, int nz, float c, const int* bc) {
+  apply_f(phi, out, nx, ny, nz, c, bc);
+}
+
+/* RHS with BCs folded in (Sec. 2.4 and Sec. 4.3 "BC Handling for Scalar Potentials": the RHS
+ * is adapted once, on the finest grid only):
+ *   f = rho / eps;  Dirichlet face cells f += 2 g / h^2;  Neumann face cells f += g / h.
+ * Edge and corner cells receive the term of every face they touch. */
+void ccmg_or_rhs(const double* rho, double* f, int nx, int ny, int nz, double h, double eps,
+                 const int* bc, const double* bcv) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        double v = rho[p] / eps;
+        const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
+        for (int q = 0; q < 6; ++q) {
+          if (!on_face[q]) continue;
+          if (bc[q] == BC_DIRICHLET)
+            v = v + 2.0 * bcv[q] / (h * h);
+          else
+            v = v + bcv[q] / h;
+        }
+        f[p] = v;
+      }
+}
+
+/* Adjoint of ccmg_or_rhs: given lambda = dJ/df, returns dJ/drho = lambda / eps and
+ * dJ/dbc_value[q] = sum over the face-q cells of lambda * (2/h^2 Dirichlet, 1/h Neumann). */
+void ccmg_or_rhs_adjoint(const double* lam, double* grho, double* gbc, int nx, int ny, int nz,
+                         double h, double eps, const int* bc) {
+  for (int q = 0; q < 6; ++q) gbc[q] = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        grho[p] = lam[p] / eps;
+        const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
+        for (int q = 0; q < 6; ++q) {
+          if (!on_face[q]) continue;
+          gbc[q] = gbc[q] + lam[p] * (bc[q] == BC_DIRICHLET ? 2.0 / (h * h) : 1.0 / h);
+        }
+      }
+}
+
+static double dot_d(const double* a, const double* b, size_t n) {
+  double s = 0.0;
+  for (size_t p = 0; p < n; ++p) s = s + a[p] * b[p];
+  return s;
+}
+
+/* Unpreconditioned conjugate gradients (Hestenes-Stiefel) on the coarsest grid (Sec. 4.3),
+ * started from x = 0 and stopped when ||r||_2 <= rtol ||b||_2 or after maxit iterations.
+ * Returns the iteration count. */
+int ccmg_or_cg(double* x, const double* b, int nx, int ny, int nz, double c, const int* bc, double rtol,
+               int maxit) {
+  const size_t n = (size_t)nx * ny * nz;
+  double* r = (double*)malloc(n * sizeof(double));
+  double* p = (double*)malloc(n * sizeof(double));
+  double* ap = (double*)malloc(n * sizeof(double));
+  for (size_t q = 0; q < n; ++q) {
+    x[q] = 0.0;
+    r[q] = b[q];
+    p[q] = b[q];
+  }
+  const double bnorm = sqrt(dot_d(b, b, n));
+  double rr = dot_d(r, r, n);
+  int it = 0;
+  if (bnorm > 0.0) {
+    while (it < maxit) {
+      apply_d(p, ap, nx, ny, nz, c, bc);
+      const double alpha = rr / dot_d(p, ap, n);
+      for (size_t q = 0; q < n; ++q) {
+        x[q] = x[q] + alpha * p[q];
+        r[q] = r[q] - alpha * ap[q];
+      }
+      ++it;
+      const double rr_new = dot_d(r, r, n);
+      if (sqrt(rr_new) <= rtol * bnorm) break;
+      const double beta = rr_new / rr;
+      for (size_t q = 0; q < n; ++q) p[q] = r[q] + beta * p[q];
+      rr = rr_new;
+    }
+  }
+  free(r);
+  free(p);
+  free(ap);
+  return it;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* V-cycle (Sec. 3, Sec. 4.3): at level l < L-1:
+ *   nu1 x (red, black);  r = f - A phi;  f_{l+1} = R r;  phi_{l+1} = 0;  V at l+1;
+ *   phi += omega P phi_{l+1};  nu2 x (black, red).
+ * At the coarsest level: CG from zero to rtol 1e-14 (cap 2 N_c iterations). */
+
+typedef struct {
+  int L;
+  int dims[OR_MAX_LEVELS][3];
+  double* phi[OR_MAX_LEVELS]; /* level 0 is the caller's array */
+  double* f[OR_MAX_LEVELS];   /* level 0 is the caller's array */
+  double* r;                  /* scratch, finest size */
+  float* phif[OR_MAX_LEVELS]; /* single-precision hierarchy (mixed mode) */
+  float* ff[OR_MAX_LEVELS];
+  float* rf;
+} hierarchy;
+
+static size_t ncells(const int* d) { return (size_t)d[0] * d[1] * d[2]; }
+
+static void hier_init(hierarchy* H, int nx, int ny, int nz, int single) {
+  int dims[3 * OR_MAX_LEVELS];
+  memset(H, 0, sizeof(*H));
+  H->L = ccmg_or_levels(nx, ny, nz, dims);
+  for (int l = 0; l < H->L; ++l) {
+    for (int a = 0; a < 3; ++a) H->dims[l][a] = dims[3 * l + a];
+    const size_t n = ncells(H->dims[l]);
+    if (l > 0) {
+      H->phi[l] = (double*)calloc(n, sizeof(double));
+      H->f[l] = (double*)calloc(n, sizeof(double));
+    }
+    if (single) {
+      H->phif[l] = (float*)calloc(n, sizeof(float));
+      H->ff[l] = (float*)calloc(n, sizeof(float));
+    }
+  }
+  H->r = (double*)calloc(ncells(H->dims[0]), sizeof(double));
+  if (single) H->rf = (float*)calloc(ncells(H->dims[0]), sizeof(float));
+}
+
+static void hier_free(hierarchy* H) {
+  for (int l = 0; l < H->L; ++l) {
+    if (l > 0) {
+      free(H->phi[l]);
+      free(H->f[l]);
+    }
+    free(H->phif[l]);
+    free(H->ff[l]);
+  }
+  free(H->r);
+  free(H->rf);
+}
+
+#define CG_RTOL 1e-14
+
+static void vcycle_d(hierarchy* H, int l, double h, const int* bc, int nu1, int nu2, double omega,
+                     int* cg_iters) {
+  const int* d = H->dims[l];
+  const double c = level_coeff(h, l);
+  if (l == H->L - 1) {
+    const int it = ccmg_or_cg(H->phi[l], H->f[l], d[0], d[1], d[2], c, bc, CG_RTOL, 2 * (int)ncells(d));
+    if (cg_iters) *cg_iters = it;
+    return;
+  }
+  for (int s = 0; s < nu1; ++s) {
+    rbgs_half_d(H->phi[l], H->f[l], d[0], d[1], d[2], c, bc, 0);
+    rbgs_half_d(H->phi[l], H->f[l], d[0], d[1], d[2], c, bc, 1);
+  }
+  residual_d(H->phi[l], H->f[l], H->r, d[0], d[1], d[2], c, bc);
+  restrict_avg_d(H->r, H->f[l + 1], d[0], d[1], d[2]);
+  memset(H->phi[l + 1], 0, ncells(H->dims[l + 1]) * sizeof(double));
+  vcycle_d(H, l + 1, h, bc, nu1, nu2, omega, cg_iters);
+  prolong_correct_d(H->phi[l], H->phi[l + 1], d[0], d[1], d[2], omega);
+  for (int s = 0; s < nu2; ++s) {
+    rbgs_half_d(H->phi[l], H->f[l], d[0], d[1], d[2], c, bc, 1);
+    rbgs_half_d(H->phi[l], H->f[l], d[0], d[1], d[2], c, bc, 0);
+  }
+}
+
+/* Same cycle in single precision; the coarsest-grid CG stays in double. */
+static void vcycle_f(hierarchy* H, int l, double h, const int* bc, int nu1, int nu2, float omega,
+                     int* cg_iters) {
+  const int* d = H->dims[l];
+  const size_t n = ncells(d);
+  if (l == H->L - 1) {
+    double* b = (double*)malloc(n * sizeof(double));
+    double* x = (double*)malloc(n * sizeof(double));
+    for (size_t q = 0; q < n; ++q) b[q] = (double)H->ff[l][q];
+    const int it = ccmg_or_cg(x, b, d[0], d[1], d[2], level_coeff(h, l), bc, CG_RTOL, 2 * (int)n);
+    for (size_t q = 0; q < n; ++q) H->phif[l][q] = (float)x[q];
+    if (cg_iters) *cg_iters = it;
+    free(b);
+    free(x);
+    return;
+  }
+  const float c = (float)level_coeff(h, l);
+  for (int s = 0; s < nu1; ++s) {
+    rbgs_half_f(H->phif[l], H->ff[l], d[0], d[1], d[2], c, bc, 0);
+    rbgs_half_f(H->phif[l], H->ff[l], d[0], d[1], d[2], c, bc, 1);
+  }
+  residual_f(H->phif[l], H->ff[l], H->rf, d[0], d[1], d[2], c, bc);
+  restrict_avg_f(H->rf, H->ff[l + 1], d[0], d[1], d[2]);
+  memset(H->phif[l + 1], 0, ncells(H->dims[l + 1]) * sizeof(float));
+  vcycle_f(H, l + 1, h, bc, nu1, nu2, omega, cg_iters);
+  prolong_correct_f(H->phif[l], H->phif[l + 1], d[0], d[1], d[2], omega);
+  for (int s = 0; s < nu2; ++s) {
+    rbgs_half_f(H->phif[l], H->ff[l], d[0], d[1], d[2], c, bc, 1);
+    rbgs_half_f(H->phif[l], H->ff[l], d[0], d[1], d[2], c, bc, 0);
+  }
+}
+
+static double norm2_d(const double* a, size_t n) { return sqrt(dot_d(a, a, n)); }
+
+/* ncycles V-cycles on A_0 phi = f (f already BC-adapted), phi updated in place. Returns the
+ * CG iteration count of the last coarse solve. */
+int ccmg_or_vcycles(double* phi, const double* f, int nx, int ny, int nz, double h, const int* bc,
+                    int nu1, int nu2, double omega, int ncycles) {
+  hierarchy H;
+  hier_init(&H, nx, ny, nz, 0);
+  H.phi[0] = phi;
+  H.f[0] = (double*)f;
+  int cg = 0;
+  for (int k = 0; k < ncycles; ++k) vcycle_d(&H, 0, h, bc, nu1, nu2, omega, &cg);
+  H.phi[0] = NULL;
+  H.f[0] = NULL;
+  hier_free(&H);
+  return cg;
+}
+
+/* Relative residual ||f - A_0 phi||_2 / ||f||_2 (Algorithm 1 termination test, L2 norm). */
+double ccmg_or_rel_residual(const double* phi, const double* f, int nx, int ny, int nz, double h,
+                            const int* bc) {
+  const size_t n = (size_t)nx * ny * nz;
+  double* r = (double*)malloc(n * sizeof(double));
+  residual_d(phi, f, r, nx, ny, nz, level_coeff(h, 0), bc);
+  const double fn = norm2_d(f, n);
+  const double rn = norm2_d(r, n);
+  free(r);
+  return fn > 0.0 ? rn / fn : rn;
+}
+
+/* Algorithm 1: while ||r|| / ||f|| >= tol and fewer than max_cycles cycles: one V-cycle.
+ * phi is the start value (warm start) and the result. Returns the number of cycles. */
+int ccmg_or_solve(double* phi, const double* f, int nx, int ny, int nz, double h, const int* bc, int nu1,
+                  int nu2, double omega, double tol, int max_cycles, double* rel_res_out) {
+  hierarchy H;
+  hier_init(&H, nx, ny, nz, 0);
+  H.phi[0] = phi;
+  H.f[0] = (double*)f;
+  const size_t n = (size_t)nx * ny * nz;
+  const double fn = norm2_d(f, n);
+  int k = 0;
+  double rel;
+  for (;;) {
+    residual_d(phi, f, H.r, nx, ny, nz, level_coeff(h, 0), bc);
+    rel = fn > 0.0 ? norm2_d(H.r, n) / fn : norm2_d(H.r, n);
+    if (!(rel >= tol) || k >= max_cycles) break;
+    vcycle_d(&H, 0, h, bc, nu1, nu2, omega, NULL);
+    ++k;
+  }
+  if (rel_res_out) *rel_res_out = rel;
+  H.phi[0] = NULL;
+  H.f[0] = NULL;
+  hier_free(&H);
+  return k;
+}
+
+/* Mixed-precision defect correction (not in the paper; the cycle is the paper's):
+ *   loop: r = f - A_0 phi (double); stop if ||r||/||f|| < tol;
+ *         s = RMS of the previous residual (||f|| RMS on the first pass);
+ *         one single-precision V-cycle on A_0 e = r / s from e = 0 (double CG at the bottom);
+ *         phi += s * e (double).
+ * Returns the number of outer iterations (= single-precision V-cycles). */
+int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, double h, const int* bc,
+                        int nu1, int nu2, double omega, double tol, int max_cycles, double* rel_res_out) {
+  hierarchy H;
+  hier_init(&H, nx, ny, nz, 1);
+  const size_t n = (size_t)nx * ny * nz;
+  const double fn = norm2_d(f, n);
+  double scale = fn / sqrt((double)n);
+  if (!(scale > 0.0)) scale = 1.0;
+  int k = 0;
+  double rel;
+  for (;;) {
+    residual_d(phi, f, H.r, nx, ny, nz, level_coeff(h, 0), bc);
+    const double rn = norm2_d(H.r, n);
+    rel = fn > 0.0 ? rn / fn : rn;
+    if (!(rel >= tol) || k >= max_cycles) break;
+    for (size_t q = 0; q < n; ++q) {
+      H.ff[0][q] = (float)(H.r[q] / scale);
+      H.phif[0][q] = 0.0f;
+    }
+    vcycle_f(&H, 0, h, bc, nu1, nu2, (float)omega, NULL);
+    for (size_t q = 0; q < n; ++q) phi[q] = phi[q] + scale * (double)H.phif[0][q];
+    ++k;
+    const double next = rn / sqrt((double)n);
+    if (next > 0.0) scale = next;
+  }
+  if (rel_res_out) *rel_res_out = rel;
+  hier_free(&H);
+  return k;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* E-field and Coulomb force (Sec. 2.4, Eq. ElectrostatForce; D3Q7 central differences).       */
+
+/* phi at a neighbour of (i,j,k) along axis a (0,1,2) in direction dir (-1/+1); outside the
+ * domain it is the ghost value of the face BC: Dirichlet 2g - phi, Neumann phi + h g. */
+static double phi_nb(const double* phi, int i, int j, int k, int nx, int ny, int nz, int a, int dir,
+                     double h, const int* bc, const double* bcv) {
+  int q[3] = {i, j, k};
+  const int n[3] = {nx, ny, nz};
+  q[a] += dir;
+  const double here = phi[idx3(i, j, k, nx, ny)];
+  if (q[a] < 0 || q[a] >= n[a]) {
+    const int face = 2 * a + (dir > 0 ? 1 : 0);
+    if (bc[face] == BC_DIRICHLET) return 2.0 * bcv[face] - here;
+    return here + h * bcv[face];
+  }
+  return phi[idx3(q[0], q[1], q[2], nx, ny)];
+}
+
+/* E = -grad phi, E_a(i) = -(phi(i + e_a) - phi(i - e_a)) / (2h); out is [3][N] (SoA). */
+void ccmg_or_efield(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
+                    const double* bcv) {
+  const size_t n = (size_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        for (int a = 0; a < 3; ++a) {
+          const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
+          const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+          E[(size_t)a * n + p] = -(up - dn) / (2.0 * h);
+        }
+      }
+}
+
+/* Subsampled overlap count of sphere (centre c, radius R) with cell (i,j,k): the cell is cut
+ * into sf^3 equal sub-cells and a sub-cell counts when its centre x satisfies |x - c|^2 <= R^2
+ * (Sec. 2.4, "Subsampling"; sf = 1 is the plain cell-centre mapping of Sec. 2.2). Sub-cell
+ * centre coordinate: (i + (2m+1)/(2 sf)) * h. */
+static int overlap_count(int i, int j, int k, double h, const double* c, double R, int sf) {
+  int cnt = 0;
+  const double R2 = R * R;
+  for (int mk = 0; mk < sf; ++mk) {
+    const double z = ((double)k + (double)(2 * mk + 1) / (double)(2 * sf)) * h;
+    const double dz = z - c[2];
+    for (int mj = 0; mj < sf; ++mj) {
+      const double y = ((double)j + (double)(2 * mj + 1) / (double)(2 * sf)) * h;
+      const double dy = y - c[1];
+      for (int mi = 0; mi < sf; ++mi) {
+        const double x = ((double)i + (double)(2 * mi + 1) / (double)(2 * sf)) * h;
+        const double dx = x - c[0];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 <= R2) ++cnt;
+      }
+    }
+  }
+  return cnt;
+}
+
+/* Cell range [lo, hi] along one axis that can touch a sphere (all other cells have count 0). */
+static void cell_range(double c, double R, double h, int n, int* lo, int* hi) {
+  int a = (int)floor((c - R) / h) - 1;
+  int b = (int)floor((c + R) / h) + 1;
+  if (a < 0) a = 0;
+  if (b > n - 1) b = n - 1;
+  *lo = a;
+  *hi = b;
+}
+
+/* Volume-overlap weight w_{s,b} = count / sf^3 of sphere s in cell b. */
+static double overlap_weight(int i, int j, int k, double h, const double* c, double R, int sf) {
+  const int cnt = overlap_count(i, j, k, h, c, R, sf);
+  return (double)cnt / (double)(sf * sf * sf);
+}
+
+/* Charge density field: rho(b) = sum_s density_s * w_{s,b} (spheres in index order). */
+void ccmg_or_sphere_density(double* rho, int nx, int ny, int nz, double h, int P, const double* centers,
+                            const double* radius, const double* density, int sf) {
+  memset(rho, 0, (size_t)nx * ny * nz * sizeof(double));
+  for (int s = 0; s < P; ++s) {
+    const double* c = centers + 3 * s;
+    int lo[3], hi[3];
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const int cnt = overlap_count(i, j, k, h, c, radius[s], sf);
+          if (cnt == 0) continue;
+          const size_t p = idx3(i, j, k, nx, ny);
+          rho[p] = rho[p] + density[s] * ((double)cnt / (double)(sf * sf * sf));
+        }
+  }
+}
+
+/* Adjoint of the density map: g_s += sum_b w_{s,b} gfield(b). */
+void ccmg_or_sphere_density_adjoint(const double* gfield, double* gdensity, int nx, int ny, int nz,
+                                    double h, int P, const double* centers, const double* radius, int sf) {
+  for (int s = 0; s < P; ++s) {
+    const double* c = centers + 3 * s;
+    int lo[3], hi[3];
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    double acc = 0.0;
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
+          if (w == 0.0) continue;
+          acc = acc + w * gfield[idx3(i, j, k, nx, ny)];
+        }
+    gdensity[s] = gdensity[s] + acc;
+  }
+}
+
+/* Coulomb force on each sphere (Eq. ElectrostatForce with E = -grad phi):
+ *   F_s = h^3 * sum_b w_{s,b} density_s E(x_b),
+ * E by the central differences of ccmg_or_efield. forces is [P][3]. */
+void ccmg_or_force_gather(const double* phi, int nx, int ny, int nz, double h, const int* bc,
+                          const double* bcv, int P, const double* centers, const double* radius,
+                          const double* density, int sf, double* forces) {
+  const double h3 = h * h * h;
+  for (int s = 0; s < P; ++s) {
+    const double* c = centers + 3 * s;
+    int lo[3], hi[3];
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    double F[3] = {0.0, 0.0, 0.0};
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
+          if (w == 0.0) continue;
+          for (int a = 0; a < 3; ++a) {
+            const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
+            const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+            const double Ea = -(up - dn) / (2.0 * h);
+            F[a] = F[a] + w * Ea;
+          }
+        }
+    for (int a = 0; a < 3; ++a) forces[3 * s + a] = h3 * density[s] * F[a];
+  }
+}
+
+/* Adjoint of ccmg_or_force_gather for J = sum_{s,a} wF[s][a] * F_s[a]:
+ *   gphi   (N)  += dJ/dphi      (scatter of the central differences, ghosts included)
+ *   gdens  (P)  += dJ/ddensity_s through the explicit density factor
+ *   gbc    (6)  += dJ/dbc_value through the ghost values used by the differences. */
+void ccmg_or_force_gather_adjoint(const double* phi, int nx, int ny, int nz, double h, const int* bc,
+                                  const double* bcv, int P, const double* centers, const double* radius,
+                                  const double* density, int sf, const double* wF, double* gphi,
+                                  double* gdens, double* gbc) {
+  const double h3 = h * h * h;
+  const int n[3] = {nx, ny, nz};
+  for (int s = 0; s < P; ++s) {
+    const double* c = centers + 3 * s;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    double Fsum[3] = {0.0, 0.0, 0.0};
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
+          if (w == 0.0) continue;
+          const size_t p = idx3(i, j, k, nx, ny);
+          for (int a = 0; a < 3; ++a) {
+            const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
+            const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+            Fsum[a] = Fsum[a] + w * (-(up - dn) / (2.0 * h));
+            /* dJ/dE_a(b) = wF[s][a] * h3 * density_s * w; E_a = -(up - dn)/(2h). */
+            const double gE = wF[3 * s + a] * h3 * density[s] * w;
+            const double g_up = -gE / (2.0 * h);
+            const double g_dn = +gE / (2.0 * h);
+            const int cell[3] = {i, j, k};
+            for (int side = 0; side < 2; ++side) {
+              const int dir = side == 0 ? +1 : -1;
+              const double g = side == 0 ? g_up : g_dn;
+              int qn[3] = {cell[0], cell[1], cell[2]};
+              qn[a] += dir;
+              if (qn[a] < 0 || qn[a] >= n[a]) {
+                const int face = 2 * a + (dir > 0 ? 1 : 0);
+                if (bc[face] == BC_DIRICHLET) {
+                  gbc[face] = gbc[face] + 2.0 * g;
+                  gphi[p] = gphi[p] - g;
+                } else {
+                  gbc[face] = gbc[face] + h * g;
+                  gphi[p] = gphi[p] + g;
+                }
+              } else {
+                const size_t pn = idx3(qn[0], qn[1], qn[2], nx, ny);
+                gphi[pn] = gphi[pn] + g;
+              }
+            }
+          }
+        }
+    for (int a = 0; a < 3; ++a) gdens[s] = gdens[s] + wF[3 * s + a] * h3 * Fsum[a];
+  }
+}
