@@ -1,0 +1,172 @@
+/* ccmg.h -- C ABI of the GB300 cell-centred multigrid electrostatics library (libccmg.so).
+ *
+ * Solves the finite-volume Poisson problem of Bartuschat & Ruede (arXiv 1410.6609),
+ *     -lap(phi) = rho / eps            (Sec. 2.4, Eq. Poisson)
+ * on a uniform grid of nx*ny*nz cubic cells of size h, with Dirichlet or Neumann conditions on
+ * each of the six walls folded into stencil and right-hand side (Sec. 2.4, "Boundary
+ * conditions"), by the cell-centred geometric multigrid of Sec. 3 / Sec. 4.3 (red-black
+ * Gauss-Seidel, averaging restriction, constant prolongation with a x2 magnified correction,
+ * Galerkin coarse operators, CG on the coarsest grid), iterated until the L2 norm of the
+ * residual drops below a tolerance (Algorithm 1). It then evaluates the E-field by central
+ * differences and the Coulomb force on charged spheres (Eq. ElectrostatForce) with subsampled
+ * volume overlap (Sec. 2.4, "Subsampling").
+ *
+ * Conventions shared by every entry point
+ *   - Fields are dense arrays of nx*ny*nz doubles, x fastest: index i + nx*(j + ny*k); cell
+ *     (i,j,k) has its centre at ((i+1/2)h, (j+1/2)h, (k+1/2)h).
+ *   - Faces are numbered 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z. A Dirichlet value is the potential on
+ *     the face; a Neumann value is the outward normal derivative of phi on the face.
+ *   - Pointers named d_* are DEVICE memory, h_* are HOST memory. All are borrowed for the
+ *     duration of the call only; the context copies what it keeps.
+ *   - Work is enqueued on the stream given to mg_create (NULL = the legacy default stream) in
+ *     call order. Only calls that return host scalars (mg_solve, mg_residual, the *_host
+ *     calls) synchronise with that stream.
+ *   - Every call returns a status; none aborts. mg_last_error() gives a message for the last
+ *     failing call on a context. A NULL context gives MG_ERR_INVALID.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef CCMG_H
+#define CCMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,       /* bad argument or state */
+  MG_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  MG_ERR_OOM = 3,           /* device allocation failed */
+  MG_ERR_NOT_CONVERGED = 4, /* max_cycles reached, or NaN/Inf residual */
+  MG_ERR_DIVERGED = 5,      /* residual grew by more than 1e3 over its starting value */
+  MG_ERR_TIMEOUT = 6        /* a bounded device-side wait ran out */
+} mg_status;
+
+typedef enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1 } mg_bc;
+
+/* MG_FP64: every operation in double precision.
+ * MG_MIXED: FP64 defect correction around single-precision V-cycles. The outer residual, the
+ *   solution update and the coarsest-grid CG are double; smoothing, restriction and
+ *   prolongation are float. (Not in the paper; the cycle itself is the paper's.) */
+typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_prec;
+
+typedef struct {
+  int nx, ny, nz;        /* cells per axis; each >= 4 and even */
+  double h;              /* cell size (> 0) */
+  int bc_type[6];        /* mg_bc per face; all-Neumann is refused (singular) */
+  double bc_value[6];    /* Dirichlet potential / Neumann outward derivative per face */
+  int nu1, nu2;          /* pre- and post-smoothing sweeps (V(nu1,nu2)); 0..16, nu2 >= 1 */
+  double cgc_weight;     /* magnification of the coarse-grid correction (Sec. 3: about 2) */
+  int prec;              /* mg_prec */
+  double eps;            /* permittivity (> 0) */
+} mg_params;
+
+/* Fills p with the defaults: V(2,2), cgc_weight 2, MG_FP64, eps 1, all walls Dirichlet 0. */
+void mg_default_params(mg_params* p, int nx, int ny, int nz, double h);
+
+/* Create a solver context: validates p, builds the level hierarchy (halve every dimension
+ * while all are even and their halves are >= 3, Sec. 3), allocates every level on the current
+ * device and captures nothing yet. The coarsest grid must have at most 4096 cells.
+ * stream is a cudaStream_t (NULL = legacy default stream). */
+mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out);
+mg_status mg_destroy(mg_ctx* ctx);
+const char* mg_last_error(const mg_ctx* ctx);
+
+/* Hierarchy introspection: number of levels and the dimensions of level l (0 = finest). */
+int mg_num_levels(const mg_ctx* ctx);
+mg_status mg_level_dims(const mg_ctx* ctx, int level, int* h_dims3);
+
+/* Replace the six wall values (host array of 6 doubles). Takes effect at the next
+ * mg_set_rhs, mg_efield, mg_force_gather and mg_force_gather_adjoint call. */
+mg_status mg_set_bc_values(mg_ctx* ctx, const double* h_bc_value6);
+
+/* Right-hand side from a charge density: f = rho/eps, then adapted to the wall values once
+ * on the finest grid (Sec. 2.4 and Sec. 4.3: Dirichlet face cells += 2 g / h^2, Neumann face
+ * cells += g / h). d_rho: nx*ny*nz doubles. */
+mg_status mg_set_rhs(mg_ctx* ctx, const double* d_rho);
+/* Right-hand side f of A phi = f taken as is (no 1/eps, no wall terms): used for adjoint
+ * solves, whose wall conditions are homogeneous. d_f: nx*ny*nz doubles. */
+mg_status mg_set_rhs_f(mg_ctx* ctx, const double* d_f);
+
+/* Start value of the iteration (warm start, Sec. 6.1: later time steps reuse the previous
+ * potential). d_phi NULL sets zero. */
+mg_status mg_set_solution(mg_ctx* ctx, const double* d_phi);
+mg_status mg_get_solution(mg_ctx* ctx, double* d_phi);
+
+/* ncycles V(nu1,nu2)-cycles (Sec. 3, Sec. 4.3) on the current right-hand side and solution.
+ * In MG_MIXED mode one cycle is one outer defect-correction step. Stream-ordered; no sync. */
+mg_status mg_vcycle(mg_ctx* ctx, int ncycles);
+
+/* Algorithm 1: while ||f - A phi||_2 / ||f||_2 >= rel_tol and fewer than max_cycles cycles:
+ * one cycle. Writes the cycle count and the final relative residual (host pointers, either
+ * may be NULL). Returns MG_ERR_NOT_CONVERGED if max_cycles is reached first or the residual
+ * is not finite, MG_ERR_DIVERGED if it grows above 1e3 times its starting value. */
+mg_status mg_solve(mg_ctx* ctx, double rel_tol, int max_cycles, int* h_cycles, double* h_rel_res);
+
+/* Relative residual ||f - A phi||_2 / ||f||_2 of the current solution (host scalar), and, if
+ * d_r is not NULL, the residual field f - A phi itself (nx*ny*nz doubles). */
+mg_status mg_residual(mg_ctx* ctx, double* h_rel_res, double* d_r);
+
+/* E = -grad(phi) by central differences (D3Q7), with the wall ghost values
+ * (Dirichlet 2 g - phi, Neumann phi + h g). d_E: 3 arrays of nx*ny*nz doubles (Ex, Ey, Ez). */
+mg_status mg_efield(mg_ctx* ctx, double* d_E);
+
+/* Charge density of P spheres with subsampling factor sf (1..8): each cell is split into sf^3
+ * sub-cells and rho(cell) = sum_s density_s * (sub-cells whose centre lies in sphere s) / sf^3
+ * (Sec. 2.4, "Subsampling"). d_centers: P*3 doubles (x,y,z); d_radius, d_density: P doubles.
+ * d_rho (nx*ny*nz doubles) is overwritten. */
+mg_status mg_sphere_density(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
+                            const double* d_density, int sf, double* d_rho);
+
+/* Coulomb force on each sphere, F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce,
+ * E by the central differences of mg_efield, w the subsampled overlap). d_forces: P*3 doubles. */
+mg_status mg_force_gather(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
+                          const double* d_density, int sf, double* d_forces);
+
+/* Adjoints for J = sum_{s,a} wF[s][a] F_s[a] (not in the paper). All outputs are overwritten.
+ *   mg_force_gather_adjoint: d_gphi (N) = dJ/dphi, d_gdensity (P) = dJ/ddensity through the
+ *     explicit density factor, d_gbc (6, device) = dJ/dbc_value through the ghost values.
+ *   mg_sphere_density_adjoint: d_gdensity[s] = sum_b w_{s,b} d_gfield[b].
+ *   mg_rhs_adjoint: given lambda = dJ/df, d_grho = lambda / eps and d_gbc (6, device) =
+ *     sum over each face's cells of lambda * (2/h^2 Dirichlet, 1/h Neumann). */
+mg_status mg_force_gather_adjoint(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
+                                  const double* d_density, int sf, const double* d_wF, double* d_gphi,
+                                  double* d_gdensity, double* d_gbc);
+mg_status mg_sphere_density_adjoint(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
+                                    int sf, const double* d_gfield, double* d_gdensity);
+mg_status mg_rhs_adjoint(mg_ctx* ctx, const double* d_lambda, double* d_grho, double* d_gbc);
+
+/* One electrostatics step with HOST buffers (Algorithm 1, the potential part): copy the
+ * spheres in, set the right-hand side from their subsampled charge, solve to rel_tol from the
+ * current solution (warm start), compute the force on every sphere and copy it out.
+ * h_forces: P*3 doubles; h_cycles / h_rel_res may be NULL. Synchronises. */
+mg_status mg_step_host(mg_ctx* ctx, int P, const double* h_centers, const double* h_radius,
+                       const double* h_density, int sf, double rel_tol, int max_cycles, double* h_forces,
+                       int* h_cycles, double* h_rel_res);
+
+/* ----------------------------------------------------------------------------------------- */
+/* Level-wise operations, for verifying each kernel on its own. level 0 is the finest.
+ * Level fields are exchanged in natural (x-fastest) order, in double, whatever the internal
+ * layout and precision. which: 0 = solution/correction phi_l, 1 = right-hand side f_l.
+ * In MG_MIXED mode these address the single-precision hierarchy (values rounded to float). */
+mg_status mg_level_set(mg_ctx* ctx, int level, int which, const double* d_in);
+mg_status mg_level_get(mg_ctx* ctx, int level, int which, double* d_out);
+/* One red (colour 0, i+j+k even) or black (colour 1) Gauss-Seidel half-sweep on level l. */
+mg_status mg_op_smooth(mg_ctx* ctx, int level, int colour);
+/* f_{l+1} = averaging restriction of (f_l - A_l phi_l). */
+mg_status mg_op_residual_restrict(mg_ctx* ctx, int level);
+/* phi_l += cgc_weight * constant prolongation of phi_{l+1}. */
+mg_status mg_op_prolong_correct(mg_ctx* ctx, int level);
+/* CG on the coarsest level: phi_L = A_L^-1 f_L (rtol 1e-14, at most 2 N_L iterations);
+ * h_iters (may be NULL) receives the iteration count. Synchronises. */
+mg_status mg_op_coarse_solve(mg_ctx* ctx, int* h_iters);
+
+/* Number of kernels this context has enqueued since creation (graph nodes included). */
+long long mg_kernel_launches(const mg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCMG_H */

@@ -1,0 +1,661 @@
+// ccmg_api.cu -- host side of libccmg: the C ABI declared in include/ccmg.h.
+//
+// A context owns the level hierarchy on one device (Sec. 4.3: the multigrid solver allocates all
+// coarse-grid data itself), the wall conditions and a few device scalars. The V-cycle of Sec. 3 /
+// Sec. 4.3 is enqueued as a fixed kernel sequence, captured once into a CUDA graph on a private
+// stream and replayed on the caller's stream; the termination test of Algorithm 1 is a second,
+// small graph (residual norm + fixed-order reduction) followed by one 8-byte read-back.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/ccmg.h"
+#include "ccmg_internal.cuh"
+
+using namespace ccmg;
+
+namespace {
+
+enum Slot { S_GSUM = 0, S_RSUM = 1, S_REL = 2, S_SCALE = 3, S_INV_SCALE = 4, S_COUNT = 8 };
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct mg_ctx {
+  mg_params p{};
+  cudaStream_t stream = nullptr;  // caller's stream
+  cudaStream_t cap = nullptr;     // private stream used only for graph capture
+  int L = 0;
+  Geom geo[kMaxLevels]{};
+  double* x64[kMaxLevels]{};
+  double* g64[kMaxLevels]{};
+  float* x32[kMaxLevels]{};
+  float* g32[kMaxLevels]{};
+  double* partials = nullptr;
+  double* scal = nullptr;
+  double* h_pin = nullptr;
+  int* d_iters = nullptr;
+  InvDiag<double> inv64{};
+  InvDiag<float> inv32{};
+  FaceBC bc{};
+  cudaGraphExec_t g_cycle = nullptr;
+  cudaGraphExec_t g_resid = nullptr;
+  long long n_cycle = 0, n_resid = 0;  // kernel nodes per graph
+  long long launches = 0;
+  double* d_rho = nullptr;  // step_host scratch: density field
+  double* d_sph = nullptr;  // step_host scratch: 8*P doubles (centres, radius, density, forces)
+  int sph_cap = 0;
+  std::string err;
+};
+
+namespace {
+
+mg_status fail(mg_ctx* c, mg_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+mg_status cuda_fail(mg_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+bool mixed(const mg_ctx* c) { return c->p.prec == MG_MIXED; }
+long long cells(const Geom& G) { return G.packed ? 2 * G.csz : G.csz; }
+double level_coeff(const mg_ctx* c, int l) { return 1.0 / (std::ldexp(1.0, l) * c->p.h * c->p.h); }
+
+void free_all(mg_ctx* c) {
+  if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
+  if (c->g_resid) cudaGraphExecDestroy(c->g_resid);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    cudaFree(c->x64[l]);
+    cudaFree(c->g64[l]);
+    cudaFree(c->x32[l]);
+    cudaFree(c->g32[l]);
+  }
+  cudaFree(c->partials);
+  cudaFree(c->scal);
+  cudaFree(c->d_iters);
+  cudaFree(c->d_rho);
+  cudaFree(c->d_sph);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+// ------------------------------------------------------------------------------------------
+// Enqueue helpers (usable inside stream capture)
+
+template <typename T>
+cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>& inv, int l, bool zero,
+                           cudaStream_t s, long long* nk) {
+  const Geom& G = c->geo[l];
+  cudaError_t e;
+  if (l == c->L - 1) {
+    const int n = G.nx * G.ny * G.nz;
+    ++*nk;
+    return launch_coarse_cg<T>(x[l], g[l], G, 1e-14, 2 * n, c->d_iters, s);
+  }
+  if (zero && c->p.nu1 == 0) {
+    e = cudaMemsetAsync(x[l], 0, sizeof(T) * (size_t)cells(G), s);
+    if (e != cudaSuccess) return e;
+  }
+  for (int it = 0; it < c->p.nu1; ++it) {
+    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 0, zero && it == 0, s)) != cudaSuccess) return e;
+    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s)) != cudaSuccess) return e;
+    *nk += 2;
+  }
+  if ((e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
+  ++*nk;
+  if ((e = enqueue_vcycle<T>(c, x, g, inv, l + 1, true, s, nk)) != cudaSuccess) return e;
+  if ((e = launch_prolong<T>(x[l], G, x[l + 1], c->geo[l + 1], (T)c->p.cgc_weight, c->p.nu2 >= 1, s)) != cudaSuccess)
+    return e;
+  ++*nk;
+  for (int it = 0; it < c->p.nu2; ++it) {
+    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s)) != cudaSuccess) return e;
+    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 0, false, s)) != cudaSuccess) return e;
+    *nk += 2;
+  }
+  return cudaSuccess;
+}
+
+// One cycle: FP64 V-cycle, or (mixed) single-precision V-cycle on the scaled residual that the
+// residual graph left in g32[0], followed by phi += scale * e and the next scale.
+cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk) {
+  if (!mixed(c)) return enqueue_vcycle<double>(c, c->x64, c->g64, c->inv64, 0, false, s, nk);
+  cudaError_t e = enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, true, s, nk);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_update_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s)) != cudaSuccess) return e;
+  if ((e = launch_set_scale(c->scal, S_RSUM, S_SCALE, (double)cells(c->geo[0]), s)) != cudaSuccess) return e;
+  *nk += 2;
+  return cudaSuccess;
+}
+
+// Termination quantity ||r|| / ||f|| into scal[S_REL]; in mixed mode also the scaled
+// single-precision residual for the next inner cycle.
+cudaError_t enqueue_resid(mg_ctx* c, int mode, double* out_natural, cudaStream_t s, long long* nk) {
+  int np = 0;
+  cudaError_t e = launch_resid_norm<double>(c->x64[0], c->g64[0], c->geo[0], c->partials, &np, mode,
+                                            level_coeff(c, 0), out_natural, mode == 2 ? c->g32[0] : nullptr,
+                                            c->scal + S_INV_SCALE, s);
+  if (e != cudaSuccess) return e;
+  *nk += 2;
+  return launch_finalize(c->partials, np, c->scal, S_RSUM, S_REL, S_GSUM, s);
+}
+
+template <typename F>
+mg_status capture(mg_ctx* c, cudaGraphExec_t* out, long long* nodes, F body, const char* what) {
+  if (*out) return MG_OK;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  long long nk = 0;
+  cudaError_t eb = body(c->cap, &nk);
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+  if (eb != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return cuda_fail(c, eb != cudaSuccess ? eb : ee, what);
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return cuda_fail(c, e, what);
+  }
+  *nodes = nk;
+  return MG_OK;
+}
+
+mg_status ensure_graphs(mg_ctx* c) {
+  mg_status st = capture(c, &c->g_cycle, &c->n_cycle,
+                         [c](cudaStream_t s, long long* nk) { return enqueue_cycle(c, s, nk); }, "capture cycle");
+  if (st != MG_OK) return st;
+  const int mode = mixed(c) ? 2 : 0;
+  return capture(c, &c->g_resid, &c->n_resid,
+                 [c, mode](cudaStream_t s, long long* nk) { return enqueue_resid(c, mode, nullptr, s, nk); },
+                 "capture residual");
+}
+
+mg_status run_graph(mg_ctx* c, cudaGraphExec_t g, long long nodes, const char* what) {
+  CK(cudaGraphLaunch(g, c->stream), what);
+  c->launches += nodes;
+  return MG_OK;
+}
+
+// Relative residual of the current state: run the residual graph, read scal[S_REL].
+mg_status read_rel(mg_ctx* c, double* rel) {
+  mg_status st = run_graph(c, c->g_resid, c->n_resid, "residual");
+  if (st != MG_OK) return st;
+  CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read residual");
+  CK(cudaStreamSynchronize(c->stream), "residual sync");
+  *rel = c->h_pin[0];
+  return MG_OK;
+}
+
+mg_status check_sph(mg_ctx* c, int P, const double* ctr, const double* rad, int sf) {
+  if (P < 0 || (P > 0 && (!ctr || !rad))) return fail(c, MG_ERR_INVALID, "invalid sphere arrays");
+  if (sf < 1 || sf > 8) return fail(c, MG_ERR_INVALID, "subsampling factor must be in 1..8");
+  return MG_OK;
+}
+
+}  // namespace
+
+// ============================================================================================
+
+extern "C" {
+
+void mg_default_params(mg_params* p, int nx, int ny, int nz, double h) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->h = h;
+  for (int q = 0; q < 6; ++q) {
+    p->bc_type[q] = MG_BC_DIRICHLET;
+    p->bc_value[q] = 0.0;
+  }
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->cgc_weight = 2.0;
+  p->prec = MG_FP64;
+  p->eps = 1.0;
+}
+
+const char* mg_last_error(const mg_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
+  mg_ctx* c = nullptr;
+  if (!p || !out) return fail(c, MG_ERR_INVALID, "null argument");
+  *out = nullptr;
+  const int d[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; ++a)
+    if (d[a] < 4 || (d[a] % 2) != 0) return fail(c, MG_ERR_INVALID, "grid dimensions must be even and >= 4");
+  if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(c, MG_ERR_INVALID, "h must be positive");
+  if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(c, MG_ERR_INVALID, "eps must be positive");
+  bool all_neumann = true;
+  for (int q = 0; q < 6; ++q) {
+    if (p->bc_type[q] != MG_BC_DIRICHLET && p->bc_type[q] != MG_BC_NEUMANN)
+      return fail(c, MG_ERR_INVALID, "bc_type must be MG_BC_DIRICHLET or MG_BC_NEUMANN");
+    if (!std::isfinite(p->bc_value[q])) return fail(c, MG_ERR_INVALID, "bc_value must be finite");
+    if (p->bc_type[q] == MG_BC_DIRICHLET) all_neumann = false;
+  }
+  if (all_neumann) return fail(c, MG_ERR_INVALID, "all-Neumann walls give a singular problem");
+  if (p->nu1 < 0 || p->nu1 > 16 || p->nu2 < 1 || p->nu2 > 16)
+    return fail(c, MG_ERR_INVALID, "need 0 <= nu1 <= 16 and 1 <= nu2 <= 16");
+  if (!std::isfinite(p->cgc_weight)) return fail(c, MG_ERR_INVALID, "cgc_weight must be finite");
+  if (p->prec != MG_FP64 && p->prec != MG_MIXED) return fail(c, MG_ERR_INVALID, "prec must be MG_FP64 or MG_MIXED");
+
+  c = new mg_ctx();
+  c->p = *p;
+  c->stream = (cudaStream_t)stream;
+  for (int q = 0; q < 6; ++q) {
+    c->bc.type[q] = p->bc_type[q];
+    c->bc.value[q] = p->bc_value[q];
+  }
+  // level hierarchy: halve while every dimension is even and its half is >= 3 (Sec. 3)
+  int dims[3] = {p->nx, p->ny, p->nz};
+  for (;;) {
+    if (c->L >= kMaxLevels) break;
+    Geom& G = c->geo[c->L];
+    G.nx = dims[0];
+    G.ny = dims[1];
+    G.nz = dims[2];
+    for (int q = 0; q < 6; ++q) G.sh[q] = p->bc_type[q] == MG_BC_DIRICHLET ? 1 : -1;
+    ++c->L;
+    bool ok = true;
+    for (int a = 0; a < 3; ++a)
+      if ((dims[a] % 2) != 0 || dims[a] / 2 < 3) ok = false;
+    if (!ok) break;
+    for (int a = 0; a < 3; ++a) dims[a] /= 2;
+  }
+  for (int l = 0; l < c->L; ++l) {
+    Geom& G = c->geo[l];
+    G.packed = (l < c->L - 1) ? 1 : 0;
+    G.hx = G.nx / 2;
+    G.csz = G.packed ? (long long)G.hx * G.ny * G.nz : (long long)G.nx * G.ny * G.nz;
+  }
+  const Geom& Gc = c->geo[c->L - 1];
+  if ((long long)Gc.nx * Gc.ny * Gc.nz > kMaxCoarseCells) {
+    delete c;
+    return fail(nullptr, MG_ERR_INVALID,
+                "coarsest grid has more than 4096 cells: choose dimensions with more factors of two");
+  }
+  for (int d6 = -3; d6 <= 3; ++d6) {
+    c->inv64.v[d6 + 3] = 1.0 / (double)(6 + d6);
+    c->inv32.v[d6 + 3] = 1.0f / (float)(6 + d6);
+  }
+
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  for (int l = 0; l < c->L; ++l) {
+    const size_t n = (size_t)cells(c->geo[l]);
+    if (!mixed(c) || l == 0) {
+      alloc((void**)&c->x64[l], n * sizeof(double));
+      alloc((void**)&c->g64[l], n * sizeof(double));
+    }
+    if (mixed(c)) {
+      alloc((void**)&c->x32[l], n * sizeof(float));
+      alloc((void**)&c->g32[l], n * sizeof(float));
+    }
+  }
+  alloc((void**)&c->partials, kMaxPartials * sizeof(double));
+  alloc((void**)&c->scal, S_COUNT * sizeof(double));
+  alloc((void**)&c->d_iters, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = prepare_coarse_cg();
+  if (e != cudaSuccess) {
+    const bool oom = (e == cudaErrorMemoryAllocation);
+    std::string msg = std::string("mg_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return fail(nullptr, oom ? MG_ERR_OOM : MG_ERR_CUDA, msg);
+  }
+  // zero state: phi = 0, f = 0, scalars 0 (scale 1)
+  for (int l = 0; l < c->L; ++l) {
+    const size_t n = (size_t)cells(c->geo[l]);
+    if (c->x64[l]) e = cudaMemsetAsync(c->x64[l], 0, n * sizeof(double), c->stream);
+    if (e == cudaSuccess && c->g64[l]) e = cudaMemsetAsync(c->g64[l], 0, n * sizeof(double), c->stream);
+    if (e == cudaSuccess && c->x32[l]) e = cudaMemsetAsync(c->x32[l], 0, n * sizeof(float), c->stream);
+    if (e == cudaSuccess && c->g32[l]) e = cudaMemsetAsync(c->g32[l], 0, n * sizeof(float), c->stream);
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->scal, 0, S_COUNT * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("mg_create: ") + cudaGetErrorString(e);
+    free_all(c);
+    delete c;
+    return fail(nullptr, MG_ERR_CUDA, msg);
+  }
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_destroy(mg_ctx* c) {
+  if (!c) return MG_ERR_INVALID;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return MG_OK;
+}
+
+int mg_num_levels(const mg_ctx* c) { return c ? c->L : 0; }
+
+mg_status mg_level_dims(const mg_ctx* c, int level, int* dims) {
+  if (!c || !dims || level < 0 || level >= c->L) return MG_ERR_INVALID;
+  dims[0] = c->geo[level].nx;
+  dims[1] = c->geo[level].ny;
+  dims[2] = c->geo[level].nz;
+  return MG_OK;
+}
+
+long long mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : 0; }
+
+mg_status mg_set_bc_values(mg_ctx* c, const double* v) {
+  if (!c) return MG_ERR_INVALID;
+  if (!v) return fail(c, MG_ERR_INVALID, "null bc values");
+  for (int q = 0; q < 6; ++q) {
+    if (!std::isfinite(v[q])) return fail(c, MG_ERR_INVALID, "bc values must be finite");
+  }
+  for (int q = 0; q < 6; ++q) {
+    c->bc.value[q] = v[q];
+    c->p.bc_value[q] = v[q];
+  }
+  return MG_OK;
+}
+
+static mg_status set_rhs_impl(mg_ctx* c, const double* d_rho, int raw) {
+  if (!c) return MG_ERR_INVALID;
+  if (!d_rho) return fail(c, MG_ERR_INVALID, "null right-hand side");
+  const Geom& G = c->geo[0];
+  CK(launch_set_rhs<double>(c->g64[0], G, d_rho, 1.0 / c->p.eps, c->p.h, c->bc, raw, c->stream), "set_rhs");
+  int np = 0;
+  CK(launch_sumsq<double>(c->g64[0], cells(G), c->partials, &np, c->stream), "set_rhs norm");
+  CK(launch_finalize(c->partials, np, c->scal, S_GSUM, -1, 0, c->stream), "set_rhs norm");
+  CK(launch_set_scale(c->scal, S_GSUM, S_SCALE, (double)cells(G), c->stream), "set_rhs scale");
+  c->launches += 4;
+  return MG_OK;
+}
+
+mg_status mg_set_rhs(mg_ctx* c, const double* d_rho) { return set_rhs_impl(c, d_rho, 0); }
+mg_status mg_set_rhs_f(mg_ctx* c, const double* d_f) { return set_rhs_impl(c, d_f, 1); }
+
+mg_status mg_set_solution(mg_ctx* c, const double* d_phi) {
+  if (!c) return MG_ERR_INVALID;
+  CK(launch_pack<double>(c->x64[0], c->geo[0], d_phi, 1.0, c->stream), "set_solution");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_get_solution(mg_ctx* c, double* d_phi) {
+  if (!c) return MG_ERR_INVALID;
+  if (!d_phi) return fail(c, MG_ERR_INVALID, "null output");
+  CK(launch_unpack<double>(d_phi, c->x64[0], c->geo[0], 1.0, c->stream), "get_solution");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_vcycle(mg_ctx* c, int ncycles) {
+  if (!c) return MG_ERR_INVALID;
+  if (ncycles < 0) return fail(c, MG_ERR_INVALID, "ncycles must be >= 0");
+  mg_status st = ensure_graphs(c);
+  if (st != MG_OK) return st;
+  for (int k = 0; k < ncycles; ++k) {
+    if (mixed(c) && (st = run_graph(c, c->g_resid, c->n_resid, "residual")) != MG_OK) return st;
+    if ((st = run_graph(c, c->g_cycle, c->n_cycle, "cycle")) != MG_OK) return st;
+  }
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_ctx* c, double tol, int max_cycles, int* h_cycles, double* h_rel) {
+  if (!c) return MG_ERR_INVALID;
+  if (!(tol >= 0.0) || max_cycles < 0) return fail(c, MG_ERR_INVALID, "need tol >= 0 and max_cycles >= 0");
+  mg_status st = ensure_graphs(c);
+  if (st != MG_OK) return st;
+  int k = 0;
+  double rel = 0.0, rel0 = -1.0;
+  mg_status out = MG_OK;
+  for (;;) {
+    if ((st = read_rel(c, &rel)) != MG_OK) return st;
+    if (!std::isfinite(rel)) {
+      out = fail(c, MG_ERR_NOT_CONVERGED, "residual is not finite");
+      break;
+    }
+    if (rel0 < 0.0) rel0 = rel;
+    if (rel > 1e3 * rel0 && rel > tol) {
+      out = fail(c, MG_ERR_DIVERGED, "residual grew by more than 1e3");
+      break;
+    }
+    if (!(rel >= tol)) break;
+    if (k >= max_cycles) {
+      out = fail(c, MG_ERR_NOT_CONVERGED, "max_cycles reached before the tolerance");
+      break;
+    }
+    if ((st = run_graph(c, c->g_cycle, c->n_cycle, "cycle")) != MG_OK) return st;
+    ++k;
+  }
+  if (h_cycles) *h_cycles = k;
+  if (h_rel) *h_rel = rel;
+  return out;
+}
+
+mg_status mg_residual(mg_ctx* c, double* h_rel, double* d_r) {
+  if (!c) return MG_ERR_INVALID;
+  long long nk = 0;
+  CK(enqueue_resid(c, d_r ? 1 : 0, d_r, c->stream, &nk), "residual");
+  c->launches += nk;
+  CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "residual");
+  CK(cudaStreamSynchronize(c->stream), "residual sync");
+  if (h_rel) *h_rel = c->h_pin[0];
+  return MG_OK;
+}
+
+mg_status mg_efield(mg_ctx* c, double* d_E) {
+  if (!c) return MG_ERR_INVALID;
+  if (!d_E) return fail(c, MG_ERR_INVALID, "null output");
+  CK(launch_efield(c->x64[0], c->geo[0], c->p.h, c->bc, d_E, c->stream), "efield");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_sphere_density(mg_ctx* c, int P, const double* ctr, const double* rad, const double* dens, int sf,
+                            double* d_rho) {
+  if (!c) return MG_ERR_INVALID;
+  mg_status st = check_sph(c, P, ctr, rad, sf);
+  if (st != MG_OK) return st;
+  if (!d_rho || (P > 0 && !dens)) return fail(c, MG_ERR_INVALID, "null argument");
+  Spheres sp{P, ctr, rad, dens};
+  CK(launch_sphere_density(c->geo[0], c->p.h, sp, sf, d_rho, c->stream), "sphere_density");
+  c->launches += P > 0 ? 1 : 0;
+  return MG_OK;
+}
+
+mg_status mg_force_gather(mg_ctx* c, int P, const double* ctr, const double* rad, const double* dens, int sf,
+                          double* d_F) {
+  if (!c) return MG_ERR_INVALID;
+  mg_status st = check_sph(c, P, ctr, rad, sf);
+  if (st != MG_OK) return st;
+  if ((P > 0 && (!dens || !d_F))) return fail(c, MG_ERR_INVALID, "null argument");
+  Spheres sp{P, ctr, rad, dens};
+  CK(launch_force_gather(c->x64[0], c->geo[0], c->p.h, c->bc, sp, sf, d_F, c->stream), "force_gather");
+  c->launches += P > 0 ? 1 : 0;
+  return MG_OK;
+}
+
+mg_status mg_force_gather_adjoint(mg_ctx* c, int P, const double* ctr, const double* rad, const double* dens, int sf,
+                                  const double* d_wF, double* d_gphi, double* d_gdens, double* d_gbc) {
+  if (!c) return MG_ERR_INVALID;
+  mg_status st = check_sph(c, P, ctr, rad, sf);
+  if (st != MG_OK) return st;
+  if (!d_gphi || !d_gbc || (P > 0 && (!dens || !d_wF || !d_gdens))) return fail(c, MG_ERR_INVALID, "null argument");
+  Spheres sp{P, ctr, rad, dens};
+  CK(launch_force_adjoint(c->x64[0], c->geo[0], c->p.h, c->bc, sp, sf, d_wF, d_gphi, d_gdens, d_gbc, c->stream),
+     "force_gather_adjoint");
+  c->launches += P > 0 ? 1 : 0;
+  return MG_OK;
+}
+
+mg_status mg_sphere_density_adjoint(mg_ctx* c, int P, const double* ctr, const double* rad, int sf,
+                                    const double* d_gfield, double* d_gdens) {
+  if (!c) return MG_ERR_INVALID;
+  mg_status st = check_sph(c, P, ctr, rad, sf);
+  if (st != MG_OK) return st;
+  if (P > 0 && (!d_gfield || !d_gdens)) return fail(c, MG_ERR_INVALID, "null argument");
+  Spheres sp{P, ctr, rad, nullptr};
+  CK(launch_density_adjoint(c->geo[0], c->p.h, sp, sf, d_gfield, d_gdens, c->stream), "sphere_density_adjoint");
+  c->launches += P > 0 ? 1 : 0;
+  return MG_OK;
+}
+
+mg_status mg_rhs_adjoint(mg_ctx* c, const double* d_lam, double* d_grho, double* d_gbc) {
+  if (!c) return MG_ERR_INVALID;
+  if (!d_lam || !d_grho || !d_gbc) return fail(c, MG_ERR_INVALID, "null argument");
+  CK(launch_rhs_adjoint(c->geo[0], c->p.h, 1.0 / c->p.eps, c->bc, d_lam, d_grho, d_gbc, c->stream), "rhs_adjoint");
+  c->launches += 2;
+  return MG_OK;
+}
+
+mg_status mg_step_host(mg_ctx* c, int P, const double* h_ctr, const double* h_rad, const double* h_dens, int sf,
+                       double tol, int max_cycles, double* h_F, int* h_cycles, double* h_rel) {
+  if (!c) return MG_ERR_INVALID;
+  mg_status st = check_sph(c, P, h_ctr, h_rad, sf);
+  if (st != MG_OK) return st;
+  if (P > 0 && (!h_dens || !h_F)) return fail(c, MG_ERR_INVALID, "null argument");
+  const Geom& G = c->geo[0];
+  if (!c->d_rho) CK(cudaMalloc((void**)&c->d_rho, sizeof(double) * (size_t)G.nx * G.ny * G.nz), "step scratch");
+  if (P > c->sph_cap) {
+    cudaFree(c->d_sph);
+    c->d_sph = nullptr;
+    c->sph_cap = 0;
+    CK(cudaMalloc((void**)&c->d_sph, sizeof(double) * 8 * (size_t)P), "step scratch");
+    c->sph_cap = P;
+  }
+  double* dc = c->d_sph;
+  double* dr = dc + 3 * (size_t)c->sph_cap;
+  double* dq = dr + c->sph_cap;
+  double* dF = dq + c->sph_cap;
+  if (P > 0) {
+    CK(cudaMemcpyAsync(dc, h_ctr, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, c->stream), "step copy");
+    CK(cudaMemcpyAsync(dr, h_rad, sizeof(double) * P, cudaMemcpyHostToDevice, c->stream), "step copy");
+    CK(cudaMemcpyAsync(dq, h_dens, sizeof(double) * P, cudaMemcpyHostToDevice, c->stream), "step copy");
+  }
+  if ((st = mg_sphere_density(c, P, dc, dr, dq, sf, c->d_rho)) != MG_OK) return st;
+  if ((st = mg_set_rhs(c, c->d_rho)) != MG_OK) return st;
+  mg_status solve_st = mg_solve(c, tol, max_cycles, h_cycles, h_rel);
+  if (solve_st != MG_OK && solve_st != MG_ERR_NOT_CONVERGED) return solve_st;
+  if (P > 0) {
+    if ((st = mg_force_gather(c, P, dc, dr, dq, sf, dF)) != MG_OK) return st;
+    CK(cudaMemcpyAsync(h_F, dF, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, c->stream), "step copy");
+  }
+  CK(cudaStreamSynchronize(c->stream), "step sync");
+  return solve_st;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Level-wise operations
+
+mg_status mg_level_set(mg_ctx* c, int level, int which, const double* d_in) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L || (which != 0 && which != 1) || !d_in)
+    return fail(c, MG_ERR_INVALID, "bad level, field or pointer");
+  const double scale = which == 0 ? 1.0 : 1.0 / level_coeff(c, level);
+  if (mixed(c))
+    CK(launch_pack<float>(which == 0 ? c->x32[level] : c->g32[level], c->geo[level], d_in, scale, c->stream),
+       "level_set");
+  else
+    CK(launch_pack<double>(which == 0 ? c->x64[level] : c->g64[level], c->geo[level], d_in, scale, c->stream),
+       "level_set");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_level_get(mg_ctx* c, int level, int which, double* d_out) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L || (which != 0 && which != 1) || !d_out)
+    return fail(c, MG_ERR_INVALID, "bad level, field or pointer");
+  const double scale = which == 0 ? 1.0 : level_coeff(c, level);
+  if (mixed(c))
+    CK(launch_unpack<float>(d_out, which == 0 ? c->x32[level] : c->g32[level], c->geo[level], scale, c->stream),
+       "level_get");
+  else
+    CK(launch_unpack<double>(d_out, which == 0 ? c->x64[level] : c->g64[level], c->geo[level], scale, c->stream),
+       "level_get");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L - 1 || (colour != 0 && colour != 1))
+    return fail(c, MG_ERR_INVALID, "smoothing needs a non-coarsest level and colour 0 or 1");
+  if (mixed(c))
+    CK(launch_smooth<float>(c->x32[level], c->g32[level], c->geo[level], c->inv32, colour, false, c->stream), "smooth");
+  else
+    CK(launch_smooth<double>(c->x64[level], c->g64[level], c->geo[level], c->inv64, colour, false, c->stream),
+       "smooth");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_op_residual_restrict(mg_ctx* c, int level) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "restriction needs a non-coarsest level");
+  if (mixed(c))
+    CK(launch_resid_restrict<float>(c->x32[level], c->g32[level], c->geo[level], c->g32[level + 1],
+                                    c->geo[level + 1], c->stream),
+       "residual_restrict");
+  else
+    CK(launch_resid_restrict<double>(c->x64[level], c->g64[level], c->geo[level], c->g64[level + 1],
+                                     c->geo[level + 1], c->stream),
+       "residual_restrict");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_op_prolong_correct(mg_ctx* c, int level) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "prolongation needs a non-coarsest level");
+  if (mixed(c))
+    CK(launch_prolong<float>(c->x32[level], c->geo[level], c->x32[level + 1], c->geo[level + 1],
+                             (float)c->p.cgc_weight, false, c->stream),
+       "prolong");
+  else
+    CK(launch_prolong<double>(c->x64[level], c->geo[level], c->x64[level + 1], c->geo[level + 1], c->p.cgc_weight,
+                              false, c->stream),
+       "prolong");
+  c->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
+  if (!c) return MG_ERR_INVALID;
+  const int l = c->L - 1;
+  const Geom& G = c->geo[l];
+  const int n = G.nx * G.ny * G.nz;
+  if (mixed(c))
+    CK(launch_coarse_cg<float>(c->x32[l], c->g32[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
+  else
+    CK(launch_coarse_cg<double>(c->x64[l], c->g64[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
+  c->launches += 1;
+  int it = 0;
+  CK(cudaMemcpyAsync(c->h_pin, c->d_iters, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "coarse_solve");
+  CK(cudaStreamSynchronize(c->stream), "coarse_solve");
+  std::memcpy(&it, c->h_pin, sizeof(int));
+  if (h_iters) *h_iters = it;
+  return MG_OK;
+}
+
+}  // extern "C"

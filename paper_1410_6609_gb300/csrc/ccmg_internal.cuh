@@ -1,0 +1,111 @@
+// ccmg_internal.cuh -- internal types and kernel launchers of libccmg (not part of the ABI).
+//
+// Storage of a multigrid level. Every level except the coarsest stores its cells in the
+// checkerboard-separated order that red-black Gauss-Seidel works in (Sec. 4.3: the unknowns are
+// rearranged in a checker-board manner so that each colour updates in parallel): two arrays per
+// field, one per colour, each of (nx/2) x ny x nz entries, x fastest. Cell (i,j,k) has colour
+// c = (i+j+k) & 1 and sits at index m = i/2 of row (j,k) of its colour's array; within the row,
+// i = 2m + s with s = (j+k+c) & 1. Then
+//   - its two x-neighbours are at m+s-1 and m+s of the other colour's row (j,k),
+//   - its four y/z-neighbours are at the same m in the other colour's rows (j+-1,k), (j,k+-1),
+// so a half-sweep reads one colour and writes the other with unit-stride, fully used lines.
+// The coarsest level (solved by CG, possibly with odd dimensions) is stored in natural order.
+//
+// Every level stores the scaled right-hand side g_l = f_l / c_l (c_l = 1/(2^l h^2) is the
+// coefficient of the Galerkin operator on level l), so the smoother is
+//   phi_i = (g_i + sum of neighbours) / (6 + d_i),
+// the scaled residual is r_i / c_l = g_i + sum - (6 + d_i) phi_i, and the averaging restriction
+// into the next level's scaled right-hand side is (1/4) * (sum of the 8 children's scaled
+// residuals): all level-to-level factors are powers of two.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccmg {
+
+constexpr int kMaxLevels = 24;
+constexpr int kMaxCoarseCells = 4096;
+
+struct Geom {
+  int nx, ny, nz;  // cells per axis
+  int hx;          // nx / 2 on packed levels
+  long long csz;   // entries per colour array (packed) or nx*ny*nz (natural)
+  int packed;      // 1: red/black arrays; 0: natural order
+  int sh[6];       // diagonal shift of each face (+1 Dirichlet, -1 Neumann)
+};
+
+template <typename T>
+struct InvDiag {
+  T v[7];  // 1 / (6 + d) for d = -3 .. 3
+};
+
+struct FaceBC {
+  int type[6];
+  double value[6];
+};
+
+// Kernel launchers (all enqueue on `s`; return cudaGetLastError()).
+template <typename T>
+cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv, int colour, bool zero_start,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong(T* x, const Geom& G, const T* ec, const Geom& Gc, T omega, bool red_only,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_cg(T* x, const T* b, const Geom& Gc, double rtol, int maxit, int* d_iters,
+                             cudaStream_t s);
+cudaError_t prepare_coarse_cg();
+
+// Scaled residual r~ = g + sum - (6+d) x over the finest level. Writes per-block partial sums
+// of r~^2 to `partials` (at most kMaxPartials) and, by mode:
+//   0: nothing else;
+//   1: r = r~ * c0 in natural order, double (d_out_natural);
+//   2: float(r~ * inv_scale[0]) into a packed float array of the same geometry (d_out_packed).
+constexpr int kMaxPartials = 4096;
+template <typename T>
+cudaError_t launch_resid_norm(const T* x, const T* g, const Geom& G, double* partials, int* nparts, int mode,
+                              double c0, double* out_natural, float* out_packed, const double* inv_scale,
+                              cudaStream_t s);
+// Sum of squares of a packed or natural field (||g||^2), same partial-sum protocol.
+template <typename T>
+cudaError_t launch_sumsq(const T* a, long long n, double* partials, int* nparts, cudaStream_t s);
+// Fixed-order sum of partials into scal[slot]; if slot_rel >= 0 also writes
+// scal[slot_rel] = sqrt(scal[slot]) / sqrt(scal[slot_ref]) (or sqrt(scal[slot]) if ref is 0).
+cudaError_t launch_finalize(const double* partials, int nparts, double* scal, int slot, int slot_rel, int slot_ref,
+                            cudaStream_t s);
+// scal[dst] = sqrt(scal[src] / n) if positive else 1; scal[dst+1] = 1 / scal[dst].
+cudaError_t launch_set_scale(double* scal, int src, int dst, double n, cudaStream_t s);
+
+// g = (rho/eps + wall terms) * h^2 written into a packed (or natural) level-0 array.
+template <typename T>
+cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_eps, double h, const FaceBC& bc,
+                           int raw, cudaStream_t s);
+// Natural-order double <-> level layout and precision.
+template <typename T>
+cudaError_t launch_pack(T* dst, const Geom& G, const double* src, double scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack(double* dst, const T* src, const Geom& G, double scale, cudaStream_t s);
+// x64 += scal[slot] * double(e32) elementwise over n entries.
+cudaError_t launch_update_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
+
+// Fields and forces (finest level, FP64 packed potential).
+struct Spheres {
+  int P;
+  const double* c;  // P*3
+  const double* r;  // P
+  const double* q;  // P (density), may be null where unused
+};
+cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, double* E, cudaStream_t s);
+cudaError_t launch_sphere_density(const Geom& G, double h, const Spheres& sp, int sf, double* rho, cudaStream_t s);
+cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
+                                double* F, cudaStream_t s);
+cudaError_t launch_force_adjoint(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
+                                 const double* wF, double* gphi, double* gdens, double* gbc, cudaStream_t s);
+cudaError_t launch_density_adjoint(const Geom& G, double h, const Spheres& sp, int sf, const double* gfield,
+                                   double* gdens, cudaStream_t s);
+cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* lam,
+                               double* grho, double* gbc, cudaStream_t s);
+
+}  // namespace ccmg

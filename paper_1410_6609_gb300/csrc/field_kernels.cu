@@ -1,0 +1,392 @@
+// field_kernels.cu -- E-field, charged-sphere density, Coulomb force and their adjoints (sm_103a).
+//
+// Sec. 2.4 of the paper: the force on a particle is F = -h^3 sum_b grad(phi)(x_b) rho(x_b)
+// (Eq. ElectrostatForce) with an O(h^2) finite-difference gradient; charges are mapped to cells by
+// subsampling each cell into sf^3 sub-cells and counting the sub-cell centres inside the sphere.
+// Here the gradient is the D3Q7 central difference, with wall ghost values Dirichlet 2g - phi and
+// Neumann phi + h g. The potential is read from the finest level's storage (packed colours, or
+// natural order for a single-level grid).
+//
+// The sub-cell inside test decides an integer count from floating point; it is evaluated with
+// explicitly rounded operations (no contraction) in the order (((x-cx)^2 + (y-cy)^2) + (z-cz)^2)
+// <= R^2, the sub-cell centre coordinate being (i + (2m+1)/(2 sf)) * h.
+#include "ccmg_internal.cuh"
+
+namespace ccmg {
+namespace {
+
+struct SubOff {
+  double o[8];  // (2m+1) / (2 sf), m < sf
+};
+
+__device__ __forceinline__ long long nat(const Geom& G, int i, int j, int k) {
+  return (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+}
+
+__device__ __forceinline__ double ld_phi(const double* __restrict__ x, const Geom& G, int i, int j, int k) {
+  if (G.packed) {
+    const int c = (i + j + k) & 1;
+    return __ldg(x + (long long)c * G.csz + ((long long)k * G.ny + j) * G.hx + (i >> 1));
+  }
+  return __ldg(x + nat(G, i, j, k));
+}
+
+// phi at the neighbour of (i,j,k) along axis a in direction dir, or the wall ghost value.
+__device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geom& G, int i, int j, int k, int a,
+                                         int dir, double here, double h, const FaceBC& bc) {
+  int q[3] = {i, j, k};
+  const int n[3] = {G.nx, G.ny, G.nz};
+  q[a] += dir;
+  if (q[a] < 0 || q[a] >= n[a]) {
+    const int face = 2 * a + (dir > 0 ? 1 : 0);
+    if (bc.type[face] == 0) return 2.0 * bc.value[face] - here;
+    return here + h * bc.value[face];
+  }
+  return ld_phi(x, G, q[0], q[1], q[2]);
+}
+
+// E_a = -(phi(+e_a) - phi(-e_a)) / (2h) at cell (i,j,k), a = 0..2.
+__device__ __forceinline__ void efield_at(const double* __restrict__ x, const Geom& G, int i, int j, int k, double h,
+                                          double inv2h, const FaceBC& bc, double E[3]) {
+  const double here = ld_phi(x, G, i, j, k);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double up = phi_nb(x, G, i, j, k, a, +1, here, h, bc);
+    const double dn = phi_nb(x, G, i, j, k, a, -1, here, h, bc);
+    E[a] = -((up - dn) * inv2h);
+  }
+}
+
+__device__ __forceinline__ int overlap_count(int i, int j, int k, double h, double cx, double cy, double cz, double R2,
+                                             int sf, const SubOff& so) {
+  int cnt = 0;
+#pragma unroll
+  for (int mk = 0; mk < 8; ++mk) {
+    if (mk >= sf) break;
+    const double dz = __dsub_rn(__dmul_rn(__dadd_rn((double)k, so.o[mk]), h), cz);
+    const double dz2 = __dmul_rn(dz, dz);
+#pragma unroll
+    for (int mj = 0; mj < 8; ++mj) {
+      if (mj >= sf) break;
+      const double dy = __dsub_rn(__dmul_rn(__dadd_rn((double)j, so.o[mj]), h), cy);
+      const double dy2 = __dmul_rn(dy, dy);
+#pragma unroll
+      for (int mi = 0; mi < 8; ++mi) {
+        if (mi >= sf) break;
+        const double dx = __dsub_rn(__dmul_rn(__dadd_rn((double)i, so.o[mi]), h), cx);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), dy2), dz2);
+        cnt += (d2 <= R2) ? 1 : 0;
+      }
+    }
+  }
+  return cnt;
+}
+
+// Cells [lo, hi] along one axis that can touch the sphere (every other cell has count 0).
+__device__ __forceinline__ void cell_range(double c, double R, double h, int n, int& lo, int& hi) {
+  int a = (int)floor((c - R) / h) - 1;
+  int b = (int)floor((c + R) / h) + 1;
+  lo = a < 0 ? 0 : a;
+  hi = b > n - 1 ? n - 1 : b;
+}
+
+struct Box {
+  int lo[3], hi[3], nb[3];
+  long long ncell;
+};
+
+__device__ __forceinline__ Box sphere_box(const Geom& G, double h, const double* c, double R, int dilate) {
+  Box B;
+  const int n[3] = {G.nx, G.ny, G.nz};
+  for (int a = 0; a < 3; ++a) {
+    cell_range(c[a], R, h, n[a], B.lo[a], B.hi[a]);
+    B.lo[a] = max(B.lo[a] - dilate, 0);
+    B.hi[a] = min(B.hi[a] + dilate, n[a] - 1);
+    B.nb[a] = B.hi[a] - B.lo[a] + 1;
+    if (B.nb[a] < 0) B.nb[a] = 0;
+  }
+  B.ncell = (long long)B.nb[0] * B.nb[1] * B.nb[2];
+  return B;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of three per-thread values over the block, in a fixed order; result valid in thread 0.
+__device__ void block_sum3(double v[3], double (*red)[3]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int a = 0; a < 3; ++a) v[a] = warp_sum(v[a]);
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) red[w][a] = v[a];
+  __syncthreads();
+  if (w == 0) {
+    for (int a = 0; a < 3; ++a) {
+      double t = lane < nw ? red[lane][a] : 0.0;
+      v[a] = warp_sum(t);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Geom G, double h, double inv2h, FaceBC bc,
+                                                double* __restrict__ E) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  double e[3];
+  efield_at(x, G, i, j, k, h, inv2h, bc, e);
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  const long long p = nat(G, i, j, k);
+  E[p] = e[0];
+  E[N + p] = e[1];
+  E[2 * N + p] = e[2];
+}
+
+// One CTA per sphere: rho(b) += density_s * count / sf^3 over the sphere's cells.
+__global__ void __launch_bounds__(256) k_sphere_density(Geom G, double h, Spheres sp, int sf, SubOff so,
+                                                        double* __restrict__ rho) {
+  const int s = blockIdx.x;
+  const double c[3] = {sp.c[3 * s], sp.c[3 * s + 1], sp.c[3 * s + 2]};
+  const double R = sp.r[s];
+  const double R2 = __dmul_rn(R, R);
+  const double q = sp.q[s];
+  const Box B = sphere_box(G, h, c, R, 0);
+  const double sf3 = (double)(sf * sf * sf);
+  for (long long t = threadIdx.x; t < B.ncell; t += blockDim.x) {
+    const int i = B.lo[0] + (int)(t % B.nb[0]);
+    const int j = B.lo[1] + (int)((t / B.nb[0]) % B.nb[1]);
+    const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
+    const int cnt = overlap_count(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
+    if (cnt == 0) continue;
+    atomicAdd(rho + nat(G, i, j, k), q * ((double)cnt / sf3));
+  }
+}
+
+// One CTA per sphere: F_s = (h^3 density_s) * sum_b w_{s,b} E(x_b).
+__global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__ x, Geom G, double h, double inv2h,
+                                                      FaceBC bc, Spheres sp, int sf, SubOff so,
+                                                      double* __restrict__ F) {
+  __shared__ double red[32][3];
+  const int s = blockIdx.x;
+  const double c[3] = {sp.c[3 * s], sp.c[3 * s + 1], sp.c[3 * s + 2]};
+  const double R = sp.r[s];
+  const double R2 = __dmul_rn(R, R);
+  const Box B = sphere_box(G, h, c, R, 0);
+  const double sf3 = (double)(sf * sf * sf);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long t = threadIdx.x; t < B.ncell; t += blockDim.x) {
+    const int i = B.lo[0] + (int)(t % B.nb[0]);
+    const int j = B.lo[1] + (int)((t / B.nb[0]) % B.nb[1]);
+    const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
+    const int cnt = overlap_count(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
+    if (cnt == 0) continue;
+    const double w = (double)cnt / sf3;
+    double e[3];
+    efield_at(x, G, i, j, k, h, inv2h, bc, e);
+    for (int a = 0; a < 3; ++a) acc[a] = acc[a] + w * e[a];
+  }
+  block_sum3(acc, red);
+  if (threadIdx.x == 0) {
+    const double pre = (h * h * h) * sp.q[s];
+    for (int a = 0; a < 3; ++a) F[3 * s + a] = pre * acc[a];
+  }
+}
+
+// Adjoint of k_force_gather for J = sum wF[s][a] F_s[a], as a gather over the sphere's cell box
+// dilated by one: gphi(p) collects, from every cell b whose central difference reads p, the
+// derivative of J through that difference; ghost values of wall cells route their part to the
+// cell itself and to the wall value (Dirichlet ghost 2g - phi, Neumann phi + h g).
+__global__ void __launch_bounds__(256) k_force_adjoint(const double* __restrict__ x, Geom G, double h, double inv2h,
+                                                       FaceBC bc, Spheres sp, int sf, SubOff so,
+                                                       const double* __restrict__ wF, double* __restrict__ gphi,
+                                                       double* __restrict__ gdens, double* __restrict__ gbc) {
+  __shared__ double red[32][3];
+  const int s = blockIdx.x;
+  const double c[3] = {sp.c[3 * s], sp.c[3 * s + 1], sp.c[3 * s + 2]};
+  const double R = sp.r[s];
+  const double R2 = __dmul_rn(R, R);
+  const Box B = sphere_box(G, h, c, R, 1);
+  const double sf3 = (double)(sf * sf * sf);
+  const double pre = (h * h * h) * sp.q[s];
+  const double wa[3] = {wF[3 * s], wF[3 * s + 1], wF[3 * s + 2]};
+  const int n[3] = {G.nx, G.ny, G.nz};
+  double fsum[3] = {0.0, 0.0, 0.0};
+  for (long long t = threadIdx.x; t < B.ncell; t += blockDim.x) {
+    const int p[3] = {B.lo[0] + (int)(t % B.nb[0]), B.lo[1] + (int)((t / B.nb[0]) % B.nb[1]),
+                      B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]))};
+    double gp = 0.0;
+    const int cnt_p = overlap_count(p[0], p[1], p[2], h, c[0], c[1], c[2], R2, sf, so);
+    const double w_p = (double)cnt_p / sf3;
+    if (cnt_p) {
+      double e[3];
+      efield_at(x, G, p[0], p[1], p[2], h, inv2h, bc, e);
+      for (int a = 0; a < 3; ++a) fsum[a] = fsum[a] + w_p * e[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      // p is the +e_a neighbour of b = p - e_a:  dE_a(b)/dphi(p) = -1/(2h)
+      if (p[a] - 1 >= 0) {
+        int b[3] = {p[0], p[1], p[2]};
+        b[a] -= 1;
+        const int cb = overlap_count(b[0], b[1], b[2], h, c[0], c[1], c[2], R2, sf, so);
+        if (cb) gp = gp - (wa[a] * pre * ((double)cb / sf3)) * inv2h;
+      }
+      // p is the -e_a neighbour of b = p + e_a:  dE_a(b)/dphi(p) = +1/(2h)
+      if (p[a] + 1 < n[a]) {
+        int b[3] = {p[0], p[1], p[2]};
+        b[a] += 1;
+        const int cb = overlap_count(b[0], b[1], b[2], h, c[0], c[1], c[2], R2, sf, so);
+        if (cb) gp = gp + (wa[a] * pre * ((double)cb / sf3)) * inv2h;
+      }
+      if (cnt_p) {
+        const double gE = wa[a] * pre * w_p;
+        if (p[a] == 0) {  // -e_a neighbour is the ghost of face 2a
+          const int face = 2 * a;
+          const double g = gE * inv2h;
+          if (bc.type[face] == 0) {
+            atomicAdd(gbc + face, 2.0 * g);
+            gp = gp - g;
+          } else {
+            atomicAdd(gbc + face, h * g);
+            gp = gp + g;
+          }
+        }
+        if (p[a] == n[a] - 1) {  // +e_a neighbour is the ghost of face 2a+1
+          const int face = 2 * a + 1;
+          const double g = -gE * inv2h;
+          if (bc.type[face] == 0) {
+            atomicAdd(gbc + face, 2.0 * g);
+            gp = gp - g;
+          } else {
+            atomicAdd(gbc + face, h * g);
+            gp = gp + g;
+          }
+        }
+      }
+    }
+    if (gp != 0.0) atomicAdd(gphi + nat(G, p[0], p[1], p[2]), gp);
+  }
+  block_sum3(fsum, red);
+  if (threadIdx.x == 0) {
+    const double h3 = h * h * h;
+    double g = 0.0;
+    for (int a = 0; a < 3; ++a) g = g + wa[a] * h3 * fsum[a];
+    gdens[s] = g;
+  }
+}
+
+// One CTA per sphere: gdens[s] = sum_b w_{s,b} gfield[b].
+__global__ void __launch_bounds__(256) k_density_adjoint(Geom G, double h, Spheres sp, int sf, SubOff so,
+                                                         const double* __restrict__ gf, double* __restrict__ gdens) {
+  __shared__ double red[32][3];
+  const int s = blockIdx.x;
+  const double c[3] = {sp.c[3 * s], sp.c[3 * s + 1], sp.c[3 * s + 2]};
+  const double R = sp.r[s];
+  const double R2 = __dmul_rn(R, R);
+  const Box B = sphere_box(G, h, c, R, 0);
+  const double sf3 = (double)(sf * sf * sf);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long t = threadIdx.x; t < B.ncell; t += blockDim.x) {
+    const int i = B.lo[0] + (int)(t % B.nb[0]);
+    const int j = B.lo[1] + (int)((t / B.nb[0]) % B.nb[1]);
+    const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
+    const int cnt = overlap_count(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
+    if (cnt == 0) continue;
+    acc[0] = acc[0] + ((double)cnt / sf3) * gf[nat(G, i, j, k)];
+  }
+  block_sum3(acc, red);
+  if (threadIdx.x == 0) gdens[s] = acc[0];
+}
+
+__global__ void __launch_bounds__(256) k_scale_copy(const double* __restrict__ a, double* __restrict__ b, long long n,
+                                                    double s) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i] * s;
+}
+
+// Six CTAs, one per wall: gbc[q] = sum over the wall's cells of lambda * (2/h^2 or 1/h).
+__global__ void __launch_bounds__(256) k_face_sums(Geom G, double h, FaceBC bc, const double* __restrict__ lam,
+                                                   double* __restrict__ gbc) {
+  __shared__ double red[32][3];
+  const int q = blockIdx.x;
+  const int a = q >> 1;
+  const int n[3] = {G.nx, G.ny, G.nz};
+  const int fix = (q & 1) ? n[a] - 1 : 0;
+  const int u = (a + 1) % 3, v = (a + 2) % 3;
+  const long long cnt = (long long)n[u] * n[v];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+    int p[3];
+    p[a] = fix;
+    p[u] = (int)(t % n[u]);
+    p[v] = (int)(t / n[u]);
+    acc[0] = acc[0] + lam[nat(G, p[0], p[1], p[2])];
+  }
+  block_sum3(acc, red);
+  if (threadIdx.x == 0) gbc[q] = acc[0] * (bc.type[q] == 0 ? 2.0 / (h * h) : 1.0 / h);
+}
+
+SubOff make_suboff(int sf) {
+  SubOff so;
+  for (int m = 0; m < 8; ++m) so.o[m] = m < sf ? (double)(2 * m + 1) / (double)(2 * sf) : 0.0;
+  return so;
+}
+
+}  // namespace
+
+cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, double* E, cudaStream_t s) {
+  const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
+  dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
+  k_efield<<<g, b, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sphere_density(const Geom& G, double h, const Spheres& sp, int sf, double* rho, cudaStream_t s) {
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  cudaError_t e = cudaMemsetAsync(rho, 0, (size_t)N * sizeof(double), s);
+  if (e != cudaSuccess || sp.P == 0) return e;
+  k_sphere_density<<<sp.P, 256, 0, s>>>(G, h, sp, sf, make_suboff(sf), rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
+                                double* F, cudaStream_t s) {
+  if (sp.P == 0) return cudaSuccess;
+  k_force_gather<<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_adjoint(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
+                                 const double* wF, double* gphi, double* gdens, double* gbc, cudaStream_t s) {
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  cudaError_t e = cudaMemsetAsync(gphi, 0, (size_t)N * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gbc, 0, 6 * sizeof(double), s);
+  if (e != cudaSuccess || sp.P == 0) return e;
+  k_force_adjoint<<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), wF, gphi, gdens, gbc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density_adjoint(const Geom& G, double h, const Spheres& sp, int sf, const double* gfield,
+                                   double* gdens, cudaStream_t s) {
+  if (sp.P == 0) return cudaSuccess;
+  k_density_adjoint<<<sp.P, 256, 0, s>>>(G, h, sp, sf, make_suboff(sf), gfield, gdens);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* lam,
+                               double* grho, double* gbc, cudaStream_t s) {
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  long long blocks = (N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_scale_copy<<<(int)blocks, 256, 0, s>>>(lam, grho, N, inv_eps);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_face_sums<<<6, 256, 0, s>>>(G, h, bc, lam, gbc);
+  return cudaGetLastError();
+}
+
+}  // namespace ccmg

@@ -1,0 +1,241 @@
+"""Python face of libccmg: a cell-centred multigrid Poisson solver context on one GPU.
+
+PyTorch provides device memory and the CUDA stream only; every operation runs in the library's
+CUDA kernels through the C ABI of ``include/ccmg.h``. Fields are float64 CUDA tensors of shape
+``[nz, ny, nx]`` (x fastest), the layout the ABI expects.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DIRICHLET, NEUMANN, MG_FP64, MG_MIXED, MgError  # noqa: F401
+
+PRECISIONS = {"fp64": MG_FP64, "mixed": MG_MIXED}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Poisson:
+    """Solver context for -lap(phi) = rho/eps on an nx*ny*nz grid (see include/ccmg.h).
+
+    Work is enqueued on the stream that is current when the context is created.
+    """
+
+    def __init__(self, dims, h: float = 1.0, bc_type=(DIRICHLET,) * 6, bc_value=(0.0,) * 6, nu1: int = 2,
+                 nu2: int = 2, cgc_weight: float = 2.0, precision: str = "fp64", eps: float = 1.0,
+                 device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libccmg needs a CUDA device; there is no CPU implementation")
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        nx, ny, nz = (int(v) for v in dims)
+        self.dims = (nx, ny, nz)
+        self.shape = (nz, ny, nx)
+        self.h = float(h)
+        self.eps = float(eps)
+        self.bc_type = tuple(int(v) for v in bc_type)
+        self.bc_value = tuple(float(v) for v in bc_value)
+        p = _lib.MgParams()
+        self.lib.mg_default_params(ctypes.byref(p), nx, ny, nz, self.h)
+        for q in range(6):
+            p.bc_type[q] = self.bc_type[q]
+            p.bc_value[q] = self.bc_value[q]
+        p.nu1, p.nu2, p.cgc_weight = int(nu1), int(nu2), float(cgc_weight)
+        p.prec = PRECISIONS[precision]
+        p.eps = self.eps
+        self.precision = precision
+        self.params = p
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            ctx = ctypes.c_void_p()
+            st = self.lib.mg_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+            _lib.check(self.lib, None, st, "mg_create")
+        self.ctx = ctx
+
+    # -- housekeeping ----------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st, what):
+        _lib.check(self.lib, self.ctx, st, what)
+
+    def _field(self, t, name, shape=None):
+        shape = self.shape if shape is None else shape
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float64:
+            raise TypeError(f"{name} must be a float64 tensor on {self.device}")
+        if tuple(t.shape) != tuple(shape) and t.numel() != int(np.prod(shape)):
+            raise ValueError(f"{name} must have shape {shape}")
+        return t.contiguous()
+
+    def new_field(self, *lead):
+        return torch.empty(*lead, *self.shape, dtype=torch.float64, device=self.device)
+
+    @property
+    def num_levels(self) -> int:
+        return self.lib.mg_num_levels(self.ctx)
+
+    def level_dims(self, level: int):
+        d = (ctypes.c_int * 3)()
+        self._check(self.lib.mg_level_dims(self.ctx, level, d), "mg_level_dims")
+        return tuple(d)
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.mg_kernel_launches(self.ctx))
+
+    # -- problem set-up --------------------------------------------------------------------
+    def set_bc_values(self, values):
+        v = (ctypes.c_double * 6)(*[float(x) for x in values])
+        self._check(self.lib.mg_set_bc_values(self.ctx, v), "mg_set_bc_values")
+        self.bc_value = tuple(float(x) for x in values)
+
+    def set_rhs(self, rho):
+        rho = self._field(rho, "rho")
+        self._check(self.lib.mg_set_rhs(self.ctx, _ptr(rho)), "mg_set_rhs")
+
+    def set_rhs_f(self, f):
+        f = self._field(f, "f")
+        self._check(self.lib.mg_set_rhs_f(self.ctx, _ptr(f)), "mg_set_rhs_f")
+
+    def set_solution(self, phi=None):
+        if phi is not None:
+            phi = self._field(phi, "phi")
+        self._check(self.lib.mg_set_solution(self.ctx, _ptr(phi)), "mg_set_solution")
+
+    def solution(self, out=None):
+        out = self.new_field() if out is None else out
+        self._check(self.lib.mg_get_solution(self.ctx, _ptr(out)), "mg_get_solution")
+        return out
+
+    # -- iteration -------------------------------------------------------------------------
+    def vcycle(self, ncycles: int = 1):
+        self._check(self.lib.mg_vcycle(self.ctx, int(ncycles)), "mg_vcycle")
+
+    def solve(self, tol: float = 1e-10, max_cycles: int = 100, raise_on_fail: bool = True):
+        k = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = self.lib.mg_solve(self.ctx, float(tol), int(max_cycles), ctypes.byref(k), ctypes.byref(rel))
+        if raise_on_fail:
+            self._check(st, "mg_solve")
+        return k.value, rel.value
+
+    def residual(self, field: bool = False):
+        rel = ctypes.c_double()
+        r = self.new_field() if field else None
+        self._check(self.lib.mg_residual(self.ctx, ctypes.byref(rel), _ptr(r)), "mg_residual")
+        return (rel.value, r) if field else rel.value
+
+    # -- fields and forces -----------------------------------------------------------------
+    def efield(self, out=None):
+        out = self.new_field(3) if out is None else out
+        self._check(self.lib.mg_efield(self.ctx, _ptr(out)), "mg_efield")
+        return out
+
+    @staticmethod
+    def _sph(centers, radius, density=None):
+        c = centers.contiguous()
+        r = radius.contiguous()
+        q = density.contiguous() if density is not None else None
+        return c, r, q, int(r.shape[0])
+
+    def sphere_density(self, centers, radius, density, sf: int = 2, out=None):
+        c, r, q, P = self._sph(centers, radius, density)
+        out = self.new_field() if out is None else out
+        self._check(self.lib.mg_sphere_density(self.ctx, P, _ptr(c), _ptr(r), _ptr(q), int(sf), _ptr(out)),
+                    "mg_sphere_density")
+        return out
+
+    def force_gather(self, centers, radius, density, sf: int = 2, out=None):
+        c, r, q, P = self._sph(centers, radius, density)
+        out = torch.empty(P, 3, dtype=torch.float64, device=self.device) if out is None else out
+        self._check(self.lib.mg_force_gather(self.ctx, P, _ptr(c), _ptr(r), _ptr(q), int(sf), _ptr(out)),
+                    "mg_force_gather")
+        return out
+
+    def force_gather_adjoint(self, centers, radius, density, wF, sf: int = 2):
+        c, r, q, P = self._sph(centers, radius, density)
+        wF = wF.contiguous()
+        gphi = self.new_field()
+        gd = torch.empty(P, dtype=torch.float64, device=self.device)
+        gbc = torch.empty(6, dtype=torch.float64, device=self.device)
+        self._check(self.lib.mg_force_gather_adjoint(self.ctx, P, _ptr(c), _ptr(r), _ptr(q), int(sf), _ptr(wF),
+                                                     _ptr(gphi), _ptr(gd), _ptr(gbc)), "mg_force_gather_adjoint")
+        return gphi, gd, gbc
+
+    def sphere_density_adjoint(self, centers, radius, gfield, sf: int = 2):
+        c, r, _, P = self._sph(centers, radius)
+        gfield = self._field(gfield, "gfield")
+        gd = torch.empty(P, dtype=torch.float64, device=self.device)
+        self._check(self.lib.mg_sphere_density_adjoint(self.ctx, P, _ptr(c), _ptr(r), int(sf), _ptr(gfield),
+                                                       _ptr(gd)), "mg_sphere_density_adjoint")
+        return gd
+
+    def rhs_adjoint(self, lam):
+        lam = self._field(lam, "lambda")
+        grho = self.new_field()
+        gbc = torch.empty(6, dtype=torch.float64, device=self.device)
+        self._check(self.lib.mg_rhs_adjoint(self.ctx, _ptr(lam), _ptr(grho), _ptr(gbc)), "mg_rhs_adjoint")
+        return grho, gbc
+
+    def step_host(self, centers: np.ndarray, radius: np.ndarray, density: np.ndarray, sf: int = 2,
+                  tol: float = 1e-10, max_cycles: int = 100, forces: np.ndarray | None = None):
+        """One electrostatics step through host buffers (see mg_step_host)."""
+        c = np.ascontiguousarray(centers, dtype=np.float64)
+        r = np.ascontiguousarray(radius, dtype=np.float64)
+        q = np.ascontiguousarray(density, dtype=np.float64)
+        P = int(r.shape[0])
+        F = np.empty((P, 3)) if forces is None else forces
+        k = ctypes.c_int()
+        rel = ctypes.c_double()
+        vp = ctypes.c_void_p
+        st = self.lib.mg_step_host(self.ctx, P, vp(c.ctypes.data), vp(r.ctypes.data), vp(q.ctypes.data), int(sf),
+                                   float(tol), int(max_cycles), vp(F.ctypes.data), ctypes.byref(k),
+                                   ctypes.byref(rel))
+        self._check(st, "mg_step_host")
+        return F, k.value, rel.value
+
+    # -- level-wise operations (kernel verification) ---------------------------------------
+    def level_set(self, level: int, which: int, t):
+        shape = tuple(reversed(self.level_dims(level)))
+        t = self._field(t, "level field", shape)
+        self._check(self.lib.mg_level_set(self.ctx, level, which, _ptr(t)), "mg_level_set")
+
+    def level_get(self, level: int, which: int):
+        shape = tuple(reversed(self.level_dims(level)))
+        out = torch.empty(*shape, dtype=torch.float64, device=self.device)
+        self._check(self.lib.mg_level_get(self.ctx, level, which, _ptr(out)), "mg_level_get")
+        return out
+
+    def op_smooth(self, level: int, colour: int):
+        self._check(self.lib.mg_op_smooth(self.ctx, level, colour), "mg_op_smooth")
+
+    def op_residual_restrict(self, level: int):
+        self._check(self.lib.mg_op_residual_restrict(self.ctx, level), "mg_op_residual_restrict")
+
+    def op_prolong_correct(self, level: int):
+        self._check(self.lib.mg_op_prolong_correct(self.ctx, level), "mg_op_prolong_correct")
+
+    def op_coarse_solve(self) -> int:
+        it = ctypes.c_int()
+        self._check(self.lib.mg_op_coarse_solve(self.ctx, ctypes.byref(it)), "mg_op_coarse_solve")
+        return it.value

@@ -1,0 +1,260 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, kernel by kernel and cycle by
+cycle, on seeded inputs. FP64 tolerance: 1e-12 relative in solution and residual (the method is
+the same algorithm; only rounding order differs: reciprocal multiply for the diagonal, FMA
+contraction, tree reductions). Integer decisions (sub-cell counts) are bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1410_6609_gb300 import synth
+from paper_1410_6609_gb300.solver import Poisson
+
+pytestmark = pytest.mark.gpu
+
+D, N = 0, 1
+TOL = 1e-12
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def cpu(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def maxrel(a, b):
+    m = np.abs(b).max()
+    return np.abs(a - b).max() / (m if m > 0 else 1.0)
+
+
+# (nx, ny, nz) cases: a ragged multi-block case with 5 levels and an odd coarsest grid, a small
+# non-cubic one, and the 32^3 manufactured grid.
+CASES = [((144, 80, 48), (N, N, N, N, D, D)), ((12, 10, 14), (D, N, N, D, D, N)), ((32, 32, 32), (D,) * 6)]
+
+
+@pytest.mark.parametrize("dims,bc", CASES)
+def test_level_operations_match_oracle(dims, bc):
+    h = 0.5
+    P = Poisson(dims, h=h, bc_type=bc)
+    L = P.num_levels
+    assert [tuple(P.level_dims(l)) for l in range(L)] == oracle.levels(*dims)
+    rng = np.random.default_rng(1)
+    for l in range(L - 1):
+        nx, ny, nz = P.level_dims(l)
+        c = oracle.level_coeff(h, l)
+        phi = rng.standard_normal((nz, ny, nx))
+        f = rng.standard_normal((nz, ny, nx)) * c
+        for colour in (0, 1):
+            P.level_set(l, 0, gpu(phi))
+            P.level_set(l, 1, gpu(f))
+            P.op_smooth(l, colour)
+            got = cpu(P.level_get(l, 0))
+            ref = oracle.rbgs_half(phi, f, c, bc, colour)
+            assert maxrel(got, ref) < 1e-14, (l, colour)
+        # fused residual + restriction
+        P.level_set(l, 0, gpu(phi))
+        P.level_set(l, 1, gpu(f))
+        P.op_residual_restrict(l)
+        got = cpu(P.level_get(l + 1, 1))
+        ref = oracle.restrict(oracle.residual(phi, f, c, bc))
+        assert maxrel(got, ref) < 1e-13, l
+        # prolongation with the x2 correction
+        ec = rng.standard_normal(tuple(reversed(P.level_dims(l + 1))))
+        P.level_set(l, 0, gpu(phi))
+        P.level_set(l + 1, 0, gpu(ec))
+        P.op_prolong_correct(l)
+        got = cpu(P.level_get(l, 0))
+        assert maxrel(got, oracle.prolong_correct(phi, ec, 2.0)) < 1e-15
+    # coarsest-grid CG
+    nx, ny, nz = P.level_dims(L - 1)
+    cL = oracle.level_coeff(h, L - 1)
+    b = rng.standard_normal((nz, ny, nx))
+    P.level_set(L - 1, 1, gpu(b))
+    its = P.op_coarse_solve()
+    x_ref, it_ref = oracle.cg(b, cL, bc)
+    assert rel(cpu(P.level_get(L - 1, 0)), x_ref) < 1e-12
+    assert abs(its - it_ref) <= 2
+    P.close()
+
+
+@pytest.mark.parametrize("dims,bc", CASES)
+@pytest.mark.parametrize("ncycles", [1, 3])
+def test_vcycles_match_oracle(dims, bc, ncycles):
+    nx, ny, nz = dims
+    h = 1.0
+    bcv = (0.1, -0.2, 0.3, 0.0, -1.0, 1.0)
+    rho = synth.random_field(dims, seed=5)
+    P = Poisson(dims, h=h, bc_type=bc, bc_value=bcv)
+    P.set_rhs(gpu(rho))
+    P.set_solution(None)
+    P.vcycle(ncycles)
+    got = cpu(P.solution())
+    f = oracle.rhs(rho, h, bc, bcv)
+    ref, _ = oracle.vcycles(np.zeros_like(f), f, h, bc, ncycles)
+    assert rel(got, ref) < TOL
+    # residual of the same state, relative to ||f||
+    r_rel, r = P.residual(field=True)
+    r_ref = oracle.residual(ref, f, oracle.level_coeff(h, 0), bc)
+    assert np.linalg.norm(cpu(r) - r_ref) / np.linalg.norm(f) < TOL
+    assert abs(r_rel - np.linalg.norm(r_ref) / np.linalg.norm(f)) < TOL
+    P.close()
+
+
+def test_manufactured_solution_to_1e10():
+    """32^3, h = 1/32, homogeneous Dirichlet, f = 3 pi^2 sin sin sin: V(2,2) over 4 levels to a
+    1e-10 relative residual; the O(h^2) error is the closed form (x/sin x)^2 - 1, x = pi h/2."""
+    f, h = synth.manufactured_rhs(32)
+    P = Poisson((32, 32, 32), h=h, bc_type=(D,) * 6)
+    assert P.num_levels == 4 and P.level_dims(3) == (4, 4, 4)
+    P.set_rhs(gpu(f))
+    k, r = P.solve(1e-10, 50)
+    phi = cpu(P.solution())
+    ref, k_ref, r_ref = oracle.solve(f, h, (D,) * 6, tol=1e-10)
+    assert k == k_ref and r < 1e-10
+    assert rel(phi, ref) < TOL
+    u = synth.manufactured_exact(32)
+    x = np.pi * h / 2
+    err = np.linalg.norm(phi - u) / np.linalg.norm(u)
+    assert abs(err - ((x / np.sin(x)) ** 2 - 1)) < 1e-6 * err + 1e-9
+    P.close()
+
+
+def _spheres_case(dims, count, seed, R=4.0):
+    sp = synth.random_spheres(dims, count, R, seed)
+    return sp, gpu(sp.centers), gpu(sp.radius), gpu(sp.density)
+
+
+@pytest.mark.parametrize("sf", [1, 2, 3])
+def test_sphere_density_bit_exact(sf):
+    dims = (96, 64, 80)
+    sp, c, r, q = _spheres_case(dims, 25, 7, R=3.5)
+    P = Poisson(dims, bc_type=synth.WALL_BC_TYPE)
+    got = cpu(P.sphere_density(c, r, q, sf))
+    ref = oracle.sphere_density((dims[2], dims[1], dims[0]), 1.0, sp.centers, sp.radius, sp.density, sf)
+    assert np.array_equal(got, ref)
+    P.close()
+
+
+def test_efield_and_forces_match_oracle():
+    dims = (64, 48, 80)
+    bc = synth.WALL_BC_TYPE
+    bcv = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    sp, c, r, q = _spheres_case(dims, 12, 3)
+    phi = synth.random_field(dims, 9)
+    P = Poisson(dims, bc_type=bc, bc_value=bcv)
+    P.set_solution(gpu(phi))
+    E = cpu(P.efield())
+    Eref = oracle.efield(phi, 1.0, bc, bcv)
+    assert maxrel(E, Eref) < 1e-15
+    F = cpu(P.force_gather(c, r, q, 2))
+    Fref = oracle.force_gather(phi, 1.0, bc, bcv, sp.centers, sp.radius, sp.density, 2)
+    assert maxrel(F, Fref) < 1e-12
+    # walls touched by the E-field stencil: Neumann slope and Dirichlet on x
+    bc2 = (D, N, N, N, D, D)
+    bcv2 = (0.3, -0.7, 0.2, 0.0, -1.0, 1.0)
+    P2 = Poisson(dims, bc_type=bc2, bc_value=bcv2)
+    P2.set_solution(gpu(phi))
+    assert maxrel(cpu(P2.efield()), oracle.efield(phi, 1.0, bc2, bcv2)) < 1e-15
+    P.close()
+    P2.close()
+
+
+def test_adjoint_kernels_match_oracle():
+    dims = (32, 32, 40)
+    bc = (D, N, N, N, D, D)
+    bcv = (0.5, 0.1, 0.0, 0.0, 0.0, 1.0)
+    # spheres close to the walls so the ghost terms are exercised
+    centers = np.array([[2.2, 16.0, 20.0], [16.0, 30.1, 1.7], [20.3, 11.2, 38.4], [12.0, 12.0, 12.0]])
+    radius = np.array([2.5, 2.0, 2.2, 3.0])
+    dens = np.array([1.0, -0.7, 0.4, 0.9])
+    wF = np.random.default_rng(2).standard_normal((4, 3))
+    phi = synth.random_field(dims, 4)
+    P = Poisson(dims, bc_type=bc, bc_value=bcv)
+    P.set_solution(gpu(phi))
+    gphi, gd, gbc = P.force_gather_adjoint(gpu(centers), gpu(radius), gpu(dens), gpu(wF), 2)
+    r_gphi, r_gd, r_gbc = oracle.force_gather_adjoint(phi, 1.0, bc, bcv, centers, radius, dens, wF, 2)
+    assert maxrel(cpu(gphi), r_gphi) < 1e-13
+    assert maxrel(cpu(gd), r_gd) < 1e-12
+    assert maxrel(cpu(gbc), r_gbc) < 1e-12
+    gfield = synth.random_field(dims, 6)
+    got = cpu(P.sphere_density_adjoint(gpu(centers), gpu(radius), gpu(gfield), 2))
+    assert maxrel(got, oracle.sphere_density_adjoint(gfield, 1.0, centers, radius, 2)) < 1e-13
+    lam = synth.random_field(dims, 8)
+    grho, gbc2 = P.rhs_adjoint(gpu(lam))
+    r_grho, r_gbc2 = oracle.rhs_adjoint(lam, 1.0, bc)
+    assert maxrel(cpu(grho), r_grho) == 0.0
+    assert maxrel(cpu(gbc2), r_gbc2) < 1e-13
+    P.close()
+
+
+def test_mixed_precision_reaches_tolerance():
+    dims = (64, 64, 64)
+    bc = synth.WALL_BC_TYPE
+    bcv = synth.wall_bc_value(1.0)
+    sp = synth.random_spheres(dims, 20, 4.0, 17)
+    rho = oracle.sphere_density((64, 64, 64), 1.0, sp.centers, sp.radius, sp.density, 2)
+    f = oracle.rhs(rho, 1.0, bc, bcv)
+    P = Poisson(dims, bc_type=bc, bc_value=bcv, precision="mixed")
+    P.set_rhs(gpu(rho))
+    k, r = P.solve(1e-9, 50)
+    phi = cpu(P.solution())
+    assert r < 1e-9
+    assert oracle.rel_residual(phi, f, 1.0, bc) < 1.0001e-9  # checked independently on the CPU
+    ref, k_ref, _ = oracle.solve_mixed(f, 1.0, bc, tol=1e-9)
+    assert abs(k - k_ref) <= 1
+    ref64, _, _ = oracle.solve(f, 1.0, bc, tol=1e-12)
+    assert rel(phi, ref64) < 1e-7
+    P.close()
+
+
+def test_step_host_matches_device_path():
+    dims = (64, 64, 48)
+    bc = synth.WALL_BC_TYPE
+    bcv = synth.wall_bc_value(1.0)
+    sp, c, r, q = _spheres_case(dims, 10, 23)
+    P = Poisson(dims, bc_type=bc, bc_value=bcv)
+    F, k, rel_res = P.step_host(sp.centers, sp.radius, sp.density, 2, 1e-10, 50)
+    assert rel_res < 1e-10 and k > 0
+    P2 = Poisson(dims, bc_type=bc, bc_value=bcv)
+    P2.set_rhs(P2.sphere_density(c, r, q, 2))
+    P2.solve(1e-10, 50)
+    F2 = cpu(P2.force_gather(c, r, q, 2))
+    assert np.array_equal(F, F2)
+    P.close()
+    P2.close()
+
+
+def test_single_level_grid_is_a_cg_solve():
+    dims = (4, 4, 6)  # 4/2 = 2 < 3: the finest grid is the coarsest
+    bc = (D, N, N, D, D, N)
+    rho = synth.random_field(dims, 2)
+    P = Poisson(dims, bc_type=bc)
+    assert P.num_levels == 1
+    P.set_rhs(gpu(rho))
+    k, r = P.solve(1e-12, 5)
+    f = oracle.rhs(rho, 1.0, bc, (0.0,) * 6)
+    ref, _, _ = oracle.solve(f, 1.0, bc, tol=1e-12)
+    assert rel(cpu(P.solution()), ref) < TOL and k == 1
+    P.close()
+
+
+def test_solve_reports_not_converged():
+    f, h = synth.manufactured_rhs(32)
+    P = Poisson((32, 32, 32), h=h)
+    P.set_rhs(gpu(f))
+    k, r = P.solve(1e-10, 2, raise_on_fail=False)
+    assert k == 2 and r > 1e-10
+    from paper_1410_6609_gb300._lib import MgError
+    P.set_solution(None)
+    with pytest.raises(MgError):
+        P.solve(1e-10, 1)
+    P.close()
