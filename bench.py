@@ -1,0 +1,420 @@
+"""Benchmark of the electrostatics step (charged spheres -> multigrid Poisson solve -> E-field ->
+Coulomb forces) on one or more GB300s; prints ONE JSON line on rank 0.
+
+A step is one pass of the hot path over the workload: subsampled sphere charge density, RHS with
+wall terms, solve from zero to the relative-residual tolerance (FP32 V(2,2)-cycles inside FP64
+defect correction for the default 512^3 workload), the E-field, and the force on every sphere.
+value = fine-grid cells solved per second (MLUP/s, the paper's metric, Sec. 6.1), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload spheres512|spheres256|...]
+  python bench.py --impl reference ...   # the CPU oracle on the same workload (bounded sample)
+
+Several GPUs run independent replicas of the workload (one process per GPU, no collective on
+the data path); the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1410_6609_gb300 import synth  # noqa: E402
+
+METRIC = "V-cycle MLUP/s & time-to-1e-9 residual vs FP64 GPU; % HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="spheres512", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and kernel timings")
+    return ap.parse_args()
+
+
+def workload_config(w, rank_seed_offset=0):
+    return {
+        "workload": f"{w.name}: {w.dims[0]}x{w.dims[1]}x{w.dims[2]} cells, {w.sphere_count} spheres R={w.sphere_radius:g} "
+                    f"(N(0,1) charge, zero sum, subsampling {w.subsample}), phi=0/1 on z walls, Neumann 0 on x/y, "
+                    f"{'FP32 V(2,2) inside FP64 defect correction' if w.precision == 'mixed' else 'FP64 V(2,2)'} "
+                    f"to {w.tol:g} relative residual from zero, then E-field and forces",
+        "grid": list(w.dims),
+        "spheres": w.sphere_count,
+        "tol": w.tol,
+        "precision": w.precision,
+        "cycle": "V(2,2), x2 coarse-grid correction, CG coarsest",
+        "l2": "inputs larger than L2 (each fine-grid field >= 134 MB for 256^3 and up)",
+        "seed": w.seed + rank_seed_offset,
+    }
+
+
+# ------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu_index = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timings (bounded samples)
+
+def oracle_sample(w, cycles_needed: int):
+    """Time the oracle on a bounded sample of the workload: density, RHS, one outer cycle, one
+    residual, forces; project the time of the whole step with the cycle count of the solve."""
+    import oracle
+    nx, ny, nz = w.dims
+    sp = w.spheres()
+    t0 = time.perf_counter()
+    rho = oracle.sphere_density((nz, ny, nx), w.h, sp.centers, sp.radius, sp.density, w.subsample)
+    f = oracle.rhs(rho, w.h, w.bc_type, w.bc_value)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rel = oracle.rel_residual(np.zeros_like(f), f, w.h, w.bc_type)
+    t_res = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if w.precision == "mixed":
+        phi, k, _ = oracle.solve_mixed(f, w.h, w.bc_type, tol=0.0, max_cycles=1)
+    else:
+        phi, k, _ = oracle.solve(f, w.h, w.bc_type, tol=0.0, max_cycles=1)
+    t_one = time.perf_counter() - t0  # 2 residuals + 1 cycle
+    t_cycle = max(t_one - 2 * t_res, 0.0)
+    t0 = time.perf_counter()
+    oracle.force_gather(phi, w.h, w.bc_type, w.bc_value, sp.centers, sp.radius, sp.density, w.subsample)
+    t_force = time.perf_counter() - t0
+    t_step = t_setup + (cycles_needed + 1) * t_res + cycles_needed * t_cycle + t_force
+    N = nx * ny * nz
+    return {
+        "value": N / t_step / 1e6,
+        "unit": "MLUP/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"oracle (plain C, 1 thread) on the full {nx}x{ny}x{nz} workload: density+RHS {t_setup:.2f}s, "
+                   f"one residual {t_res:.2f}s, one {'outer mixed' if w.precision == 'mixed' else 'V(2,2)'} cycle "
+                   f"{t_cycle:.2f}s, forces {t_force:.2f}s; step time projected with the GPU solve's "
+                   f"{cycles_needed} cycles = {t_step:.1f}s"),
+        "t_step_s": t_step,
+        "rel0": rel,
+    }
+
+
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    """The oracle on the host cores, on the same workload and metric (bounded per-step sample)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    cycles = {"spheres512": 9, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
+    for _ in range(min(args.warmup, 1)):
+        pass
+    samples = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(oracle_sample(w, cycles))
+    wall = time.perf_counter() - t_all
+    t_step = statistics.mean(s["t_step_s"] for s in samples)
+    N = int(np.prod(w.dims))
+    value = N / t_step / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f64+f32",
+        "data": "synthetic", "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
+                         "sample": samples[0]["sample"] + f"; {args.steps} samples in {wall:.1f}s"},
+        "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1410_6609_gb300.solver import Poisson
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = synth.WORKLOADS[args.workload]
+    nx, ny, nz = w.dims
+    N = nx * ny * nz
+    sp = synth.random_spheres(w.dims, w.sphere_count, w.sphere_radius, w.seed + 100 * rank, w.h)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    c, r, q = dev(sp.centers), dev(sp.radius), dev(sp.density)
+    P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision=w.precision)
+    rho = P.new_field()
+    E = P.new_field(3)
+    F = torch.empty(sp.count, 3, dtype=torch.float64, device="cuda")
+    stream = P.stream
+    cycles_seen = []
+
+    def step():
+        P.sphere_density(c, r, q, w.subsample, out=rho)
+        P.set_rhs(rho)
+        P.set_solution(None)
+        k, rel = P.solve(w.tol, 100)
+        P.efield(out=E)
+        P.force_gather(c, r, q, w.subsample, out=F)
+        cycles_seen.append((k, rel))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    cycles_seen.clear()
+    launches0 = P.kernel_launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (P.kernel_launches - launches0) // args.steps
+    ms_all = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * N / (ms_all / 1e3) / 1e6
+    k_step = cycles_seen[-1][0]
+    rel_final = max(v for _, v in cycles_seen)
+
+    extras = {}
+    if not args.no_extras:
+        extras = measure_extras(P, w, sp, c, r, q, rho, stream, k_step)
+
+    # e2e: the public host-buffer call (spheres in, forces out) plus the E-field, timed by wall clock
+    P.set_solution(None)
+    P.step_host(sp.centers, sp.radius, sp.density, w.subsample, w.tol, 100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.set_solution(None)
+        Fh, k_e2e, _ = P.step_host(sp.centers, sp.radius, sp.density, w.subsample, w.tol, 100)
+        P.efield(out=E)
+        torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": world * N / t_e2e / 1e6, "unit": "MLUP/s", "ms_per_step": t_e2e * 1e3,
+           "h2d_bytes_per_step": int(sp.centers.nbytes + sp.radius.nbytes + sp.density.nbytes),
+           "d2h_bytes_per_step": int(Fh.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, k_step)
+        cpu.pop("t_step_s", None)
+        cpu.pop("rel0", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f64+f32", "data": "synthetic",
+            "config": {**workload_config(w), "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+                       "cycles_per_step": k_step, "final_rel_residual": rel_final},
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            **extras,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _time(fn, stream, reps):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# FP64 issue peak: 1.25 TFLOP/s nominal FP64 with an FMA counted as two FLOPs, i.e. 625 G FP64
+# instruction lanes per second at 2070 MHz (152 SMs x ~2 lanes/clk); every DADD/DMUL/DFMA lane is one op.
+FP64_OPS_PEAK = 0.625  # Tops/s
+
+
+def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
+    """Kernel-level timings for the roofline, the FP64 GPU solve at the same tolerance, and the
+    error of the mixed solution against it."""
+    import torch
+
+    from paper_1410_6609_gb300.solver import Poisson
+
+    peaks, src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    nx, ny, nz = w.dims
+    N = nx * ny * nz
+    out = {}
+    kern = {}
+    phi_m = P.solution().clone()  # the step's solution, before the kernel timings below reuse the state
+    # outer FP64 residual (+ single-precision scaled residual in mixed mode)
+    t_res = _time(P.op_residual_norm, stream, 10)
+    mixed = w.precision == "mixed"
+    bytes_res = N * (8 + 8 + (4 if mixed else 0))
+    ops_res = N * (9 if mixed else 8)
+    kern["residual_fp64"] = {"ms": t_res, "GB/s": bytes_res / t_res / 1e6, "Tops/s": ops_res / t_res / 1e9,
+                             "launches_per_step": k_step + 1}
+    # smoother half-sweep and fused residual+restriction on the finest level
+    esz = 4 if mixed else 8
+    t_sm = _time(lambda: P.op_smooth(0, 0), stream, 20)
+    kern["smooth_half_sweep"] = {"ms": t_sm, "GB/s": 1.5 * N * esz / t_sm / 1e6, "Tops/s": 0.5 * N * 7 / t_sm / 1e9,
+                                 "launches_per_step": 8 * k_step, "precision": "f32" if mixed else "f64"}
+    t_rr = _time(lambda: P.op_residual_restrict(0), stream, 20)
+    kern["resid_restrict"] = {"ms": t_rr, "GB/s": (2 * N * esz + N * esz / 8) / t_rr / 1e6,
+                              "Tops/s": N * 8 / t_rr / 1e9, "launches_per_step": k_step,
+                              "precision": "f32" if mixed else "f64"}
+    # the state changed: restore a consistent solve state for later use
+    for name, d in kern.items():
+        d["share_ms_per_step"] = d["ms"] * d["launches_per_step"]
+    dom = max(kern, key=lambda n: kern[n]["share_ms_per_step"])
+    d = kern[dom]
+    alu = (dom == "residual_fp64") or (not mixed)
+    if alu:
+        out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": d["Tops/s"], "peak": FP64_OPS_PEAK,
+                           "unit": "Tops/s (FP64 lane-ops)", "frac": d["Tops/s"] / FP64_OPS_PEAK,
+                           "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA=2) at 2070 MHz",
+                           "hbm_frac": d["GB/s"] / hbm}
+    else:
+        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": d["GB/s"], "peak": hbm, "unit": "GB/s",
+                           "frac": d["GB/s"] / hbm, "traffic": None, "peak_source": src}
+    out["kernels"] = kern
+
+    # FP64 GPU solve of the same problem to the same tolerance, and the error between them
+    P64 = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="fp64")
+    P64.set_rhs(rho)
+
+    def solve64():
+        P64.set_solution(None)
+        return P64.solve(w.tol, 100)
+
+    k64, rel64 = solve64()
+    t64 = _time(lambda: solve64(), P64.stream, 2)
+    phi64 = P64.solution()
+    err = float(torch.linalg.norm(phi_m - phi64) / torch.linalg.norm(phi64))
+
+    def solve_m():
+        P.set_solution(None)
+        return P.solve(w.tol, 100)
+
+    km, relm = solve_m()
+    tm = _time(lambda: solve_m(), stream, 2)
+    tv64 = _time(lambda: P64.vcycle(1), P64.stream, 3)
+    tvm = _time(lambda: P.vcycle(1), stream, 3)
+    out["time_to_tol"] = {
+        "tol": w.tol,
+        "mixed": {"ms": tm, "cycles": km, "rel_residual": relm, "solve_mlups": N / tm / 1e3},
+        "fp64": {"ms": t64, "cycles": k64, "rel_residual": rel64, "solve_mlups": N / t64 / 1e3},
+        "speedup_mixed_vs_fp64": t64 / tm,
+        "rel_error_mixed_vs_fp64": err,
+    }
+    out["vcycle_mlups"] = {"mixed_outer_cycle": N / tvm / 1e3, "fp64_vcycle": N / tv64 / 1e3,
+                           "mixed_outer_cycle_ms": tvm, "fp64_vcycle_ms": tv64}
+    P64.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -163,6 +163,11 @@ mg_status mg_op_prolong_correct(mg_ctx* ctx, int level);
  * h_iters (may be NULL) receives the iteration count. Synchronises. */
 mg_status mg_op_coarse_solve(mg_ctx* ctx, int* h_iters);
 
+/* Enqueue the termination residual of Algorithm 1 on its own (scaled residual and the fixed-order
+ * reduction of its squared norm; in MG_MIXED mode also the scaled single-precision residual that
+ * the next inner cycle solves for), without reading anything back. For timing that kernel. */
+mg_status mg_op_residual_norm(mg_ctx* ctx);
+
 /* Number of kernels this context has enqueued since creation (graph nodes included). */
 long long mg_kernel_launches(const mg_ctx* ctx);
 

@@ -72,6 +72,7 @@ SIGNATURES = {
     "mg_op_residual_restrict": (_I, [_P, _I]),
     "mg_op_prolong_correct": (_I, [_P, _I]),
     "mg_op_coarse_solve": (_I, [_P, _P]),
+    "mg_op_residual_norm": (_I, [_P]),
     "mg_kernel_launches": (ctypes.c_longlong, [_P]),
 }
 

@@ -658,4 +658,12 @@ mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
   return MG_OK;
 }
 
+mg_status mg_op_residual_norm(mg_ctx* c) {
+  if (!c) return MG_ERR_INVALID;
+  long long nk = 0;
+  CK(enqueue_resid(c, mixed(c) ? 2 : 0, nullptr, c->stream, &nk), "residual_norm");
+  c->launches += nk;
+  return MG_OK;
+}
+
 }  // extern "C"

@@ -235,6 +235,9 @@ class Poisson:
     def op_prolong_correct(self, level: int):
         self._check(self.lib.mg_op_prolong_correct(self.ctx, level), "mg_op_prolong_correct")
 
+    def op_residual_norm(self):
+        self._check(self.lib.mg_op_residual_norm(self.ctx), "mg_op_residual_norm")
+
     def op_coarse_solve(self) -> int:
         it = ctypes.c_int()
         self._check(self.lib.mg_op_coarse_solve(self.ctx, ctypes.byref(it)), "mg_op_coarse_solve")
