@@ -171,6 +171,33 @@ mg_status mg_op_residual_norm(mg_ctx* ctx);
 /* Number of kernels this context has enqueued since creation (graph nodes included). */
 long long mg_kernel_launches(const mg_ctx* ctx);
 
+/* ----------------------------------------------------------------------------------------- */
+/* Residual norm without any device allocation. The paper has no counterpart to this call.
+ *
+ * For callers that must not have a library call cudaMalloc or cudaFree: code whose device
+ * memory is already claimed and budgeted by another allocator or a fixed pool, and
+ * latency-critical loops where an allocation call (which can synchronise the whole device) is
+ * not acceptable. No context is needed and nothing is allocated.
+ *
+ * Computes, for caller-owned fields in natural order (nx*ny*nz doubles, x fastest), the
+ * residual r = f - A phi of the operator of mg_create (cell size h, wall types h_bc_type6 folded
+ * into the stencil; f must already contain the wall terms, as from mg_level_get(ctx, 0, 1, ...))
+ * and writes d_out2[0] = ||r||_2 / ||f||_2 (||r||_2 if f is zero) and d_out2[1] = ||r||_2 to
+ * device memory, enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *
+ * Scratch: a file-scope static device array of 2 x 4096 doubles (64 KiB), one pair of partial
+ * sums per z-plane. Every GPU that loads the library holds it until the process exits. Limits:
+ * nz <= 4096 (larger nz returns MG_ERR_INVALID before anything is enqueued), nx, ny >= 1, h > 0.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any stream capture. Every
+ * call shares the one array: each call overwrites the partials of its own planes before
+ * reading them (nothing needs to start at zero), but calls whose kernels overlap on the GPU
+ * (different streams, or different host threads on one device) race on it and give wrong
+ * results. Returns MG_ERR_INVALID for bad arguments, MG_ERR_CUDA if the lookup or the launch
+ * fails. */
+mg_status mg_residual_norm_static(int nx, int ny, int nz, double h, const int* h_bc_type6, const double* d_phi,
+                                  const double* d_f, double* d_out2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ SIGNATURES = {
     "mg_op_coarse_solve": (_I, [_P, _P]),
     "mg_op_residual_norm": (_I, [_P]),
     "mg_kernel_launches": (ctypes.c_longlong, [_P]),
+    "mg_residual_norm_static": (_I, [_I, _I, _I, _D, _P, _P, _P, _P, _P]),
 }
 
 
