@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="spheres512", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="override the workload's precision (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and kernel timings")
     return ap.parse_args()
@@ -166,7 +168,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = synth.WORKLOADS[args.workload]
+    w = workload(args)
     cycles = {"spheres512": 9, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
     for _ in range(min(args.warmup, 1)):
         pass
@@ -190,6 +192,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def workload(args):
+    w = synth.WORKLOADS[args.workload]
+    if args.precision and args.precision != w.precision:
+        import dataclasses
+        w = dataclasses.replace(w, precision=args.precision, name=f"{w.name}-{args.precision}")
+    return w
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -207,7 +217,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    w = synth.WORKLOADS[args.workload]
+    w = workload(args)
     nx, ny, nz = w.dims
     N = nx * ny * nz
     sp = synth.random_spheres(w.dims, w.sphere_count, w.sphere_radius, w.seed + 100 * rank, w.h)

@@ -61,9 +61,11 @@ typedef struct {
   double cgc_weight;     /* magnification of the coarse-grid correction (Sec. 3: about 2) */
   int prec;              /* mg_prec */
   double eps;            /* permittivity (> 0) */
+  int mixed_inner;       /* MG_MIXED: single-precision V-cycles per outer defect-correction step, 1..16 */
 } mg_params;
 
-/* Fills p with the defaults: V(2,2), cgc_weight 2, MG_FP64, eps 1, all walls Dirichlet 0. */
+/* Fills p with the defaults: V(2,2), cgc_weight 2, MG_FP64, eps 1, all walls Dirichlet 0,
+ * mixed_inner 4. */
 void mg_default_params(mg_params* p, int nx, int ny, int nz, double h);
 
 /* Create a solver context: validates p, builds the level hierarchy (halve every dimension

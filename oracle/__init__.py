@@ -68,7 +68,7 @@ def _load():
                 "ccmg_or_vcycles": (I, [P, P, I, I, I, D, P, I, I, D, I]),
                 "ccmg_or_rel_residual": (D, [P, P, I, I, I, D, P]),
                 "ccmg_or_solve": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
-                "ccmg_or_solve_mixed": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
+                "ccmg_or_solve_mixed": (I, [P, P, I, I, I, D, P, I, I, D, D, I, I, P]),
                 "ccmg_or_efield": (None, [P, P, I, I, I, D, P, P]),
                 "ccmg_or_sphere_density": (None, [P, I, I, I, D, I, P, P, P, I]),
                 "ccmg_or_sphere_density_adjoint": (None, [P, P, I, I, I, D, I, P, P, I]),
@@ -226,13 +226,14 @@ def solve(f, h: float, bc_type, tol: float = 1e-10, max_cycles: int = 100, nu1: 
 
 
 def solve_mixed(f, h: float, bc_type, tol: float = 1e-9, max_cycles: int = 100, nu1: int = 2,
-                nu2: int = 2, omega: float = 2.0, phi0=None):
-    """FP64 defect correction around single-precision V-cycles. Returns (phi, cycles, rel_res)."""
+                nu2: int = 2, omega: float = 2.0, phi0=None, inner: int = 4):
+    """FP64 defect correction around `inner` single-precision V-cycles per outer step.
+    Returns (phi, outer iterations, rel_res)."""
     f = _f64(f)
     phi = np.zeros_like(f) if phi0 is None else _f64(phi0).copy()
     rel = ctypes.c_double()
     k = _load().ccmg_or_solve_mixed(_p(phi), _p(f), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega,
-                                    tol, max_cycles, ctypes.byref(rel))
+                                    tol, max_cycles, inner, ctypes.byref(rel))
     return phi, k, rel.value
 
 

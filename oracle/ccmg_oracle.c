@@ -373,11 +373,13 @@ int ccmg_or_solve(double* phi, const double* f, int nx, int ny, int nz, double h
 /* Mixed-precision defect correction (not in the paper; the cycle is the paper's):
  *   loop: r = f - A_0 phi (double); stop if ||r||/||f|| < tol;
  *         s = RMS of the previous residual (||f|| RMS on the first pass);
- *         one single-precision V-cycle on A_0 e = r / s from e = 0 (double CG at the bottom);
+ *         `inner` single-precision V-cycles on A_0 e = r / s, the first from e = 0 (double CG
+ *         at the bottom);
  *         phi += s * e (double).
- * Returns the number of outer iterations (= single-precision V-cycles). */
+ * Returns the number of outer iterations. */
 int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, double h, const int* bc,
-                        int nu1, int nu2, double omega, double tol, int max_cycles, double* rel_res_out) {
+                        int nu1, int nu2, double omega, double tol, int max_cycles, int inner,
+                        double* rel_res_out) {
   hierarchy H;
   hier_init(&H, nx, ny, nz, 1);
   const size_t n = (size_t)nx * ny * nz;
@@ -395,7 +397,7 @@ int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, do
       H.ff[0][q] = (float)(H.r[q] / scale);
       H.phif[0][q] = 0.0f;
     }
-    vcycle_f(&H, 0, h, bc, nu1, nu2, (float)omega, NULL);
+    for (int it = 0; it < inner; ++it) vcycle_f(&H, 0, h, bc, nu1, nu2, (float)omega, NULL);
     for (size_t q = 0; q < n; ++q) phi[q] = phi[q] + scale * (double)H.phif[0][q];
     ++k;
     const double next = rn / sqrt((double)n);

@@ -31,6 +31,7 @@ class MgParams(ctypes.Structure):
         ("cgc_weight", ctypes.c_double),
         ("prec", ctypes.c_int),
         ("eps", ctypes.c_double),
+        ("mixed_inner", ctypes.c_int),
     ]
 
 

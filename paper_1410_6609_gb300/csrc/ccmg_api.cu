@@ -126,12 +126,14 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
   return cudaSuccess;
 }
 
-// One cycle: FP64 V-cycle, or (mixed) single-precision V-cycle on the scaled residual that the
-// residual graph left in g32[0], followed by phi += scale * e and the next scale.
+// One cycle: FP64 V-cycle, or (mixed) mixed_inner single-precision V-cycles on the scaled
+// residual that the residual graph left in g32[0] (the first from e = 0), followed by
+// phi += scale * e and the next scale.
 cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk) {
   if (!mixed(c)) return enqueue_vcycle<double>(c, c->x64, c->g64, c->inv64, 0, false, s, nk);
-  cudaError_t e = enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, true, s, nk);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < c->p.mixed_inner; ++it)
+    if ((e = enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, it == 0, s, nk)) != cudaSuccess) return e;
   if ((e = launch_update_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s)) != cudaSuccess) return e;
   if ((e = launch_set_scale(c->scal, S_RSUM, S_SCALE, (double)cells(c->geo[0]), s)) != cudaSuccess) return e;
   *nk += 2;
@@ -228,6 +230,7 @@ void mg_default_params(mg_params* p, int nx, int ny, int nz, double h) {
   p->cgc_weight = 2.0;
   p->prec = MG_FP64;
   p->eps = 1.0;
+  p->mixed_inner = 4;
 }
 
 const char* mg_last_error(const mg_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
@@ -253,6 +256,8 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
     return fail(c, MG_ERR_INVALID, "need 0 <= nu1 <= 16 and 1 <= nu2 <= 16");
   if (!std::isfinite(p->cgc_weight)) return fail(c, MG_ERR_INVALID, "cgc_weight must be finite");
   if (p->prec != MG_FP64 && p->prec != MG_MIXED) return fail(c, MG_ERR_INVALID, "prec must be MG_FP64 or MG_MIXED");
+  if (p->prec == MG_MIXED && (p->mixed_inner < 1 || p->mixed_inner > 16))
+    return fail(c, MG_ERR_INVALID, "mixed_inner must be in 1..16");
 
   c = new mg_ctx();
   c->p = *p;

@@ -4,61 +4,14 @@
 // (two colour arrays per field, unit-stride rows) with the scaled right-hand side g = f / c_l.
 // Templated on the storage/arithmetic type T (double for the FP64 solver, float for the inner
 // cycle of the mixed-precision defect correction). The coarsest-grid CG always computes in
-// double.
-#include "ccmg_internal.cuh"
+// double. The per-thread arithmetic is in level_ops.cuh; these are single-system launches.
+#include "level_ops.cuh"
 
 namespace ccmg {
 namespace {
 
-__device__ __forceinline__ double fmat(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float fmat(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+using namespace ops;
 
-// Diagonal shift d of the folded boundary stencil for packed-row coordinates (m, s, j, k):
-// +1 per Dirichlet face, -1 per Neumann face the cell touches (Sec. 2.4, Boundary conditions).
-__device__ __forceinline__ int diag_shift_packed(const Geom& G, int m, int s, int j, int k) {
-  int d = 0;
-  if (m == 0 && s == 0) d += G.sh[0];
-  if (m == G.hx - 1 && s == 1) d += G.sh[1];
-  if (j == 0) d += G.sh[2];
-  if (j == G.ny - 1) d += G.sh[3];
-  if (k == 0) d += G.sh[4];
-  if (k == G.nz - 1) d += G.sh[5];
-  return d;
-}
-
-// 1/(6+d) from the per-type table without dynamic indexing (keeps the table in registers).
-template <typename T>
-__device__ __forceinline__ T inv_of(const InvDiag<T>& inv, int d) {
-  T r = inv.v[3];
-  r = (d == -3) ? inv.v[0] : r;
-  r = (d == -2) ? inv.v[1] : r;
-  r = (d == -1) ? inv.v[2] : r;
-  r = (d == 1) ? inv.v[4] : r;
-  r = (d == 2) ? inv.v[5] : r;
-  r = (d == 3) ? inv.v[6] : r;
-  return r;
-}
-
-// Sum of the six neighbours (in the order -x,+x,-y,+y,-z,+z; absent ones are zero) of the cell at
-// index m of row `row` in colour c, where y points at the other colour's array.
-template <typename T>
-__device__ __forceinline__ T nbsum_packed(const T* __restrict__ y, const Geom& G, long long row, int m, int s, int j,
-                                          int k) {
-  const long long plane = (long long)G.ny * G.hx;
-  const T* yr = y + row;
-  const T xm = (m == 0 && s == 0) ? T(0) : __ldg(yr + m + s - 1);
-  const T xp = (m == G.hx - 1 && s == 1) ? T(0) : __ldg(yr + m + s);
-  const T ym = (j > 0) ? __ldg(yr + m - G.hx) : T(0);
-  const T yp = (j < G.ny - 1) ? __ldg(yr + m + G.hx) : T(0);
-  const T zm = (k > 0) ? __ldg(yr + m - plane) : T(0);
-  const T zp = (k < G.nz - 1) ? __ldg(yr + m + plane) : T(0);
-  return ((((xm + xp) + ym) + yp) + zm) + zp;
-}
-
-// ---------------------------------------------------------------------------------------------
-// Red-black Gauss-Seidel half-sweep (Sec. 4.3): every cell of `colour` becomes the solution of
-// its own row, phi = (g + sum of neighbours) / (6 + d). ZERO: the level's current iterate is
-// zero (first sweep after restriction), so the neighbour sum is exactly zero and is not read.
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256) k_smooth(T* __restrict__ x, const T* __restrict__ g, Geom G, InvDiag<T> inv,
                                                 int colour) {
@@ -66,19 +19,19 @@ __global__ void __launch_bounds__(256) k_smooth(T* __restrict__ x, const T* __re
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (m >= G.hx || j >= G.ny) return;
-  const int s = (j + k + colour) & 1;
-  const long long row = ((long long)k * G.ny + j) * G.hx;
-  const long long own = (long long)colour * G.csz + row + m;
-  const int d = diag_shift_packed(G, m, s, j, k);
-  T S = T(0);
-  if (!ZERO) S = nbsum_packed(x + (long long)(1 - colour) * G.csz, G, row, m, s, j, k);
-  x[own] = (__ldg(g + own) + S) * inv_of(inv, d);
+  smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
 }
 
-// ---------------------------------------------------------------------------------------------
-// Fused residual + averaging restriction (Sec. 3; sweeps "Resid" and "Restr" of Sec. 6.3). One
-// thread per coarse cell (I,J,K): the scaled residuals of its 8 children, summed in the order
-// (dk, dj, di), times 1/4 give the coarse scaled right-hand side.
+template <typename T, int V, bool ZERO>
+__global__ void __launch_bounds__(256) k_smooth_vec(T* __restrict__ x, const T* __restrict__ g, Geom G,
+                                                    InvDiag<T> inv, int colour) {
+  const int mv = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (mv >= G.hx / V || j >= G.ny) return;
+  smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                         T* __restrict__ gc, Geom Gc) {
@@ -86,37 +39,9 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x,
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= Gc.nx || J >= Gc.ny) return;
-  T acc = T(0);
-#pragma unroll
-  for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        const int j = 2 * J + dj, k = 2 * K + dk;
-        const int c = (di + dj + dk) & 1;  // colour of child (2I+di, j, k)
-        const long long row = ((long long)k * G.ny + j) * G.hx;
-        const long long own = (long long)c * G.csz + row + I;
-        const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, I, di, j, k);
-        const int d = diag_shift_packed(G, I, di, j, k);
-        const T r = fmat(-T(6 + d), __ldg(x + own), __ldg(g + own) + S);
-        acc = acc + r;
-      }
-  const T val = acc * T(0.25);
-  long long o;
-  if (Gc.packed) {
-    const int C = (I + J + K) & 1;
-    o = (long long)C * Gc.csz + ((long long)K * Gc.ny + J) * Gc.hx + (I >> 1);
-  } else {
-    o = (long long)I + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
-  }
-  gc[o] = val;
+  resid_restrict_cell<T>(x, g, G, gc, Gc, I, J, K);
 }
 
-// ---------------------------------------------------------------------------------------------
-// Constant prolongation with the magnified correction (Sec. 3): children += omega * e_parent.
-// red_only: the black children are about to be overwritten by a black half-sweep that does not
-// read them, so only the red ones are corrected.
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ x, Geom G, const T* __restrict__ ec, Geom Gc,
                                                  T omega, int red_only) {
@@ -124,111 +49,15 @@ __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ x, Geom G, cons
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= Gc.nx || J >= Gc.ny) return;
-  long long o;
-  if (Gc.packed) {
-    const int C = (I + J + K) & 1;
-    o = (long long)C * Gc.csz + ((long long)K * Gc.ny + J) * Gc.hx + (I >> 1);
-  } else {
-    o = (long long)I + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
-  }
-  const T w = omega * __ldg(ec + o);
-#pragma unroll
-  for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        const int c = (di + dj + dk) & 1;
-        if (red_only && c) continue;
-        const long long idx = (long long)c * G.csz + ((long long)(2 * K + dk) * G.ny + (2 * J + dj)) * G.hx + I;
-        x[idx] = x[idx] + w;
-      }
+  prolong_cell<T>(x, G, ec, Gc, omega, red_only, I, J, K);
 }
 
-// ---------------------------------------------------------------------------------------------
-// Block-wide sum in a fixed order (warp shuffles, then warp 0 over the per-warp sums).
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ double block_sum(double v, double* red /* >= 33 doubles of shared memory */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    double t = (lane < nw) ? red[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-// Unpreconditioned CG (Hestenes-Stiefel) on the coarsest grid (Sec. 4.3), one CTA, in double,
-// vectors in shared memory, natural cell order. Operator: the scaled A_L / c_L, i.e.
-// (6 + d_i) p_i - sum of interior neighbours. Stops when ||r|| <= rtol ||b|| or after maxit.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_cg(T* __restrict__ xo, const T* __restrict__ bi, Geom G, double rtol,
                                                     int maxit, int* iters) {
   extern __shared__ double sm[];
   __shared__ double red[33];
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const int n = nx * ny * nz;
-  double* x = sm;
-  double* r = x + n;
-  double* p = r + n;
-  double* ap = p + n;
-  double loc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double b = (double)bi[i];
-    x[i] = 0.0;
-    r[i] = b;
-    p[i] = b;
-    loc += b * b;
-  }
-  double rr = block_sum(loc, red);
-  const double bnorm = sqrt(rr);
-  int it = 0;
-  if (bnorm > 0.0) {
-    while (it < maxit) {
-      loc = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-        int d = 0;
-        double S = 0.0;
-        if (ix > 0) S += p[i - 1]; else d += G.sh[0];
-        if (ix < nx - 1) S += p[i + 1]; else d += G.sh[1];
-        if (iy > 0) S += p[i - nx]; else d += G.sh[2];
-        if (iy < ny - 1) S += p[i + nx]; else d += G.sh[3];
-        if (iz > 0) S += p[i - nx * ny]; else d += G.sh[4];
-        if (iz < nz - 1) S += p[i + nx * ny]; else d += G.sh[5];
-        const double a = (double)(6 + d) * p[i] - S;
-        ap[i] = a;
-        loc += p[i] * a;
-      }
-      const double pap = block_sum(loc, red);
-      const double alpha = rr / pap;
-      loc = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        x[i] = x[i] + alpha * p[i];
-        const double ri = r[i] - alpha * ap[i];
-        r[i] = ri;
-        loc += ri * ri;
-      }
-      const double rrn = block_sum(loc, red);
-      ++it;
-      if (sqrt(rrn) <= rtol * bnorm) break;
-      const double beta = rrn / rr;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = r[i] + beta * p[i];
-      __syncthreads();
-      rr = rrn;
-    }
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xo[i] = (T)x[i];
+  const int it = coarse_cg_block<T>(xo, bi, G, rtol, maxit, sm, red);
   if (threadIdx.x == 0 && iters) *iters = it;
 }
 
@@ -246,19 +75,17 @@ __global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ x, con
   double isc = 0.0;
   if (MODE == 2) isc = inv_scale[0];
   double acc = 0.0;
+  // rows in (k, j, colour) order, so the red and black rows of one (j,k) are visited together and
+  // every neighbour row is still in L2 when it is needed
   for (long long rw = (long long)blockIdx.x * by + threadIdx.y; rw < rows; rw += (long long)gridDim.x * by) {
-    const int c = (int)(rw / ((long long)G.nz * G.ny));
-    const int rem = (int)(rw - (long long)c * G.nz * G.ny);
-    const int k = rem / G.ny, j = rem - k * G.ny;
+    const int k = (int)(rw / (2LL * G.ny));
+    const int rem = (int)(rw - 2LL * G.ny * k);
+    const int j = rem >> 1, c = rem & 1;
     const int s = (j + k + c) & 1;
     const long long row = ((long long)k * G.ny + j) * G.hx;
-    const T* y = x + (long long)(1 - c) * G.csz;
     for (int m = threadIdx.x; m < G.hx; m += bx) {
       const long long own = (long long)c * G.csz + row + m;
-      const T S = nbsum_packed(y, G, row, m, s, j, k);
-      const int d = diag_shift_packed(G, m, s, j, k);
-      const T r = fmat(-T(6 + d), __ldg(x + own), __ldg(g + own) + S);
-      const double rd = (double)r;
+      const double rd = (double)resid_packed<T>(x, g, G, c, m, j, k);
       acc = fma(rd, rd, acc);
       if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)G.ny * k)] = rd * c0;
       if (MODE == 2) outp[own] = (float)(rd * isc);
@@ -306,7 +133,7 @@ __global__ void __launch_bounds__(256) k_resid_norm_natural(const T* __restrict_
     if (iy == ny - 1) d += G.sh[3];
     if (iz == 0) d += G.sh[4];
     if (iz == nz - 1) d += G.sh[5];
-    const T r = fmat(-T(6 + d), x[i], g[i] + S);
+    const T r = fmat(neg_diag<T>(d), x[i], g[i] + S);
     const double rd = (double)r;
     acc = fma(rd, rd, acc);
     if (MODE == 1) outn[i] = rd * c0;
@@ -436,6 +263,19 @@ int resid_grid(const Geom& G) {
 template <typename T>
 cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv, int colour, bool zero_start,
                           cudaStream_t s) {
+  constexpr int V = 16 / sizeof(T);
+  if (G.hx % V == 0) {
+    const int nvec = G.hx / V;
+    int bx = 1;
+    while (bx < nvec && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
+    if (zero_start)
+      k_smooth_vec<T, V, true><<<gr, b, 0, s>>>(x, g, G, inv, colour);
+    else
+      k_smooth_vec<T, V, false><<<gr, b, 0, s>>>(x, g, G, inv, colour);
+    return cudaGetLastError();
+  }
   dim3 b, gr;
   shape(G.hx, G.ny, G.nz, b, gr);
   if (zero_start)

@@ -1,0 +1,330 @@
+// level_ops.cuh -- device-side bodies of the per-level multigrid operations (Sec. 3, Sec. 4.3).
+//
+// Shared by the single-system kernels (level_kernels.cu) and the batched kernels over many
+// systems of different sizes (batch_kernels.cu): each body works on one thread's cell (or vector
+// of cells) at explicit coordinates, so both launch schemes perform bit-identical arithmetic.
+// Layout and scaling conventions are those of ccmg_internal.cuh.
+#pragma once
+#include "ccmg_internal.cuh"
+
+namespace ccmg {
+namespace ops {
+
+__device__ __forceinline__ double fmat(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmat(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Diagonal shift d of the folded boundary stencil for packed-row coordinates (m, s, j, k):
+// +1 per Dirichlet face, -1 per Neumann face the cell touches (Sec. 2.4, Boundary conditions).
+__device__ __forceinline__ int diag_shift_packed(const Geom& G, int m, int s, int j, int k) {
+  int d = 0;
+  if (m == 0 && s == 0) d += G.sh[0];
+  if (m == G.hx - 1 && s == 1) d += G.sh[1];
+  if (j == 0) d += G.sh[2];
+  if (j == G.ny - 1) d += G.sh[3];
+  if (k == 0) d += G.sh[4];
+  if (k == G.nz - 1) d += G.sh[5];
+  return d;
+}
+
+// 1/(6+d) from the per-type table without dynamic indexing (keeps the table in registers).
+template <typename T>
+__device__ __forceinline__ T inv_of(const InvDiag<T>& inv, int d) {
+  T r = inv.v[3];
+  r = (d == -3) ? inv.v[0] : r;
+  r = (d == -2) ? inv.v[1] : r;
+  r = (d == -1) ? inv.v[2] : r;
+  r = (d == 1) ? inv.v[4] : r;
+  r = (d == 2) ? inv.v[5] : r;
+  r = (d == 3) ? inv.v[6] : r;
+  return r;
+}
+
+// -(6 + d) as a floating-point constant chosen by selects (an int->double conversion would run
+// on the FP64 pipe, which is the bottleneck of the FP64 kernels).
+template <typename T>
+__device__ __forceinline__ T neg_diag(int d) {
+  T r = T(-6);
+  r = (d == -3) ? T(-3) : r;
+  r = (d == -2) ? T(-4) : r;
+  r = (d == -1) ? T(-5) : r;
+  r = (d == 1) ? T(-7) : r;
+  r = (d == 2) ? T(-8) : r;
+  r = (d == 3) ? T(-9) : r;
+  return r;
+}
+
+// Sum of the six neighbours (in the order -x,+x,-y,+y,-z,+z; absent ones are zero) of the cell at
+// index m of row `row` in colour c, where y points at the other colour's array.
+template <typename T>
+__device__ __forceinline__ T nbsum_packed(const T* __restrict__ y, const Geom& G, long long row, int m, int s, int j,
+                                          int k) {
+  const long long plane = (long long)G.ny * G.hx;
+  const T* yr = y + row;
+  const T xm = (m == 0 && s == 0) ? T(0) : __ldg(yr + m + s - 1);
+  const T xp = (m == G.hx - 1 && s == 1) ? T(0) : __ldg(yr + m + s);
+  const T ym = (j > 0) ? __ldg(yr + m - G.hx) : T(0);
+  const T yp = (j < G.ny - 1) ? __ldg(yr + m + G.hx) : T(0);
+  const T zm = (k > 0) ? __ldg(yr + m - plane) : T(0);
+  const T zp = (k < G.nz - 1) ? __ldg(yr + m + plane) : T(0);
+  return ((((xm + xp) + ym) + yp) + zm) + zp;
+}
+
+// 16-byte vector loads and stores (4 floats or 2 doubles).
+__device__ __forceinline__ void load_vec(const float* p, float (&o)[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load_vec(const double* p, double (&o)[2]) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ void store_vec(float* p, const float (&o)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void store_vec(double* p, const double (&o)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Red-black Gauss-Seidel half-sweep (Sec. 4.3): every cell of `colour` becomes the solution of
+// its own row, phi = (g + sum of neighbours) / (6 + d). ZERO: the level's current iterate is
+// zero (first sweep after restriction), so the neighbour sum is exactly zero and is not read.
+// Cell (m, j, k) of the colour's array; caller guarantees m < hx, j < ny, k < nz.
+template <typename T, bool ZERO>
+__device__ __forceinline__ void smooth_cell(T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                            const InvDiag<T>& inv, int colour, int m, int j, int k) {
+  const int s = (j + k + colour) & 1;
+  const long long row = ((long long)k * G.ny + j) * G.hx;
+  const long long own = (long long)colour * G.csz + row + m;
+  const int d = diag_shift_packed(G, m, s, j, k);
+  T S = T(0);
+  if (!ZERO) S = nbsum_packed(x + (long long)(1 - colour) * G.csz, G, row, m, s, j, k);
+  x[own] = (__ldg(g + own) + S) * inv_of(inv, d);
+}
+
+// The same half-sweep for V consecutive cells m0 = V*mv .. m0+V-1 of a colour row (rows whose
+// length is a multiple of V). The other colour's row segment m0..m0+V-1 supplies one x-neighbour
+// of every cell; the remaining one is the scalar just before (s = 0) or just after (s = 1) the
+// segment. Each cell's sum is formed in the same order as in smooth_cell: identical results.
+template <typename T, int V, bool ZERO>
+__device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                           const InvDiag<T>& inv, int colour, int mv, int j, int k) {
+  const int m0 = mv * V;
+  const int s = (j + k + colour) & 1;
+  const long long row = ((long long)k * G.ny + j) * G.hx;
+  const long long own = (long long)colour * G.csz + row + m0;
+  int dbase = 0;
+  if (j == 0) dbase += G.sh[2];
+  if (j == G.ny - 1) dbase += G.sh[3];
+  if (k == 0) dbase += G.sh[4];
+  if (k == G.nz - 1) dbase += G.sh[5];
+  T gv[V], out[V];
+  load_vec(g + own, gv);
+  if (ZERO) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      int d = dbase;
+      if (m0 + i == 0 && s == 0) d += G.sh[0];
+      if (m0 + i == G.hx - 1 && s == 1) d += G.sh[1];
+      out[i] = (gv[i] + T(0)) * inv_of(inv, d);
+    }
+  } else {
+    const T* yr = x + (long long)(1 - colour) * G.csz + row;
+    const long long plane = (long long)G.ny * G.hx;
+    T yc[V], ym[V], yp[V], zm[V], zp[V];
+    load_vec(yr + m0, yc);
+    if (j > 0) load_vec(yr + m0 - G.hx, ym);
+    else
+#pragma unroll
+      for (int i = 0; i < V; ++i) ym[i] = T(0);
+    if (j < G.ny - 1) load_vec(yr + m0 + G.hx, yp);
+    else
+#pragma unroll
+      for (int i = 0; i < V; ++i) yp[i] = T(0);
+    if (k > 0) load_vec(yr + m0 - plane, zm);
+    else
+#pragma unroll
+      for (int i = 0; i < V; ++i) zm[i] = T(0);
+    if (k < G.nz - 1) load_vec(yr + m0 + plane, zp);
+    else
+#pragma unroll
+      for (int i = 0; i < V; ++i) zp[i] = T(0);
+    T extra;
+    if (s == 0) extra = (m0 > 0) ? __ldg(yr + m0 - 1) : T(0);
+    else extra = (m0 + V < G.hx) ? __ldg(yr + m0 + V) : T(0);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      T xm, xp;
+      if (s == 0) {
+        xm = (i == 0) ? extra : yc[(i + V - 1) % V];
+        xp = yc[i];
+      } else {
+        xm = yc[i];
+        xp = (i == V - 1) ? extra : yc[(i + 1) % V];
+      }
+      const T S = ((((xm + xp) + ym[i]) + yp[i]) + zm[i]) + zp[i];
+      int d = dbase;
+      if (m0 + i == 0 && s == 0) d += G.sh[0];
+      if (m0 + i == G.hx - 1 && s == 1) d += G.sh[1];
+      out[i] = (gv[i] + S) * inv_of(inv, d);
+    }
+  }
+  store_vec(x + own, out);
+}
+
+// Index of coarse cell (I,J,K) in its level's storage (packed colours or natural order).
+__device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, int K) {
+  if (Gc.packed) {
+    const int C = (I + J + K) & 1;
+    return (long long)C * Gc.csz + ((long long)K * Gc.ny + J) * Gc.hx + (I >> 1);
+  }
+  return (long long)I + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
+}
+
+// Fused residual + averaging restriction (Sec. 3; sweeps "Resid" and "Restr" of Sec. 6.3) for
+// coarse cell (I,J,K): the scaled residuals of its 8 children, summed in the order (dk, dj, di),
+// times 1/4 give the coarse scaled right-hand side.
+template <typename T>
+__device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                                    T* __restrict__ gc, const Geom& Gc, int I, int J, int K) {
+  T acc = T(0);
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const int j = 2 * J + dj, k = 2 * K + dk;
+        const int c = (di + dj + dk) & 1;  // colour of child (2I+di, j, k)
+        const long long row = ((long long)k * G.ny + j) * G.hx;
+        const long long own = (long long)c * G.csz + row + I;
+        const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, I, di, j, k);
+        const int d = diag_shift_packed(G, I, di, j, k);
+        const T r = fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
+        acc = acc + r;
+      }
+  gc[coarse_index(Gc, I, J, K)] = acc * T(0.25);
+}
+
+// Constant prolongation with the magnified correction (Sec. 3): children += omega * e_parent.
+// red_only: the black children are about to be overwritten by a black half-sweep that does not
+// read them, so only the red ones are corrected.
+template <typename T>
+__device__ __forceinline__ void prolong_cell(T* __restrict__ x, const Geom& G, const T* __restrict__ ec,
+                                             const Geom& Gc, T omega, int red_only, int I, int J, int K) {
+  const T w = omega * __ldg(ec + coarse_index(Gc, I, J, K));
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const int c = (di + dj + dk) & 1;
+        if (red_only && c) continue;
+        const long long idx = (long long)c * G.csz + ((long long)(2 * K + dk) * G.ny + (2 * J + dj)) * G.hx + I;
+        x[idx] = x[idx] + w;
+      }
+}
+
+// Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x.
+template <typename T>
+__device__ __forceinline__ T resid_packed(const T* __restrict__ x, const T* __restrict__ g, const Geom& G, int c,
+                                          int m, int j, int k) {
+  const int s = (j + k + c) & 1;
+  const long long row = ((long long)k * G.ny + j) * G.hx;
+  const long long own = (long long)c * G.csz + row + m;
+  const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
+  const int d = diag_shift_packed(G, m, s, j, k);
+  return fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block-wide sum in a fixed order (warp shuffles, then warp 0 over the per-warp sums). Works for
+// 1D and 2D blocks (threads flattened); result returned to every thread.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubles of shared memory */) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Unpreconditioned CG (Hestenes-Stiefel) on the coarsest grid (Sec. 4.3), one CTA, in double,
+// vectors in shared memory `sm` (4 n doubles), natural cell order. Operator: the scaled
+// A_L / c_L, i.e. (6 + d_i) p_i - sum of interior neighbours. Stops when ||r|| <= rtol ||b|| or
+// after maxit iterations; returns the iteration count.
+template <typename T>
+__device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
+                               double* sm, double* red) {
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const int n = nx * ny * nz;
+  double* x = sm;
+  double* r = x + n;
+  double* p = r + n;
+  double* ap = p + n;
+  double loc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double b = (double)bi[i];
+    x[i] = 0.0;
+    r[i] = b;
+    p[i] = b;
+    loc += b * b;
+  }
+  double rr = block_sum(loc, red);
+  const double bnorm = sqrt(rr);
+  int it = 0;
+  if (bnorm > 0.0) {
+    while (it < maxit) {
+      loc = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+        int d = 0;
+        double S = 0.0;
+        if (ix > 0) S += p[i - 1]; else d += G.sh[0];
+        if (ix < nx - 1) S += p[i + 1]; else d += G.sh[1];
+        if (iy > 0) S += p[i - nx]; else d += G.sh[2];
+        if (iy < ny - 1) S += p[i + nx]; else d += G.sh[3];
+        if (iz > 0) S += p[i - nx * ny]; else d += G.sh[4];
+        if (iz < nz - 1) S += p[i + nx * ny]; else d += G.sh[5];
+        const double a = -neg_diag<double>(d) * p[i] - S;
+        ap[i] = a;
+        loc += p[i] * a;
+      }
+      const double pap = block_sum(loc, red);
+      const double alpha = rr / pap;
+      loc = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        x[i] = x[i] + alpha * p[i];
+        const double ri = r[i] - alpha * ap[i];
+        r[i] = ri;
+        loc += ri * ri;
+      }
+      const double rrn = block_sum(loc, red);
+      ++it;
+      if (sqrt(rrn) <= rtol * bnorm) break;
+      const double beta = rrn / rr;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = r[i] + beta * p[i];
+      __syncthreads();
+      rr = rrn;
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xo[i] = (T)x[i];
+  return it;
+}
+
+}  // namespace ops
+}  // namespace ccmg

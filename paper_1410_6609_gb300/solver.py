@@ -29,7 +29,7 @@ class Poisson:
 
     def __init__(self, dims, h: float = 1.0, bc_type=(DIRICHLET,) * 6, bc_value=(0.0,) * 6, nu1: int = 2,
                  nu2: int = 2, cgc_weight: float = 2.0, precision: str = "fp64", eps: float = 1.0,
-                 device=None):
+                 mixed_inner: int = 4, device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("libccmg needs a CUDA device; there is no CPU implementation")
         self.lib = _lib.load()
@@ -49,6 +49,8 @@ class Poisson:
         p.nu1, p.nu2, p.cgc_weight = int(nu1), int(nu2), float(cgc_weight)
         p.prec = PRECISIONS[precision]
         p.eps = self.eps
+        p.mixed_inner = int(mixed_inner)
+        self.mixed_inner = int(mixed_inner)
         self.precision = precision
         self.params = p
         with torch.cuda.device(self.device):
