@@ -174,6 +174,41 @@ mg_status mg_op_residual_norm(mg_ctx* ctx);
 long long mg_kernel_launches(const mg_ctx* ctx);
 
 /* ----------------------------------------------------------------------------------------- */
+/* Batches: B independent problems (own dimensions, cell size, walls, right-hand side; not in the
+ * paper, which solves one domain) solved together. Every multigrid operation is one kernel launch
+ * over all systems that take part in it; systems with different numbers of levels are scheduled
+ * by depth below their finest level, all coarsest-grid CG solves share one launch, and the cycle
+ * and the residual test are each one CUDA graph. Each system's iterates are bit-identical to a
+ * single context solving it alone with the same parameters. All systems share prec, nu1, nu2
+ * (both >= 1), cgc_weight and mixed_inner. Field pointers follow the single-context conventions
+ * with the system's own dimensions. */
+typedef struct mg_batch mg_batch;
+mg_status mg_batch_create(int B, const mg_params* params /* B entries */, void* stream, mg_batch** out);
+mg_status mg_batch_destroy(mg_batch* b);
+const char* mg_batch_last_error(const mg_batch* b);
+int mg_batch_size(const mg_batch* b);
+mg_status mg_batch_set_rhs(mg_batch* b, int sys, const double* d_rho);        /* as mg_set_rhs */
+mg_status mg_batch_set_solution(mg_batch* b, int sys, const double* d_phi);   /* NULL = zero */
+mg_status mg_batch_get_solution(mg_batch* b, int sys, double* d_phi);
+/* ncycles cycles of every system (MG_MIXED: outer defect-correction steps). No sync. */
+mg_status mg_batch_vcycle(mg_batch* b, int ncycles);
+/* Algorithm 1 for every system at once: a system stops cycling as soon as its own relative
+ * residual is below rel_tol (or after max_cycles); h_cycles and h_rel_res (B entries each, may
+ * be NULL) receive its cycle count and final relative residual. MG_ERR_NOT_CONVERGED if any
+ * system missed the tolerance. Synchronises once per cycle. */
+mg_status mg_batch_solve(mg_batch* b, double rel_tol, int max_cycles, int* h_cycles, double* h_rel_res);
+/* Thread-block shapes of the batched launches: h_tiles4 = {smoother bx, by, transfer bx, by},
+ * bx*by a multiple of 32 and at most 256 (the smoother's bx counts 16-byte vectors of a row). */
+mg_status mg_batch_set_tiles(mg_batch* b, const int* h_tiles4);
+mg_status mg_batch_get_tiles(const mg_batch* b, int* h_tiles4);
+/* Autotuner: times `reps` whole batched cycles for each built-in tile candidate (h_ms, at least
+ * 16 entries, receives ms per cycle; *h_ncand the number of candidates), keeps the fastest and
+ * returns it in h_best4. It runs cycles on the current state, so call it before setting the
+ * problem, or reset the solutions afterwards. */
+mg_status mg_batch_autotune(mg_batch* b, int reps, int* h_best4, double* h_ms, int* h_ncand);
+long long mg_batch_kernel_launches(const mg_batch* b);
+
+/* ----------------------------------------------------------------------------------------- */
 /* Residual norm without any device allocation. The paper has no counterpart to this call.
  *
  * For callers that must not have a library call cudaMalloc or cudaFree: code whose device

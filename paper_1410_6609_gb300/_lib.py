@@ -76,6 +76,19 @@ SIGNATURES = {
     "mg_op_residual_norm": (_I, [_P]),
     "mg_kernel_launches": (ctypes.c_longlong, [_P]),
     "mg_residual_norm_static": (_I, [_I, _I, _I, _D, _P, _P, _P, _P, _P]),
+    "mg_batch_create": (_I, [_I, _P, _P, _P]),
+    "mg_batch_destroy": (_I, [_P]),
+    "mg_batch_last_error": (ctypes.c_char_p, [_P]),
+    "mg_batch_size": (_I, [_P]),
+    "mg_batch_set_rhs": (_I, [_P, _I, _P]),
+    "mg_batch_set_solution": (_I, [_P, _I, _P]),
+    "mg_batch_get_solution": (_I, [_P, _I, _P]),
+    "mg_batch_vcycle": (_I, [_P, _I]),
+    "mg_batch_solve": (_I, [_P, _D, _I, _P, _P]),
+    "mg_batch_set_tiles": (_I, [_P, _P]),
+    "mg_batch_get_tiles": (_I, [_P, _P]),
+    "mg_batch_autotune": (_I, [_P, _I, _P, _P, _P]),
+    "mg_batch_kernel_launches": (ctypes.c_longlong, [_P]),
 }
 
 

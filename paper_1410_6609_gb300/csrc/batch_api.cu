@@ -1,0 +1,660 @@
+// batch_api.cu -- many independent Poisson systems of different sizes solved together.
+//
+// Each system is the single-system problem of ccmg_api.cu (own dimensions, cell size, walls,
+// right-hand side). Every multigrid operation is ONE launch over all systems that take part in it
+// (batch_kernels.cu). Systems with different level counts are scheduled by depth below the finest
+// level: descend (smoothing + residual/restriction at depth d for every system with more than d+1
+// levels), one coarse-CG launch for all systems, ascend. Per-system activity flags in device memory
+// let converged systems drop out of the same captured graphs. The smoother and transfer tile
+// shapes are chosen by mg_batch_autotune, which times the whole batched cycle per candidate.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/ccmg.h"
+#include "level_ops.cuh"
+
+using namespace ccmg;
+
+namespace {
+
+struct BSys {
+  mg_params p{};
+  int L = 0;
+  Geom geo[kMaxLevels]{};
+  double* x64[kMaxLevels]{};
+  double* g64[kMaxLevels]{};
+  float* x32[kMaxLevels]{};
+  float* g32[kMaxLevels]{};
+  FaceBC bc{};
+};
+
+struct Plan {
+  int e0 = 0, s0 = 0, count = 0, blocks = 0;
+  dim3 block{1, 1, 1};
+};
+
+thread_local std::string g_batch_error;
+
+long long cells(const Geom& G) { return G.packed ? 2 * G.csz : G.csz; }
+
+const int kCandidates[][4] = {{32, 8, 64, 4}, {64, 4, 64, 4}, {128, 2, 64, 4}, {16, 16, 32, 8},
+                              {32, 8, 32, 8}, {64, 4, 128, 2}, {8, 32, 32, 8}, {128, 2, 128, 2}};
+constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
+
+}  // namespace
+
+struct mg_batch {
+  int B = 0;
+  int prec = MG_FP64;
+  int nu1 = 2, nu2 = 2, inner = 4;
+  double omega = 2.0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<BSys> sys;
+  int maxL = 0;
+  char* arena = nullptr;
+  InvDiag<double> inv64{};
+  InvDiag<float> inv32{};
+  int tile[4] = {64, 4, 64, 4};  // smoother (bx, by), transfers (bx, by)
+  std::vector<BEntry> h_entries;
+  std::vector<int> h_starts;
+  BEntry* d_entries = nullptr;
+  int* d_starts = nullptr;
+  size_t cap_entries = 0, cap_starts = 0;
+  Plan smooth[kMaxLevels], xfer[kMaxLevels], cg, resid, update;
+  size_t cg_smem = 0;
+  int* d_active = nullptr;
+  int* h_active = nullptr;
+  double* d_scal = nullptr;
+  double* h_scal = nullptr;
+  double* d_partials = nullptr;
+  size_t cap_partials = 0;
+  cudaGraphExec_t g_cycle = nullptr, g_resid = nullptr;
+  long long n_cycle = 0, n_resid = 0;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+mg_status bfail(mg_batch* b, mg_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_batch_error = msg;
+  return st;
+}
+
+#define BCK(call, where)                                                                             \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return bfail(b, MG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool bmixed(const mg_batch* b) { return b->prec == MG_MIXED; }
+
+BLaunch bl(const mg_batch* b, const Plan& p) {
+  BLaunch L;
+  L.entries = b->d_entries + p.e0;
+  L.start = b->d_starts + p.s0;
+  L.count = p.count;
+  L.blocks = p.blocks;
+  L.block = p.block;
+  return L;
+}
+
+void add_plan(mg_batch* b, Plan& p, const std::vector<BEntry>& ents, dim3 block) {
+  p.e0 = (int)b->h_entries.size();
+  p.s0 = (int)b->h_starts.size();
+  p.count = (int)ents.size();
+  p.block = block;
+  int acc = 0;
+  for (const BEntry& e : ents) {
+    b->h_starts.push_back(acc);
+    acc += e.gx * e.gy * e.gz;
+    b->h_entries.push_back(e);
+  }
+  b->h_starts.push_back(acc);
+  p.blocks = acc;
+}
+
+void destroy_graphs(mg_batch* b) {
+  if (b->g_cycle) cudaGraphExecDestroy(b->g_cycle);
+  if (b->g_resid) cudaGraphExecDestroy(b->g_resid);
+  b->g_cycle = b->g_resid = nullptr;
+}
+
+int ceil_div(long long a, long long c) { return (int)((a + c - 1) / c); }
+
+// Build every launch's entry table for the current tiles and upload it.
+mg_status plan(mg_batch* b) {
+  destroy_graphs(b);
+  b->h_entries.clear();
+  b->h_starts.clear();
+  const bool mx = bmixed(b);
+  const int V = mx ? 4 : 2;
+  const int sbx = b->tile[0], sby = b->tile[1], tbx = b->tile[2], tby = b->tile[3];
+  for (int d = 0; d < kMaxLevels; ++d) {
+    b->smooth[d] = Plan();
+    b->xfer[d] = Plan();
+  }
+  for (int d = 0; d + 1 < b->maxL; ++d) {
+    std::vector<BEntry> es, et;
+    for (int s = 0; s < b->B; ++s) {
+      BSys& S = b->sys[s];
+      if (d >= S.L - 1) continue;
+      BEntry e{};
+      e.G = S.geo[d];
+      e.Gc = S.geo[d + 1];
+      e.x = mx ? (void*)S.x32[d] : (void*)S.x64[d];
+      e.g = mx ? (void*)S.g32[d] : (void*)S.g64[d];
+      e.xc = mx ? (void*)S.x32[d + 1] : (void*)S.x64[d + 1];
+      e.gc = mx ? (void*)S.g32[d + 1] : (void*)S.g64[d + 1];
+      e.sys = s;
+      BEntry es1 = e;
+      es1.vec = (e.G.hx % V == 0) ? 1 : 0;
+      const int w = es1.vec ? e.G.hx / V : e.G.hx;
+      es1.gx = ceil_div(w, sbx);
+      es1.gy = ceil_div(e.G.ny, sby);
+      es1.gz = e.G.nz;
+      es.push_back(es1);
+      BEntry et1 = e;
+      et1.gx = ceil_div(e.Gc.nx, tbx);
+      et1.gy = ceil_div(e.Gc.ny, tby);
+      et1.gz = e.Gc.nz;
+      et.push_back(et1);
+    }
+    add_plan(b, b->smooth[d], es, dim3(sbx, sby, 1));
+    add_plan(b, b->xfer[d], et, dim3(tbx, tby, 1));
+  }
+  {  // coarsest grids: one CTA each, as many threads as the largest single-system launch would use
+    std::vector<BEntry> ec;
+    int threads = 32, nmax = 1;
+    for (int s = 0; s < b->B; ++s) {
+      BSys& S = b->sys[s];
+      BEntry e{};
+      e.G = S.geo[S.L - 1];
+      e.x = mx ? (void*)S.x32[S.L - 1] : (void*)S.x64[S.L - 1];
+      e.g = mx ? (void*)S.g32[S.L - 1] : (void*)S.g64[S.L - 1];
+      e.sys = s;
+      e.gx = e.gy = e.gz = 1;
+      ec.push_back(e);
+      const int n = e.G.nx * e.G.ny * e.G.nz;
+      int t = ((n + 31) / 32) * 32;
+      if (t > 256) t = 256;
+      if (t > threads) threads = t;
+      if (n > nmax) nmax = n;
+    }
+    add_plan(b, b->cg, ec, dim3(threads, 1, 1));
+    b->cg_smem = (size_t)4 * nmax * sizeof(double);
+  }
+  {  // finest-level FP64 residual (the termination test) and the mixed-precision update
+    std::vector<BEntry> er, eu;
+    for (int s = 0; s < b->B; ++s) {
+      BSys& S = b->sys[s];
+      BEntry e{};
+      e.G = S.geo[0];
+      e.x = S.x64[0];
+      e.g = S.g64[0];
+      e.aux = mx ? (void*)S.g32[0] : nullptr;
+      e.sys = s;
+      e.gx = ops::resid_norm_blocks(S.geo[0]);
+      e.gy = e.gz = 1;
+      er.push_back(e);
+      BEntry u = e;
+      u.aux = mx ? (void*)S.x32[0] : nullptr;
+      u.gx = std::max(1, std::min(ceil_div(cells(S.geo[0]), 256), 152 * 16));
+      eu.push_back(u);
+    }
+    add_plan(b, b->resid, er, dim3(ops::kResBX, ops::kResBY, 1));
+    add_plan(b, b->update, eu, dim3(256, 1, 1));
+  }
+  if (b->h_entries.size() > b->cap_entries) {
+    cudaFree(b->d_entries);
+    b->d_entries = nullptr;
+    b->cap_entries = 0;
+    BCK(cudaMalloc((void**)&b->d_entries, b->h_entries.size() * sizeof(BEntry)), "batch plan");
+    b->cap_entries = b->h_entries.size();
+  }
+  if (b->h_starts.size() > b->cap_starts) {
+    cudaFree(b->d_starts);
+    b->d_starts = nullptr;
+    b->cap_starts = 0;
+    BCK(cudaMalloc((void**)&b->d_starts, b->h_starts.size() * sizeof(int)), "batch plan");
+    b->cap_starts = b->h_starts.size();
+  }
+  const size_t np = std::max((size_t)b->resid.blocks, (size_t)kMaxPartials);
+  if (np > b->cap_partials) {
+    cudaFree(b->d_partials);
+    b->d_partials = nullptr;
+    b->cap_partials = 0;
+    BCK(cudaMalloc((void**)&b->d_partials, np * sizeof(double)), "batch plan");
+    b->cap_partials = np;
+  }
+  BCK(cudaMemcpyAsync(b->d_entries, b->h_entries.data(), b->h_entries.size() * sizeof(BEntry), cudaMemcpyHostToDevice,
+                      b->stream),
+      "batch plan");
+  BCK(cudaMemcpyAsync(b->d_starts, b->h_starts.data(), b->h_starts.size() * sizeof(int), cudaMemcpyHostToDevice,
+                      b->stream),
+      "batch plan");
+  BCK(cudaStreamSynchronize(b->stream), "batch plan");
+  return MG_OK;
+}
+
+template <typename T>
+cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cudaStream_t s, long long* nk) {
+  cudaError_t e;
+  const int* act = b->d_active;
+  for (int d = 0; d + 1 < b->maxL; ++d) {
+    const BLaunch Ls = bl(b, b->smooth[d]);
+    if (Ls.count == 0) continue;
+    const bool zero = (d > 0) || zero0;
+    for (int it = 0; it < b->nu1; ++it) {
+      if ((e = launch_b_smooth<T>(Ls, act, inv, 0, zero && it == 0, s)) != cudaSuccess) return e;
+      if ((e = launch_b_smooth<T>(Ls, act, inv, 1, false, s)) != cudaSuccess) return e;
+      *nk += 2;
+    }
+    if ((e = launch_b_resid_restrict<T>(bl(b, b->xfer[d]), act, s)) != cudaSuccess) return e;
+    ++*nk;
+  }
+  if ((e = launch_b_coarse_cg<T>(bl(b, b->cg), act, b->cg_smem, 1e-14, s)) != cudaSuccess) return e;
+  ++*nk;
+  for (int d = b->maxL - 2; d >= 0; --d) {
+    const BLaunch Ls = bl(b, b->smooth[d]);
+    if (Ls.count == 0) continue;
+    if ((e = launch_b_prolong<T>(bl(b, b->xfer[d]), act, (T)b->omega, b->nu2 >= 1, s)) != cudaSuccess) return e;
+    ++*nk;
+    for (int it = 0; it < b->nu2; ++it) {
+      if ((e = launch_b_smooth<T>(Ls, act, inv, 1, false, s)) != cudaSuccess) return e;
+      if ((e = launch_b_smooth<T>(Ls, act, inv, 0, false, s)) != cudaSuccess) return e;
+      *nk += 2;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_bcycle(mg_batch* b, cudaStream_t s, long long* nk) {
+  if (!bmixed(b)) return enqueue_bvcycle<double>(b, b->inv64, false, s, nk);
+  cudaError_t e;
+  for (int it = 0; it < b->inner; ++it)
+    if ((e = enqueue_bvcycle<float>(b, b->inv32, it == 0, s, nk)) != cudaSuccess) return e;
+  if ((e = launch_b_update(bl(b, b->update), b->d_active, b->d_scal, s)) != cudaSuccess) return e;
+  if ((e = launch_b_set_scale(bl(b, b->resid), b->d_active, b->d_scal, s)) != cudaSuccess) return e;
+  *nk += 2;
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_bresid(mg_batch* b, cudaStream_t s, long long* nk) {
+  *nk += 2;
+  return launch_b_resid_norm(bl(b, b->resid), b->d_active, bmixed(b) ? 2 : 0, b->d_scal, b->d_partials, s);
+}
+
+template <typename F>
+mg_status bcapture(mg_batch* b, cudaGraphExec_t* out, long long* nodes, F body, const char* what) {
+  if (*out) return MG_OK;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(b, MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  long long nk = 0;
+  cudaError_t eb = body(b->cap, &nk);
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+  if (eb != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return bfail(b, MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(eb != cudaSuccess ? eb : ee));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return bfail(b, MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  *nodes = nk;
+  return MG_OK;
+}
+
+mg_status bgraphs(mg_batch* b) {
+  mg_status st = bcapture(b, &b->g_cycle, &b->n_cycle,
+                          [b](cudaStream_t s, long long* nk) { return enqueue_bcycle(b, s, nk); }, "batch cycle");
+  if (st != MG_OK) return st;
+  return bcapture(b, &b->g_resid, &b->n_resid,
+                  [b](cudaStream_t s, long long* nk) { return enqueue_bresid(b, s, nk); }, "batch residual");
+}
+
+mg_status brun(mg_batch* b, cudaGraphExec_t g, long long nodes, const char* what) {
+  BCK(cudaGraphLaunch(g, b->stream), what);
+  b->launches += nodes;
+  return MG_OK;
+}
+
+mg_status set_all_active(mg_batch* b, int v) {
+  for (int s = 0; s < b->B; ++s) b->h_active[s] = v;
+  BCK(cudaMemcpyAsync(b->d_active, b->h_active, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "active");
+  return MG_OK;
+}
+
+void free_batch(mg_batch* b) {
+  destroy_graphs(b);
+  cudaFree(b->arena);
+  cudaFree(b->d_entries);
+  cudaFree(b->d_starts);
+  cudaFree(b->d_active);
+  cudaFree(b->d_scal);
+  cudaFree(b->d_partials);
+  if (b->h_active) cudaFreeHost(b->h_active);
+  if (b->h_scal) cudaFreeHost(b->h_scal);
+  if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+mg_status check_sys(mg_batch* b, int s) {
+  if (!b) return MG_ERR_INVALID;
+  if (s < 0 || s >= b->B) return bfail(b, MG_ERR_INVALID, "system index out of range");
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mg_batch_last_error(const mg_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch** out) {
+  mg_batch* b = nullptr;
+  if (!params || !out || B < 1) return bfail(b, MG_ERR_INVALID, "need B >= 1 and non-null params and out");
+  *out = nullptr;
+  const mg_params& p0 = params[0];
+  for (int s = 0; s < B; ++s) {
+    // validate each system with the single-system rules
+    const mg_params& p = params[s];
+    const int d[3] = {p.nx, p.ny, p.nz};
+    for (int a = 0; a < 3; ++a)
+      if (d[a] < 4 || (d[a] % 2) != 0) return bfail(b, MG_ERR_INVALID, "grid dimensions must be even and >= 4");
+    if (!(p.h > 0.0) || !std::isfinite(p.h) || !(p.eps > 0.0) || !std::isfinite(p.eps))
+      return bfail(b, MG_ERR_INVALID, "h and eps must be positive");
+    bool all_neumann = true;
+    for (int q = 0; q < 6; ++q) {
+      if (p.bc_type[q] != MG_BC_DIRICHLET && p.bc_type[q] != MG_BC_NEUMANN)
+        return bfail(b, MG_ERR_INVALID, "bc_type must be MG_BC_DIRICHLET or MG_BC_NEUMANN");
+      if (!std::isfinite(p.bc_value[q])) return bfail(b, MG_ERR_INVALID, "bc_value must be finite");
+      if (p.bc_type[q] == MG_BC_DIRICHLET) all_neumann = false;
+    }
+    if (all_neumann) return bfail(b, MG_ERR_INVALID, "all-Neumann walls give a singular problem");
+    if (p.prec != p0.prec || p.nu1 != p0.nu1 || p.nu2 != p0.nu2 || p.cgc_weight != p0.cgc_weight ||
+        (p0.prec == MG_MIXED && p.mixed_inner != p0.mixed_inner))
+      return bfail(b, MG_ERR_INVALID, "all systems of a batch share prec, nu1, nu2, cgc_weight and mixed_inner");
+  }
+  if (p0.nu1 < 1 || p0.nu1 > 16 || p0.nu2 < 1 || p0.nu2 > 16)
+    return bfail(b, MG_ERR_INVALID, "a batch needs 1 <= nu1, nu2 <= 16");
+  if (p0.prec != MG_FP64 && p0.prec != MG_MIXED) return bfail(b, MG_ERR_INVALID, "prec must be MG_FP64 or MG_MIXED");
+  if (p0.prec == MG_MIXED && (p0.mixed_inner < 1 || p0.mixed_inner > 16))
+    return bfail(b, MG_ERR_INVALID, "mixed_inner must be in 1..16");
+  if (!std::isfinite(p0.cgc_weight)) return bfail(b, MG_ERR_INVALID, "cgc_weight must be finite");
+
+  b = new mg_batch();
+  b->B = B;
+  b->prec = p0.prec;
+  b->nu1 = p0.nu1;
+  b->nu2 = p0.nu2;
+  b->inner = p0.mixed_inner;
+  b->omega = p0.cgc_weight;
+  b->stream = (cudaStream_t)stream;
+  b->sys.resize(B);
+  for (int d6 = -3; d6 <= 3; ++d6) {
+    b->inv64.v[d6 + 3] = 1.0 / (double)(6 + d6);
+    b->inv32.v[d6 + 3] = 1.0f / (float)(6 + d6);
+  }
+  // hierarchies (Sec. 3 coarsening rule) and the arena size
+  size_t bytes = 0;
+  auto reserve = [&bytes](size_t n) {
+    const size_t off = bytes;
+    bytes += (n + 255) / 256 * 256;
+    return off;
+  };
+  std::vector<std::vector<size_t>> offs(B);
+  for (int s = 0; s < B; ++s) {
+    BSys& S = b->sys[s];
+    S.p = params[s];
+    for (int q = 0; q < 6; ++q) {
+      S.bc.type[q] = S.p.bc_type[q];
+      S.bc.value[q] = S.p.bc_value[q];
+    }
+    int dims[3] = {S.p.nx, S.p.ny, S.p.nz};
+    for (;;) {
+      if (S.L >= kMaxLevels) break;
+      Geom& G = S.geo[S.L];
+      G.nx = dims[0];
+      G.ny = dims[1];
+      G.nz = dims[2];
+      for (int q = 0; q < 6; ++q) G.sh[q] = S.p.bc_type[q] == MG_BC_DIRICHLET ? 1 : -1;
+      ++S.L;
+      bool ok = true;
+      for (int a = 0; a < 3; ++a)
+        if ((dims[a] % 2) != 0 || dims[a] / 2 < 3) ok = false;
+      if (!ok) break;
+      for (int a = 0; a < 3; ++a) dims[a] /= 2;
+    }
+    for (int l = 0; l < S.L; ++l) {
+      Geom& G = S.geo[l];
+      G.packed = (l < S.L - 1) ? 1 : 0;
+      G.hx = G.nx / 2;
+      G.csz = G.packed ? (long long)G.hx * G.ny * G.nz : (long long)G.nx * G.ny * G.nz;
+    }
+    const Geom& Gc = S.geo[S.L - 1];
+    if ((long long)Gc.nx * Gc.ny * Gc.nz > kMaxCoarseCells) {
+      delete b;
+      return bfail(nullptr, MG_ERR_INVALID, "a coarsest grid has more than 4096 cells");
+    }
+    if (S.L > b->maxL) b->maxL = S.L;
+    for (int l = 0; l < S.L; ++l) {
+      const size_t n = (size_t)cells(S.geo[l]);
+      if (!bmixed(b) || l == 0) {
+        offs[s].push_back(reserve(n * sizeof(double)));
+        offs[s].push_back(reserve(n * sizeof(double)));
+      }
+      if (bmixed(b)) {
+        offs[s].push_back(reserve(n * sizeof(float)));
+        offs[s].push_back(reserve(n * sizeof(float)));
+      }
+    }
+  }
+  cudaError_t e = cudaMalloc((void**)&b->arena, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_active, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_scal, (size_t)B * kScalStride * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_active, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_scal, (size_t)B * kScalStride * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = prepare_b_coarse_cg();
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->arena, 0, bytes, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scal, 0, (size_t)B * kScalStride * sizeof(double), b->stream);
+  if (e != cudaSuccess) {
+    const bool oom = (e == cudaErrorMemoryAllocation);
+    std::string msg = std::string("mg_batch_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    free_batch(b);
+    delete b;
+    return bfail(nullptr, oom ? MG_ERR_OOM : MG_ERR_CUDA, msg);
+  }
+  for (int s = 0; s < B; ++s) {
+    BSys& S = b->sys[s];
+    size_t k = 0;
+    for (int l = 0; l < S.L; ++l) {
+      if (!bmixed(b) || l == 0) {
+        S.x64[l] = (double*)(b->arena + offs[s][k++]);
+        S.g64[l] = (double*)(b->arena + offs[s][k++]);
+      }
+      if (bmixed(b)) {
+        S.x32[l] = (float*)(b->arena + offs[s][k++]);
+        S.g32[l] = (float*)(b->arena + offs[s][k++]);
+      }
+    }
+  }
+  mg_status st = plan(b);
+  if (st == MG_OK) st = set_all_active(b, 1);
+  if (st != MG_OK) {
+    std::string msg = b->err;
+    free_batch(b);
+    delete b;
+    return bfail(nullptr, st, msg);
+  }
+  *out = b;
+  return MG_OK;
+}
+
+mg_status mg_batch_destroy(mg_batch* b) {
+  if (!b) return MG_ERR_INVALID;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  delete b;
+  return MG_OK;
+}
+
+int mg_batch_size(const mg_batch* b) { return b ? b->B : 0; }
+
+mg_status mg_batch_set_rhs(mg_batch* b, int s, const double* d_rho) {
+  mg_status st = check_sys(b, s);
+  if (st != MG_OK) return st;
+  if (!d_rho) return bfail(b, MG_ERR_INVALID, "null right-hand side");
+  BSys& S = b->sys[s];
+  const Geom& G = S.geo[0];
+  double* sc = b->d_scal + (size_t)kScalStride * s;
+  int np = 0;
+  BCK(launch_set_rhs<double>(S.g64[0], G, d_rho, 1.0 / S.p.eps, S.p.h, S.bc, 0, b->stream), "batch set_rhs");
+  BCK(launch_sumsq<double>(S.g64[0], cells(G), b->d_partials, &np, b->stream), "batch set_rhs");
+  BCK(launch_finalize(b->d_partials, np, sc, kSlotGsum, -1, 0, b->stream), "batch set_rhs");
+  BCK(launch_set_scale(sc, kSlotGsum, kSlotScale, (double)cells(G), b->stream), "batch set_rhs");
+  b->launches += 4;
+  return MG_OK;
+}
+
+mg_status mg_batch_set_solution(mg_batch* b, int s, const double* d_phi) {
+  mg_status st = check_sys(b, s);
+  if (st != MG_OK) return st;
+  BCK(launch_pack<double>(b->sys[s].x64[0], b->sys[s].geo[0], d_phi, 1.0, b->stream), "batch set_solution");
+  b->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_batch_get_solution(mg_batch* b, int s, double* d_phi) {
+  mg_status st = check_sys(b, s);
+  if (st != MG_OK) return st;
+  if (!d_phi) return bfail(b, MG_ERR_INVALID, "null output");
+  BCK(launch_unpack<double>(d_phi, b->sys[s].x64[0], b->sys[s].geo[0], 1.0, b->stream), "batch get_solution");
+  b->launches += 1;
+  return MG_OK;
+}
+
+mg_status mg_batch_vcycle(mg_batch* b, int ncycles) {
+  if (!b) return MG_ERR_INVALID;
+  if (ncycles < 0) return bfail(b, MG_ERR_INVALID, "ncycles must be >= 0");
+  mg_status st = bgraphs(b);
+  if (st == MG_OK) st = set_all_active(b, 1);
+  for (int k = 0; k < ncycles && st == MG_OK; ++k) {
+    if (bmixed(b)) st = brun(b, b->g_resid, b->n_resid, "batch residual");
+    if (st == MG_OK) st = brun(b, b->g_cycle, b->n_cycle, "batch cycle");
+  }
+  return st;
+}
+
+mg_status mg_batch_solve(mg_batch* b, double tol, int max_cycles, int* h_cycles, double* h_rel) {
+  if (!b) return MG_ERR_INVALID;
+  if (!(tol >= 0.0) || max_cycles < 0) return bfail(b, MG_ERR_INVALID, "need tol >= 0 and max_cycles >= 0");
+  mg_status st = bgraphs(b);
+  if (st != MG_OK) return st;
+  if ((st = set_all_active(b, 1)) != MG_OK) return st;
+  std::vector<int> cyc(b->B, 0), conv(b->B, 0);
+  for (;;) {
+    if ((st = brun(b, b->g_resid, b->n_resid, "batch residual")) != MG_OK) return st;
+    BCK(cudaMemcpyAsync(b->h_scal, b->d_scal, (size_t)b->B * kScalStride * sizeof(double), cudaMemcpyDeviceToHost,
+                        b->stream),
+        "batch residual");
+    BCK(cudaStreamSynchronize(b->stream), "batch residual");
+    bool any = false;
+    for (int s = 0; s < b->B; ++s) {
+      if (!b->h_active[s]) continue;
+      const double rel = b->h_scal[(size_t)kScalStride * s + kSlotRel];
+      if (!std::isfinite(rel)) {
+        b->h_active[s] = 0;
+      } else if (!(rel >= tol)) {
+        b->h_active[s] = 0;
+        conv[s] = 1;
+      } else if (cyc[s] >= max_cycles) {
+        b->h_active[s] = 0;
+      } else {
+        any = true;
+      }
+    }
+    if (!any) break;
+    BCK(cudaMemcpyAsync(b->d_active, b->h_active, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "active");
+    if ((st = brun(b, b->g_cycle, b->n_cycle, "batch cycle")) != MG_OK) return st;
+    for (int s = 0; s < b->B; ++s) cyc[s] += b->h_active[s];
+  }
+  bool all = true;
+  for (int s = 0; s < b->B; ++s) {
+    if (h_cycles) h_cycles[s] = cyc[s];
+    if (h_rel) h_rel[s] = b->h_scal[(size_t)kScalStride * s + kSlotRel];
+    if (!conv[s]) all = false;
+  }
+  if ((st = set_all_active(b, 1)) != MG_OK) return st;
+  if (!all) return bfail(b, MG_ERR_NOT_CONVERGED, "some systems did not reach the tolerance");
+  return MG_OK;
+}
+
+mg_status mg_batch_set_tiles(mg_batch* b, const int* h_tiles4) {
+  if (!b) return MG_ERR_INVALID;
+  if (!h_tiles4) return bfail(b, MG_ERR_INVALID, "null tiles");
+  for (int q = 0; q < 2; ++q) {
+    const int bx = h_tiles4[2 * q], by = h_tiles4[2 * q + 1];
+    if (bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32 != 0)
+      return bfail(b, MG_ERR_INVALID, "tile bx*by must be a multiple of 32 and at most 256");
+  }
+  for (int q = 0; q < 4; ++q) b->tile[q] = h_tiles4[q];
+  return plan(b);
+}
+
+mg_status mg_batch_get_tiles(const mg_batch* b, int* h_tiles4) {
+  if (!b || !h_tiles4) return MG_ERR_INVALID;
+  for (int q = 0; q < 4; ++q) h_tiles4[q] = b->tile[q];
+  return MG_OK;
+}
+
+mg_status mg_batch_autotune(mg_batch* b, int reps, int* h_best4, double* h_ms, int* h_ncand) {
+  if (!b) return MG_ERR_INVALID;
+  if (reps < 1) reps = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(cudaEventCreate(&e0), "autotune");
+  BCK(cudaEventCreate(&e1), "autotune");
+  double best = 1e300;
+  int bi = 0;
+  mg_status st = MG_OK;
+  for (int c = 0; c < kNumCandidates && st == MG_OK; ++c) {
+    st = mg_batch_set_tiles(b, kCandidates[c]);
+    if (st == MG_OK) st = bgraphs(b);
+    if (st == MG_OK) st = set_all_active(b, 1);
+    if (st == MG_OK) st = brun(b, b->g_cycle, b->n_cycle, "autotune");
+    if (st != MG_OK) break;
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < reps && st == MG_OK; ++r) st = brun(b, b->g_cycle, b->n_cycle, "autotune");
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / reps;
+    if (h_ms) h_ms[c] = per;
+    if (per < best) {
+      best = per;
+      bi = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MG_OK) return st;
+  if (h_ncand) *h_ncand = kNumCandidates;
+  if (h_best4)
+    for (int q = 0; q < 4; ++q) h_best4[q] = kCandidates[bi][q];
+  return mg_batch_set_tiles(b, kCandidates[bi]);
+}
+
+long long mg_batch_kernel_launches(const mg_batch* b) { return b ? b->launches : 0; }
+
+}  // extern "C"

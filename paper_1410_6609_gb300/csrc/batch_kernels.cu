@@ -1,0 +1,232 @@
+// batch_kernels.cu -- multigrid operations over many independent systems in one launch.
+//
+// Each launch walks a table of entries (one system at one level, see BEntry). A block finds its
+// entry by binary search over the entries' block offsets, skips the whole block when its system
+// is inactive (converged or out of cycles), and runs the same per-thread body as the
+// single-system kernel (level_ops.cuh) at the decoded coordinates. The residual norm reproduces
+// the single-system block decomposition and reduction order per system, so every system's
+// iterates are bit-identical to a solve of that system alone.
+#include "level_ops.cuh"
+
+namespace ccmg {
+namespace {
+
+using namespace ops;
+
+__device__ __forceinline__ int find_entry(const int* __restrict__ start, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
+                                                 const int* __restrict__ active, InvDiag<T> inv, int colour) {
+  constexpr int V = 16 / sizeof(T);
+  const int e = find_entry(start, count, blockIdx.x);
+  const BEntry& en = E[e];
+  if (!active[en.sys]) return;
+  const int lb = blockIdx.x - start[e];
+  const int bxi = lb % en.gx, rest = lb / en.gx;
+  const int byi = rest % en.gy, k = rest / en.gy;
+  const Geom G = en.G;
+  const int j = byi * blockDim.y + threadIdx.y;
+  T* x = (T*)en.x;
+  const T* g = (const T*)en.g;
+  if (en.vec) {
+    const int mv = bxi * blockDim.x + threadIdx.x;
+    if (mv < G.hx / V && j < G.ny) smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
+  } else {
+    const int m = bxi * blockDim.x + threadIdx.x;
+    if (m < G.hx && j < G.ny) smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restrict__ E, const int* __restrict__ start,
+                                                         int count, const int* __restrict__ active) {
+  const int e = find_entry(start, count, blockIdx.x);
+  const BEntry& en = E[e];
+  if (!active[en.sys]) return;
+  const int lb = blockIdx.x - start[e];
+  const int bxi = lb % en.gx, rest = lb / en.gx;
+  const int byi = rest % en.gy, K = rest / en.gy;
+  const Geom G = en.G, Gc = en.Gc;
+  const int I = bxi * blockDim.x + threadIdx.x;
+  const int J = byi * blockDim.y + threadIdx.y;
+  if (I < Gc.nx && J < Gc.ny) resid_restrict_cell<T>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_prolong(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
+                                                  const int* __restrict__ active, T omega, int red_only) {
+  const int e = find_entry(start, count, blockIdx.x);
+  const BEntry& en = E[e];
+  if (!active[en.sys]) return;
+  const int lb = blockIdx.x - start[e];
+  const int bxi = lb % en.gx, rest = lb / en.gx;
+  const int byi = rest % en.gy, K = rest / en.gy;
+  const Geom G = en.G, Gc = en.Gc;
+  const int I = bxi * blockDim.x + threadIdx.x;
+  const int J = byi * blockDim.y + threadIdx.y;
+  if (I < Gc.nx && J < Gc.ny) prolong_cell<T>((T*)en.x, G, (const T*)en.xc, Gc, omega, red_only, I, J, K);
+}
+
+// One CTA per system: CG on the system's coarsest grid.
+template <typename T>
+__global__ void __launch_bounds__(1024) kb_coarse_cg(const BEntry* __restrict__ E, const int* __restrict__ active,
+                                                     double rtol) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  const BEntry& en = E[blockIdx.x];
+  if (!active[en.sys]) return;
+  const Geom G = en.G;
+  const int n = G.nx * G.ny * G.nz;
+  coarse_cg_block<T>((T*)en.x, (const T*)en.g, G, rtol, 2 * n, sm, red);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) kb_resid_norm(const BEntry* __restrict__ E, const int* __restrict__ start,
+                                                     int count, const int* __restrict__ active,
+                                                     const double* __restrict__ scal,
+                                                     double* __restrict__ partials) {
+  __shared__ double red[33];
+  const int e = find_entry(start, count, blockIdx.x);
+  const BEntry& en = E[e];
+  if (!active[en.sys]) return;
+  const int lb = blockIdx.x - start[e];
+  const int nb = start[e + 1] - start[e];
+  const double isc = (MODE == 2) ? scal[kScalStride * en.sys + kSlotInvScale] : 0.0;
+  double acc = resid_norm_accum<double, MODE>((const double*)en.x, (const double*)en.g, en.G, lb, nb, 0.0, nullptr,
+                                              (float*)en.aux, isc);
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) kb_finalize(const BEntry* __restrict__ E, const int* __restrict__ start,
+                                                   const int* __restrict__ active, const double* __restrict__ partials,
+                                                   double* __restrict__ scal) {
+  __shared__ double red[33];
+  const int e = blockIdx.x;
+  const int sys = E[e].sys;
+  if (!active[sys]) return;
+  const double acc = sum_partials(partials + start[e], start[e + 1] - start[e], red);
+  if (threadIdx.x == 0) {
+    double* sc = scal + kScalStride * sys;
+    sc[kSlotRsum] = acc;
+    const double ref = sc[kSlotGsum];
+    sc[kSlotRel] = ref > 0.0 ? sqrt(acc) / sqrt(ref) : sqrt(acc);
+  }
+}
+
+__global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
+                                                 const int* __restrict__ active, const double* __restrict__ scal) {
+  const int e = find_entry(start, count, blockIdx.x);
+  const BEntry& en = E[e];
+  if (!active[en.sys]) return;
+  const long long lb = blockIdx.x - start[e];
+  const long long nb = start[e + 1] - start[e];
+  const Geom G = en.G;
+  const long long n = G.packed ? 2 * G.csz : G.csz;
+  double* x = (double*)en.x;
+  const float* ev = (const float*)en.aux;
+  const double sc = scal[kScalStride * en.sys + kSlotScale];
+  for (long long i = lb * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) x[i] = fma(sc, (double)ev[i], x[i]);
+}
+
+__global__ void kb_set_scale(const BEntry* __restrict__ E, int count, const int* __restrict__ active,
+                             double* __restrict__ scal) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const int sys = E[e].sys;
+  if (!active[sys]) return;
+  const Geom G = E[e].G;
+  const double n = (double)(G.packed ? 2 * G.csz : G.csz);
+  double* sc = scal + kScalStride * sys;
+  const double v = sqrt(sc[kSlotRsum] / n);
+  const double s = (v > 0.0 && v == v && v < 1e300) ? v : 1.0;
+  sc[kSlotScale] = s;
+  sc[kSlotInvScale] = 1.0 / s;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_b_smooth(const BLaunch& L, const int* active, const InvDiag<T>& inv, int colour, bool zero,
+                            cudaStream_t s) {
+  if (L.count == 0 || L.blocks == 0) return cudaSuccess;
+  if (zero)
+    kb_smooth<T, true><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active, inv, colour);
+  else
+    kb_smooth<T, false><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active, inv, colour);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, cudaStream_t s) {
+  if (L.count == 0 || L.blocks == 0) return cudaSuccess;
+  kb_resid_restrict<T><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_b_prolong(const BLaunch& L, const int* active, T omega, bool red_only, cudaStream_t s) {
+  if (L.count == 0 || L.blocks == 0) return cudaSuccess;
+  kb_prolong<T><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active, omega, red_only ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_b_coarse_cg(const BLaunch& L, const int* active, size_t smem, double rtol, cudaStream_t s) {
+  if (L.count == 0) return cudaSuccess;
+  kb_coarse_cg<T><<<L.count, L.block, smem, s>>>(L.entries, active, rtol);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_b_coarse_cg() {
+  const int bytes = (int)(4 * kMaxCoarseCells * sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(kb_coarse_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kb_coarse_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, int mode, double* scal, double* partials,
+                                cudaStream_t s) {
+  if (L.count == 0 || L.blocks == 0) return cudaSuccess;
+  const dim3 b(kResBX, kResBY, 1);
+  if (mode == 2)
+    kb_resid_norm<2><<<L.blocks, b, 0, s>>>(L.entries, L.start, L.count, active, scal, partials);
+  else
+    kb_resid_norm<0><<<L.blocks, b, 0, s>>>(L.entries, L.start, L.count, active, scal, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  kb_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, partials, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_update(const BLaunch& L, const int* active, const double* scal, cudaStream_t s) {
+  if (L.count == 0 || L.blocks == 0) return cudaSuccess;
+  kb_update<<<L.blocks, 256, 0, s>>>(L.entries, L.start, L.count, active, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, double* scal, cudaStream_t s) {
+  if (L.count == 0) return cudaSuccess;
+  kb_set_scale<<<(L.count + 63) / 64, 64, 0, s>>>(L.entries, L.count, active, scal);
+  return cudaGetLastError();
+}
+
+#define CCMG_B_INSTANTIATE(T)                                                                                  \
+  template cudaError_t launch_b_smooth<T>(const BLaunch&, const int*, const InvDiag<T>&, int, bool, cudaStream_t); \
+  template cudaError_t launch_b_resid_restrict<T>(const BLaunch&, const int*, cudaStream_t);                    \
+  template cudaError_t launch_b_prolong<T>(const BLaunch&, const int*, T, bool, cudaStream_t);                  \
+  template cudaError_t launch_b_coarse_cg<T>(const BLaunch&, const int*, size_t, double, cudaStream_t);
+
+CCMG_B_INSTANTIATE(double)
+CCMG_B_INSTANTIATE(float)
+
+}  // namespace ccmg

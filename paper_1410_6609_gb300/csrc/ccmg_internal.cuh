@@ -25,6 +25,7 @@ namespace ccmg {
 
 constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarseCells = 4096;
+constexpr int kMaxPartialsPerSystem = 1216;  // residual-norm blocks of one system (8 per SM)
 
 struct Geom {
   int nx, ny, nz;  // cells per axis
@@ -107,5 +108,53 @@ cudaError_t launch_density_adjoint(const Geom& G, double h, const Spheres& sp, i
                                    double* gdens, cudaStream_t s);
 cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* lam,
                                double* grho, double* gbc, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------------
+// Batched launches over many independent systems of different sizes. One entry describes one
+// system at one level; an entry owns the block range [start[e], start[e+1]) of the launch, laid
+// out as gx * gy * gz blocks (gz = planes). A block whose system is inactive returns at once.
+struct BEntry {
+  Geom G;        // the entry's level
+  Geom Gc;       // next-coarser level (restriction / prolongation entries)
+  void* x;       // level iterate (T)
+  void* g;       // level scaled right-hand side (T)
+  void* xc;      // next-coarser iterate
+  void* gc;      // next-coarser right-hand side
+  void* aux;     // residual entries: float residual output (mixed); update entries: float correction
+  int sys;       // system index
+  int gx, gy, gz;
+  int vec;       // smoother: 16-byte vector path
+  int pad;
+};
+
+struct BLaunch {
+  const BEntry* entries;  // device
+  const int* start;       // device, count + 1 block offsets
+  int count;
+  int blocks;             // start[count]
+  dim3 block;
+};
+
+template <typename T>
+cudaError_t launch_b_smooth(const BLaunch& L, const int* active, const InvDiag<T>& inv, int colour, bool zero,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, cudaStream_t s);
+template <typename T>
+cudaError_t launch_b_prolong(const BLaunch& L, const int* active, T omega, bool red_only, cudaStream_t s);
+template <typename T>
+cudaError_t launch_b_coarse_cg(const BLaunch& L, const int* active, size_t smem, double rtol, cudaStream_t s);
+cudaError_t prepare_b_coarse_cg();
+// Per-system scalars of a batch: kScalStride doubles per system, same slots as a single context.
+constexpr int kScalStride = 8;
+constexpr int kSlotGsum = 0, kSlotRsum = 1, kSlotRel = 2, kSlotScale = 3, kSlotInvScale = 4;
+// FP64 residual of every system's finest level (mode 0 or 2, as launch_resid_norm), per-block
+// partials, then one finalize block per system: rsum, rel = sqrt(rsum / gsum) in its slots.
+cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, int mode, double* scal, double* partials,
+                                cudaStream_t s);
+// x64 += scale * double(e32) on every active system's finest level (update entries).
+cudaError_t launch_b_update(const BLaunch& L, const int* active, const double* scal, cudaStream_t s);
+// scale = sqrt(rsum / n) (1 if not positive and finite), inv_scale = 1 / scale, per system.
+cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, double* scal, cudaStream_t s);
 
 }  // namespace ccmg

@@ -62,85 +62,19 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(T* __restrict__ xo, const T*
 }
 
 // ---------------------------------------------------------------------------------------------
-// Scaled residual over a packed level with per-block partial sums of r~^2 (the termination test
-// of Algorithm 1). Grid-stride over rows (colour, k, j) so the partial count is the grid size.
+// Scaled residual with per-block partial sums of r~^2 (the termination test of Algorithm 1); the
+// row walk and the reduction are in level_ops.cuh (resid_norm_accum), so a batched launch over
+// many systems reproduces each system's partial sums exactly.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                     double* __restrict__ partials, double c0,
                                                     double* __restrict__ outn, float* __restrict__ outp,
                                                     const double* __restrict__ inv_scale) {
   __shared__ double red[33];
-  const int bx = blockDim.x, by = blockDim.y;
-  const long long rows = 2LL * G.nz * G.ny;
-  double isc = 0.0;
-  if (MODE == 2) isc = inv_scale[0];
-  double acc = 0.0;
-  // rows in (k, j, colour) order, so the red and black rows of one (j,k) are visited together and
-  // every neighbour row is still in L2 when it is needed
-  for (long long rw = (long long)blockIdx.x * by + threadIdx.y; rw < rows; rw += (long long)gridDim.x * by) {
-    const int k = (int)(rw / (2LL * G.ny));
-    const int rem = (int)(rw - 2LL * G.ny * k);
-    const int j = rem >> 1, c = rem & 1;
-    const int s = (j + k + c) & 1;
-    const long long row = ((long long)k * G.ny + j) * G.hx;
-    for (int m = threadIdx.x; m < G.hx; m += bx) {
-      const long long own = (long long)c * G.csz + row + m;
-      const double rd = (double)resid_packed<T>(x, g, G, c, m, j, k);
-      acc = fma(rd, rd, acc);
-      if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)G.ny * k)] = rd * c0;
-      if (MODE == 2) outp[own] = (float)(rd * isc);
-    }
-  }
-  // flatten the 2D block for the reduction
-  const int tid = threadIdx.y * bx + threadIdx.x;
-  const int lane = tid & 31, w = tid >> 5, nw = (bx * by + 31) >> 5;
-  acc = warp_sum(acc);
-  if (lane == 0) red[w] = acc;
-  __syncthreads();
-  if (w == 0) {
-    double t = (lane < nw) ? red[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) partials[blockIdx.x] = t;
-  }
-}
-
-// Residual of a natural-order (single-level) grid: used when the finest level is also the
-// coarsest. One block.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_resid_norm_natural(const T* __restrict__ x, const T* __restrict__ g, Geom G,
-                                                            double* __restrict__ partials, double c0,
-                                                            double* __restrict__ outn, float* __restrict__ outp,
-                                                            const double* __restrict__ inv_scale) {
-  __shared__ double red[33];
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const long long n = (long long)nx * ny * nz;
-  double isc = 0.0;
-  if (MODE == 2) isc = inv_scale[0];
-  double acc = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
-    int d = 0;
-    T S = T(0);
-    S = S + (ix > 0 ? x[i - 1] : T(0));
-    S = S + (ix < nx - 1 ? x[i + 1] : T(0));
-    S = S + (iy > 0 ? x[i - nx] : T(0));
-    S = S + (iy < ny - 1 ? x[i + nx] : T(0));
-    S = S + (iz > 0 ? x[i - (long long)nx * ny] : T(0));
-    S = S + (iz < nz - 1 ? x[i + (long long)nx * ny] : T(0));
-    if (ix == 0) d += G.sh[0];
-    if (ix == nx - 1) d += G.sh[1];
-    if (iy == 0) d += G.sh[2];
-    if (iy == ny - 1) d += G.sh[3];
-    if (iz == 0) d += G.sh[4];
-    if (iz == nz - 1) d += G.sh[5];
-    const T r = fmat(neg_diag<T>(d), x[i], g[i] + S);
-    const double rd = (double)r;
-    acc = fma(rd, rd, acc);
-    if (MODE == 1) outn[i] = rd * c0;
-    if (MODE == 2) outp[i] = (float)(rd * isc);
-  }
+  const double isc = (MODE == 2) ? inv_scale[0] : 0.0;
+  double acc = resid_norm_accum<T, MODE>(x, g, G, blockIdx.x, gridDim.x, c0, outn, outp, isc);
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = acc;
 }
 
 template <typename T>
@@ -158,9 +92,7 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ a, long lon
 __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int n, double* scal, int slot,
                                                   int slot_rel, int slot_ref) {
   __shared__ double red[33];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
-  acc = block_sum(acc, red);
+  const double acc = sum_partials(partials, n, red);
   if (threadIdx.x == 0) {
     scal[slot] = acc;
     if (slot_rel >= 0) {
@@ -247,14 +179,6 @@ void shape(int w, int h, int depth, dim3& b, dim3& g) {
   g = dim3((w + bx - 1) / bx, (h + by - 1) / by, depth);
 }
 
-int resid_grid(const Geom& G) {
-  const long long rows = 2LL * G.nz * G.ny;
-  long long blocks = (rows + 1) / 2;
-  const long long cap = 152 * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  return (int)blocks;
-}
 
 }  // namespace
 
@@ -325,20 +249,12 @@ template <typename T>
 cudaError_t launch_resid_norm(const T* x, const T* g, const Geom& G, double* partials, int* nparts, int mode,
                               double c0, double* out_natural, float* out_packed, const double* inv_scale,
                               cudaStream_t s) {
-  if (G.packed) {
-    const int grid = resid_grid(G);
-    const int bx = G.hx >= 128 ? 128 : (G.hx >= 64 ? 64 : 32);
-    dim3 b(bx, 256 / bx, 1);
-    if (mode == 0) k_resid_norm<T, 0><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-    if (mode == 1) k_resid_norm<T, 1><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-    if (mode == 2) k_resid_norm<T, 2><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-    *nparts = grid;
-  } else {
-    if (mode == 0) k_resid_norm_natural<T, 0><<<1, 256, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-    if (mode == 1) k_resid_norm_natural<T, 1><<<1, 256, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-    if (mode == 2) k_resid_norm_natural<T, 2><<<1, 256, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-    *nparts = 1;
-  }
+  const int grid = resid_norm_blocks(G);
+  const dim3 b(kResBX, kResBY, 1);
+  if (mode == 0) k_resid_norm<T, 0><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+  if (mode == 1) k_resid_norm<T, 1><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+  if (mode == 2) k_resid_norm<T, 2><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+  *nparts = grid;
   return cudaGetLastError();
 }
 

@@ -326,5 +326,81 @@ __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, con
   return it;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Residual-norm decomposition shared by the single-system and the batched launches: blocks of
+// kResBX x kResBY threads; block lb of nb walks the rows of the level in (k, j, colour) order (so
+// the red and black rows of one (j,k) are visited together and every neighbour row is still in
+// L2 when it is needed), kResBY rows at a time, threads along the row. A natural-order level
+// (single-level grid) is walked cell by cell. Returns the thread's sum of r~^2; by MODE also
+// writes r = r~ c0 in natural order (1) or float(r~ isc) in the level's own order (2).
+constexpr int kResBX = 64, kResBY = 4;
+
+template <typename T, int MODE>
+__device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                                   long long lb, long long nb, double c0, double* __restrict__ outn,
+                                                   float* __restrict__ outp, double isc) {
+  double acc = 0.0;
+  if (G.packed) {
+    const long long rows = 2LL * G.nz * G.ny;
+    for (long long rw = lb * kResBY + threadIdx.y; rw < rows; rw += nb * kResBY) {
+      const int k = (int)(rw / (2LL * G.ny));
+      const int rem = (int)(rw - 2LL * G.ny * k);
+      const int j = rem >> 1, c = rem & 1;
+      const int s = (j + k + c) & 1;
+      const long long row = ((long long)k * G.ny + j) * G.hx;
+      for (int m = threadIdx.x; m < G.hx; m += kResBX) {
+        const double rd = (double)resid_packed<T>(x, g, G, c, m, j, k);
+        acc = fma(rd, rd, acc);
+        if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)G.ny * k)] = rd * c0;
+        if (MODE == 2) outp[(long long)c * G.csz + row + m] = (float)(rd * isc);
+      }
+    }
+  } else {
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const long long n = (long long)nx * ny * nz;
+    const int tid = threadIdx.y * kResBX + threadIdx.x;
+    for (long long i = lb * (kResBX * kResBY) + tid; i < n; i += nb * (kResBX * kResBY)) {
+      const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
+      int d = 0;
+      T S = T(0);
+      S = S + (ix > 0 ? x[i - 1] : T(0));
+      S = S + (ix < nx - 1 ? x[i + 1] : T(0));
+      S = S + (iy > 0 ? x[i - nx] : T(0));
+      S = S + (iy < ny - 1 ? x[i + nx] : T(0));
+      S = S + (iz > 0 ? x[i - (long long)nx * ny] : T(0));
+      S = S + (iz < nz - 1 ? x[i + (long long)nx * ny] : T(0));
+      if (ix == 0) d += G.sh[0];
+      if (ix == nx - 1) d += G.sh[1];
+      if (iy == 0) d += G.sh[2];
+      if (iy == ny - 1) d += G.sh[3];
+      if (iz == 0) d += G.sh[4];
+      if (iz == nz - 1) d += G.sh[5];
+      const double rd = (double)fmat(neg_diag<T>(d), x[i], g[i] + S);
+      acc = fma(rd, rd, acc);
+      if (MODE == 1) outn[i] = rd * c0;
+      if (MODE == 2) outp[i] = (float)(rd * isc);
+    }
+  }
+  return acc;
+}
+
+// Number of blocks of the residual-norm launch for level G (= the number of partial sums).
+__host__ __device__ __forceinline__ int resid_norm_blocks(const Geom& G) {
+  if (!G.packed) return 1;
+  const long long rows = 2LL * G.nz * G.ny;
+  long long blocks = (rows + kResBY - 1) / kResBY;
+  if (blocks > kMaxPartialsPerSystem) blocks = kMaxPartialsPerSystem;
+  return (int)blocks;
+}
+
+// Fixed-order sum of n partials by one block (strided per-thread sums, then block_sum).
+__device__ __forceinline__ double sum_partials(const double* __restrict__ partials, int n, double* red) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nt = blockDim.x * blockDim.y;
+  double acc = 0.0;
+  for (int i = tid; i < n; i += nt) acc += partials[i];
+  return block_sum(acc, red);
+}
+
 }  // namespace ops
 }  // namespace ccmg

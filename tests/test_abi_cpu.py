@@ -81,3 +81,20 @@ def test_null_context_is_invalid():
 
 def test_build_script_uses_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+@needs_nvcc
+def test_batch_create_rejects_invalid_params():
+    lib = _lib.load()
+    arr = (_lib.MgParams * 2)()
+    for b in range(2):
+        lib.mg_default_params(ctypes.byref(arr[b]), 32, 32, 32, 1.0)
+    arr[1].prec = 1  # systems of one batch must share the precision
+    h = ctypes.c_void_p()
+    assert lib.mg_batch_create(2, arr, None, ctypes.byref(h)) == _lib.MG_ERR_INVALID and not h.value
+    assert lib.mg_batch_create(0, arr, None, ctypes.byref(h)) == _lib.MG_ERR_INVALID
+    arr[1].prec = 0
+    arr[1].nx = 30 + 1  # odd
+    assert lib.mg_batch_create(2, arr, None, ctypes.byref(h)) == _lib.MG_ERR_INVALID
+    assert b"even" in lib.mg_batch_last_error(None)
+    assert lib.mg_batch_solve(None, 1e-9, 10, None, None) == _lib.MG_ERR_INVALID

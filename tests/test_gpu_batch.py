@@ -1,0 +1,113 @@
+"""Batched solves over systems of different sizes: bit-identical to single contexts, converged
+per system (checked by the CPU oracle), unaffected by the tile shapes the autotuner picks."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1410_6609_gb300 import synth
+from paper_1410_6609_gb300.batch import BatchPoisson
+from paper_1410_6609_gb300.solver import Poisson
+
+pytestmark = pytest.mark.gpu
+
+D, N = 0, 1
+
+# different sizes and level counts: coarsest grids 4^3, 3^3, 6x5x3 and a single-level 4x4x6
+SYSTEMS = [
+    dict(dims=(32, 32, 32), h=1.0, bc_type=synth.WALL_BC_TYPE, bc_value=synth.wall_bc_value(1.0)),
+    dict(dims=(48, 48, 48), h=0.5, bc_type=(D,) * 6, bc_value=(0.0, 0.1, 0.0, 0.0, 0.0, 1.0)),
+    dict(dims=(24, 40, 12), h=1.0, bc_type=(D, N, N, D, D, N), bc_value=(0.2, 0.0, -0.1, 0.0, 0.0, 0.3)),
+    dict(dims=(64, 32, 48), h=1.0, bc_type=synth.WALL_BC_TYPE, bc_value=synth.wall_bc_value(-0.5)),
+    dict(dims=(4, 4, 6), h=1.0, bc_type=(D, N, N, D, D, N), bc_value=(0.0,) * 6),
+    dict(dims=(96, 96, 96), h=1.0, bc_type=synth.WALL_BC_TYPE, bc_value=synth.wall_bc_value(1.0)),
+]
+
+
+def rhos():
+    return [torch.from_numpy(synth.random_field(s["dims"], 30 + i)).cuda() for i, s in enumerate(SYSTEMS)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_is_bit_identical_to_single_contexts(precision):
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    rho = rhos()
+    Bt = BatchPoisson(SYSTEMS, precision=precision)
+    for b, r in enumerate(rho):
+        Bt.set_rhs(b, r)
+    cyc, rel = Bt.solve(tol, 50)
+    for b, s in enumerate(SYSTEMS):
+        P = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision=precision)
+        P.set_rhs(rho[b])
+        k, r = P.solve(tol, 50)
+        assert (k, r) == (cyc[b], rel[b]), (b, k, cyc[b], r, rel[b])
+        assert torch.equal(P.solution(), Bt.solution(b)), b
+        P.close()
+    Bt.close()
+
+
+def test_batch_converges_per_system_checked_by_oracle():
+    rho = rhos()
+    Bt = BatchPoisson(SYSTEMS, precision="mixed")
+    for b, r in enumerate(rho):
+        Bt.set_rhs(b, r)
+    cyc, rel = Bt.solve(1e-9, 50)
+    assert max(rel) < 1e-9
+    for b, s in enumerate(SYSTEMS):
+        f = oracle.rhs(rho[b].cpu().numpy(), s["h"], s["bc_type"], s["bc_value"])
+        phi = Bt.solution(b).cpu().numpy()
+        assert oracle.rel_residual(phi, f, s["h"], s["bc_type"]) < 1.0001e-9, b
+    Bt.close()
+
+
+def test_tiles_change_speed_not_results():
+    rho = rhos()
+    out = []
+    for tiles in [(64, 4, 64, 4), (16, 16, 32, 8), (128, 2, 128, 2)]:
+        Bt = BatchPoisson(SYSTEMS, precision="mixed")
+        Bt.set_tiles(tiles)
+        assert Bt.tiles() == tiles
+        for b, r in enumerate(rho):
+            Bt.set_rhs(b, r)
+        Bt.solve(1e-9, 50)
+        out.append([Bt.solution(b) for b in range(len(SYSTEMS))])
+        Bt.close()
+    for other in out[1:]:
+        for a, c in zip(out[0], other):
+            assert torch.equal(a, c)
+
+
+def test_autotune_picks_a_candidate(tmp_path, monkeypatch):
+    monkeypatch.setenv("CCMG_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    Bt = BatchPoisson(SYSTEMS[:4], precision="mixed")
+    res = Bt.autotune(reps=2)
+    assert not res["cached"] and len(res["ms"]) >= 4 and min(res["ms"]) > 0
+    assert Bt.tiles() == res["tiles"]
+    Bt2 = BatchPoisson(SYSTEMS[:4], precision="mixed")
+    res2 = Bt2.autotune(reps=2)
+    assert res2["cached"] and Bt2.tiles() == res["tiles"]
+    Bt.close()
+    Bt2.close()
+
+
+def test_batched_workload_64_systems():
+    """The batched charged-sphere workload: 64 systems of 64^3..192^3 with 20..120 spheres each,
+    FP32 cycles inside FP64 defect correction, all to a 1e-9 relative residual in one batch."""
+    ws = synth.batched_workloads()
+    systems = [dict(dims=w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value) for w in ws]
+    Bt = BatchPoisson(systems, precision="mixed")
+    rho = []
+    for b, w in enumerate(ws):
+        sp = w.spheres()
+        P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+        rho.append(P.sphere_density(dev(sp.centers), dev(sp.radius), dev(sp.density), w.subsample))
+        P.close()
+        Bt.set_rhs(b, rho[b])
+    cyc, rel = Bt.solve(1e-9, 50)
+    assert max(rel) < 1e-9 and max(cyc) <= 6
+    for b in (0, 17, 63):  # sampled systems, residual checked by the oracle
+        w = ws[b]
+        f = oracle.rhs(rho[b].cpu().numpy(), w.h, w.bc_type, w.bc_value)
+        assert oracle.rel_residual(Bt.solution(b).cpu().numpy(), f, w.h, w.bc_type) < 1.0001e-9
+    Bt.close()
