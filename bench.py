@@ -163,13 +163,30 @@ def oracle_sample(w, cycles_needed: int):
 
 # ------------------------------------------------------------------------------------------
 
+def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
+    """Maximum of a per-rank scalar over all ranks (the step time every replica waits for)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank: int, world: int, ms: float) -> float:
+    """MLUP/s of the whole job: every replica solves cells_per_rank cells in ms milliseconds."""
+    return world * cells_per_rank / (ms / 1e3) / 1e6
+
+
 def run_reference(args):
     """The oracle on the host cores, on the same workload and metric (bounded per-step sample)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = workload(args)
-    cycles = {"spheres512": 9, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
+    # cycles of the solve to tolerance measured on the GPU (mixed: outer steps of mixed_inner = 4 cycles)
+    cycles = {"spheres512": 3, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
     for _ in range(min(args.warmup, 1)):
         pass
     samples = []
@@ -257,12 +274,8 @@ def run_ours(args):
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = (P.kernel_launches - launches0) // args.steps
-    ms_all = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * N / (ms_all / 1e3) / 1e6
+    ms_all = max_over_ranks(ms, world, "cuda")
+    value = whole_job_mlups(N, world, ms_all)
     k_step = cycles_seen[-1][0]
     rel_final = max(v for _, v in cycles_seen)
 
@@ -337,6 +350,10 @@ def load_peaks():
 # instruction lanes per second at 2070 MHz (152 SMs x ~2 lanes/clk); every DADD/DMUL/DFMA lane is one op.
 FP64_OPS_PEAK = 0.625  # Tops/s
 
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of that kernel on the
+# same workload (profiles/); None where no capture of the current kernel exists.
+MEASURED_TRAFFIC = {}
+
 
 def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     """Kernel-level timings for the roofline, the FP64 GPU solve at the same tolerance, and the
@@ -358,30 +375,35 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     bytes_res = N * (8 + 8 + (4 if mixed else 0))
     ops_res = N * (9 if mixed else 8)
     kern["residual_fp64"] = {"ms": t_res, "GB/s": bytes_res / t_res / 1e6, "Tops/s": ops_res / t_res / 1e9,
-                             "launches_per_step": k_step + 1}
+                             "launches_per_step": k_step + 1, "bytes_per_launch": int(bytes_res)}
     # smoother half-sweep and fused residual+restriction on the finest level
     esz = 4 if mixed else 8
+    inner = P.mixed_inner if mixed else 1  # finest-level V-cycles per outer step
     t_sm = _time(lambda: P.op_smooth(0, 0), stream, 20)
     kern["smooth_half_sweep"] = {"ms": t_sm, "GB/s": 1.5 * N * esz / t_sm / 1e6, "Tops/s": 0.5 * N * 7 / t_sm / 1e9,
-                                 "launches_per_step": 8 * k_step, "precision": "f32" if mixed else "f64"}
+                                 "launches_per_step": 8 * k_step * inner, "precision": "f32" if mixed else "f64",
+                                 "bytes_per_launch": int(1.5 * N * esz)}
     t_rr = _time(lambda: P.op_residual_restrict(0), stream, 20)
     kern["resid_restrict"] = {"ms": t_rr, "GB/s": (2 * N * esz + N * esz / 8) / t_rr / 1e6,
-                              "Tops/s": N * 8 / t_rr / 1e9, "launches_per_step": k_step,
-                              "precision": "f32" if mixed else "f64"}
+                              "Tops/s": N * 8 / t_rr / 1e9, "launches_per_step": k_step * inner,
+                              "precision": "f32" if mixed else "f64",
+                              "bytes_per_launch": int(2 * N * esz + N * esz / 8)}
     # the state changed: restore a consistent solve state for later use
     for name, d in kern.items():
         d["share_ms_per_step"] = d["ms"] * d["launches_per_step"]
     dom = max(kern, key=lambda n: kern[n]["share_ms_per_step"])
     d = kern[dom]
     alu = (dom == "residual_fp64") or (not mixed)
+    traffic = MEASURED_TRAFFIC.get((w.name, dom))
     if alu:
         out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": d["Tops/s"], "peak": FP64_OPS_PEAK,
                            "unit": "Tops/s (FP64 lane-ops)", "frac": d["Tops/s"] / FP64_OPS_PEAK,
-                           "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA=2) at 2070 MHz",
+                           "traffic": traffic, "peak_source": "nominal FP64 1.25 TFLOP/s (FMA=2) at 2070 MHz",
                            "hbm_frac": d["GB/s"] / hbm}
     else:
         out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": d["GB/s"], "peak": hbm, "unit": "GB/s",
-                           "frac": d["GB/s"] / hbm, "traffic": None, "peak_source": src}
+                           "frac": d["GB/s"] / hbm, "traffic": traffic, "peak_source": src,
+                           "algorithmic_bytes": d["bytes_per_launch"]}
     out["kernels"] = kern
 
     # FP64 GPU solve of the same problem to the same tolerance, and the error between them
@@ -415,7 +437,99 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     out["vcycle_mlups"] = {"mixed_outer_cycle": N / tvm / 1e3, "fp64_vcycle": N / tv64 / 1e3,
                            "mixed_outer_cycle_ms": tvm, "fp64_vcycle_ms": tv64}
     P64.close()
+    try:
+        out["batched"] = measure_batched()
+    except Exception as e:  # reported, never fatal for the main line
+        out["batched"] = {"error": repr(e)}
+    try:
+        out["adjoint"] = measure_adjoint()
+    except Exception as e:
+        out["adjoint"] = {"error": repr(e)}
     return out
+
+
+def measure_batched(tol: float = 1e-9):
+    """64 independent charged-sphere systems of 64^3..192^3 solved as one batch (mixed precision)
+    vs the same systems solved one after another with single contexts."""
+    import torch
+
+    from paper_1410_6609_gb300.batch import BatchPoisson
+    from paper_1410_6609_gb300.solver import Poisson
+
+    ws = synth.batched_workloads()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    rho = []
+    for w in ws:
+        sp = w.spheres()
+        P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value)
+        rho.append(P.sphere_density(dev(sp.centers), dev(sp.radius), dev(sp.density), w.subsample))
+        P.close()
+    cells = sum(int(np.prod(w.dims)) for w in ws)
+    systems = [dict(dims=w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value) for w in ws]
+    Bt = BatchPoisson(systems, precision="mixed")
+    tune = Bt.autotune(reps=2)
+    stream = Bt.stream
+
+    def run_batch():
+        for b in range(len(ws)):
+            Bt.set_rhs(b, rho[b])
+            Bt.set_solution(b, None)
+        return Bt.solve(tol, 50)
+
+    cyc, rel = run_batch()
+    l0 = Bt.kernel_launches
+    t_batch = _time(run_batch, stream, 3)
+    launches = (Bt.kernel_launches - l0) // 4
+    Bt.close()
+    singles = [Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="mixed") for w in ws]
+
+    def run_singles():
+        for b, P in enumerate(singles):
+            P.set_rhs(rho[b])
+            P.set_solution(None)
+            P.solve(tol, 50)
+
+    run_singles()
+    t_seq = _time(run_singles, singles[0].stream, 2)
+    for P in singles:
+        P.close()
+    return {"systems": len(ws), "cells": cells, "tol": tol, "tiles": list(tune["tiles"]),
+            "batch_ms": t_batch, "batch_mlups": cells / t_batch / 1e3, "max_cycles": max(cyc),
+            "max_rel_residual": max(rel), "kernel_launches_per_solve": int(launches),
+            "sequential_single_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch}
+
+
+def measure_adjoint():
+    """Adjoint workload: 256^3, 32 spheres; J = sum of z-forces and dJ/d(densities, wall values)
+    through the hand-written autograd functions (forward solve + one adjoint solve)."""
+    import torch
+
+    from paper_1410_6609_gb300.autograd import z_force_objective
+    from paper_1410_6609_gb300.solver import Poisson
+
+    w = synth.WORKLOADS["adjoint256"]
+    sp = w.spheres()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    c, r = dev(sp.centers), dev(sp.radius)
+    res = {}
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-10)):
+        P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision=prec)
+
+        def grad():
+            q = dev(sp.density).requires_grad_(True)
+            v = dev(np.array(w.bc_value)).requires_grad_(True)
+            J = z_force_objective(P, q, v, c, r, w.subsample, tol=tol)
+            J.backward()
+            return q.grad, v.grad
+
+        gq, gv = grad()
+        t = _time(grad, P.stream, 3)
+        res[prec] = {"ms_forward_and_gradient": t, "tol": tol, "dJ_dV_top": float(gv[5])}
+        res[prec + "_grad"] = gq
+        P.close()
+    g64, gm = res.pop("fp64_grad"), res.pop("mixed_grad")
+    res["rel_diff_mixed_vs_fp64_grad"] = float(torch.linalg.norm(gm - g64) / torch.linalg.norm(g64))
+    return res
 
 
 def main():

@@ -64,7 +64,7 @@ struct mg_batch {
   BEntry* d_entries = nullptr;
   int* d_starts = nullptr;
   size_t cap_entries = 0, cap_starts = 0;
-  Plan smooth[kMaxLevels], xfer[kMaxLevels], cg, resid, update;
+  Plan smooth[kMaxLevels], xfer[kMaxLevels], restr[kMaxLevels], cg, resid, update;
   size_t cg_smem = 0;
   int* d_active = nullptr;
   int* h_active = nullptr;
@@ -138,9 +138,10 @@ mg_status plan(mg_batch* b) {
   for (int d = 0; d < kMaxLevels; ++d) {
     b->smooth[d] = Plan();
     b->xfer[d] = Plan();
+    b->restr[d] = Plan();
   }
   for (int d = 0; d + 1 < b->maxL; ++d) {
-    std::vector<BEntry> es, et;
+    std::vector<BEntry> es, et, er;
     for (int s = 0; s < b->B; ++s) {
       BSys& S = b->sys[s];
       if (d >= S.L - 1) continue;
@@ -159,14 +160,19 @@ mg_status plan(mg_batch* b) {
       es1.gy = ceil_div(e.G.ny, sby);
       es1.gz = e.G.nz;
       es.push_back(es1);
-      BEntry et1 = e;
+      BEntry et1 = e;  // prolongation: one thread per coarse cell
       et1.gx = ceil_div(e.Gc.nx, tbx);
       et1.gy = ceil_div(e.Gc.ny, tby);
       et1.gz = e.Gc.nz;
       et.push_back(et1);
+      BEntry er1 = et1;  // residual + restriction: V coarse cells per thread where rows allow
+      er1.vec = (e.G.hx % V == 0) ? 1 : 0;
+      er1.gx = ceil_div(er1.vec ? e.Gc.nx / V : e.Gc.nx, tbx);
+      er.push_back(er1);
     }
     add_plan(b, b->smooth[d], es, dim3(sbx, sby, 1));
     add_plan(b, b->xfer[d], et, dim3(tbx, tby, 1));
+    add_plan(b, b->restr[d], er, dim3(tbx, tby, 1));
   }
   {  // coarsest grids: one CTA each, as many threads as the largest single-system launch would use
     std::vector<BEntry> ec;
@@ -255,7 +261,7 @@ cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cuda
       if ((e = launch_b_smooth<T>(Ls, act, inv, 1, false, s)) != cudaSuccess) return e;
       *nk += 2;
     }
-    if ((e = launch_b_resid_restrict<T>(bl(b, b->xfer[d]), act, s)) != cudaSuccess) return e;
+    if ((e = launch_b_resid_restrict<T>(bl(b, b->restr[d]), act, s)) != cudaSuccess) return e;
     ++*nk;
   }
   if ((e = launch_b_coarse_cg<T>(bl(b, b->cg), act, b->cg_smem, 1e-14, s)) != cudaSuccess) return e;

@@ -58,7 +58,12 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restric
   const Geom G = en.G, Gc = en.Gc;
   const int I = bxi * blockDim.x + threadIdx.x;
   const int J = byi * blockDim.y + threadIdx.y;
-  if (I < Gc.nx && J < Gc.ny) resid_restrict_cell<T>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+  if (en.vec) {
+    constexpr int V = 16 / sizeof(T);
+    if (I < Gc.nx / V && J < Gc.ny) resid_restrict_vec<T, V>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+  } else if (I < Gc.nx && J < Gc.ny) {
+    resid_restrict_cell<T>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+  }
 }
 
 template <typename T>

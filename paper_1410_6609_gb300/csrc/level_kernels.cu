@@ -32,6 +32,17 @@ __global__ void __launch_bounds__(256) k_smooth_vec(T* __restrict__ x, const T* 
   smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
 }
 
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, Geom G,
+                                                            InvDiag<T> inv, const T* __restrict__ ec, Geom Gc,
+                                                            T omega) {
+  const int mv = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (mv >= G.hx / V || j >= G.ny) return;
+  smooth_vec_prolong<T, V>(x, g, G, inv, ec, Gc, omega, mv, j, k);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                         T* __restrict__ gc, Geom Gc) {
@@ -40,6 +51,16 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x,
   const int K = blockIdx.z;
   if (I >= Gc.nx || J >= Gc.ny) return;
   resid_restrict_cell<T>(x, g, G, gc, Gc, I, J, K);
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) k_resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g, Geom G,
+                                                            T* __restrict__ gc, Geom Gc) {
+  const int iv = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (iv >= Gc.nx / V || J >= Gc.ny) return;
+  resid_restrict_vec<T, V>(x, g, G, gc, Gc, iv, J, K);
 }
 
 template <typename T>
@@ -115,6 +136,15 @@ __global__ void k_set_scale(double* scal, int src, int dst, double n) {
 struct WallTerms {
   double t[6];
 };
+__device__ __forceinline__ double add_wall_terms(double v, int i, int j, int k, const Geom& G, const WallTerms& wt) {
+  if (i == 0) v = v + wt.t[0];
+  if (i == G.nx - 1) v = v + wt.t[1];
+  if (j == 0) v = v + wt.t[2];
+  if (j == G.ny - 1) v = v + wt.t[3];
+  if (k == 0) v = v + wt.t[4];
+  if (k == G.nz - 1) v = v + wt.t[5];
+  return v;
+}
 template <typename T>
 __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
                                                  double inv_eps, double hsq, WallTerms wt, int raw) {
@@ -126,12 +156,10 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
   double v = rho[p];
   if (!raw) {
     v = v * inv_eps;
-    if (i == 0) v = v + wt.t[0];
-    if (i == G.nx - 1) v = v + wt.t[1];
-    if (j == 0) v = v + wt.t[2];
-    if (j == G.ny - 1) v = v + wt.t[3];
-    if (k == 0) v = v + wt.t[4];
-    if (k == G.nz - 1) v = v + wt.t[5];
+    // only warps holding wall cells add wall terms (a warp vote keeps the compiler from turning
+    // the rare branches into FP64 adds of zero by every cell)
+    const bool wall = i == 0 || i == G.nx - 1 || j == 0 || j == G.ny - 1 || k == 0 || k == G.nz - 1;
+    if (__any_sync(__activemask(), wall)) v = add_wall_terms(v, i, j, k, G, wt);
   }
   long long o = p;
   if (G.packed) o = (long long)((i + j + k) & 1) * G.csz + ((long long)k * G.ny + j) * G.hx + (i >> 1);
@@ -209,8 +237,31 @@ cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv
   return cudaGetLastError();
 }
 
+cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const InvDiag<float>& inv, const float* ec,
+                                  const Geom& Gc, float omega, cudaStream_t s) {
+  constexpr int V = 4;
+  if (G.hx % V != 0) return cudaErrorInvalidValue;
+  const int nvec = G.hx / V;
+  int bx = 1;
+  while (bx < nvec && bx < 128) bx *= 2;
+  const int by = 256 / bx;
+  dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
+  k_smooth_vec_prolong<float, V><<<gr, b, 0, s>>>(x, g, G, inv, ec, Gc, omega);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, cudaStream_t s) {
+  constexpr int V = 16 / sizeof(T);
+  if (G.hx % V == 0) {
+    const int nvec = Gc.nx / V;
+    int bx = 1;
+    while (bx < nvec && bx < 64) bx *= 2;
+    const int by = 256 / bx;
+    dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (Gc.ny + by - 1) / by, Gc.nz);
+    k_resid_restrict_vec<T, V><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+    return cudaGetLastError();
+  }
   dim3 b, gr;
   shape(Gc.nx, Gc.ny, Gc.nz, b, gr);
   k_resid_restrict<T><<<gr, b, 0, s>>>(x, g, G, gc, Gc);

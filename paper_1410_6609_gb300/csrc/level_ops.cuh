@@ -172,6 +172,118 @@ __device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restric
   store_vec(x + own, out);
 }
 
+// V consecutive coarse values e(I0..I0+V-1, J, K) times omega (I0 a multiple of V), from packed
+// colours (two vectors of V/2) or natural order (one vector).
+template <typename T, int V>
+__device__ __forceinline__ void coarse_row_w(const T* __restrict__ ec, const Geom& Gc, int I0, int J, int K, T omega,
+                                             T (&w)[V]) {
+  if (Gc.packed) {
+    const long long rowc = ((long long)K * Gc.ny + J) * Gc.hx + (I0 >> 1);
+    const int C0 = (I0 + J + K) & 1;  // colour of I0 (and I0+2, ...); I0+1, I0+3 have the other
+    const T* a = ec + (long long)C0 * Gc.csz + rowc;
+    const T* b = ec + (long long)(C0 ^ 1) * Gc.csz + rowc;
+#pragma unroll
+    for (int v = 0; v < V; ++v) w[v] = omega * __ldg(((v & 1) ? b : a) + (v >> 1));
+  } else {
+    const long long o = (long long)I0 + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
+#pragma unroll
+    for (int v = 0; v < V; ++v) w[v] = omega * __ldg(ec + o + v);
+  }
+}
+
+// Index of coarse cell (I,J,K) in its level's storage (packed colours or natural order).
+__device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, int K);
+
+// First post-smoothing half-sweep (black) fused with the constant prolongation of the coarse
+// correction e_c (Sec. 3): every red neighbour is read as red + omega * e_parent, the value the
+// separate prolongation would have stored. A red cell at packed index m of fine row (j', k') has
+// its parent at coarse (m, j'/2, k'/2). The red cells themselves are left uncorrected: the red
+// half-sweep that follows overwrites them without reading them. Same arithmetic as prolongation
+// followed by smooth_vec, hence identical results.
+template <typename T, int V>
+__device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                                   const InvDiag<T>& inv, const T* __restrict__ ec, const Geom& Gc,
+                                                   T omega, int mv, int j, int k) {
+  const int colour = 1;
+  const int m0 = mv * V;
+  const int s = (j + k + colour) & 1;
+  const long long row = ((long long)k * G.ny + j) * G.hx;
+  const long long own = (long long)colour * G.csz + row + m0;
+  int dbase = 0;
+  if (j == 0) dbase += G.sh[2];
+  if (j == G.ny - 1) dbase += G.sh[3];
+  if (k == 0) dbase += G.sh[4];
+  if (k == G.nz - 1) dbase += G.sh[5];
+  const T* yr = x + row;  // red array, row (j,k)
+  const long long plane = (long long)G.ny * G.hx;
+  const int J = j >> 1, K = k >> 1;
+  T gv[V], out[V], yc[V], ym[V], yp[V], zm[V], zp[V], w[V];
+  load_vec(g + own, gv);
+  load_vec(yr + m0, yc);
+  coarse_row_w<T, V>(ec, Gc, m0, J, K, omega, w);
+#pragma unroll
+  for (int v = 0; v < V; ++v) yc[v] = yc[v] + w[v];
+  T extra = T(0);
+  if (s == 0) {
+    if (m0 > 0) extra = __ldg(yr + m0 - 1) + omega * __ldg(ec + coarse_index(Gc, m0 - 1, J, K));
+  } else {
+    if (m0 + V < G.hx) extra = __ldg(yr + m0 + V) + omega * __ldg(ec + coarse_index(Gc, m0 + V, J, K));
+  }
+  if (j > 0) {
+    load_vec(yr + m0 - G.hx, ym);
+    coarse_row_w<T, V>(ec, Gc, m0, (j - 1) >> 1, K, omega, w);
+#pragma unroll
+    for (int v = 0; v < V; ++v) ym[v] = ym[v] + w[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) ym[v] = T(0);
+  }
+  if (j < G.ny - 1) {
+    load_vec(yr + m0 + G.hx, yp);
+    coarse_row_w<T, V>(ec, Gc, m0, (j + 1) >> 1, K, omega, w);
+#pragma unroll
+    for (int v = 0; v < V; ++v) yp[v] = yp[v] + w[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) yp[v] = T(0);
+  }
+  if (k > 0) {
+    load_vec(yr + m0 - plane, zm);
+    coarse_row_w<T, V>(ec, Gc, m0, J, (k - 1) >> 1, omega, w);
+#pragma unroll
+    for (int v = 0; v < V; ++v) zm[v] = zm[v] + w[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) zm[v] = T(0);
+  }
+  if (k < G.nz - 1) {
+    load_vec(yr + m0 + plane, zp);
+    coarse_row_w<T, V>(ec, Gc, m0, J, (k + 1) >> 1, omega, w);
+#pragma unroll
+    for (int v = 0; v < V; ++v) zp[v] = zp[v] + w[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) zp[v] = T(0);
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    T xm, xp;
+    if (s == 0) {
+      xm = (v == 0) ? extra : yc[(v + V - 1) % V];
+      xp = yc[v];
+    } else {
+      xm = yc[v];
+      xp = (v == V - 1) ? extra : yc[(v + 1) % V];
+    }
+    const T S = ((((xm + xp) + ym[v]) + yp[v]) + zm[v]) + zp[v];
+    int d = dbase;
+    if (m0 + v == 0 && s == 0) d += G.sh[0];
+    if (m0 + v == G.hx - 1 && s == 1) d += G.sh[1];
+    out[v] = (gv[v] + S) * inv_of(inv, d);
+  }
+  store_vec(x + own, out);
+}
+
 // Index of coarse cell (I,J,K) in its level's storage (packed colours or natural order).
 __device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, int K) {
   if (Gc.packed) {
@@ -204,6 +316,88 @@ __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, con
         acc = acc + r;
       }
   gc[coarse_index(Gc, I, J, K)] = acc * T(0.25);
+}
+
+// resid_restrict_cell for V consecutive coarse cells I0 = V*iv .. I0+V-1 of coarse row (J,K)
+// (fine rows whose length hx is a multiple of V). Their children in fine row (j,k) are the V
+// consecutive entries I0.. of both colour arrays of that row, so every load is a 16-byte vector
+// plus one scalar per colour; each coarse value is summed in the (dk, dj, di) order of
+// resid_restrict_cell, so the results are identical.
+template <typename T, int V>
+__device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                                   T* __restrict__ gc, const Geom& Gc, int iv, int J, int K) {
+  const int I0 = iv * V;
+  const long long plane = (long long)G.ny * G.hx;
+  T acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = T(0);
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+      const int j = 2 * J + dj, k = 2 * K + dk;
+      const long long row = ((long long)k * G.ny + j) * G.hx;
+      int dyz = 0;
+      if (j == 0) dyz += G.sh[2];
+      if (j == G.ny - 1) dyz += G.sh[3];
+      if (k == 0) dyz += G.sh[4];
+      if (k == G.nz - 1) dyz += G.sh[5];
+      // children di = 0 (colour c0) and di = 1 (colour c1) of the V coarse cells
+      const int c0 = (dj + dk) & 1, c1 = c0 ^ 1;
+      const T* r0 = x + (long long)c0 * G.csz + row;
+      const T* r1 = x + (long long)c1 * G.csz + row;
+      T x0[V], x1[V], g0[V], g1[V];
+      load_vec(r0 + I0, x0);
+      load_vec(r1 + I0, x1);
+      load_vec(g + (long long)c0 * G.csz + row + I0, g0);
+      load_vec(g + (long long)c1 * G.csz + row + I0, g1);
+      const T left = (I0 > 0) ? __ldg(r1 + I0 - 1) : T(0);        // x-neighbour of child (I0, di=0)
+      const T right = (I0 + V < G.hx) ? __ldg(r0 + I0 + V) : T(0);  // x-neighbour of child (I0+V-1, di=1)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const T* y = di == 0 ? r1 : r0;  // the other colour's row
+        T ym[V], yp[V], zm[V], zp[V];
+        if (j > 0) load_vec(y + I0 - G.hx, ym);
+        else
+#pragma unroll
+          for (int v = 0; v < V; ++v) ym[v] = T(0);
+        if (j < G.ny - 1) load_vec(y + I0 + G.hx, yp);
+        else
+#pragma unroll
+          for (int v = 0; v < V; ++v) yp[v] = T(0);
+        if (k > 0) load_vec(y + I0 - plane, zm);
+        else
+#pragma unroll
+          for (int v = 0; v < V; ++v) zm[v] = T(0);
+        if (k < G.nz - 1) load_vec(y + I0 + plane, zp);
+        else
+#pragma unroll
+          for (int v = 0; v < V; ++v) zp[v] = T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int I = I0 + v;
+          T xm, xp, xv, gv;
+          if (di == 0) {  // cell i = 2I: x-neighbours 2I-1 (other colour, index I-1) and 2I+1 (index I)
+            xm = (v == 0) ? left : x1[(v + V - 1) % V];
+            xp = x1[v];
+            xv = x0[v];
+            gv = g0[v];
+          } else {  // cell i = 2I+1: x-neighbours 2I (index I) and 2I+2 (index I+1)
+            xm = x0[v];
+            xp = (v == V - 1) ? right : x0[(v + 1) % V];
+            xv = x1[v];
+            gv = g1[v];
+          }
+          const T S = ((((xm + xp) + ym[v]) + yp[v]) + zm[v]) + zp[v];
+          int d = dyz;
+          if (I == 0 && di == 0) d += G.sh[0];
+          if (I == G.hx - 1 && di == 1) d += G.sh[1];
+          acc[v] = acc[v] + fmat(neg_diag<T>(d), xv, gv + S);
+        }
+      }
+    }
+#pragma unroll
+  for (int v = 0; v < V; ++v) gc[coarse_index(Gc, I0 + v, J, K)] = acc[v] * T(0.25);
 }
 
 // Constant prolongation with the magnified correction (Sec. 3): children += omega * e_parent.
