@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "../../include/ccmg.h"
 #include "ccmg_internal.cuh"
@@ -115,11 +116,21 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
   if ((e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
   ++*nk;
   if ((e = enqueue_vcycle<T>(c, x, g, inv, l + 1, true, s, nk)) != cudaSuccess) return e;
-  if ((e = launch_prolong<T>(x[l], G, x[l + 1], c->geo[l + 1], (T)c->p.cgc_weight, c->p.nu2 >= 1, s)) != cudaSuccess)
-    return e;
-  ++*nk;
+  // single precision, vector rows: the prolongation is fused into the first black half-sweep
+  const bool fuse = std::is_same<T, float>::value && (G.hx % 4 == 0) && c->p.nu2 >= 1;
+  if (!fuse) {
+    if ((e = launch_prolong<T>(x[l], G, x[l + 1], c->geo[l + 1], (T)c->p.cgc_weight, c->p.nu2 >= 1, s)) !=
+        cudaSuccess)
+      return e;
+    ++*nk;
+  }
   for (int it = 0; it < c->p.nu2; ++it) {
-    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s)) != cudaSuccess) return e;
+    if (fuse && it == 0)
+      e = launch_smooth_prolong((float*)x[l], (const float*)g[l], G, c->inv32, (const float*)x[l + 1],
+                                c->geo[l + 1], (float)c->p.cgc_weight, s);
+    else
+      e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s);
+    if (e != cudaSuccess) return e;
     if ((e = launch_smooth<T>(x[l], g[l], G, inv, 0, false, s)) != cudaSuccess) return e;
     *nk += 2;
   }

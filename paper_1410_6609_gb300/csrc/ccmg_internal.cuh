@@ -55,16 +55,6 @@ cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const
                                   const Geom& Gc, float omega, cudaStream_t s);
 template <typename T>
 cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, cudaStream_t s);
-// Temporally blocked single-precision V(2,2) smoothing (fused_kernels.cu): a packed level whose
-// rows are a multiple of 4 long. Pre: 4 half-sweeps + residual/restriction into (gc, Gc), reading
-// xin (unless zero) and writing xout. Post: prolongation of ec into the red neighbours + 4
-// half-sweeps, reading the red part of xin and writing xout.
-bool fused_level_ok(const Geom& G);
-cudaError_t prepare_fused();
-cudaError_t launch_pre_fused(const float* xin, float* xout, const float* g, const Geom& G, const InvDiag<float>& inv,
-                             float* gc, const Geom& Gc, bool zero, cudaStream_t s);
-cudaError_t launch_post_fused(const float* xin, float* xout, const float* g, const Geom& G, const InvDiag<float>& inv,
-                              const float* ec, const Geom& Gc, float omega, cudaStream_t s);
 template <typename T>
 cudaError_t launch_prolong(T* x, const Geom& G, const T* ec, const Geom& Gc, T omega, bool red_only,
                            cudaStream_t s);
