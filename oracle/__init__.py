@@ -58,6 +58,10 @@ def _load():
                 "ccmg_or_levels": (I, [I, I, I, P]),
                 "ccmg_or_apply": (None, [P, P, I, I, I, D, P]),
                 "ccmg_or_apply_f": (None, [P, P, I, I, I, F, P]),
+                "ccmg_or_rbgs_half_f": (None, [P, P, I, I, I, F, P, I]),
+                "ccmg_or_residual_f": (None, [P, P, P, I, I, I, F, P]),
+                "ccmg_or_restrict_f": (None, [P, P, I, I, I]),
+                "ccmg_or_prolong_correct_f": (None, [P, P, I, I, I, F]),
                 "ccmg_or_residual": (None, [P, P, P, I, I, I, D, P]),
                 "ccmg_or_rbgs_half": (None, [P, P, I, I, I, D, P, I]),
                 "ccmg_or_restrict": (None, [P, P, I, I, I]),
@@ -133,6 +137,38 @@ def apply_f32(phi, c: float, bc_type) -> np.ndarray:
     out = np.empty_like(phi)
     _load().ccmg_or_apply_f(_p(phi), _p(out), *_dims(phi), c, _p(_bc(bc_type)))
     return out
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def rbgs_half_f32(phi, f, c: float, bc_type, colour: int) -> np.ndarray:
+    """Single-precision red/black half-sweep (the mixed-precision inner cycle, Sec. 4.3)."""
+    phi = _f32(phi).copy()
+    _load().ccmg_or_rbgs_half_f(_p(phi), _p(_f32(f)), *_dims(phi), c, _p(_bc(bc_type)), colour)
+    return phi
+
+
+def residual_f32(phi, f, c: float, bc_type) -> np.ndarray:
+    phi = _f32(phi)
+    r = np.empty_like(phi)
+    _load().ccmg_or_residual_f(_p(phi), _p(_f32(f)), _p(r), *_dims(phi), c, _p(_bc(bc_type)))
+    return r
+
+
+def restrict_f32(r) -> np.ndarray:
+    r = _f32(r)
+    nz, ny, nx = r.shape
+    fc = np.empty((nz // 2, ny // 2, nx // 2), dtype=np.float32)
+    _load().ccmg_or_restrict_f(_p(r), _p(fc), nx, ny, nz)
+    return fc
+
+
+def prolong_correct_f32(phi, ec, omega: float = 2.0) -> np.ndarray:
+    phi = _f32(phi).copy()
+    _load().ccmg_or_prolong_correct_f(_p(phi), _p(_f32(ec)), *_dims(phi), omega)
+    return phi
 
 
 def residual(phi, f, c: float, bc_type) -> np.ndarray:

@@ -117,6 +117,17 @@ void ccmg_or_prolong_correct(double* phi, const double* ec, int nx, int ny, int 
 void ccmg_or_apply_f(const float* phi, float* out, int nx, int ny, int nz, float c, const int* bc) {
   apply_f(phi, out, nx, ny, nz, c, bc);
 }
+/* Single-precision level operations (the inner cycle of the mixed-precision solve). */
+void ccmg_or_rbgs_half_f(float* phi, const float* f, int nx, int ny, int nz, float c, const int* bc, int colour) {
+  rbgs_half_f(phi, f, nx, ny, nz, c, bc, colour);
+}
+void ccmg_or_residual_f(const float* phi, const float* f, float* r, int nx, int ny, int nz, float c, const int* bc) {
+  residual_f(phi, f, r, nx, ny, nz, c, bc);
+}
+void ccmg_or_restrict_f(const float* r, float* fc, int nx, int ny, int nz) { restrict_avg_f(r, fc, nx, ny, nz); }
+void ccmg_or_prolong_correct_f(float* phi, const float* ec, int nx, int ny, int nz, float omega) {
+  prolong_correct_f(phi, ec, nx, ny, nz, omega);
+}
 
 /* RHS with BCs folded in (Sec. 2.4 and Sec. 4.3 "BC Handling for Scalar Potentials": the RHS
  * is adapted once, on the finest grid only):

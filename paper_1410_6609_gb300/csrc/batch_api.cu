@@ -261,7 +261,9 @@ cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cuda
       if ((e = launch_b_smooth<T>(Ls, act, inv, 1, false, s)) != cudaSuccess) return e;
       *nk += 2;
     }
-    if ((e = launch_b_resid_restrict<T>(bl(b, b->restr[d]), act, s)) != cudaSuccess) return e;
+    // as the single-system cycle: red-only restriction in single precision only
+    const bool red_only = sizeof(T) == sizeof(float) && b->nu1 >= 1;
+    if ((e = launch_b_resid_restrict<T>(bl(b, b->restr[d]), act, red_only, s)) != cudaSuccess) return e;
     ++*nk;
   }
   if ((e = launch_b_coarse_cg<T>(bl(b, b->cg), act, b->cg_smem, 1e-14, s)) != cudaSuccess) return e;

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, c
   }
 }
 
-template <typename T>
+template <typename T, bool RED_ONLY>
 __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restrict__ E, const int* __restrict__ start,
                                                          int count, const int* __restrict__ active) {
   const int e = find_entry(start, count, blockIdx.x);
@@ -60,9 +60,10 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restric
   const int J = byi * blockDim.y + threadIdx.y;
   if (en.vec) {
     constexpr int V = 16 / sizeof(T);
-    if (I < Gc.nx / V && J < Gc.ny) resid_restrict_vec<T, V>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+    if (I < Gc.nx / V && J < Gc.ny)
+      resid_restrict_vec<T, V, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
   } else if (I < Gc.nx && J < Gc.ny) {
-    resid_restrict_cell<T>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+    resid_restrict_cell<T, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
   }
 }
 
@@ -172,9 +173,12 @@ cudaError_t launch_b_smooth(const BLaunch& L, const int* active, const InvDiag<T
 }
 
 template <typename T>
-cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, cudaStream_t s) {
+cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, bool red_only, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  kb_resid_restrict<T><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active);
+  if (red_only)
+    kb_resid_restrict<T, true><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active);
+  else
+    kb_resid_restrict<T, false><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active);
   return cudaGetLastError();
 }
 
@@ -227,7 +231,7 @@ cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, double* scal
 
 #define CCMG_B_INSTANTIATE(T)                                                                                  \
   template cudaError_t launch_b_smooth<T>(const BLaunch&, const int*, const InvDiag<T>&, int, bool, cudaStream_t); \
-  template cudaError_t launch_b_resid_restrict<T>(const BLaunch&, const int*, cudaStream_t);                    \
+  template cudaError_t launch_b_resid_restrict<T>(const BLaunch&, const int*, bool, cudaStream_t);              \
   template cudaError_t launch_b_prolong<T>(const BLaunch&, const int*, T, bool, cudaStream_t);                  \
   template cudaError_t launch_b_coarse_cg<T>(const BLaunch&, const int*, size_t, double, cudaStream_t);
 

@@ -113,7 +113,11 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
     if ((e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s)) != cudaSuccess) return e;
     *nk += 2;
   }
-  if ((e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
+  // single precision: after a black half-sweep the black residuals are at float rounding level,
+  // below what the inner cycle resolves, so only the red residuals are restricted. Double
+  // precision keeps them: near FP64 convergence those rounding residuals are the residual.
+  const bool red_only = std::is_same<T, float>::value && c->p.nu1 >= 1;
+  if ((e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], red_only, s)) != cudaSuccess) return e;
   ++*nk;
   if ((e = enqueue_vcycle<T>(c, x, g, inv, l + 1, true, s, nk)) != cudaSuccess) return e;
   // single precision, vector rows: the prolongation is fused into the first black half-sweep
@@ -631,11 +635,11 @@ mg_status mg_op_residual_restrict(mg_ctx* c, int level) {
   if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "restriction needs a non-coarsest level");
   if (mixed(c))
     CK(launch_resid_restrict<float>(c->x32[level], c->g32[level], c->geo[level], c->g32[level + 1],
-                                    c->geo[level + 1], c->stream),
+                                    c->geo[level + 1], false, c->stream),
        "residual_restrict");
   else
     CK(launch_resid_restrict<double>(c->x64[level], c->g64[level], c->geo[level], c->g64[level + 1],
-                                     c->geo[level + 1], c->stream),
+                                     c->geo[level + 1], false, c->stream),
        "residual_restrict");
   c->launches += 1;
   return MG_OK;

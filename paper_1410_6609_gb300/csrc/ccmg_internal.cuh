@@ -54,7 +54,10 @@ cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv
 cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const InvDiag<float>& inv, const float* ec,
                                   const Geom& Gc, float omega, cudaStream_t s);
 template <typename T>
-cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, cudaStream_t s);
+// red_only: restrict only the red children's residuals (right after a black half-sweep the black
+// residuals are zero up to rounding).
+cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, bool red_only,
+                                  cudaStream_t s);
 template <typename T>
 cudaError_t launch_prolong(T* x, const Geom& G, const T* ec, const Geom& Gc, T omega, bool red_only,
                            cudaStream_t s);
@@ -143,7 +146,7 @@ template <typename T>
 cudaError_t launch_b_smooth(const BLaunch& L, const int* active, const InvDiag<T>& inv, int colour, bool zero,
                             cudaStream_t s);
 template <typename T>
-cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, cudaStream_t s);
+cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, bool red_only, cudaStream_t s);
 template <typename T>
 cudaError_t launch_b_prolong(const BLaunch& L, const int* active, T omega, bool red_only, cudaStream_t s);
 template <typename T>

@@ -43,24 +43,24 @@ __global__ void __launch_bounds__(256) k_smooth_vec_prolong(T* __restrict__ x, c
   smooth_vec_prolong<T, V>(x, g, G, inv, ec, Gc, omega, mv, j, k);
 }
 
-template <typename T>
+template <typename T, bool RED_ONLY>
 __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                         T* __restrict__ gc, Geom Gc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= Gc.nx || J >= Gc.ny) return;
-  resid_restrict_cell<T>(x, g, G, gc, Gc, I, J, K);
+  resid_restrict_cell<T, RED_ONLY>(x, g, G, gc, Gc, I, J, K);
 }
 
-template <typename T, int V>
+template <typename T, int V, bool RED_ONLY>
 __global__ void __launch_bounds__(256) k_resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                             T* __restrict__ gc, Geom Gc) {
   const int iv = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (iv >= Gc.nx / V || J >= Gc.ny) return;
-  resid_restrict_vec<T, V>(x, g, G, gc, Gc, iv, J, K);
+  resid_restrict_vec<T, V, RED_ONLY>(x, g, G, gc, Gc, iv, J, K);
 }
 
 template <typename T>
@@ -251,7 +251,8 @@ cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const
 }
 
 template <typename T>
-cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, cudaStream_t s) {
+cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, bool red_only,
+                                  cudaStream_t s) {
   constexpr int V = 16 / sizeof(T);
   if (G.hx % V == 0) {
     const int nvec = Gc.nx / V;
@@ -259,12 +260,18 @@ cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, 
     while (bx < nvec && bx < 64) bx *= 2;
     const int by = 256 / bx;
     dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (Gc.ny + by - 1) / by, Gc.nz);
-    k_resid_restrict_vec<T, V><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+    if (red_only)
+      k_resid_restrict_vec<T, V, true><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+    else
+      k_resid_restrict_vec<T, V, false><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
     return cudaGetLastError();
   }
   dim3 b, gr;
   shape(Gc.nx, Gc.ny, Gc.nz, b, gr);
-  k_resid_restrict<T><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+  if (red_only)
+    k_resid_restrict<T, true><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+  else
+    k_resid_restrict<T, false><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
   return cudaGetLastError();
 }
 
@@ -368,7 +375,7 @@ cudaError_t launch_update_mixed(double* x, const float* e, long long n, const do
 
 #define CCMG_INSTANTIATE(T)                                                                                         \
   template cudaError_t launch_smooth<T>(T*, const T*, const Geom&, const InvDiag<T>&, int, bool, cudaStream_t);     \
-  template cudaError_t launch_resid_restrict<T>(const T*, const T*, const Geom&, T*, const Geom&, cudaStream_t);    \
+  template cudaError_t launch_resid_restrict<T>(const T*, const T*, const Geom&, T*, const Geom&, bool, cudaStream_t);    \
   template cudaError_t launch_prolong<T>(T*, const Geom&, const T*, const Geom&, T, bool, cudaStream_t);            \
   template cudaError_t launch_coarse_cg<T>(T*, const T*, const Geom&, double, int, int*, cudaStream_t);             \
   template cudaError_t launch_resid_norm<T>(const T*, const T*, const Geom&, double*, int*, int, double, double*,   \

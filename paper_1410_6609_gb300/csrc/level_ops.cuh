@@ -295,8 +295,10 @@ __device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, 
 
 // Fused residual + averaging restriction (Sec. 3; sweeps "Resid" and "Restr" of Sec. 6.3) for
 // coarse cell (I,J,K): the scaled residuals of its 8 children, summed in the order (dk, dj, di),
-// times 1/4 give the coarse scaled right-hand side.
-template <typename T>
+// times 1/4 give the coarse scaled right-hand side. RED_ONLY: the black cells were just updated
+// by a black half-sweep, so their residuals are zero up to rounding and only the 4 red children
+// are summed (same order otherwise).
+template <typename T, bool RED_ONLY = false>
 __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                     T* __restrict__ gc, const Geom& Gc, int I, int J, int K) {
   T acc = T(0);
@@ -308,6 +310,7 @@ __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, con
       for (int di = 0; di < 2; ++di) {
         const int j = 2 * J + dj, k = 2 * K + dk;
         const int c = (di + dj + dk) & 1;  // colour of child (2I+di, j, k)
+        if (RED_ONLY && c == 1) continue;
         const long long row = ((long long)k * G.ny + j) * G.hx;
         const long long own = (long long)c * G.csz + row + I;
         const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, I, di, j, k);
@@ -323,7 +326,7 @@ __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, con
 // consecutive entries I0.. of both colour arrays of that row, so every load is a 16-byte vector
 // plus one scalar per colour; each coarse value is summed in the (dk, dj, di) order of
 // resid_restrict_cell, so the results are identical.
-template <typename T, int V>
+template <typename T, int V, bool RED_ONLY = false>
 __device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                    T* __restrict__ gc, const Geom& Gc, int iv, int J, int K) {
   const int I0 = iv * V;
@@ -349,12 +352,15 @@ __device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, cons
       T x0[V], x1[V], g0[V], g1[V];
       load_vec(r0 + I0, x0);
       load_vec(r1 + I0, x1);
-      load_vec(g + (long long)c0 * G.csz + row + I0, g0);
-      load_vec(g + (long long)c1 * G.csz + row + I0, g1);
-      const T left = (I0 > 0) ? __ldg(r1 + I0 - 1) : T(0);        // x-neighbour of child (I0, di=0)
-      const T right = (I0 + V < G.hx) ? __ldg(r0 + I0 + V) : T(0);  // x-neighbour of child (I0+V-1, di=1)
+      const bool need0 = !RED_ONLY || c0 == 0, need1 = !RED_ONLY || c1 == 0;  // children computed
+      if (need0) load_vec(g + (long long)c0 * G.csz + row + I0, g0);
+      if (need1) load_vec(g + (long long)c1 * G.csz + row + I0, g1);
+      // x-neighbour of child (I0, di=0) and of child (I0+V-1, di=1)
+      const T left = (need0 && I0 > 0) ? __ldg(r1 + I0 - 1) : T(0);
+      const T right = (need1 && I0 + V < G.hx) ? __ldg(r0 + I0 + V) : T(0);
 #pragma unroll
       for (int di = 0; di < 2; ++di) {
+        if (di == 0 ? !need0 : !need1) continue;
         const T* y = di == 0 ? r1 : r0;  // the other colour's row
         T ym[V], yp[V], zm[V], zp[V];
         if (j > 0) load_vec(y + I0 - G.hx, ym);

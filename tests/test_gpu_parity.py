@@ -258,3 +258,78 @@ def test_solve_reports_not_converged():
     with pytest.raises(MgError):
         P.solve(1e-10, 1)
     P.close()
+
+
+@pytest.mark.parametrize("dims,bc", CASES[:2])
+def test_single_precision_level_operations_match_oracle(dims, bc):
+    """The FP32 kernels of the mixed-precision inner cycle against the oracle's single-precision
+    level operations. Both round in float; the GPU multiplies by 1/(6+d) where the oracle
+    divides and contracts with FMA, so agreement is to a few float ulps (rel. 1e-6)."""
+    h = 0.5
+    P = Poisson(dims, h=h, bc_type=bc, precision="mixed")
+    rng = np.random.default_rng(3)
+    tol = 1e-6
+    for l in range(P.num_levels - 1):
+        nx, ny, nz = P.level_dims(l)
+        c = oracle.level_coeff(h, l)
+        phi = rng.standard_normal((nz, ny, nx)).astype(np.float32).astype(np.float64)
+        f = (rng.standard_normal((nz, ny, nx)) * c).astype(np.float32).astype(np.float64)
+        for colour in (0, 1):
+            P.level_set(l, 0, gpu(phi))
+            P.level_set(l, 1, gpu(f))
+            P.op_smooth(l, colour)
+            assert maxrel(cpu(P.level_get(l, 0)), oracle.rbgs_half_f32(phi, f, c, bc, colour)) < tol
+        P.level_set(l, 0, gpu(phi))
+        P.level_set(l, 1, gpu(f))
+        P.op_residual_restrict(l)
+        ref = oracle.restrict_f32(oracle.residual_f32(phi, f, c, bc))
+        # the residual cancels O(1) terms to O(1) results: compare against the operands' scale
+        assert np.abs(cpu(P.level_get(l + 1, 1)) - ref).max() < tol * 8 * np.abs(f).max()
+        ec = rng.standard_normal(tuple(reversed(P.level_dims(l + 1)))).astype(np.float32).astype(np.float64)
+        P.level_set(l, 0, gpu(phi))
+        P.level_set(l + 1, 0, gpu(ec))
+        P.op_prolong_correct(l)
+        assert maxrel(cpu(P.level_get(l, 0)), oracle.prolong_correct_f32(phi, ec, 2.0)) == 0.0
+    P.close()
+
+
+@pytest.mark.parametrize("nu1,nu2,omega,h,eps,bc", [
+    (1, 1, 2.0, 1.0, 1.0, (N, N, N, N, D, D)),
+    (3, 3, 2.0, 0.3, 2.5, (D,) * 6),                      # V(3,3) (the paper's production cycle), h not a power of 2
+    (2, 2, 1.0, 1.0, 1.0, (D, N, N, D, D, N)),            # plain (unmagnified) correction
+    (0, 2, 2.0, 1.0, 1.0, (N, N, N, N, N, D)),            # no pre-smoothing; five Neumann walls
+    (2, 1, 1.7, 0.125, 78.5, (N, D, N, D, D, N)),
+])
+def test_cycle_variants_match_oracle(nu1, nu2, omega, h, eps, bc):
+    dims = (48, 32, 40)
+    bcv = (0.2, -0.1, 0.05, 0.3, -0.4, 0.6)
+    rho = synth.random_field(dims, seed=13)
+    P = Poisson(dims, h=h, bc_type=bc, bc_value=bcv, nu1=nu1, nu2=nu2, cgc_weight=omega, eps=eps)
+    P.set_rhs(gpu(rho))
+    P.set_solution(None)
+    P.vcycle(3)
+    f = oracle.rhs(rho, h, bc, bcv, eps)
+    ref, _ = oracle.vcycles(np.zeros_like(f), f, h, bc, 3, nu1=nu1, nu2=nu2, omega=omega)
+    assert rel(cpu(P.solution()), ref) < TOL
+    rr, r = P.residual(field=True)
+    assert np.linalg.norm(cpu(r) - oracle.residual(ref, f, oracle.level_coeff(h, 0), bc)) / np.linalg.norm(f) < TOL
+    P.close()
+
+
+def test_warm_start_continues_the_iteration():
+    """mg_set_solution restarts from a given potential (warm start of later time steps): k cycles
+    then k more from the saved state equal 2k cycles."""
+    dims = (32, 32, 32)
+    bc = synth.WALL_BC_TYPE
+    rho = synth.random_field(dims, seed=4)
+    P = Poisson(dims, bc_type=bc, bc_value=synth.wall_bc_value(1.0))
+    P.set_rhs(gpu(rho))
+    P.set_solution(None)
+    P.vcycle(2)
+    mid = P.solution().clone()
+    P.vcycle(2)
+    full = P.solution().clone()
+    P.set_solution(mid)
+    P.vcycle(2)
+    assert torch.equal(P.solution(), full)
+    P.close()
