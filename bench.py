@@ -352,7 +352,12 @@ FP64_OPS_PEAK = 0.625  # Tops/s
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of that kernel on the
 # same workload (profiles/); None where no capture of the current kernel exists.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/dram_traffic_spheres512_mixed.md: finest-level FP32 half-sweep, 536.90 MB read + 238.74 MB written
+    ("spheres512", "smooth_half_sweep"): 775_640_000,
+    # same file: FP64 outer residual with the 608-block grid, 3369.18 MB read + 526.74 MB written
+    ("spheres512", "residual_fp64"): 3_895_920_000,
+}
 
 
 def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):

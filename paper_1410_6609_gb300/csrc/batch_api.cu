@@ -68,6 +68,8 @@ struct mg_batch {
   size_t cg_smem = 0;
   int* d_active = nullptr;
   int* h_active = nullptr;
+  int* d_zero = nullptr;  // per system: iterate known to be exactly zero
+  int* h_zero = nullptr;
   double* d_scal = nullptr;
   double* h_scal = nullptr;
   double* d_partials = nullptr;
@@ -295,7 +297,8 @@ cudaError_t enqueue_bcycle(mg_batch* b, cudaStream_t s, long long* nk) {
 
 cudaError_t enqueue_bresid(mg_batch* b, cudaStream_t s, long long* nk) {
   *nk += 2;
-  return launch_b_resid_norm(bl(b, b->resid), b->d_active, bmixed(b) ? 2 : 0, b->d_scal, b->d_partials, s);
+  return launch_b_resid_norm(bl(b, b->resid), b->d_active, b->d_zero, bmixed(b) ? 2 : 0, b->d_scal, b->d_partials,
+                             s);
 }
 
 template <typename F>
@@ -342,15 +345,33 @@ mg_status set_all_active(mg_batch* b, int v) {
   return MG_OK;
 }
 
+mg_status upload_zero(mg_batch* b) {
+  BCK(cudaMemcpyAsync(b->d_zero, b->h_zero, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "zero flags");
+  return MG_OK;
+}
+
+// After a cycle graph ran: the iterates of the systems that took part are no longer zero.
+mg_status clear_zero_of_active(mg_batch* b) {
+  bool changed = false;
+  for (int s = 0; s < b->B; ++s)
+    if (b->h_active[s] && b->h_zero[s]) {
+      b->h_zero[s] = 0;
+      changed = true;
+    }
+  return changed ? upload_zero(b) : MG_OK;
+}
+
 void free_batch(mg_batch* b) {
   destroy_graphs(b);
   cudaFree(b->arena);
   cudaFree(b->d_entries);
   cudaFree(b->d_starts);
   cudaFree(b->d_active);
+  cudaFree(b->d_zero);
   cudaFree(b->d_scal);
   cudaFree(b->d_partials);
   if (b->h_active) cudaFreeHost(b->h_active);
+  if (b->h_zero) cudaFreeHost(b->h_zero);
   if (b->h_scal) cudaFreeHost(b->h_scal);
   if (b->cap) cudaStreamDestroy(b->cap);
 }
@@ -468,6 +489,8 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
   }
   cudaError_t e = cudaMalloc((void**)&b->arena, bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_active, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_zero, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_zero, B * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_scal, (size_t)B * kScalStride * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_active, B * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_scal, (size_t)B * kScalStride * sizeof(double));
@@ -497,8 +520,10 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
       }
     }
   }
+  for (int s = 0; s < B; ++s) b->h_zero[s] = 1;  // the arena starts zeroed
   mg_status st = plan(b);
   if (st == MG_OK) st = set_all_active(b, 1);
+  if (st == MG_OK) st = upload_zero(b);
   if (st != MG_OK) {
     std::string msg = b->err;
     free_batch(b);
@@ -540,7 +565,8 @@ mg_status mg_batch_set_solution(mg_batch* b, int s, const double* d_phi) {
   if (st != MG_OK) return st;
   BCK(launch_pack<double>(b->sys[s].x64[0], b->sys[s].geo[0], d_phi, 1.0, b->stream), "batch set_solution");
   b->launches += 1;
-  return MG_OK;
+  b->h_zero[s] = (d_phi == nullptr) ? 1 : 0;
+  return upload_zero(b);
 }
 
 mg_status mg_batch_get_solution(mg_batch* b, int s, double* d_phi) {
@@ -560,6 +586,7 @@ mg_status mg_batch_vcycle(mg_batch* b, int ncycles) {
   for (int k = 0; k < ncycles && st == MG_OK; ++k) {
     if (bmixed(b)) st = brun(b, b->g_resid, b->n_resid, "batch residual");
     if (st == MG_OK) st = brun(b, b->g_cycle, b->n_cycle, "batch cycle");
+    if (st == MG_OK) st = clear_zero_of_active(b);
   }
   return st;
 }
@@ -595,6 +622,7 @@ mg_status mg_batch_solve(mg_batch* b, double tol, int max_cycles, int* h_cycles,
     if (!any) break;
     BCK(cudaMemcpyAsync(b->d_active, b->h_active, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "active");
     if ((st = brun(b, b->g_cycle, b->n_cycle, "batch cycle")) != MG_OK) return st;
+    if ((st = clear_zero_of_active(b)) != MG_OK) return st;
     for (int s = 0; s < b->B; ++s) cyc[s] += b->h_active[s];
   }
   bool all = true;
@@ -660,6 +688,9 @@ mg_status mg_batch_autotune(mg_batch* b, int reps, int* h_best4, double* h_ms, i
   if (h_ncand) *h_ncand = kNumCandidates;
   if (h_best4)
     for (int q = 0; q < 4; ++q) h_best4[q] = kCandidates[bi][q];
+  // the timed cycles may have changed the iterates: no longer known to be zero
+  for (int s = 0; s < b->B; ++s) b->h_zero[s] = 0;
+  if ((st = upload_zero(b)) != MG_OK) return st;
   return mg_batch_set_tiles(b, kCandidates[bi]);
 }
 

@@ -114,13 +114,16 @@ __global__ void __launch_bounds__(256) kb_resid_norm(const BEntry* __restrict__ 
 }
 
 __global__ void __launch_bounds__(256) kb_finalize(const BEntry* __restrict__ E, const int* __restrict__ start,
-                                                   const int* __restrict__ active, const double* __restrict__ partials,
-                                                   double* __restrict__ scal) {
+                                                   const int* __restrict__ active, const int* __restrict__ zero,
+                                                   const double* __restrict__ partials, double* __restrict__ scal) {
   __shared__ double red[33];
   const int e = blockIdx.x;
   const int sys = E[e].sys;
   if (!active[sys]) return;
-  const double acc = sum_partials(partials + start[e], start[e + 1] - start[e], red);
+  double acc = sum_partials(partials + start[e], start[e + 1] - start[e], red);
+  // a zero iterate has r = f exactly; its norm is the one taken when f was set (as a single
+  // context reports it without evaluating the stencil)
+  if (zero[sys]) acc = scal[kScalStride * sys + kSlotGsum];
   if (threadIdx.x == 0) {
     double* sc = scal + kScalStride * sys;
     sc[kSlotRsum] = acc;
@@ -203,8 +206,8 @@ cudaError_t prepare_b_coarse_cg() {
   return cudaFuncSetAttribute(kb_coarse_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, int mode, double* scal, double* partials,
-                                cudaStream_t s) {
+cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* zero, int mode, double* scal,
+                                double* partials, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
   const dim3 b(kResBX, kResBY, 1);
   if (mode == 2)
@@ -213,7 +216,7 @@ cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, int mode, d
     kb_resid_norm<0><<<L.blocks, b, 0, s>>>(L.entries, L.start, L.count, active, scal, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  kb_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, partials, scal);
+  kb_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, zero, partials, scal);
   return cudaGetLastError();
 }
 

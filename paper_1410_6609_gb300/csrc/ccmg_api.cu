@@ -43,7 +43,9 @@ struct mg_ctx {
   FaceBC bc{};
   cudaGraphExec_t g_cycle = nullptr;
   cudaGraphExec_t g_resid = nullptr;
-  long long n_cycle = 0, n_resid = 0;  // kernel nodes per graph
+  cudaGraphExec_t g_resid0 = nullptr;  // the termination residual of a zero iterate (r = f)
+  long long n_cycle = 0, n_resid = 0, n_resid0 = 0;  // kernel nodes per graph
+  bool phi_zero = true;                // the finest iterate is known to be exactly zero
   long long launches = 0;
   double* d_rho = nullptr;  // step_host scratch: density field
   double* d_sph = nullptr;  // step_host scratch: 8*P doubles (centres, radius, density, forces)
@@ -76,6 +78,7 @@ double level_coeff(const mg_ctx* c, int l) { return 1.0 / (std::ldexp(1.0, l) * 
 void free_all(mg_ctx* c) {
   if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
   if (c->g_resid) cudaGraphExecDestroy(c->g_resid);
+  if (c->g_resid0) cudaGraphExecDestroy(c->g_resid0);
   for (int l = 0; l < kMaxLevels; ++l) {
     cudaFree(c->x64[l]);
     cudaFree(c->g64[l]);
@@ -196,9 +199,17 @@ mg_status ensure_graphs(mg_ctx* c) {
                          [c](cudaStream_t s, long long* nk) { return enqueue_cycle(c, s, nk); }, "capture cycle");
   if (st != MG_OK) return st;
   const int mode = mixed(c) ? 2 : 0;
-  return capture(c, &c->g_resid, &c->n_resid,
-                 [c, mode](cudaStream_t s, long long* nk) { return enqueue_resid(c, mode, nullptr, s, nk); },
-                 "capture residual");
+  st = capture(c, &c->g_resid, &c->n_resid,
+               [c, mode](cudaStream_t s, long long* nk) { return enqueue_resid(c, mode, nullptr, s, nk); },
+               "capture residual");
+  if (st != MG_OK) return st;
+  return capture(c, &c->g_resid0, &c->n_resid0,
+                 [c](cudaStream_t s, long long* nk) {
+                   ++*nk;
+                   return launch_resid_zero(c->g64[0], cells(c->geo[0]), mixed(c) ? c->g32[0] : nullptr, c->scal,
+                                            S_RSUM, S_REL, S_GSUM, S_INV_SCALE, s);
+                 },
+                 "capture zero residual");
 }
 
 mg_status run_graph(mg_ctx* c, cudaGraphExec_t g, long long nodes, const char* what) {
@@ -209,7 +220,9 @@ mg_status run_graph(mg_ctx* c, cudaGraphExec_t g, long long nodes, const char* w
 
 // Relative residual of the current state: run the residual graph, read scal[S_REL].
 mg_status read_rel(mg_ctx* c, double* rel) {
-  mg_status st = run_graph(c, c->g_resid, c->n_resid, "residual");
+  // a zero iterate has r = f: its residual needs no stencil evaluation
+  mg_status st = c->phi_zero ? run_graph(c, c->g_resid0, c->n_resid0, "residual")
+                             : run_graph(c, c->g_resid, c->n_resid, "residual");
   if (st != MG_OK) return st;
   CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read residual");
   CK(cudaStreamSynchronize(c->stream), "residual sync");
@@ -417,6 +430,7 @@ mg_status mg_set_solution(mg_ctx* c, const double* d_phi) {
   if (!c) return MG_ERR_INVALID;
   CK(launch_pack<double>(c->x64[0], c->geo[0], d_phi, 1.0, c->stream), "set_solution");
   c->launches += 1;
+  c->phi_zero = (d_phi == nullptr);
   return MG_OK;
 }
 
@@ -434,8 +448,13 @@ mg_status mg_vcycle(mg_ctx* c, int ncycles) {
   mg_status st = ensure_graphs(c);
   if (st != MG_OK) return st;
   for (int k = 0; k < ncycles; ++k) {
-    if (mixed(c) && (st = run_graph(c, c->g_resid, c->n_resid, "residual")) != MG_OK) return st;
+    if (mixed(c)) {
+      if (c->phi_zero) st = run_graph(c, c->g_resid0, c->n_resid0, "residual");
+      else st = run_graph(c, c->g_resid, c->n_resid, "residual");
+      if (st != MG_OK) return st;
+    }
     if ((st = run_graph(c, c->g_cycle, c->n_cycle, "cycle")) != MG_OK) return st;
+    c->phi_zero = false;
   }
   return MG_OK;
 }
@@ -465,6 +484,7 @@ mg_status mg_solve(mg_ctx* c, double tol, int max_cycles, int* h_cycles, double*
       break;
     }
     if ((st = run_graph(c, c->g_cycle, c->n_cycle, "cycle")) != MG_OK) return st;
+    c->phi_zero = false;
     ++k;
   }
   if (h_cycles) *h_cycles = k;
@@ -598,6 +618,7 @@ mg_status mg_level_set(mg_ctx* c, int level, int which, const double* d_in) {
   else
     CK(launch_pack<double>(which == 0 ? c->x64[level] : c->g64[level], c->geo[level], d_in, scale, c->stream),
        "level_set");
+  if (!mixed(c) && level == 0 && which == 0) c->phi_zero = false;
   c->launches += 1;
   return MG_OK;
 }
@@ -618,6 +639,7 @@ mg_status mg_level_get(mg_ctx* c, int level, int which, double* d_out) {
 }
 
 mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
+  if (c && !mixed(c) && level == 0) c->phi_zero = false;
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1 || (colour != 0 && colour != 1))
     return fail(c, MG_ERR_INVALID, "smoothing needs a non-coarsest level and colour 0 or 1");
@@ -646,6 +668,7 @@ mg_status mg_op_residual_restrict(mg_ctx* c, int level) {
 }
 
 mg_status mg_op_prolong_correct(mg_ctx* c, int level) {
+  if (c && !mixed(c) && level == 0) c->phi_zero = false;
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "prolongation needs a non-coarsest level");
   if (mixed(c))
@@ -665,6 +688,7 @@ mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
   const int l = c->L - 1;
   const Geom& G = c->geo[l];
   const int n = G.nx * G.ny * G.nz;
+  if (!mixed(c) && l == 0) c->phi_zero = false;  // single-level grid: the CG writes the finest iterate
   if (mixed(c))
     CK(launch_coarse_cg<float>(c->x32[l], c->g32[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
   else

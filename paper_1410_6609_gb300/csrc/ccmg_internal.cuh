@@ -25,7 +25,9 @@ namespace ccmg {
 
 constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarseCells = 4096;
-constexpr int kMaxPartialsPerSystem = 1216;  // residual-norm blocks of one system (8 per SM)
+// Residual-norm blocks of one system: the co-resident count (152 SMs x 4 blocks of 64x4 threads
+// at <= 64 registers), so that the z-neighbour rows a block reads are still in L2.
+constexpr int kMaxPartialsPerSystem = 608;
 
 struct Geom {
   int nx, ny, nz;  // cells per axis
@@ -95,6 +97,10 @@ template <typename T>
 cudaError_t launch_pack(T* dst, const Geom& G, const double* src, double scale, cudaStream_t s);
 template <typename T>
 cudaError_t launch_unpack(double* dst, const T* src, const Geom& G, double scale, cudaStream_t s);
+// Termination residual of a zero iterate (r = f exactly): scal[rsum] = scal[gsum], scal[rel] = 1
+// (0 if f = 0); with outp also float(g * scal[inv_scale]) over n entries (mixed precision).
+cudaError_t launch_resid_zero(const double* g, long long n, float* outp, double* scal, int slot_rsum, int slot_rel,
+                              int slot_gsum, int slot_inv_scale, cudaStream_t s);
 // x64 += scal[slot] * double(e32) elementwise over n entries.
 cudaError_t launch_update_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
 
@@ -157,8 +163,9 @@ constexpr int kScalStride = 8;
 constexpr int kSlotGsum = 0, kSlotRsum = 1, kSlotRel = 2, kSlotScale = 3, kSlotInvScale = 4;
 // FP64 residual of every system's finest level (mode 0 or 2, as launch_resid_norm), per-block
 // partials, then one finalize block per system: rsum, rel = sqrt(rsum / gsum) in its slots.
-cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, int mode, double* scal, double* partials,
-                                cudaStream_t s);
+// zero[s] != 0: system s's iterate is exactly zero, its norm is taken from the gsum slot.
+cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* zero, int mode, double* scal,
+                                double* partials, cudaStream_t s);
 // x64 += scale * double(e32) on every active system's finest level (update entries).
 cudaError_t launch_b_update(const BLaunch& L, const int* active, const double* scal, cudaStream_t s);
 // scale = sqrt(rsum / n) (1 if not positive and finite), inv_scale = 1 / scale, per system.

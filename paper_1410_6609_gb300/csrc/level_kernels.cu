@@ -192,6 +192,24 @@ __global__ void __launch_bounds__(256) k_unpack(double* __restrict__ dst, const 
   dst[p] = (double)src[o] * scale;
 }
 
+// Termination residual of a zero iterate: r = f exactly (g + 0 - (6+d) 0 = g), so ||r|| = ||f||
+// and the relative residual is 1 (0 for f = 0). Writes the scalars; with outp also the scaled
+// single-precision residual float(g * inv_scale), the values the residual kernel would produce.
+__global__ void __launch_bounds__(256) k_resid_zero(const double* __restrict__ g, long long n, float* __restrict__ outp,
+                                                    double* __restrict__ scal, int slot_rsum, int slot_rel,
+                                                    int slot_gsum, int slot_inv_scale) {
+  const double gsum = scal[slot_gsum];
+  if (outp) {
+    const double isc = scal[slot_inv_scale];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      outp[i] = (float)(g[i] * isc);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[slot_rsum] = gsum;
+    scal[slot_rel] = gsum > 0.0 ? sqrt(gsum) / sqrt(gsum) : 0.0;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_update_mixed(double* __restrict__ x, const float* __restrict__ e, long long n,
                                                       const double* __restrict__ scal, int slot) {
   const double sc = scal[slot];
@@ -362,6 +380,14 @@ cudaError_t launch_unpack(double* dst, const T* src, const Geom& G, double scale
   dim3 b, gr;
   shape(G.nx, G.ny, G.nz, b, gr);
   k_unpack<T><<<gr, b, 0, s>>>(dst, src, G, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_zero(const double* g, long long n, float* outp, double* scal, int slot_rsum, int slot_rel,
+                              int slot_gsum, int slot_inv_scale, cudaStream_t s) {
+  long long blocks = outp ? (n + 255) / 256 : 1;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_resid_zero<<<(int)blocks, 256, 0, s>>>(g, n, outp, scal, slot_rsum, slot_rel, slot_gsum, slot_inv_scale);
   return cudaGetLastError();
 }
 
