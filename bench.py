@@ -36,7 +36,7 @@ METRIC = "V-cycle MLUP/s & time-to-1e-9 residual vs FP64 GPU; % HBM roofline"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="spheres512", choices=sorted(synth.WORKLOADS))
@@ -66,15 +66,21 @@ def workload_config(w, rank_seed_offset=0):
 # ------------------------------------------------------------------------------------------
 # Clock sampling during the timed region
 
-CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
 
 class ClockSampler:
+    """nvidia-smi sampling every 50 ms, started before the warm-up; summary() keeps the samples
+    whose timestamps fall inside the marked timed region (the nearest ones if it was shorter than
+    the sampling period)."""
+
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu_index = gpu_index
+        self.window = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
@@ -82,11 +88,21 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={CLOCK_FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        t_end = time.time() + 5.0  # the first sample, so that the timed region is covered
+        while time.time() < t_end and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
         return self
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -97,26 +113,39 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
-    def summary(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    def _rows(self):
+        import datetime
+        rows = []
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return rows
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = self._rows()
+        if self.window is not None and rows:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if not inside:  # region shorter than the period: the samples nearest to it
+                mid = 0.5 * (t0 + t1)
+                inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+            rows = inside
+        reasons = {nm for r in rows for nm, v in zip(CLOCK_REASONS, r[3]) if v.lower().startswith("active")}
+        out = {"sm_mhz": statistics.median(r[1] for r in rows) if rows else None,
+               "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+               "reasons": sorted(reasons), "samples": len(rows), "period_ms": 50}
+        if self.window is not None:
+            out["window_ms"] = round(1e3 * (self.window[1] - self.window[0]), 1)
+        return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -256,21 +285,23 @@ def run_ours(args):
         P.force_gather(c, r, q, w.subsample, out=F)
         cycles_seen.append((k, rel))
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    cycles_seen.clear()
-    launches0 = P.kernel_launches
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        cycles_seen.clear()
+        launches0 = P.kernel_launches
         barrier()
         torch.cuda.synchronize()
+        t_wall0 = time.time()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(t_wall0, time.time())
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = (P.kernel_launches - launches0) // args.steps
@@ -380,7 +411,8 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     bytes_res = N * (8 + 8 + (4 if mixed else 0))
     ops_res = N * (9 if mixed else 8)
     kern["residual_fp64"] = {"ms": t_res, "GB/s": bytes_res / t_res / 1e6, "Tops/s": ops_res / t_res / 1e9,
-                             "launches_per_step": k_step + 1, "bytes_per_launch": int(bytes_res)}
+                             "launches_per_step": k_step, "bytes_per_launch": int(bytes_res),
+                             "note": "plus one stencil-free residual of the zero start per step"}
     # smoother half-sweep and fused residual+restriction on the finest level
     esz = 4 if mixed else 8
     inner = P.mixed_inner if mixed else 1  # finest-level V-cycles per outer step

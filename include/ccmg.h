@@ -170,8 +170,35 @@ mg_status mg_op_coarse_solve(mg_ctx* ctx, int* h_iters);
  * the next inner cycle solves for), without reading anything back. For timing that kernel. */
 mg_status mg_op_residual_norm(mg_ctx* ctx);
 
+/* The power-of-two products and precision conversions on caller data, for verifying them (not in
+ * the paper): d_xf[i] = float(d_x[i] * (1/sc)) as MG_MIXED hands the outer residual to the inner
+ * cycles, d_yo[i] = fma(sc, double(d_e[i]), d_y[i]) as it adds the correction, d_xs[i] =
+ * d_x[i] * sc as the right-hand side and E-field kernels apply 1/eps, h^2 and 1/(2h). For a
+ * power-of-two sc these run as integer exponent arithmetic with one round-to-nearest-even (the
+ * solver's scales are powers of two in [2^-800, 2^800]); any other sc > 0 takes the plain
+ * floating-point formula. n elements of device memory each, borrowed; enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default); no context. MG_ERR_INVALID for n < 0, null pointers
+ * with n > 0, or sc not positive and finite with a finite 1/sc; MG_ERR_CUDA on a failed launch. */
+mg_status mg_op_scale_convert(const double* d_x, const float* d_e, const double* d_y, long long n, double sc,
+                              float* d_xf, double* d_yo, double* d_xs, void* stream);
+
 /* Number of kernels this context has enqueued since creation (graph nodes included). */
 long long mg_kernel_launches(const mg_ctx* ctx);
+/* Which kernel performs the half-sweeps of a non-coarsest level: 1 = the TMA-staged z-slab
+ * kernel, 0 = the vectorised direct-load kernel; -1 for an invalid context or level. Both give
+ * bit-identical results. MG_MIXED takes the TMA kernel on single-precision levels with rows of
+ * whole 4-float vectors, at least 8 planes and 2^24 cells per colour (where it measured faster).
+ * The environment variable CCMG_SWEEP, read by mg_create, overrides this: "vec" never uses it,
+ * "tma" uses it on every level it can run on (2^16 cells per colour and up). */
+int mg_level_sweep_kind(const mg_ctx* ctx, int level);
+/* Self-test of the device-side failure path (not in the paper): runs one TMA-staged red
+ * half-sweep of `level` in which every CTA leaves one of its plane copies unissued, with a wait
+ * budget of 2e7 clock cycles (about 10 ms). Each CTA's wait for that copy runs out; it sets the
+ * context's error flag, waits for the copies it did issue and returns without writing the level.
+ * Returns MG_ERR_TIMEOUT when the flag came back as expected (and clears it; later calls work
+ * normally), MG_OK if it did not, MG_ERR_INVALID if the level has no TMA-staged sweep (see
+ * mg_level_sweep_kind). Synchronises. Solves report the same flag as MG_ERR_TIMEOUT. */
+mg_status mg_selftest_wait_timeout(mg_ctx* ctx, int level);
 
 /* ----------------------------------------------------------------------------------------- */
 /* Batches: B independent problems (own dimensions, cell size, walls, right-hand side; not in the

@@ -381,9 +381,22 @@ int ccmg_or_solve(double* phi, const double* f, int nx, int ny, int nz, double h
   return k;
 }
 
+/* Largest power of two not above v (for finite v > 0; exponent clamped to [-1000, 1000]),
+ * else 1. */
+static double pow2_floor(double v) {
+  if (!(v > 0.0) || !(v < 1e300)) return 1.0;
+  int e = 0;
+  frexp(v, &e); /* v = m 2^e with 0.5 <= m < 1 */
+  e -= 1;
+  if (e < -1000) e = -1000;
+  if (e > 1000) e = 1000;
+  return ldexp(1.0, e);
+}
+
 /* Mixed-precision defect correction (not in the paper; the cycle is the paper's):
  *   loop: r = f - A_0 phi (double); stop if ||r||/||f|| < tol;
- *         s = RMS of the previous residual (||f|| RMS on the first pass);
+ *         s = the largest power of two not above the RMS of the previous residual (of f on
+ *         the first pass), so that r / s and s e are exact;
  *         `inner` single-precision V-cycles on A_0 e = r / s, the first from e = 0 (double CG
  *         at the bottom);
  *         phi += s * e (double).
@@ -395,8 +408,7 @@ int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, do
   hier_init(&H, nx, ny, nz, 1);
   const size_t n = (size_t)nx * ny * nz;
   const double fn = norm2_d(f, n);
-  double scale = fn / sqrt((double)n);
-  if (!(scale > 0.0)) scale = 1.0;
+  double scale = pow2_floor(fn / sqrt((double)n));
   int k = 0;
   double rel;
   for (;;) {
@@ -412,7 +424,7 @@ int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, do
     for (size_t q = 0; q < n; ++q) phi[q] = phi[q] + scale * (double)H.phif[0][q];
     ++k;
     const double next = rn / sqrt((double)n);
-    if (next > 0.0) scale = next;
+    if (next > 0.0) scale = pow2_floor(next);
   }
   if (rel_res_out) *rel_res_out = rel;
   hier_free(&H);

@@ -74,7 +74,10 @@ SIGNATURES = {
     "mg_op_prolong_correct": (_I, [_P, _I]),
     "mg_op_coarse_solve": (_I, [_P, _P]),
     "mg_op_residual_norm": (_I, [_P]),
+    "mg_op_scale_convert": (_I, [_P, _P, _P, ctypes.c_longlong, _D, _P, _P, _P, _P]),
     "mg_kernel_launches": (ctypes.c_longlong, [_P]),
+    "mg_level_sweep_kind": (_I, [_P, _I]),
+    "mg_selftest_wait_timeout": (_I, [_P, _I]),
     "mg_residual_norm_static": (_I, [_I, _I, _I, _D, _P, _P, _P, _P, _P]),
     "mg_batch_create": (_I, [_I, _P, _P, _P]),
     "mg_batch_destroy": (_I, [_P]),

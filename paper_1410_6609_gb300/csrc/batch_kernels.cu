@@ -144,7 +144,12 @@ __global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, c
   double* x = (double*)en.x;
   const float* ev = (const float*)en.aux;
   const double sc = scal[kScalStride * en.sys + kSlotScale];
-  for (long long i = lb * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) x[i] = fma(sc, (double)ev[i], x[i]);
+  const int p = pow2_exponent(sc);
+  const long long i0 = lb * blockDim.x + threadIdx.x, st = nb * blockDim.x;
+  if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
+    for (long long i = i0; i < n; i += st) x[i] = x[i] + f64_of_scaled(ev[i], p);
+  else
+    for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)ev[i], x[i]);
 }
 
 __global__ void kb_set_scale(const BEntry* __restrict__ E, int count, const int* __restrict__ active,
@@ -156,8 +161,7 @@ __global__ void kb_set_scale(const BEntry* __restrict__ E, int count, const int*
   const Geom G = E[e].G;
   const double n = (double)(G.packed ? 2 * G.csz : G.csz);
   double* sc = scal + kScalStride * sys;
-  const double v = sqrt(sc[kSlotRsum] / n);
-  const double s = (v > 0.0 && v == v && v < 1e300) ? v : 1.0;
+  const double s = pow2_floor(sqrt(sc[kSlotRsum] / n));
   sc[kSlotScale] = s;
   sc[kSlotInvScale] = 1.0 / s;
 }

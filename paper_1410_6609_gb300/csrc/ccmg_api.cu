@@ -7,6 +7,7 @@
 // small graph (residual norm + fixed-order reduction) followed by one 8-byte read-back.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -50,6 +51,8 @@ struct mg_ctx {
   double* d_rho = nullptr;  // step_host scratch: density field
   double* d_sph = nullptr;  // step_host scratch: 8*P doubles (centres, radius, density, forces)
   int sph_cap = 0;
+  TmaSweep tma[kMaxLevels]{};  // TMA-staged single-precision half-sweeps, per level
+  int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   std::string err;
 };
 
@@ -90,12 +93,23 @@ void free_all(mg_ctx* c) {
   cudaFree(c->d_iters);
   cudaFree(c->d_rho);
   cudaFree(c->d_sph);
+  cudaFree(c->d_err);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   if (c->cap) cudaStreamDestroy(c->cap);
 }
 
 // ------------------------------------------------------------------------------------------
 // Enqueue helpers (usable inside stream capture)
+
+// One half-sweep of level l: the TMA-staged kernel where the level has one (single precision,
+// not from a zero iterate), else the vectorised one; identical results.
+template <typename T>
+cudaError_t sweep(mg_ctx* c, T* x, const T* g, const InvDiag<T>& inv, int l, int colour, bool zero, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value)
+    if (!zero && c->tma[l].ok && x == c->x32[l] && g == c->g32[l])
+      return launch_smooth_tma(x, c->geo[l], inv, colour, c->tma[l], c->d_err, s);
+  return launch_smooth<T>(x, g, c->geo[l], inv, colour, zero, s);
+}
 
 template <typename T>
 cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>& inv, int l, bool zero,
@@ -112,8 +126,8 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
     if (e != cudaSuccess) return e;
   }
   for (int it = 0; it < c->p.nu1; ++it) {
-    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 0, zero && it == 0, s)) != cudaSuccess) return e;
-    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s)) != cudaSuccess) return e;
+    if ((e = sweep<T>(c, x[l], g[l], inv, l, 0, zero && it == 0, s)) != cudaSuccess) return e;
+    if ((e = sweep<T>(c, x[l], g[l], inv, l, 1, false, s)) != cudaSuccess) return e;
     *nk += 2;
   }
   // single precision: after a black half-sweep the black residuals are at float rounding level,
@@ -136,9 +150,9 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
       e = launch_smooth_prolong((float*)x[l], (const float*)g[l], G, c->inv32, (const float*)x[l + 1],
                                 c->geo[l + 1], (float)c->p.cgc_weight, s);
     else
-      e = launch_smooth<T>(x[l], g[l], G, inv, 1, false, s);
+      e = sweep<T>(c, x[l], g[l], inv, l, 1, false, s);
     if (e != cudaSuccess) return e;
-    if ((e = launch_smooth<T>(x[l], g[l], G, inv, 0, false, s)) != cudaSuccess) return e;
+    if ((e = sweep<T>(c, x[l], g[l], inv, l, 0, false, s)) != cudaSuccess) return e;
     *nk += 2;
   }
   return cudaSuccess;
@@ -218,6 +232,16 @@ mg_status run_graph(mg_ctx* c, cudaGraphExec_t g, long long nodes, const char* w
   return MG_OK;
 }
 
+// The device error flag as read into h_pin[1]: a kernel whose bounded wait ran out (the result
+// of that launch is incomplete). The flag is cleared for the calls that follow.
+mg_status check_err_flag(mg_ctx* c) {
+  int flag = 0;
+  std::memcpy(&flag, c->h_pin + 1, sizeof(int));
+  if (flag == 0) return MG_OK;
+  cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  return fail(c, MG_ERR_TIMEOUT, "a kernel's bounded wait for its staged copies ran out; the result is incomplete");
+}
+
 // Relative residual of the current state: run the residual graph, read scal[S_REL].
 mg_status read_rel(mg_ctx* c, double* rel) {
   // a zero iterate has r = f: its residual needs no stencil evaluation
@@ -225,9 +249,10 @@ mg_status read_rel(mg_ctx* c, double* rel) {
                              : run_graph(c, c->g_resid, c->n_resid, "residual");
   if (st != MG_OK) return st;
   CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read residual");
+  CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error flag");
   CK(cudaStreamSynchronize(c->stream), "residual sync");
   *rel = c->h_pin[0];
-  return MG_OK;
+  return check_err_flag(c);
 }
 
 mg_status check_sph(mg_ctx* c, int P, const double* ctr, const double* rad, int sf) {
@@ -345,9 +370,23 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
   alloc((void**)&c->partials, kMaxPartials * sizeof(double));
   alloc((void**)&c->scal, S_COUNT * sizeof(double));
   alloc((void**)&c->d_iters, sizeof(int));
+  alloc((void**)&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_coarse_cg();
+  // TMA-staged half-sweeps on the single-precision levels where they are the faster kernel;
+  // CCMG_SWEEP=vec keeps the direct-load kernel everywhere, CCMG_SWEEP=tma takes the TMA one on
+  // every level it can run on (both for comparing and testing the two)
+  const char* sweep_env = std::getenv("CCMG_SWEEP");
+  const bool no_tma = sweep_env && std::strcmp(sweep_env, "vec") == 0;
+  const bool all_tma = sweep_env && std::strcmp(sweep_env, "tma") == 0;
+  if (mixed(c) && !no_tma) {
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    for (int l = 0; l + 1 < c->L && e == cudaSuccess; ++l)
+      if (all_tma ? tma_sweep_applies(c->geo[l]) : tma_sweep_pays(c->geo[l]))
+        e = prepare_tma_sweep(c->tma[l], c->x32[l], c->g32[l], c->geo[l], dev);
+  }
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     std::string msg = std::string("mg_create: ") + cudaGetErrorString(e);
@@ -366,6 +405,7 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
     if (e != cudaSuccess) break;
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(c->scal, 0, S_COUNT * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     std::string msg = std::string("mg_create: ") + cudaGetErrorString(e);
@@ -396,6 +436,24 @@ mg_status mg_level_dims(const mg_ctx* c, int level, int* dims) {
 }
 
 long long mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : 0; }
+
+mg_status mg_selftest_wait_timeout(mg_ctx* c, int level) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L - 1 || !c->tma[level].ok)
+    return fail(c, MG_ERR_INVALID, "the level has no TMA-staged half-sweep");
+  CK(launch_smooth_tma_withheld(c->x32[level], c->geo[level], c->inv32, c->tma[level], c->d_err, 20000000LL,
+                                c->stream),
+     "wait-timeout self-test");
+  c->launches += 1;
+  CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "self-test flag");
+  CK(cudaStreamSynchronize(c->stream), "self-test sync");
+  return check_err_flag(c);
+}
+
+int mg_level_sweep_kind(const mg_ctx* c, int level) {
+  if (!c || level < 0 || level >= c->L - 1) return -1;
+  return c->tma[level].ok ? 1 : 0;
+}
 
 mg_status mg_set_bc_values(mg_ctx* c, const double* v) {
   if (!c) return MG_ERR_INVALID;
@@ -498,9 +556,10 @@ mg_status mg_residual(mg_ctx* c, double* h_rel, double* d_r) {
   CK(enqueue_resid(c, d_r ? 1 : 0, d_r, c->stream, &nk), "residual");
   c->launches += nk;
   CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "residual");
+  CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "residual");
   CK(cudaStreamSynchronize(c->stream), "residual sync");
   if (h_rel) *h_rel = c->h_pin[0];
-  return MG_OK;
+  return check_err_flag(c);
 }
 
 mg_status mg_efield(mg_ctx* c, double* d_E) {
@@ -644,7 +703,7 @@ mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
   if (level < 0 || level >= c->L - 1 || (colour != 0 && colour != 1))
     return fail(c, MG_ERR_INVALID, "smoothing needs a non-coarsest level and colour 0 or 1");
   if (mixed(c))
-    CK(launch_smooth<float>(c->x32[level], c->g32[level], c->geo[level], c->inv32, colour, false, c->stream), "smooth");
+    CK(sweep<float>(c, c->x32[level], c->g32[level], c->inv32, level, colour, false, c->stream), "smooth");
   else
     CK(launch_smooth<double>(c->x64[level], c->g64[level], c->geo[level], c->inv64, colour, false, c->stream),
        "smooth");
@@ -707,6 +766,16 @@ mg_status mg_op_residual_norm(mg_ctx* c) {
   long long nk = 0;
   CK(enqueue_resid(c, mixed(c) ? 2 : 0, nullptr, c->stream, &nk), "residual_norm");
   c->launches += nk;
+  return MG_OK;
+}
+
+mg_status mg_op_scale_convert(const double* d_x, const float* d_e, const double* d_y, long long n, double sc,
+                              float* d_xf, double* d_yo, double* d_xs, void* stream) {
+  if (n < 0 || !(sc > 0.0) || !std::isfinite(sc) || !std::isfinite(1.0 / sc)) return MG_ERR_INVALID;
+  if (n == 0) return MG_OK;
+  if (!d_x || !d_e || !d_y || !d_xf || !d_yo || !d_xs) return MG_ERR_INVALID;
+  if (launch_scale_convert(d_x, d_e, d_y, n, sc, d_xf, d_yo, d_xs, (cudaStream_t)stream) != cudaSuccess)
+    return MG_ERR_CUDA;
   return MG_OK;
 }
 

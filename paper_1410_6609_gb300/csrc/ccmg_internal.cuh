@@ -18,6 +18,7 @@
 // into the next level's scaled right-hand side is (1/4) * (sum of the 8 children's scaled
 // residuals): all level-to-level factors are powers of two.
 #pragma once
+#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,9 +26,10 @@ namespace ccmg {
 
 constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarseCells = 4096;
-// Residual-norm blocks of one system: the co-resident count (152 SMs x 4 blocks of 64x4 threads
-// at <= 64 registers), so that the z-neighbour rows a block reads are still in L2.
-constexpr int kMaxPartialsPerSystem = 608;
+// Residual-norm blocks of one system (152 SMs x 12 blocks of 64x4 threads). The FP64 residual is
+// bound by the FP64 pipe, not by DRAM: three waves of 4 co-resident blocks per SM balance the
+// SMs better than one wave, although the later waves re-read some neighbour rows.
+constexpr int kMaxPartialsPerSystem = 1824;
 
 struct Geom {
   int nx, ny, nz;  // cells per axis
@@ -55,6 +57,30 @@ cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv
 // coarse correction ec (level Gc) into its red neighbours; rows must be a multiple of 4 long.
 cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const InvDiag<float>& inv, const float* ec,
                                   const Geom& Gc, float omega, cudaStream_t s);
+// TMA-staged single-precision half-sweep (smooth_tma.cu): persistent CTAs march tiles of a level
+// through z-slabs, the other colour's planes staged in shared memory by tensor-map copies.
+struct TmaSweep {
+  CUtensorMap other[2];  // other[c]: the colour-(1-c) array, read by a colour-c half-sweep
+  CUtensorMap rhs[2];    // rhs[c]: the colour-c right-hand side
+  long long nwork;       // tiles x slabs
+  int kz;                // planes per slab
+  int grid;              // persistent CTAs
+  int ok;                // 1 when the level uses this path
+};
+bool tma_sweep_applies(const Geom& G);  // the kernel can run on this level
+bool tma_sweep_pays(const Geom& G);     // ... and is the faster of the two here
+// Encode the tensor maps of level arrays x and g (both colours) and size the launch; t.ok = 0
+// when the level does not qualify.
+cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom& G, int device);
+// Same result as launch_smooth<float>(x, g, ..., zero_start = false), bit for bit (g is the one
+// the maps were made for). On a wait that runs out of its budget a CTA sets *err = 1 and returns.
+cudaError_t launch_smooth_tma(float* x, const Geom& G, const InvDiag<float>& inv, int colour, const TmaSweep& t,
+                              int* err, cudaStream_t s);
+// Failure-path self-test: the same red half-sweep with one plane copy of every CTA's first item
+// never issued, and a wait budget of budget_cycles; every CTA then sets *err and returns.
+cudaError_t launch_smooth_tma_withheld(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t, int* err,
+                                       long long budget_cycles, cudaStream_t s);
+
 template <typename T>
 // red_only: restrict only the red children's residuals (right after a black half-sweep the black
 // residuals are zero up to rounding).
@@ -102,6 +128,8 @@ cudaError_t launch_unpack(double* dst, const T* src, const Geom& G, double scale
 cudaError_t launch_resid_zero(const double* g, long long n, float* outp, double* scal, int slot_rsum, int slot_rel,
                               int slot_gsum, int slot_inv_scale, cudaStream_t s);
 // x64 += scal[slot] * double(e32) elementwise over n entries.
+cudaError_t launch_scale_convert(const double* x, const float* e, const double* y, long long n, double sc, float* xf,
+                                 double* yo, double* xs, cudaStream_t s);
 cudaError_t launch_update_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
 
 // Fields and forces (finest level, FP64 packed potential).

@@ -11,9 +11,14 @@
 // explicitly rounded operations (no contraction) in the order (((x-cx)^2 + (y-cy)^2) + (z-cz)^2)
 // <= R^2, the sub-cell centre coordinate being (i + (2m+1)/(2 sf)) * h.
 #include "ccmg_internal.cuh"
+#include "level_ops.cuh"
 
 namespace ccmg {
 namespace {
+
+using ops::host_pow2_exponent;
+using ops::kBadPow2;
+using ops::ldexp_rne;
 
 struct SubOff {
   double o[8];  // (2m+1) / (2 sf), m < sf
@@ -49,13 +54,19 @@ __device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geo
 // interior take a path without any wall code (a warp vote, so the compiler cannot turn the rare
 // ghost-value branches into FP64 work done by every cell); (dn - up) * inv2h equals
 // -((up - dn) * inv2h) exactly.
+// POW2: inv2h = 2^q2 (a power-of-two cell size); the interior products are then exponent shifts
+// (ldexp_rne), equal to the FP64 multiply.
+template <bool POW2>
 __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Geom& G, int i, int j, int k, double h,
-                                          double inv2h, const FaceBC& bc, double E[3]) {
+                                          double inv2h, int q2, const FaceBC& bc, double E[3]) {
   const bool interior = i > 0 && i < G.nx - 1 && j > 0 && j < G.ny - 1 && k > 0 && k < G.nz - 1;
   if (__all_sync(__activemask(), interior)) {
-    E[0] = (ld_phi(x, G, i - 1, j, k) - ld_phi(x, G, i + 1, j, k)) * inv2h;
-    E[1] = (ld_phi(x, G, i, j - 1, k) - ld_phi(x, G, i, j + 1, k)) * inv2h;
-    E[2] = (ld_phi(x, G, i, j, k - 1) - ld_phi(x, G, i, j, k + 1)) * inv2h;
+    const double d0 = ld_phi(x, G, i - 1, j, k) - ld_phi(x, G, i + 1, j, k);
+    const double d1 = ld_phi(x, G, i, j - 1, k) - ld_phi(x, G, i, j + 1, k);
+    const double d2 = ld_phi(x, G, i, j, k - 1) - ld_phi(x, G, i, j, k + 1);
+    E[0] = POW2 ? ldexp_rne(d0, q2) : d0 * inv2h;
+    E[1] = POW2 ? ldexp_rne(d1, q2) : d1 * inv2h;
+    E[2] = POW2 ? ldexp_rne(d2, q2) : d2 * inv2h;
   } else {
     const double here = ld_phi(x, G, i, j, k);
 #pragma unroll
@@ -142,14 +153,16 @@ __device__ void block_sum3(double v[3], double (*red)[3]) {
 
 // ---------------------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Geom G, double h, double inv2h, FaceBC bc,
+template <bool POW2>
+__global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Geom G, double h, double inv2h, int q2,
+                                                FaceBC bc,
                                                 double* __restrict__ E) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= G.nx || j >= G.ny) return;
   double e[3];
-  efield_at(x, G, i, j, k, h, inv2h, bc, e);
+  efield_at<POW2>(x, G, i, j, k, h, inv2h, q2, bc, e);
   const long long N = (long long)G.nx * G.ny * G.nz;
   const long long p = nat(G, i, j, k);
   E[p] = e[0];
@@ -197,7 +210,7 @@ __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__
     if (cnt == 0) continue;
     const double w = (double)cnt / sf3;
     double e[3];
-    efield_at(x, G, i, j, k, h, inv2h, bc, e);
+    efield_at<false>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
     for (int a = 0; a < 3; ++a) acc[a] = acc[a] + w * e[a];
   }
   block_sum3(acc, red);
@@ -234,7 +247,7 @@ __global__ void __launch_bounds__(256) k_force_adjoint(const double* __restrict_
     const double w_p = (double)cnt_p / sf3;
     if (cnt_p) {
       double e[3];
-      efield_at(x, G, p[0], p[1], p[2], h, inv2h, bc, e);
+      efield_at<false>(x, G, p[0], p[1], p[2], h, inv2h, kBadPow2, bc, e);
       for (int a = 0; a < 3; ++a) fsum[a] = fsum[a] + w_p * e[a];
     }
     for (int a = 0; a < 3; ++a) {
@@ -351,7 +364,12 @@ SubOff make_suboff(int sf) {
 cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, double* E, cudaStream_t s) {
   const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
   dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
-  k_efield<<<g, b, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, E);
+  const double inv2h = 1.0 / (2.0 * h);
+  const int q2 = host_pow2_exponent(inv2h);
+  if (q2 != kBadPow2)
+    k_efield<true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+  else
+    k_efield<false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
   return cudaGetLastError();
 }
 

@@ -123,9 +123,10 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
   }
 }
 
+// Scale of the next defect-correction step: the largest power of two not above the RMS of the
+// residual (exact scaling in both directions).
 __global__ void k_set_scale(double* scal, int src, int dst, double n) {
-  const double v = sqrt(scal[src] / n);
-  const double s = (v > 0.0 && v == v && v < 1e300) ? v : 1.0;
+  const double s = pow2_floor(sqrt(scal[src] / n));
   scal[dst] = s;
   scal[dst + 1] = 1.0 / s;
 }
@@ -145,9 +146,10 @@ __device__ __forceinline__ double add_wall_terms(double v, int i, int j, int k, 
   if (k == G.nz - 1) v = v + wt.t[5];
   return v;
 }
-template <typename T>
+// POW2: 1/eps = 2^qe and h^2 = 2^qh (lattice units), the products are exponent shifts.
+template <typename T, bool POW2>
 __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
-                                                 double inv_eps, double hsq, WallTerms wt, int raw) {
+                                                 double inv_eps, double hsq, int qe, int qh, WallTerms wt, int raw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
   const long long p = (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
   double v = rho[p];
   if (!raw) {
-    v = v * inv_eps;
+    v = POW2 ? ldexp_rne(v, qe) : v * inv_eps;
     // only warps holding wall cells add wall terms (a warp vote keeps the compiler from turning
     // the rare branches into FP64 adds of zero by every cell)
     const bool wall = i == 0 || i == G.nx - 1 || j == 0 || j == G.ny - 1 || k == 0 || k == G.nz - 1;
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
   }
   long long o = p;
   if (G.packed) o = (long long)((i + j + k) & 1) * G.csz + ((long long)k * G.ny + j) * G.hx + (i >> 1);
-  gout[o] = (T)(v * hsq);
+  gout[o] = (T)(POW2 ? ldexp_rne(v, qh) : v * hsq);
 }
 
 template <typename T>
@@ -201,8 +203,12 @@ __global__ void __launch_bounds__(256) k_resid_zero(const double* __restrict__ g
   const double gsum = scal[slot_gsum];
   if (outp) {
     const double isc = scal[slot_inv_scale];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-      outp[i] = (float)(g[i] * isc);
+    const int p = pow2_exponent(isc);
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    if (p != kBadPow2)
+      for (long long i = i0; i < n; i += st) outp[i] = f32_of_scaled(g[i], p);
+    else
+      for (long long i = i0; i < n; i += st) outp[i] = (float)(g[i] * isc);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     scal[slot_rsum] = gsum;
@@ -213,8 +219,36 @@ __global__ void __launch_bounds__(256) k_resid_zero(const double* __restrict__ g
 __global__ void __launch_bounds__(256) k_update_mixed(double* __restrict__ x, const float* __restrict__ e, long long n,
                                                       const double* __restrict__ scal, int slot) {
   const double sc = scal[slot];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    x[i] = fma(sc, (double)e[i], x[i]);
+  const int p = pow2_exponent(sc);
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  // sc = 2^p within the scale bounds: s e is exact, so fma(sc, e, x) = x + s e
+  if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
+    for (long long i = i0; i < n; i += st) x[i] = x[i] + f64_of_scaled(e[i], p);
+  else
+    for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)e[i], x[i]);
+}
+
+// The power-of-two products and conversions on arbitrary data (for verification): xf =
+// float(x * isc) as the residual kernels write it, yo = fma(sc, double(e), y) as the update
+// applies it, xs = x * sc as the lattice-unit products take it; isc = 1/sc.
+__global__ void __launch_bounds__(256) k_scale_convert(const double* __restrict__ x, const float* __restrict__ e,
+                                                       const double* __restrict__ y, long long n, double sc,
+                                                       double isc, float* __restrict__ xf, double* __restrict__ yo,
+                                                       double* __restrict__ xs) {
+  const int p = pow2_exponent(sc), q = pow2_exponent(isc);
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if (q != kBadPow2)
+    for (long long i = i0; i < n; i += st) xf[i] = f32_of_scaled(x[i], q);
+  else
+    for (long long i = i0; i < n; i += st) xf[i] = (float)(x[i] * isc);
+  if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
+    for (long long i = i0; i < n; i += st) yo[i] = y[i] + f64_of_scaled(e[i], p);
+  else
+    for (long long i = i0; i < n; i += st) yo[i] = fma(sc, (double)e[i], y[i]);
+  if (p != kBadPow2)
+    for (long long i = i0; i < n; i += st) xs[i] = ldexp_rne(x[i], p);
+  else
+    for (long long i = i0; i < n; i += st) xs[i] = x[i] * sc;
 }
 
 // Launch shape for a (w x h x depth) thread grid with 256-thread blocks.
@@ -363,7 +397,12 @@ cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_ep
     wt.t[q] = bc.type[q] == 0 ? 2.0 * bc.value[q] / (h * h) : bc.value[q] / h;
   dim3 b, gr;
   shape(G.nx, G.ny, G.nz, b, gr);
-  k_set_rhs<T><<<gr, b, 0, s>>>(g, G, rho, inv_eps, h * h, wt, raw);
+  const double hsq = h * h;
+  const int qe = host_pow2_exponent(inv_eps), qh = host_pow2_exponent(hsq);
+  if (qe != kBadPow2 && qh != kBadPow2)
+    k_set_rhs<T, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+  else
+    k_set_rhs<T, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
   return cudaGetLastError();
 }
 
@@ -388,6 +427,15 @@ cudaError_t launch_resid_zero(const double* g, long long n, float* outp, double*
   long long blocks = outp ? (n + 255) / 256 : 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_resid_zero<<<(int)blocks, 256, 0, s>>>(g, n, outp, scal, slot_rsum, slot_rel, slot_gsum, slot_inv_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_convert(const double* x, const float* e, const double* y, long long n, double sc, float* xf,
+                                 double* yo, double* xs, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_scale_convert<<<(int)blocks, 256, 0, s>>>(x, e, y, n, sc, 1.0 / sc, xf, yo, xs);
   return cudaGetLastError();
 }
 

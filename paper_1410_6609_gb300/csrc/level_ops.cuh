@@ -5,6 +5,8 @@
 // of cells) at explicit coordinates, so both launch schemes perform bit-identical arithmetic.
 // Layout and scaling conventions are those of ccmg_internal.cuh.
 #pragma once
+#include <cstring>
+
 #include "ccmg_internal.cuh"
 
 namespace ccmg {
@@ -51,6 +53,145 @@ __device__ __forceinline__ T neg_diag(int d) {
   r = (d == 2) ? T(-8) : r;
   r = (d == 3) ? T(-9) : r;
   return r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Power-of-two scaling. The defect-correction scale is a power of two, and so are the 1/(2h),
+// 1/eps and h^2 factors of the lattice-unit workloads. Multiplying by 2^q and the conversions
+// float(x 2^q) and double(e) 2^p then reduce to exponent arithmetic and one round-to-nearest-even
+// of the significand, done here in integer operations: on GB300 the FP64 pipe runs at 1/64 of
+// the FP32 rate and the FP64 multiply and the conversion instructions would occupy it. The
+// routines are total (zeros, subnormal inputs and results, overflow, infinities and NaN), so the
+// kernels call them without a fallback; whether a factor is a power of two is decided once per
+// launch (pow2_exponent) and the kernels select their loop by it.
+
+constexpr int kBadPow2 = -100000;  // pow2_exponent of a factor that is not a power of two
+constexpr int kScaleExpLimit = 800;  // |log2| bound of defect-correction scales (keeps s e exact)
+
+// Largest power of two <= v, with the exponent clamped to [-kScaleExpLimit, kScaleExpLimit], for
+// finite v > 0; 1 otherwise.
+__device__ __forceinline__ double pow2_floor(double v) {
+  if (!(v > 0.0) || !(v < 1e300)) return 1.0;
+  int e = 0;
+  frexp(v, &e);  // v = m 2^e, 0.5 <= m < 1
+  e -= 1;
+  e = e < -kScaleExpLimit ? -kScaleExpLimit : (e > kScaleExpLimit ? kScaleExpLimit : e);
+  return ldexp(1.0, e);
+}
+
+// p with v = 2^p for a positive normal power of two, else kBadPow2.
+__device__ __forceinline__ int pow2_exponent(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((u >> 52) & 0x7ff);
+  if ((u & 0x800fffffffffffffULL) != 0ULL || E == 0 || E == 0x7ff) return kBadPow2;
+  return E - 1023;
+}
+
+// The same test on the host (launchers choose the kernel variant with it).
+inline int host_pow2_exponent(double v) {
+  unsigned long long u = 0;
+  std::memcpy(&u, &v, sizeof(u));
+  const int E = (int)((u >> 52) & 0x7ff);
+  if ((u & 0x800fffffffffffffULL) != 0ULL || E == 0 || E == 0x7ff) return kBadPow2;
+  return E - 1023;
+}
+
+// m >> s rounded to nearest, ties to even (1 <= s <= 63).
+__device__ __forceinline__ unsigned long long rshift_rne(unsigned long long m, int s) {
+  const unsigned long long kept = m >> s;
+  const unsigned long long rem = m & ((1ULL << s) - 1ULL);
+  const unsigned long long half = 1ULL << (s - 1);
+  return kept + ((rem > half || (rem == half && (kept & 1ULL))) ? 1ULL : 0ULL);
+}
+
+// Significand (leading one at bit 52) and biased exponent of a finite nonzero double; a
+// subnormal is normalised (its exponent then drops below 1).
+__device__ __forceinline__ void unpack_f64(unsigned long long u, unsigned long long& M, int& E) {
+  E = (int)((u >> 52) & 0x7ff);
+  M = u & 0xfffffffffffffULL;
+  if (E == 0) {
+    const int lz = __clzll((long long)M) - 11;
+    M <<= lz;
+    E = 1 - lz;
+  } else {
+    M |= 1ULL << 52;
+  }
+}
+
+// v * 2^q rounded to nearest even (q = pow2_exponent of the factor): all cases.
+static __device__ __noinline__ double ldexp_rne_general(double v, int q) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long sign = u & 0x8000000000000000ULL;
+  if ((u << 1) == 0ULL || ((u >> 52) & 0x7ff) == 0x7ff) return v;  // zeros, infinities, NaN
+  unsigned long long M;
+  int E;
+  unpack_f64(u, M, E);
+  const int En = E + q;
+  if (En >= 2047) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ULL));
+  if (En >= 1) return __longlong_as_double((long long)(sign | ((unsigned long long)En << 52) | (M & 0xfffffffffffffULL)));
+  const int sh = 1 - En;  // subnormal result in units of 2^-1074 (a carry to 2^52 encodes 2^-1022)
+  if (sh > 54) return __longlong_as_double((long long)sign);
+  return __longlong_as_double((long long)(sign | rshift_rne(M, sh)));
+}
+
+// The common cases inline: zeros, and normal in and out (only the exponent field changes).
+__device__ __forceinline__ double ldexp_rne(double v, int q) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const int En = E + q;
+  if (E != 0 && E != 0x7ff && En >= 1 && En <= 2046)
+    return __hiloint2double((int)((hi & 0x800fffffu) | ((unsigned)En << 20)), (int)lo);
+  if (((hi & 0x7fffffffu) | lo) == 0u) return v;
+  return ldexp_rne_general(v, q);
+}
+
+// float(x * 2^q) rounded to nearest even: all cases.
+static __device__ __noinline__ float f32_of_scaled_general(double x, int q) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  if ((u << 1) == 0ULL) return __uint_as_float(sign);
+  if (((u >> 52) & 0x7ff) == 0x7ff)
+    return __uint_as_float(sign | 0x7f800000u | ((u & 0xfffffffffffffULL) ? 0x00400000u : 0u));
+  unsigned long long M;
+  int E;
+  unpack_f64(u, M, E);
+  const int eL = E - 1023 + q;  // the value lies in [2^eL, 2^(eL+1))
+  if (eL > 127) return __uint_as_float(sign | 0x7f800000u);
+  if (eL >= -126) {  // normal float: keep 24 of the 53 bits; a carry may reach the exponent (or inf)
+    const unsigned r = (unsigned)rshift_rne(M, 29);
+    return __uint_as_float(sign | (((unsigned)(eL + 126) << 23) + r));
+  }
+  const int sh = 29 + (-126 - eL);  // subnormal float in units of 2^-149
+  if (sh > 54) return __uint_as_float(sign);
+  return __uint_as_float(sign | (unsigned)rshift_rne(M, sh));
+}
+
+// The common case inline (normal double to normal float), in 32-bit operations.
+__device__ __forceinline__ float f32_of_scaled(double x, int q) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const int eL = E - 1023 + q;
+  if (E != 0 && E != 0x7ff && eL >= -126 && eL <= 127) {
+    const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 of the 52 significand bits
+    const unsigned rest = lo & 0x1fffffffu;                    // the 29 dropped bits
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+    // a carry out of the significand raises the exponent (to inf past the largest float)
+    return __uint_as_float((hi & 0x80000000u) | ((((unsigned)(eL + 127) << 23) | m23) + up));
+  }
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  return f32_of_scaled_general(x, q);
+}
+
+// double(e) * 2^p rounded to nearest even (exact unless it leaves the normal range).
+__device__ __forceinline__ double f64_of_scaled(float e, int p) {
+  const unsigned b = __float_as_uint(e);
+  const int Ef = (int)((b >> 23) & 0xffu);
+  const int En = Ef - 127 + 1023 + p;
+  if (Ef != 0 && Ef != 0xff && En >= 1 && En <= 2046)
+    return __hiloint2double((int)((b & 0x80000000u) | ((unsigned)En << 20) | ((b & 0x7fffffu) >> 3)),
+                            (int)(b << 29));
+  if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return ldexp_rne_general((double)e, p);  // subnormals, infinities, NaN, range ends
 }
 
 // Sum of the six neighbours (in the order -x,+x,-y,+y,-z,+z; absent ones are zero) of the cell at
@@ -467,11 +608,84 @@ __device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubl
 // vectors in shared memory `sm` (4 n doubles), natural cell order. Operator: the scaled
 // A_L / c_L, i.e. (6 + d_i) p_i - sum of interior neighbours. Stops when ||r|| <= rtol ||b|| or
 // after maxit iterations; returns the iteration count.
+// The same iteration by warp 0 alone, for coarsest grids of at most kCoarseWarpCells cells:
+// lane l owns cells l, l+32, ...; the dot products are warp_sum reductions, and __syncwarp orders
+// the direction update before the next product reads its neighbours. No block barrier is taken,
+// which makes an iteration several times cheaper than the block-wide version on the 27- to
+// 64-cell grids the hierarchies here end on.
+constexpr int kCoarseWarpCells = 256;
+
+template <typename T>
+__device__ int coarse_cg_warp(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
+                              double* sm) {
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const int n = nx * ny * nz;
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  double* x = sm;
+  double* r = x + n;
+  double* p = r + n;
+  double* ap = p + n;
+  double loc = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double b = (double)bi[i];
+    x[i] = 0.0;
+    r[i] = b;
+    p[i] = b;
+    loc += b * b;
+  }
+  __syncwarp();
+  double rr = warp_sum(loc);
+  const double bnorm = sqrt(rr);
+  int it = 0;
+  if (bnorm > 0.0) {
+    while (it < maxit) {
+      loc = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+        int d = 0;
+        double S = 0.0;
+        if (ix > 0) S += p[i - 1]; else d += G.sh[0];
+        if (ix < nx - 1) S += p[i + 1]; else d += G.sh[1];
+        if (iy > 0) S += p[i - nx]; else d += G.sh[2];
+        if (iy < ny - 1) S += p[i + nx]; else d += G.sh[3];
+        if (iz > 0) S += p[i - nx * ny]; else d += G.sh[4];
+        if (iz < nz - 1) S += p[i + nx * ny]; else d += G.sh[5];
+        const double a = -neg_diag<double>(d) * p[i] - S;
+        ap[i] = a;
+        loc += p[i] * a;
+      }
+      const double pap = warp_sum(loc);
+      const double alpha = rr / pap;
+      loc = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        x[i] = x[i] + alpha * p[i];
+        const double ri = r[i] - alpha * ap[i];
+        r[i] = ri;
+        loc += ri * ri;
+      }
+      const double rrn = warp_sum(loc);
+      ++it;
+      if (sqrt(rrn) <= rtol * bnorm) break;
+      const double beta = rrn / rr;
+      __syncwarp();  // every lane has read p for its product before p changes
+      for (int i = lane; i < n; i += 32) p[i] = r[i] + beta * p[i];
+      __syncwarp();
+      rr = rrn;
+    }
+  }
+  for (int i = lane; i < n; i += 32) xo[i] = (T)x[i];
+  return it;
+}
+
 template <typename T>
 __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
                                double* sm, double* red) {
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = nx * ny * nz;
+  if (n <= kCoarseWarpCells) {  // uniform over the block
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    return tid < 32 ? coarse_cg_warp<T>(xo, bi, G, rtol, maxit, sm) : 0;
+  }
   double* x = sm;
   double* r = x + n;
   double* p = r + n;
@@ -535,10 +749,11 @@ __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, con
 // writes r = r~ c0 in natural order (1) or float(r~ isc) in the level's own order (2).
 constexpr int kResBX = 64, kResBY = 4;
 
-template <typename T, int MODE>
-__device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
-                                                   long long lb, long long nb, double c0, double* __restrict__ outn,
-                                                   float* __restrict__ outp, double isc) {
+template <typename T, int MODE, bool POW2 = false>
+__device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x, const T* __restrict__ g,
+                                                        const Geom& G, long long lb, long long nb, double c0,
+                                                        double* __restrict__ outn, float* __restrict__ outp,
+                                                        double isc, int p2) {
   double acc = 0.0;
   if (G.packed) {
     const long long rows = 2LL * G.nz * G.ny;
@@ -552,7 +767,7 @@ __device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, cons
         const double rd = (double)resid_packed<T>(x, g, G, c, m, j, k);
         acc = fma(rd, rd, acc);
         if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)G.ny * k)] = rd * c0;
-        if (MODE == 2) outp[(long long)c * G.csz + row + m] = (float)(rd * isc);
+        if (MODE == 2) outp[(long long)c * G.csz + row + m] = POW2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);
       }
     }
   } else {
@@ -578,10 +793,23 @@ __device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, cons
       const double rd = (double)fmat(neg_diag<T>(d), x[i], g[i] + S);
       acc = fma(rd, rd, acc);
       if (MODE == 1) outn[i] = rd * c0;
-      if (MODE == 2) outp[i] = (float)(rd * isc);
+      if (MODE == 2) outp[i] = POW2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);
     }
   }
   return acc;
+}
+
+// The residual walk; in MODE 2 the single-precision copy float(r~ isc) is formed by exponent
+// arithmetic when isc is a power of two (the branch is uniform over the launch).
+template <typename T, int MODE>
+__device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
+                                                   long long lb, long long nb, double c0, double* __restrict__ outn,
+                                                   float* __restrict__ outp, double isc) {
+  if (MODE == 2) {
+    const int p2 = pow2_exponent(isc);
+    if (p2 != kBadPow2) return resid_norm_accum_impl<T, MODE, true>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
+  }
+  return resid_norm_accum_impl<T, MODE, false>(x, g, G, lb, nb, c0, outn, outp, isc, kBadPow2);
 }
 
 // Number of blocks of the residual-norm launch for level G (= the number of partial sums).

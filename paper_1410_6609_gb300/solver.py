@@ -21,6 +21,26 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def scale_convert(x: torch.Tensor, e: torch.Tensor, y: torch.Tensor, sc: float):
+    """The power-of-two products and conversions on caller data (mg_op_scale_convert): returns
+    float(x * (1/sc)), fma(sc, double(e), y) and x * sc."""
+    lib = _lib.load()
+    n = x.numel()
+    if not (x.dtype == torch.float64 and y.dtype == torch.float64 and e.dtype == torch.float32):
+        raise TypeError("x, y must be float64 and e float32")
+    if not (x.is_cuda and e.is_cuda and y.is_cuda) or e.numel() != n or y.numel() != n:
+        raise ValueError("x, e, y must be CUDA tensors with the same number of elements")
+    x, e, y = x.contiguous(), e.contiguous(), y.contiguous()
+    xf = torch.empty(n, dtype=torch.float32, device=x.device)
+    yo = torch.empty(n, dtype=torch.float64, device=x.device)
+    xs = torch.empty(n, dtype=torch.float64, device=x.device)
+    st = lib.mg_op_scale_convert(_ptr(x), _ptr(e), _ptr(y), n, float(sc), _ptr(xf), _ptr(yo), _ptr(xs),
+                                 ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream))
+    if st != _lib.MG_OK:
+        raise MgError(st, "mg_op_scale_convert")
+    return xf.view(x.shape), yo.view(x.shape), xs.view(x.shape)
+
+
 class Poisson:
     """Solver context for -lap(phi) = rho/eps on an nx*ny*nz grid (see include/ccmg.h).
 
@@ -95,6 +115,13 @@ class Poisson:
     @property
     def num_levels(self) -> int:
         return self.lib.mg_num_levels(self.ctx)
+
+    def level_sweep_kind(self, level: int) -> str:
+        """'tma' or 'vec': the kernel that performs the level's half-sweeps (mg_level_sweep_kind)."""
+        k = self.lib.mg_level_sweep_kind(self.ctx, level)
+        if k < 0:
+            raise ValueError(f"no half-sweeps on level {level}")
+        return "tma" if k == 1 else "vec"
 
     def level_dims(self, level: int):
         d = (ctypes.c_int * 3)()
