@@ -384,10 +384,9 @@ FP64_OPS_PEAK = 0.625  # Tops/s
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of that kernel on the
 # same workload (profiles/); None where no capture of the current kernel exists.
 MEASURED_TRAFFIC = {
-    # profiles/dram_traffic_spheres512_mixed.md: finest-level FP32 half-sweep, 536.90 MB read + 238.74 MB written
-    ("spheres512", "smooth_half_sweep"): 775_640_000,
-    # same file: FP64 outer residual with the 608-block grid, 3369.18 MB read + 526.74 MB written
-    ("spheres512", "residual_fp64"): 3_895_920_000,
+    # profiles/dram_traffic_spheres512_mixed.md: finest-level FP32 half-sweep of the direct-load
+    # kernel, 536.90 MB read + 238.74 MB written (kept for runs with CCMG_SWEEP=vec)
+    ("spheres512", "k_smooth_vec<float,4,0>"): 775_640_000,
 }
 
 
@@ -409,7 +408,7 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     t_res = _time(P.op_residual_norm, stream, 10)
     mixed = w.precision == "mixed"
     bytes_res = N * (8 + 8 + (4 if mixed else 0))
-    ops_res = N * (9 if mixed else 8)
+    ops_res = N * 8  # 5 neighbour adds, g + sum, the diagonal FMA, the norm FMA (the float copy is integer work)
     kern["residual_fp64"] = {"ms": t_res, "GB/s": bytes_res / t_res / 1e6, "Tops/s": ops_res / t_res / 1e9,
                              "launches_per_step": k_step, "bytes_per_launch": int(bytes_res),
                              "note": "plus one stencil-free residual of the zero start per step"}
@@ -417,21 +416,27 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     esz = 4 if mixed else 8
     inner = P.mixed_inner if mixed else 1  # finest-level V-cycles per outer step
     t_sm = _time(lambda: P.op_smooth(0, 0), stream, 20)
+    sweep_kernel = ("k_smooth_tma" if P.level_sweep_kind(0) == "tma" else
+                    ("k_smooth_vec<float,4,0>" if mixed else "k_smooth_vec<double,2,0>"))
     kern["smooth_half_sweep"] = {"ms": t_sm, "GB/s": 1.5 * N * esz / t_sm / 1e6, "Tops/s": 0.5 * N * 7 / t_sm / 1e9,
                                  "launches_per_step": 8 * k_step * inner, "precision": "f32" if mixed else "f64",
-                                 "bytes_per_launch": int(1.5 * N * esz)}
-    t_rr = _time(lambda: P.op_residual_restrict(0), stream, 20)
-    kern["resid_restrict"] = {"ms": t_rr, "GB/s": (2 * N * esz + N * esz / 8) / t_rr / 1e6,
-                              "Tops/s": N * 8 / t_rr / 1e9, "launches_per_step": k_step * inner,
-                              "precision": "f32" if mixed else "f64",
-                              "bytes_per_launch": int(2 * N * esz + N * esz / 8)}
+                                 "bytes_per_launch": int(1.5 * N * esz), "device_kernel": sweep_kernel,
+                                 "note": "the first post-smoothing black sweep runs fused with the prolongation"
+                                 if mixed else ""}
+    # the restriction the cycle runs: red children only in single precision (after a black sweep)
+    t_rr = _time(lambda: P.op_residual_restrict(0, red_only=mixed), stream, 20)
+    rr_bytes = (1.5 * N * esz + N * esz / 8) if mixed else (2 * N * esz + N * esz / 8)
+    kern["resid_restrict"] = {"ms": t_rr, "GB/s": rr_bytes / t_rr / 1e6,
+                              "Tops/s": N * (4 if mixed else 8) / t_rr / 1e9, "launches_per_step": k_step * inner,
+                              "precision": "f32" if mixed else "f64", "red_only": mixed,
+                              "bytes_per_launch": int(rr_bytes)}
     # the state changed: restore a consistent solve state for later use
     for name, d in kern.items():
         d["share_ms_per_step"] = d["ms"] * d["launches_per_step"]
     dom = max(kern, key=lambda n: kern[n]["share_ms_per_step"])
     d = kern[dom]
     alu = (dom == "residual_fp64") or (not mixed)
-    traffic = MEASURED_TRAFFIC.get((w.name, dom))
+    traffic = MEASURED_TRAFFIC.get((w.name, d.get("device_kernel", dom)))
     if alu:
         out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": d["Tops/s"], "peak": FP64_OPS_PEAK,
                            "unit": "Tops/s (FP64 lane-ops)", "frac": d["Tops/s"] / FP64_OPS_PEAK,

@@ -159,6 +159,10 @@ mg_status mg_level_get(mg_ctx* ctx, int level, int which, double* d_out);
 mg_status mg_op_smooth(mg_ctx* ctx, int level, int colour);
 /* f_{l+1} = averaging restriction of (f_l - A_l phi_l). */
 mg_status mg_op_residual_restrict(mg_ctx* ctx, int level);
+/* The same restriction over the red children only (their residuals times 1/4, summed in the
+ * same order), the variant the single-precision cycle runs right after a black half-sweep, when
+ * the black residuals are zero up to rounding. Not in the paper. */
+mg_status mg_op_residual_restrict_red(mg_ctx* ctx, int level);
 /* phi_l += cgc_weight * constant prolongation of phi_{l+1}. */
 mg_status mg_op_prolong_correct(mg_ctx* ctx, int level);
 /* CG on the coarsest level: phi_L = A_L^-1 f_L (rtol 1e-14, at most 2 N_L iterations);

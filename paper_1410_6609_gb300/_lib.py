@@ -71,6 +71,7 @@ SIGNATURES = {
     "mg_level_get": (_I, [_P, _I, _I, _P]),
     "mg_op_smooth": (_I, [_P, _I, _I]),
     "mg_op_residual_restrict": (_I, [_P, _I]),
+    "mg_op_residual_restrict_red": (_I, [_P, _I]),
     "mg_op_prolong_correct": (_I, [_P, _I]),
     "mg_op_coarse_solve": (_I, [_P, _P]),
     "mg_op_residual_norm": (_I, [_P]),

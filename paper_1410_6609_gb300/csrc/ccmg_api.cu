@@ -43,10 +43,12 @@ struct mg_ctx {
   InvDiag<float> inv32{};
   FaceBC bc{};
   cudaGraphExec_t g_cycle = nullptr;
+  cudaGraphExec_t g_cycle0 = nullptr;  // mixed: the first cycle from a zero iterate (phi = s e)
   cudaGraphExec_t g_resid = nullptr;
   cudaGraphExec_t g_resid0 = nullptr;  // the termination residual of a zero iterate (r = f)
-  long long n_cycle = 0, n_resid = 0, n_resid0 = 0;  // kernel nodes per graph
+  long long n_cycle = 0, n_cycle0 = 0, n_resid = 0, n_resid0 = 0;  // kernel nodes per graph
   bool phi_zero = true;                // the finest iterate is known to be exactly zero
+  bool x_lazy = false;                 // mixed: x64[0] holds no data, its value is zero
   long long launches = 0;
   double* d_rho = nullptr;  // step_host scratch: density field
   double* d_sph = nullptr;  // step_host scratch: 8*P doubles (centres, radius, density, forces)
@@ -80,6 +82,7 @@ double level_coeff(const mg_ctx* c, int l) { return 1.0 / (std::ldexp(1.0, l) * 
 
 void free_all(mg_ctx* c) {
   if (c->g_cycle) cudaGraphExecDestroy(c->g_cycle);
+  if (c->g_cycle0) cudaGraphExecDestroy(c->g_cycle0);
   if (c->g_resid) cudaGraphExecDestroy(c->g_resid);
   if (c->g_resid0) cudaGraphExecDestroy(c->g_resid0);
   for (int l = 0; l < kMaxLevels; ++l) {
@@ -146,7 +149,9 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
     ++*nk;
   }
   for (int it = 0; it < c->p.nu2; ++it) {
-    if (fuse && it == 0)
+    if (fuse && it == 0 && c->tma[l].ok_pro)
+      e = launch_smooth_prolong_tma((float*)x[l], G, c->inv32, c->tma[l], (float)c->p.cgc_weight, c->d_err, s);
+    else if (fuse && it == 0)
       e = launch_smooth_prolong((float*)x[l], (const float*)g[l], G, c->inv32, (const float*)x[l + 1],
                                 c->geo[l + 1], (float)c->p.cgc_weight, s);
     else
@@ -160,13 +165,15 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
 
 // One cycle: FP64 V-cycle, or (mixed) mixed_inner single-precision V-cycles on the scaled
 // residual that the residual graph left in g32[0] (the first from e = 0), followed by
-// phi += scale * e and the next scale.
-cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk) {
+// phi += scale * e (phi = scale * e for a zero iterate, `first`) and the next scale.
+cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk, bool first) {
   if (!mixed(c)) return enqueue_vcycle<double>(c, c->x64, c->g64, c->inv64, 0, false, s, nk);
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < c->p.mixed_inner; ++it)
     if ((e = enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, it == 0, s, nk)) != cudaSuccess) return e;
-  if ((e = launch_update_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s)) != cudaSuccess) return e;
+  e = first ? launch_set_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s)
+            : launch_update_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s);
+  if (e != cudaSuccess) return e;
   if ((e = launch_set_scale(c->scal, S_RSUM, S_SCALE, (double)cells(c->geo[0]), s)) != cudaSuccess) return e;
   *nk += 2;
   return cudaSuccess;
@@ -210,8 +217,14 @@ mg_status capture(mg_ctx* c, cudaGraphExec_t* out, long long* nodes, F body, con
 
 mg_status ensure_graphs(mg_ctx* c) {
   mg_status st = capture(c, &c->g_cycle, &c->n_cycle,
-                         [c](cudaStream_t s, long long* nk) { return enqueue_cycle(c, s, nk); }, "capture cycle");
+                         [c](cudaStream_t s, long long* nk) { return enqueue_cycle(c, s, nk, false); },
+                         "capture cycle");
   if (st != MG_OK) return st;
+  if (mixed(c)) {
+    st = capture(c, &c->g_cycle0, &c->n_cycle0,
+                 [c](cudaStream_t s, long long* nk) { return enqueue_cycle(c, s, nk, true); }, "capture cycle");
+    if (st != MG_OK) return st;
+  }
   const int mode = mixed(c) ? 2 : 0;
   st = capture(c, &c->g_resid, &c->n_resid,
                [c, mode](cudaStream_t s, long long* nk) { return enqueue_resid(c, mode, nullptr, s, nk); },
@@ -229,6 +242,26 @@ mg_status ensure_graphs(mg_ctx* c) {
 mg_status run_graph(mg_ctx* c, cudaGraphExec_t g, long long nodes, const char* what) {
   CK(cudaGraphLaunch(g, c->stream), what);
   c->launches += nodes;
+  return MG_OK;
+}
+
+// One cycle of the solve; the first one from a zero iterate that was never written (mixed
+// mode) stores phi = s e instead of adding to it.
+mg_status run_cycle(mg_ctx* c) {
+  mg_status st = c->x_lazy ? run_graph(c, c->g_cycle0, c->n_cycle0, "cycle")
+                           : run_graph(c, c->g_cycle, c->n_cycle, "cycle");
+  if (st != MG_OK) return st;
+  c->x_lazy = false;
+  c->phi_zero = false;
+  return MG_OK;
+}
+
+// Write the zeros of a finest iterate that mg_set_solution(NULL) left unwritten, before a call
+// that reads it.
+mg_status materialize(mg_ctx* c) {
+  if (!c->x_lazy) return MG_OK;
+  CK(cudaMemsetAsync(c->x64[0], 0, sizeof(double) * (size_t)cells(c->geo[0]), c->stream), "zero iterate");
+  c->x_lazy = false;
   return MG_OK;
 }
 
@@ -384,8 +417,10 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     for (int l = 0; l + 1 < c->L && e == cudaSuccess; ++l)
-      if (all_tma ? tma_sweep_applies(c->geo[l]) : tma_sweep_pays(c->geo[l]))
+      if (all_tma ? tma_sweep_applies(c->geo[l]) : tma_sweep_pays(c->geo[l])) {
         e = prepare_tma_sweep(c->tma[l], c->x32[l], c->g32[l], c->geo[l], dev);
+        if (e == cudaSuccess) e = prepare_tma_prolong(c->tma[l], c->x32[l + 1], c->geo[l + 1], c->geo[l], dev);
+      }
   }
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
@@ -486,15 +521,22 @@ mg_status mg_set_rhs_f(mg_ctx* c, const double* d_f) { return set_rhs_impl(c, d_
 
 mg_status mg_set_solution(mg_ctx* c, const double* d_phi) {
   if (!c) return MG_ERR_INVALID;
+  c->phi_zero = (d_phi == nullptr);
+  if (mixed(c) && !d_phi) {  // nothing is written: the first cycle stores phi = s e
+    c->x_lazy = true;
+    return MG_OK;
+  }
   CK(launch_pack<double>(c->x64[0], c->geo[0], d_phi, 1.0, c->stream), "set_solution");
   c->launches += 1;
-  c->phi_zero = (d_phi == nullptr);
+  c->x_lazy = false;
   return MG_OK;
 }
 
 mg_status mg_get_solution(mg_ctx* c, double* d_phi) {
   if (!c) return MG_ERR_INVALID;
   if (!d_phi) return fail(c, MG_ERR_INVALID, "null output");
+  mg_status st = materialize(c);
+  if (st != MG_OK) return st;
   CK(launch_unpack<double>(d_phi, c->x64[0], c->geo[0], 1.0, c->stream), "get_solution");
   c->launches += 1;
   return MG_OK;
@@ -511,8 +553,7 @@ mg_status mg_vcycle(mg_ctx* c, int ncycles) {
       else st = run_graph(c, c->g_resid, c->n_resid, "residual");
       if (st != MG_OK) return st;
     }
-    if ((st = run_graph(c, c->g_cycle, c->n_cycle, "cycle")) != MG_OK) return st;
-    c->phi_zero = false;
+    if ((st = run_cycle(c)) != MG_OK) return st;
   }
   return MG_OK;
 }
@@ -541,8 +582,7 @@ mg_status mg_solve(mg_ctx* c, double tol, int max_cycles, int* h_cycles, double*
       out = fail(c, MG_ERR_NOT_CONVERGED, "max_cycles reached before the tolerance");
       break;
     }
-    if ((st = run_graph(c, c->g_cycle, c->n_cycle, "cycle")) != MG_OK) return st;
-    c->phi_zero = false;
+    if ((st = run_cycle(c)) != MG_OK) return st;
     ++k;
   }
   if (h_cycles) *h_cycles = k;
@@ -552,6 +592,8 @@ mg_status mg_solve(mg_ctx* c, double tol, int max_cycles, int* h_cycles, double*
 
 mg_status mg_residual(mg_ctx* c, double* h_rel, double* d_r) {
   if (!c) return MG_ERR_INVALID;
+  mg_status st = materialize(c);
+  if (st != MG_OK) return st;
   long long nk = 0;
   CK(enqueue_resid(c, d_r ? 1 : 0, d_r, c->stream, &nk), "residual");
   c->launches += nk;
@@ -565,6 +607,8 @@ mg_status mg_residual(mg_ctx* c, double* h_rel, double* d_r) {
 mg_status mg_efield(mg_ctx* c, double* d_E) {
   if (!c) return MG_ERR_INVALID;
   if (!d_E) return fail(c, MG_ERR_INVALID, "null output");
+  mg_status st = materialize(c);
+  if (st != MG_OK) return st;
   CK(launch_efield(c->x64[0], c->geo[0], c->p.h, c->bc, d_E, c->stream), "efield");
   c->launches += 1;
   return MG_OK;
@@ -589,6 +633,7 @@ mg_status mg_force_gather(mg_ctx* c, int P, const double* ctr, const double* rad
   if (st != MG_OK) return st;
   if ((P > 0 && (!dens || !d_F))) return fail(c, MG_ERR_INVALID, "null argument");
   Spheres sp{P, ctr, rad, dens};
+  if ((st = materialize(c)) != MG_OK) return st;
   CK(launch_force_gather(c->x64[0], c->geo[0], c->p.h, c->bc, sp, sf, d_F, c->stream), "force_gather");
   c->launches += P > 0 ? 1 : 0;
   return MG_OK;
@@ -601,6 +646,7 @@ mg_status mg_force_gather_adjoint(mg_ctx* c, int P, const double* ctr, const dou
   if (st != MG_OK) return st;
   if (!d_gphi || !d_gbc || (P > 0 && (!dens || !d_wF || !d_gdens))) return fail(c, MG_ERR_INVALID, "null argument");
   Spheres sp{P, ctr, rad, dens};
+  if ((st = materialize(c)) != MG_OK) return st;
   CK(launch_force_adjoint(c->x64[0], c->geo[0], c->p.h, c->bc, sp, sf, d_wF, d_gphi, d_gdens, d_gbc, c->stream),
      "force_gather_adjoint");
   c->launches += P > 0 ? 1 : 0;
@@ -711,20 +757,23 @@ mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
   return MG_OK;
 }
 
-mg_status mg_op_residual_restrict(mg_ctx* c, int level) {
+static mg_status residual_restrict_op(mg_ctx* c, int level, bool red_only) {
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "restriction needs a non-coarsest level");
   if (mixed(c))
     CK(launch_resid_restrict<float>(c->x32[level], c->g32[level], c->geo[level], c->g32[level + 1],
-                                    c->geo[level + 1], false, c->stream),
+                                    c->geo[level + 1], red_only, c->stream),
        "residual_restrict");
   else
     CK(launch_resid_restrict<double>(c->x64[level], c->g64[level], c->geo[level], c->g64[level + 1],
-                                     c->geo[level + 1], false, c->stream),
+                                     c->geo[level + 1], red_only, c->stream),
        "residual_restrict");
   c->launches += 1;
   return MG_OK;
 }
+
+mg_status mg_op_residual_restrict(mg_ctx* c, int level) { return residual_restrict_op(c, level, false); }
+mg_status mg_op_residual_restrict_red(mg_ctx* c, int level) { return residual_restrict_op(c, level, true); }
 
 mg_status mg_op_prolong_correct(mg_ctx* c, int level) {
   if (c && !mixed(c) && level == 0) c->phi_zero = false;
@@ -763,6 +812,8 @@ mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
 
 mg_status mg_op_residual_norm(mg_ctx* c) {
   if (!c) return MG_ERR_INVALID;
+  mg_status st = materialize(c);
+  if (st != MG_OK) return st;
   long long nk = 0;
   CK(enqueue_resid(c, mixed(c) ? 2 : 0, nullptr, c->stream, &nk), "residual_norm");
   c->launches += nk;

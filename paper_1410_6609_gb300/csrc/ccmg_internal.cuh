@@ -60,12 +60,14 @@ cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const
 // TMA-staged single-precision half-sweep (smooth_tma.cu): persistent CTAs march tiles of a level
 // through z-slabs, the other colour's planes staged in shared memory by tensor-map copies.
 struct TmaSweep {
-  CUtensorMap other[2];  // other[c]: the colour-(1-c) array, read by a colour-c half-sweep
-  CUtensorMap rhs[2];    // rhs[c]: the colour-c right-hand side
-  long long nwork;       // tiles x slabs
-  int kz;                // planes per slab
-  int grid;              // persistent CTAs
-  int ok;                // 1 when the level uses this path
+  CUtensorMap other[2];   // other[c]: the colour-(1-c) array, read by a colour-c half-sweep
+  CUtensorMap rhs[2];     // rhs[c]: the colour-c right-hand side
+  CUtensorMap coarse[2];  // the next level's correction (both colours), for the fused prolongation
+  long long nwork, nwork_pro;  // tiles x slabs
+  int kz, kz_pro;              // planes per slab
+  int grid, grid_pro;          // persistent CTAs
+  int ok;                      // 1 when the level uses this path
+  int ok_pro;                  // 1 when its first black post-sweep runs fused with the prolongation
 };
 bool tma_sweep_applies(const Geom& G);  // the kernel can run on this level
 bool tma_sweep_pays(const Geom& G);     // ... and is the faster of the two here
@@ -76,6 +78,11 @@ cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom&
 // the maps were made for). On a wait that runs out of its budget a CTA sets *err = 1 and returns.
 cudaError_t launch_smooth_tma(float* x, const Geom& G, const InvDiag<float>& inv, int colour, const TmaSweep& t,
                               int* err, cudaStream_t s);
+// The fused prolongation + black sweep in the same scheme (t prepared with a packed coarse level
+// ec, Gc of half the size in every direction); same result as launch_smooth_prolong.
+cudaError_t prepare_tma_prolong(TmaSweep& t, const float* ec, const Geom& Gc, const Geom& G, int device);
+cudaError_t launch_smooth_prolong_tma(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t,
+                                      float omega, int* err, cudaStream_t s);
 // Failure-path self-test: the same red half-sweep with one plane copy of every CTA's first item
 // never issued, and a wait budget of budget_cycles; every CTA then sets *err and returns.
 cudaError_t launch_smooth_tma_withheld(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t, int* err,
@@ -130,6 +137,8 @@ cudaError_t launch_resid_zero(const double* g, long long n, float* outp, double*
 // x64 += scal[slot] * double(e32) elementwise over n entries.
 cudaError_t launch_scale_convert(const double* x, const float* e, const double* y, long long n, double sc, float* xf,
                                  double* yo, double* xs, cudaStream_t s);
+// x = s e for an iterate that is zero (x is not read).
+cudaError_t launch_set_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
 cudaError_t launch_update_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
 
 // Fields and forces (finest level, FP64 packed potential).

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_smooth_vec(T* __restrict__ x, const T* 
 }
 
 template <typename T, int V>
-__global__ void __launch_bounds__(256) k_smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 5) k_smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                             InvDiag<T> inv, const T* __restrict__ ec, Geom Gc,
                                                             T omega) {
   const int mv = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,6 +251,22 @@ __global__ void __launch_bounds__(256) k_scale_convert(const double* __restrict_
     for (long long i = i0; i < n; i += st) xs[i] = x[i] * sc;
 }
 
+// The update of a zero iterate: x = fma(sc, double(e), +0), i.e. s e with a zero product
+// stored as +0; x itself is not read.
+__global__ void __launch_bounds__(256) k_set_mixed(double* __restrict__ x, const float* __restrict__ e, long long n,
+                                                   const double* __restrict__ scal, int slot) {
+  const double sc = scal[slot];
+  const int p = pow2_exponent(sc);
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
+    for (long long i = i0; i < n; i += st) {
+      const double v = f64_of_scaled(e[i], p);
+      x[i] = (__double_as_longlong(v) == (long long)0x8000000000000000ULL) ? 0.0 : v;
+    }
+  else
+    for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)e[i], 0.0);
+}
+
 // Launch shape for a (w x h x depth) thread grid with 256-thread blocks.
 void shape(int w, int h, int depth, dim3& b, dim3& g) {
   const int bx = w >= 128 ? 128 : (w >= 64 ? 64 : 32);
@@ -436,6 +452,14 @@ cudaError_t launch_scale_convert(const double* x, const float* e, const double* 
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   k_scale_convert<<<(int)blocks, 256, 0, s>>>(x, e, y, n, sc, 1.0 / sc, xf, yo, xs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_set_mixed<<<(int)blocks, 256, 0, s>>>(x, e, n, scal, slot);
   return cudaGetLastError();
 }
 

@@ -323,8 +323,19 @@ __device__ __forceinline__ void coarse_row_w(const T* __restrict__ ec, const Geo
     const int C0 = (I0 + J + K) & 1;  // colour of I0 (and I0+2, ...); I0+1, I0+3 have the other
     const T* a = ec + (long long)C0 * Gc.csz + rowc;
     const T* b = ec + (long long)(C0 ^ 1) * Gc.csz + rowc;
+    if constexpr (V == 4 && sizeof(T) == 4) {
+      // I0 is a multiple of 4 and the coarse rows are an even number of floats long (the fine
+      // rows hold whole 4-float vectors), so both pairs are 8-byte aligned
+      const float2 pa = __ldg(reinterpret_cast<const float2*>(a));
+      const float2 pb = __ldg(reinterpret_cast<const float2*>(b));
+      w[0] = omega * pa.x;
+      w[1] = omega * pb.x;
+      w[2] = omega * pa.y;
+      w[3] = omega * pb.y;
+    } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) w[v] = omega * __ldg(((v & 1) ? b : a) + (v >> 1));
+      for (int v = 0; v < V; ++v) w[v] = omega * __ldg(((v & 1) ? b : a) + (v >> 1));
+    }
   } else {
     const long long o = (long long)I0 + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
 #pragma unroll
@@ -358,50 +369,52 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
   const T* yr = x + row;  // red array, row (j,k)
   const long long plane = (long long)G.ny * G.hx;
   const int J = j >> 1, K = k >> 1;
-  T gv[V], out[V], yc[V], ym[V], yp[V], zm[V], zp[V], w[V];
+  T gv[V], out[V], yc[V], ym[V], yp[V], zm[V], zp[V], wc[V], wy[V], wz[V];
   load_vec(g + own, gv);
   load_vec(yr + m0, yc);
-  coarse_row_w<T, V>(ec, Gc, m0, J, K, omega, w);
+  // coarse parents: row (J, K) serves the row itself and the y- and z-neighbour rows inside the
+  // same coarse cell; the other y (z) neighbour row has its parent in row J -+ 1 (K -+ 1)
+  coarse_row_w<T, V>(ec, Gc, m0, J, K, omega, wc);
+  const bool jy = (j & 1) ? (j < G.ny - 1) : (j > 0), kz = (k & 1) ? (k < G.nz - 1) : (k > 0);
+  if (jy) coarse_row_w<T, V>(ec, Gc, m0, (j & 1) ? J + 1 : J - 1, K, omega, wy);
+  if (kz) coarse_row_w<T, V>(ec, Gc, m0, J, (k & 1) ? K + 1 : K - 1, omega, wz);
 #pragma unroll
-  for (int v = 0; v < V; ++v) yc[v] = yc[v] + w[v];
+  for (int v = 0; v < V; ++v) yc[v] = yc[v] + wc[v];
   T extra = T(0);
   if (s == 0) {
     if (m0 > 0) extra = __ldg(yr + m0 - 1) + omega * __ldg(ec + coarse_index(Gc, m0 - 1, J, K));
   } else {
     if (m0 + V < G.hx) extra = __ldg(yr + m0 + V) + omega * __ldg(ec + coarse_index(Gc, m0 + V, J, K));
   }
+  // (j-1)>>1 is J-1 for even j and J for odd j; (j+1)>>1 is J for even j and J+1 for odd j
   if (j > 0) {
     load_vec(yr + m0 - G.hx, ym);
-    coarse_row_w<T, V>(ec, Gc, m0, (j - 1) >> 1, K, omega, w);
 #pragma unroll
-    for (int v = 0; v < V; ++v) ym[v] = ym[v] + w[v];
+    for (int v = 0; v < V; ++v) ym[v] = ym[v] + ((j & 1) ? wc[v] : wy[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) ym[v] = T(0);
   }
   if (j < G.ny - 1) {
     load_vec(yr + m0 + G.hx, yp);
-    coarse_row_w<T, V>(ec, Gc, m0, (j + 1) >> 1, K, omega, w);
 #pragma unroll
-    for (int v = 0; v < V; ++v) yp[v] = yp[v] + w[v];
+    for (int v = 0; v < V; ++v) yp[v] = yp[v] + ((j & 1) ? wy[v] : wc[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) yp[v] = T(0);
   }
   if (k > 0) {
     load_vec(yr + m0 - plane, zm);
-    coarse_row_w<T, V>(ec, Gc, m0, J, (k - 1) >> 1, omega, w);
 #pragma unroll
-    for (int v = 0; v < V; ++v) zm[v] = zm[v] + w[v];
+    for (int v = 0; v < V; ++v) zm[v] = zm[v] + ((k & 1) ? wc[v] : wz[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) zm[v] = T(0);
   }
   if (k < G.nz - 1) {
     load_vec(yr + m0 + plane, zp);
-    coarse_row_w<T, V>(ec, Gc, m0, J, (k + 1) >> 1, omega, w);
 #pragma unroll
-    for (int v = 0; v < V; ++v) zp[v] = zp[v] + w[v];
+    for (int v = 0; v < V; ++v) zp[v] = zp[v] + ((k & 1) ? wz[v] : wc[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) zp[v] = T(0);
@@ -609,15 +622,16 @@ __device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubl
 // A_L / c_L, i.e. (6 + d_i) p_i - sum of interior neighbours. Stops when ||r|| <= rtol ||b|| or
 // after maxit iterations; returns the iteration count.
 // The same iteration by warp 0 alone, for coarsest grids of at most kCoarseWarpCells cells:
-// lane l owns cells l, l+32, ...; the dot products are warp_sum reductions, and __syncwarp orders
-// the direction update before the next product reads its neighbours. No block barrier is taken,
-// which makes an iteration several times cheaper than the block-wide version on the 27- to
-// 64-cell grids the hierarchies here end on.
-constexpr int kCoarseWarpCells = 256;
+// lane l owns cells l and l+32; the dot products are warp_sum reductions, and __syncwarp orders
+// the direction update before the next product reads its neighbours. No block barrier is taken.
+// (Two cells per lane at most: the per-cell work is unrolled, and unused slots would still issue
+// their predicated FP64 instructions.)
+constexpr int kCoarseWarpCells = 64;
 
 template <typename T>
 __device__ int coarse_cg_warp(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
                               double* sm) {
+  constexpr int kPer = kCoarseWarpCells / 32;  // cells per lane at most
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = nx * ny * nz;
   const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
@@ -625,50 +639,80 @@ __device__ int coarse_cg_warp(T* __restrict__ xo, const T* __restrict__ bi, cons
   double* r = x + n;
   double* p = r + n;
   double* ap = p + n;
+  // per owned cell: which of its six neighbours exist (bits -x,+x,-y,+y,-z,+z) and -(6 + d)
+  unsigned nbm[kPer];
+  double nd[kPer];
   double loc = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    const double b = (double)bi[i];
-    x[i] = 0.0;
-    r[i] = b;
-    p[i] = b;
-    loc += b * b;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int i = lane + 32 * t;
+    nbm[t] = 0u;
+    nd[t] = 0.0;
+    if (i < n) {
+      const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+      int d = 0;
+      if (ix > 0) nbm[t] |= 1u; else d += G.sh[0];
+      if (ix < nx - 1) nbm[t] |= 2u; else d += G.sh[1];
+      if (iy > 0) nbm[t] |= 4u; else d += G.sh[2];
+      if (iy < ny - 1) nbm[t] |= 8u; else d += G.sh[3];
+      if (iz > 0) nbm[t] |= 16u; else d += G.sh[4];
+      if (iz < nz - 1) nbm[t] |= 32u; else d += G.sh[5];
+      nd[t] = neg_diag<double>(d);
+      const double b = (double)bi[i];
+      x[i] = 0.0;
+      r[i] = b;
+      p[i] = b;
+      loc += b * b;
+    }
   }
   __syncwarp();
   double rr = warp_sum(loc);
   const double bnorm = sqrt(rr);
+  const double stop = rtol * bnorm;
   int it = 0;
   if (bnorm > 0.0) {
     while (it < maxit) {
       loc = 0.0;
-      for (int i = lane; i < n; i += 32) {
-        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-        int d = 0;
-        double S = 0.0;
-        if (ix > 0) S += p[i - 1]; else d += G.sh[0];
-        if (ix < nx - 1) S += p[i + 1]; else d += G.sh[1];
-        if (iy > 0) S += p[i - nx]; else d += G.sh[2];
-        if (iy < ny - 1) S += p[i + nx]; else d += G.sh[3];
-        if (iz > 0) S += p[i - nx * ny]; else d += G.sh[4];
-        if (iz < nz - 1) S += p[i + nx * ny]; else d += G.sh[5];
-        const double a = -neg_diag<double>(d) * p[i] - S;
-        ap[i] = a;
-        loc += p[i] * a;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) {
+          const unsigned m = nbm[t];
+          double S = 0.0;
+          if (m & 1u) S += p[i - 1];
+          if (m & 2u) S += p[i + 1];
+          if (m & 4u) S += p[i - nx];
+          if (m & 8u) S += p[i + nx];
+          if (m & 16u) S += p[i - nx * ny];
+          if (m & 32u) S += p[i + nx * ny];
+          const double a = -nd[t] * p[i] - S;
+          ap[i] = a;
+          loc += p[i] * a;
+        }
       }
       const double pap = warp_sum(loc);
       const double alpha = rr / pap;
       loc = 0.0;
-      for (int i = lane; i < n; i += 32) {
-        x[i] = x[i] + alpha * p[i];
-        const double ri = r[i] - alpha * ap[i];
-        r[i] = ri;
-        loc += ri * ri;
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) {
+          x[i] = x[i] + alpha * p[i];
+          const double ri = r[i] - alpha * ap[i];
+          r[i] = ri;
+          loc += ri * ri;
+        }
       }
       const double rrn = warp_sum(loc);
       ++it;
-      if (sqrt(rrn) <= rtol * bnorm) break;
+      if (sqrt(rrn) <= stop) break;
       const double beta = rrn / rr;
       __syncwarp();  // every lane has read p for its product before p changes
-      for (int i = lane; i < n; i += 32) p[i] = r[i] + beta * p[i];
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int i = lane + 32 * t;
+        if (i < n) p[i] = r[i] + beta * p[i];
+      }
       __syncwarp();
       rr = rrn;
     }

@@ -24,20 +24,42 @@ namespace {
 
 using ops::inv_of;
 
-constexpr int kTX = 32;                    // 4-float vectors per tile row
-constexpr int kTY = 8;                     // rows per tile
-constexpr int kHaloX = 4;                  // floats on each side of the tile row (16-byte aligned box start)
+constexpr int kTX = 32;    // 4-float vectors per tile row (threads in x)
+constexpr int kHaloX = 4;  // floats on each side of the tile row (16-byte aligned box start)
 constexpr int kBoxX = 4 * kTX + 2 * kHaloX;  // 136
-constexpr int kBoxY = kTY + 2;             // 10
-constexpr int kSlots = 6;
-constexpr int kBoxBytes = kBoxX * kBoxY * 4;                 // 5440: other-colour box
-constexpr int kGBoxBytes = 4 * kTX * kTY * 4;                // 4096: right-hand-side box
-constexpr int kGOff = ((kBoxBytes + 127) / 128) * 128;       // 5504: the rhs box within a slot
-constexpr int kSlotBytes = ((kGOff + kGBoxBytes + 127) / 128) * 128;  // 9600
-constexpr int kSmemBytes = kSlots * kSlotBytes + 64;         // + the mbarriers
-// tensor-copy destinations in shared memory must be 128-byte aligned
-static_assert(kGOff % 128 == 0 && kSlotBytes % 128 == 0, "TMA destinations need 128-byte alignment");
-constexpr long long kWaitCycles = 4000000000LL;           // wait budget, about 2 s at 2 GHz
+constexpr long long kWaitCycles = 4000000000LL;  // wait budget, about 2 s at 2 GHz
+
+constexpr int kCHalo = 4;  // coarse floats on each side of a tile's parents (16-byte aligned box start)
+constexpr int kCBoxX = 2 * kTX + 2 * kCHalo;  // 72: parents of the other-colour box, per coarse colour
+
+__host__ __device__ constexpr int round128(int b) { return ((b + 127) / 128) * 128; }
+
+// Tile of TY rows (one per thread row), ring of SLOTS plane slots. PRO: the black sweep fused
+// with the prolongation; each slot then also holds the coarse-correction rows (both coarse
+// colour arrays) under the other-colour box.
+template <int TY, int SLOTS, bool PRO = false>
+struct Cfg {
+  static constexpr int kTY = TY;
+  static constexpr int kSlots = SLOTS;
+  static constexpr bool kPro = PRO;
+  static constexpr int kBoxY = TY + 2;
+  static constexpr int kBoxBytes = kBoxX * kBoxY * 4;                  // other-colour box
+  static constexpr int kGBoxBytes = 4 * kTX * TY * 4;                  // right-hand-side box
+  static constexpr int kCBoxY = TY / 2 + 2;                            // coarse rows of the parents
+  static constexpr int kCBoxBytes = kCBoxX * kCBoxY * 4;               // one coarse colour's box
+  static constexpr int kGOff = round128(kBoxBytes);                    // rhs box within a slot
+  static constexpr int kC0Off = round128(kGOff + kGBoxBytes);          // coarse colour-0 box
+  static constexpr int kC1Off = round128(kC0Off + kCBoxBytes);         // coarse colour-1 box
+  static constexpr int kSlotBytes = PRO ? round128(kC1Off + kCBoxBytes) : round128(kGOff + kGBoxBytes);
+  static constexpr int kSmemBytes = SLOTS * kSlotBytes + 8 * SLOTS;    // + the mbarriers
+  // tensor-copy destinations in shared memory must be 128-byte aligned
+  static_assert(kGOff % 128 == 0 && kC0Off % 128 == 0 && kC1Off % 128 == 0 && kSlotBytes % 128 == 0,
+                "TMA destinations need 128-byte alignment");
+  static_assert(SLOTS >= 4, "planes k-1, k, k+1 and at least one copy in flight");
+  static_assert(TY % 2 == 0, "tiles cover whole coarse rows");
+};
+using Product = Cfg<8, 6>;           // 9600-byte slots, 57.6 KB per CTA, 3 CTAs per SM
+using ProductPro = Cfg<8, 5, true>;  // 13184-byte slots, 65.9 KB per CTA, 3 CTAs per SM
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -80,6 +102,7 @@ __device__ __forceinline__ void tma_load_box(unsigned dst, const CUtensorMap* ma
 struct Work {
   int x0, y0, k0, k1;  // tile origin (colour-array index, row) and planes [k0, k1)
 };
+template <int kTY>
 __device__ __forceinline__ Work work_item(const Geom& G, int kz, long long w) {
   const int tiles_x = (G.hx + 4 * kTX - 1) / (4 * kTX);
   const int tiles_y = (G.ny + kTY - 1) / kTY;
@@ -100,11 +123,21 @@ __device__ __forceinline__ Work work_item(const Geom& G, int kz, long long w) {
 // brings other-colour plane k0-1+i and, for i >= 2, right-hand-side plane k0-2+i. withhold >= 0
 // (the failure-path self-test only) leaves that load of each CTA's first item unissued, so the
 // waits for it run out of their `budget`.
-__global__ void __launch_bounds__(kTX* kTY) k_smooth_tma(float* __restrict__ x, Geom G, InvDiag<float> inv,
-                                                        int colour, int kz, long long nwork,
-                                                        const __grid_constant__ CUtensorMap other,
-                                                        const __grid_constant__ CUtensorMap rhs, int* err,
-                                                        long long budget, int withhold) {
+// With C::kPro the sweep is the first black post-smoothing sweep fused with the prolongation of
+// the coarse correction e_c (Sec. 3): every red value read is red + omega e_c(parent), the parent
+// of the red cell at packed index m of fine row (j', k') being coarse cell (m, j'/2, k'/2) (as in
+// ops::smooth_vec_prolong, whose arithmetic this repeats); the coarse rows arrive with each
+// red plane (coarse plane floor(p/2) for red plane p), out-of-range parents as zeros.
+template <class C>
+__global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ x, Geom G, InvDiag<float> inv,
+                                                           int colour, int kz, long long nwork,
+                                                           const __grid_constant__ CUtensorMap other,
+                                                           const __grid_constant__ CUtensorMap rhs,
+                                                           const __grid_constant__ CUtensorMap coarse0,
+                                                           const __grid_constant__ CUtensorMap coarse1, float omega,
+                                                           int* err, long long budget, int withhold) {
+  constexpr int kTY = C::kTY, kSlots = C::kSlots, kBoxBytes = C::kBoxBytes, kGBoxBytes = C::kGBoxBytes;
+  constexpr int kGOff = C::kGOff, kSlotBytes = C::kSlotBytes, kCBoxBytes = C::kCBoxBytes;
   extern __shared__ __align__(128) unsigned char smem[];
   float* ring = reinterpret_cast<float*>(smem);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kSlots * kSlotBytes);
@@ -124,7 +157,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_smooth_tma(float* __restrict__ x, 
   bool failed = false;
 
   for (long long w = blockIdx.x; w < nwork && !failed; w += gridDim.x) {
-    const Work t = work_item(G, kz, w);
+    const Work t = work_item<kTY>(G, kz, w);
     const int np = (t.k1 - t.k0) + 2;  // other-colour planes k0-1 .. k1
     // load i of the item into slot (seq+i) % kSlots
     auto issue = [&](int i) {
@@ -134,9 +167,14 @@ __global__ void __launch_bounds__(kTX* kTY) k_smooth_tma(float* __restrict__ x, 
       const unsigned bar = bar0 + 8u * q;
       const unsigned dst = ring0 + (unsigned)(q * kSlotBytes);
       const bool with_rhs = i >= 2;
-      mbar_expect_tx(bar, kBoxBytes + (with_rhs ? kGBoxBytes : 0));
+      mbar_expect_tx(bar, kBoxBytes + (with_rhs ? kGBoxBytes : 0) + (C::kPro ? 2 * kCBoxBytes : 0));
       tma_load_box(dst, &other, t.x0 - kHaloX, t.y0 - 1, t.k0 - 1 + i, bar);
       if (with_rhs) tma_load_box(dst + kGOff, &rhs, t.x0, t.y0, t.k0 - 2 + i, bar);
+      if (C::kPro) {
+        const int kc = (t.k0 - 1 + i + 2) / 2 - 1;  // floor(p / 2) for red plane p >= -1
+        tma_load_box(dst + C::kC0Off, &coarse0, t.x0 / 2 - kCHalo, t.y0 / 2 - 1, kc, bar);
+        tma_load_box(dst + C::kC1Off, &coarse1, t.x0 / 2 - kCHalo, t.y0 / 2 - 1, kc, bar);
+      }
       issued = n + 1;
     };
     __syncthreads();  // every thread is done with the previous item's slots
@@ -173,9 +211,51 @@ __global__ void __launch_bounds__(kTX* kTY) k_smooth_tma(float* __restrict__ x, 
         const float4 zp = *reinterpret_cast<const float4*>(pp + c0);
         const float extra = s == 0 ? pk[c0 - 1] : pk[c0 + 4];
         const float4 gv = *reinterpret_cast<const float4*>(pp + kGOff / 4 + ty * (4 * kTX) + 4 * tx);
-        const float ycv[4] = {yc.x, yc.y, yc.z, yc.w}, ymv[4] = {ym.x, ym.y, ym.z, ym.w};
-        const float ypv[4] = {yp.x, yp.y, yp.z, yp.w}, zmv[4] = {zm.x, zm.y, zm.z, zm.w};
-        const float zpv[4] = {zp.x, zp.y, zp.z, zp.w}, gvv[4] = {gv.x, gv.y, gv.z, gv.w};
+        float ycv[4] = {yc.x, yc.y, yc.z, yc.w}, ymv[4] = {ym.x, ym.y, ym.z, ym.w};
+        float ypv[4] = {yp.x, yp.y, yp.z, yp.w}, zmv[4] = {zm.x, zm.y, zm.z, zm.w};
+        float zpv[4] = {zp.x, zp.y, zp.z, zp.w};
+        const float gvv[4] = {gv.x, gv.y, gv.z, gv.w};
+        float extra_c = extra;
+        if constexpr (C::kPro) {
+          // omega e_c for the parents (m0 .. m0+3, J, K) of a red row segment, from a slot's
+          // coarse boxes: coarse cell I of row (J, K) has colour (I + J + K) & 1 and packed
+          // index I >> 1; box column (I >> 1) - (x0/2 - kCHalo), box row J - (y0/2 - 1)
+          const int K = k >> 1;
+          auto parents = [&](const float* slot, int Jc, int Kc, float (&w)[4]) {
+            const float* c0 = slot + C::kC0Off / 4;
+            const float* c1 = slot + C::kC1Off / 4;
+            const int rowb = (Jc - (t.y0 / 2 - 1)) * kCBoxX + 2 * tx + kCHalo;  // (m0 >> 1) - (x0/2 - kCHalo)
+            const bool even0 = ((m0 + Jc + Kc) & 1) == 0;                        // I = m0 has colour 0
+            const float2 a = *reinterpret_cast<const float2*>((even0 ? c0 : c1) + rowb);
+            const float2 b = *reinterpret_cast<const float2*>((even0 ? c1 : c0) + rowb);
+            w[0] = omega * a.x;
+            w[1] = omega * b.x;
+            w[2] = omega * a.y;
+            w[3] = omega * b.y;
+          };
+          auto parent1 = [&](const float* slot, int I, int Jc, int Kc) {
+            const float* cc = slot + (((I + Jc + Kc) & 1) ? C::kC1Off : C::kC0Off) / 4;
+            return omega * cc[(Jc - (t.y0 / 2 - 1)) * kCBoxX + (I >> 1) - (t.x0 / 2 - kCHalo)];
+          };
+          const int J = j >> 1;
+          float w[4];
+          parents(pk, J, K, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ycv[e] = ycv[e] + w[e];
+          extra_c = s == 0 ? extra + parent1(pk, m0 - 1, J, K) : extra + parent1(pk, m0 + 4, J, K);
+          parents(pk, (j - 1) >> 1, K, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ymv[e] = ymv[e] + w[e];
+          parents(pk, (j + 1) >> 1, K, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ypv[e] = ypv[e] + w[e];
+          parents(pm, J, (k - 1 + 2) / 2 - 1, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) zmv[e] = zmv[e] + w[e];
+          parents(pp, J, (k + 1) >> 1, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) zpv[e] = zpv[e] + w[e];
+        }
         int dbase = 0;
         if (j == 0) dbase += G.sh[2];
         if (j == G.ny - 1) dbase += G.sh[3];
@@ -186,11 +266,11 @@ __global__ void __launch_bounds__(kTX* kTY) k_smooth_tma(float* __restrict__ x, 
         for (int e = 0; e < 4; ++e) {
           float xm, xp;
           if (s == 0) {
-            xm = (e == 0) ? extra : ycv[e - 1 < 0 ? 0 : e - 1];
+            xm = (e == 0) ? extra_c : ycv[e - 1 < 0 ? 0 : e - 1];
             xp = ycv[e];
           } else {
             xm = ycv[e];
-            xp = (e == 3) ? extra : ycv[e + 1 > 3 ? 3 : e + 1];
+            xp = (e == 3) ? extra_c : ycv[e + 1 > 3 ? 3 : e + 1];
           }
           const float S = ((((xm + xp) + ymv[e]) + ypv[e]) + zmv[e]) + zpv[e];
           int d = dbase;
@@ -225,12 +305,13 @@ bool tma_sweep_pays(const Geom& G) {
   return tma_sweep_applies(G) && (long long)G.hx * G.ny * G.nz >= (1LL << 24);
 }
 
-cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom& G, int device) {
-  t.ok = 0;
-  if (!tma_sweep_applies(G)) return cudaSuccess;
-  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+namespace {
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encoder(EncodeFn* out) {
   static EncodeFn encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -240,58 +321,120 @@ cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom&
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<EncodeFn>(fn);
   }
+  *out = encode;
+  return cudaSuccess;
+}
+
+// 3D float map of one colour array of level G (x = packed index, y = row, z = plane).
+cudaError_t colour_map(EncodeFn encode, CUtensorMap* map, const float* base, const Geom& G, int box_x, int box_y) {
   const cuuint64_t dims[3] = {(cuuint64_t)G.hx, (cuuint64_t)G.ny, (cuuint64_t)G.nz};
   const cuuint64_t strides[2] = {(cuuint64_t)G.hx * 4, (cuuint64_t)G.hx * G.ny * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)kBoxX, (cuuint32_t)kBoxY, 1};
-  const cuuint32_t gbox[3] = {(cuuint32_t)(4 * kTX), (cuuint32_t)kTY, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  for (int c = 0; c < 2; ++c) {
-    float* base = x + (long long)(1 - c) * G.csz;          // a colour-c sweep reads colour 1-c
-    float* gbase = const_cast<float*>(g) + (long long)c * G.csz;  // and its own right-hand side
-    if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || reinterpret_cast<uintptr_t>(gbase) % 16 != 0)
-      return cudaSuccess;
-    CUresult r = encode(&t.other[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    r = encode(&t.rhs[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, gbase, dims, strides, gbox, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  }
-  cudaError_t e = cudaFuncSetAttribute(k_smooth_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Persistent grid and slab length for configuration C on level G.
+template <class C>
+cudaError_t size_launch(const Geom& G, int device, int& kz, long long& nwork, int& grid) {
+  cudaError_t e = cudaFuncSetAttribute(k_smooth_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_tma, kTX * kTY, kSmemBytes)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_tma<C>, kTX * C::kTY, C::kSmemBytes)) !=
+      cudaSuccess)
     return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
-  if (per_sm < 1) return cudaSuccess;
-  const long long tiles = (long long)((G.hx + 4 * kTX - 1) / (4 * kTX)) * ((G.ny + kTY - 1) / kTY);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long tiles = (long long)((G.hx + 4 * kTX - 1) / (4 * kTX)) * ((G.ny + C::kTY - 1) / C::kTY);
   const long long slots = (long long)per_sm * sms;
-  // planes per item: at least four items per resident CTA, at most 32 planes
-  int kz = 32;
-  while (kz > 8 && tiles * ((G.nz + kz - 1) / kz) < 4 * slots) kz /= 2;
-  t.kz = kz;
-  t.nwork = tiles * ((G.nz + kz - 1) / kz);
-  t.grid = (int)(t.nwork < slots ? t.nwork : slots);
+  // planes per item: long slabs (each starts by loading two extra planes), but at least two
+  // items per resident CTA; 64 planes measured best at 512^3
+  kz = 64;
+  while (kz > 8 && tiles * ((G.nz + kz - 1) / kz) < 2 * slots) kz /= 2;
+  nwork = tiles * ((G.nz + kz - 1) / kz);
+  grid = (int)(nwork < slots ? nwork : slots);
+  return cudaSuccess;
+}
+
+template <class C>
+cudaError_t prepare_tma_sweep_cfg(TmaSweep& t, float* x, const float* g, const Geom& G, int device) {
+  t.ok = 0;
+  if (!tma_sweep_applies(G)) return cudaSuccess;
+  EncodeFn encode = nullptr;
+  cudaError_t e = encoder(&encode);
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < 2; ++c) {
+    const float* base = x + (long long)(1 - c) * G.csz;  // a colour-c sweep reads colour 1-c
+    const float* gbase = g + (long long)c * G.csz;       // and its own right-hand side
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || reinterpret_cast<uintptr_t>(gbase) % 16 != 0)
+      return cudaSuccess;
+    if ((e = colour_map(encode, &t.other[c], base, G, kBoxX, C::kBoxY)) != cudaSuccess) return e;
+    if ((e = colour_map(encode, &t.rhs[c], gbase, G, 4 * kTX, C::kTY)) != cudaSuccess) return e;
+  }
+  if ((e = size_launch<C>(G, device, t.kz, t.nwork, t.grid)) != cudaSuccess) return e;
   t.ok = 1;
   return cudaSuccess;
 }
 
+// The prolongation-fused black sweep of level G with coarse correction ec on level Gc (packed).
+template <class C>
+cudaError_t prepare_tma_prolong_cfg(TmaSweep& t, const float* ec, const Geom& Gc, const Geom& G, int device) {
+  t.ok_pro = 0;
+  if (!t.ok || !Gc.packed || (Gc.hx % 4) != 0 || Gc.hx * 2 != G.hx || Gc.ny * 2 != G.ny || Gc.nz * 2 != G.nz)
+    return cudaSuccess;
+  EncodeFn encode = nullptr;
+  cudaError_t e = encoder(&encode);
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < 2; ++c) {
+    const float* base = ec + (long long)c * Gc.csz;
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return cudaSuccess;
+    if ((e = colour_map(encode, &t.coarse[c], base, Gc, kCBoxX, C::kCBoxY)) != cudaSuccess) return e;
+  }
+  if ((e = size_launch<C>(G, device, t.kz_pro, t.nwork_pro, t.grid_pro)) != cudaSuccess) return e;
+  t.ok_pro = 1;
+  return cudaSuccess;
+}
+
+template <class C>
+cudaError_t launch_smooth_tma_cfg(float* x, const Geom& G, const InvDiag<float>& inv, int colour, const TmaSweep& t,
+                                  int* err, long long budget, int withhold, cudaStream_t s) {
+  if (!t.ok) return cudaErrorInvalidValue;
+  k_smooth_tma<C><<<t.grid, dim3(kTX, C::kTY, 1), C::kSmemBytes, s>>>(
+      x, G, inv, colour, t.kz, t.nwork, t.other[colour], t.rhs[colour], t.other[colour], t.other[colour], 0.0f, err,
+      budget, withhold);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom& G, int device) {
+  return prepare_tma_sweep_cfg<Product>(t, x, g, G, device);
+}
+
+cudaError_t prepare_tma_prolong(TmaSweep& t, const float* ec, const Geom& Gc, const Geom& G, int device) {
+  return prepare_tma_prolong_cfg<ProductPro>(t, ec, Gc, G, device);
+}
+
 cudaError_t launch_smooth_tma(float* x, const Geom& G, const InvDiag<float>& inv, int colour, const TmaSweep& t,
                               int* err, cudaStream_t s) {
-  if (!t.ok) return cudaErrorInvalidValue;
-  k_smooth_tma<<<t.grid, dim3(kTX, kTY, 1), kSmemBytes, s>>>(x, G, inv, colour, t.kz, t.nwork, t.other[colour],
-                                                              t.rhs[colour], err, kWaitCycles, -1);
+  return launch_smooth_tma_cfg<Product>(x, G, inv, colour, t, err, kWaitCycles, -1, s);
+}
+
+cudaError_t launch_smooth_prolong_tma(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t,
+                                      float omega, int* err, cudaStream_t s) {
+  if (!t.ok_pro) return cudaErrorInvalidValue;
+  k_smooth_tma<ProductPro><<<t.grid_pro, dim3(kTX, ProductPro::kTY, 1), ProductPro::kSmemBytes, s>>>(
+      x, G, inv, 1, t.kz_pro, t.nwork_pro, t.other[1], t.rhs[1], t.coarse[0], t.coarse[1], omega, err, kWaitCycles,
+      -1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_smooth_tma_withheld(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t, int* err,
                                        long long budget_cycles, cudaStream_t s) {
-  if (!t.ok) return cudaErrorInvalidValue;
-  k_smooth_tma<<<t.grid, dim3(kTX, kTY, 1), kSmemBytes, s>>>(x, G, inv, 0, t.kz, t.nwork, t.other[0], t.rhs[0], err,
-                                                              budget_cycles, 2);
-  return cudaGetLastError();
+  return launch_smooth_tma_cfg<Product>(x, G, inv, 0, t, err, budget_cycles, 2, s);
 }
 
 }  // namespace ccmg

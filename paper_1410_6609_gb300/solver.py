@@ -258,8 +258,11 @@ class Poisson:
     def op_smooth(self, level: int, colour: int):
         self._check(self.lib.mg_op_smooth(self.ctx, level, colour), "mg_op_smooth")
 
-    def op_residual_restrict(self, level: int):
-        self._check(self.lib.mg_op_residual_restrict(self.ctx, level), "mg_op_residual_restrict")
+    def op_residual_restrict(self, level: int, red_only: bool = False):
+        if red_only:
+            self._check(self.lib.mg_op_residual_restrict_red(self.ctx, level), "mg_op_residual_restrict_red")
+        else:
+            self._check(self.lib.mg_op_residual_restrict(self.ctx, level), "mg_op_residual_restrict")
 
     def op_prolong_correct(self, level: int):
         self._check(self.lib.mg_op_prolong_correct(self.ctx, level), "mg_op_prolong_correct")

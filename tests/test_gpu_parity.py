@@ -285,6 +285,16 @@ def test_single_precision_level_operations_match_oracle(dims, bc):
         ref = oracle.restrict_f32(oracle.residual_f32(phi, f, c, bc))
         # the residual cancels O(1) terms to O(1) results: compare against the operands' scale
         assert np.abs(cpu(P.level_get(l + 1, 1)) - ref).max() < tol * 8 * np.abs(f).max()
+        # the red-only variant of the cycle: the same restriction with the black residuals dropped
+        P.level_set(l, 0, gpu(phi))
+        P.level_set(l, 1, gpu(f))
+        P.op_residual_restrict(l, red_only=True)
+        res = oracle.residual_f32(phi, f, c, bc)
+        kk, jj, ii = np.indices(res.shape)
+        res[(ii + jj + kk) % 2 == 1] = 0.0
+        ref_red = oracle.restrict_f32(res)
+        assert np.abs(cpu(P.level_get(l + 1, 1)) - ref_red).max() < tol * 8 * np.abs(f).max()
+        assert np.abs(ref_red - ref).max() > 1e-3 * np.abs(ref).max()  # the variants differ on this data
         ec = rng.standard_normal(tuple(reversed(P.level_dims(l + 1)))).astype(np.float32).astype(np.float64)
         P.level_set(l, 0, gpu(phi))
         P.level_set(l + 1, 0, gpu(ec))
@@ -333,3 +343,28 @@ def test_warm_start_continues_the_iteration():
     P.vcycle(2)
     assert torch.equal(P.solution(), full)
     P.close()
+
+
+def test_zero_start_without_writing_the_iterate():
+    """In mixed precision mg_set_solution(NULL) writes nothing (the first cycle stores phi = s e);
+    the solve, and every call that reads phi before it, equal those of an explicit zero field."""
+    dims = (64, 48, 32)
+    bc = synth.WALL_BC_TYPE
+    rho = synth.random_field(dims, seed=8)
+    outs = []
+    for explicit in (False, True):
+        P = Poisson(dims, bc_type=bc, bc_value=synth.wall_bc_value(1.0), precision="mixed")
+        P.set_rhs(gpu(rho))
+        zeros = torch.zeros(tuple(reversed(dims)), dtype=torch.float64, device="cuda")
+        P.set_solution(zeros if explicit else None)
+        phi0 = P.solution().clone()
+        rel0 = P.residual()
+        P.set_solution(zeros if explicit else None)
+        k, rel = P.solve(1e-9, 20)
+        outs.append((phi0, rel0, k, rel, P.solution().clone()))
+        P.close()
+    (a0, ra0, ka, rela, a), (b0, rb0, kb, relb, b) = outs
+    assert torch.equal(a0, b0) and not torch.any(a0 != 0)
+    assert ra0 == rb0 and abs(ra0 - 1.0) < 1e-12
+    assert ka == kb and rela == relb and rela < 1e-9
+    assert torch.equal(a, b)

@@ -112,14 +112,16 @@ def test_wait_timeout_reported_and_context_usable():
     b.close()
 
 
-def test_tma_solve_bit_identical():
-    """A whole mixed-precision solve (TMA on the two finest levels) equals the vectorised one."""
+@pytest.mark.parametrize("dims,tma_levels", [((256, 192, 128), 2), ((144, 84, 16), 1)])
+def test_tma_solve_bit_identical(dims, tma_levels):
+    """A whole mixed-precision solve equals the vectorised one: TMA half-sweeps and the
+    TMA-fused prolongation + black sweep on the finest levels (a partial tile in x and y on the
+    second grid)."""
     from paper_1410_6609_gb300 import synth
 
-    dims = (256, 192, 128)
     a, b = _pair(dims, bc_type=(N, N, N, N, D, D), bc_value=(0, 0, 0, 0, 0.0, 1.0))
-    assert [a.level_sweep_kind(l) for l in range(2)] == ["tma", "tma"]
-    sp = synth.random_spheres(dims, 60, 4.0, 21, 1.0)
+    assert [a.level_sweep_kind(l) for l in range(tma_levels + 1)] == ["tma"] * tma_levels + ["vec"]
+    sp = synth.random_spheres(dims, 60 if dims[2] > 64 else 6, 4.0, 21, 1.0)
     dev = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()  # noqa: E731
     c, r, q = dev(sp.centers), dev(sp.radius), dev(sp.density)
     out = []
