@@ -215,7 +215,7 @@ def run_reference(args):
         return
     w = workload(args)
     # cycles of the solve to tolerance measured on the GPU (mixed: outer steps of mixed_inner = 4 cycles)
-    cycles = {"spheres512": 3, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
+    cycles = {"spheres512": 3, "spheres384": 3, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
     for _ in range(min(args.warmup, 1)):
         pass
     samples = []

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_smooth_vec(T* __restrict__ x, const T* 
 }
 
 template <typename T, int V>
-__global__ void __launch_bounds__(256, 5) k_smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, Geom G,
+__global__ void __launch_bounds__(256) k_smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                             InvDiag<T> inv, const T* __restrict__ ec, Geom Gc,
                                                             T omega) {
   const int mv = blockIdx.x * blockDim.x + threadIdx.x;

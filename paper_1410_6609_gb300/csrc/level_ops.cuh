@@ -55,6 +55,31 @@ __device__ __forceinline__ T neg_diag(int d) {
   return r;
 }
 
+// 1/(6 + d) for the V cells m0 .. m0+V-1 of packed row (s, j, k). Cells away from every wall
+// (the bulk) take 1/6 without evaluating the per-cell shift; the branch is taken by the few
+// threads at a wall.
+template <typename T, int V>
+__device__ __forceinline__ void inv_diag_vec(const Geom& G, const InvDiag<T>& inv, int m0, int s, int j, int k,
+                                             T (&invd)[V]) {
+  if (j == 0 || j == G.ny - 1 || k == 0 || k == G.nz - 1 || m0 == 0 || m0 + V >= G.hx) {
+    int dbase = 0;
+    if (j == 0) dbase += G.sh[2];
+    if (j == G.ny - 1) dbase += G.sh[3];
+    if (k == 0) dbase += G.sh[4];
+    if (k == G.nz - 1) dbase += G.sh[5];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      int d = dbase;
+      if (m0 + v == 0 && s == 0) d += G.sh[0];
+      if (m0 + v == G.hx - 1 && s == 1) d += G.sh[1];
+      invd[v] = inv_of(inv, d);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) invd[v] = inv.v[3];
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Power-of-two scaling. The defect-correction scale is a power of two, and so are the 1/(2h),
 // 1/eps and h^2 factors of the lattice-unit workloads. Multiplying by 2^q and the conversions
@@ -254,21 +279,12 @@ __device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restric
   const int s = (j + k + colour) & 1;
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)colour * G.csz + row + m0;
-  int dbase = 0;
-  if (j == 0) dbase += G.sh[2];
-  if (j == G.ny - 1) dbase += G.sh[3];
-  if (k == 0) dbase += G.sh[4];
-  if (k == G.nz - 1) dbase += G.sh[5];
-  T gv[V], out[V];
+  T gv[V], out[V], invd[V];
   load_vec(g + own, gv);
+  inv_diag_vec<T, V>(G, inv, m0, s, j, k, invd);
   if (ZERO) {
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-      int d = dbase;
-      if (m0 + i == 0 && s == 0) d += G.sh[0];
-      if (m0 + i == G.hx - 1 && s == 1) d += G.sh[1];
-      out[i] = (gv[i] + T(0)) * inv_of(inv, d);
-    }
+    for (int i = 0; i < V; ++i) out[i] = (gv[i] + T(0)) * invd[i];
   } else {
     const T* yr = x + (long long)(1 - colour) * G.csz + row;
     const long long plane = (long long)G.ny * G.hx;
@@ -304,10 +320,7 @@ __device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restric
         xp = (i == V - 1) ? extra : yc[(i + 1) % V];
       }
       const T S = ((((xm + xp) + ym[i]) + yp[i]) + zm[i]) + zp[i];
-      int d = dbase;
-      if (m0 + i == 0 && s == 0) d += G.sh[0];
-      if (m0 + i == G.hx - 1 && s == 1) d += G.sh[1];
-      out[i] = (gv[i] + S) * inv_of(inv, d);
+      out[i] = (gv[i] + S) * invd[i];
     }
   }
   store_vec(x + own, out);
@@ -361,15 +374,11 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
   const int s = (j + k + colour) & 1;
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)colour * G.csz + row + m0;
-  int dbase = 0;
-  if (j == 0) dbase += G.sh[2];
-  if (j == G.ny - 1) dbase += G.sh[3];
-  if (k == 0) dbase += G.sh[4];
-  if (k == G.nz - 1) dbase += G.sh[5];
   const T* yr = x + row;  // red array, row (j,k)
   const long long plane = (long long)G.ny * G.hx;
   const int J = j >> 1, K = k >> 1;
-  T gv[V], out[V], yc[V], ym[V], yp[V], zm[V], zp[V], wc[V], wy[V], wz[V];
+  T gv[V], out[V], yc[V], ym[V], yp[V], zm[V], zp[V], wc[V], wy[V], wz[V], invd[V];
+  inv_diag_vec<T, V>(G, inv, m0, s, j, k, invd);
   load_vec(g + own, gv);
   load_vec(yr + m0, yc);
   // coarse parents: row (J, K) serves the row itself and the y- and z-neighbour rows inside the
@@ -430,10 +439,7 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
       xp = (v == V - 1) ? extra : yc[(v + 1) % V];
     }
     const T S = ((((xm + xp) + ym[v]) + yp[v]) + zm[v]) + zp[v];
-    int d = dbase;
-    if (m0 + v == 0 && s == 0) d += G.sh[0];
-    if (m0 + v == G.hx - 1 && s == 1) d += G.sh[1];
-    out[v] = (gv[v] + S) * inv_of(inv, d);
+    out[v] = (gv[v] + S) * invd[v];
   }
   store_vec(x + own, out);
 }

@@ -184,14 +184,23 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
     const int m0 = t.x0 + 4 * tx;
     const int j = t.y0 + ty;
     const bool mine = m0 < G.hx && j < G.ny;
+    // ring positions of loads i-1, i, i+1 (planes k-1, k, k+1) and the phase parity of load
+    // i+1, advanced by one slot per plane instead of being recomputed
+    int qm = seq % kSlots, qk = (seq + 1) % kSlots, qp = (seq + 2) % kSlots;
+    unsigned php = (unsigned)(((seq + 2) / kSlots) & 1);
+    float* xrow = xo + ((long long)t.k0 * G.ny + j) * G.hx + m0;  // own row of plane k
+    const long long plane_stride = (long long)G.ny * G.hx;
+    // walls touched by this thread's cells in every plane but the first and last (x and y);
+    // without any, every cell's diagonal is 6
+    const bool xy_wall = j == 0 || j == G.ny - 1 || (m0 == 0) || (m0 + 4 >= G.hx);
     for (int k = t.k0; k < t.k1; ++k) {
       const int i = k - t.k0 + 1;  // load index of plane k (k-1 is i-1; k+1 and g(k) are i+1)
-      const long long row = ((long long)k * G.ny + j) * G.hx;
       bool ok = true;
-      for (int d = (k == t.k0 ? -1 : 1); d <= 1; ++d) {
-        const int n = seq + i + d;
-        ok = ok && mbar_wait(bar0 + 8u * (unsigned)(n % kSlots), (unsigned)((n / kSlots) & 1), budget);
+      if (k == t.k0) {
+        ok = mbar_wait(bar0 + 8u * (unsigned)qm, (unsigned)((seq / kSlots) & 1), budget);
+        ok = ok && mbar_wait(bar0 + 8u * (unsigned)qk, (unsigned)(((seq + 1) / kSlots) & 1), budget);
       }
+      ok = ok && mbar_wait(bar0 + 8u * (unsigned)qp, php, budget);
       // the barrier also retires iteration k-1, freeing the slot of load i-2 for load i+kSlots-2
       if (__syncthreads_or(!ok)) {
         failed = true;
@@ -200,9 +209,9 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
       if (leader && i + kSlots - 2 < np) issue(i + kSlots - 2);
       if (mine) {
         const int s = (j + k + colour) & 1;
-        const float* pk = ring + (size_t)((seq + i) % kSlots) * (kSlotBytes / 4);
-        const float* pm = ring + (size_t)((seq + i - 1) % kSlots) * (kSlotBytes / 4);
-        const float* pp = ring + (size_t)((seq + i + 1) % kSlots) * (kSlotBytes / 4);
+        const float* pk = ring + qk * (kSlotBytes / 4);
+        const float* pm = ring + qm * (kSlotBytes / 4);
+        const float* pp = ring + qp * (kSlotBytes / 4);
         const int c0 = (ty + 1) * kBoxX + kHaloX + 4 * tx;
         const float4 yc = *reinterpret_cast<const float4*>(pk + c0);
         const float4 ym = *reinterpret_cast<const float4*>(pk + c0 - kBoxX);
@@ -256,11 +265,24 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
 #pragma unroll
           for (int e = 0; e < 4; ++e) zpv[e] = zpv[e] + w[e];
         }
-        int dbase = 0;
-        if (j == 0) dbase += G.sh[2];
-        if (j == G.ny - 1) dbase += G.sh[3];
-        if (k == 0) dbase += G.sh[4];
-        if (k == G.nz - 1) dbase += G.sh[5];
+        float invd[4];
+        if (xy_wall || k == 0 || k == G.nz - 1) {
+          int dbase = 0;
+          if (j == 0) dbase += G.sh[2];
+          if (j == G.ny - 1) dbase += G.sh[3];
+          if (k == 0) dbase += G.sh[4];
+          if (k == G.nz - 1) dbase += G.sh[5];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            int d = dbase;
+            if (m0 + e == 0 && s == 0) d += G.sh[0];
+            if (m0 + e == G.hx - 1 && s == 1) d += G.sh[1];
+            invd[e] = inv_of(inv, d);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) invd[e] = inv.v[3];  // 1/6
+        }
         float out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -273,12 +295,16 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
             xp = (e == 3) ? extra_c : ycv[e + 1 > 3 ? 3 : e + 1];
           }
           const float S = ((((xm + xp) + ymv[e]) + ypv[e]) + zmv[e]) + zpv[e];
-          int d = dbase;
-          if (m0 + e == 0 && s == 0) d += G.sh[0];
-          if (m0 + e == G.hx - 1 && s == 1) d += G.sh[1];
-          out[e] = (gvv[e] + S) * inv_of(inv, d);
+          out[e] = (gvv[e] + S) * invd[e];
         }
-        *reinterpret_cast<float4*>(xo + row + m0) = make_float4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<float4*>(xrow) = make_float4(out[0], out[1], out[2], out[3]);
+      }
+      xrow += plane_stride;
+      qm = qk;
+      qk = qp;
+      if (++qp == kSlots) {
+        qp = 0;
+        php ^= 1u;
       }
     }
     seq += np;

@@ -126,6 +126,11 @@ WORKLOADS = {
                            "mixed", sphere_count=1600, seed=3),
     "adjoint256": Workload("adjoint256", (256, 256, 256), 1.0, WALL_BC_TYPE, wall_bc_value(1.0), 1e-10,
                            "fp64", sphere_count=32, seed=5),
+    # the 512^3 setup at 384^3 (same sphere density, 675 spheres): each colour array of the finest
+    # single-precision level (113 MB) is about the size of L2, the whole problem about 1.6 GB,
+    # which suits detailed hardware-counter captures of the finest-level kernels
+    "spheres384": Workload("spheres384", (384, 384, 384), 1.0, WALL_BC_TYPE, wall_bc_value(1.0), 1e-9,
+                           "mixed", sphere_count=675, seed=6),
 }
 
 
