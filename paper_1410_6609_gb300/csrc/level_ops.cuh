@@ -675,6 +675,7 @@ __device__ int coarse_cg_warp(T* __restrict__ xo, const T* __restrict__ bi, cons
   double rr = warp_sum(loc);
   const double bnorm = sqrt(rr);
   const double stop = rtol * bnorm;
+  const double stop2 = stop * stop;  // ||r|| <= stop as ||r||^2 <= stop^2: no square root per iteration
   int it = 0;
   if (bnorm > 0.0) {
     while (it < maxit) {
@@ -711,7 +712,7 @@ __device__ int coarse_cg_warp(T* __restrict__ xo, const T* __restrict__ bi, cons
       }
       const double rrn = warp_sum(loc);
       ++it;
-      if (sqrt(rrn) <= stop) break;
+      if (rrn <= stop2) break;
       const double beta = rrn / rr;
       __syncwarp();  // every lane has read p for its product before p changes
 #pragma unroll
