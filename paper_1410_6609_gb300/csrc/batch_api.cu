@@ -155,21 +155,34 @@ mg_status plan(mg_batch* b) {
       e.xc = mx ? (void*)S.x32[d + 1] : (void*)S.x64[d + 1];
       e.gc = mx ? (void*)S.g32[d + 1] : (void*)S.g64[d + 1];
       e.sys = s;
+      // vector entries and the prolongation take chunks of a plane's (row, element) pairs with
+      // sbx * sby (tbx * tby) threads per block; the rest a 2D (element, row) tile
       BEntry es1 = e;
       es1.vec = (e.G.hx % V == 0) ? 1 : 0;
-      const int w = es1.vec ? e.G.hx / V : e.G.hx;
-      es1.gx = ceil_div(w, sbx);
-      es1.gy = ceil_div(e.G.ny, sby);
+      if (es1.vec) {
+        es1.gx = ceil_div((long long)(e.G.hx / V) * e.G.ny, sbx * sby);
+        es1.gy = 1;
+      } else {
+        es1.gx = ceil_div(e.G.hx, sbx);
+        es1.gy = ceil_div(e.G.ny, sby);
+      }
       es1.gz = e.G.nz;
       es.push_back(es1);
       BEntry et1 = e;  // prolongation: one thread per coarse cell
-      et1.gx = ceil_div(e.Gc.nx, tbx);
-      et1.gy = ceil_div(e.Gc.ny, tby);
+      et1.gx = ceil_div((long long)e.Gc.nx * e.Gc.ny, tbx * tby);
+      et1.gy = 1;
       et1.gz = e.Gc.nz;
       et.push_back(et1);
-      BEntry er1 = et1;  // residual + restriction: V coarse cells per thread where rows allow
+      BEntry er1 = e;  // residual + restriction: V coarse cells per thread where rows allow
       er1.vec = (e.G.hx % V == 0) ? 1 : 0;
-      er1.gx = ceil_div(er1.vec ? e.Gc.nx / V : e.Gc.nx, tbx);
+      if (er1.vec) {
+        er1.gx = ceil_div((long long)(e.Gc.nx / V) * e.Gc.ny, tbx * tby);
+        er1.gy = 1;
+      } else {
+        er1.gx = ceil_div(e.Gc.nx, tbx);
+        er1.gy = ceil_div(e.Gc.ny, tby);
+      }
+      er1.gz = e.Gc.nz;
       er.push_back(er1);
     }
     add_plan(b, b->smooth[d], es, dim3(sbx, sby, 1));

@@ -23,6 +23,19 @@ __device__ __forceinline__ int find_entry(const int* __restrict__ start, int cou
   return lo;
 }
 
+// Vector entries map a block to a chunk of one plane's (row, vector) pairs, taken row-major:
+// the rows of a plane are contiguous in a colour array, so every lane has work and a warp's
+// accesses are contiguous whatever the row length (entry.gx = chunks per plane, gy = 1). Other
+// entries keep a 2D tile of (packed index, row).
+__device__ __forceinline__ bool flat_coords(int lb, int gx, int per_row, int rows, int& a, int& row, int& plane) {
+  const int nt = blockDim.x * blockDim.y;
+  plane = lb / gx;
+  const int idx = (lb - plane * gx) * nt + threadIdx.y * blockDim.x + threadIdx.x;
+  row = idx / per_row;
+  a = idx - row * per_row;
+  return row < rows;
+}
+
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
                                                  const int* __restrict__ active, InvDiag<T> inv, int colour) {
@@ -31,16 +44,16 @@ __global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, c
   const BEntry& en = E[e];
   if (!active[en.sys]) return;
   const int lb = blockIdx.x - start[e];
-  const int bxi = lb % en.gx, rest = lb / en.gx;
-  const int byi = rest % en.gy, k = rest / en.gy;
   const Geom G = en.G;
-  const int j = byi * blockDim.y + threadIdx.y;
   T* x = (T*)en.x;
   const T* g = (const T*)en.g;
   if (en.vec) {
-    const int mv = bxi * blockDim.x + threadIdx.x;
-    if (mv < G.hx / V && j < G.ny) smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
+    int mv, j, k;
+    if (flat_coords(lb, en.gx, G.hx / V, G.ny, mv, j, k)) smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
   } else {
+    const int bxi = lb % en.gx, rest = lb / en.gx;
+    const int byi = rest % en.gy, k = rest / en.gy;
+    const int j = byi * blockDim.y + threadIdx.y;
     const int m = bxi * blockDim.x + threadIdx.x;
     if (m < G.hx && j < G.ny) smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
   }
@@ -53,17 +66,18 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restric
   const BEntry& en = E[e];
   if (!active[en.sys]) return;
   const int lb = blockIdx.x - start[e];
-  const int bxi = lb % en.gx, rest = lb / en.gx;
-  const int byi = rest % en.gy, K = rest / en.gy;
   const Geom G = en.G, Gc = en.Gc;
-  const int I = bxi * blockDim.x + threadIdx.x;
-  const int J = byi * blockDim.y + threadIdx.y;
   if (en.vec) {
     constexpr int V = 16 / sizeof(T);
-    if (I < Gc.nx / V && J < Gc.ny)
-      resid_restrict_vec<T, V, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
-  } else if (I < Gc.nx && J < Gc.ny) {
-    resid_restrict_cell<T, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+    int iv, J, K;
+    if (flat_coords(lb, en.gx, Gc.nx / V, Gc.ny, iv, J, K))
+      resid_restrict_vec<T, V, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, iv, J, K);
+  } else {
+    const int bxi = lb % en.gx, rest = lb / en.gx;
+    const int byi = rest % en.gy, K = rest / en.gy;
+    const int I = bxi * blockDim.x + threadIdx.x;
+    const int J = byi * blockDim.y + threadIdx.y;
+    if (I < Gc.nx && J < Gc.ny) resid_restrict_cell<T, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
   }
 }
 
@@ -74,12 +88,10 @@ __global__ void __launch_bounds__(256) kb_prolong(const BEntry* __restrict__ E, 
   const BEntry& en = E[e];
   if (!active[en.sys]) return;
   const int lb = blockIdx.x - start[e];
-  const int bxi = lb % en.gx, rest = lb / en.gx;
-  const int byi = rest % en.gy, K = rest / en.gy;
   const Geom G = en.G, Gc = en.Gc;
-  const int I = bxi * blockDim.x + threadIdx.x;
-  const int J = byi * blockDim.y + threadIdx.y;
-  if (I < Gc.nx && J < Gc.ny) prolong_cell<T>((T*)en.x, G, (const T*)en.xc, Gc, omega, red_only, I, J, K);
+  int I, J, K;
+  if (flat_coords(lb, en.gx, Gc.nx, Gc.ny, I, J, K))
+    prolong_cell<T>((T*)en.x, G, (const T*)en.xc, Gc, omega, red_only, I, J, K);
 }
 
 // One CTA per system: CG on the system's coarsest grid.

@@ -78,22 +78,26 @@ __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Ge
   }
 }
 
+// SFC > 0: the loops run exactly SFC steps (sf == SFC, the common s_f = 2 compiled alone, which
+// keeps the kernels small); SFC == 0: any sf <= 8. Same operations in the same order either way.
+template <int SFC = 0>
 __device__ __forceinline__ int overlap_count(int i, int j, int k, double h, double cx, double cy, double cz, double R2,
                                              int sf, const SubOff& so) {
+  constexpr int kMax = SFC > 0 ? SFC : 8;
   int cnt = 0;
 #pragma unroll
-  for (int mk = 0; mk < 8; ++mk) {
-    if (mk >= sf) break;
+  for (int mk = 0; mk < kMax; ++mk) {
+    if (SFC == 0 && mk >= sf) break;
     const double dz = __dsub_rn(__dmul_rn(__dadd_rn((double)k, so.o[mk]), h), cz);
     const double dz2 = __dmul_rn(dz, dz);
 #pragma unroll
-    for (int mj = 0; mj < 8; ++mj) {
-      if (mj >= sf) break;
+    for (int mj = 0; mj < kMax; ++mj) {
+      if (SFC == 0 && mj >= sf) break;
       const double dy = __dsub_rn(__dmul_rn(__dadd_rn((double)j, so.o[mj]), h), cy);
       const double dy2 = __dmul_rn(dy, dy);
 #pragma unroll
-      for (int mi = 0; mi < 8; ++mi) {
-        if (mi >= sf) break;
+      for (int mi = 0; mi < kMax; ++mi) {
+        if (SFC == 0 && mi >= sf) break;
         const double dx = __dsub_rn(__dmul_rn(__dadd_rn((double)i, so.o[mi]), h), cx);
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), dy2), dz2);
         cnt += (d2 <= R2) ? 1 : 0;
@@ -170,7 +174,52 @@ __global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Ge
   E[2 * N + p] = e[2];
 }
 
+// The same on a packed level, two cells per thread: cells 2m and 2m+1 of row (j, k) sit at index m
+// of the two colour arrays, so a warp's loads (the pair, its x-neighbours at m-1 and m+1, both
+// colours in the four neighbour rows) and its 16-byte stores of each component are contiguous.
+// Interior pairs take the differences directly, in efield_at's order; pairs at a wall call
+// efield_at per cell.
+template <bool POW2>
+__global__ void __launch_bounds__(256) k_efield_pair(const double* __restrict__ x, Geom G, double h, double inv2h,
+                                                     int q2, FaceBC bc, double* __restrict__ E) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (m >= G.hx || j >= G.ny) return;
+  const int i0 = 2 * m;
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  const long long p = (long long)i0 + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+  double e0[3], e1[3];
+  const bool interior = m > 0 && m < G.hx - 1 && j > 0 && j < G.ny - 1 && k > 0 && k < G.nz - 1;
+  if (__all_sync(__activemask(), interior)) {
+    const int c0 = (i0 + j + k) & 1;  // colour of cell 2m; cell 2m+1 has the other
+    const long long row = ((long long)k * G.ny + j) * G.hx + m;
+    const long long plane = (long long)G.ny * G.hx;
+    const double* a0 = x + (long long)c0 * G.csz;        // colour of 2m
+    const double* a1 = x + (long long)(c0 ^ 1) * G.csz;  // colour of 2m+1 (and of 2m's y/z neighbours)
+    const double p0 = __ldg(a0 + row), p1 = __ldg(a1 + row);
+    const double xm = __ldg(a1 + row - 1), xp = __ldg(a0 + row + 1);  // cells 2m-1 and 2m+2
+    const double d00 = xm - p1, d10 = p0 - xp;
+    const double d01 = __ldg(a1 + row - G.hx) - __ldg(a1 + row + G.hx);
+    const double d11 = __ldg(a0 + row - G.hx) - __ldg(a0 + row + G.hx);
+    const double d02 = __ldg(a1 + row - plane) - __ldg(a1 + row + plane);
+    const double d12 = __ldg(a0 + row - plane) - __ldg(a0 + row + plane);
+    e0[0] = POW2 ? ldexp_rne(d00, q2) : d00 * inv2h;
+    e0[1] = POW2 ? ldexp_rne(d01, q2) : d01 * inv2h;
+    e0[2] = POW2 ? ldexp_rne(d02, q2) : d02 * inv2h;
+    e1[0] = POW2 ? ldexp_rne(d10, q2) : d10 * inv2h;
+    e1[1] = POW2 ? ldexp_rne(d11, q2) : d11 * inv2h;
+    e1[2] = POW2 ? ldexp_rne(d12, q2) : d12 * inv2h;
+  } else {
+    efield_at<POW2>(x, G, i0, j, k, h, inv2h, q2, bc, e0);
+    efield_at<POW2>(x, G, i0 + 1, j, k, h, inv2h, q2, bc, e1);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) *reinterpret_cast<double2*>(E + a * N + p) = make_double2(e0[a], e1[a]);
+}
+
 // One CTA per sphere: rho(b) += density_s * count / sf^3 over the sphere's cells.
+template <int SFC>
 __global__ void __launch_bounds__(256) k_sphere_density(Geom G, double h, Spheres sp, int sf, SubOff so,
                                                         double* __restrict__ rho) {
   const int s = blockIdx.x;
@@ -184,13 +233,14 @@ __global__ void __launch_bounds__(256) k_sphere_density(Geom G, double h, Sphere
     const int i = B.lo[0] + (int)(t % B.nb[0]);
     const int j = B.lo[1] + (int)((t / B.nb[0]) % B.nb[1]);
     const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
-    const int cnt = overlap_count(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
+    const int cnt = overlap_count<SFC>(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
     if (cnt == 0) continue;
     atomicAdd(rho + nat(G, i, j, k), q * ((double)cnt / sf3));
   }
 }
 
 // One CTA per sphere: F_s = (h^3 density_s) * sum_b w_{s,b} E(x_b).
+template <int SFC>
 __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__ x, Geom G, double h, double inv2h,
                                                       FaceBC bc, Spheres sp, int sf, SubOff so,
                                                       double* __restrict__ F) {
@@ -206,7 +256,7 @@ __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__
     const int i = B.lo[0] + (int)(t % B.nb[0]);
     const int j = B.lo[1] + (int)((t / B.nb[0]) % B.nb[1]);
     const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
-    const int cnt = overlap_count(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
+    const int cnt = overlap_count<SFC>(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
     if (cnt == 0) continue;
     const double w = (double)cnt / sf3;
     double e[3];
@@ -362,10 +412,17 @@ SubOff make_suboff(int sf) {
 }  // namespace
 
 cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, double* E, cudaStream_t s) {
-  const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
-  dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
   const double inv2h = 1.0 / (2.0 * h);
   const int q2 = host_pow2_exponent(inv2h);
+  if (G.packed && reinterpret_cast<uintptr_t>(E) % 16 == 0) {
+    const int bx = G.hx >= 128 ? 128 : (G.hx >= 64 ? 64 : 32);
+    dim3 b(bx, 256 / bx, 1), g((G.hx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
+    if (q2 != kBadPow2) k_efield_pair<true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    else k_efield_pair<false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    return cudaGetLastError();
+  }
+  const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
+  dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
   if (q2 != kBadPow2)
     k_efield<true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
   else
@@ -377,14 +434,18 @@ cudaError_t launch_sphere_density(const Geom& G, double h, const Spheres& sp, in
   const long long N = (long long)G.nx * G.ny * G.nz;
   cudaError_t e = cudaMemsetAsync(rho, 0, (size_t)N * sizeof(double), s);
   if (e != cudaSuccess || sp.P == 0) return e;
-  k_sphere_density<<<sp.P, 256, 0, s>>>(G, h, sp, sf, make_suboff(sf), rho);
+  if (sf == 2) k_sphere_density<2><<<sp.P, 256, 0, s>>>(G, h, sp, sf, make_suboff(sf), rho);
+  else if (sf == 1) k_sphere_density<1><<<sp.P, 256, 0, s>>>(G, h, sp, sf, make_suboff(sf), rho);
+  else k_sphere_density<0><<<sp.P, 256, 0, s>>>(G, h, sp, sf, make_suboff(sf), rho);
   return cudaGetLastError();
 }
 
 cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
                                 double* F, cudaStream_t s) {
   if (sp.P == 0) return cudaSuccess;
-  k_force_gather<<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
+  if (sf == 2) k_force_gather<2><<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
+  else if (sf == 1) k_force_gather<1><<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
+  else k_force_gather<0><<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
   return cudaGetLastError();
 }
 

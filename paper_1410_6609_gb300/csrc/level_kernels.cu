@@ -168,6 +168,36 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
   gout[o] = (T)(POW2 ? ldexp_rne(v, qh) : v * hsq);
 }
 
+// The same for a packed level, two cells per thread: cells 2m and 2m+1 of row (j, k) are one
+// 16-byte load of rho and land at index m of the two colour arrays, so both the loads and the
+// stores of a warp are contiguous.
+template <typename T, bool POW2>
+__global__ void __launch_bounds__(256) k_set_rhs_pair(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
+                                                      double inv_eps, double hsq, int qe, int qh, WallTerms wt,
+                                                      int raw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (m >= G.hx || j >= G.ny) return;
+  const int i0 = 2 * m;
+  const long long p = (long long)i0 + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+  const double2 r = __ldg(reinterpret_cast<const double2*>(rho + p));
+  double v0 = r.x, v1 = r.y;
+  if (!raw) {
+    v0 = POW2 ? ldexp_rne(v0, qe) : v0 * inv_eps;
+    v1 = POW2 ? ldexp_rne(v1, qe) : v1 * inv_eps;
+    const bool wall = i0 == 0 || i0 + 1 == G.nx - 1 || j == 0 || j == G.ny - 1 || k == 0 || k == G.nz - 1;
+    if (__any_sync(__activemask(), wall)) {
+      v0 = add_wall_terms(v0, i0, j, k, G, wt);
+      v1 = add_wall_terms(v1, i0 + 1, j, k, G, wt);
+    }
+  }
+  const int c0 = (i0 + j + k) & 1;
+  const long long o = ((long long)k * G.ny + j) * G.hx + m;
+  gout[(long long)c0 * G.csz + o] = (T)(POW2 ? ldexp_rne(v0, qh) : v0 * hsq);
+  gout[(long long)(c0 ^ 1) * G.csz + o] = (T)(POW2 ? ldexp_rne(v1, qh) : v1 * hsq);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(T* __restrict__ dst, Geom G, const double* __restrict__ src,
                                               double scale) {
@@ -412,13 +442,18 @@ cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_ep
   for (int q = 0; q < 6; ++q)
     wt.t[q] = bc.type[q] == 0 ? 2.0 * bc.value[q] / (h * h) : bc.value[q] / h;
   dim3 b, gr;
-  shape(G.nx, G.ny, G.nz, b, gr);
   const double hsq = h * h;
   const int qe = host_pow2_exponent(inv_eps), qh = host_pow2_exponent(hsq);
-  if (qe != kBadPow2 && qh != kBadPow2)
-    k_set_rhs<T, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
-  else
-    k_set_rhs<T, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+  const bool pow2 = qe != kBadPow2 && qh != kBadPow2;
+  if (G.packed && reinterpret_cast<uintptr_t>(rho) % 16 == 0) {
+    shape(G.hx, G.ny, G.nz, b, gr);
+    if (pow2) k_set_rhs_pair<T, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    else k_set_rhs_pair<T, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    return cudaGetLastError();
+  }
+  shape(G.nx, G.ny, G.nz, b, gr);
+  if (pow2) k_set_rhs<T, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+  else k_set_rhs<T, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
   return cudaGetLastError();
 }
 
