@@ -65,6 +65,7 @@ struct mg_batch {
   int* d_starts = nullptr;
   size_t cap_entries = 0, cap_starts = 0;
   Plan smooth[kMaxLevels], xfer[kMaxLevels], restr[kMaxLevels], cg, resid, update;
+  Plan xfer_nv[kMaxLevels];  // prolongation entries of the systems whose rows are not whole vectors
   size_t cg_smem = 0;
   int* d_active = nullptr;
   int* h_active = nullptr;
@@ -140,10 +141,11 @@ mg_status plan(mg_batch* b) {
   for (int d = 0; d < kMaxLevels; ++d) {
     b->smooth[d] = Plan();
     b->xfer[d] = Plan();
+    b->xfer_nv[d] = Plan();
     b->restr[d] = Plan();
   }
   for (int d = 0; d + 1 < b->maxL; ++d) {
-    std::vector<BEntry> es, et, er;
+    std::vector<BEntry> es, et, er, etn;
     for (int s = 0; s < b->B; ++s) {
       BSys& S = b->sys[s];
       if (d >= S.L - 1) continue;
@@ -173,6 +175,7 @@ mg_status plan(mg_batch* b) {
       et1.gy = 1;
       et1.gz = e.Gc.nz;
       et.push_back(et1);
+      if (e.G.hx % V != 0) etn.push_back(et1);
       BEntry er1 = e;  // residual + restriction: V coarse cells per thread where rows allow
       er1.vec = (e.G.hx % V == 0) ? 1 : 0;
       if (er1.vec) {
@@ -187,6 +190,7 @@ mg_status plan(mg_batch* b) {
     }
     add_plan(b, b->smooth[d], es, dim3(sbx, sby, 1));
     add_plan(b, b->xfer[d], et, dim3(tbx, tby, 1));
+    add_plan(b, b->xfer_nv[d], etn, dim3(tbx, tby, 1));
     add_plan(b, b->restr[d], er, dim3(tbx, tby, 1));
   }
   {  // coarsest grids: one CTA each, as many threads as the largest single-system launch would use
@@ -283,13 +287,21 @@ cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cuda
   }
   if ((e = launch_b_coarse_cg<T>(bl(b, b->cg), act, b->cg_smem, 1e-14, s)) != cudaSuccess) return e;
   ++*nk;
+  // single precision, as the single-system cycle: the prolongation is fused into the first black
+  // sweep of the systems whose rows are whole vectors; the others prolong first
+  const bool fuse = sizeof(T) == sizeof(float) && b->nu2 >= 1;
   for (int d = b->maxL - 2; d >= 0; --d) {
     const BLaunch Ls = bl(b, b->smooth[d]);
     if (Ls.count == 0) continue;
-    if ((e = launch_b_prolong<T>(bl(b, b->xfer[d]), act, (T)b->omega, b->nu2 >= 1, s)) != cudaSuccess) return e;
-    ++*nk;
+    const BLaunch Lp = bl(b, fuse ? b->xfer_nv[d] : b->xfer[d]);
+    if ((e = launch_b_prolong<T>(Lp, act, (T)b->omega, b->nu2 >= 1, s)) != cudaSuccess) return e;
+    *nk += Lp.count > 0 ? 1 : 0;
     for (int it = 0; it < b->nu2; ++it) {
-      if ((e = launch_b_smooth<T>(Ls, act, inv, 1, false, s)) != cudaSuccess) return e;
+      if (fuse && it == 0)
+        e = launch_b_smooth_prolong(Ls, act, b->inv32, (float)b->omega, s);
+      else
+        e = launch_b_smooth<T>(Ls, act, inv, 1, false, s);
+      if (e != cudaSuccess) return e;
       if ((e = launch_b_smooth<T>(Ls, act, inv, 0, false, s)) != cudaSuccess) return e;
       *nk += 2;
     }

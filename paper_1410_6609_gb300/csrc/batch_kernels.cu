@@ -1,9 +1,11 @@
 // batch_kernels.cu -- multigrid operations over many independent systems in one launch.
 //
-// Each launch walks a table of entries (one system at one level, see BEntry). A block finds its
-// entry by binary search over the entries' block offsets, skips the whole block when its system
-// is inactive (converged or out of cycles), and runs the same per-thread body as the
-// single-system kernel (level_ops.cuh) at the decoded coordinates. The residual norm reproduces
+// Each launch walks a table of entries (one system at one level, see BEntry), each entry split
+// into virtual blocks (start[] holds their offsets). The launch is persistent: a CTA takes
+// virtual blocks blockIdx.x, blockIdx.x + gridDim.x, ..., finds the first one's entry by binary
+// search and then advances the entry index as it goes (the offsets ascend), skips a virtual block
+// whose system is inactive (converged or out of cycles), and runs the same per-thread body as
+// the single-system kernel (level_ops.cuh) at the decoded coordinates. The residual norm reproduces
 // the single-system block decomposition and reduction order per system, so every system's
 // iterates are bit-identical to a solve of that system alone.
 #include "level_ops.cuh"
@@ -36,62 +38,94 @@ __device__ __forceinline__ bool flat_coords(int lb, int gx, int per_row, int row
   return row < rows;
 }
 
+// Iteration over a launch's virtual blocks (see the file comment); `body` gets the entry and the
+// block's index within it. Every thread of a CTA sees the same sequence, so bodies may use
+// __syncthreads.
+template <typename F>
+__device__ __forceinline__ void for_vblocks(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
+                                            int total, const int* __restrict__ active, F body) {
+  if ((int)blockIdx.x >= total) return;
+  int e = find_entry(start, count, blockIdx.x);
+  for (int b = blockIdx.x; b < total; b += gridDim.x) {
+    while (__ldg(start + e + 1) <= b) ++e;
+    if (!active[E[e].sys]) continue;
+    body(E[e], e, b - __ldg(start + e));
+  }
+}
+
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
-                                                 const int* __restrict__ active, InvDiag<T> inv, int colour) {
+                                                 int total, const int* __restrict__ active, InvDiag<T> inv,
+                                                 int colour) {
   constexpr int V = 16 / sizeof(T);
-  const int e = find_entry(start, count, blockIdx.x);
-  const BEntry& en = E[e];
-  if (!active[en.sys]) return;
-  const int lb = blockIdx.x - start[e];
-  const Geom G = en.G;
-  T* x = (T*)en.x;
-  const T* g = (const T*)en.g;
-  if (en.vec) {
-    int mv, j, k;
-    if (flat_coords(lb, en.gx, G.hx / V, G.ny, mv, j, k)) smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
-  } else {
-    const int bxi = lb % en.gx, rest = lb / en.gx;
-    const int byi = rest % en.gy, k = rest / en.gy;
-    const int j = byi * blockDim.y + threadIdx.y;
-    const int m = bxi * blockDim.x + threadIdx.x;
-    if (m < G.hx && j < G.ny) smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
-  }
+  for_vblocks(E, start, count, total, active, [&](const BEntry& en, int, int lb) {
+    const Geom G = en.G;
+    T* x = (T*)en.x;
+    const T* g = (const T*)en.g;
+    if (en.vec) {
+      int mv, j, k;
+      if (flat_coords(lb, en.gx, G.hx / V, G.ny, mv, j, k)) smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
+    } else {
+      const int bxi = lb % en.gx, rest = lb / en.gx;
+      const int byi = rest % en.gy, k = rest / en.gy;
+      const int j = byi * blockDim.y + threadIdx.y;
+      const int m = bxi * blockDim.x + threadIdx.x;
+      if (m < G.hx && j < G.ny) smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
+    }
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_smooth_prolong(const BEntry* __restrict__ E, const int* __restrict__ start,
+                                                         int count, int total, const int* __restrict__ active,
+                                                         InvDiag<float> inv, float omega) {
+  for_vblocks(E, start, count, total, active, [&](const BEntry& en, int, int lb) {
+    const Geom G = en.G;
+    float* x = (float*)en.x;
+    const float* g = (const float*)en.g;
+    if (en.vec) {
+      int mv, j, k;
+      if (flat_coords(lb, en.gx, G.hx / 4, G.ny, mv, j, k))
+        smooth_vec_prolong<float, 4>(x, g, G, inv, (const float*)en.xc, en.Gc, omega, mv, j, k);
+    } else {
+      const int bxi = lb % en.gx, rest = lb / en.gx;
+      const int byi = rest % en.gy, k = rest / en.gy;
+      const int j = byi * blockDim.y + threadIdx.y;
+      const int m = bxi * blockDim.x + threadIdx.x;
+      if (m < G.hx && j < G.ny) smooth_cell<float, false>(x, g, G, inv, 1, m, j, k);
+    }
+  });
 }
 
 template <typename T, bool RED_ONLY>
 __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restrict__ E, const int* __restrict__ start,
-                                                         int count, const int* __restrict__ active) {
-  const int e = find_entry(start, count, blockIdx.x);
-  const BEntry& en = E[e];
-  if (!active[en.sys]) return;
-  const int lb = blockIdx.x - start[e];
-  const Geom G = en.G, Gc = en.Gc;
-  if (en.vec) {
-    constexpr int V = 16 / sizeof(T);
-    int iv, J, K;
-    if (flat_coords(lb, en.gx, Gc.nx / V, Gc.ny, iv, J, K))
-      resid_restrict_vec<T, V, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, iv, J, K);
-  } else {
-    const int bxi = lb % en.gx, rest = lb / en.gx;
-    const int byi = rest % en.gy, K = rest / en.gy;
-    const int I = bxi * blockDim.x + threadIdx.x;
-    const int J = byi * blockDim.y + threadIdx.y;
-    if (I < Gc.nx && J < Gc.ny) resid_restrict_cell<T, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
-  }
+                                                         int count, int total, const int* __restrict__ active) {
+  for_vblocks(E, start, count, total, active, [&](const BEntry& en, int, int lb) {
+    const Geom G = en.G, Gc = en.Gc;
+    if (en.vec) {
+      constexpr int V = 16 / sizeof(T);
+      int iv, J, K;
+      if (flat_coords(lb, en.gx, Gc.nx / V, Gc.ny, iv, J, K))
+        resid_restrict_vec<T, V, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, iv, J, K);
+    } else {
+      const int bxi = lb % en.gx, rest = lb / en.gx;
+      const int byi = rest % en.gy, K = rest / en.gy;
+      const int I = bxi * blockDim.x + threadIdx.x;
+      const int J = byi * blockDim.y + threadIdx.y;
+      if (I < Gc.nx && J < Gc.ny)
+        resid_restrict_cell<T, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+    }
+  });
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) kb_prolong(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
-                                                  const int* __restrict__ active, T omega, int red_only) {
-  const int e = find_entry(start, count, blockIdx.x);
-  const BEntry& en = E[e];
-  if (!active[en.sys]) return;
-  const int lb = blockIdx.x - start[e];
-  const Geom G = en.G, Gc = en.Gc;
-  int I, J, K;
-  if (flat_coords(lb, en.gx, Gc.nx, Gc.ny, I, J, K))
-    prolong_cell<T>((T*)en.x, G, (const T*)en.xc, Gc, omega, red_only, I, J, K);
+                                                  int total, const int* __restrict__ active, T omega, int red_only) {
+  for_vblocks(E, start, count, total, active, [&](const BEntry& en, int, int lb) {
+    const Geom G = en.G, Gc = en.Gc;
+    int I, J, K;
+    if (flat_coords(lb, en.gx, Gc.nx, Gc.ny, I, J, K))
+      prolong_cell<T>((T*)en.x, G, (const T*)en.xc, Gc, omega, red_only, I, J, K);
+  });
 }
 
 // One CTA per system: CG on the system's coarsest grid.
@@ -109,20 +143,18 @@ __global__ void __launch_bounds__(1024) kb_coarse_cg(const BEntry* __restrict__ 
 
 template <int MODE>
 __global__ void __launch_bounds__(256) kb_resid_norm(const BEntry* __restrict__ E, const int* __restrict__ start,
-                                                     int count, const int* __restrict__ active,
+                                                     int count, int total, const int* __restrict__ active,
                                                      const double* __restrict__ scal,
                                                      double* __restrict__ partials) {
   __shared__ double red[33];
-  const int e = find_entry(start, count, blockIdx.x);
-  const BEntry& en = E[e];
-  if (!active[en.sys]) return;
-  const int lb = blockIdx.x - start[e];
-  const int nb = start[e + 1] - start[e];
-  const double isc = (MODE == 2) ? scal[kScalStride * en.sys + kSlotInvScale] : 0.0;
-  double acc = resid_norm_accum<double, MODE>((const double*)en.x, (const double*)en.g, en.G, lb, nb, 0.0, nullptr,
-                                              (float*)en.aux, isc);
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = acc;
+  for_vblocks(E, start, count, total, active, [&](const BEntry& en, int e, int lb) {
+    const int nb = __ldg(start + e + 1) - __ldg(start + e);
+    const double isc = (MODE == 2) ? scal[kScalStride * en.sys + kSlotInvScale] : 0.0;
+    double acc = resid_norm_accum<double, MODE>((const double*)en.x, (const double*)en.g, en.G, lb, nb, 0.0, nullptr,
+                                                (float*)en.aux, isc);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[__ldg(start + e) + lb] = acc;
+  });
 }
 
 __global__ void __launch_bounds__(256) kb_finalize(const BEntry* __restrict__ E, const int* __restrict__ start,
@@ -145,23 +177,22 @@ __global__ void __launch_bounds__(256) kb_finalize(const BEntry* __restrict__ E,
 }
 
 __global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
-                                                 const int* __restrict__ active, const double* __restrict__ scal) {
-  const int e = find_entry(start, count, blockIdx.x);
-  const BEntry& en = E[e];
-  if (!active[en.sys]) return;
-  const long long lb = blockIdx.x - start[e];
-  const long long nb = start[e + 1] - start[e];
-  const Geom G = en.G;
-  const long long n = G.packed ? 2 * G.csz : G.csz;
-  double* x = (double*)en.x;
-  const float* ev = (const float*)en.aux;
-  const double sc = scal[kScalStride * en.sys + kSlotScale];
-  const int p = pow2_exponent(sc);
-  const long long i0 = lb * blockDim.x + threadIdx.x, st = nb * blockDim.x;
-  if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
-    for (long long i = i0; i < n; i += st) x[i] = x[i] + f64_of_scaled(ev[i], p);
-  else
-    for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)ev[i], x[i]);
+                                                 int total, const int* __restrict__ active,
+                                                 const double* __restrict__ scal) {
+  for_vblocks(E, start, count, total, active, [&](const BEntry& en, int e, int lb) {
+    const long long nb = __ldg(start + e + 1) - __ldg(start + e);
+    const Geom G = en.G;
+    const long long n = G.packed ? 2 * G.csz : G.csz;
+    double* x = (double*)en.x;
+    const float* ev = (const float*)en.aux;
+    const double sc = scal[kScalStride * en.sys + kSlotScale];
+    const int p = pow2_exponent(sc);
+    const long long i0 = (long long)lb * blockDim.x + threadIdx.x, st = nb * blockDim.x;
+    if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
+      for (long long i = i0; i < n; i += st) x[i] = x[i] + f64_of_scaled(ev[i], p);
+    else
+      for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)ev[i], x[i]);
+  });
 }
 
 __global__ void kb_set_scale(const BEntry* __restrict__ E, int count, const int* __restrict__ active,
@@ -178,6 +209,13 @@ __global__ void kb_set_scale(const BEntry* __restrict__ E, int count, const int*
   sc[kSlotInvScale] = 1.0 / s;
 }
 
+// Persistent grid: per_sm CTAs per SM (of kSMs), at most the launch's virtual blocks.
+constexpr int kSMs = 152;
+int persist(const BLaunch& L, int per_sm = 8) {
+  const long long g = (long long)kSMs * per_sm;
+  return (int)(L.blocks < g ? L.blocks : g);
+}
+
 }  // namespace
 
 template <typename T>
@@ -185,9 +223,16 @@ cudaError_t launch_b_smooth(const BLaunch& L, const int* active, const InvDiag<T
                             cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
   if (zero)
-    kb_smooth<T, true><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active, inv, colour);
+    kb_smooth<T, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
   else
-    kb_smooth<T, false><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active, inv, colour);
+    kb_smooth<T, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_smooth_prolong(const BLaunch& L, const int* active, const InvDiag<float>& inv, float omega,
+                                    cudaStream_t s) {
+  if (L.count == 0 || L.blocks == 0) return cudaSuccess;
+  kb_smooth_prolong<<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, omega);
   return cudaGetLastError();
 }
 
@@ -195,16 +240,17 @@ template <typename T>
 cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, bool red_only, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
   if (red_only)
-    kb_resid_restrict<T, true><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active);
+    kb_resid_restrict<T, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
   else
-    kb_resid_restrict<T, false><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active);
+    kb_resid_restrict<T, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_b_prolong(const BLaunch& L, const int* active, T omega, bool red_only, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  kb_prolong<T><<<L.blocks, L.block, 0, s>>>(L.entries, L.start, L.count, active, omega, red_only ? 1 : 0);
+  kb_prolong<T><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, omega,
+                                                red_only ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -227,9 +273,9 @@ cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* 
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
   const dim3 b(kResBX, kResBY, 1);
   if (mode == 2)
-    kb_resid_norm<2><<<L.blocks, b, 0, s>>>(L.entries, L.start, L.count, active, scal, partials);
+    kb_resid_norm<2><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, scal, partials);
   else
-    kb_resid_norm<0><<<L.blocks, b, 0, s>>>(L.entries, L.start, L.count, active, scal, partials);
+    kb_resid_norm<0><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, scal, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   kb_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, zero, partials, scal);
@@ -238,7 +284,7 @@ cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* 
 
 cudaError_t launch_b_update(const BLaunch& L, const int* active, const double* scal, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  kb_update<<<L.blocks, 256, 0, s>>>(L.entries, L.start, L.count, active, scal);
+  kb_update<<<persist(L), 256, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, scal);
   return cudaGetLastError();
 }
 

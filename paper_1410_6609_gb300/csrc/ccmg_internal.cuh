@@ -192,6 +192,10 @@ template <typename T>
 cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, bool red_only, cudaStream_t s);
 template <typename T>
 cudaError_t launch_b_prolong(const BLaunch& L, const int* active, T omega, bool red_only, cudaStream_t s);
+// First black post-sweep (single precision): fused with the prolongation for vector entries (as
+// launch_smooth_prolong), a plain black sweep for the others (prolonged before).
+cudaError_t launch_b_smooth_prolong(const BLaunch& L, const int* active, const InvDiag<float>& inv, float omega,
+                                    cudaStream_t s);
 template <typename T>
 cudaError_t launch_b_coarse_cg(const BLaunch& L, const int* active, size_t smem, double rtol, cudaStream_t s);
 cudaError_t prepare_b_coarse_cg();
