@@ -71,6 +71,13 @@ struct mg_batch {
   int* h_active = nullptr;
   int* d_zero = nullptr;  // per system: iterate known to be exactly zero
   int* h_zero = nullptr;
+  std::vector<char> lazy;  // per system (mixed): finest iterate zero but never written
+  // pinned staging slots for flag uploads: a slot is rewritten only after the copy that read it
+  // last has run (its event), so a later host-side change never leaks into an earlier upload
+  static constexpr int kFlagSlots = 16;
+  int* h_flag_ring = nullptr;
+  cudaEvent_t flag_ev[kFlagSlots]{};
+  int flag_slot = 0;
   double* d_scal = nullptr;
   double* h_scal = nullptr;
   double* d_partials = nullptr;
@@ -314,7 +321,7 @@ cudaError_t enqueue_bcycle(mg_batch* b, cudaStream_t s, long long* nk) {
   cudaError_t e;
   for (int it = 0; it < b->inner; ++it)
     if ((e = enqueue_bvcycle<float>(b, b->inv32, it == 0, s, nk)) != cudaSuccess) return e;
-  if ((e = launch_b_update(bl(b, b->update), b->d_active, b->d_scal, s)) != cudaSuccess) return e;
+  if ((e = launch_b_update(bl(b, b->update), b->d_active, b->d_zero, b->d_scal, s)) != cudaSuccess) return e;
   if ((e = launch_b_set_scale(bl(b, b->resid), b->d_active, b->d_scal, s)) != cudaSuccess) return e;
   *nk += 2;
   return cudaSuccess;
@@ -364,26 +371,45 @@ mg_status brun(mg_batch* b, cudaGraphExec_t g, long long nodes, const char* what
   return MG_OK;
 }
 
+mg_status upload_flags(mg_batch* b, int* d_dst, const int* h_src) {
+  const int k = b->flag_slot;
+  b->flag_slot = (k + 1) % mg_batch::kFlagSlots;
+  int* slot = b->h_flag_ring + (size_t)k * b->B;
+  BCK(cudaEventSynchronize(b->flag_ev[k]), "flag upload");
+  std::memcpy(slot, h_src, (size_t)b->B * sizeof(int));
+  BCK(cudaMemcpyAsync(d_dst, slot, (size_t)b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "flag upload");
+  BCK(cudaEventRecord(b->flag_ev[k], b->stream), "flag upload");
+  return MG_OK;
+}
+
 mg_status set_all_active(mg_batch* b, int v) {
   for (int s = 0; s < b->B; ++s) b->h_active[s] = v;
-  BCK(cudaMemcpyAsync(b->d_active, b->h_active, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "active");
+  if (mg_status st = upload_flags(b, b->d_active, b->h_active); st != MG_OK) return st;
   return MG_OK;
 }
 
-mg_status upload_zero(mg_batch* b) {
-  BCK(cudaMemcpyAsync(b->d_zero, b->h_zero, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "zero flags");
-  return MG_OK;
-}
+mg_status upload_zero(mg_batch* b) { return upload_flags(b, b->d_zero, b->h_zero); }
 
-// After a cycle graph ran: the iterates of the systems that took part are no longer zero.
+// After a cycle graph ran: the iterates of the systems that took part are no longer zero (and a
+// never-written one has been stored by the update).
 mg_status clear_zero_of_active(mg_batch* b) {
   bool changed = false;
   for (int s = 0; s < b->B; ++s)
     if (b->h_active[s] && b->h_zero[s]) {
       b->h_zero[s] = 0;
+      b->lazy[s] = 0;
       changed = true;
     }
   return changed ? upload_zero(b) : MG_OK;
+}
+
+// Write the zeros of a finest iterate that set_solution(NULL) left unwritten.
+mg_status materialize(mg_batch* b, int s) {
+  if (!b->lazy[s]) return MG_OK;
+  BCK(cudaMemsetAsync(b->sys[s].x64[0], 0, sizeof(double) * (size_t)cells(b->sys[s].geo[0]), b->stream),
+      "zero iterate");
+  b->lazy[s] = 0;
+  return MG_OK;
 }
 
 void free_batch(mg_batch* b) {
@@ -397,6 +423,9 @@ void free_batch(mg_batch* b) {
   cudaFree(b->d_partials);
   if (b->h_active) cudaFreeHost(b->h_active);
   if (b->h_zero) cudaFreeHost(b->h_zero);
+  if (b->h_flag_ring) cudaFreeHost(b->h_flag_ring);
+  for (int k = 0; k < mg_batch::kFlagSlots; ++k)
+    if (b->flag_ev[k]) cudaEventDestroy(b->flag_ev[k]);
   if (b->h_scal) cudaFreeHost(b->h_scal);
   if (b->cap) cudaStreamDestroy(b->cap);
 }
@@ -518,6 +547,10 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_zero, B * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_scal, (size_t)B * kScalStride * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_active, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_flag_ring, (size_t)mg_batch::kFlagSlots * B * sizeof(int));
+  for (int k = 0; k < mg_batch::kFlagSlots && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&b->flag_ev[k], cudaEventDisableTiming);
+  b->lazy.assign(B, 0);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_scal, (size_t)B * kScalStride * sizeof(double));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_b_coarse_cg();
@@ -588,9 +621,14 @@ mg_status mg_batch_set_rhs(mg_batch* b, int s, const double* d_rho) {
 mg_status mg_batch_set_solution(mg_batch* b, int s, const double* d_phi) {
   mg_status st = check_sys(b, s);
   if (st != MG_OK) return st;
+  b->h_zero[s] = (d_phi == nullptr) ? 1 : 0;
+  if (bmixed(b) && !d_phi) {  // nothing is written: the first cycle's update stores phi = s e
+    b->lazy[s] = 1;
+    return upload_zero(b);
+  }
   BCK(launch_pack<double>(b->sys[s].x64[0], b->sys[s].geo[0], d_phi, 1.0, b->stream), "batch set_solution");
   b->launches += 1;
-  b->h_zero[s] = (d_phi == nullptr) ? 1 : 0;
+  b->lazy[s] = 0;
   return upload_zero(b);
 }
 
@@ -598,6 +636,7 @@ mg_status mg_batch_get_solution(mg_batch* b, int s, double* d_phi) {
   mg_status st = check_sys(b, s);
   if (st != MG_OK) return st;
   if (!d_phi) return bfail(b, MG_ERR_INVALID, "null output");
+  if ((st = materialize(b, s)) != MG_OK) return st;
   BCK(launch_unpack<double>(d_phi, b->sys[s].x64[0], b->sys[s].geo[0], 1.0, b->stream), "batch get_solution");
   b->launches += 1;
   return MG_OK;
@@ -645,7 +684,7 @@ mg_status mg_batch_solve(mg_batch* b, double tol, int max_cycles, int* h_cycles,
       }
     }
     if (!any) break;
-    BCK(cudaMemcpyAsync(b->d_active, b->h_active, b->B * sizeof(int), cudaMemcpyHostToDevice, b->stream), "active");
+    if ((st = upload_flags(b, b->d_active, b->h_active)) != MG_OK) return st;
     if ((st = brun(b, b->g_cycle, b->n_cycle, "batch cycle")) != MG_OK) return st;
     if ((st = clear_zero_of_active(b)) != MG_OK) return st;
     for (int s = 0; s < b->B; ++s) cyc[s] += b->h_active[s];
@@ -714,7 +753,10 @@ mg_status mg_batch_autotune(mg_batch* b, int reps, int* h_best4, double* h_ms, i
   if (h_best4)
     for (int q = 0; q < 4; ++q) h_best4[q] = kCandidates[bi][q];
   // the timed cycles may have changed the iterates: no longer known to be zero
-  for (int s = 0; s < b->B; ++s) b->h_zero[s] = 0;
+  for (int s = 0; s < b->B; ++s) {
+    b->h_zero[s] = 0;
+    b->lazy[s] = 0;
+  }
   if ((st = upload_zero(b)) != MG_OK) return st;
   return mg_batch_set_tiles(b, kCandidates[bi]);
 }

@@ -144,12 +144,17 @@ __global__ void __launch_bounds__(1024) kb_coarse_cg(const BEntry* __restrict__ 
 template <int MODE>
 __global__ void __launch_bounds__(256) kb_resid_norm(const BEntry* __restrict__ E, const int* __restrict__ start,
                                                      int count, int total, const int* __restrict__ active,
-                                                     const double* __restrict__ scal,
+                                                     const int* __restrict__ zero, const double* __restrict__ scal,
                                                      double* __restrict__ partials) {
   __shared__ double red[33];
   for_vblocks(E, start, count, total, active, [&](const BEntry& en, int e, int lb) {
     const int nb = __ldg(start + e + 1) - __ldg(start + e);
     const double isc = (MODE == 2) ? scal[kScalStride * en.sys + kSlotInvScale] : 0.0;
+    if (zero[en.sys]) {  // a zero iterate: r = f, no stencil (kb_finalize takes the norm of f)
+      if (MODE == 2) resid_zero_rows((const double*)en.g, en.G, lb, nb, (float*)en.aux, isc);
+      if (threadIdx.x == 0 && threadIdx.y == 0) partials[__ldg(start + e) + lb] = 0.0;
+      return;
+    }
     double acc = resid_norm_accum<double, MODE>((const double*)en.x, (const double*)en.g, en.G, lb, nb, 0.0, nullptr,
                                                 (float*)en.aux, isc);
     acc = block_sum(acc, red);
@@ -176,9 +181,11 @@ __global__ void __launch_bounds__(256) kb_finalize(const BEntry* __restrict__ E,
   }
 }
 
+// phi += s e; for a system whose iterate is zero (possibly never written) phi = fma(s, e, +0),
+// without reading phi (as k_set_mixed).
 __global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
                                                  int total, const int* __restrict__ active,
-                                                 const double* __restrict__ scal) {
+                                                 const int* __restrict__ zero, const double* __restrict__ scal) {
   for_vblocks(E, start, count, total, active, [&](const BEntry& en, int e, int lb) {
     const long long nb = __ldg(start + e + 1) - __ldg(start + e);
     const Geom G = en.G;
@@ -188,10 +195,20 @@ __global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, c
     const double sc = scal[kScalStride * en.sys + kSlotScale];
     const int p = pow2_exponent(sc);
     const long long i0 = (long long)lb * blockDim.x + threadIdx.x, st = nb * blockDim.x;
-    if (p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit)
+    const bool pow2 = p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit;
+    if (zero[en.sys]) {
+      if (pow2)
+        for (long long i = i0; i < n; i += st) {
+          const double v = f64_of_scaled(ev[i], p);
+          x[i] = (__double_as_longlong(v) == (long long)0x8000000000000000ULL) ? 0.0 : v;
+        }
+      else
+        for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)ev[i], 0.0);
+    } else if (pow2) {
       for (long long i = i0; i < n; i += st) x[i] = x[i] + f64_of_scaled(ev[i], p);
-    else
+    } else {
       for (long long i = i0; i < n; i += st) x[i] = fma(sc, (double)ev[i], x[i]);
+    }
   });
 }
 
@@ -273,18 +290,20 @@ cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* 
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
   const dim3 b(kResBX, kResBY, 1);
   if (mode == 2)
-    kb_resid_norm<2><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, scal, partials);
+    kb_resid_norm<2><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal,
+                                                  partials);
   else
-    kb_resid_norm<0><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, scal, partials);
+    kb_resid_norm<0><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal,
+                                                  partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   kb_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, zero, partials, scal);
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_update(const BLaunch& L, const int* active, const double* scal, cudaStream_t s) {
+cudaError_t launch_b_update(const BLaunch& L, const int* active, const int* zero, const double* scal, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  kb_update<<<persist(L), 256, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, scal);
+  kb_update<<<persist(L), 256, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal);
   return cudaGetLastError();
 }
 

@@ -208,7 +208,7 @@ constexpr int kSlotGsum = 0, kSlotRsum = 1, kSlotRel = 2, kSlotScale = 3, kSlotI
 cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* zero, int mode, double* scal,
                                 double* partials, cudaStream_t s);
 // x64 += scale * double(e32) on every active system's finest level (update entries).
-cudaError_t launch_b_update(const BLaunch& L, const int* active, const double* scal, cudaStream_t s);
+cudaError_t launch_b_update(const BLaunch& L, const int* active, const int* zero, const double* scal, cudaStream_t s);
 // scale = sqrt(rsum / n) (1 if not positive and finite), inv_scale = 1 / scale, per system.
 cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, double* scal, cudaStream_t s);
 

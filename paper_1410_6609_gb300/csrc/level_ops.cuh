@@ -863,6 +863,31 @@ __device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, cons
   return resid_norm_accum_impl<T, MODE, false>(x, g, G, lb, nb, c0, outn, outp, isc, kBadPow2);
 }
 
+// The single-precision residual copy of a zero iterate (r~ = g exactly) over the same rows of
+// block lb of nb as resid_norm_accum: float(g isc), without evaluating the stencil.
+__device__ __forceinline__ void resid_zero_rows(const double* __restrict__ g, const Geom& G, long long lb, long long nb,
+                                                float* __restrict__ outp, double isc) {
+  const int p2 = pow2_exponent(isc);
+  if (G.packed) {
+    const long long rows = 2LL * G.nz * G.ny;
+    for (long long rw = lb * kResBY + threadIdx.y; rw < rows; rw += nb * kResBY) {
+      const int k = (int)(rw / (2LL * G.ny));
+      const int rem = (int)(rw - 2LL * G.ny * k);
+      const int j = rem >> 1, c = rem & 1;
+      const long long base = (long long)c * G.csz + ((long long)k * G.ny + j) * G.hx;
+      for (int m = threadIdx.x; m < G.hx; m += kResBX) {
+        const double v = g[base + m];
+        outp[base + m] = (p2 != kBadPow2) ? f32_of_scaled(v, p2) : (float)(v * isc);
+      }
+    }
+  } else {
+    const long long n = (long long)G.nx * G.ny * G.nz;
+    const int tid = threadIdx.y * kResBX + threadIdx.x;
+    for (long long i = lb * (kResBX * kResBY) + tid; i < n; i += nb * (kResBX * kResBY))
+      outp[i] = (p2 != kBadPow2) ? f32_of_scaled(g[i], p2) : (float)(g[i] * isc);
+  }
+}
+
 // Number of blocks of the residual-norm launch for level G (= the number of partial sums).
 __host__ __device__ __forceinline__ int resid_norm_blocks(const Geom& G) {
   if (!G.packed) return 1;

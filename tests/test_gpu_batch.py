@@ -111,3 +111,27 @@ def test_batched_workload_64_systems():
         f = oracle.rhs(rho[b].cpu().numpy(), w.h, w.bc_type, w.bc_value)
         assert oracle.rel_residual(Bt.solution(b).cpu().numpy(), f, w.h, w.bc_type) < 1.0001e-9
     Bt.close()
+
+
+def test_zero_start_without_writing_and_flag_uploads_in_order():
+    """set_solution(None) in a mixed batch writes nothing (the first cycle's update stores phi = s e):
+    reading a system before any cycle gives zeros, and cycles issued right after the resets (no
+    synchronisation between host flag changes and the queued work) match single contexts bit
+    for bit, also after a first solve has left non-zero iterates behind."""
+    rho = rhos()
+    Bt = BatchPoisson(SYSTEMS, precision="mixed")
+    for b, r in enumerate(rho):
+        Bt.set_rhs(b, r)
+    Bt.solve(1e-9, 50)
+    Bt.reset_solutions()
+    assert not torch.any(Bt.solution(2) != 0)
+    Bt.reset_solutions()
+    Bt.vcycle(2)
+    for b, s in enumerate(SYSTEMS):
+        P = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision="mixed")
+        P.set_rhs(rho[b])
+        P.set_solution(None)
+        P.vcycle(2)
+        assert torch.equal(P.solution(), Bt.solution(b)), b
+        P.close()
+    Bt.close()
