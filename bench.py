@@ -384,9 +384,11 @@ FP64_OPS_PEAK = 0.625  # Tops/s
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of that kernel on the
 # same workload (profiles/); None where no capture of the current kernel exists.
 MEASURED_TRAFFIC = {
-    # profiles/dram_traffic_spheres512_mixed.md: finest-level FP32 half-sweep of the direct-load
-    # kernel, 536.90 MB read + 238.74 MB written (kept for runs with CCMG_SWEEP=vec)
-    ("spheres512", "k_smooth_vec<float,4,0>"): 775_640_000,
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one finest-level FP32 half-sweep of the
+    # 512^3 mixed step (TMA kernel as of commit db4ad4e): 545.2 MB read + 234.7 MB written, mean
+    # of the 12 captured launches; the algorithmic figure is 805.3 MB (the rest of the writes are
+    # still in L2 when the launch ends)
+    ("spheres512", "k_smooth_tma"): 779_880_000,
 }
 
 
