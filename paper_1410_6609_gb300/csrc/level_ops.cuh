@@ -586,16 +586,126 @@ __device__ __forceinline__ void prolong_cell(T* __restrict__ x, const Geom& G, c
       }
 }
 
-// Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x.
+// ---------------------------------------------------------------------------------------------
+// The FP64 scaled residual r~ = g + (x_-x + x_+x + x_-y + x_+y + x_-z + x_+z) - D x_c of one cell
+// (D = 6 + d), evaluated in 64-bit fixed point. Every operand's 53-bit significand is aligned to
+// the largest biased exponent E among the eight operands, with its leading bit 2^5 below the top
+// of a 63-bit magnitude (so the signed sum of at most 16 such magnitudes cannot overflow), and the
+// integer sum is rounded once to the nearest double. The units of the sum are 2^(E-1080): an
+// operand below the largest loses only bits under that unit (the centre's loss is scaled by D),
+// so the result lies within 16 units and half an ulp of the exact residual, closer than the seven
+// rounded FP64 operations of the direct formula.
+// All of it is integer work: on GB300 the FP64 pipe, which the direct formula occupies, runs at
+// 1/64 of the FP32 rate. Zero operands (biased exponent 0) are shifted out of the sum, which
+// needs E >= 64; cells whose operands all lie below 2^-959, or reach 2^1017, infinities and NaN
+// take the direct formula, as do those the caller routes there.
+constexpr int kFxMinExp = 64, kFxMaxExp = 2040;
+
+__host__ __device__ __forceinline__ int fx_clz64(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+
+// Biased exponent field of the double with high word hi.
+__host__ __device__ __forceinline__ int fx_exp(unsigned hi) { return (int)((hi >> 20) & 0x7ffu); }
+
+// The operand with words (hi, lo) and biased exponent e, aligned to exponent E, in two's
+// complement (mod 2^64), negated when `flip` is set.
+__host__ __device__ __forceinline__ unsigned long long fx_term(unsigned hi, unsigned lo, int e, int E, bool flip) {
+  const unsigned long long sig = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 37) | ((unsigned long long)lo << 5);
+  int d = E - e;
+  d = d < 63 ? d : 63;  // sig < 2^58: a shift by 63 leaves 0
+  const unsigned long long mag = sig >> d;
+  const unsigned long long neg = (unsigned long long)(-(long long)(((hi >> 31) ^ (flip ? 1u : 0u)) & 1u));
+  return (mag ^ neg) - neg;
+}
+
+// The signed fixed-point sum S (units 2^(E-1080)) rounded to the nearest double, ties to even.
+// Requires kFxMinExp <= E <= kFxMaxExp and |S| < 2^62.
+__host__ __device__ __forceinline__ double fx_to_double(unsigned long long S, int E) {
+  const unsigned long long sgn = S & 0x8000000000000000ULL;
+  const unsigned long long A = sgn ? (0ULL - S) : S;
+  if (A == 0ULL) return 0.0;
+  const int lz = fx_clz64(A);
+  const unsigned long long N = A << lz;  // leading one at bit 63
+  const unsigned long long m53 = N >> 11;
+  const unsigned rem = (unsigned)(N & 0x7ffULL);
+  const unsigned long long up = (rem > 0x400u || (rem == 0x400u && (m53 & 1ULL))) ? 1ULL : 0ULL;
+  // value = N 2^(E-1080-lz) = (N / 2^63) 2^(E-1017-lz): biased exponent E + 6 - lz (>= 7 here);
+  // the implicit bit of m53 adds the 1 back and a rounding carry moves on into the exponent
+  const unsigned long long bits = ((unsigned long long)(E + 6 - lz - 1) << 52) + m53 + up;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)(sgn | bits));
+#else
+  double r;
+  const unsigned long long b = sgn | bits;
+  memcpy(&r, &b, sizeof(r));
+  return r;
+#endif
+}
+
+// r~ of one cell from its eight operands; absent neighbours are passed as 0.
+__host__ __device__ __forceinline__ double resid_fx(double gv, double xc, int D, double xm, double xp, double ym,
+                                                   double yp, double zm, double zp) {
+  const double v[7] = {gv, xm, xp, ym, yp, zm, zp};
+  unsigned hi[8], lo[8];
+  int e[8];
+  int E = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    unsigned long long u;
+    const double vi = i < 7 ? v[i] : xc;
+#ifdef __CUDA_ARCH__
+    u = (unsigned long long)__double_as_longlong(vi);
+#else
+    memcpy(&u, &vi, sizeof(u));
+#endif
+    hi[i] = (unsigned)(u >> 32);
+    lo[i] = (unsigned)u;
+    e[i] = fx_exp(hi[i]);
+    E = e[i] > E ? e[i] : E;
+  }
+  if (E < kFxMinExp || E > kFxMaxExp) {
+    const double S = ((((xm + xp) + ym) + yp) + zm) + zp;
+#ifdef __CUDA_ARCH__
+    return __fma_rn(-(double)D, xc, gv + S);
+#else
+    return fma(-(double)D, xc, gv + S);
+#endif
+  }
+  unsigned long long acc = 0ULL;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) acc += fx_term(hi[i], lo[i], e[i], E, false);
+  acc += fx_term(hi[7], lo[7], e[7], E, true) * (unsigned long long)D;
+  return fx_to_double(acc, E);
+}
+
+// Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x. The FP64
+// residual is summed in fixed point (resid_fx); single precision keeps the direct formula.
 template <typename T>
 __device__ __forceinline__ T resid_packed(const T* __restrict__ x, const T* __restrict__ g, const Geom& G, int c,
                                           int m, int j, int k) {
   const int s = (j + k + c) & 1;
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)c * G.csz + row + m;
-  const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
   const int d = diag_shift_packed(G, m, s, j, k);
-  return fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
+  if constexpr (sizeof(T) == 8) {
+    const long long plane = (long long)G.ny * G.hx;
+    const T* yr = x + (long long)(1 - c) * G.csz + row;
+    const double xm = (m == 0 && s == 0) ? 0.0 : __ldg(yr + m + s - 1);
+    const double xp = (m == G.hx - 1 && s == 1) ? 0.0 : __ldg(yr + m + s);
+    const double ym = (j > 0) ? __ldg(yr + m - G.hx) : 0.0;
+    const double yp = (j < G.ny - 1) ? __ldg(yr + m + G.hx) : 0.0;
+    const double zm = (k > 0) ? __ldg(yr + m - plane) : 0.0;
+    const double zp = (k < G.nz - 1) ? __ldg(yr + m + plane) : 0.0;
+    return resid_fx(__ldg(g + own), __ldg(x + own), 6 + d, xm, xp, ym, yp, zm, zp);
+  } else {
+    const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
+    return fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -828,20 +938,25 @@ __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x,
     for (long long i = lb * (kResBX * kResBY) + tid; i < n; i += nb * (kResBX * kResBY)) {
       const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
       int d = 0;
-      T S = T(0);
-      S = S + (ix > 0 ? x[i - 1] : T(0));
-      S = S + (ix < nx - 1 ? x[i + 1] : T(0));
-      S = S + (iy > 0 ? x[i - nx] : T(0));
-      S = S + (iy < ny - 1 ? x[i + nx] : T(0));
-      S = S + (iz > 0 ? x[i - (long long)nx * ny] : T(0));
-      S = S + (iz < nz - 1 ? x[i + (long long)nx * ny] : T(0));
+      const T xm = ix > 0 ? x[i - 1] : T(0);
+      const T xp = ix < nx - 1 ? x[i + 1] : T(0);
+      const T ym = iy > 0 ? x[i - nx] : T(0);
+      const T yp = iy < ny - 1 ? x[i + nx] : T(0);
+      const T zm = iz > 0 ? x[i - (long long)nx * ny] : T(0);
+      const T zp = iz < nz - 1 ? x[i + (long long)nx * ny] : T(0);
       if (ix == 0) d += G.sh[0];
       if (ix == nx - 1) d += G.sh[1];
       if (iy == 0) d += G.sh[2];
       if (iy == ny - 1) d += G.sh[3];
       if (iz == 0) d += G.sh[4];
       if (iz == nz - 1) d += G.sh[5];
-      const double rd = (double)fmat(neg_diag<T>(d), x[i], g[i] + S);
+      double rd;
+      if constexpr (sizeof(T) == 8) {
+        rd = resid_fx(g[i], x[i], 6 + d, xm, xp, ym, yp, zm, zp);
+      } else {
+        const T S = ((((xm + xp) + ym) + yp) + zm) + zp;
+        rd = (double)fmat(neg_diag<T>(d), x[i], g[i] + S);
+      }
       acc = fma(rd, rd, acc);
       if (MODE == 1) outn[i] = rd * c0;
       if (MODE == 2) outp[i] = POW2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);

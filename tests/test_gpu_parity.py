@@ -368,3 +368,47 @@ def test_zero_start_without_writing_the_iterate():
     assert ra0 == rb0 and abs(ra0 - 1.0) < 1e-12
     assert ka == kb and rela == relb and rela < 1e-9
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("dims,bc", [((24, 20, 18), (D, N, N, D, D, N)), ((4, 6, 4), (N, D, D, N, N, D))])
+def test_fp64_residual_against_exact_arithmetic(dims, bc):
+    """The FP64 residual r = g + (sum of the six neighbours) - (6 + d) phi of every cell (h = 1, so
+    the scaled and the plain residual coincide) lies within half an ulp of its largest operand
+    plus half an ulp of itself from the exact rational value: operands spread over 2^-40 .. 2^40
+    with zeros among them, and on half the cells a right-hand side that cancels the stencil to its
+    rounding error. A multi-level (checkerboard-packed) grid and a single-level (natural order) one."""
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    phi = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
+    phi[rng.random(shape) < 0.1] = 0.0
+    sh = {D: 1, N: -1}
+    diag = np.full(shape, 6, dtype=np.int64)
+    diag[:, :, 0] += sh[bc[0]]
+    diag[:, :, -1] += sh[bc[1]]
+    diag[:, 0, :] += sh[bc[2]]
+    diag[:, -1, :] += sh[bc[3]]
+    diag[0] += sh[bc[4]]
+    diag[-1] += sh[bc[5]]
+    p = np.pad(phi, 1)
+    nbs = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
+           p[2:, 1:-1, 1:-1]]
+    g = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
+    g[rng.random(shape) < 0.05] = 0.0
+    cancel = rng.random(shape) < 0.5
+    g[cancel] = (diag * phi - sum(nbs))[cancel]
+    P = Poisson(dims, h=1.0, bc_type=bc)
+    P.level_set(0, 0, gpu(phi))
+    P.level_set(0, 1, gpu(g))
+    _, r = P.residual(field=True)
+    r = cpu(r)
+    P.close()
+    worst = 0.0
+    for idx in np.ndindex(*shape):
+        ops = [g[idx], phi[idx]] + [float(n[idx]) for n in nbs]
+        exact = Fraction(g[idx]) + sum(Fraction(float(n[idx])) for n in nbs) - int(diag[idx]) * Fraction(phi[idx])
+        bound = Fraction(np.spacing(max(abs(v) for v in ops))) / 2 + Fraction(np.spacing(abs(r[idx]))) / 2
+        err = abs(Fraction(float(r[idx])) - exact)
+        worst = max(worst, float(err / bound))
+    assert worst <= 1.0, worst
