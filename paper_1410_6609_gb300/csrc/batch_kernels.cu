@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(1024) kb_coarse_cg(const BEntry* __restrict__ 
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) kb_resid_norm(const BEntry* __restrict__ E, const int* __restrict__ start,
+__global__ void __launch_bounds__(256, 3) kb_resid_norm(const BEntry* __restrict__ E, const int* __restrict__ start,
                                                      int count, int total, const int* __restrict__ active,
                                                      const int* __restrict__ zero, const double* __restrict__ scal,
                                                      double* __restrict__ partials) {

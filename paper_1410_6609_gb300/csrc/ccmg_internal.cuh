@@ -26,10 +26,6 @@ namespace ccmg {
 
 constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarseCells = 4096;
-// Residual-norm blocks of one system (152 SMs x 12 blocks of 64x4 threads). The FP64 residual is
-// bound by the FP64 pipe, not by DRAM: three waves of 4 co-resident blocks per SM balance the
-// SMs better than one wave, although the later waves re-read some neighbour rows.
-constexpr int kMaxPartialsPerSystem = 1824;
 
 struct Geom {
   int nx, ny, nz;  // cells per axis

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(T* __restrict__ xo, const T*
 // row walk and the reduction are in level_ops.cuh (resid_norm_accum), so a batched launch over
 // many systems reproduces each system's partial sums exactly.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_resid_norm(const T* __restrict__ x, const T* __restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 3) k_resid_norm(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                     double* __restrict__ partials, double c0,
                                                     double* __restrict__ outn, float* __restrict__ outp,
                                                     const double* __restrict__ inv_scale) {

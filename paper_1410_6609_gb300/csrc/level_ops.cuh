@@ -588,103 +588,145 @@ __device__ __forceinline__ void prolong_cell(T* __restrict__ x, const Geom& G, c
 
 // ---------------------------------------------------------------------------------------------
 // The FP64 scaled residual r~ = g + (x_-x + x_+x + x_-y + x_+y + x_-z + x_+z) - D x_c of one cell
-// (D = 6 + d), evaluated in 64-bit fixed point. Every operand's 53-bit significand is aligned to
-// the largest biased exponent E among the eight operands, with its leading bit 2^5 below the top
-// of a 63-bit magnitude (so the signed sum of at most 16 such magnitudes cannot overflow), and the
-// integer sum is rounded once to the nearest double. The units of the sum are 2^(E-1080): an
-// operand below the largest loses only bits under that unit (the centre's loss is scaled by D),
-// so the result lies within 16 units and half an ulp of the exact residual, closer than the seven
-// rounded FP64 operations of the direct formula.
-// All of it is integer work: on GB300 the FP64 pipe, which the direct formula occupies, runs at
-// 1/64 of the FP32 rate. Zero operands (biased exponent 0) are shifted out of the sum, which
-// needs E >= 64; cells whose operands all lie below 2^-959, or reach 2^1017, infinities and NaN
-// take the direct formula, as do those the caller routes there.
-constexpr int kFxMinExp = 64, kFxMaxExp = 2040;
+// (D = 6 + d), evaluated in 64-bit fixed point. Each operand is first put in a form that does not
+// depend on the cell (FxOp: its 53-bit significand times 2^5 with its sign applied, and its biased
+// exponent), so the tiled kernel below converts every value once and reuses it for the seven
+// cells it enters. A cell then aligns its operands to the largest biased exponent E among them,
+// rounding each down to the unit 2^(E-1080) (an arithmetic shift), adds them as integers (the
+// magnitudes stay below 2^58 each, so the sum of at most 16 of them fits), and rounds the sum
+// once to the nearest double. Each operand loses less than one unit (the centre's loss is scaled
+// by D), so the result lies within 16 units, i.e. half an ulp of the largest operand, plus half
+// an ulp of itself, of the exact residual: closer than the seven rounded FP64 operations of the
+// direct formula. All of it is integer work: on GB300 the FP64 pipe, which the direct formula
+// occupies, runs at 1/64 of the FP32 rate. Subnormal operands count as zero (they lie below one
+// unit unless every operand is that small); a cell with an infinite or NaN operand takes the
+// direct formula.
+struct FxOp {
+  unsigned lo, hi;  // two's complement of +-significand * 2^5 (0 for zero and subnormal operands)
+  unsigned pk;      // biased exponent e in bits 0..15, and (e ? 2047 - e : 0) in bits 16..31
+};
 
-__host__ __device__ __forceinline__ int fx_clz64(unsigned long long v) {
+__host__ __device__ __forceinline__ unsigned long long fx_bits(double v) {
 #ifdef __CUDA_ARCH__
-  return __clzll((long long)v);
+  return (unsigned long long)__double_as_longlong(v);
 #else
-  return __builtin_clzll(v);
+  unsigned long long u;
+  memcpy(&u, &v, sizeof(u));
+  return u;
 #endif
 }
 
-// Biased exponent field of the double with high word hi.
-__host__ __device__ __forceinline__ int fx_exp(unsigned hi) { return (int)((hi >> 20) & 0x7ffu); }
-
-// The operand with words (hi, lo) and biased exponent e, aligned to exponent E, in two's
-// complement (mod 2^64), negated when `flip` is set.
-__host__ __device__ __forceinline__ unsigned long long fx_term(unsigned hi, unsigned lo, int e, int E, bool flip) {
-  const unsigned long long sig = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 37) | ((unsigned long long)lo << 5);
-  int d = E - e;
-  d = d < 63 ? d : 63;  // sig < 2^58: a shift by 63 leaves 0
-  const unsigned long long mag = sig >> d;
-  const unsigned long long neg = (unsigned long long)(-(long long)(((hi >> 31) ^ (flip ? 1u : 0u)) & 1u));
-  return (mag ^ neg) - neg;
+__host__ __device__ __forceinline__ double fx_double(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  memcpy(&v, &u, sizeof(v));
+  return v;
+#endif
 }
 
-// The signed fixed-point sum S (units 2^(E-1080)) rounded to the nearest double, ties to even.
-// Requires kFxMinExp <= E <= kFxMaxExp and |S| < 2^62.
+__host__ __device__ __forceinline__ FxOp fx_op(double v) {
+  const unsigned long long u = fx_bits(v);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned keep = e ? 0xffffffffu : 0u;
+  const unsigned mh = (hi & 0xfffffu) | 0x100000u;
+  const unsigned long long mag = ((unsigned long long)(((mh << 5) | (lo >> 27)) & keep) << 32) | ((lo << 5) & keep);
+  const unsigned long long neg = (unsigned long long)(long long)((int)hi >> 31);
+  const unsigned long long S = (mag ^ neg) - neg;
+  FxOp o;
+  o.lo = (unsigned)S;
+  o.hi = (unsigned)(S >> 32);
+  o.pk = e | ((e ? 2047u - e : 0u) << 16);
+  return o;
+}
+
+// Lane-wise maximum of two pairs of 16-bit fields.
+__host__ __device__ __forceinline__ unsigned fx_max2(unsigned a, unsigned b) {
+#ifdef __CUDA_ARCH__
+  unsigned d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+#else
+  const unsigned l = (a & 0xffffu) > (b & 0xffffu) ? (a & 0xffffu) : (b & 0xffffu);
+  const unsigned h = (a >> 16) > (b >> 16) ? (a >> 16) : (b >> 16);
+  return l | (h << 16);
+#endif
+}
+
+// floor(S / 2^(E - e)) for an operand with E - e <= 31 (or S = 0): a funnel shift of the two words.
+__host__ __device__ __forceinline__ unsigned long long fx_align31(const FxOp& o, int E) {
+  const unsigned d = ((unsigned)E - o.pk) & 31u;  // the upper field of pk drops out of the low 5 bits
+#ifdef __CUDA_ARCH__
+  const unsigned lo = __funnelshift_r(o.lo, o.hi, d);
+  const unsigned hi = (unsigned)((int)o.hi >> d);
+  return ((unsigned long long)hi << 32) | lo;
+#else
+  return (unsigned long long)((long long)(((unsigned long long)o.hi << 32) | o.lo) >> d);
+#endif
+}
+
+// The same for any exponent gap (shifts of 63 and more leave 0 or -1).
+__host__ __device__ __forceinline__ unsigned long long fx_align(const FxOp& o, int E) {
+  int d = E - (int)(o.pk & 0xffffu);
+  d = d < 63 ? d : 63;
+  return (unsigned long long)((long long)(((unsigned long long)o.hi << 32) | o.lo) >> d);
+}
+
+// The signed sum S in units 2^(E-1080) as a double: the integer rounded to nearest (ties to even)
+// by the conversion instruction, then scaled by the power of two, which is exact unless the result
+// leaves the normal range (then it is rounded once more, or overflows to infinity, as ldexp does).
 __host__ __device__ __forceinline__ double fx_to_double(unsigned long long S, int E) {
-  const unsigned long long sgn = S & 0x8000000000000000ULL;
-  const unsigned long long A = sgn ? (0ULL - S) : S;
-  if (A == 0ULL) return 0.0;
-  const int lz = fx_clz64(A);
-  const unsigned long long N = A << lz;  // leading one at bit 63
-  const unsigned long long m53 = N >> 11;
-  const unsigned rem = (unsigned)(N & 0x7ffULL);
-  const unsigned long long up = (rem > 0x400u || (rem == 0x400u && (m53 & 1ULL))) ? 1ULL : 0ULL;
-  // value = N 2^(E-1080-lz) = (N / 2^63) 2^(E-1017-lz): biased exponent E + 6 - lz (>= 7 here);
-  // the implicit bit of m53 adds the 1 back and a rounding carry moves on into the exponent
-  const unsigned long long bits = ((unsigned long long)(E + 6 - lz - 1) << 52) + m53 + up;
 #ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)(sgn | bits));
+  return ldexp_rne(__ll2double_rn((long long)S), E - 1080);
 #else
-  double r;
-  const unsigned long long b = sgn | bits;
-  memcpy(&r, &b, sizeof(r));
-  return r;
+  return ldexp((double)(long long)S, E - 1080);
 #endif
 }
 
-// r~ of one cell from its eight operands; absent neighbours are passed as 0.
-__host__ __device__ __forceinline__ double resid_fx(double gv, double xc, int D, double xm, double xp, double ym,
-                                                   double yp, double zm, double zp) {
-  const double v[7] = {gv, xm, xp, ym, yp, zm, zp};
-  unsigned hi[8], lo[8];
-  int e[8];
-  int E = 0;
+// The operand back as a double (exact for normal values, infinities and NaN; subnormals give 0).
+__host__ __device__ __forceinline__ double fx_value(const FxOp& o) {
+  const unsigned long long S = ((unsigned long long)o.hi << 32) | o.lo;
+  const unsigned e = o.pk & 0xffffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long sgn = S & 0x8000000000000000ULL;
+  const unsigned long long mag = (sgn ? (0ULL - S) : S) >> 5;
+  return fx_double(sgn | ((unsigned long long)e << 52) | (mag & 0xfffffffffffffULL));
+}
+
+// The direct FP64 formula, for cells with an infinite or NaN operand.
+__host__ __device__ __forceinline__ double fx_direct(const FxOp (&op)[8], int D) {
+  const double S = ((((fx_value(op[1]) + fx_value(op[2])) + fx_value(op[3])) + fx_value(op[4])) + fx_value(op[5])) +
+                   fx_value(op[6]);
+  return fma(-(double)D, fx_value(op[7]), fx_value(op[0]) + S);
+}
+
+// r~ of one cell from op[0] = g, op[1..6] = the six neighbours (absent ones as fx_op(0.0)) and
+// op[7] = the centre, with D = 6 + d.
+__host__ __device__ __forceinline__ double fx_residual(const FxOp (&op)[8], int D) {
+  unsigned P = op[0].pk;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    unsigned long long u;
-    const double vi = i < 7 ? v[i] : xc;
-#ifdef __CUDA_ARCH__
-    u = (unsigned long long)__double_as_longlong(vi);
-#else
-    memcpy(&u, &vi, sizeof(u));
-#endif
-    hi[i] = (unsigned)(u >> 32);
-    lo[i] = (unsigned)u;
-    e[i] = fx_exp(hi[i]);
-    E = e[i] > E ? e[i] : E;
-  }
-  if (E < kFxMinExp || E > kFxMaxExp) {
-    const double S = ((((xm + xp) + ym) + yp) + zm) + zp;
-#ifdef __CUDA_ARCH__
-    return __fma_rn(-(double)D, xc, gv + S);
-#else
-    return fma(-(double)D, xc, gv + S);
-#endif
-  }
+  for (int i = 1; i < 8; ++i) P = fx_max2(P, op[i].pk);
+  const int E = (int)(P & 0xffffu);
+  if (E == 0) return 0.0;  // every operand zero or subnormal
+  if (E == 2047) return fx_direct(op, D);
+  const int emin = 2047 - (int)(P >> 16);  // smallest exponent among the nonzero operands
   unsigned long long acc = 0ULL;
+  if (E - emin <= 31) {
 #pragma unroll
-  for (int i = 0; i < 7; ++i) acc += fx_term(hi[i], lo[i], e[i], E, false);
-  acc += fx_term(hi[7], lo[7], e[7], E, true) * (unsigned long long)D;
+    for (int i = 0; i < 7; ++i) acc += fx_align31(op[i], E);
+    acc -= fx_align31(op[7], E) * (unsigned long long)D;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) acc += fx_align(op[i], E);
+    acc -= fx_align(op[7], E) * (unsigned long long)D;
+  }
   return fx_to_double(acc, E);
 }
 
-// Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x. The FP64
-// residual is summed in fixed point (resid_fx); single precision keeps the direct formula.
+// Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x (single
+// precision: the direct formula; the FP64 levels use the tiled walk below).
 template <typename T>
 __device__ __forceinline__ T resid_packed(const T* __restrict__ x, const T* __restrict__ g, const Geom& G, int c,
                                           int m, int j, int k) {
@@ -692,20 +734,8 @@ __device__ __forceinline__ T resid_packed(const T* __restrict__ x, const T* __re
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)c * G.csz + row + m;
   const int d = diag_shift_packed(G, m, s, j, k);
-  if constexpr (sizeof(T) == 8) {
-    const long long plane = (long long)G.ny * G.hx;
-    const T* yr = x + (long long)(1 - c) * G.csz + row;
-    const double xm = (m == 0 && s == 0) ? 0.0 : __ldg(yr + m + s - 1);
-    const double xp = (m == G.hx - 1 && s == 1) ? 0.0 : __ldg(yr + m + s);
-    const double ym = (j > 0) ? __ldg(yr + m - G.hx) : 0.0;
-    const double yp = (j < G.ny - 1) ? __ldg(yr + m + G.hx) : 0.0;
-    const double zm = (k > 0) ? __ldg(yr + m - plane) : 0.0;
-    const double zp = (k < G.nz - 1) ? __ldg(yr + m + plane) : 0.0;
-    return resid_fx(__ldg(g + own), __ldg(x + own), 6 + d, xm, xp, ym, yp, zm, zp);
-  } else {
-    const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
-    return fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
-  }
+  const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
+  return fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -903,12 +933,157 @@ __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, con
 
 // ---------------------------------------------------------------------------------------------
 // Residual-norm decomposition shared by the single-system and the batched launches: blocks of
-// kResBX x kResBY threads; block lb of nb walks the rows of the level in (k, j, colour) order (so
-// the red and black rows of one (j,k) are visited together and every neighbour row is still in
-// L2 when it is needed), kResBY rows at a time, threads along the row. A natural-order level
-// (single-level grid) is walked cell by cell. Returns the thread's sum of r~^2; by MODE also
-// writes r = r~ c0 in natural order (1) or float(r~ isc) in the level's own order (2).
+// kResBX x kResBY threads, block lb of nb. Packed FP64 levels are cut into tiles of kResTM packed
+// columns (one per lane) x kResTJ rows (one per warp) x kResTZ planes, both colours; block lb
+// takes tiles lb, lb + nb, ... and each warp marches its row through the tile's planes; the
+// operands of a plane pass through shared memory, so every value is read and converted (fx_op)
+// once per tile (plus a one-cell halo) and serves the seven cells it enters from there. Packed
+// single-precision levels are walked row by row in (k, j, colour) order, kResBY rows at a time,
+// threads along the row; a natural-order level (single-level grid) cell by cell. Returns the
+// thread's sum of r~^2; by MODE also writes r = r~ c0 in natural order (1) or float(r~ isc) in
+// the level's own order (2).
 constexpr int kResBX = 64, kResBY = 4;
+constexpr int kResTM = 32, kResTJ = 8, kResTZ = 64;
+static_assert(kResBX * kResBY == 32 * kResTJ && kResTM == 32, "one warp per tile row");
+
+__host__ __device__ __forceinline__ long long resid_tile_count(const Geom& G, int* nmb = nullptr, int* njb = nullptr) {
+  const int a = (G.hx + kResTM - 1) / kResTM, b = (G.ny + kResTJ - 1) / kResTJ, c = (G.nz + kResTZ - 1) / kResTZ;
+  if (nmb) *nmb = a;
+  if (njb) *njb = b;
+  return (long long)a * b * c;
+}
+
+// The FP64 walk over the tiles of block lb of nb (packed level). Each tile plane is converted into
+// shared memory (a ring of four planes, so one barrier per plane suffices: a plane is rewritten
+// only after every warp has passed the barrier of the plane after the one that read it last),
+// with a one-cell halo: rows j0-1 and j0+kResTJ loaded by the first and last warp, and the column
+// beyond each end of a row loaded by the edge lanes in the colour the row's parity needs there.
+constexpr int kResXR = kResTJ + 2, kResXC = kResTM + 2;
+
+template <int MODE>
+__device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x, const double* __restrict__ g,
+                                                    const Geom& G, long long lb, long long nb, double c0,
+                                                    double* __restrict__ outn, float* __restrict__ outp, double isc,
+                                                    int p2) {
+  // ring slot b, row r (0 and kResXR-1 are the halo rows), colour c, column col (0 and kResXC-1 are
+  // the halo columns) at b * kSlot + r * kRow + c * kResXC + col
+  constexpr int kRow = 2 * kResXC, kSlot = kResXR * kRow;
+  __shared__ unsigned long long sS[4 * kSlot];  // FxOp::lo, hi
+  __shared__ unsigned sP[4 * kSlot];            // FxOp::pk
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31;
+  int nmb, njb;
+  const long long ntiles = resid_tile_count(G, &nmb, &njb);
+  const int hx = G.hx, ny = G.ny, nz = G.nz;
+  const long long plane = (long long)ny * hx;
+  // colour c at (mm, jj, kk); zero outside the level (the absent neighbours)
+  auto ld = [&](const double* __restrict__ a, int c, int mm, int jj, int kk) -> double {
+    double v = 0.0;
+    if (mm >= 0 && mm < hx && jj >= 0 && jj < ny && kk >= 0 && kk < nz)
+      v = __ldg(a + (long long)c * G.csz + kk * plane + (long long)jj * hx + mm);
+    return v;
+  };
+  auto put = [&](int b, int r, int c, int col, const FxOp& o) {
+    const int i = b * kSlot + r * kRow + c * kResXC + col;
+    sS[i] = ((unsigned long long)o.hi << 32) | o.lo;
+    sP[i] = o.pk;
+  };
+  auto get = [&](int i) -> FxOp {
+    const unsigned long long v = sS[i];
+    FxOp o;
+    o.lo = (unsigned)v;
+    o.hi = (unsigned)(v >> 32);
+    o.pk = sP[i];
+    return o;
+  };
+  double acc = 0.0;
+  for (long long t = lb; t < ntiles; t += nb) {
+    const int mb = (int)(t % nmb);
+    const long long rest = t / nmb;
+    const int jb = (int)(rest % njb);
+    const int k0 = (int)(rest / njb) * kResTZ;
+    const int k1 = min(k0 + kResTZ, nz);
+    const int m = mb * kResTM + lane, j = jb * kResTJ + w;
+    const bool live = m < hx && j < ny;
+    const int hside = lane == 0 ? -1 : (lane == kResTM - 1 ? 1 : 0);
+    const int dj = (j == 0 ? G.sh[2] : 0) + (j == ny - 1 ? G.sh[3] : 0);
+    // The values of plane kk this thread contributes to the ring: its own column in both colours,
+    // the column beyond the row's end (edge lanes; left end: red cells with s = 0 need black m-1
+    // and black cells with s = 0 red m-1; right end likewise with s = 1), and the rows beyond the
+    // tile (first and last warp). Fetched one plane ahead of their conversion into slot kk & 3.
+    struct Raw {
+      double own[2], halo, row[2];
+    };
+    auto fetch = [&](int kk, Raw& r) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) r.own[c] = ld(x, c, m, j, kk);
+      r.halo = 0.0;
+      if (hside != 0) {
+        const int hc = (hside < 0) == (((j + kk) & 1) != 0) ? 0 : 1;
+        r.halo = ld(x, hc, m + hside, j, kk);
+      }
+      if (w == 0 || w == kResTJ - 1) {
+        const int jj = w == 0 ? j - 1 : j + 1;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) r.row[c] = ld(x, c, m, jj, kk);
+      }
+    };
+    auto store = [&](int kk, const Raw& r) {
+      const int b = kk & 3;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) put(b, w + 1, c, lane + 1, fx_op(r.own[c]));
+      if (hside != 0) {
+        const int hc = (hside < 0) == (((j + kk) & 1) != 0) ? 0 : 1;
+        put(b, w + 1, hc, hside < 0 ? 0 : kResXC - 1, fx_op(r.halo));
+      }
+      if (w == 0 || w == kResTJ - 1) {
+        const int rr = w == 0 ? 0 : kResXR - 1;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) put(b, rr, c, lane + 1, fx_op(r.row[c]));
+      }
+    };
+    __syncthreads();  // the previous tile's last reads of the ring are done
+    Raw pre;
+    fetch(k0 - 1, pre);
+    store(k0 - 1, pre);
+    fetch(k0, pre);
+    store(k0, pre);
+    fetch(k0 + 1, pre);
+    double gpre[2] = {ld(g, 0, live ? m : -1, j, k0), ld(g, 1, live ? m : -1, j, k0)};
+    for (int k = k0; k < k1; ++k) {
+      const Raw cur = pre;
+      const double gv[2] = {gpre[0], gpre[1]};
+      if (k + 2 <= k1) fetch(k + 2, pre);
+      if (k + 1 < k1) {
+        gpre[0] = ld(g, 0, live ? m : -1, j, k + 1);
+        gpre[1] = ld(g, 1, live ? m : -1, j, k + 1);
+      }
+      store(k + 1, cur);
+      __syncthreads();
+      if (live) {
+        const int own = (w + 1) * kRow + lane + 1;
+        const int B0 = (k & 3) * kSlot + own, BM = ((k - 1) & 3) * kSlot + own, BP = ((k + 1) & 3) * kSlot + own;
+        // diagonal shift: the walls of this row and plane, then the x walls per cell
+        const int dbase = dj + (k == 0 ? G.sh[4] : 0) + (k == nz - 1 ? G.sh[5] : 0);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int s = (j + k + c) & 1, o = (1 - c) * kResXC;
+          // x neighbours: the other colour at m + s - 1 and m + s (columns shifted by the halo)
+          const FxOp op[8] = {fx_op(gv[c]),       get(B0 + o + s - 1), get(B0 + o + s), get(B0 + o - kRow),
+                              get(B0 + o + kRow), get(BM + o),         get(BP + o),     get(B0 + c * kResXC)};
+          const int d = dbase + (m == 0 && s == 0 ? G.sh[0] : 0) + (m == hx - 1 && s == 1 ? G.sh[1] : 0);
+          const double rd = fx_residual(op, 6 + d);
+          acc = fma(rd, rd, acc);
+          if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)ny * k)] = rd * c0;
+          if (MODE == 2)
+            outp[(long long)c * G.csz + k * plane + (long long)j * hx + m] =
+                p2 != kBadPow2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);
+        }
+      }
+    }
+  }
+  return acc;
+}
 
 template <typename T, int MODE, bool POW2 = false>
 __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x, const T* __restrict__ g,
@@ -952,7 +1127,8 @@ __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x,
       if (iz == nz - 1) d += G.sh[5];
       double rd;
       if constexpr (sizeof(T) == 8) {
-        rd = resid_fx(g[i], x[i], 6 + d, xm, xp, ym, yp, zm, zp);
+        const FxOp op[8] = {fx_op(g[i]), fx_op(xm), fx_op(xp), fx_op(ym), fx_op(yp), fx_op(zm), fx_op(zp), fx_op(x[i])};
+        rd = fx_residual(op, 6 + d);
       } else {
         const T S = ((((xm + xp) + ym) + yp) + zm) + zp;
         rd = (double)fmat(neg_diag<T>(d), x[i], g[i] + S);
@@ -971,10 +1147,11 @@ template <typename T, int MODE>
 __device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                    long long lb, long long nb, double c0, double* __restrict__ outn,
                                                    float* __restrict__ outp, double isc) {
-  if (MODE == 2) {
-    const int p2 = pow2_exponent(isc);
-    if (p2 != kBadPow2) return resid_norm_accum_impl<T, MODE, true>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
+  const int p2 = MODE == 2 ? pow2_exponent(isc) : kBadPow2;
+  if constexpr (sizeof(T) == 8) {
+    if (G.packed) return resid_tiles_accum<MODE>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
   }
+  if (p2 != kBadPow2) return resid_norm_accum_impl<T, MODE, true>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
   return resid_norm_accum_impl<T, MODE, false>(x, g, G, lb, nb, c0, outn, outp, isc, kBadPow2);
 }
 
@@ -1006,10 +1183,8 @@ __device__ __forceinline__ void resid_zero_rows(const double* __restrict__ g, co
 // Number of blocks of the residual-norm launch for level G (= the number of partial sums).
 __host__ __device__ __forceinline__ int resid_norm_blocks(const Geom& G) {
   if (!G.packed) return 1;
-  const long long rows = 2LL * G.nz * G.ny;
-  long long blocks = (rows + kResBY - 1) / kResBY;
-  if (blocks > kMaxPartialsPerSystem) blocks = kMaxPartialsPerSystem;
-  return (int)blocks;
+  const long long tiles = resid_tile_count(G);
+  return (int)(tiles < kMaxPartials ? tiles : kMaxPartials);
 }
 
 // Fixed-order sum of n partials by one block (strided per-thread sums, then block_sum).
