@@ -14,6 +14,12 @@ namespace ops {
 
 __device__ __forceinline__ double fmat(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmat(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// A product and a sum that the compiler may not fuse into one FMA (kernels that must agree bit
+// for bit round both).
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
 // Diagonal shift d of the folded boundary stencil for packed-row coordinates (m, s, j, k):
 // +1 per Dirichlet face, -1 per Neumann face the cell touches (Sec. 2.4, Boundary conditions).
@@ -341,18 +347,18 @@ __device__ __forceinline__ void coarse_row_w(const T* __restrict__ ec, const Geo
       // rows hold whole 4-float vectors), so both pairs are 8-byte aligned
       const float2 pa = __ldg(reinterpret_cast<const float2*>(a));
       const float2 pb = __ldg(reinterpret_cast<const float2*>(b));
-      w[0] = omega * pa.x;
-      w[1] = omega * pb.x;
-      w[2] = omega * pa.y;
-      w[3] = omega * pb.y;
+      w[0] = mul_rn(omega, pa.x);
+      w[1] = mul_rn(omega, pb.x);
+      w[2] = mul_rn(omega, pa.y);
+      w[3] = mul_rn(omega, pb.y);
     } else {
 #pragma unroll
-      for (int v = 0; v < V; ++v) w[v] = omega * __ldg(((v & 1) ? b : a) + (v >> 1));
+      for (int v = 0; v < V; ++v) w[v] = mul_rn(omega, __ldg(((v & 1) ? b : a) + (v >> 1)));
     }
   } else {
     const long long o = (long long)I0 + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
 #pragma unroll
-    for (int v = 0; v < V; ++v) w[v] = omega * __ldg(ec + o + v);
+    for (int v = 0; v < V; ++v) w[v] = mul_rn(omega, __ldg(ec + o + v));
   }
 }
 
@@ -388,18 +394,18 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
   if (jy) coarse_row_w<T, V>(ec, Gc, m0, (j & 1) ? J + 1 : J - 1, K, omega, wy);
   if (kz) coarse_row_w<T, V>(ec, Gc, m0, J, (k & 1) ? K + 1 : K - 1, omega, wz);
 #pragma unroll
-  for (int v = 0; v < V; ++v) yc[v] = yc[v] + wc[v];
+  for (int v = 0; v < V; ++v) yc[v] = add_rn(yc[v], wc[v]);
   T extra = T(0);
   if (s == 0) {
-    if (m0 > 0) extra = __ldg(yr + m0 - 1) + omega * __ldg(ec + coarse_index(Gc, m0 - 1, J, K));
+    if (m0 > 0) extra = add_rn(__ldg(yr + m0 - 1), mul_rn(omega, __ldg(ec + coarse_index(Gc, m0 - 1, J, K))));
   } else {
-    if (m0 + V < G.hx) extra = __ldg(yr + m0 + V) + omega * __ldg(ec + coarse_index(Gc, m0 + V, J, K));
+    if (m0 + V < G.hx) extra = add_rn(__ldg(yr + m0 + V), mul_rn(omega, __ldg(ec + coarse_index(Gc, m0 + V, J, K))));
   }
   // (j-1)>>1 is J-1 for even j and J for odd j; (j+1)>>1 is J for even j and J+1 for odd j
   if (j > 0) {
     load_vec(yr + m0 - G.hx, ym);
 #pragma unroll
-    for (int v = 0; v < V; ++v) ym[v] = ym[v] + ((j & 1) ? wc[v] : wy[v]);
+    for (int v = 0; v < V; ++v) ym[v] = add_rn(ym[v], (j & 1) ? wc[v] : wy[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) ym[v] = T(0);
@@ -407,7 +413,7 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
   if (j < G.ny - 1) {
     load_vec(yr + m0 + G.hx, yp);
 #pragma unroll
-    for (int v = 0; v < V; ++v) yp[v] = yp[v] + ((j & 1) ? wy[v] : wc[v]);
+    for (int v = 0; v < V; ++v) yp[v] = add_rn(yp[v], (j & 1) ? wy[v] : wc[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) yp[v] = T(0);
@@ -415,7 +421,7 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
   if (k > 0) {
     load_vec(yr + m0 - plane, zm);
 #pragma unroll
-    for (int v = 0; v < V; ++v) zm[v] = zm[v] + ((k & 1) ? wc[v] : wz[v]);
+    for (int v = 0; v < V; ++v) zm[v] = add_rn(zm[v], (k & 1) ? wc[v] : wz[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) zm[v] = T(0);
@@ -423,7 +429,7 @@ __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* _
   if (k < G.nz - 1) {
     load_vec(yr + m0 + plane, zp);
 #pragma unroll
-    for (int v = 0; v < V; ++v) zp[v] = zp[v] + ((k & 1) ? wz[v] : wc[v]);
+    for (int v = 0; v < V; ++v) zp[v] = add_rn(zp[v], (k & 1) ? wz[v] : wc[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) zp[v] = T(0);
@@ -572,7 +578,7 @@ __device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, cons
 template <typename T>
 __device__ __forceinline__ void prolong_cell(T* __restrict__ x, const Geom& G, const T* __restrict__ ec,
                                              const Geom& Gc, T omega, int red_only, int I, int J, int K) {
-  const T w = omega * __ldg(ec + coarse_index(Gc, I, J, K));
+  const T w = mul_rn(omega, __ldg(ec + coarse_index(Gc, I, J, K)));
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
@@ -582,7 +588,7 @@ __device__ __forceinline__ void prolong_cell(T* __restrict__ x, const Geom& G, c
         const int c = (di + dj + dk) & 1;
         if (red_only && c) continue;
         const long long idx = (long long)c * G.csz + ((long long)(2 * K + dk) * G.ny + (2 * J + dj)) * G.hx + I;
-        x[idx] = x[idx] + w;
+        x[idx] = add_rn(x[idx], w);
       }
 }
 
@@ -976,13 +982,6 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
   const long long ntiles = resid_tile_count(G, &nmb, &njb);
   const int hx = G.hx, ny = G.ny, nz = G.nz;
   const long long plane = (long long)ny * hx;
-  // colour c at (mm, jj, kk); zero outside the level (the absent neighbours)
-  auto ld = [&](const double* __restrict__ a, int c, int mm, int jj, int kk) -> double {
-    double v = 0.0;
-    if (mm >= 0 && mm < hx && jj >= 0 && jj < ny && kk >= 0 && kk < nz)
-      v = __ldg(a + (long long)c * G.csz + kk * plane + (long long)jj * hx + mm);
-    return v;
-  };
   auto put = [&](int b, int r, int c, int col, const FxOp& o) {
     const int i = b * kSlot + r * kRow + c * kResXC + col;
     sS[i] = ((unsigned long long)o.hi << 32) | o.lo;
@@ -1010,33 +1009,36 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
     // The values of plane kk this thread contributes to the ring: its own column in both colours,
     // the column beyond the row's end (edge lanes; left end: red cells with s = 0 need black m-1
     // and black cells with s = 0 red m-1; right end likewise with s = 1), and the rows beyond the
-    // tile (first and last warp). Fetched one plane ahead of their conversion into slot kk & 3.
+    // tile (first and last warp); zero outside the level (the absent neighbours). Fetched one
+    // plane ahead of their conversion into slot kk & 3.
+    const long long col = (long long)j * hx + m;  // the column's offset within a colour plane
+    const bool hok = hside != 0 && m + hside >= 0 && m + hside < hx && j < ny;
+    const bool edge = w == 0 || w == kResTJ - 1;
+    const int jr = w == 0 ? j - 1 : j + 1;
+    const bool rok = edge && jr >= 0 && jr < ny && m < hx;
+    const long long rcol = (long long)jr * hx + m;
     struct Raw {
       double own[2], halo, row[2];
     };
+    auto hcol = [&](int kk) { return (hside < 0) == (((j + kk) & 1) != 0) ? 0 : 1; };
     auto fetch = [&](int kk, Raw& r) {
+      const bool zin = kk >= 0 && kk < nz;
+      const long long po = (long long)kk * plane;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) r.own[c] = ld(x, c, m, j, kk);
-      r.halo = 0.0;
-      if (hside != 0) {
-        const int hc = (hside < 0) == (((j + kk) & 1) != 0) ? 0 : 1;
-        r.halo = ld(x, hc, m + hside, j, kk);
-      }
-      if (w == 0 || w == kResTJ - 1) {
-        const int jj = w == 0 ? j - 1 : j + 1;
+      for (int c = 0; c < 2; ++c) r.own[c] = (live && zin) ? __ldg(x + c * G.csz + po + col) : 0.0;
+      r.halo = (hok && zin) ? __ldg(x + hcol(kk) * G.csz + po + col + hside) : 0.0;
+      if (edge) {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) r.row[c] = ld(x, c, m, jj, kk);
+        for (int c = 0; c < 2; ++c) r.row[c] = (rok && zin) ? __ldg(x + c * G.csz + po + rcol) : 0.0;
       }
     };
+    auto gload = [&](int c, int kk) { return live ? __ldg(g + c * G.csz + (long long)kk * plane + col) : 0.0; };
     auto store = [&](int kk, const Raw& r) {
       const int b = kk & 3;
 #pragma unroll
       for (int c = 0; c < 2; ++c) put(b, w + 1, c, lane + 1, fx_op(r.own[c]));
-      if (hside != 0) {
-        const int hc = (hside < 0) == (((j + kk) & 1) != 0) ? 0 : 1;
-        put(b, w + 1, hc, hside < 0 ? 0 : kResXC - 1, fx_op(r.halo));
-      }
-      if (w == 0 || w == kResTJ - 1) {
+      if (hside != 0) put(b, w + 1, hcol(kk), hside < 0 ? 0 : kResXC - 1, fx_op(r.halo));
+      if (edge) {
         const int rr = w == 0 ? 0 : kResXR - 1;
 #pragma unroll
         for (int c = 0; c < 2; ++c) put(b, rr, c, lane + 1, fx_op(r.row[c]));
@@ -1049,14 +1051,14 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
     fetch(k0, pre);
     store(k0, pre);
     fetch(k0 + 1, pre);
-    double gpre[2] = {ld(g, 0, live ? m : -1, j, k0), ld(g, 1, live ? m : -1, j, k0)};
+    double gpre[2] = {gload(0, k0), gload(1, k0)};
     for (int k = k0; k < k1; ++k) {
       const Raw cur = pre;
       const double gv[2] = {gpre[0], gpre[1]};
       if (k + 2 <= k1) fetch(k + 2, pre);
       if (k + 1 < k1) {
-        gpre[0] = ld(g, 0, live ? m : -1, j, k + 1);
-        gpre[1] = ld(g, 1, live ? m : -1, j, k + 1);
+        gpre[0] = gload(0, k + 1);
+        gpre[1] = gload(1, k + 1);
       }
       store(k + 1, cur);
       __syncthreads();
@@ -1076,7 +1078,7 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
           acc = fma(rd, rd, acc);
           if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)ny * k)] = rd * c0;
           if (MODE == 2)
-            outp[(long long)c * G.csz + k * plane + (long long)j * hx + m] =
+            outp[(long long)c * G.csz + k * plane + col] =
                 p2 != kBadPow2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);
         }
       }

@@ -125,9 +125,10 @@ __device__ __forceinline__ Work work_item(const Geom& G, int kz, long long w) {
 // waits for it run out of their `budget`.
 // With C::kPro the sweep is the first black post-smoothing sweep fused with the prolongation of
 // the coarse correction e_c (Sec. 3): every red value read is red + omega e_c(parent), the parent
-// of the red cell at packed index m of fine row (j', k') being coarse cell (m, j'/2, k'/2) (as in
-// ops::smooth_vec_prolong, whose arithmetic this repeats); the coarse rows arrive with each
-// red plane (coarse plane floor(p/2) for red plane p), out-of-range parents as zeros.
+// of the red cell at packed index m of fine row (j', k') being coarse cell (m, j'/2, k'/2), both
+// operations rounded separately as in ops::smooth_vec_prolong; the coarse rows arrive with each
+// red plane (coarse plane floor(p/2) for red plane p), out-of-range parents as zeros, and each
+// landed red plane is corrected once in shared memory before the cells read it.
 template <class C>
 __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ x, Geom G, InvDiag<float> inv,
                                                            int colour, int kz, long long nwork,
@@ -193,6 +194,33 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
     // walls touched by this thread's cells in every plane but the first and last (x and y);
     // without any, every cell's diagonal is 6
     const bool xy_wall = j == 0 || j == G.ny - 1 || (m0 == 0) || (m0 + 4 >= G.hx);
+    // PRO: red plane p in slot q becomes red + omega e_c(parent) in place. The parent of the red
+    // cell at packed index m of fine row (j', p) is coarse cell (m, j'/2, p/2), of colour
+    // (m + j'/2 + p/2) & 1 at packed index m >> 1; its coarse row sits in box row
+    // j'/2 - (y0/2 - 1), column (m >> 1) - (x0/2 - kCHalo). Out-of-range red values and parents
+    // arrived as zeros, so walls stay zero.
+    auto correct = [&](int q, int p) {
+      float* slot = ring + q * (kSlotBytes / 4);
+      const int K = (p + 2) / 2 - 1;  // floor(p / 2) for p >= -1
+      constexpr int kVecs = kBoxX / 4 * C::kBoxY;
+      for (int f = ty * kTX + tx; f < kVecs; f += kTX * kTY) {
+        const int by = f / (kBoxX / 4), bx = 4 * (f - by * (kBoxX / 4));
+        const int m = t.x0 - kHaloX + bx, J = (t.y0 - 1 + by) >> 1;
+        const int rowb = (J - (t.y0 / 2 - 1)) * kCBoxX + (bx >> 1) + (kCHalo - kHaloX / 2);
+        const bool even0 = ((m + J + K) & 1) == 0;  // parent I = m has colour 0
+        const float* ca = slot + (even0 ? C::kC0Off : C::kC1Off) / 4 + rowb;
+        const float* cb = slot + (even0 ? C::kC1Off : C::kC0Off) / 4 + rowb;
+        const float2 pa = *reinterpret_cast<const float2*>(ca);
+        const float2 pb = *reinterpret_cast<const float2*>(cb);
+        float4* v = reinterpret_cast<float4*>(slot + by * kBoxX + bx);
+        float4 r = *v;
+        r.x = __fadd_rn(r.x, __fmul_rn(omega, pa.x));
+        r.y = __fadd_rn(r.y, __fmul_rn(omega, pb.x));
+        r.z = __fadd_rn(r.z, __fmul_rn(omega, pa.y));
+        r.w = __fadd_rn(r.w, __fmul_rn(omega, pb.y));
+        *v = r;
+      }
+    };
     for (int k = t.k0; k < t.k1; ++k) {
       const int i = k - t.k0 + 1;  // load index of plane k (k-1 is i-1; k+1 and g(k) are i+1)
       bool ok = true;
@@ -201,7 +229,19 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
         ok = ok && mbar_wait(bar0 + 8u * (unsigned)qk, (unsigned)(((seq + 1) / kSlots) & 1), budget);
       }
       ok = ok && mbar_wait(bar0 + 8u * (unsigned)qp, php, budget);
-      // the barrier also retires iteration k-1, freeing the slot of load i-2 for load i+kSlots-2
+      if constexpr (C::kPro) {
+        // red planes k-1 and k arrived with the item's first plane, k+1 just now: add the
+        // prolongated correction to them in place, once, before any cell reads them
+        if (ok) {
+          if (k == t.k0) {
+            correct(qm, k - 1);
+            correct(qk, k);
+          }
+          correct(qp, k + 1);
+        }
+      }
+      // the barrier also retires iteration k-1 (and publishes the corrected planes), freeing the
+      // slot of load i-2 for load i+kSlots-2
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -220,51 +260,10 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
         const float4 zp = *reinterpret_cast<const float4*>(pp + c0);
         const float extra = s == 0 ? pk[c0 - 1] : pk[c0 + 4];
         const float4 gv = *reinterpret_cast<const float4*>(pp + kGOff / 4 + ty * (4 * kTX) + 4 * tx);
-        float ycv[4] = {yc.x, yc.y, yc.z, yc.w}, ymv[4] = {ym.x, ym.y, ym.z, ym.w};
-        float ypv[4] = {yp.x, yp.y, yp.z, yp.w}, zmv[4] = {zm.x, zm.y, zm.z, zm.w};
-        float zpv[4] = {zp.x, zp.y, zp.z, zp.w};
+        const float ycv[4] = {yc.x, yc.y, yc.z, yc.w}, ymv[4] = {ym.x, ym.y, ym.z, ym.w};
+        const float ypv[4] = {yp.x, yp.y, yp.z, yp.w}, zmv[4] = {zm.x, zm.y, zm.z, zm.w};
+        const float zpv[4] = {zp.x, zp.y, zp.z, zp.w};
         const float gvv[4] = {gv.x, gv.y, gv.z, gv.w};
-        float extra_c = extra;
-        if constexpr (C::kPro) {
-          // omega e_c for the parents (m0 .. m0+3, J, K) of a red row segment, from a slot's
-          // coarse boxes: coarse cell I of row (J, K) has colour (I + J + K) & 1 and packed
-          // index I >> 1; box column (I >> 1) - (x0/2 - kCHalo), box row J - (y0/2 - 1)
-          const int K = k >> 1;
-          auto parents = [&](const float* slot, int Jc, int Kc, float (&w)[4]) {
-            const float* c0 = slot + C::kC0Off / 4;
-            const float* c1 = slot + C::kC1Off / 4;
-            const int rowb = (Jc - (t.y0 / 2 - 1)) * kCBoxX + 2 * tx + kCHalo;  // (m0 >> 1) - (x0/2 - kCHalo)
-            const bool even0 = ((m0 + Jc + Kc) & 1) == 0;                        // I = m0 has colour 0
-            const float2 a = *reinterpret_cast<const float2*>((even0 ? c0 : c1) + rowb);
-            const float2 b = *reinterpret_cast<const float2*>((even0 ? c1 : c0) + rowb);
-            w[0] = omega * a.x;
-            w[1] = omega * b.x;
-            w[2] = omega * a.y;
-            w[3] = omega * b.y;
-          };
-          auto parent1 = [&](const float* slot, int I, int Jc, int Kc) {
-            const float* cc = slot + (((I + Jc + Kc) & 1) ? C::kC1Off : C::kC0Off) / 4;
-            return omega * cc[(Jc - (t.y0 / 2 - 1)) * kCBoxX + (I >> 1) - (t.x0 / 2 - kCHalo)];
-          };
-          const int J = j >> 1;
-          float w[4];
-          parents(pk, J, K, w);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) ycv[e] = ycv[e] + w[e];
-          extra_c = s == 0 ? extra + parent1(pk, m0 - 1, J, K) : extra + parent1(pk, m0 + 4, J, K);
-          parents(pk, (j - 1) >> 1, K, w);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) ymv[e] = ymv[e] + w[e];
-          parents(pk, (j + 1) >> 1, K, w);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) ypv[e] = ypv[e] + w[e];
-          parents(pm, J, (k - 1 + 2) / 2 - 1, w);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) zmv[e] = zmv[e] + w[e];
-          parents(pp, J, (k + 1) >> 1, w);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) zpv[e] = zpv[e] + w[e];
-        }
         float invd[4];
         if (xy_wall || k == 0 || k == G.nz - 1) {
           int dbase = 0;
@@ -288,11 +287,11 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
         for (int e = 0; e < 4; ++e) {
           float xm, xp;
           if (s == 0) {
-            xm = (e == 0) ? extra_c : ycv[e - 1 < 0 ? 0 : e - 1];
+            xm = (e == 0) ? extra : ycv[e - 1 < 0 ? 0 : e - 1];
             xp = ycv[e];
           } else {
             xm = ycv[e];
-            xp = (e == 3) ? extra_c : ycv[e + 1 > 3 ? 3 : e + 1];
+            xp = (e == 3) ? extra : ycv[e + 1 > 3 ? 3 : e + 1];
           }
           const float S = ((((xm + xp) + ymv[e]) + ypv[e]) + zmv[e]) + zpv[e];
           out[e] = (gvv[e] + S) * invd[e];
