@@ -59,7 +59,10 @@ struct Cfg {
   static_assert(TY % 2 == 0, "tiles cover whole coarse rows");
 };
 using Product = Cfg<8, 6>;           // 9600-byte slots, 57.6 KB per CTA, 3 CTAs per SM
-using ProductPro = Cfg<8, 5, true>;  // 13184-byte slots, 65.9 KB per CTA, 3 CTAs per SM
+using ProductPro = Cfg<8, 5, true>;  // 13184-byte slots, 65.9 KB per CTA, 3 CTAs per SM (6 slots: 2 per SM, slower)
+// the fused sweep reads the other colour through the plain sweep's tensor maps, whose boxes are
+// Product::kBoxY rows high: the expected transaction bytes must match them
+static_assert(ProductPro::kTY == Product::kTY, "the fused sweep shares the plain sweep's other-colour boxes");
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
