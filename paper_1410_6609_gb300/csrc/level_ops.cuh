@@ -773,104 +773,89 @@ __device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubl
 // vectors in shared memory `sm` (4 n doubles), natural cell order. Operator: the scaled
 // A_L / c_L, i.e. (6 + d_i) p_i - sum of interior neighbours. Stops when ||r|| <= rtol ||b|| or
 // after maxit iterations; returns the iteration count.
-// The same iteration by warp 0 alone, for coarsest grids of at most kCoarseWarpCells cells:
-// lane l owns cells l and l+32; the dot products are warp_sum reductions, and __syncwarp orders
-// the direction update before the next product reads its neighbours. No block barrier is taken.
-// (Two cells per lane at most: the per-cell work is unrolled, and unused slots would still issue
-// their predicated FP64 instructions.)
-constexpr int kCoarseWarpCells = 64;
+// The same iteration for coarsest grids of at most 2 x 32 cells, one cell per thread of one warp
+// (n <= 32) or two (named barrier 1 over the first 64 threads): each thread keeps its cell's x
+// and r in registers, only p (which the neighbours read) lives in shared memory, and the dot
+// products are warp_sum reductions, added over the two warps in a fixed order. On GB300 an FP64
+// warp instruction takes 64 cycles of its sub-partition's FP64 pipe, so one cell per lane on two
+// sub-partitions halves the issue time of the former two-cells-per-lane warp.
+constexpr int kCoarseSmallCells = 64;
 
 template <typename T>
-__device__ int coarse_cg_warp(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
-                              double* sm) {
-  constexpr int kPer = kCoarseWarpCells / 32;  // cells per lane at most
+__device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
+                               double* __restrict__ p, double* __restrict__ red) {
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = nx * ny * nz;
-  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-  double* x = sm;
-  double* r = x + n;
-  double* p = r + n;
-  double* ap = p + n;
-  // per owned cell: which of its six neighbours exist (bits -x,+x,-y,+y,-z,+z) and -(6 + d)
-  unsigned nbm[kPer];
-  double nd[kPer];
-  double loc = 0.0;
-#pragma unroll
-  for (int t = 0; t < kPer; ++t) {
-    const int i = lane + 32 * t;
-    nbm[t] = 0u;
-    nd[t] = 0.0;
-    if (i < n) {
-      const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
-      int d = 0;
-      if (ix > 0) nbm[t] |= 1u; else d += G.sh[0];
-      if (ix < nx - 1) nbm[t] |= 2u; else d += G.sh[1];
-      if (iy > 0) nbm[t] |= 4u; else d += G.sh[2];
-      if (iy < ny - 1) nbm[t] |= 8u; else d += G.sh[3];
-      if (iz > 0) nbm[t] |= 16u; else d += G.sh[4];
-      if (iz < nz - 1) nbm[t] |= 32u; else d += G.sh[5];
-      nd[t] = neg_diag<double>(d);
-      const double b = (double)bi[i];
-      x[i] = 0.0;
-      r[i] = b;
-      p[i] = b;
-      loc += b * b;
-    }
+  const int W = n > 32 ? 2 : 1;  // warps taking part (uniform)
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, w = t >> 5;
+  const bool own = t < n;
+  auto sync = [&]() {
+    if (W == 2) asm volatile("bar.sync 1, 64;" ::: "memory");
+    else __syncwarp();
+  };
+  int slot = 0;
+  // sum of one value per thread over the W warps, in a fixed order
+  auto psum = [&](double v) -> double {
+    v = warp_sum(v);
+    if (W == 1) return v;
+    if (lane == 0) red[2 * slot + w] = v;
+    sync();
+    const double sv = red[2 * slot] + red[2 * slot + 1];
+    slot ^= 1;  // the next sum writes the other pair; its barrier follows every read of this one
+    return sv;
+  };
+  // the cell's neighbours (bits -x,+x,-y,+y,-z,+z) and -(6 + d)
+  unsigned nbm = 0u;
+  double nd = 0.0, xi = 0.0, ri = 0.0;
+  if (own) {
+    const int ix = t % nx, iy = (t / nx) % ny, iz = t / (nx * ny);
+    int d = 0;
+    if (ix > 0) nbm |= 1u; else d += G.sh[0];
+    if (ix < nx - 1) nbm |= 2u; else d += G.sh[1];
+    if (iy > 0) nbm |= 4u; else d += G.sh[2];
+    if (iy < ny - 1) nbm |= 8u; else d += G.sh[3];
+    if (iz > 0) nbm |= 16u; else d += G.sh[4];
+    if (iz < nz - 1) nbm |= 32u; else d += G.sh[5];
+    nd = neg_diag<double>(d);
+    ri = (double)bi[t];
+    p[t] = ri;
   }
-  __syncwarp();
-  double rr = warp_sum(loc);
+  double rr = psum(ri * ri);  // its barrier also publishes p
   const double bnorm = sqrt(rr);
   const double stop = rtol * bnorm;
   const double stop2 = stop * stop;  // ||r|| <= stop as ||r||^2 <= stop^2: no square root per iteration
   int it = 0;
   if (bnorm > 0.0) {
     while (it < maxit) {
-      loc = 0.0;
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        const int i = lane + 32 * t;
-        if (i < n) {
-          const unsigned m = nbm[t];
-          double S = 0.0;
-          if (m & 1u) S += p[i - 1];
-          if (m & 2u) S += p[i + 1];
-          if (m & 4u) S += p[i - nx];
-          if (m & 8u) S += p[i + nx];
-          if (m & 16u) S += p[i - nx * ny];
-          if (m & 32u) S += p[i + nx * ny];
-          const double a = -nd[t] * p[i] - S;
-          ap[i] = a;
-          loc += p[i] * a;
-        }
+      double a = 0.0, pi = 0.0;
+      if (own) {
+        pi = p[t];
+        double S = 0.0;
+        if (nbm & 1u) S += p[t - 1];
+        if (nbm & 2u) S += p[t + 1];
+        if (nbm & 4u) S += p[t - nx];
+        if (nbm & 8u) S += p[t + nx];
+        if (nbm & 16u) S += p[t - nx * ny];
+        if (nbm & 32u) S += p[t + nx * ny];
+        a = -nd * pi - S;
       }
-      const double pap = warp_sum(loc);
+      const double pap = psum(pi * a);  // after its barrier nobody reads p of this iteration again
       const double alpha = rr / pap;
-      loc = 0.0;
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        const int i = lane + 32 * t;
-        if (i < n) {
-          x[i] = x[i] + alpha * p[i];
-          const double ri = r[i] - alpha * ap[i];
-          r[i] = ri;
-          loc += ri * ri;
-        }
+      if (own) {
+        xi = xi + alpha * pi;
+        ri = ri - alpha * a;
       }
-      const double rrn = warp_sum(loc);
+      const double rrn = psum(ri * ri);
       ++it;
       if (rrn <= stop2) break;
       const double beta = rrn / rr;
-      __syncwarp();  // every lane has read p for its product before p changes
-#pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        const int i = lane + 32 * t;
-        if (i < n) p[i] = r[i] + beta * p[i];
-      }
-      __syncwarp();
+      if (own) p[t] = ri + beta * pi;
+      sync();  // p complete before the next product reads its neighbours
       rr = rrn;
     }
   }
-  for (int i = lane; i < n; i += 32) xo[i] = (T)x[i];
+  if (own) xo[t] = (T)xi;
   return it;
 }
 
@@ -879,9 +864,9 @@ __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, con
                                double* sm, double* red) {
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = nx * ny * nz;
-  if (n <= kCoarseWarpCells) {  // uniform over the block
+  if (n <= kCoarseSmallCells) {  // uniform over the block; launches give such grids >= 32 (n <= 32) or 64 threads
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    return tid < 32 ? coarse_cg_warp<T>(xo, bi, G, rtol, maxit, sm) : 0;
+    return tid < (n > 32 ? 64 : 32) ? coarse_cg_small<T>(xo, bi, G, rtol, maxit, sm, red) : 0;
   }
   double* x = sm;
   double* r = x + n;
