@@ -44,6 +44,10 @@ def _step(w):
     Ev = E.reshape(3, -1)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
     out.update(E_idx=idx, E_vals=Ev)
     del E
+    # the FP64 residual field of the final iterate at the same cells (h = 1: r = r~)
+    _, rf = P.residual(field=True)
+    out.update(r_vals=rf.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy())
+    del rf
     P.close()
     return out
 
@@ -68,6 +72,29 @@ def test_benchmark_step_at_full_size(name):
     F_ref = oracle.force_gather(g["phi"], w.h, w.bc_type, w.bc_value, sp.centers, sp.radius, sp.density,
                                 w.subsample)
     assert np.max(np.abs(g["F"] - F_ref)) <= 1e-12 * np.max(np.abs(F_ref))
+    # sampled FP64 residuals against exact rational arithmetic on the GPU iterate: within half an
+    # ulp of the cell's largest operand plus half an ulp of the result
+    assert w.h == 1.0
+    _assert_exact_residuals(g["phi"], f, w.bc_type, g["E_idx"], g["r_vals"])
+
+
+def _assert_exact_residuals(phi, f, bc, idx, r_vals):
+    from fractions import Fraction
+    nz, ny, nx = phi.shape
+    sh = {0: 1, 1: -1}
+    for q, r in zip(idx, r_vals):
+        k, rem = divmod(int(q), ny * nx)
+        j, i = divmod(rem, nx)
+        ops, d = [float(f[k, j, i]), float(phi[k, j, i])], 6
+        for (ii, jj, kk, face) in ((i - 1, j, k, 0), (i + 1, j, k, 1), (i, j - 1, k, 2), (i, j + 1, k, 3),
+                                   (i, j, k - 1, 4), (i, j, k + 1, 5)):
+            if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz:
+                ops.append(float(phi[kk, jj, ii]))
+            else:
+                d += sh[bc[face]]
+        exact = Fraction(ops[0]) + sum(Fraction(v) for v in ops[2:]) - d * Fraction(ops[1])
+        bound = Fraction(np.spacing(max(abs(v) for v in ops))) / 2 + Fraction(np.spacing(abs(float(r)))) / 2
+        assert abs(Fraction(float(r)) - exact) <= bound, (q, r, float(exact))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
