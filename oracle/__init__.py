@@ -74,9 +74,11 @@ def _load():
                 "ccmg_or_solve": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
                 "ccmg_or_solve_mixed": (I, [P, P, I, I, I, D, P, I, I, D, D, I, I, P]),
                 "ccmg_or_efield": (None, [P, P, I, I, I, D, P, P]),
+                "ccmg_or_efield_stencil": (None, [P, P, I, I, I, D, P, P, I]),
                 "ccmg_or_sphere_density": (None, [P, I, I, I, D, I, P, P, P, I]),
                 "ccmg_or_sphere_density_adjoint": (None, [P, P, I, I, I, D, I, P, P, I]),
                 "ccmg_or_force_gather": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P]),
+                "ccmg_or_force_gather_stencil": (None, [P, I, I, I, D, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_adjoint": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -276,11 +278,16 @@ def solve_mixed(f, h: float, bc_type, tol: float = 1e-9, max_cycles: int = 100, 
 # --------------------------------------------------------------------------------------------
 # Fields and forces (Sec. 2.4: Eq. ElectrostatForce, central differences, subsampling)
 
-def efield(phi, h: float, bc_type, bc_value) -> np.ndarray:
-    """E = -grad phi by central differences with BC ghost values; returns [3, nz, ny, nx]."""
+def efield(phi, h: float, bc_type, bc_value, stencil: int = 7) -> np.ndarray:
+    """E = -grad phi; returns [3, nz, ny, nx]. stencil 7: central differences with BC ghost
+    values; 19: the D3Q19 gradient (Sec. 2.4) where all 18 neighbours are inside, else 7."""
     phi = _f64(phi)
     E = np.empty((3,) + phi.shape)
-    _load().ccmg_or_efield(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    if stencil == 7:
+        _load().ccmg_or_efield(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    else:
+        _load().ccmg_or_efield_stencil(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                       int(stencil))
     return E
 
 
@@ -310,13 +317,18 @@ def sphere_density_adjoint(gfield, h: float, centers, radius, sf: int = 2) -> np
     return g
 
 
-def force_gather(phi, h: float, bc_type, bc_value, centers, radius, density, sf: int = 2):
-    """F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce). Returns [P, 3]."""
+def force_gather(phi, h: float, bc_type, bc_value, centers, radius, density, sf: int = 2, stencil: int = 7):
+    """F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce), E by the gradient stencil
+    of efield (7 or 19). Returns [P, 3]."""
     phi = _f64(phi)
     c, r, d = _spheres(centers, radius, density)
     F = np.empty((c.shape[0], 3))
-    _load().ccmg_or_force_gather(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
-                                 c.shape[0], _p(c), _p(r), _p(d), sf, _p(F))
+    if stencil == 7:
+        _load().ccmg_or_force_gather(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                     c.shape[0], _p(c), _p(r), _p(d), sf, _p(F))
+    else:
+        _load().ccmg_or_force_gather_stencil(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                             c.shape[0], _p(c), _p(r), _p(d), sf, int(stencil), _p(F))
     return F
 
 

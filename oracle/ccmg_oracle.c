@@ -466,6 +466,49 @@ void ccmg_or_efield(const double* phi, double* E, int nx, int ny, int nz, double
       }
 }
 
+/* The isotropy-preserving D3Q19 gradient (Sec. 2.4, "Coulomb force"): with lattice directions
+ * e_q (6 face directions of weight 1/18, 12 edge directions of weight 1/36; the rest weight
+ * w_1 = 1/3), grad phi(x) ~ (1/w_1) sum_q w_q phi(x + e_q h) e_q / h. Used where all 18
+ * neighbours lie inside the domain; at the other cells the D3Q7 central differences with the
+ * face ghosts above ("where possible"). The directions are taken face directions first
+ * (+x,-x,+y,-y,+z,-z), then the edge directions (+a+b, -a-b, +a-b, -a+b) for the axis pairs
+ * (x,y), (x,z), (y,z); E_a = -grad_a phi. */
+static const int d3q19_dir[18][3] = {{1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                     {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1},
+                                     {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static int d3q19_inside(int i, int j, int k, int nx, int ny, int nz) {
+  return i > 0 && i < nx - 1 && j > 0 && j < ny - 1 && k > 0 && k < nz - 1;
+}
+
+static void efield_d3q19_at(const double* phi, int i, int j, int k, int nx, int ny, double h, double E[3]) {
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < 18; ++q) {
+    const int* e = d3q19_dir[q];
+    const double w = q < 6 ? 1.0 / 18.0 : 1.0 / 36.0;
+    const double v = phi[idx3(i + e[0], j + e[1], k + e[2], nx, ny)];
+    for (int a = 0; a < 3; ++a)
+      if (e[a] != 0) g[a] = g[a] + w * v * (double)e[a];
+  }
+  for (int a = 0; a < 3; ++a) E[a] = -(3.0 * g[a]) / h;  /* 1 / w_1 = 3 */
+}
+
+/* E-field with the chosen gradient stencil: 7 (D3Q7 everywhere) or 19 (D3Q19 where possible). */
+void ccmg_or_efield_stencil(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
+                            const double* bcv, int stencil) {
+  ccmg_or_efield(phi, E, nx, ny, nz, h, bc, bcv);
+  if (stencil != 19) return;
+  const size_t n = (size_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (!d3q19_inside(i, j, k, nx, ny, nz)) continue;
+        double e[3];
+        efield_d3q19_at(phi, i, j, k, nx, ny, h, e);
+        for (int a = 0; a < 3; ++a) E[(size_t)a * n + idx3(i, j, k, nx, ny)] = e[a];
+      }
+}
+
 /* Subsampled overlap count of sphere (centre c, radius R) with cell (i,j,k): the cell is cut
  * into sf^3 equal sub-cells and a sub-cell counts when its centre x satisfies |x - c|^2 <= R^2
  * (Sec. 2.4, "Subsampling"; sf = 1 is the plain cell-centre mapping of Sec. 2.2). Sub-cell
@@ -548,7 +591,39 @@ void ccmg_or_sphere_density_adjoint(const double* gfield, double* gdensity, int 
 
 /* Coulomb force on each sphere (Eq. ElectrostatForce with E = -grad phi):
  *   F_s = h^3 * sum_b w_{s,b} density_s E(x_b),
- * E by the central differences of ccmg_or_efield. forces is [P][3]. */
+ * E by the gradient stencil of ccmg_or_efield_stencil (7: central differences everywhere; 19:
+ * D3Q19 where possible). forces is [P][3]. */
+void ccmg_or_force_gather_stencil(const double* phi, int nx, int ny, int nz, double h, const int* bc,
+                                  const double* bcv, int P, const double* centers, const double* radius,
+                                  const double* density, int sf, int stencil, double* forces) {
+  const double h3 = h * h * h;
+  for (int s = 0; s < P; ++s) {
+    const double* c = centers + 3 * s;
+    int lo[3], hi[3];
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    double F[3] = {0.0, 0.0, 0.0};
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
+          if (w == 0.0) continue;
+          double E[3];
+          if (stencil == 19 && d3q19_inside(i, j, k, nx, ny, nz)) {
+            efield_d3q19_at(phi, i, j, k, nx, ny, h, E);
+          } else {
+            for (int a = 0; a < 3; ++a) {
+              const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
+              const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+              E[a] = -(up - dn) / (2.0 * h);
+            }
+          }
+          for (int a = 0; a < 3; ++a) F[a] = F[a] + w * E[a];
+        }
+    for (int a = 0; a < 3; ++a) forces[3 * s + a] = h3 * density[s] * F[a];
+  }
+}
+
 void ccmg_or_force_gather(const double* phi, int nx, int ny, int nz, double h, const int* bc,
                           const double* bcv, int P, const double* centers, const double* radius,
                           const double* density, int sf, double* forces) {

@@ -417,3 +417,71 @@ def test_mixed_precision_defect_correction(inner):
     ex = spectral.solve(f, 1.0, bc)  # exact discrete solution (the BC terms are part of f)
     assert np.linalg.norm(pm - pd) / np.linalg.norm(pd) < 1e-7
     assert np.linalg.norm(pm - ex) / np.linalg.norm(ex) < 1e-7
+
+
+# ------------------------------------------------------------------------------------------
+# The D3Q19 gradient (Sec. 2.4, "Coulomb force"): (1/w_1) sum_q w_q phi(x + e_q) e_q / h^2 with
+# D3Q19 weights, used where all 18 neighbours exist. Closed forms on polynomial fields; cell
+# centres at (i + 1/2) h.
+
+def _centres(n, h):
+    return (np.arange(n) + 0.5) * h
+
+
+def _interior(a):
+    return a[..., 1:-1, 1:-1, 1:-1]
+
+
+@pytest.mark.parametrize("h", [1.0, 0.25])
+def test_d3q19_gradient_exact_for_quadratics(h):
+    nx, ny, nz = 9, 8, 7
+    x, y, z = np.meshgrid(_centres(nx, h), _centres(ny, h), _centres(nz, h), indexing="xy")
+    x, y, z = (np.transpose(v, (2, 0, 1)).copy() for v in (x, y, z))  # [nz, ny, nx]
+    bc = (D,) * 6
+    phi = 0.7 * x - 1.3 * y + 0.4 * z + 0.25 * x * x - 0.5 * y * z + 2.0
+    E = oracle.efield(phi, h, bc, (0.0,) * 6, stencil=19)
+    ref = [-(0.7 + 0.5 * x), -(-1.3 - 0.5 * z), -(0.4 - 0.5 * y)]
+    for a in range(3):
+        assert np.abs(_interior(E[a]) - _interior(ref[a])).max() < 1e-12 / h
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5])
+def test_d3q19_gradient_of_x_y2_carries_the_edge_term(h):
+    """For phi = x y^2 the D3Q19 x-derivative is y^2 + h^2/3 (the edge directions contribute
+    h^2 sum_q w_q e_qx^2 e_qy^2 / w_1 = h^2 (4/36) 3), the y-derivative 2xy and the z-derivative 0
+    exactly, while the D3Q7 central difference gives y^2: a dropped or mis-weighted edge term, or
+    a wrong sign, fails here."""
+    nx, ny, nz = 8, 9, 6
+    x, y, z = np.meshgrid(_centres(nx, h), _centres(ny, h), _centres(nz, h), indexing="xy")
+    x, y, z = (np.transpose(v, (2, 0, 1)).copy() for v in (x, y, z))
+    phi = x * y * y
+    bc = (N,) * 4 + (D, D)
+    E19 = oracle.efield(phi, h, bc, (0.0,) * 6, stencil=19)
+    E7 = oracle.efield(phi, h, bc, (0.0,) * 6, stencil=7)
+    scale = np.abs(phi).max() / h
+    assert np.abs(_interior(E19[0]) + _interior(y * y + h * h / 3.0)).max() < 1e-13 * scale
+    assert np.abs(_interior(E19[1]) + _interior(2 * x * y)).max() < 1e-13 * scale
+    assert np.abs(_interior(E19[2])).max() < 1e-13 * scale
+    assert np.abs(_interior(E7[0]) + _interior(y * y)).max() < 1e-13 * scale
+    # cells without all 18 neighbours take the D3Q7 differences (ghosts included)
+    border = np.ones(phi.shape, bool)
+    border[1:-1, 1:-1, 1:-1] = False
+    assert np.array_equal(E19[:, border], E7[:, border])
+
+
+def test_d3q19_force_on_symmetric_sphere_in_uniform_field():
+    """As for the D3Q7 gradient: the self-force vanishes by reflection symmetry and the applied
+    field is linear, so F = Q_mapped * E_applied."""
+    n = 24
+    V = -10.0
+    bc = (N, N, N, N, D, D)
+    bcv = (0, 0, 0, 0, 0.0, V)
+    c = np.array([[n / 2, n / 2, n / 2]])
+    for sf in (1, 2):
+        rho = oracle.sphere_density((n, n, n), 1.0, c, [4.0], [1.5], sf)
+        f = oracle.rhs(rho, 1.0, bc, bcv)
+        phi, _, _ = oracle.solve(f, 1.0, bc, tol=1e-13, max_cycles=200)
+        F = oracle.force_gather(phi, 1.0, bc, bcv, c, [4.0], [1.5], sf, stencil=19)[0]
+        Q = rho.sum()
+        assert abs(F[2] - Q * (-V / n)) < 1e-9 * abs(Q * V / n)
+        assert abs(F[0]) < 1e-9 * abs(Q * V / n) and abs(F[1]) < 1e-9 * abs(Q * V / n)
