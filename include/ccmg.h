@@ -112,8 +112,20 @@ mg_status mg_solve(mg_ctx* ctx, double rel_tol, int max_cycles, int* h_cycles, d
 mg_status mg_residual(mg_ctx* ctx, double* h_rel_res, double* d_r);
 
 /* E = -grad(phi) by central differences (D3Q7), with the wall ghost values
- * (Dirichlet 2 g - phi, Neumann phi + h g). d_E: 3 arrays of nx*ny*nz doubles (Ex, Ey, Ez). */
+ * (Dirichlet 2 g - phi, Neumann phi + h g), or by the stencil mg_set_gradient_stencil chose.
+ * d_E: 3 arrays of nx*ny*nz doubles (Ex, Ey, Ez). */
 mg_status mg_efield(mg_ctx* ctx, double* d_E);
+
+/* Gradient stencil of mg_efield, mg_force_gather and mg_step_host (Sec. 2.4, "Coulomb force"):
+ *   7  (default) D3Q7 central differences everywhere, with the wall ghost values;
+ *   19 the isotropy-preserving D3Q19 stencil, grad phi ~ (1/w_1) sum_q w_q phi(x + e_q) e_q / h^2
+ *      (weights 1/3 rest, 1/18 faces, 1/36 edges), at every cell whose 18 neighbours lie in the
+ *      domain, and D3Q7 with ghosts at the others ("where possible").
+ * Other values return MG_ERR_INVALID and leave the setting unchanged. mg_force_gather_adjoint
+ * is implemented for the D3Q7 gradient only and returns MG_ERR_INVALID while 19 is set.
+ * mg_gradient_stencil returns the setting (-1 for a NULL context). */
+mg_status mg_set_gradient_stencil(mg_ctx* ctx, int stencil);
+int mg_gradient_stencil(const mg_ctx* ctx);
 
 /* Charge density of P spheres with subsampling factor sf (1..8): each cell is split into sf^3
  * sub-cells and rho(cell) = sum_s density_s * (sub-cells whose centre lies in sphere s) / sf^3
@@ -123,7 +135,7 @@ mg_status mg_sphere_density(mg_ctx* ctx, int P, const double* d_centers, const d
                             const double* d_density, int sf, double* d_rho);
 
 /* Coulomb force on each sphere, F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce,
- * E by the central differences of mg_efield, w the subsampled overlap). d_forces: P*3 doubles. */
+ * E by the gradient of mg_efield, w the subsampled overlap). d_forces: P*3 doubles. */
 mg_status mg_force_gather(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
                           const double* d_density, int sf, double* d_forces);
 

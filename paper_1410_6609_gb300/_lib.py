@@ -61,6 +61,8 @@ SIGNATURES = {
     "mg_solve": (_I, [_P, _D, _I, _P, _P]),
     "mg_residual": (_I, [_P, _P, _P]),
     "mg_efield": (_I, [_P, _P]),
+    "mg_set_gradient_stencil": (_I, [_P, _I]),
+    "mg_gradient_stencil": (_I, [_P]),
     "mg_sphere_density": (_I, [_P, _I, _P, _P, _P, _I, _P]),
     "mg_force_gather": (_I, [_P, _I, _P, _P, _P, _I, _P]),
     "mg_force_gather_adjoint": (_I, [_P, _I, _P, _P, _P, _I, _P, _P, _P, _P]),

@@ -55,6 +55,7 @@ struct mg_ctx {
   int sph_cap = 0;
   TmaSweep tma[kMaxLevels]{};  // TMA-staged single-precision half-sweeps, per level
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
+  int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
   std::string err;
 };
 
@@ -609,7 +610,7 @@ mg_status mg_efield(mg_ctx* c, double* d_E) {
   if (!d_E) return fail(c, MG_ERR_INVALID, "null output");
   mg_status st = materialize(c);
   if (st != MG_OK) return st;
-  CK(launch_efield(c->x64[0], c->geo[0], c->p.h, c->bc, d_E, c->stream), "efield");
+  CK(launch_efield(c->x64[0], c->geo[0], c->p.h, c->bc, c->grad_stencil, d_E, c->stream), "efield");
   c->launches += 1;
   return MG_OK;
 }
@@ -634,7 +635,7 @@ mg_status mg_force_gather(mg_ctx* c, int P, const double* ctr, const double* rad
   if ((P > 0 && (!dens || !d_F))) return fail(c, MG_ERR_INVALID, "null argument");
   Spheres sp{P, ctr, rad, dens};
   if ((st = materialize(c)) != MG_OK) return st;
-  CK(launch_force_gather(c->x64[0], c->geo[0], c->p.h, c->bc, sp, sf, d_F, c->stream), "force_gather");
+  CK(launch_force_gather(c->x64[0], c->geo[0], c->p.h, c->bc, c->grad_stencil, sp, sf, d_F, c->stream), "force_gather");
   c->launches += P > 0 ? 1 : 0;
   return MG_OK;
 }
@@ -645,6 +646,7 @@ mg_status mg_force_gather_adjoint(mg_ctx* c, int P, const double* ctr, const dou
   mg_status st = check_sph(c, P, ctr, rad, sf);
   if (st != MG_OK) return st;
   if (!d_gphi || !d_gbc || (P > 0 && (!dens || !d_wF || !d_gdens))) return fail(c, MG_ERR_INVALID, "null argument");
+  if (c->grad_stencil != 7) return fail(c, MG_ERR_INVALID, "the force adjoint is implemented for the D3Q7 gradient");
   Spheres sp{P, ctr, rad, dens};
   if ((st = materialize(c)) != MG_OK) return st;
   CK(launch_force_adjoint(c->x64[0], c->geo[0], c->p.h, c->bc, sp, sf, d_wF, d_gphi, d_gdens, d_gbc, c->stream),
@@ -652,6 +654,15 @@ mg_status mg_force_gather_adjoint(mg_ctx* c, int P, const double* ctr, const dou
   c->launches += P > 0 ? 1 : 0;
   return MG_OK;
 }
+
+mg_status mg_set_gradient_stencil(mg_ctx* c, int stencil) {
+  if (!c) return MG_ERR_INVALID;
+  if (stencil != 7 && stencil != 19) return fail(c, MG_ERR_INVALID, "the gradient stencil must be 7 or 19");
+  c->grad_stencil = stencil;
+  return MG_OK;
+}
+
+int mg_gradient_stencil(const mg_ctx* c) { return c ? c->grad_stencil : -1; }
 
 mg_status mg_sphere_density_adjoint(mg_ctx* c, int P, const double* ctr, const double* rad, int sf,
                                     const double* d_gfield, double* d_gdens) {

@@ -144,10 +144,13 @@ struct Spheres {
   const double* r;  // P
   const double* q;  // P (density), may be null where unused
 };
-cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, double* E, cudaStream_t s);
+// E = -grad phi, [3][N] natural order; stencil 7 (D3Q7 central differences) or 19 (D3Q19 where
+// all 18 neighbours exist, D3Q7 elsewhere).
+cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, int stencil, double* E,
+                          cudaStream_t s);
 cudaError_t launch_sphere_density(const Geom& G, double h, const Spheres& sp, int sf, double* rho, cudaStream_t s);
-cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
-                                double* F, cudaStream_t s);
+cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, int stencil,
+                                const Spheres& sp, int sf, double* F, cudaStream_t s);
 cudaError_t launch_force_adjoint(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
                                  const double* wF, double* gphi, double* gdens, double* gbc, cudaStream_t s);
 cudaError_t launch_density_adjoint(const Geom& G, double h, const Spheres& sp, int sf, const double* gfield,

@@ -4,7 +4,8 @@
 // (Eq. ElectrostatForce) with an O(h^2) finite-difference gradient; charges are mapped to cells by
 // subsampling each cell into sf^3 sub-cells and counting the sub-cell centres inside the sphere.
 // Here the gradient is the D3Q7 central difference, with wall ghost values Dirichlet 2g - phi and
-// Neumann phi + h g. The potential is read from the finest level's storage (packed colours, or
+// Neumann phi + h g, or (on request) the D3Q19 stencil of the same section where a cell's 18
+// neighbours all lie in the domain. The potential is read from the finest level's storage (packed colours, or
 // natural order for a single-level grid).
 //
 // The sub-cell inside test decides an integer count from floating point; it is evaluated with
@@ -76,6 +77,34 @@ __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Ge
       E[a] = -((up - dn) * inv2h);
     }
   }
+}
+
+// The D3Q19 gradient (Sec. 2.4, "Coulomb force"): grad phi ~ (1/w_1) sum_q w_q phi(x + e_q) e_q / h
+// with w_1 = 1/3, 1/18 for the 6 face and 1/36 for the 12 edge directions, taken in the order face
+// directions (+x,-x,+y,-y,+z,-z), then (+a+b, -a-b, +a-b, -a+b) for (x,y), (x,z), (y,z); every
+// product and sum rounded separately. For cells whose 18 neighbours all lie in the domain.
+__constant__ int kD3Q19[18][3] = {{1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},   {0, 0, -1},
+                                  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1},
+                                  {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+__device__ __forceinline__ bool d3q19_inside(const Geom& G, int i, int j, int k) {
+  return i > 0 && i < G.nx - 1 && j > 0 && j < G.ny - 1 && k > 0 && k < G.nz - 1;
+}
+
+__device__ __forceinline__ void efield19_at(const double* __restrict__ x, const Geom& G, int i, int j, int k, double h,
+                                            double E[3]) {
+  double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < 18; ++q) {
+    const int e0 = kD3Q19[q][0], e1 = kD3Q19[q][1], e2 = kD3Q19[q][2];
+    const double w = q < 6 ? 1.0 / 18.0 : 1.0 / 36.0;
+    const double wv = __dmul_rn(w, ld_phi(x, G, i + e0, j + e1, k + e2));
+    if (e0) g[0] = __dadd_rn(g[0], e0 > 0 ? wv : -wv);
+    if (e1) g[1] = __dadd_rn(g[1], e1 > 0 ? wv : -wv);
+    if (e2) g[2] = __dadd_rn(g[2], e2 > 0 ? wv : -wv);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) E[a] = __ddiv_rn(-__dmul_rn(3.0, g[a]), h);  // 1 / w_1 = 3
 }
 
 // SFC > 0: the loops run exactly SFC steps (sf == SFC, the common s_f = 2 compiled alone, which
@@ -156,6 +185,23 @@ __device__ void block_sum3(double v[3], double (*red)[3]) {
 }
 
 // ---------------------------------------------------------------------------------------------
+
+// E with the D3Q19 gradient where all 18 neighbours exist, D3Q7 central differences elsewhere.
+__global__ void __launch_bounds__(256) k_efield19(const double* __restrict__ x, Geom G, double h, double inv2h,
+                                                  FaceBC bc, double* __restrict__ E) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  double e[3];
+  if (d3q19_inside(G, i, j, k)) efield19_at(x, G, i, j, k, h, e);
+  else efield_at<false>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
+  const long long N = (long long)G.nx * G.ny * G.nz;
+  const long long p = nat(G, i, j, k);
+  E[p] = e[0];
+  E[N + p] = e[1];
+  E[2 * N + p] = e[2];
+}
 
 template <bool POW2>
 __global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Geom G, double h, double inv2h, int q2,
@@ -242,7 +288,7 @@ __global__ void __launch_bounds__(256) k_sphere_density(Geom G, double h, Sphere
 // One CTA per sphere: F_s = (h^3 density_s) * sum_b w_{s,b} E(x_b).
 template <int SFC>
 __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__ x, Geom G, double h, double inv2h,
-                                                      FaceBC bc, Spheres sp, int sf, SubOff so,
+                                                      FaceBC bc, Spheres sp, int sf, SubOff so, int st19,
                                                       double* __restrict__ F) {
   __shared__ double red[32][3];
   const int s = blockIdx.x;
@@ -260,7 +306,8 @@ __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__
     if (cnt == 0) continue;
     const double w = (double)cnt / sf3;
     double e[3];
-    efield_at<false>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
+    if (st19 && d3q19_inside(G, i, j, k)) efield19_at(x, G, i, j, k, h, e);
+    else efield_at<false>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
     for (int a = 0; a < 3; ++a) acc[a] = acc[a] + w * e[a];
   }
   block_sum3(acc, red);
@@ -411,9 +458,16 @@ SubOff make_suboff(int sf) {
 
 }  // namespace
 
-cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, double* E, cudaStream_t s) {
+cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC& bc, int stencil, double* E,
+                          cudaStream_t s) {
   const double inv2h = 1.0 / (2.0 * h);
   const int q2 = host_pow2_exponent(inv2h);
+  if (stencil == 19) {
+    const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
+    dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
+    k_efield19<<<g, b, 0, s>>>(x, G, h, inv2h, bc, E);
+    return cudaGetLastError();
+  }
   if (G.packed && reinterpret_cast<uintptr_t>(E) % 16 == 0) {
     const int bx = G.hx >= 128 ? 128 : (G.hx >= 64 ? 64 : 32);
     dim3 b(bx, 256 / bx, 1), g((G.hx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
@@ -440,12 +494,14 @@ cudaError_t launch_sphere_density(const Geom& G, double h, const Spheres& sp, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, const Spheres& sp, int sf,
-                                double* F, cudaStream_t s) {
+cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const FaceBC& bc, int stencil,
+                                const Spheres& sp, int sf, double* F, cudaStream_t s) {
   if (sp.P == 0) return cudaSuccess;
-  if (sf == 2) k_force_gather<2><<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
-  else if (sf == 1) k_force_gather<1><<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
-  else k_force_gather<0><<<sp.P, 256, 0, s>>>(x, G, h, 1.0 / (2.0 * h), bc, sp, sf, make_suboff(sf), F);
+  const int st19 = stencil == 19 ? 1 : 0;
+  const double inv2h = 1.0 / (2.0 * h);
+  if (sf == 2) k_force_gather<2><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, make_suboff(sf), st19, F);
+  else if (sf == 1) k_force_gather<1><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, make_suboff(sf), st19, F);
+  else k_force_gather<0><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, make_suboff(sf), st19, F);
   return cudaGetLastError();
 }
 

@@ -180,6 +180,15 @@ class Poisson:
         self._check(self.lib.mg_efield(self.ctx, _ptr(out)), "mg_efield")
         return out
 
+    @property
+    def gradient_stencil(self) -> int:
+        """Gradient of efield / force_gather / step: 7 (D3Q7) or 19 (D3Q19 where possible)."""
+        return int(self.lib.mg_gradient_stencil(self.ctx))
+
+    @gradient_stencil.setter
+    def gradient_stencil(self, stencil: int):
+        self._check(self.lib.mg_set_gradient_stencil(self.ctx, int(stencil)), "mg_set_gradient_stencil")
+
     @staticmethod
     def _sph(centers, radius, density=None):
         c = centers.contiguous()

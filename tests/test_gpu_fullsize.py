@@ -36,7 +36,11 @@ def _step(w):
     k, rel = P.solve(w.tol, 100)
     E = P.efield()
     F = P.force_gather(c, r, q, w.subsample)
-    out = dict(sp=sp, rho=rho.cpu().numpy(), k=k, rel=rel, phi=P.solution().cpu().numpy(), F=F.cpu().numpy())
+    P.gradient_stencil = 19
+    F19 = P.force_gather(c, r, q, w.subsample)
+    P.gradient_stencil = 7
+    out = dict(sp=sp, rho=rho.cpu().numpy(), k=k, rel=rel, phi=P.solution().cpu().numpy(), F=F.cpu().numpy(),
+               F19=F19.cpu().numpy())
     # E-field: all three components at 4096 random cells (the whole field is 3 GB at 512^3)
     rng = np.random.default_rng(0)
     nz, ny, nx = P.shape
@@ -72,6 +76,9 @@ def test_benchmark_step_at_full_size(name):
     F_ref = oracle.force_gather(g["phi"], w.h, w.bc_type, w.bc_value, sp.centers, sp.radius, sp.density,
                                 w.subsample)
     assert np.max(np.abs(g["F"] - F_ref)) <= 1e-12 * np.max(np.abs(F_ref))
+    F19_ref = oracle.force_gather(g["phi"], w.h, w.bc_type, w.bc_value, sp.centers, sp.radius, sp.density,
+                                  w.subsample, stencil=19)
+    assert np.max(np.abs(g["F19"] - F19_ref)) <= 1e-12 * np.max(np.abs(F19_ref))
     # sampled FP64 residuals against exact rational arithmetic on the GPU iterate: within half an
     # ulp of the cell's largest operand plus half an ulp of the result
     assert w.h == 1.0

@@ -168,6 +168,41 @@ def test_efield_and_forces_match_oracle():
     P2.close()
 
 
+@pytest.mark.parametrize("h", [1.0, 0.3])
+def test_d3q19_efield_and_forces_match_oracle(h):
+    """The D3Q19 gradient (Sec. 2.4) where all 18 neighbours exist, D3Q7 elsewhere: the GPU repeats
+    the oracle's per-cell operations, so interior E values are bit-identical; forces (sums over
+    cells in another order) to 1e-12. A non-power-of-two h exercises the division path. The
+    force adjoint refuses this stencil; other stencil values are rejected."""
+    dims = (40, 36, 32)
+    bc = (D, N, N, N, D, D)
+    bcv = (0.3, -0.7, 0.2, 0.0, -1.0, 1.0)
+    sp, c, r, q = _spheres_case(dims, 8, 4)
+    phi = synth.random_field(dims, 13)
+    P = Poisson(dims, h=h, bc_type=bc, bc_value=bcv)
+    assert P.gradient_stencil == 7
+    P.gradient_stencil = 19
+    assert P.gradient_stencil == 19
+    P.set_solution(gpu(phi))
+    E = cpu(P.efield())
+    Eref = oracle.efield(phi, h, bc, bcv, stencil=19)
+    assert np.array_equal(E[:, 1:-1, 1:-1, 1:-1], Eref[:, 1:-1, 1:-1, 1:-1])
+    assert maxrel(E, Eref) < 1e-15
+    assert maxrel(E, oracle.efield(phi, h, bc, bcv, stencil=7)) > 1e-3  # the stencils differ on this field
+    cs, rs = sp.centers * h, sp.radius * h
+    F = cpu(P.force_gather(gpu(cs), gpu(rs), q, 2))
+    Fref = oracle.force_gather(phi, h, bc, bcv, cs, rs, sp.density, 2, stencil=19)
+    assert maxrel(F, Fref) < 1e-12
+    with pytest.raises(Exception):
+        P.gradient_stencil = 5
+    assert P.gradient_stencil == 19
+    with pytest.raises(Exception):
+        P.force_gather_adjoint(gpu(cs), gpu(rs), q, gpu(np.ones((len(rs), 3))), 2)
+    P.gradient_stencil = 7
+    assert maxrel(cpu(P.efield()), oracle.efield(phi, h, bc, bcv)) < 1e-15
+    P.close()
+
+
 def test_adjoint_kernels_match_oracle():
     dims = (32, 32, 40)
     bc = (D, N, N, N, D, D)
