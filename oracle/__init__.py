@@ -75,10 +75,13 @@ def _load():
                 "ccmg_or_solve_mixed": (I, [P, P, I, I, I, D, P, I, I, D, D, I, I, P]),
                 "ccmg_or_efield": (None, [P, P, I, I, I, D, P, P]),
                 "ccmg_or_efield_stencil": (None, [P, P, I, I, I, D, P, P, I]),
+                "ccmg_or_efield_field": (None, [P, P, I, I, I, D, P, P, P, P, I]),
+                "ccmg_or_rhs_field": (None, [P, P, I, I, I, D, D, P, P, P, P]),
                 "ccmg_or_sphere_density": (None, [P, I, I, I, D, I, P, P, P, I]),
                 "ccmg_or_sphere_density_adjoint": (None, [P, P, I, I, I, D, I, P, P, I]),
                 "ccmg_or_force_gather": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P]),
                 "ccmg_or_force_gather_stencil": (None, [P, I, I, I, D, P, P, I, P, P, P, I, I, P]),
+                "ccmg_or_force_gather_field": (None, [P, I, I, I, D, P, P, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_adjoint": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -206,11 +209,35 @@ def prolong_correct(phi, ec, omega: float = 2.0) -> np.ndarray:
     return phi
 
 
-def rhs(rho, h: float, bc_type, bc_value, eps: float = 1.0) -> np.ndarray:
-    """f = rho/eps with Dirichlet (+2g/h^2) and Neumann (+g/h) face terms (Sec. 2.4, 4.3)."""
+def _bc_field(shape, bc_field):
+    """Per-cell boundary values for the C oracle: one slot per face (faces 0,1 [nz, ny], 2,3
+    [nz, nx], 4,5 [ny, nx]; None keeps the face's uniform value) -> (values, mask)."""
+    nz, ny, nx = shape
+    shapes = [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+    parts, on = [], np.zeros(6, dtype=np.int32)
+    for q in range(6):
+        v = None if bc_field is None else bc_field[q]
+        if v is None:
+            parts.append(np.zeros(shapes[q]).ravel())
+        else:
+            v = np.asarray(v, dtype=np.float64)
+            assert v.shape == shapes[q], (q, v.shape, shapes[q])
+            parts.append(v.ravel())
+            on[q] = 1
+    return np.ascontiguousarray(np.concatenate(parts)), on
+
+
+def rhs(rho, h: float, bc_type, bc_value, eps: float = 1.0, bc_field=None) -> np.ndarray:
+    """f = rho/eps with Dirichlet (+2g/h^2) and Neumann (+g/h) face terms (Sec. 2.4, 4.3); g per
+    face cell where bc_field gives the face an array (see _bc_field)."""
     rho = _f64(rho)
     f = np.empty_like(rho)
-    _load().ccmg_or_rhs(_p(rho), _p(f), *_dims(rho), h, eps, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    if bc_field is None:
+        _load().ccmg_or_rhs(_p(rho), _p(f), *_dims(rho), h, eps, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    else:
+        vals, on = _bc_field(rho.shape, bc_field)
+        _load().ccmg_or_rhs_field(_p(rho), _p(f), *_dims(rho), h, eps, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                  _p(vals), on.ctypes.data_as(ctypes.c_void_p))
     return f
 
 
@@ -278,12 +305,16 @@ def solve_mixed(f, h: float, bc_type, tol: float = 1e-9, max_cycles: int = 100, 
 # --------------------------------------------------------------------------------------------
 # Fields and forces (Sec. 2.4: Eq. ElectrostatForce, central differences, subsampling)
 
-def efield(phi, h: float, bc_type, bc_value, stencil: int = 7) -> np.ndarray:
+def efield(phi, h: float, bc_type, bc_value, stencil: int = 7, bc_field=None) -> np.ndarray:
     """E = -grad phi; returns [3, nz, ny, nx]. stencil 7: central differences with BC ghost
     values; 19: the D3Q19 gradient (Sec. 2.4) where all 18 neighbours are inside, else 7."""
     phi = _f64(phi)
     E = np.empty((3,) + phi.shape)
-    if stencil == 7:
+    if bc_field is not None:
+        vals, on = _bc_field(phi.shape, bc_field)
+        _load().ccmg_or_efield_field(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                     _p(vals), on.ctypes.data_as(ctypes.c_void_p), int(stencil))
+    elif stencil == 7:
         _load().ccmg_or_efield(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)))
     else:
         _load().ccmg_or_efield_stencil(_p(phi), _p(E), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
@@ -317,13 +348,19 @@ def sphere_density_adjoint(gfield, h: float, centers, radius, sf: int = 2) -> np
     return g
 
 
-def force_gather(phi, h: float, bc_type, bc_value, centers, radius, density, sf: int = 2, stencil: int = 7):
+def force_gather(phi, h: float, bc_type, bc_value, centers, radius, density, sf: int = 2, stencil: int = 7,
+                 bc_field=None):
     """F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce), E by the gradient stencil
-    of efield (7 or 19). Returns [P, 3]."""
+    of efield (7 or 19) with its boundary values. Returns [P, 3]."""
     phi = _f64(phi)
     c, r, d = _spheres(centers, radius, density)
     F = np.empty((c.shape[0], 3))
-    if stencil == 7:
+    if bc_field is not None:
+        vals, on = _bc_field(phi.shape, bc_field)
+        _load().ccmg_or_force_gather_field(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
+                                           _p(vals), on.ctypes.data_as(ctypes.c_void_p), c.shape[0], _p(c), _p(r),
+                                           _p(d), sf, int(stencil), _p(F))
+    elif stencil == 7:
         _load().ccmg_or_force_gather(_p(phi), *_dims(phi), h, _p(_bc(bc_type)), _p(_f64(bc_value)),
                                      c.shape[0], _p(c), _p(r), _p(d), sf, _p(F))
     else:

@@ -152,6 +152,44 @@ void ccmg_or_rhs(const double* rho, double* f, int nx, int ny, int nz, double h,
       }
 }
 
+/* Boundary values given per face cell (the validation runs of Sec. 5.3 prescribe the analytic
+ * potential on the boundary). bcf holds one slot per face, in face order: faces 0 and 1 (x)
+ * ny*nz values indexed j + ny k, faces 2 and 3 (y) nx*nz values indexed i + nx k, faces 4 and 5
+ * (z) nx*ny values indexed i + nx j; bcf_on[q] selects face q's slot over the uniform bcv[q]. The
+ * value belongs to the face of the boundary cell (i,j,k). */
+static double bc_at(int q, int i, int j, int k, int nx, int ny, int nz, const double* bcv, const double* bcf,
+                    const int* bcf_on) {
+  if (!bcf || !bcf_on || !bcf_on[q]) return bcv[q];
+  const size_t sx = (size_t)ny * nz, sy = (size_t)nx * nz, sz = (size_t)nx * ny;
+  const size_t off[6] = {0, sx, 2 * sx, 2 * sx + sy, 2 * sx + 2 * sy, 2 * sx + 2 * sy + sz};
+  size_t t;
+  if (q < 2) t = (size_t)j + (size_t)ny * k;
+  else if (q < 4) t = (size_t)i + (size_t)nx * k;
+  else t = (size_t)i + (size_t)nx * j;
+  return bcf[off[q] + t];
+}
+
+/* ccmg_or_rhs with per-cell boundary values (bc_at): the same terms in the same order. */
+void ccmg_or_rhs_field(const double* rho, double* f, int nx, int ny, int nz, double h, double eps, const int* bc,
+                       const double* bcv, const double* bcf, const int* bcf_on) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        double v = rho[p] / eps;
+        const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
+        for (int q = 0; q < 6; ++q) {
+          if (!on_face[q]) continue;
+          const double g = bc_at(q, i, j, k, nx, ny, nz, bcv, bcf, bcf_on);
+          if (bc[q] == BC_DIRICHLET)
+            v = v + 2.0 * g / (h * h);
+          else
+            v = v + g / h;
+        }
+        f[p] = v;
+      }
+}
+
 /* Adjoint of ccmg_or_rhs: given lambda = dJ/df, returns dJ/drho = lambda / eps and
  * dJ/dbc_value[q] = sum over the face-q cells of lambda * (2/h^2 Dirichlet, 1/h Neumann). */
 void ccmg_or_rhs_adjoint(const double* lam, double* grho, double* gbc, int nx, int ny, int nz,
@@ -450,6 +488,22 @@ static double phi_nb(const double* phi, int i, int j, int k, int nx, int ny, int
   return phi[idx3(q[0], q[1], q[2], nx, ny)];
 }
 
+/* phi_nb with per-cell boundary values (bc_at). */
+static double phi_nb_f(const double* phi, int i, int j, int k, int nx, int ny, int nz, int a, int dir, double h,
+                       const int* bc, const double* bcv, const double* bcf, const int* bcf_on) {
+  int q[3] = {i, j, k};
+  const int n[3] = {nx, ny, nz};
+  q[a] += dir;
+  const double here = phi[idx3(i, j, k, nx, ny)];
+  if (q[a] < 0 || q[a] >= n[a]) {
+    const int face = 2 * a + (dir > 0 ? 1 : 0);
+    const double g = bc_at(face, i, j, k, nx, ny, nz, bcv, bcf, bcf_on);
+    if (bc[face] == BC_DIRICHLET) return 2.0 * g - here;
+    return here + h * g;
+  }
+  return phi[idx3(q[0], q[1], q[2], nx, ny)];
+}
+
 /* E = -grad phi, E_a(i) = -(phi(i + e_a) - phi(i - e_a)) / (2h); out is [3][N] (SoA). */
 void ccmg_or_efield(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
                     const double* bcv) {
@@ -493,12 +547,22 @@ static void efield_d3q19_at(const double* phi, int i, int j, int k, int nx, int 
   for (int a = 0; a < 3; ++a) E[a] = -(3.0 * g[a]) / h;  /* 1 / w_1 = 3 */
 }
 
-/* E-field with the chosen gradient stencil: 7 (D3Q7 everywhere) or 19 (D3Q19 where possible). */
-void ccmg_or_efield_stencil(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
-                            const double* bcv, int stencil) {
-  ccmg_or_efield(phi, E, nx, ny, nz, h, bc, bcv);
-  if (stencil != 19) return;
+/* E-field with the chosen gradient stencil, 7 (D3Q7 everywhere) or 19 (D3Q19 where possible),
+ * and per-cell boundary values (bc_at; NULL bcf: the uniform ones). */
+void ccmg_or_efield_field(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
+                          const double* bcv, const double* bcf, const int* bcf_on, int stencil) {
   const size_t n = (size_t)nx * ny * nz;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        for (int a = 0; a < 3; ++a) {
+          const double up = phi_nb_f(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv, bcf, bcf_on);
+          const double dn = phi_nb_f(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv, bcf, bcf_on);
+          E[(size_t)a * n + p] = -(up - dn) / (2.0 * h);
+        }
+      }
+  if (stencil != 19) return;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -507,6 +571,11 @@ void ccmg_or_efield_stencil(const double* phi, double* E, int nx, int ny, int nz
         efield_d3q19_at(phi, i, j, k, nx, ny, h, e);
         for (int a = 0; a < 3; ++a) E[(size_t)a * n + idx3(i, j, k, nx, ny)] = e[a];
       }
+}
+
+void ccmg_or_efield_stencil(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
+                            const double* bcv, int stencil) {
+  ccmg_or_efield_field(phi, E, nx, ny, nz, h, bc, bcv, NULL, NULL, stencil);
 }
 
 /* Subsampled overlap count of sphere (centre c, radius R) with cell (i,j,k): the cell is cut
@@ -593,9 +662,10 @@ void ccmg_or_sphere_density_adjoint(const double* gfield, double* gdensity, int 
  *   F_s = h^3 * sum_b w_{s,b} density_s E(x_b),
  * E by the gradient stencil of ccmg_or_efield_stencil (7: central differences everywhere; 19:
  * D3Q19 where possible). forces is [P][3]. */
-void ccmg_or_force_gather_stencil(const double* phi, int nx, int ny, int nz, double h, const int* bc,
-                                  const double* bcv, int P, const double* centers, const double* radius,
-                                  const double* density, int sf, int stencil, double* forces) {
+void ccmg_or_force_gather_field(const double* phi, int nx, int ny, int nz, double h, const int* bc,
+                                const double* bcv, const double* bcf, const int* bcf_on, int P,
+                                const double* centers, const double* radius, const double* density, int sf,
+                                int stencil, double* forces) {
   const double h3 = h * h * h;
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
@@ -613,8 +683,8 @@ void ccmg_or_force_gather_stencil(const double* phi, int nx, int ny, int nz, dou
             efield_d3q19_at(phi, i, j, k, nx, ny, h, E);
           } else {
             for (int a = 0; a < 3; ++a) {
-              const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
-              const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+              const double up = phi_nb_f(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv, bcf, bcf_on);
+              const double dn = phi_nb_f(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv, bcf, bcf_on);
               E[a] = -(up - dn) / (2.0 * h);
             }
           }
@@ -622,6 +692,13 @@ void ccmg_or_force_gather_stencil(const double* phi, int nx, int ny, int nz, dou
         }
     for (int a = 0; a < 3; ++a) forces[3 * s + a] = h3 * density[s] * F[a];
   }
+}
+
+void ccmg_or_force_gather_stencil(const double* phi, int nx, int ny, int nz, double h, const int* bc,
+                                  const double* bcv, int P, const double* centers, const double* radius,
+                                  const double* density, int sf, int stencil, double* forces) {
+  ccmg_or_force_gather_field(phi, nx, ny, nz, h, bc, bcv, NULL, NULL, P, centers, radius, density, sf, stencil,
+                             forces);
 }
 
 void ccmg_or_force_gather(const double* phi, int nx, int ny, int nz, double h, const int* bc,

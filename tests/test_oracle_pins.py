@@ -485,3 +485,64 @@ def test_d3q19_force_on_symmetric_sphere_in_uniform_field():
         Q = rho.sum()
         assert abs(F[2] - Q * (-V / n)) < 1e-9 * abs(Q * V / n)
         assert abs(F[0]) < 1e-9 * abs(Q * V / n) and abs(F[1]) < 1e-9 * abs(Q * V / n)
+
+
+# ------------------------------------------------------------------------------------------
+# Boundary values per face cell (the validation runs of Sec. 5.3 prescribe the analytic potential
+# on the boundary): each face carries an array over its cells instead of one value.
+
+def _xy_fields(nx, ny, nz, h, a, b):
+    xc, yc = (np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h
+    phi = np.broadcast_to(a * xc[None, None, :] * yc[None, :, None] + b, (nz, ny, nx)).copy()
+    # faces: 0,1 [nz, ny]; 2,3 [nz, nx]; 4,5 [ny, nx]. Neumann values are outward derivatives.
+    fx = np.broadcast_to(a * yc[None, :], (nz, ny))
+    fy = np.broadcast_to(a * xc[None, :], (nz, nx))
+    fz = a * xc[None, :] * yc[:, None] + b
+    return phi, [-fx, fx, -fy, fy, fz, fz]
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5])
+def test_per_cell_boundary_values_reproduce_a_harmonic_field(h):
+    """phi = a x y + b is harmonic and its 7-point finite-volume Laplacian vanishes; with Neumann
+    values per face cell on the x and y faces (the outward derivative, varying along each face)
+    and Dirichlet values per face cell on the z faces, the ghosts are exact, so the discrete
+    solution and the E-field (boundary cells included) equal phi and -grad phi: a transposed or
+    shifted face index, or a wrong ghost sign, fails here."""
+    nx, ny, nz = 12, 10, 8
+    a, b = 0.37, -1.2
+    phi_ex, field = _xy_fields(nx, ny, nz, h, a, b)
+    bc = (N, N, N, N, D, D)
+    f = oracle.rhs(np.zeros((nz, ny, nx)), h, bc, (0.0,) * 6, bc_field=field)
+    phi, _, _ = oracle.solve(f, h, bc, tol=1e-14, max_cycles=100)
+    assert np.abs(phi - phi_ex).max() < 1e-11 * np.abs(phi_ex).max()
+    xc, yc = (np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h
+    for stencil in (7, 19):
+        E = oracle.efield(phi_ex, h, bc, (0.0,) * 6, stencil=stencil, bc_field=field)
+        assert np.abs(E[0] + a * yc[None, :, None]).max() < 1e-12 * a * yc.max()
+        assert np.abs(E[1] + a * xc[None, None, :]).max() < 1e-12 * a * xc.max()
+        assert np.abs(E[2]).max() < 1e-12 * a * xc.max()
+    # the uniform slots still apply to faces without an array
+    f2 = oracle.rhs(np.zeros((nz, ny, nx)), h, bc, (0.0, 0.0, 0.0, 0.0, 0.5, -0.5),
+                    bc_field=field[:4] + [None, None])
+    f3 = oracle.rhs(np.zeros((nz, ny, nx)), h, bc, (0.0,) * 6,
+                    bc_field=field[:4] + [np.full((ny, nx), 0.5), np.full((ny, nx), -0.5)])
+    assert np.array_equal(f2, f3)
+
+
+def test_per_cell_dirichlet_values_of_a_linear_field():
+    """Dirichlet values per face cell taken from a linear potential on all six faces (each face
+    array varies in both of its directions) reproduce the potential exactly."""
+    nx, ny, nz, h = 10, 12, 14, 0.25
+    xc, yc, zc = ((np.arange(n) + 0.5) * h for n in (nx, ny, nz))
+    g = np.array([0.3, -0.8, 0.55])
+    lin = lambda x, y, z: g[0] * x + g[1] * y + g[2] * z + 0.1
+    X, Y, Z = xc[None, None, :], yc[None, :, None], zc[:, None, None]
+    phi_ex = lin(X, Y, Z) + 0 * (X + Y + Z)
+    Lx, Ly, Lz = nx * h, ny * h, nz * h
+    field = [lin(0.0, yc[None, :], zc[:, None]), lin(Lx, yc[None, :], zc[:, None]),
+             lin(xc[None, :], 0.0, zc[:, None]), lin(xc[None, :], Ly, zc[:, None]),
+             lin(xc[None, :], yc[:, None], 0.0), lin(xc[None, :], yc[:, None], Lz)]
+    bc = (D,) * 6
+    f = oracle.rhs(np.zeros((nz, ny, nx)), h, bc, (0.0,) * 6, bc_field=field)
+    phi, _, _ = oracle.solve(f, h, bc, tol=1e-14, max_cycles=100)
+    assert np.abs(phi - phi_ex).max() < 1e-11 * np.abs(phi_ex).max()
