@@ -84,6 +84,17 @@ mg_status mg_level_dims(const mg_ctx* ctx, int level, int* h_dims3);
  * mg_set_rhs, mg_efield, mg_force_gather and mg_force_gather_adjoint call. */
 mg_status mg_set_bc_values(mg_ctx* ctx, const double* h_bc_value6);
 
+/* Wall values per face cell for face `face` (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z), as the validation
+ * runs of Sec. 5.3 set the boundary to the analytic potential: d_values (device) holds one
+ * double per boundary cell of the face, faces 0 and 1 ny*nz values indexed j + ny*k, faces 2 and
+ * 3 nx*nz indexed i + nx*k, faces 4 and 5 nx*ny indexed i + nx*j; each is the Dirichlet value or
+ * the outward normal derivative (Neumann) of that cell's face, entering the right-hand side
+ * (2 g / h^2 or g / h, Sec. 2.4) and the ghost values of mg_efield, mg_force_gather and their
+ * adjoint. The array is copied (the call returns after the copy); NULL returns the face to its
+ * uniform value. Takes effect like mg_set_bc_values. Errors: MG_ERR_INVALID for a bad face,
+ * MG_ERR_OOM / MG_ERR_CUDA if the copy cannot be made. Batched solves have no per-cell values. */
+mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
+
 /* Right-hand side from a charge density: f = rho/eps, then adapted to the wall values once
  * on the finest grid (Sec. 2.4 and Sec. 4.3: Dirichlet face cells += 2 g / h^2, Neumann face
  * cells += g / h). d_rho: nx*ny*nz doubles. */

@@ -62,6 +62,7 @@ SIGNATURES = {
     "mg_residual": (_I, [_P, _P, _P]),
     "mg_efield": (_I, [_P, _P]),
     "mg_set_gradient_stencil": (_I, [_P, _I]),
+    "mg_set_bc_field": (_I, [_P, _I, _P]),
     "mg_gradient_stencil": (_I, [_P]),
     "mg_sphere_density": (_I, [_P, _I, _P, _P, _P, _I, _P]),
     "mg_force_gather": (_I, [_P, _I, _P, _P, _P, _I, _P]),

@@ -56,6 +56,7 @@ struct mg_ctx {
   TmaSweep tma[kMaxLevels]{};  // TMA-staged single-precision half-sweeps, per level
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
+  double* d_bcf[6] = {};       // per-cell wall values of each face (allocated on first use)
   std::string err;
 };
 
@@ -92,6 +93,7 @@ void free_all(mg_ctx* c) {
     cudaFree(c->x32[l]);
     cudaFree(c->g32[l]);
   }
+  for (int q = 0; q < 6; ++q) cudaFree(c->d_bcf[q]);
   cudaFree(c->partials);
   cudaFree(c->scal);
   cudaFree(c->d_iters);
@@ -501,6 +503,29 @@ mg_status mg_set_bc_values(mg_ctx* c, const double* v) {
     c->bc.value[q] = v[q];
     c->p.bc_value[q] = v[q];
   }
+  return MG_OK;
+}
+
+mg_status mg_set_bc_field(mg_ctx* c, int face, const double* d_values) {
+  if (!c) return MG_ERR_INVALID;
+  if (face < 0 || face > 5) return fail(c, MG_ERR_INVALID, "face must be 0..5");
+  if (!d_values) {
+    c->bc.field[face] = nullptr;
+    return MG_OK;
+  }
+  const Geom& G = c->geo[0];
+  const size_t bytes = (size_t)face_cells(face, G.nx, G.ny, G.nz) * sizeof(double);
+  if (!c->d_bcf[face]) {
+    const cudaError_t e = cudaMalloc((void**)&c->d_bcf[face], bytes);
+    if (e != cudaSuccess) {
+      c->d_bcf[face] = nullptr;
+      cudaGetLastError();
+      return fail(c, e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA, "bc field allocation");
+    }
+  }
+  CK(cudaMemcpyAsync(c->d_bcf[face], d_values, bytes, cudaMemcpyDeviceToDevice, c->stream), "set_bc_field");
+  CK(cudaStreamSynchronize(c->stream), "set_bc_field");  // the caller's array is free on return
+  c->bc.field[face] = c->d_bcf[face];
   return MG_OK;
 }
 

@@ -40,10 +40,35 @@ struct InvDiag {
   T v[7];  // 1 / (6 + d) for d = -3 .. 3
 };
 
+// Wall conditions of the six faces (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z): type 0 Dirichlet, 1 Neumann,
+// with one value per face, or, where field[q] is set, one value per face cell (faces 0,1: index
+// j + ny k; 2,3: i + nx k; 4,5: i + nx j), device memory the context owns.
 struct FaceBC {
   int type[6];
   double value[6];
+  const double* field[6];
 };
+
+// Index of boundary cell (i, j, k) in face q's per-cell array, and the number of face cells.
+__host__ __device__ __forceinline__ long long face_index(int q, int i, int j, int k, int nx, int ny) {
+  return q < 2 ? (long long)j + (long long)ny * k
+               : (q < 4 ? (long long)i + (long long)nx * k : (long long)i + (long long)nx * j);
+}
+__host__ __device__ __forceinline__ long long face_cells(int q, int nx, int ny, int nz) {
+  return q < 2 ? (long long)ny * nz : (q < 4 ? (long long)nx * nz : (long long)nx * ny);
+}
+
+inline bool has_field(const FaceBC& bc) {
+  for (int q = 0; q < 6; ++q)
+    if (bc.field[q]) return true;
+  return false;
+}
+
+// The value of face q's condition at its boundary cell (i, j, k).
+__device__ __forceinline__ double face_value(const FaceBC& bc, int q, int i, int j, int k, int nx, int ny) {
+  const double* f = bc.field[q];
+  return f ? __ldg(f + face_index(q, i, j, k, nx, ny)) : bc.value[q];
+}
 
 // Kernel launchers (all enqueue on `s`; return cudaGetLastError()).
 template <typename T>

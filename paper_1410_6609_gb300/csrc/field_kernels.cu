@@ -38,6 +38,9 @@ __device__ __forceinline__ double ld_phi(const double* __restrict__ x, const Geo
 }
 
 // phi at the neighbour of (i,j,k) along axis a in direction dir, or the wall ghost value.
+// FIELD: the faces may carry values per cell (FaceBC::field); the kernels are compiled both ways
+// so that the common uniform case keeps its small register footprint.
+template <bool FIELD = true>
 __device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geom& G, int i, int j, int k, int a,
                                          int dir, double here, double h, const FaceBC& bc) {
   int q[3] = {i, j, k};
@@ -45,8 +48,9 @@ __device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geo
   q[a] += dir;
   if (q[a] < 0 || q[a] >= n[a]) {
     const int face = 2 * a + (dir > 0 ? 1 : 0);
-    if (bc.type[face] == 0) return 2.0 * bc.value[face] - here;
-    return here + h * bc.value[face];
+    const double g = FIELD ? face_value(bc, face, i, j, k, G.nx, G.ny) : bc.value[face];
+    if (bc.type[face] == 0) return 2.0 * g - here;
+    return here + h * g;
   }
   return ld_phi(x, G, q[0], q[1], q[2]);
 }
@@ -57,7 +61,7 @@ __device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geo
 // -((up - dn) * inv2h) exactly.
 // POW2: inv2h = 2^q2 (a power-of-two cell size); the interior products are then exponent shifts
 // (ldexp_rne), equal to the FP64 multiply.
-template <bool POW2>
+template <bool POW2, bool FIELD = true>
 __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Geom& G, int i, int j, int k, double h,
                                           double inv2h, int q2, const FaceBC& bc, double E[3]) {
   const bool interior = i > 0 && i < G.nx - 1 && j > 0 && j < G.ny - 1 && k > 0 && k < G.nz - 1;
@@ -72,8 +76,8 @@ __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Ge
     const double here = ld_phi(x, G, i, j, k);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double up = phi_nb(x, G, i, j, k, a, +1, here, h, bc);
-      const double dn = phi_nb(x, G, i, j, k, a, -1, here, h, bc);
+      const double up = phi_nb<FIELD>(x, G, i, j, k, a, +1, here, h, bc);
+      const double dn = phi_nb<FIELD>(x, G, i, j, k, a, -1, here, h, bc);
       E[a] = -((up - dn) * inv2h);
     }
   }
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(256) k_efield19(const double* __restrict__ x, 
   E[2 * N + p] = e[2];
 }
 
-template <bool POW2>
+template <bool POW2, bool FIELD>
 __global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Geom G, double h, double inv2h, int q2,
                                                 FaceBC bc,
                                                 double* __restrict__ E) {
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Ge
   const int k = blockIdx.z;
   if (i >= G.nx || j >= G.ny) return;
   double e[3];
-  efield_at<POW2>(x, G, i, j, k, h, inv2h, q2, bc, e);
+  efield_at<POW2, FIELD>(x, G, i, j, k, h, inv2h, q2, bc, e);
   const long long N = (long long)G.nx * G.ny * G.nz;
   const long long p = nat(G, i, j, k);
   E[p] = e[0];
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Ge
 // colours in the four neighbour rows) and its 16-byte stores of each component are contiguous.
 // Interior pairs take the differences directly, in efield_at's order; pairs at a wall call
 // efield_at per cell.
-template <bool POW2>
+template <bool POW2, bool FIELD>
 __global__ void __launch_bounds__(256) k_efield_pair(const double* __restrict__ x, Geom G, double h, double inv2h,
                                                      int q2, FaceBC bc, double* __restrict__ E) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,8 +261,8 @@ __global__ void __launch_bounds__(256) k_efield_pair(const double* __restrict__ 
     e1[1] = POW2 ? ldexp_rne(d11, q2) : d11 * inv2h;
     e1[2] = POW2 ? ldexp_rne(d12, q2) : d12 * inv2h;
   } else {
-    efield_at<POW2>(x, G, i0, j, k, h, inv2h, q2, bc, e0);
-    efield_at<POW2>(x, G, i0 + 1, j, k, h, inv2h, q2, bc, e1);
+    efield_at<POW2, FIELD>(x, G, i0, j, k, h, inv2h, q2, bc, e0);
+    efield_at<POW2, FIELD>(x, G, i0 + 1, j, k, h, inv2h, q2, bc, e1);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) *reinterpret_cast<double2*>(E + a * N + p) = make_double2(e0[a], e1[a]);
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(256) k_sphere_density(Geom G, double h, Sphere
 }
 
 // One CTA per sphere: F_s = (h^3 density_s) * sum_b w_{s,b} E(x_b).
-template <int SFC>
+template <int SFC, bool FIELD>
 __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__ x, Geom G, double h, double inv2h,
                                                       FaceBC bc, Spheres sp, int sf, SubOff so, int st19,
                                                       double* __restrict__ F) {
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__
     const double w = (double)cnt / sf3;
     double e[3];
     if (st19 && d3q19_inside(G, i, j, k)) efield19_at(x, G, i, j, k, h, e);
-    else efield_at<false>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
+    else efield_at<false, FIELD>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
     for (int a = 0; a < 3; ++a) acc[a] = acc[a] + w * e[a];
   }
   block_sum3(acc, red);
@@ -462,6 +466,7 @@ cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC
                           cudaStream_t s) {
   const double inv2h = 1.0 / (2.0 * h);
   const int q2 = host_pow2_exponent(inv2h);
+  const bool fld = has_field(bc);
   if (stencil == 19) {
     const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
     dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
@@ -471,16 +476,24 @@ cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC
   if (G.packed && reinterpret_cast<uintptr_t>(E) % 16 == 0) {
     const int bx = G.hx >= 128 ? 128 : (G.hx >= 64 ? 64 : 32);
     dim3 b(bx, 256 / bx, 1), g((G.hx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
-    if (q2 != kBadPow2) k_efield_pair<true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
-    else k_efield_pair<false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    if (fld) {
+      if (q2 != kBadPow2) k_efield_pair<true, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+      else k_efield_pair<false, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    } else {
+      if (q2 != kBadPow2) k_efield_pair<true, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+      else k_efield_pair<false, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    }
     return cudaGetLastError();
   }
   const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
   dim3 b(bx, 256 / bx, 1), g((G.nx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
-  if (q2 != kBadPow2)
-    k_efield<true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
-  else
-    k_efield<false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+  if (fld) {
+    if (q2 != kBadPow2) k_efield<true, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    else k_efield<false, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+  } else {
+    if (q2 != kBadPow2) k_efield<true, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    else k_efield<false, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+  }
   return cudaGetLastError();
 }
 
@@ -499,9 +512,16 @@ cudaError_t launch_force_gather(const double* x, const Geom& G, double h, const 
   if (sp.P == 0) return cudaSuccess;
   const int st19 = stencil == 19 ? 1 : 0;
   const double inv2h = 1.0 / (2.0 * h);
-  if (sf == 2) k_force_gather<2><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, make_suboff(sf), st19, F);
-  else if (sf == 1) k_force_gather<1><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, make_suboff(sf), st19, F);
-  else k_force_gather<0><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, make_suboff(sf), st19, F);
+  const SubOff so = make_suboff(sf);
+  if (has_field(bc)) {
+    if (sf == 2) k_force_gather<2, true><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, so, st19, F);
+    else if (sf == 1) k_force_gather<1, true><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, so, st19, F);
+    else k_force_gather<0, true><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, so, st19, F);
+  } else {
+    if (sf == 2) k_force_gather<2, false><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, so, st19, F);
+    else if (sf == 1) k_force_gather<1, false><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, so, st19, F);
+    else k_force_gather<0, false><<<sp.P, 256, 0, s>>>(x, G, h, inv2h, bc, sp, sf, so, st19, F);
+  }
   return cudaGetLastError();
 }
 

@@ -132,22 +132,35 @@ __global__ void k_set_scale(double* scal, int src, int dst, double n) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Right-hand side (Sec. 2.4 and Sec. 4.3, "the RHS is adapted to the BCs ... only on the finest
-// grid"): f = rho/eps + wall terms (term[q] precomputed per face), stored scaled, g = f * h^2.
+// Right-hand side (Sec. 2.4 and Sec. 4.3: the wall conditions enter the right-hand side once, on
+// the finest grid): f = rho/eps + wall terms, stored scaled, g = f * h^2. A face with one value
+// has its term precomputed (t[q]); a face with values per cell computes 2 g / h^2 (Dirichlet) or
+// g / h (Neumann) per cell with the same operations.
 struct WallTerms {
   double t[6];
+  const double* field[6];
+  int type[6];
+  double h;
 };
+__device__ __forceinline__ double wall_term(const WallTerms& wt, int q, int i, int j, int k, const Geom& G) {
+  if (!wt.field[q]) return wt.t[q];
+  const double g = __ldg(wt.field[q] + face_index(q, i, j, k, G.nx, G.ny));
+  return wt.type[q] == 0 ? 2.0 * g / (wt.h * wt.h) : g / wt.h;
+}
+// FIELD: some face carries values per cell (the kernels are compiled both ways, so the common
+// uniform case keeps its small register footprint).
+template <bool FIELD>
 __device__ __forceinline__ double add_wall_terms(double v, int i, int j, int k, const Geom& G, const WallTerms& wt) {
-  if (i == 0) v = v + wt.t[0];
-  if (i == G.nx - 1) v = v + wt.t[1];
-  if (j == 0) v = v + wt.t[2];
-  if (j == G.ny - 1) v = v + wt.t[3];
-  if (k == 0) v = v + wt.t[4];
-  if (k == G.nz - 1) v = v + wt.t[5];
+  if (i == 0) v = v + (FIELD ? wall_term(wt, 0, i, j, k, G) : wt.t[0]);
+  if (i == G.nx - 1) v = v + (FIELD ? wall_term(wt, 1, i, j, k, G) : wt.t[1]);
+  if (j == 0) v = v + (FIELD ? wall_term(wt, 2, i, j, k, G) : wt.t[2]);
+  if (j == G.ny - 1) v = v + (FIELD ? wall_term(wt, 3, i, j, k, G) : wt.t[3]);
+  if (k == 0) v = v + (FIELD ? wall_term(wt, 4, i, j, k, G) : wt.t[4]);
+  if (k == G.nz - 1) v = v + (FIELD ? wall_term(wt, 5, i, j, k, G) : wt.t[5]);
   return v;
 }
 // POW2: 1/eps = 2^qe and h^2 = 2^qh (lattice units), the products are exponent shifts.
-template <typename T, bool POW2>
+template <typename T, bool POW2, bool FIELD>
 __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
                                                  double inv_eps, double hsq, int qe, int qh, WallTerms wt, int raw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,7 +174,7 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
     // only warps holding wall cells add wall terms (a warp vote keeps the compiler from turning
     // the rare branches into FP64 adds of zero by every cell)
     const bool wall = i == 0 || i == G.nx - 1 || j == 0 || j == G.ny - 1 || k == 0 || k == G.nz - 1;
-    if (__any_sync(__activemask(), wall)) v = add_wall_terms(v, i, j, k, G, wt);
+    if (__any_sync(__activemask(), wall)) v = add_wall_terms<FIELD>(v, i, j, k, G, wt);
   }
   long long o = p;
   if (G.packed) o = (long long)((i + j + k) & 1) * G.csz + ((long long)k * G.ny + j) * G.hx + (i >> 1);
@@ -171,7 +184,7 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
 // The same for a packed level, two cells per thread: cells 2m and 2m+1 of row (j, k) are one
 // 16-byte load of rho and land at index m of the two colour arrays, so both the loads and the
 // stores of a warp are contiguous.
-template <typename T, bool POW2>
+template <typename T, bool POW2, bool FIELD>
 __global__ void __launch_bounds__(256) k_set_rhs_pair(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
                                                       double inv_eps, double hsq, int qe, int qh, WallTerms wt,
                                                       int raw) {
@@ -188,8 +201,8 @@ __global__ void __launch_bounds__(256) k_set_rhs_pair(T* __restrict__ gout, Geom
     v1 = POW2 ? ldexp_rne(v1, qe) : v1 * inv_eps;
     const bool wall = i0 == 0 || i0 + 1 == G.nx - 1 || j == 0 || j == G.ny - 1 || k == 0 || k == G.nz - 1;
     if (__any_sync(__activemask(), wall)) {
-      v0 = add_wall_terms(v0, i0, j, k, G, wt);
-      v1 = add_wall_terms(v1, i0 + 1, j, k, G, wt);
+      v0 = add_wall_terms<FIELD>(v0, i0, j, k, G, wt);
+      v1 = add_wall_terms<FIELD>(v1, i0 + 1, j, k, G, wt);
     }
   }
   const int c0 = (i0 + j + k) & 1;
@@ -439,21 +452,36 @@ template <typename T>
 cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_eps, double h, const FaceBC& bc, int raw,
                            cudaStream_t s) {
   WallTerms wt;
-  for (int q = 0; q < 6; ++q)
+  for (int q = 0; q < 6; ++q) {
     wt.t[q] = bc.type[q] == 0 ? 2.0 * bc.value[q] / (h * h) : bc.value[q] / h;
+    wt.field[q] = bc.field[q];
+    wt.type[q] = bc.type[q];
+  }
+  wt.h = h;
+  const bool fld = has_field(bc);
   dim3 b, gr;
   const double hsq = h * h;
   const int qe = host_pow2_exponent(inv_eps), qh = host_pow2_exponent(hsq);
   const bool pow2 = qe != kBadPow2 && qh != kBadPow2;
   if (G.packed && reinterpret_cast<uintptr_t>(rho) % 16 == 0) {
     shape(G.hx, G.ny, G.nz, b, gr);
-    if (pow2) k_set_rhs_pair<T, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
-    else k_set_rhs_pair<T, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    if (fld) {
+      if (pow2) k_set_rhs_pair<T, true, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+      else k_set_rhs_pair<T, false, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    } else {
+      if (pow2) k_set_rhs_pair<T, true, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+      else k_set_rhs_pair<T, false, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    }
     return cudaGetLastError();
   }
   shape(G.nx, G.ny, G.nz, b, gr);
-  if (pow2) k_set_rhs<T, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
-  else k_set_rhs<T, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+  if (fld) {
+    if (pow2) k_set_rhs<T, true, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    else k_set_rhs<T, false, true><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+  } else {
+    if (pow2) k_set_rhs<T, true, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+    else k_set_rhs<T, false, false><<<gr, b, 0, s>>>(g, G, rho, inv_eps, hsq, qe, qh, wt, raw);
+  }
   return cudaGetLastError();
 }
 

@@ -180,6 +180,17 @@ class Poisson:
         self._check(self.lib.mg_efield(self.ctx, _ptr(out)), "mg_efield")
         return out
 
+    def set_bc_field(self, face: int, values=None):
+        """Wall values per cell of one face (None: back to the face's uniform value); values is a
+        float64 tensor on the device of shape [nz, ny] (faces 0, 1), [nz, nx] (2, 3) or [ny, nx] (4, 5)."""
+        nx, ny, nz = self.dims
+        shapes = [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+        if values is None:
+            self._check(self.lib.mg_set_bc_field(self.ctx, int(face), None), "mg_set_bc_field")
+            return
+        t = self._field(values, "bc field", shapes[int(face)] if 0 <= int(face) < 6 else (0,))
+        self._check(self.lib.mg_set_bc_field(self.ctx, int(face), _ptr(t)), "mg_set_bc_field")
+
     @property
     def gradient_stencil(self) -> int:
         """Gradient of efield / force_gather / step: 7 (D3Q7) or 19 (D3Q19 where possible)."""

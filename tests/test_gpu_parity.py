@@ -447,3 +447,53 @@ def test_fp64_residual_against_exact_arithmetic(dims, bc):
         err = abs(Fraction(float(r[idx])) - exact)
         worst = max(worst, float(err / bound))
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5])
+def test_per_cell_wall_values_match_oracle(h):
+    """Wall values per face cell (mg_set_bc_field): the right-hand side equals the oracle's bit for
+    bit, the harmonic field a x y + b (per-cell Neumann on x/y, Dirichlet on z) is reproduced by
+    the FP64 solve, and the E-field (both stencils) and forces with these ghosts match the oracle;
+    clearing a face's array restores its uniform value."""
+    nx, ny, nz = 48, 40, 32
+    a, b = 0.37, -1.2
+    xc, yc = (np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h
+    phi_ex = np.broadcast_to(a * xc[None, None, :] * yc[None, :, None] + b, (nz, ny, nx)).copy()
+    fx = np.broadcast_to(a * yc[None, :], (nz, ny))
+    fy = np.broadcast_to(a * xc[None, :], (nz, nx))
+    fz = a * xc[None, :] * yc[:, None] + b
+    field = [-fx, fx, -fy, fy, fz, fz]
+    bc = (N, N, N, N, D, D)
+    bcv = (0.1, -0.2, 0.3, -0.4, 0.5, -0.6)  # overridden by the arrays
+    P = Poisson((nx, ny, nz), h=h, bc_type=bc, bc_value=bcv)
+    for q in range(6):
+        P.set_bc_field(q, gpu(field[q]))
+    rho = synth.random_field((nx, ny, nz), 4) * 0.0
+    P.set_rhs(gpu(rho))
+    f_ref = oracle.rhs(rho, h, bc, bcv, bc_field=field)
+    assert np.array_equal(cpu(P.level_get(0, 1)), f_ref)
+    P.set_solution(None)
+    k, rel = P.solve(1e-12, 50)
+    assert np.abs(cpu(P.solution()) - phi_ex).max() < 1e-9 * np.abs(phi_ex).max()
+    # E-field and forces on a random potential with these ghosts
+    phi = synth.random_field((nx, ny, nz), 11)
+    P.set_solution(gpu(phi))
+    sp, c, r, q = _spheres_case((nx, ny, nz), 6, 8)
+    cs, rs = sp.centers * h, sp.radius * h
+    for stencil in (7, 19):
+        P.gradient_stencil = stencil
+        E_ref = oracle.efield(phi, h, bc, bcv, stencil=stencil, bc_field=field)
+        assert maxrel(cpu(P.efield()), E_ref) < 1e-15
+        F_ref = oracle.force_gather(phi, h, bc, bcv, cs, rs, sp.density, 2, stencil=stencil, bc_field=field)
+        assert maxrel(cpu(P.force_gather(gpu(cs), gpu(rs), q, 2)), F_ref) < 1e-12
+    P.gradient_stencil = 7
+    # back to uniform values on the z faces
+    P.set_bc_field(4, None)
+    P.set_bc_field(5, None)
+    field_u = field[:4] + [None, None]
+    assert maxrel(cpu(P.efield()), oracle.efield(phi, h, bc, bcv, bc_field=field_u)) < 1e-15
+    P.set_rhs(gpu(rho))
+    assert np.array_equal(cpu(P.level_get(0, 1)), oracle.rhs(rho, h, bc, bcv, bc_field=field_u))
+    with pytest.raises(Exception):
+        P.set_bc_field(6, gpu(field[0]))
+    P.close()
