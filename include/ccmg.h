@@ -131,7 +131,7 @@ mg_status mg_efield(mg_ctx* ctx, double* d_E);
  *   7  (default) D3Q7 central differences everywhere, with the wall ghost values;
  *   19 the isotropy-preserving D3Q19 stencil, grad phi ~ (1/w_1) sum_q w_q phi(x + e_q) e_q / h^2
  *      (weights 1/3 rest, 1/18 faces, 1/36 edges), at every cell whose 18 neighbours lie in the
- *      domain, and D3Q7 with ghosts at the others ("where possible").
+ *      domain, and D3Q7 with ghosts at the others.
  * Other values return MG_ERR_INVALID and leave the setting unchanged. mg_force_gather_adjoint
  * is implemented for the D3Q7 gradient only and returns MG_ERR_INVALID while 19 is set.
  * mg_gradient_stencil returns the setting (-1 for a NULL context). */

@@ -524,7 +524,7 @@ void ccmg_or_efield(const double* phi, double* E, int nx, int ny, int nz, double
  * e_q (6 face directions of weight 1/18, 12 edge directions of weight 1/36; the rest weight
  * w_1 = 1/3), grad phi(x) ~ (1/w_1) sum_q w_q phi(x + e_q h) e_q / h. Used where all 18
  * neighbours lie inside the domain; at the other cells the D3Q7 central differences with the
- * face ghosts above ("where possible"). The directions are taken face directions first
+ * face ghosts above (the paper applies D3Q19 wherever it can). The directions are taken face directions first
  * (+x,-x,+y,-y,+z,-z), then the edge directions (+a+b, -a-b, +a-b, -a+b) for the axis pairs
  * (x,y), (x,z), (y,z); E_a = -grad_a phi. */
 static const int d3q19_dir[18][3] = {{1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
@@ -547,7 +547,7 @@ static void efield_d3q19_at(const double* phi, int i, int j, int k, int nx, int 
   for (int a = 0; a < 3; ++a) E[a] = -(3.0 * g[a]) / h;  /* 1 / w_1 = 3 */
 }
 
-/* E-field with the chosen gradient stencil, 7 (D3Q7 everywhere) or 19 (D3Q19 where possible),
+/* E-field with the chosen gradient stencil, 7 (D3Q7 everywhere) or 19 (D3Q19 wherever it fits),
  * and per-cell boundary values (bc_at; NULL bcf: the uniform ones). */
 void ccmg_or_efield_field(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
                           const double* bcv, const double* bcf, const int* bcf_on, int stencil) {
@@ -661,7 +661,7 @@ void ccmg_or_sphere_density_adjoint(const double* gfield, double* gdensity, int 
 /* Coulomb force on each sphere (Eq. ElectrostatForce with E = -grad phi):
  *   F_s = h^3 * sum_b w_{s,b} density_s E(x_b),
  * E by the gradient stencil of ccmg_or_efield_stencil (7: central differences everywhere; 19:
- * D3Q19 where possible). forces is [P][3]. */
+ * D3Q19 wherever it fits). forces is [P][3]. */
 void ccmg_or_force_gather_field(const double* phi, int nx, int ny, int nz, double h, const int* bc,
                                 const double* bcv, const double* bcf, const int* bcf_on, int P,
                                 const double* centers, const double* radius, const double* density, int sf,

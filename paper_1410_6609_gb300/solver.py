@@ -193,7 +193,7 @@ class Poisson:
 
     @property
     def gradient_stencil(self) -> int:
-        """Gradient of efield / force_gather / step: 7 (D3Q7) or 19 (D3Q19 where possible)."""
+        """Gradient of efield / force_gather / step: 7 (D3Q7) or 19 (D3Q19 wherever it fits in the domain)."""
         return int(self.lib.mg_gradient_stencil(self.ctx))
 
     @gradient_stencil.setter
