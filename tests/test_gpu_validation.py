@@ -1,6 +1,6 @@
 """The potential validation of Sec. 5.3 (Table ValidPotSubs) on the GPU: a homogeneously charged
 sphere in a 256^3 domain whose walls carry the analytic potential (per-cell Dirichlet values),
-placed at the position of maximal volume-mapping error for its subsampling factor, solved in
+shifted to where its subsampling factor maps the volume worst, solved in
 FP64; the relative error e_rPhi = (Phi* - Phi)/Phi over the whole domain is compared with the
 published table (tests/golden/valid_pot_errors.txt).
 
