@@ -4,7 +4,7 @@ Coulomb forces) on one or more GB300s; prints ONE JSON line on rank 0.
 A step is one pass of the hot path over the workload: subsampled sphere charge density, RHS with
 wall terms, solve from zero to the relative-residual tolerance (FP32 V(2,2)-cycles inside FP64
 defect correction for the default 512^3 workload), the E-field, and the force on every sphere.
-value = fine-grid cells solved per second (MLUP/s, the paper's metric, Sec. 6.1), whole job.
+value = fine-grid cells solved per second (MLUP/s, the paper's metric, Sec. 8.1), whole job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload spheres512|spheres256|...]
   python bench.py --impl reference ...   # the CPU oracle on the same workload (bounded sample)

@@ -4,7 +4,7 @@
  *     -lap(phi) = rho / eps            (Sec. 2.4, Eq. Poisson)
  * on a uniform grid of nx*ny*nz cubic cells of size h, with Dirichlet or Neumann conditions on
  * each of the six walls folded into stencil and right-hand side (Sec. 2.4, "Boundary
- * conditions"), by the cell-centred geometric multigrid of Sec. 3 / Sec. 4.3 (red-black
+ * conditions"), by the cell-centred geometric multigrid of Sec. 3 / Sec. 5.3 (red-black
  * Gauss-Seidel, averaging restriction, constant prolongation with a x2 magnified correction,
  * Galerkin coarse operators, CG on the coarsest grid), iterated until the L2 norm of the
  * residual drops below a tolerance (Algorithm 1). It then evaluates the E-field by central
@@ -85,7 +85,7 @@ mg_status mg_level_dims(const mg_ctx* ctx, int level, int* h_dims3);
 mg_status mg_set_bc_values(mg_ctx* ctx, const double* h_bc_value6);
 
 /* Wall values per face cell for face `face` (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z), as the validation
- * runs of Sec. 5.3 set the boundary to the analytic potential: d_values (device) holds one
+ * runs of Sec. 6.3 set the boundary to the analytic potential: d_values (device) holds one
  * double per boundary cell of the face, faces 0 and 1 ny*nz values indexed j + ny*k, faces 2 and
  * 3 nx*nz indexed i + nx*k, faces 4 and 5 nx*ny indexed i + nx*j; each is the Dirichlet value or
  * the outward normal derivative (Neumann) of that cell's face, entering the right-hand side
@@ -96,19 +96,19 @@ mg_status mg_set_bc_values(mg_ctx* ctx, const double* h_bc_value6);
 mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
 
 /* Right-hand side from a charge density: f = rho/eps, then adapted to the wall values once
- * on the finest grid (Sec. 2.4 and Sec. 4.3: Dirichlet face cells += 2 g / h^2, Neumann face
+ * on the finest grid (Sec. 2.4 and Sec. 5.3: Dirichlet face cells += 2 g / h^2, Neumann face
  * cells += g / h). d_rho: nx*ny*nz doubles. */
 mg_status mg_set_rhs(mg_ctx* ctx, const double* d_rho);
 /* Right-hand side f of A phi = f taken as is (no 1/eps, no wall terms): used for adjoint
  * solves, whose wall conditions are homogeneous. d_f: nx*ny*nz doubles. */
 mg_status mg_set_rhs_f(mg_ctx* ctx, const double* d_f);
 
-/* Start value of the iteration (warm start, Sec. 6.1: later time steps reuse the previous
+/* Start value of the iteration (warm start, Sec. 8.1: later time steps reuse the previous
  * potential). d_phi NULL sets zero. */
 mg_status mg_set_solution(mg_ctx* ctx, const double* d_phi);
 mg_status mg_get_solution(mg_ctx* ctx, double* d_phi);
 
-/* ncycles V(nu1,nu2)-cycles (Sec. 3, Sec. 4.3) on the current right-hand side and solution.
+/* ncycles V(nu1,nu2)-cycles (Sec. 3, Sec. 5.3) on the current right-hand side and solution.
  * In MG_MIXED mode one cycle is one outer defect-correction step. Stream-ordered; no sync. */
 mg_status mg_vcycle(mg_ctx* ctx, int ncycles);
 

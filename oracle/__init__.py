@@ -127,7 +127,7 @@ def level_coeff(h: float, l: int) -> float:
 
 
 # --------------------------------------------------------------------------------------------
-# Single-level operations (Sec. 2.4 stencil, Sec. 3 transfers, Sec. 4.3 RBGS and CG)
+# Single-level operations (Sec. 2.4 stencil, Sec. 3 transfers, Sec. 5.3 RBGS and CG)
 
 def apply(phi, c: float, bc_type) -> np.ndarray:
     """A_l phi with the folded boundary stencil (Sec. 2.4)."""
@@ -149,7 +149,7 @@ def _f32(a) -> np.ndarray:
 
 
 def rbgs_half_f32(phi, f, c: float, bc_type, colour: int) -> np.ndarray:
-    """Single-precision red/black half-sweep (the mixed-precision inner cycle, Sec. 4.3)."""
+    """Single-precision red/black half-sweep (the mixed-precision inner cycle, Sec. 5.3)."""
     phi = _f32(phi).copy()
     _load().ccmg_or_rbgs_half_f(_p(phi), _p(_f32(f)), *_dims(phi), c, _p(_bc(bc_type)), colour)
     return phi
@@ -177,7 +177,7 @@ def prolong_correct_f32(phi, ec, omega: float = 2.0) -> np.ndarray:
 
 
 def residual(phi, f, c: float, bc_type) -> np.ndarray:
-    """r = f - A_l phi (Sec. 6.3 'Resid')."""
+    """r = f - A_l phi (Sec. 8.3 'Resid')."""
     phi, f = _f64(phi), _f64(f)
     r = np.empty_like(phi)
     _load().ccmg_or_residual(_p(phi), _p(f), _p(r), *_dims(phi), c, _p(_bc(bc_type)))
@@ -185,7 +185,7 @@ def residual(phi, f, c: float, bc_type) -> np.ndarray:
 
 
 def rbgs_half(phi, f, c: float, bc_type, colour: int) -> np.ndarray:
-    """One red (colour 0, i+j+k even) or black (colour 1) Gauss-Seidel half-sweep (Sec. 4.3)."""
+    """One red (colour 0, i+j+k even) or black (colour 1) Gauss-Seidel half-sweep (Sec. 5.3)."""
     phi = _f64(phi).copy()
     f = _f64(f)
     _load().ccmg_or_rbgs_half(_p(phi), _p(f), *_dims(phi), c, _p(_bc(bc_type)), colour)
@@ -251,7 +251,7 @@ def rhs_adjoint(lam, h: float, bc_type, eps: float = 1.0):
 
 
 def cg(b, c: float, bc_type, rtol: float = CG_RTOL, maxit: int | None = None):
-    """Unpreconditioned CG from x = 0 on A_l x = b (Sec. 4.3 coarse solver). Returns (x, iters)."""
+    """Unpreconditioned CG from x = 0 on A_l x = b (Sec. 5.3 coarse solver). Returns (x, iters)."""
     b = _f64(b)
     x = np.empty_like(b)
     if maxit is None:
@@ -261,7 +261,7 @@ def cg(b, c: float, bc_type, rtol: float = CG_RTOL, maxit: int | None = None):
 
 
 # --------------------------------------------------------------------------------------------
-# Cycles and solves (Sec. 3, Sec. 4.3, Algorithm 1)
+# Cycles and solves (Sec. 3, Sec. 5.3, Algorithm 1)
 
 def vcycles(phi, f, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2,
             omega: float = 2.0):

@@ -14,7 +14,7 @@
  *     the RHS (Sec. 2.4, Eq. Poisson and the 1D derivation of the BC treatment);
  *   - the cell-centred multigrid V(nu1,nu2)-cycle: red-black Gauss-Seidel, averaging
  *     restriction, constant prolongation with a x2 magnified correction, Galerkin coarse
- *     operators in closed form, CG on the coarsest grid (Sec. 3 and Sec. 4.3);
+ *     operators in closed form, CG on the coarsest grid (Sec. 3 and Sec. 5.3);
  *   - termination on the L2 norm of the residual (Algorithm 1);
  *   - the E-field by central differences and the Coulomb force on each particle
  *     (Sec. 2.4, Eq. ElectrostatForce, D3Q7 central differences);
@@ -129,7 +129,7 @@ void ccmg_or_prolong_correct_f(float* phi, const float* ec, int nx, int ny, int 
   prolong_correct_f(phi, ec, nx, ny, nz, omega);
 }
 
-/* RHS with BCs folded in (Sec. 2.4 and Sec. 4.3 "BC Handling for Scalar Potentials": the RHS
+/* RHS with BCs folded in (Sec. 2.4 and Sec. 5.3 "BC Handling for Scalar Potentials": the RHS
  * is adapted once, on the finest grid only):
  *   f = rho / eps;  Dirichlet face cells f += 2 g / h^2;  Neumann face cells f += g / h.
  * Edge and corner cells receive the term of every face they touch. */
@@ -152,7 +152,7 @@ void ccmg_or_rhs(const double* rho, double* f, int nx, int ny, int nz, double h,
       }
 }
 
-/* Boundary values given per face cell (the validation runs of Sec. 5.3 prescribe the analytic
+/* Boundary values given per face cell (the validation runs of Sec. 6.3 prescribe the analytic
  * potential on the boundary). bcf holds one slot per face, in face order: faces 0 and 1 (x)
  * ny*nz values indexed j + ny k, faces 2 and 3 (y) nx*nz values indexed i + nx k, faces 4 and 5
  * (z) nx*ny values indexed i + nx j; bcf_on[q] selects face q's slot over the uniform bcv[q]. The
@@ -214,7 +214,7 @@ static double dot_d(const double* a, const double* b, size_t n) {
   return s;
 }
 
-/* Unpreconditioned conjugate gradients (Hestenes-Stiefel) on the coarsest grid (Sec. 4.3),
+/* Unpreconditioned conjugate gradients (Hestenes-Stiefel) on the coarsest grid (Sec. 5.3),
  * started from x = 0 and stopped when ||r||_2 <= rtol ||b||_2 or after maxit iterations.
  * Returns the iteration count. */
 int ccmg_or_cg(double* x, const double* b, int nx, int ny, int nz, double c, const int* bc, double rtol,
@@ -254,7 +254,7 @@ int ccmg_or_cg(double* x, const double* b, int nx, int ny, int nz, double c, con
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* V-cycle (Sec. 3, Sec. 4.3): at level l < L-1:
+/* V-cycle (Sec. 3, Sec. 5.3): at level l < L-1:
  *   nu1 x (red, black);  r = f - A phi;  f_{l+1} = R r;  phi_{l+1} = 0;  V at l+1;
  *   phi += omega P phi_{l+1};  nu2 x (black, red).
  * At the coarsest level: CG from zero to rtol 1e-14 (cap 2 N_c iterations). */

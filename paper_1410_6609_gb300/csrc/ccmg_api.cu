@@ -1,8 +1,8 @@
 // ccmg_api.cu -- host side of libccmg: the C ABI declared in include/ccmg.h.
 //
-// A context owns the level hierarchy on one device (Sec. 4.3: the multigrid solver allocates all
+// A context owns the level hierarchy on one device (Sec. 5.3: the multigrid solver allocates all
 // coarse-grid data itself), the wall conditions and a few device scalars. The V-cycle of Sec. 3 /
-// Sec. 4.3 is enqueued as a fixed kernel sequence, captured once into a CUDA graph on a private
+// Sec. 5.3 is enqueued as a fixed kernel sequence, captured once into a CUDA graph on a private
 // stream and replayed on the caller's stream; the termination test of Algorithm 1 is a second,
 // small graph (residual norm + fixed-order reduction) followed by one 8-byte read-back.
 #include <cmath>

@@ -1,7 +1,7 @@
 // ccmg_internal.cuh -- internal types and kernel launchers of libccmg (not part of the ABI).
 //
 // Storage of a multigrid level. Every level except the coarsest stores its cells in the
-// checkerboard-separated order that red-black Gauss-Seidel works in (Sec. 4.3: the unknowns are
+// checkerboard-separated order that red-black Gauss-Seidel works in (Sec. 5.3: the unknowns are
 // rearranged in a checker-board manner so that each colour updates in parallel): two arrays per
 // field, one per colour, each of (nx/2) x ny x nz entries, x fastest. Cell (i,j,k) has colour
 // c = (i+j+k) & 1 and sits at index m = i/2 of row (j,k) of its colour's array; within the row,

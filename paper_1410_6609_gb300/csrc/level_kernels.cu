@@ -1,4 +1,4 @@
-// level_kernels.cu -- per-level multigrid kernels for sm_103a (Sec. 3 and Sec. 4.3 of the paper).
+// level_kernels.cu -- per-level multigrid kernels for sm_103a (Sec. 3 and Sec. 5.3 of the paper).
 //
 // All kernels work on the checkerboard-separated level layout described in ccmg_internal.cuh
 // (two colour arrays per field, unit-stride rows) with the scaled right-hand side g = f / c_l.
@@ -132,7 +132,7 @@ __global__ void k_set_scale(double* scal, int src, int dst, double n) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Right-hand side (Sec. 2.4 and Sec. 4.3: the wall conditions enter the right-hand side once, on
+// Right-hand side (Sec. 2.4 and Sec. 5.3: the wall conditions enter the right-hand side once, on
 // the finest grid): f = rho/eps + wall terms, stored scaled, g = f * h^2. A face with one value
 // has its term precomputed (t[q]); a face with values per cell computes 2 g / h^2 (Dirichlet) or
 // g / h (Neumann) per cell with the same operations.

@@ -1,4 +1,4 @@
-// level_ops.cuh -- device-side bodies of the per-level multigrid operations (Sec. 3, Sec. 4.3).
+// level_ops.cuh -- device-side bodies of the per-level multigrid operations (Sec. 3, Sec. 5.3).
 //
 // Shared by the single-system kernels (level_kernels.cu) and the batched kernels over many
 // systems of different sizes (batch_kernels.cu): each body works on one thread's cell (or vector
@@ -258,7 +258,7 @@ __device__ __forceinline__ void store_vec(double* p, const double (&o)[2]) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Red-black Gauss-Seidel half-sweep (Sec. 4.3): every cell of `colour` becomes the solution of
+// Red-black Gauss-Seidel half-sweep (Sec. 5.3): every cell of `colour` becomes the solution of
 // its own row, phi = (g + sum of neighbours) / (6 + d). ZERO: the level's current iterate is
 // zero (first sweep after restriction), so the neighbour sum is exactly zero and is not read.
 // Cell (m, j, k) of the colour's array; caller guarantees m < hx, j < ny, k < nz.
@@ -459,7 +459,7 @@ __device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, 
   return (long long)I + (long long)Gc.nx * ((long long)J + (long long)Gc.ny * K);
 }
 
-// Fused residual + averaging restriction (Sec. 3; sweeps "Resid" and "Restr" of Sec. 6.3) for
+// Fused residual + averaging restriction (Sec. 3; sweeps "Resid" and "Restr" of Sec. 8.3) for
 // coarse cell (I,J,K): the scaled residuals of its 8 children, summed in the order (dk, dj, di),
 // times 1/4 give the coarse scaled right-hand side. RED_ONLY: the black cells were just updated
 // by a black half-sweep, so their residuals are zero up to rounding and only the 4 red children
@@ -769,7 +769,7 @@ __device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubl
   return red[32];
 }
 
-// Unpreconditioned CG (Hestenes-Stiefel) on the coarsest grid (Sec. 4.3), one CTA, in double,
+// Unpreconditioned CG (Hestenes-Stiefel) on the coarsest grid (Sec. 5.3), one CTA, in double,
 // vectors in shared memory `sm` (4 n doubles), natural cell order. Operator: the scaled
 // A_L / c_L, i.e. (6 + d_i) p_i - sum of interior neighbours. Stops when ||r|| <= rtol ||b|| or
 // after maxit iterations; returns the iteration count.

@@ -1,7 +1,7 @@
 // smooth_tma.cu -- single-precision red-black Gauss-Seidel half-sweep with TMA z-slab staging
 // (sm_103a).
 //
-// The half-sweep of Sec. 4.3 (phi_i = (g_i + sum of neighbours) / (6 + d_i) on every cell of one
+// The half-sweep of Sec. 5.3 (phi_i = (g_i + sum of neighbours) / (6 + d_i) on every cell of one
 // colour) reads the other colour's array around each cell: the same row for the x-neighbours,
 // rows j+-1 and planes k+-1 for the rest. Here a CTA owns a tile of 32 x 4-cell vectors by 8
 // rows and marches it through a slab of z-planes. The other colour's planes come into shared

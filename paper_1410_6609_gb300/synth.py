@@ -4,7 +4,7 @@ This module holds input generation only (random sphere sets, analytic right-hand
 workload table). It contains none of the solver's arithmetic, so both the CUDA path and the CPU
 checker draw their inputs from here.
 
-The paper's own workloads are synthetic (charged spheres between walls, Sec. 5 and Sec. 6.1);
+The paper's own workloads are synthetic (charged spheres between walls, Sec. 6 and Sec. 8.1);
 no dataset is involved. Every generator takes an explicit seed and uses NumPy's PCG64.
 """
 from __future__ import annotations

@@ -1,4 +1,4 @@
-"""The potential validation of Sec. 5.3 (Table ValidPotSubs) on the GPU: a homogeneously charged
+"""The potential validation of Sec. 6.3 (Table ValidPotSubs) on the GPU: a homogeneously charged
 sphere in a 256^3 domain whose walls carry the analytic potential (per-cell Dirichlet values),
 shifted to where its subsampling factor maps the volume worst, solved in
 FP64; the relative error e_rPhi = (Phi* - Phi)/Phi over the whole domain is compared with the
@@ -43,7 +43,7 @@ def _max_volume_error_shift(R, sf, npts=11):
 
 
 def _analytic(r, R, Q):
-    """Sec. 5.3: Q/(4 pi eps r) outside, Q/(8 pi eps R) (3 - r^2/R^2) inside (eps = 1)."""
+    """Sec. 6.3: Q/(4 pi eps r) outside, Q/(8 pi eps R) (3 - r^2/R^2) inside (eps = 1)."""
     return torch.where(r >= R, Q / (4 * np.pi * r.clamp_min(1e-300)), Q / (8 * np.pi * R) * (3 - (r / R) ** 2))
 
 

@@ -188,7 +188,7 @@ def test_operator_symmetry_all_levels():
 
 def test_rbgs_half_solves_its_rows():
     """After a red half-sweep, every red row of A phi = f holds exactly (up to rounding), and
-    the black values are untouched (Sec. 4.3)."""
+    the black values are untouched (Sec. 5.3)."""
     dims = (6, 8, 4)
     bc = (D, N, N, D, D, N)
     f = synth.random_field(dims, 1)
@@ -228,7 +228,7 @@ def test_cg_exact_on_coarse_grids():
 
 
 def test_cg_iterations_grow_with_diameter():
-    """CG iterations grow roughly with the coarse-grid diameter (Sec. 6, Tab. WeakScalProbSizeCG)."""
+    """CG iterations grow roughly with the coarse-grid diameter (Sec. 8.3, Tab. WeakScalProbSizeCG)."""
     bc = (N, N, N, N, D, D)
     its = []
     for n in (4, 8, 16):
@@ -280,7 +280,7 @@ def test_efield_exact_for_linear_potential():
 def test_force_on_symmetric_sphere_in_uniform_field():
     """A charged sphere at the centre of a plate capacitor: by the reflection symmetry of the
     domain its self-force vanishes, so F = Q_mapped * E_applied exactly, with E_applied = -V/L
-    (Sec. 5.3, Coulomb force validation in a homogeneous field)."""
+    (Sec. 6.3, Coulomb force validation in a homogeneous field)."""
     n = 24
     V = -10.0
     h = 1.0
@@ -354,7 +354,7 @@ def test_subsampling_matches_table():
         # The paper's shift set is not given exactly; an 11^3 grid of shifts over the same range
         # reproduces the table's means to within a factor 1.4 (measured 1.09 - 1.33).
         assert mean_pct / 1.4 < ours < mean_pct * 1.4, (R, sf, ours, mean_pct)
-    # halving with each increment of s_f (Sec. 5.3)
+    # halving with each increment of s_f (Sec. 6.3)
     m = [np.abs(_volume_errors(4, sf)).mean() for sf in (1, 2, 3, 4)]
     assert m[0] > m[1] > m[2] > m[3]
 
@@ -488,7 +488,7 @@ def test_d3q19_force_on_symmetric_sphere_in_uniform_field():
 
 
 # ------------------------------------------------------------------------------------------
-# Boundary values per face cell (the validation runs of Sec. 5.3 prescribe the analytic potential
+# Boundary values per face cell (the validation runs of Sec. 6.3 prescribe the analytic potential
 # on the boundary): each face carries an array over its cells instead of one value.
 
 def _xy_fields(nx, ny, nz, h, a, b):
