@@ -166,7 +166,10 @@ mg_status mg_rhs_adjoint(mg_ctx* ctx, const double* d_lambda, double* d_grho, do
 /* One electrostatics step with HOST buffers (Algorithm 1, the potential part): copy the
  * spheres in, set the right-hand side from their subsampled charge, solve to rel_tol from the
  * current solution (warm start), compute the force on every sphere and copy it out.
- * h_forces: P*3 doubles; h_cycles / h_rel_res may be NULL. Synchronises. */
+ * rel_tol < 0 selects the time-loop mode of Sec. 8.1: exactly max_cycles cycles from the current
+ * solution (five at the first step, one at every later step there), h_rel_res then reporting the
+ * relative residual after them. h_forces: P*3 doubles; h_cycles / h_rel_res may be NULL.
+ * Synchronises. */
 mg_status mg_step_host(mg_ctx* ctx, int P, const double* h_centers, const double* h_radius,
                        const double* h_density, int sf, double rel_tol, int max_cycles, double* h_forces,
                        int* h_cycles, double* h_rel_res);

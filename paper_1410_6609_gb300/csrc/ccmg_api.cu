@@ -715,6 +715,7 @@ mg_status mg_step_host(mg_ctx* c, int P, const double* h_ctr, const double* h_ra
   mg_status st = check_sph(c, P, h_ctr, h_rad, sf);
   if (st != MG_OK) return st;
   if (P > 0 && (!h_dens || !h_F)) return fail(c, MG_ERR_INVALID, "null argument");
+  if (max_cycles < 0 || !(tol == tol)) return fail(c, MG_ERR_INVALID, "need max_cycles >= 0 and a tolerance");
   const Geom& G = c->geo[0];
   if (!c->d_rho) CK(cudaMalloc((void**)&c->d_rho, sizeof(double) * (size_t)G.nx * G.ny * G.nz), "step scratch");
   if (P > c->sph_cap) {
@@ -735,8 +736,15 @@ mg_status mg_step_host(mg_ctx* c, int P, const double* h_ctr, const double* h_ra
   }
   if ((st = mg_sphere_density(c, P, dc, dr, dq, sf, c->d_rho)) != MG_OK) return st;
   if ((st = mg_set_rhs(c, c->d_rho)) != MG_OK) return st;
-  mg_status solve_st = mg_solve(c, tol, max_cycles, h_cycles, h_rel);
-  if (solve_st != MG_OK && solve_st != MG_ERR_NOT_CONVERGED) return solve_st;
+  mg_status solve_st = MG_OK;
+  if (tol < 0.0) {  // fixed number of cycles from the current solution (the time loop of Sec. 8.1)
+    if ((st = mg_vcycle(c, max_cycles)) != MG_OK) return st;
+    if (h_cycles) *h_cycles = max_cycles;
+    if (h_rel && (st = mg_residual(c, h_rel, nullptr)) != MG_OK) return st;
+  } else {
+    solve_st = mg_solve(c, tol, max_cycles, h_cycles, h_rel);
+    if (solve_st != MG_OK && solve_st != MG_ERR_NOT_CONVERGED) return solve_st;
+  }
   if (P > 0) {
     if ((st = mg_force_gather(c, P, dc, dr, dq, sf, dF)) != MG_OK) return st;
     CK(cudaMemcpyAsync(h_F, dF, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, c->stream), "step copy");

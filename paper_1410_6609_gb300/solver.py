@@ -248,7 +248,8 @@ class Poisson:
 
     def step_host(self, centers: np.ndarray, radius: np.ndarray, density: np.ndarray, sf: int = 2,
                   tol: float = 1e-10, max_cycles: int = 100, forces: np.ndarray | None = None):
-        """One electrostatics step through host buffers (see mg_step_host)."""
+        """One electrostatics step through host buffers (see mg_step_host); tol < 0 runs exactly
+        max_cycles cycles from the current potential (the warm-started time loop of Sec. 8.1)."""
         c = np.ascontiguousarray(centers, dtype=np.float64)
         r = np.ascontiguousarray(radius, dtype=np.float64)
         q = np.ascontiguousarray(density, dtype=np.float64)
