@@ -28,6 +28,7 @@ _lib = None
 
 DIRICHLET = 0
 NEUMANN = 1
+PERIODIC = 2
 CG_RTOL = 1e-14
 
 
@@ -79,6 +80,8 @@ def _load():
                 "ccmg_or_rhs_field": (None, [P, P, I, I, I, D, D, P, P, P, P]),
                 "ccmg_or_sphere_density": (None, [P, I, I, I, D, I, P, P, P, I]),
                 "ccmg_or_sphere_density_adjoint": (None, [P, P, I, I, I, D, I, P, P, I]),
+                "ccmg_or_sphere_density_bc": (None, [P, I, I, I, D, I, P, P, P, I, P]),
+                "ccmg_or_sphere_density_adjoint_bc": (None, [P, P, I, I, I, D, I, P, P, I, P]),
                 "ccmg_or_force_gather": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P]),
                 "ccmg_or_force_gather_stencil": (None, [P, I, I, I, D, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_field": (None, [P, I, I, I, D, P, P, P, P, I, P, P, P, I, I, P]),
@@ -101,8 +104,13 @@ def _f64(a) -> np.ndarray:
 
 
 def _bc(bc_type) -> np.ndarray:
+    """Face types (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z): Dirichlet, Neumann or periodic; a periodic
+    face needs its opposite face periodic too (Sec. 2.4: the domain is extended cyclically)."""
     a = np.ascontiguousarray(bc_type, dtype=np.int32)
     assert a.shape == (6,)
+    for ax in range(3):
+        if (a[2 * ax] == PERIODIC) != (a[2 * ax + 1] == PERIODIC):
+            raise ValueError("periodic faces come in pairs")
     return a
 
 
@@ -330,21 +338,24 @@ def _spheres(centers, radius, density):
     return c, r, d
 
 
-def sphere_density(shape, h: float, centers, radius, density, sf: int = 2) -> np.ndarray:
-    """rho(b) = sum_s density_s * (subsampled overlap fraction of sphere s with cell b)."""
+def sphere_density(shape, h: float, centers, radius, density, sf: int = 2, bc_type=None) -> np.ndarray:
+    """rho(b) = sum_s density_s * (subsampled overlap fraction of sphere s with cell b); along
+    periodic axes of bc_type a sphere's charge reaches the cells at the opposite side."""
     nz, ny, nx = shape
     c, r, d = _spheres(centers, radius, density)
     rho = np.empty((nz, ny, nx))
-    _load().ccmg_or_sphere_density(_p(rho), nx, ny, nz, h, c.shape[0], _p(c), _p(r), _p(d), sf)
+    bc = None if bc_type is None else _p(_bc(bc_type))
+    _load().ccmg_or_sphere_density_bc(_p(rho), nx, ny, nz, h, c.shape[0], _p(c), _p(r), _p(d), sf, bc)
     return rho
 
 
-def sphere_density_adjoint(gfield, h: float, centers, radius, sf: int = 2) -> np.ndarray:
+def sphere_density_adjoint(gfield, h: float, centers, radius, sf: int = 2, bc_type=None) -> np.ndarray:
     gfield = _f64(gfield)
     c, r, _ = _spheres(centers, radius, np.zeros(len(_f64(radius).reshape(-1))))
     g = np.zeros(c.shape[0])
-    _load().ccmg_or_sphere_density_adjoint(_p(gfield), _p(g), *_dims(gfield), h, c.shape[0], _p(c),
-                                           _p(r), sf)
+    bct = None if bc_type is None else _bc(bc_type)
+    _load().ccmg_or_sphere_density_adjoint_bc(_p(gfield), _p(g), *_dims(gfield), h, c.shape[0], _p(c),
+                                              _p(r), sf, None if bct is None else _p(bct))
     return g
 
 
@@ -392,7 +403,7 @@ def force_objective_and_grad(shape, h: float, bc_type, bc_value, centers, radius
     A is symmetric, so the adjoint solve A lam = dJ/dphi reuses the same multigrid (homogeneous
     BCs: the BC values enter only through the RHS). Returns (J, dJ/ddensity[P], dJ/dbc[6], info).
     """
-    rho = sphere_density(shape, h, centers, radius, density, sf)
+    rho = sphere_density(shape, h, centers, radius, density, sf, bc_type)
     f = rhs(rho, h, bc_type, bc_value, eps)
     phi, k1, rel1 = solve(f, h, bc_type, tol=tol, max_cycles=max_cycles)
     F = force_gather(phi, h, bc_type, bc_value, centers, radius, density, sf)
@@ -400,5 +411,5 @@ def force_objective_and_grad(shape, h: float, bc_type, bc_value, centers, radius
     gphi, gdens, gbc = force_gather_adjoint(phi, h, bc_type, bc_value, centers, radius, density, wF, sf)
     lam, k2, rel2 = solve(gphi, h, bc_type, tol=tol, max_cycles=max_cycles)
     grho, gbc_rhs = rhs_adjoint(lam, h, bc_type, eps)
-    gdens = gdens + sphere_density_adjoint(grho, h, centers, radius, sf)
+    gdens = gdens + sphere_density_adjoint(grho, h, centers, radius, sf, bc_type)
     return J, gdens, gbc + gbc_rhs, {"phi": phi, "lam": lam, "cycles": (k1, k2), "rel": (rel1, rel2)}

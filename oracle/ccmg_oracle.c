@@ -23,9 +23,12 @@
  *     gradients of J = sum of weighted forces).
  *
  * Boundary convention: faces 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z; bc_type 0 = Dirichlet (value = the
- * potential on the face), 1 = Neumann (value = the outward normal derivative on the face).
+ * potential on the face), 1 = Neumann (value = the outward normal derivative on the face),
+ * 2 = periodic (both faces of an axis; the value is unused).
  * Ghost values: Dirichlet 2 g - phi_1, Neumann phi_1 + h g (the paper derives both for
- * spacing 1; they are scaled by h here).
+ * spacing 1; they are scaled by h here); across a periodic axis the neighbour is the cell at the
+ * opposite side (Sec. 2.4). Spheres reaching across a periodic axis map their charge to the
+ * cells at the opposite side, and take the field there.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -33,6 +36,7 @@
 
 #define BC_DIRICHLET 0
 #define BC_NEUMANN 1
+#define BC_PERIODIC 2
 
 static size_t idx3(int i, int j, int k, int nx, int ny) {
   return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * (size_t)k);
@@ -40,8 +44,15 @@ static size_t idx3(int i, int j, int k, int nx, int ny) {
 
 /* Diagonal shift of the folded stencil at cell (i,j,k): the neighbour entry on a boundary
  * face moves to the centre with sign +1 for Dirichlet (centre beta - alpha, alpha = -1) and
- * -1 for Neumann (centre beta + alpha). Sec. 2.4, "Boundary conditions". */
-static int face_shift(int type) { return type == BC_DIRICHLET ? 1 : -1; }
+ * -1 for Neumann (centre beta + alpha). Sec. 2.4, "Boundary conditions". A periodic face keeps
+ * its neighbour (the cell at the opposite side): no shift. */
+static int face_shift(int type) { return type == BC_DIRICHLET ? 1 : (type == BC_NEUMANN ? -1 : 0); }
+
+/* v modulo n in [0, n): the cell a coordinate along a periodic axis stands for. */
+static int wrap_index(int v, int n) {
+  const int r = v % n;
+  return r < 0 ? r + n : r;
+}
 static int diag_shift(int i, int j, int k, int nx, int ny, int nz, const int* bc) {
   int d = 0;
   if (i == 0) d += face_shift(bc[0]);
@@ -142,7 +153,7 @@ void ccmg_or_rhs(const double* rho, double* f, int nx, int ny, int nz, double h,
         double v = rho[p] / eps;
         const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
         for (int q = 0; q < 6; ++q) {
-          if (!on_face[q]) continue;
+          if (!on_face[q] || bc[q] == BC_PERIODIC) continue;
           if (bc[q] == BC_DIRICHLET)
             v = v + 2.0 * bcv[q] / (h * h);
           else
@@ -179,7 +190,7 @@ void ccmg_or_rhs_field(const double* rho, double* f, int nx, int ny, int nz, dou
         double v = rho[p] / eps;
         const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
         for (int q = 0; q < 6; ++q) {
-          if (!on_face[q]) continue;
+          if (!on_face[q] || bc[q] == BC_PERIODIC) continue;
           const double g = bc_at(q, i, j, k, nx, ny, nz, bcv, bcf, bcf_on);
           if (bc[q] == BC_DIRICHLET)
             v = v + 2.0 * g / (h * h);
@@ -202,7 +213,7 @@ void ccmg_or_rhs_adjoint(const double* lam, double* grho, double* gbc, int nx, i
         grho[p] = lam[p] / eps;
         const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
         for (int q = 0; q < 6; ++q) {
-          if (!on_face[q]) continue;
+          if (!on_face[q] || bc[q] == BC_PERIODIC) continue;
           gbc[q] = gbc[q] + lam[p] * (bc[q] == BC_DIRICHLET ? 2.0 / (h * h) : 1.0 / h);
         }
       }
@@ -482,6 +493,10 @@ static double phi_nb(const double* phi, int i, int j, int k, int nx, int ny, int
   const double here = phi[idx3(i, j, k, nx, ny)];
   if (q[a] < 0 || q[a] >= n[a]) {
     const int face = 2 * a + (dir > 0 ? 1 : 0);
+    if (bc[face] == BC_PERIODIC) {
+      q[a] = wrap_index(q[a], n[a]);
+      return phi[idx3(q[0], q[1], q[2], nx, ny)];
+    }
     if (bc[face] == BC_DIRICHLET) return 2.0 * bcv[face] - here;
     return here + h * bcv[face];
   }
@@ -497,6 +512,10 @@ static double phi_nb_f(const double* phi, int i, int j, int k, int nx, int ny, i
   const double here = phi[idx3(i, j, k, nx, ny)];
   if (q[a] < 0 || q[a] >= n[a]) {
     const int face = 2 * a + (dir > 0 ? 1 : 0);
+    if (bc[face] == BC_PERIODIC) {
+      q[a] = wrap_index(q[a], n[a]);
+      return phi[idx3(q[0], q[1], q[2], nx, ny)];
+    }
     const double g = bc_at(face, i, j, k, nx, ny, nz, bcv, bcf, bcf_on);
     if (bc[face] == BC_DIRICHLET) return 2.0 * g - here;
     return here + h * g;
@@ -531,16 +550,21 @@ static const int d3q19_dir[18][3] = {{1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1,
                                      {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1},
                                      {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
-static int d3q19_inside(int i, int j, int k, int nx, int ny, int nz) {
-  return i > 0 && i < nx - 1 && j > 0 && j < ny - 1 && k > 0 && k < nz - 1;
+/* Whether all 18 neighbours of (i,j,k) exist: inside the domain, or across a periodic axis. */
+static int d3q19_inside(int i, int j, int k, int nx, int ny, int nz, const int* bc) {
+  const int q[3] = {i, j, k}, n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a)
+    if (bc[2 * a] != BC_PERIODIC && (q[a] == 0 || q[a] == n[a] - 1)) return 0;
+  return 1;
 }
 
-static void efield_d3q19_at(const double* phi, int i, int j, int k, int nx, int ny, double h, double E[3]) {
+static void efield_d3q19_at(const double* phi, int i, int j, int k, int nx, int ny, int nz, double h, double E[3]) {
   double g[3] = {0.0, 0.0, 0.0};
   for (int q = 0; q < 18; ++q) {
     const int* e = d3q19_dir[q];
     const double w = q < 6 ? 1.0 / 18.0 : 1.0 / 36.0;
-    const double v = phi[idx3(i + e[0], j + e[1], k + e[2], nx, ny)];
+    /* d3q19_inside holds: an index leaves the domain only along a periodic axis */
+    const double v = phi[idx3(wrap_index(i + e[0], nx), wrap_index(j + e[1], ny), wrap_index(k + e[2], nz), nx, ny)];
     for (int a = 0; a < 3; ++a)
       if (e[a] != 0) g[a] = g[a] + w * v * (double)e[a];
   }
@@ -566,9 +590,9 @@ void ccmg_or_efield_field(const double* phi, double* E, int nx, int ny, int nz, 
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
-        if (!d3q19_inside(i, j, k, nx, ny, nz)) continue;
+        if (!d3q19_inside(i, j, k, nx, ny, nz, bc)) continue;
         double e[3];
-        efield_d3q19_at(phi, i, j, k, nx, ny, h, e);
+        efield_d3q19_at(phi, i, j, k, nx, ny, nz, h, e);
         for (int a = 0; a < 3; ++a) E[(size_t)a * n + idx3(i, j, k, nx, ny)] = e[a];
       }
 }
@@ -602,14 +626,26 @@ static int overlap_count(int i, int j, int k, double h, const double* c, double 
   return cnt;
 }
 
-/* Cell range [lo, hi] along one axis that can touch a sphere (all other cells have count 0). */
-static void cell_range(double c, double R, double h, int n, int* lo, int* hi) {
+/* Cell range [lo, hi] along one axis that can touch a sphere (all other cells have count 0);
+ * clipped to the domain unless the axis is periodic, where cells beyond an end stand for those at
+ * the opposite side (the sphere's periodic image). */
+static void cell_range(double c, double R, double h, int n, int periodic, int* lo, int* hi) {
   int a = (int)floor((c - R) / h) - 1;
   int b = (int)floor((c + R) / h) + 1;
-  if (a < 0) a = 0;
-  if (b > n - 1) b = n - 1;
+  if (!periodic && a < 0) a = 0;
+  if (!periodic && b > n - 1) b = n - 1;
   *lo = a;
   *hi = b;
+}
+
+/* The cell ranges of sphere s on the three axes (bc NULL: no periodic axis). */
+static void sphere_range(const double* c, double R, double h, const int* n, const int* bc, int* lo, int* hi) {
+  for (int a = 0; a < 3; ++a) cell_range(c[a], R, h, n[a], bc && bc[2 * a] == BC_PERIODIC, &lo[a], &hi[a]);
+}
+
+/* Storage index of the cell a (possibly periodic-image) coordinate stands for. */
+static size_t cell_index(int i, int j, int k, int nx, int ny, int nz) {
+  return idx3(wrap_index(i, nx), wrap_index(j, ny), wrap_index(k, nz), nx, ny);
 }
 
 /* Volume-overlap weight w_{s,b} = count / sf^3 of sphere s in cell b. */
@@ -618,73 +654,86 @@ static double overlap_weight(int i, int j, int k, double h, const double* c, dou
   return (double)cnt / (double)(sf * sf * sf);
 }
 
-/* Charge density field: rho(b) = sum_s density_s * w_{s,b} (spheres in index order). */
-void ccmg_or_sphere_density(double* rho, int nx, int ny, int nz, double h, int P, const double* centers,
-                            const double* radius, const double* density, int sf) {
+/* Charge density field: rho(b) = sum_s density_s * w_{s,b} (spheres in index order); bc (NULL:
+ * none) marks the periodic axes, across which a sphere's charge reaches the opposite side. */
+void ccmg_or_sphere_density_bc(double* rho, int nx, int ny, int nz, double h, int P, const double* centers,
+                               const double* radius, const double* density, int sf, const int* bc) {
   memset(rho, 0, (size_t)nx * ny * nz * sizeof(double));
+  const int n[3] = {nx, ny, nz};
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
     int lo[3], hi[3];
-    const int n[3] = {nx, ny, nz};
-    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    sphere_range(c, radius[s], h, n, bc, lo, hi);
     for (int k = lo[2]; k <= hi[2]; ++k)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int i = lo[0]; i <= hi[0]; ++i) {
           const int cnt = overlap_count(i, j, k, h, c, radius[s], sf);
           if (cnt == 0) continue;
-          const size_t p = idx3(i, j, k, nx, ny);
+          const size_t p = cell_index(i, j, k, nx, ny, nz);
           rho[p] = rho[p] + density[s] * ((double)cnt / (double)(sf * sf * sf));
         }
   }
 }
 
+void ccmg_or_sphere_density(double* rho, int nx, int ny, int nz, double h, int P, const double* centers,
+                            const double* radius, const double* density, int sf) {
+  ccmg_or_sphere_density_bc(rho, nx, ny, nz, h, P, centers, radius, density, sf, NULL);
+}
+
 /* Adjoint of the density map: g_s += sum_b w_{s,b} gfield(b). */
-void ccmg_or_sphere_density_adjoint(const double* gfield, double* gdensity, int nx, int ny, int nz,
-                                    double h, int P, const double* centers, const double* radius, int sf) {
+void ccmg_or_sphere_density_adjoint_bc(const double* gfield, double* gdensity, int nx, int ny, int nz, double h,
+                                       int P, const double* centers, const double* radius, int sf, const int* bc) {
+  const int n[3] = {nx, ny, nz};
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
     int lo[3], hi[3];
-    const int n[3] = {nx, ny, nz};
-    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    sphere_range(c, radius[s], h, n, bc, lo, hi);
     double acc = 0.0;
     for (int k = lo[2]; k <= hi[2]; ++k)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int i = lo[0]; i <= hi[0]; ++i) {
           const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
           if (w == 0.0) continue;
-          acc = acc + w * gfield[idx3(i, j, k, nx, ny)];
+          acc = acc + w * gfield[cell_index(i, j, k, nx, ny, nz)];
         }
     gdensity[s] = gdensity[s] + acc;
   }
 }
 
+void ccmg_or_sphere_density_adjoint(const double* gfield, double* gdensity, int nx, int ny, int nz,
+                                    double h, int P, const double* centers, const double* radius, int sf) {
+  ccmg_or_sphere_density_adjoint_bc(gfield, gdensity, nx, ny, nz, h, P, centers, radius, sf, NULL);
+}
+
 /* Coulomb force on each sphere (Eq. ElectrostatForce with E = -grad phi):
  *   F_s = h^3 * sum_b w_{s,b} density_s E(x_b),
  * E by the gradient stencil of ccmg_or_efield_stencil (7: central differences everywhere; 19:
- * D3Q19 wherever it fits). forces is [P][3]. */
+ * D3Q19 wherever it fits), taken at the cell a periodic-image coordinate stands for. forces is
+ * [P][3]. */
 void ccmg_or_force_gather_field(const double* phi, int nx, int ny, int nz, double h, const int* bc,
                                 const double* bcv, const double* bcf, const int* bcf_on, int P,
                                 const double* centers, const double* radius, const double* density, int sf,
                                 int stencil, double* forces) {
   const double h3 = h * h * h;
+  const int n[3] = {nx, ny, nz};
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
     int lo[3], hi[3];
-    const int n[3] = {nx, ny, nz};
-    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    sphere_range(c, radius[s], h, n, bc, lo, hi);
     double F[3] = {0.0, 0.0, 0.0};
     for (int k = lo[2]; k <= hi[2]; ++k)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int i = lo[0]; i <= hi[0]; ++i) {
           const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
           if (w == 0.0) continue;
+          const int iw = wrap_index(i, nx), jw = wrap_index(j, ny), kw = wrap_index(k, nz);
           double E[3];
-          if (stencil == 19 && d3q19_inside(i, j, k, nx, ny, nz)) {
-            efield_d3q19_at(phi, i, j, k, nx, ny, h, E);
+          if (stencil == 19 && d3q19_inside(iw, jw, kw, nx, ny, nz, bc)) {
+            efield_d3q19_at(phi, iw, jw, kw, nx, ny, nz, h, E);
           } else {
             for (int a = 0; a < 3; ++a) {
-              const double up = phi_nb_f(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv, bcf, bcf_on);
-              const double dn = phi_nb_f(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv, bcf, bcf_on);
+              const double up = phi_nb_f(phi, iw, jw, kw, nx, ny, nz, a, +1, h, bc, bcv, bcf, bcf_on);
+              const double dn = phi_nb_f(phi, iw, jw, kw, nx, ny, nz, a, -1, h, bc, bcv, bcf, bcf_on);
               E[a] = -(up - dn) / (2.0 * h);
             }
           }
@@ -705,20 +754,21 @@ void ccmg_or_force_gather(const double* phi, int nx, int ny, int nz, double h, c
                           const double* bcv, int P, const double* centers, const double* radius,
                           const double* density, int sf, double* forces) {
   const double h3 = h * h * h;
+  const int n[3] = {nx, ny, nz};
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
     int lo[3], hi[3];
-    const int n[3] = {nx, ny, nz};
-    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    sphere_range(c, radius[s], h, n, bc, lo, hi);
     double F[3] = {0.0, 0.0, 0.0};
     for (int k = lo[2]; k <= hi[2]; ++k)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int i = lo[0]; i <= hi[0]; ++i) {
           const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
           if (w == 0.0) continue;
+          const int iw = wrap_index(i, nx), jw = wrap_index(j, ny), kw = wrap_index(k, nz);
           for (int a = 0; a < 3; ++a) {
-            const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
-            const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+            const double up = phi_nb(phi, iw, jw, kw, nx, ny, nz, a, +1, h, bc, bcv);
+            const double dn = phi_nb(phi, iw, jw, kw, nx, ny, nz, a, -1, h, bc, bcv);
             const double Ea = -(up - dn) / (2.0 * h);
             F[a] = F[a] + w * Ea;
           }
@@ -728,7 +778,8 @@ void ccmg_or_force_gather(const double* phi, int nx, int ny, int nz, double h, c
 }
 
 /* Adjoint of ccmg_or_force_gather for J = sum_{s,a} wF[s][a] * F_s[a]:
- *   gphi   (N)  += dJ/dphi      (scatter of the central differences, ghosts included)
+ *   gphi   (N)  += dJ/dphi      (scatter of the central differences, ghosts included; across a
+ *                               periodic axis to the cell at the opposite side)
  *   gdens  (P)  += dJ/ddensity_s through the explicit density factor
  *   gbc    (6)  += dJ/dbc_value through the ghost values used by the differences. */
 void ccmg_or_force_gather_adjoint(const double* phi, int nx, int ny, int nz, double h, const int* bc,
@@ -740,30 +791,30 @@ void ccmg_or_force_gather_adjoint(const double* phi, int nx, int ny, int nz, dou
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
     int lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) cell_range(c[a], radius[s], h, n[a], &lo[a], &hi[a]);
+    sphere_range(c, radius[s], h, n, bc, lo, hi);
     double Fsum[3] = {0.0, 0.0, 0.0};
     for (int k = lo[2]; k <= hi[2]; ++k)
       for (int j = lo[1]; j <= hi[1]; ++j)
         for (int i = lo[0]; i <= hi[0]; ++i) {
           const double w = overlap_weight(i, j, k, h, c, radius[s], sf);
           if (w == 0.0) continue;
-          const size_t p = idx3(i, j, k, nx, ny);
+          const int cell[3] = {wrap_index(i, nx), wrap_index(j, ny), wrap_index(k, nz)};
+          const size_t p = idx3(cell[0], cell[1], cell[2], nx, ny);
           for (int a = 0; a < 3; ++a) {
-            const double up = phi_nb(phi, i, j, k, nx, ny, nz, a, +1, h, bc, bcv);
-            const double dn = phi_nb(phi, i, j, k, nx, ny, nz, a, -1, h, bc, bcv);
+            const double up = phi_nb(phi, cell[0], cell[1], cell[2], nx, ny, nz, a, +1, h, bc, bcv);
+            const double dn = phi_nb(phi, cell[0], cell[1], cell[2], nx, ny, nz, a, -1, h, bc, bcv);
             Fsum[a] = Fsum[a] + w * (-(up - dn) / (2.0 * h));
             /* dJ/dE_a(b) = wF[s][a] * h3 * density_s * w; E_a = -(up - dn)/(2h). */
             const double gE = wF[3 * s + a] * h3 * density[s] * w;
             const double g_up = -gE / (2.0 * h);
             const double g_dn = +gE / (2.0 * h);
-            const int cell[3] = {i, j, k};
             for (int side = 0; side < 2; ++side) {
               const int dir = side == 0 ? +1 : -1;
               const double g = side == 0 ? g_up : g_dn;
               int qn[3] = {cell[0], cell[1], cell[2]};
               qn[a] += dir;
-              if (qn[a] < 0 || qn[a] >= n[a]) {
-                const int face = 2 * a + (dir > 0 ? 1 : 0);
+              const int face = 2 * a + (dir > 0 ? 1 : 0);
+              if ((qn[a] < 0 || qn[a] >= n[a]) && bc[face] != BC_PERIODIC) {
                 if (bc[face] == BC_DIRICHLET) {
                   gbc[face] = gbc[face] + 2.0 * g;
                   gphi[p] = gphi[p] - g;
@@ -772,7 +823,7 @@ void ccmg_or_force_gather_adjoint(const double* phi, int nx, int ny, int nz, dou
                   gphi[p] = gphi[p] + g;
                 }
               } else {
-                const size_t pn = idx3(qn[0], qn[1], qn[2], nx, ny);
+                const size_t pn = cell_index(qn[0], qn[1], qn[2], nx, ny, nz);
                 gphi[pn] = gphi[pn] + g;
               }
             }

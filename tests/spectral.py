@@ -10,9 +10,10 @@ SIAM Review 41, 1999):
     Neumann,   Neumann       cos(pi k (j+1/2) / n)            2 - 2 cos(pi k / n)       DCT-II
     Dirichlet, Neumann       sin(pi (k+1/2) (j+1/2) / n)      2 - 2 cos(pi (k+1/2) / n) DST-IV
     Neumann,   Dirichlet     cos(pi (k+1/2) (j+1/2) / n)      2 - 2 cos(pi (k+1/2) / n) DCT-IV
+    periodic,  periodic      exp(2 pi i k j / n)              2 - 2 cos(2 pi k / n)     DFT
 
 (homogeneous conditions; the Dirichlet face value is zero on the face, i.e. the ghost is the
-negated cell value; the Neumann ghost equals the cell value). The 3D operator is the Kronecker
+negated cell value; the Neumann ghost equals the cell value; a periodic axis wraps around). The 3D operator is the Kronecker
 sum of the three 1D operators, so its eigenvalues are sums of the 1D ones.
 """
 from __future__ import annotations
@@ -20,7 +21,7 @@ from __future__ import annotations
 import numpy as np
 from scipy import fft
 
-D, N = 0, 1
+D, N, P = 0, 1, 2
 
 
 def _axis_transform(lo: int, hi: int):
@@ -40,6 +41,10 @@ def _axis_transform(lo: int, hi: int):
         return (lambda a, ax: fft.dct(a, type=4, axis=ax, norm="ortho"),
                 lambda a, ax: fft.idct(a, type=4, axis=ax, norm="ortho"),
                 lambda n: 2.0 - 2.0 * np.cos(np.pi * (np.arange(n) + 0.5) / n))
+    if (lo, hi) == (P, P):
+        return (lambda a, ax: fft.fft(a, axis=ax, norm="ortho"),
+                lambda a, ax: fft.ifft(a, axis=ax, norm="ortho"),
+                lambda n: 2.0 - 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n))
     raise ValueError((lo, hi))
 
 
@@ -51,6 +56,9 @@ def solve(f: np.ndarray, h: float, bc_type) -> np.ndarray:
             (0, nz, bc_type[4], bc_type[5])]
     g = np.array(f, dtype=np.float64, copy=True)
     lam = np.zeros(f.shape)
+    # the real transforms first, the complex DFT of periodic axes last (transforms along
+    # different axes commute); undone in the reverse order
+    axes = sorted(axes, key=lambda t: t[2] == P)
     inv = []
     for ax, n, lo, hi in axes:
         fwd, bwd, eig = _axis_transform(lo, hi)
@@ -58,10 +66,12 @@ def solve(f: np.ndarray, h: float, bc_type) -> np.ndarray:
         shape = [1, 1, 1]
         shape[ax] = n
         lam = lam + eig(n).reshape(shape) / (h * h)
-        inv.append((ax, bwd))
+        inv.append((ax, bwd, lo == P))
     if np.any(lam == 0.0):
-        raise ValueError("singular operator (all-Neumann)")
+        raise ValueError("singular operator (no Dirichlet face)")
     g = g / lam
-    for ax, bwd in inv:
+    for ax, bwd, cplx in reversed(inv):
+        if not cplx:
+            g = np.real(g)  # the periodic axes are undone: real up to rounding
         g = bwd(g, ax)
-    return g
+    return np.real(g)

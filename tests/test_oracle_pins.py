@@ -546,3 +546,153 @@ def test_per_cell_dirichlet_values_of_a_linear_field():
     f = oracle.rhs(np.zeros((nz, ny, nx)), h, bc, (0.0,) * 6, bc_field=field)
     phi, _, _ = oracle.solve(f, h, bc, tol=1e-14, max_cycles=100)
     assert np.abs(phi - phi_ex).max() < 1e-11 * np.abs(phi_ex).max()
+
+
+# ------------------------------------------------------------------------------------------
+# Periodic boundary conditions (Sec. 2.4: the domain is extended cyclically; the neighbour across
+# a periodic axis is the cell at the opposite side)
+
+PER = oracle.PERIODIC
+
+
+@pytest.mark.parametrize("bc", [(PER, PER, PER, PER, D, D), (PER, PER, N, N, D, N), (D, N, PER, PER, PER, PER),
+                                (PER, PER, D, D, PER, PER)])
+def test_periodic_spectral_random_rhs(bc):
+    """The exact discrete solution by a DFT along the periodic axes and sine/cosine transforms
+    along the others."""
+    dims = (16, 12, 20)
+    f = synth.random_field(dims, seed=7)
+    phi, k, rel = oracle.solve(f, 1.0, bc, tol=1e-13, max_cycles=200)
+    ex = spectral.solve(f, 1.0, bc)
+    assert np.linalg.norm(phi - ex) / np.linalg.norm(ex) < 1e-11
+
+
+def test_periodic_operator_eigenvector():
+    """cos(2 pi m (i+1/2)/n + a) along a periodic axis (a phase that makes it neither a Dirichlet
+    nor a Neumann eigenvector) and sin(pi (k+1/2)/nz) between Dirichlet walls: A phi = (sum of
+    the 1D eigenvalues) phi exactly, at the wrapped cells too."""
+    nx, ny, nz, h = 12, 10, 8, 0.5
+    i, j, k = np.arange(nx) + 0.5, np.arange(ny) + 0.5, np.arange(nz) + 0.5
+    phi = (np.cos(2 * np.pi * 2 * i / nx + 0.3)[None, None, :] * np.cos(2 * np.pi * 3 * j / ny - 0.7)[None, :, None]
+           * np.sin(np.pi * k / nz)[:, None, None])
+    lam = ((2 - 2 * np.cos(2 * np.pi * 2 / nx)) + (2 - 2 * np.cos(2 * np.pi * 3 / ny))
+           + (2 - 2 * np.cos(np.pi / nz))) / h ** 2
+    Aphi = oracle.apply(phi, 1.0 / h ** 2, (PER, PER, PER, PER, D, D))
+    assert np.abs(Aphi - lam * phi).max() < 1e-12 * lam
+    # a wrong pairing at the wrap (the Neumann shift, or no neighbour) breaks it
+    assert np.abs(oracle.apply(phi, 1.0 / h ** 2, (N, N, PER, PER, D, D)) - lam * phi).max() > 1e-3 * lam
+
+
+@pytest.mark.parametrize("bc", [(PER, PER, D, N, PER, PER), (PER,) * 6, (N, D, PER, PER, D, D)])
+def test_periodic_galerkin_closed_form(bc):
+    fine = (12, 12, 12)
+    c0 = 4.0
+    A0 = dense(fine, c0, bc)
+    P = injection(fine)
+    A1 = dense((6, 6, 6), c0 / 2.0, bc)
+    assert np.abs((P.T / 8.0) @ A0 @ P - A1).max() <= 1e-14 * np.abs(A1).max()
+    assert np.abs(A0 - A0.T).max() == 0.0
+
+
+def test_periodic_rhs_has_no_wall_term():
+    nx, ny, nz = 6, 4, 8
+    rho = synth.random_field((nx, ny, nz), seed=2)
+    bcv = (3.0, -1.0, 2.0, 5.0, 0.5, -0.25)
+    f = oracle.rhs(rho, 0.5, (PER, PER, PER, PER, D, N), bcv, eps=2.0)
+    ref = rho / 2.0
+    ref[0] += 2 * 0.5 / 0.25
+    ref[-1] += -0.25 / 0.5
+    assert np.array_equal(f, ref)
+
+
+def _dyadic_spheres():
+    # centres and radii with few significand bits: shifting a centre by whole cells (h = 1)
+    # leaves every sub-cell distance exactly the same
+    c = np.array([[0.75, 5.5, 3.25], [9.625, 0.375, 7.5], [4.5, 4.25, 0.5]])
+    return c, np.array([2.5, 1.75, 2.25]), np.array([1.25, -0.5, 2.0])
+
+
+def test_periodic_density_wraps_to_the_opposite_side():
+    """A sphere across periodic walls maps the same charges as the sphere moved into the
+    interior, the field rolled back: brute force by translation."""
+    nx, ny, nz = 10, 9, 11
+    c, R, q = _dyadic_spheres()
+    bc = (PER,) * 6
+    shifts = np.array([[3, 0, 0], [-3, 3, 0], [0, 0, 4]])  # moves sphere s wholly inside
+    for s in range(3):
+        for sf in (1, 2, 3):
+            rho = oracle.sphere_density((nz, ny, nx), 1.0, c[s:s + 1], R[s:s + 1], q[s:s + 1], sf, bc)
+            moved = oracle.sphere_density((nz, ny, nx), 1.0, c[s:s + 1] + shifts[s], R[s:s + 1], q[s:s + 1], sf)
+            d = shifts[s]
+            assert np.array_equal(rho, np.roll(moved, shift=(-d[2], -d[1], -d[0]), axis=(0, 1, 2)))
+        # without the periodic axes the charge beyond the walls is lost
+        assert oracle.sphere_density((nz, ny, nx), 1.0, c[s:s + 1], R[s:s + 1], q[s:s + 1], 2).sum() != rho.sum()
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_periodic_efield_closed_form(stencil):
+    """phi = cos(2 pi m (i+1/2)/n) along x (periodic): the central difference (and the D3Q19
+    gradient, which reduces to it for a function of x alone) is exactly
+    -sin(2 pi m/n) sin(2 pi m (i+1/2)/n) / h ... with the wrap at both ends."""
+    nx, ny, nz, h, m = 12, 6, 8, 0.5, 1
+    xi = 2 * np.pi * m * (np.arange(nx) + 0.5) / nx
+    phi = np.ascontiguousarray(np.broadcast_to(np.cos(xi)[None, None, :], (nz, ny, nx)))
+    E = oracle.efield(phi, h, (PER,) * 6, (0.0,) * 6, stencil=stencil)
+    ex = np.sin(2 * np.pi * m / nx) * np.sin(xi) / h  # -(cos(x+d) - cos(x-d)) / (2h)
+    assert np.abs(E[0] - ex[None, None, :]).max() < 1e-14
+    assert np.abs(E[1]).max() < 1e-15 and np.abs(E[2]).max() < 1e-15
+
+
+@pytest.mark.parametrize("stencil", [7, 19])
+def test_periodic_force_by_translation(stencil):
+    """The force on spheres across periodic walls equals that on the spheres moved into the
+    interior with the potential rolled along: the gather and the gradient wrap."""
+    nx, ny, nz = 12, 10, 14
+    c, R, q = _dyadic_spheres()
+    bc = (PER,) * 6
+    phi = synth.random_field((nx, ny, nz), seed=9)
+    shift = np.array([4, 3, 5])
+    F = oracle.force_gather(phi, 1.0, bc, (0.0,) * 6, c, R, q, 2, stencil=stencil)
+    rolled = np.roll(phi, shift=(shift[2], shift[1], shift[0]), axis=(0, 1, 2))
+    Fm = oracle.force_gather(rolled, 1.0, bc, (0.0,) * 6, c + shift, R, q, 2, stencil=stencil)
+    assert np.array_equal(F, Fm)
+
+
+def test_periodic_adjoint_gradient_vs_finite_differences():
+    dims = (12, 12, 16)
+    nx, ny, nz = dims
+    bc = (PER, PER, PER, PER, D, D)
+    bcv = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    c = np.array([[0.5, 6.0, 8.0], [7.0, 11.25, 6.5], [11.5, 0.75, 9.0]])  # across the x and y walls
+    R = np.array([2.5, 2.0, 2.25])
+    dens = np.array([1.0, -0.75, 0.5])
+    wF = np.zeros((3, 3))
+    wF[:, 0] = 1.0
+    wF[:, 2] = 0.5
+    shape = (nz, ny, nx)
+    J, gd, gbc, _ = oracle.force_objective_and_grad(shape, 1.0, bc, bcv, c, R, dens, wF, tol=1e-14, max_cycles=300)
+
+    def Jof(dn, v):
+        rho = oracle.sphere_density(shape, 1.0, c, R, dn, 2, bc)
+        f = oracle.rhs(rho, 1.0, bc, v)
+        phi, _, _ = oracle.solve(f, 1.0, bc, tol=1e-14, max_cycles=300)
+        return float(np.sum(wF * oracle.force_gather(phi, 1.0, bc, v, c, R, dn, 2)))
+
+    step = 1e-3
+    for s in range(3):
+        dp, dm = dens.copy(), dens.copy()
+        dp[s] += step
+        dm[s] -= step
+        fd = (Jof(dp, bcv) - Jof(dm, bcv)) / (2 * step)
+        assert abs(fd - gd[s]) <= 1e-7 * max(1.0, abs(fd))
+    vp, vm = bcv.copy(), bcv.copy()
+    vp[5] += step
+    vm[5] -= step
+    fd = (Jof(dens, vp) - Jof(dens, vm)) / (2 * step)
+    assert abs(fd - gbc[5]) <= 1e-7 * max(1.0, abs(fd))
+    assert np.all(gbc[:4] == 0.0)
+
+
+def test_periodic_faces_must_pair():
+    with pytest.raises(ValueError):
+        oracle.apply(np.zeros((4, 4, 4)), 1.0, (PER, D, D, D, D, D))
