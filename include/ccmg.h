@@ -44,7 +44,11 @@ typedef enum {
   MG_ERR_TIMEOUT = 6        /* a bounded device-side wait ran out */
 } mg_status;
 
-typedef enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1 } mg_bc;
+/* Wall conditions (Sec. 2.4): Dirichlet (value = the potential on the face), Neumann (value =
+ * the outward normal derivative), periodic (both faces of an axis; the domain is extended
+ * cyclically and the neighbour across the face is the cell at the opposite side; the value is
+ * unused). */
+typedef enum { MG_BC_DIRICHLET = 0, MG_BC_NEUMANN = 1, MG_BC_PERIODIC = 2 } mg_bc;
 
 /* MG_FP64: every operation in double precision.
  * MG_MIXED: FP64 defect correction around single-precision V-cycles. The outer residual, the
@@ -55,7 +59,8 @@ typedef enum { MG_FP64 = 0, MG_MIXED = 1 } mg_prec;
 typedef struct {
   int nx, ny, nz;        /* cells per axis; each >= 4 and even */
   double h;              /* cell size (> 0) */
-  int bc_type[6];        /* mg_bc per face; all-Neumann is refused (singular) */
+  int bc_type[6];        /* mg_bc per face; periodic in opposite pairs; at least one Dirichlet
+                            face (otherwise singular) */
   double bc_value[6];    /* Dirichlet potential / Neumann outward derivative per face */
   int nu1, nu2;          /* pre- and post-smoothing sweeps (V(nu1,nu2)); 0..16, nu2 >= 1 */
   double cgc_weight;     /* magnification of the coarse-grid correction (Sec. 3: about 2) */

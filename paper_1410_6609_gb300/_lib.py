@@ -18,7 +18,7 @@ MG_OK, MG_ERR_INVALID, MG_ERR_CUDA, MG_ERR_OOM, MG_ERR_NOT_CONVERGED, MG_ERR_DIV
 STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM",
                 4: "MG_ERR_NOT_CONVERGED", 5: "MG_ERR_DIVERGED", 6: "MG_ERR_TIMEOUT"}
 MG_FP64, MG_MIXED = 0, 1
-DIRICHLET, NEUMANN = 0, 1
+DIRICHLET, NEUMANN, PERIODIC = 0, 1, 2
 
 
 class MgParams(ctypes.Structure):

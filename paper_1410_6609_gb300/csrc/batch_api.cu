@@ -34,6 +34,7 @@ struct BSys {
 struct Plan {
   int e0 = 0, s0 = 0, count = 0, blocks = 0;
   dim3 block{1, 1, 1};
+  int per = 0;  // some entry's level has a periodic axis
 };
 
 thread_local std::string g_batch_error;
@@ -111,6 +112,7 @@ BLaunch bl(const mg_batch* b, const Plan& p) {
   L.count = p.count;
   L.blocks = p.blocks;
   L.block = p.block;
+  L.per = p.per;
   return L;
 }
 
@@ -120,10 +122,12 @@ void add_plan(mg_batch* b, Plan& p, const std::vector<BEntry>& ents, dim3 block)
   p.count = (int)ents.size();
   p.block = block;
   int acc = 0;
+  p.per = 0;
   for (const BEntry& e : ents) {
     b->h_starts.push_back(acc);
     acc += e.gx * e.gy * e.gz;
     b->h_entries.push_back(e);
+    if (e.G.per) p.per = 1;
   }
   b->h_starts.push_back(acc);
   p.blocks = acc;
@@ -455,14 +459,9 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
       if (d[a] < 4 || (d[a] % 2) != 0) return bfail(b, MG_ERR_INVALID, "grid dimensions must be even and >= 4");
     if (!(p.h > 0.0) || !std::isfinite(p.h) || !(p.eps > 0.0) || !std::isfinite(p.eps))
       return bfail(b, MG_ERR_INVALID, "h and eps must be positive");
-    bool all_neumann = true;
-    for (int q = 0; q < 6; ++q) {
-      if (p.bc_type[q] != MG_BC_DIRICHLET && p.bc_type[q] != MG_BC_NEUMANN)
-        return bfail(b, MG_ERR_INVALID, "bc_type must be MG_BC_DIRICHLET or MG_BC_NEUMANN");
+    if (const char* why = check_bc_types(p.bc_type)) return bfail(b, MG_ERR_INVALID, why);
+    for (int q = 0; q < 6; ++q)
       if (!std::isfinite(p.bc_value[q])) return bfail(b, MG_ERR_INVALID, "bc_value must be finite");
-      if (p.bc_type[q] == MG_BC_DIRICHLET) all_neumann = false;
-    }
-    if (all_neumann) return bfail(b, MG_ERR_INVALID, "all-Neumann walls give a singular problem");
     if (p.prec != p0.prec || p.nu1 != p0.nu1 || p.nu2 != p0.nu2 || p.cgc_weight != p0.cgc_weight ||
         (p0.prec == MG_MIXED && p.mixed_inner != p0.mixed_inner))
       return bfail(b, MG_ERR_INVALID, "all systems of a batch share prec, nu1, nu2, cgc_weight and mixed_inner");
@@ -509,7 +508,8 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
       G.nx = dims[0];
       G.ny = dims[1];
       G.nz = dims[2];
-      for (int q = 0; q < 6; ++q) G.sh[q] = S.p.bc_type[q] == MG_BC_DIRICHLET ? 1 : -1;
+      for (int q = 0; q < 6; ++q) G.sh[q] = face_shift(S.p.bc_type[q]);
+      G.per = periodic_bits(S.p.bc_type);
       ++S.L;
       bool ok = true;
       for (int a = 0; a < 3; ++a)

@@ -53,7 +53,7 @@ __device__ __forceinline__ void for_vblocks(const BEntry* __restrict__ E, const 
   }
 }
 
-template <typename T, bool ZERO>
+template <typename T, bool ZERO, bool PER>
 __global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
                                                  int total, const int* __restrict__ active, InvDiag<T> inv,
                                                  int colour) {
@@ -64,17 +64,19 @@ __global__ void __launch_bounds__(256) kb_smooth(const BEntry* __restrict__ E, c
     const T* g = (const T*)en.g;
     if (en.vec) {
       int mv, j, k;
-      if (flat_coords(lb, en.gx, G.hx / V, G.ny, mv, j, k)) smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
+      if (flat_coords(lb, en.gx, G.hx / V, G.ny, mv, j, k)) smooth_vec<T, V, ZERO, PER>(x, g, G, inv, colour, mv, j, k);
     } else {
       const int bxi = lb % en.gx, rest = lb / en.gx;
       const int byi = rest % en.gy, k = rest / en.gy;
       const int j = byi * blockDim.y + threadIdx.y;
       const int m = bxi * blockDim.x + threadIdx.x;
-      if (m < G.hx && j < G.ny) smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
+      if (m < G.hx && j < G.ny) smooth_cell<T, ZERO, PER>(x, g, G, inv, colour, m, j, k);
     }
   });
 }
 
+// PER: compiled with periodic-axis support (launched when some system of the launch has one).
+template <bool PER>
 __global__ void __launch_bounds__(256) kb_smooth_prolong(const BEntry* __restrict__ E, const int* __restrict__ start,
                                                          int count, int total, const int* __restrict__ active,
                                                          InvDiag<float> inv, float omega) {
@@ -85,18 +87,18 @@ __global__ void __launch_bounds__(256) kb_smooth_prolong(const BEntry* __restric
     if (en.vec) {
       int mv, j, k;
       if (flat_coords(lb, en.gx, G.hx / 4, G.ny, mv, j, k))
-        smooth_vec_prolong<float, 4>(x, g, G, inv, (const float*)en.xc, en.Gc, omega, mv, j, k);
+        smooth_vec_prolong<float, 4, PER>(x, g, G, inv, (const float*)en.xc, en.Gc, omega, mv, j, k);
     } else {
       const int bxi = lb % en.gx, rest = lb / en.gx;
       const int byi = rest % en.gy, k = rest / en.gy;
       const int j = byi * blockDim.y + threadIdx.y;
       const int m = bxi * blockDim.x + threadIdx.x;
-      if (m < G.hx && j < G.ny) smooth_cell<float, false>(x, g, G, inv, 1, m, j, k);
+      if (m < G.hx && j < G.ny) smooth_cell<float, false, PER>(x, g, G, inv, 1, m, j, k);
     }
   });
 }
 
-template <typename T, bool RED_ONLY>
+template <typename T, bool RED_ONLY, bool PER>
 __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restrict__ E, const int* __restrict__ start,
                                                          int count, int total, const int* __restrict__ active) {
   for_vblocks(E, start, count, total, active, [&](const BEntry& en, int, int lb) {
@@ -105,14 +107,14 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BEntry* __restric
       constexpr int V = 16 / sizeof(T);
       int iv, J, K;
       if (flat_coords(lb, en.gx, Gc.nx / V, Gc.ny, iv, J, K))
-        resid_restrict_vec<T, V, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, iv, J, K);
+        resid_restrict_vec<T, V, RED_ONLY, PER>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, iv, J, K);
     } else {
       const int bxi = lb % en.gx, rest = lb / en.gx;
       const int byi = rest % en.gy, K = rest / en.gy;
       const int I = bxi * blockDim.x + threadIdx.x;
       const int J = byi * blockDim.y + threadIdx.y;
       if (I < Gc.nx && J < Gc.ny)
-        resid_restrict_cell<T, RED_ONLY>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
+        resid_restrict_cell<T, RED_ONLY, PER>((const T*)en.x, (const T*)en.g, G, (T*)en.gc, Gc, I, J, K);
     }
   });
 }
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(1024) kb_coarse_cg(const BEntry* __restrict__ 
   coarse_cg_block<T>((T*)en.x, (const T*)en.g, G, rtol, 2 * n, sm, red);
 }
 
-template <int MODE>
+template <int MODE, bool PER>
 __global__ void __launch_bounds__(256, 3) kb_resid_norm(const BEntry* __restrict__ E, const int* __restrict__ start,
                                                      int count, int total, const int* __restrict__ active,
                                                      const int* __restrict__ zero, const double* __restrict__ scal,
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256, 3) kb_resid_norm(const BEntry* __restrict
       if (threadIdx.x == 0 && threadIdx.y == 0) partials[__ldg(start + e) + lb] = 0.0;
       return;
     }
-    double acc = resid_norm_accum<double, MODE>((const double*)en.x, (const double*)en.g, en.G, lb, nb, 0.0, nullptr,
+    double acc = resid_norm_accum<double, MODE, PER>((const double*)en.x, (const double*)en.g, en.G, lb, nb, 0.0, nullptr,
                                                 (float*)en.aux, isc);
     acc = block_sum(acc, red);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[__ldg(start + e) + lb] = acc;
@@ -239,27 +241,39 @@ template <typename T>
 cudaError_t launch_b_smooth(const BLaunch& L, const int* active, const InvDiag<T>& inv, int colour, bool zero,
                             cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  if (zero)
-    kb_smooth<T, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
+  if (zero)  // no neighbour is read
+    kb_smooth<T, true, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
+  else if (L.per)
+    kb_smooth<T, false, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
   else
-    kb_smooth<T, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
+    kb_smooth<T, false, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, colour);
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_smooth_prolong(const BLaunch& L, const int* active, const InvDiag<float>& inv, float omega,
                                     cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  kb_smooth_prolong<<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, omega);
+  if (L.per)
+    kb_smooth_prolong<true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, omega);
+  else
+    kb_smooth_prolong<false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, inv, omega);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_b_resid_restrict(const BLaunch& L, const int* active, bool red_only, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  if (red_only)
-    kb_resid_restrict<T, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
-  else
-    kb_resid_restrict<T, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
+  if (L.per) {
+    if (red_only)
+      kb_resid_restrict<T, true, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
+    else
+      kb_resid_restrict<T, false, true><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
+  } else {
+    if (red_only)
+      kb_resid_restrict<T, true, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
+    else
+      kb_resid_restrict<T, false, false><<<persist(L), L.block, 0, s>>>(L.entries, L.start, L.count, L.blocks, active);
+  }
   return cudaGetLastError();
 }
 
@@ -289,12 +303,15 @@ cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* 
                                 double* partials, cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
   const dim3 b(kResBX, kResBY, 1);
-  if (mode == 2)
-    kb_resid_norm<2><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal,
-                                                  partials);
+  const dim3 g = persist(L, 12);
+  if (mode == 2 && L.per)
+    kb_resid_norm<2, true><<<g, b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal, partials);
+  else if (mode == 2)
+    kb_resid_norm<2, false><<<g, b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal, partials);
+  else if (L.per)
+    kb_resid_norm<0, true><<<g, b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal, partials);
   else
-    kb_resid_norm<0><<<persist(L, 12), b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal,
-                                                  partials);
+    kb_resid_norm<0, false><<<g, b, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   kb_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, zero, partials, scal);

@@ -333,14 +333,9 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
     if (d[a] < 4 || (d[a] % 2) != 0) return fail(c, MG_ERR_INVALID, "grid dimensions must be even and >= 4");
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(c, MG_ERR_INVALID, "h must be positive");
   if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(c, MG_ERR_INVALID, "eps must be positive");
-  bool all_neumann = true;
-  for (int q = 0; q < 6; ++q) {
-    if (p->bc_type[q] != MG_BC_DIRICHLET && p->bc_type[q] != MG_BC_NEUMANN)
-      return fail(c, MG_ERR_INVALID, "bc_type must be MG_BC_DIRICHLET or MG_BC_NEUMANN");
+  if (const char* why = check_bc_types(p->bc_type)) return fail(c, MG_ERR_INVALID, why);
+  for (int q = 0; q < 6; ++q)
     if (!std::isfinite(p->bc_value[q])) return fail(c, MG_ERR_INVALID, "bc_value must be finite");
-    if (p->bc_type[q] == MG_BC_DIRICHLET) all_neumann = false;
-  }
-  if (all_neumann) return fail(c, MG_ERR_INVALID, "all-Neumann walls give a singular problem");
   if (p->nu1 < 0 || p->nu1 > 16 || p->nu2 < 1 || p->nu2 > 16)
     return fail(c, MG_ERR_INVALID, "need 0 <= nu1 <= 16 and 1 <= nu2 <= 16");
   if (!std::isfinite(p->cgc_weight)) return fail(c, MG_ERR_INVALID, "cgc_weight must be finite");
@@ -363,7 +358,8 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
     G.nx = dims[0];
     G.ny = dims[1];
     G.nz = dims[2];
-    for (int q = 0; q < 6; ++q) G.sh[q] = p->bc_type[q] == MG_BC_DIRICHLET ? 1 : -1;
+    for (int q = 0; q < 6; ++q) G.sh[q] = face_shift(p->bc_type[q]);
+    G.per = periodic_bits(p->bc_type);
     ++c->L;
     bool ok = true;
     for (int a = 0; a < 3; ++a)
@@ -513,6 +509,7 @@ mg_status mg_set_bc_field(mg_ctx* c, int face, const double* d_values) {
     c->bc.field[face] = nullptr;
     return MG_OK;
   }
+  if (c->bc.type[face] == MG_BC_PERIODIC) return fail(c, MG_ERR_INVALID, "a periodic face has no wall values");
   const Geom& G = c->geo[0];
   const size_t bytes = (size_t)face_cells(face, G.nx, G.ny, G.nz) * sizeof(double);
   if (!c->d_bcf[face]) {

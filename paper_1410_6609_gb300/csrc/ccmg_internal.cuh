@@ -32,8 +32,34 @@ struct Geom {
   int hx;          // nx / 2 on packed levels
   long long csz;   // entries per colour array (packed) or nx*ny*nz (natural)
   int packed;      // 1: red/black arrays; 0: natural order
-  int sh[6];       // diagonal shift of each face (+1 Dirichlet, -1 Neumann)
+  int sh[6];       // diagonal shift of each face (+1 Dirichlet, -1 Neumann, 0 periodic)
+  int per;         // bit a set: axis a (0 x, 1 y, 2 z) is periodic (its neighbour wraps around)
 };
+
+// Diagonal shift of a face of type t (0 Dirichlet, 1 Neumann, 2 periodic; Sec. 2.4).
+inline int face_shift(int t) { return t == 0 ? 1 : (t == 1 ? -1 : 0); }
+// nullptr if six face types form a valid, non-singular set: each Dirichlet, Neumann or periodic,
+// periodic faces in opposite pairs, and at least one Dirichlet face (Neumann and periodic walls
+// alone leave the constant in the null space); else the reason.
+inline const char* check_bc_types(const int* type6) {
+  bool dirichlet = false;
+  for (int q = 0; q < 6; ++q) {
+    if (type6[q] < 0 || type6[q] > 2) return "bc_type must be MG_BC_DIRICHLET, MG_BC_NEUMANN or MG_BC_PERIODIC";
+    if (type6[q] == 0) dirichlet = true;
+  }
+  for (int a = 0; a < 3; ++a)
+    if ((type6[2 * a] == 2) != (type6[2 * a + 1] == 2)) return "periodic faces come in opposite pairs";
+  if (!dirichlet) return "walls without a Dirichlet face give a singular problem";
+  return nullptr;
+}
+
+// Periodic-axis bits of six face types (both faces of an axis periodic).
+inline int periodic_bits(const int* type6) {
+  int b = 0;
+  for (int a = 0; a < 3; ++a)
+    if (type6[2 * a] == 2 && type6[2 * a + 1] == 2) b |= 1 << a;
+  return b;
+}
 
 template <typename T>
 struct InvDiag {
@@ -41,7 +67,7 @@ struct InvDiag {
 };
 
 // Wall conditions of the six faces (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z): type 0 Dirichlet, 1 Neumann,
-// with one value per face, or, where field[q] is set, one value per face cell (faces 0,1: index
+// 2 periodic (both faces of an axis; no value), with one value per face, or, where field[q] is set, one value per face cell (faces 0,1: index
 // j + ny k; 2,3: i + nx k; 4,5: i + nx j), device memory the context owns.
 struct FaceBC {
   int type[6];
@@ -207,6 +233,7 @@ struct BLaunch {
   int count;
   int blocks;             // start[count]
   dim3 block;
+  int per;                // some system of the launch has a periodic axis
 };
 
 template <typename T>

@@ -29,6 +29,18 @@ __device__ __forceinline__ long long nat(const Geom& G, int i, int j, int k) {
   return (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
 }
 
+// v modulo n in [0, n): the cell a coordinate along a periodic axis stands for.
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+  const int r = v % n;
+  return r < 0 ? r + n : r;
+}
+// The coordinate along axis a (0 x, 1 y, 2 z) wrapped where the axis is periodic (Sec. 2.4: the
+// domain extended cyclically), unchanged otherwise.
+__device__ __forceinline__ int wrap_axis(const Geom& G, int a, int v) {
+  const int n = a == 0 ? G.nx : (a == 1 ? G.ny : G.nz);
+  return ((G.per >> a) & 1) ? wrap_mod(v, n) : v;
+}
+
 __device__ __forceinline__ double ld_phi(const double* __restrict__ x, const Geom& G, int i, int j, int k) {
   if (G.packed) {
     const int c = (i + j + k) & 1;
@@ -37,16 +49,22 @@ __device__ __forceinline__ double ld_phi(const double* __restrict__ x, const Geo
   return __ldg(x + nat(G, i, j, k));
 }
 
-// phi at the neighbour of (i,j,k) along axis a in direction dir, or the wall ghost value.
+// phi at the neighbour of (i,j,k) along axis a in direction dir, or the wall ghost value (across
+// a periodic axis: the cell at the opposite side).
 // FIELD: the faces may carry values per cell (FaceBC::field); the kernels are compiled both ways
 // so that the common uniform case keeps its small register footprint.
-template <bool FIELD = true>
+// PER = false: compiled without periodic support (for kernels launched on levels without one).
+template <bool FIELD = true, bool PER = true>
 __device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geom& G, int i, int j, int k, int a,
                                          int dir, double here, double h, const FaceBC& bc) {
   int q[3] = {i, j, k};
   const int n[3] = {G.nx, G.ny, G.nz};
   q[a] += dir;
   if (q[a] < 0 || q[a] >= n[a]) {
+    if (PER && ((G.per >> a) & 1)) {  // the cell at the opposite side
+      q[a] = q[a] < 0 ? n[a] - 1 : 0;
+      return ld_phi(x, G, q[0], q[1], q[2]);
+    }
     const int face = 2 * a + (dir > 0 ? 1 : 0);
     const double g = FIELD ? face_value(bc, face, i, j, k, G.nx, G.ny) : bc.value[face];
     if (bc.type[face] == 0) return 2.0 * g - here;
@@ -61,7 +79,7 @@ __device__ __forceinline__ double phi_nb(const double* __restrict__ x, const Geo
 // -((up - dn) * inv2h) exactly.
 // POW2: inv2h = 2^q2 (a power-of-two cell size); the interior products are then exponent shifts
 // (ldexp_rne), equal to the FP64 multiply.
-template <bool POW2, bool FIELD = true>
+template <bool POW2, bool FIELD = true, bool PER = true>
 __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Geom& G, int i, int j, int k, double h,
                                           double inv2h, int q2, const FaceBC& bc, double E[3]) {
   const bool interior = i > 0 && i < G.nx - 1 && j > 0 && j < G.ny - 1 && k > 0 && k < G.nz - 1;
@@ -76,8 +94,8 @@ __device__ __forceinline__ void efield_at(const double* __restrict__ x, const Ge
     const double here = ld_phi(x, G, i, j, k);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double up = phi_nb<FIELD>(x, G, i, j, k, a, +1, here, h, bc);
-      const double dn = phi_nb<FIELD>(x, G, i, j, k, a, -1, here, h, bc);
+      const double up = phi_nb<FIELD, PER>(x, G, i, j, k, a, +1, here, h, bc);
+      const double dn = phi_nb<FIELD, PER>(x, G, i, j, k, a, -1, here, h, bc);
       E[a] = -((up - dn) * inv2h);
     }
   }
@@ -91,8 +109,10 @@ __constant__ int kD3Q19[18][3] = {{1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}
                                   {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1},
                                   {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
+// All 18 neighbours exist: inside the domain, or across a periodic axis.
 __device__ __forceinline__ bool d3q19_inside(const Geom& G, int i, int j, int k) {
-  return i > 0 && i < G.nx - 1 && j > 0 && j < G.ny - 1 && k > 0 && k < G.nz - 1;
+  return ((G.per & 1) || (i > 0 && i < G.nx - 1)) && ((G.per & 2) || (j > 0 && j < G.ny - 1)) &&
+         ((G.per & 4) || (k > 0 && k < G.nz - 1));
 }
 
 __device__ __forceinline__ void efield19_at(const double* __restrict__ x, const Geom& G, int i, int j, int k, double h,
@@ -102,7 +122,8 @@ __device__ __forceinline__ void efield19_at(const double* __restrict__ x, const 
   for (int q = 0; q < 18; ++q) {
     const int e0 = kD3Q19[q][0], e1 = kD3Q19[q][1], e2 = kD3Q19[q][2];
     const double w = q < 6 ? 1.0 / 18.0 : 1.0 / 36.0;
-    const double wv = __dmul_rn(w, ld_phi(x, G, i + e0, j + e1, k + e2));
+    // d3q19_inside holds: a coordinate leaves the domain only along a periodic axis
+    const double wv = __dmul_rn(w, ld_phi(x, G, wrap_axis(G, 0, i + e0), wrap_axis(G, 1, j + e1), wrap_axis(G, 2, k + e2)));
     if (e0) g[0] = __dadd_rn(g[0], e0 > 0 ? wv : -wv);
     if (e1) g[1] = __dadd_rn(g[1], e1 > 0 ? wv : -wv);
     if (e2) g[2] = __dadd_rn(g[2], e2 > 0 ? wv : -wv);
@@ -140,12 +161,15 @@ __device__ __forceinline__ int overlap_count(int i, int j, int k, double h, doub
   return cnt;
 }
 
-// Cells [lo, hi] along one axis that can touch the sphere (every other cell has count 0).
-__device__ __forceinline__ void cell_range(double c, double R, double h, int n, int& lo, int& hi) {
+// Cells [lo, hi] along one axis that can touch the sphere (every other cell has count 0),
+// clipped to the domain unless the axis is periodic: there cells beyond an end stand for those at
+// the opposite side (the sphere's periodic image), and the kernels keep the unwrapped coordinate
+// for the sub-cell positions and wrap it where they touch memory.
+__device__ __forceinline__ void cell_range(double c, double R, double h, int n, bool periodic, int& lo, int& hi) {
   int a = (int)floor((c - R) / h) - 1;
   int b = (int)floor((c + R) / h) + 1;
-  lo = a < 0 ? 0 : a;
-  hi = b > n - 1 ? n - 1 : b;
+  lo = (a < 0 && !periodic) ? 0 : a;
+  hi = (b > n - 1 && !periodic) ? n - 1 : b;
 }
 
 struct Box {
@@ -157,14 +181,21 @@ __device__ __forceinline__ Box sphere_box(const Geom& G, double h, const double*
   Box B;
   const int n[3] = {G.nx, G.ny, G.nz};
   for (int a = 0; a < 3; ++a) {
-    cell_range(c[a], R, h, n[a], B.lo[a], B.hi[a]);
-    B.lo[a] = max(B.lo[a] - dilate, 0);
-    B.hi[a] = min(B.hi[a] + dilate, n[a] - 1);
+    const bool per = (G.per >> a) & 1;
+    cell_range(c[a], R, h, n[a], per, B.lo[a], B.hi[a]);
+    B.lo[a] = per ? B.lo[a] - dilate : max(B.lo[a] - dilate, 0);
+    B.hi[a] = per ? B.hi[a] + dilate : min(B.hi[a] + dilate, n[a] - 1);
     B.nb[a] = B.hi[a] - B.lo[a] + 1;
     if (B.nb[a] < 0) B.nb[a] = 0;
   }
   B.ncell = (long long)B.nb[0] * B.nb[1] * B.nb[2];
   return B;
+}
+
+// Natural-order index of the cell an (unwrapped) box coordinate stands for.
+__device__ __forceinline__ long long nat_wrapped(const Geom& G, int i, int j, int k) {
+  return (long long)wrap_axis(G, 0, i) +
+         (long long)G.nx * ((long long)wrap_axis(G, 1, j) + (long long)G.ny * wrap_axis(G, 2, k));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -229,7 +260,7 @@ __global__ void __launch_bounds__(256) k_efield(const double* __restrict__ x, Ge
 // colours in the four neighbour rows) and its 16-byte stores of each component are contiguous.
 // Interior pairs take the differences directly, in efield_at's order; pairs at a wall call
 // efield_at per cell.
-template <bool POW2, bool FIELD>
+template <bool POW2, bool FIELD, bool PER>
 __global__ void __launch_bounds__(256) k_efield_pair(const double* __restrict__ x, Geom G, double h, double inv2h,
                                                      int q2, FaceBC bc, double* __restrict__ E) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,8 +292,8 @@ __global__ void __launch_bounds__(256) k_efield_pair(const double* __restrict__ 
     e1[1] = POW2 ? ldexp_rne(d11, q2) : d11 * inv2h;
     e1[2] = POW2 ? ldexp_rne(d12, q2) : d12 * inv2h;
   } else {
-    efield_at<POW2, FIELD>(x, G, i0, j, k, h, inv2h, q2, bc, e0);
-    efield_at<POW2, FIELD>(x, G, i0 + 1, j, k, h, inv2h, q2, bc, e1);
+    efield_at<POW2, FIELD, PER>(x, G, i0, j, k, h, inv2h, q2, bc, e0);
+    efield_at<POW2, FIELD, PER>(x, G, i0 + 1, j, k, h, inv2h, q2, bc, e1);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) *reinterpret_cast<double2*>(E + a * N + p) = make_double2(e0[a], e1[a]);
@@ -285,7 +316,7 @@ __global__ void __launch_bounds__(256) k_sphere_density(Geom G, double h, Sphere
     const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
     const int cnt = overlap_count<SFC>(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
     if (cnt == 0) continue;
-    atomicAdd(rho + nat(G, i, j, k), q * ((double)cnt / sf3));
+    atomicAdd(rho + nat_wrapped(G, i, j, k), q * ((double)cnt / sf3));
   }
 }
 
@@ -309,9 +340,10 @@ __global__ void __launch_bounds__(256) k_force_gather(const double* __restrict__
     const int cnt = overlap_count<SFC>(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
     if (cnt == 0) continue;
     const double w = (double)cnt / sf3;
+    const int iw = wrap_axis(G, 0, i), jw = wrap_axis(G, 1, j), kw = wrap_axis(G, 2, k);
     double e[3];
-    if (st19 && d3q19_inside(G, i, j, k)) efield19_at(x, G, i, j, k, h, e);
-    else efield_at<false, FIELD>(x, G, i, j, k, h, inv2h, kBadPow2, bc, e);
+    if (st19 && d3q19_inside(G, iw, jw, kw)) efield19_at(x, G, iw, jw, kw, h, e);
+    else efield_at<false, FIELD>(x, G, iw, jw, kw, h, inv2h, kBadPow2, bc, e);
     for (int a = 0; a < 3; ++a) acc[a] = acc[a] + w * e[a];
   }
   block_sum3(acc, red);
@@ -346,27 +378,31 @@ __global__ void __launch_bounds__(256) k_force_adjoint(const double* __restrict_
     double gp = 0.0;
     const int cnt_p = overlap_count(p[0], p[1], p[2], h, c[0], c[1], c[2], R2, sf, so);
     const double w_p = (double)cnt_p / sf3;
+    const int pw[3] = {wrap_axis(G, 0, p[0]), wrap_axis(G, 1, p[1]), wrap_axis(G, 2, p[2])};
     if (cnt_p) {
       double e[3];
-      efield_at<false>(x, G, p[0], p[1], p[2], h, inv2h, kBadPow2, bc, e);
+      efield_at<false>(x, G, pw[0], pw[1], pw[2], h, inv2h, kBadPow2, bc, e);
       for (int a = 0; a < 3; ++a) fsum[a] = fsum[a] + w_p * e[a];
     }
     for (int a = 0; a < 3; ++a) {
+      // along a periodic axis every cell has both neighbours (in the box's unwrapped frame) and
+      // no ghost
+      const bool per = (G.per >> a) & 1;
       // p is the +e_a neighbour of b = p - e_a:  dE_a(b)/dphi(p) = -1/(2h)
-      if (p[a] - 1 >= 0) {
+      if (per || p[a] - 1 >= 0) {
         int b[3] = {p[0], p[1], p[2]};
         b[a] -= 1;
         const int cb = overlap_count(b[0], b[1], b[2], h, c[0], c[1], c[2], R2, sf, so);
         if (cb) gp = gp - (wa[a] * pre * ((double)cb / sf3)) * inv2h;
       }
       // p is the -e_a neighbour of b = p + e_a:  dE_a(b)/dphi(p) = +1/(2h)
-      if (p[a] + 1 < n[a]) {
+      if (per || p[a] + 1 < n[a]) {
         int b[3] = {p[0], p[1], p[2]};
         b[a] += 1;
         const int cb = overlap_count(b[0], b[1], b[2], h, c[0], c[1], c[2], R2, sf, so);
         if (cb) gp = gp + (wa[a] * pre * ((double)cb / sf3)) * inv2h;
       }
-      if (cnt_p) {
+      if (cnt_p && !per) {
         const double gE = wa[a] * pre * w_p;
         if (p[a] == 0) {  // -e_a neighbour is the ghost of face 2a
           const int face = 2 * a;
@@ -392,7 +428,7 @@ __global__ void __launch_bounds__(256) k_force_adjoint(const double* __restrict_
         }
       }
     }
-    if (gp != 0.0) atomicAdd(gphi + nat(G, p[0], p[1], p[2]), gp);
+    if (gp != 0.0) atomicAdd(gphi + nat_wrapped(G, p[0], p[1], p[2]), gp);
   }
   block_sum3(fsum, red);
   if (threadIdx.x == 0) {
@@ -420,7 +456,7 @@ __global__ void __launch_bounds__(256) k_density_adjoint(Geom G, double h, Spher
     const int k = B.lo[2] + (int)(t / ((long long)B.nb[0] * B.nb[1]));
     const int cnt = overlap_count(i, j, k, h, c[0], c[1], c[2], R2, sf, so);
     if (cnt == 0) continue;
-    acc[0] = acc[0] + ((double)cnt / sf3) * gf[nat(G, i, j, k)];
+    acc[0] = acc[0] + ((double)cnt / sf3) * gf[nat_wrapped(G, i, j, k)];
   }
   block_sum3(acc, red);
   if (threadIdx.x == 0) gdens[s] = acc[0];
@@ -432,7 +468,8 @@ __global__ void __launch_bounds__(256) k_scale_copy(const double* __restrict__ a
     b[i] = a[i] * s;
 }
 
-// Six CTAs, one per wall: gbc[q] = sum over the wall's cells of lambda * (2/h^2 or 1/h).
+// Six CTAs, one per wall: gbc[q] = sum over the wall's cells of lambda * (2/h^2 or 1/h); a
+// periodic face has no value (0).
 __global__ void __launch_bounds__(256) k_face_sums(Geom G, double h, FaceBC bc, const double* __restrict__ lam,
                                                    double* __restrict__ gbc) {
   __shared__ double red[32][3];
@@ -451,7 +488,7 @@ __global__ void __launch_bounds__(256) k_face_sums(Geom G, double h, FaceBC bc, 
     acc[0] = acc[0] + lam[nat(G, p[0], p[1], p[2])];
   }
   block_sum3(acc, red);
-  if (threadIdx.x == 0) gbc[q] = acc[0] * (bc.type[q] == 0 ? 2.0 / (h * h) : 1.0 / h);
+  if (threadIdx.x == 0) gbc[q] = bc.type[q] == 2 ? 0.0 : acc[0] * (bc.type[q] == 0 ? 2.0 / (h * h) : 1.0 / h);
 }
 
 SubOff make_suboff(int sf) {
@@ -476,12 +513,15 @@ cudaError_t launch_efield(const double* x, const Geom& G, double h, const FaceBC
   if (G.packed && reinterpret_cast<uintptr_t>(E) % 16 == 0) {
     const int bx = G.hx >= 128 ? 128 : (G.hx >= 64 ? 64 : 32);
     dim3 b(bx, 256 / bx, 1), g((G.hx + bx - 1) / bx, (G.ny + 256 / bx - 1) / (256 / bx), G.nz);
-    if (fld) {
-      if (q2 != kBadPow2) k_efield_pair<true, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
-      else k_efield_pair<false, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    if (G.per) {  // periodic axes (no per-cell values there; other faces may have them)
+      if (q2 != kBadPow2) k_efield_pair<true, true, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+      else k_efield_pair<false, true, true><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+    } else if (fld) {
+      if (q2 != kBadPow2) k_efield_pair<true, true, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+      else k_efield_pair<false, true, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
     } else {
-      if (q2 != kBadPow2) k_efield_pair<true, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
-      else k_efield_pair<false, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+      if (q2 != kBadPow2) k_efield_pair<true, false, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
+      else k_efield_pair<false, false, false><<<g, b, 0, s>>>(x, G, h, inv2h, q2, bc, E);
     }
     return cudaGetLastError();
   }

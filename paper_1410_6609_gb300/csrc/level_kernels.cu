@@ -22,17 +22,19 @@ __global__ void __launch_bounds__(256) k_smooth(T* __restrict__ x, const T* __re
   smooth_cell<T, ZERO>(x, g, G, inv, colour, m, j, k);
 }
 
-template <typename T, int V, bool ZERO>
+template <typename T, int V, bool ZERO, bool PER>
 __global__ void __launch_bounds__(256) k_smooth_vec(T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                     InvDiag<T> inv, int colour) {
   const int mv = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (mv >= G.hx / V || j >= G.ny) return;
-  smooth_vec<T, V, ZERO>(x, g, G, inv, colour, mv, j, k);
+  smooth_vec<T, V, ZERO, PER>(x, g, G, inv, colour, mv, j, k);
 }
 
-template <typename T, int V>
+// PER: compiled with periodic-axis support (launched for levels that have a periodic axis; the
+// other variant keeps the register footprint of walls alone).
+template <typename T, int V, bool PER>
 __global__ void __launch_bounds__(256) k_smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                             InvDiag<T> inv, const T* __restrict__ ec, Geom Gc,
                                                             T omega) {
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(256) k_smooth_vec_prolong(T* __restrict__ x, c
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (mv >= G.hx / V || j >= G.ny) return;
-  smooth_vec_prolong<T, V>(x, g, G, inv, ec, Gc, omega, mv, j, k);
+  smooth_vec_prolong<T, V, PER>(x, g, G, inv, ec, Gc, omega, mv, j, k);
 }
 
 template <typename T, bool RED_ONLY>
@@ -53,14 +55,14 @@ __global__ void __launch_bounds__(256) k_resid_restrict(const T* __restrict__ x,
   resid_restrict_cell<T, RED_ONLY>(x, g, G, gc, Gc, I, J, K);
 }
 
-template <typename T, int V, bool RED_ONLY>
+template <typename T, int V, bool RED_ONLY, bool PER>
 __global__ void __launch_bounds__(256) k_resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                             T* __restrict__ gc, Geom Gc) {
   const int iv = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (iv >= Gc.nx / V || J >= Gc.ny) return;
-  resid_restrict_vec<T, V, RED_ONLY>(x, g, G, gc, Gc, iv, J, K);
+  resid_restrict_vec<T, V, RED_ONLY, PER>(x, g, G, gc, Gc, iv, J, K);
 }
 
 template <typename T>
@@ -86,14 +88,14 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(T* __restrict__ xo, const T*
 // Scaled residual with per-block partial sums of r~^2 (the termination test of Algorithm 1); the
 // row walk and the reduction are in level_ops.cuh (resid_norm_accum), so a batched launch over
 // many systems reproduces each system's partial sums exactly.
-template <typename T, int MODE>
+template <typename T, int MODE, bool PER>
 __global__ void __launch_bounds__(256, 3) k_resid_norm(const T* __restrict__ x, const T* __restrict__ g, Geom G,
                                                     double* __restrict__ partials, double c0,
                                                     double* __restrict__ outn, float* __restrict__ outp,
                                                     const double* __restrict__ inv_scale) {
   __shared__ double red[33];
   const double isc = (MODE == 2) ? inv_scale[0] : 0.0;
-  double acc = resid_norm_accum<T, MODE>(x, g, G, blockIdx.x, gridDim.x, c0, outn, outp, isc);
+  double acc = resid_norm_accum<T, MODE, PER>(x, g, G, blockIdx.x, gridDim.x, c0, outn, outp, isc);
   acc = block_sum(acc, red);
   if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = acc;
 }
@@ -149,14 +151,16 @@ __device__ __forceinline__ double wall_term(const WallTerms& wt, int q, int i, i
 }
 // FIELD: some face carries values per cell (the kernels are compiled both ways, so the common
 // uniform case keeps its small register footprint).
+// A periodic face has no wall term (its neighbour is the cell at the opposite side).
 template <bool FIELD>
 __device__ __forceinline__ double add_wall_terms(double v, int i, int j, int k, const Geom& G, const WallTerms& wt) {
-  if (i == 0) v = v + (FIELD ? wall_term(wt, 0, i, j, k, G) : wt.t[0]);
-  if (i == G.nx - 1) v = v + (FIELD ? wall_term(wt, 1, i, j, k, G) : wt.t[1]);
-  if (j == 0) v = v + (FIELD ? wall_term(wt, 2, i, j, k, G) : wt.t[2]);
-  if (j == G.ny - 1) v = v + (FIELD ? wall_term(wt, 3, i, j, k, G) : wt.t[3]);
-  if (k == 0) v = v + (FIELD ? wall_term(wt, 4, i, j, k, G) : wt.t[4]);
-  if (k == G.nz - 1) v = v + (FIELD ? wall_term(wt, 5, i, j, k, G) : wt.t[5]);
+  const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0, pz = (G.per & 4) != 0;
+  if (i == 0 && !px) v = v + (FIELD ? wall_term(wt, 0, i, j, k, G) : wt.t[0]);
+  if (i == G.nx - 1 && !px) v = v + (FIELD ? wall_term(wt, 1, i, j, k, G) : wt.t[1]);
+  if (j == 0 && !py) v = v + (FIELD ? wall_term(wt, 2, i, j, k, G) : wt.t[2]);
+  if (j == G.ny - 1 && !py) v = v + (FIELD ? wall_term(wt, 3, i, j, k, G) : wt.t[3]);
+  if (k == 0 && !pz) v = v + (FIELD ? wall_term(wt, 4, i, j, k, G) : wt.t[4]);
+  if (k == G.nz - 1 && !pz) v = v + (FIELD ? wall_term(wt, 5, i, j, k, G) : wt.t[5]);
   return v;
 }
 // POW2: 1/eps = 2^qe and h^2 = 2^qh (lattice units), the products are exponent shifts.
@@ -333,10 +337,12 @@ cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv
     while (bx < nvec && bx < 128) bx *= 2;
     const int by = 256 / bx;
     dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
-    if (zero_start)
-      k_smooth_vec<T, V, true><<<gr, b, 0, s>>>(x, g, G, inv, colour);
+    if (zero_start)  // no neighbour is read
+      k_smooth_vec<T, V, true, false><<<gr, b, 0, s>>>(x, g, G, inv, colour);
+    else if (G.per)
+      k_smooth_vec<T, V, false, true><<<gr, b, 0, s>>>(x, g, G, inv, colour);
     else
-      k_smooth_vec<T, V, false><<<gr, b, 0, s>>>(x, g, G, inv, colour);
+      k_smooth_vec<T, V, false, false><<<gr, b, 0, s>>>(x, g, G, inv, colour);
     return cudaGetLastError();
   }
   dim3 b, gr;
@@ -357,7 +363,10 @@ cudaError_t launch_smooth_prolong(float* x, const float* g, const Geom& G, const
   while (bx < nvec && bx < 128) bx *= 2;
   const int by = 256 / bx;
   dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
-  k_smooth_vec_prolong<float, V><<<gr, b, 0, s>>>(x, g, G, inv, ec, Gc, omega);
+  if (G.per)
+    k_smooth_vec_prolong<float, V, true><<<gr, b, 0, s>>>(x, g, G, inv, ec, Gc, omega);
+  else
+    k_smooth_vec_prolong<float, V, false><<<gr, b, 0, s>>>(x, g, G, inv, ec, Gc, omega);
   return cudaGetLastError();
 }
 
@@ -371,10 +380,17 @@ cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, 
     while (bx < nvec && bx < 64) bx *= 2;
     const int by = 256 / bx;
     dim3 b(bx, by, 1), gr((nvec + bx - 1) / bx, (Gc.ny + by - 1) / by, Gc.nz);
-    if (red_only)
-      k_resid_restrict_vec<T, V, true><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
-    else
-      k_resid_restrict_vec<T, V, false><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+    if (G.per) {
+      if (red_only)
+        k_resid_restrict_vec<T, V, true, true><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+      else
+        k_resid_restrict_vec<T, V, false, true><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+    } else {
+      if (red_only)
+        k_resid_restrict_vec<T, V, true, false><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+      else
+        k_resid_restrict_vec<T, V, false, false><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+    }
     return cudaGetLastError();
   }
   dim3 b, gr;
@@ -420,9 +436,15 @@ cudaError_t launch_resid_norm(const T* x, const T* g, const Geom& G, double* par
                               cudaStream_t s) {
   const int grid = resid_norm_blocks(G);
   const dim3 b(kResBX, kResBY, 1);
-  if (mode == 0) k_resid_norm<T, 0><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-  if (mode == 1) k_resid_norm<T, 1><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
-  if (mode == 2) k_resid_norm<T, 2><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+  if (G.per) {
+    if (mode == 0) k_resid_norm<T, 0, true><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+    if (mode == 1) k_resid_norm<T, 1, true><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+    if (mode == 2) k_resid_norm<T, 2, true><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+  } else {
+    if (mode == 0) k_resid_norm<T, 0, false><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+    if (mode == 1) k_resid_norm<T, 1, false><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+    if (mode == 2) k_resid_norm<T, 2, false><<<grid, b, 0, s>>>(x, g, G, partials, c0, out_natural, out_packed, inv_scale);
+  }
   *nparts = grid;
   return cudaGetLastError();
 }
@@ -453,7 +475,7 @@ cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_ep
                            cudaStream_t s) {
   WallTerms wt;
   for (int q = 0; q < 6; ++q) {
-    wt.t[q] = bc.type[q] == 0 ? 2.0 * bc.value[q] / (h * h) : bc.value[q] / h;
+    wt.t[q] = bc.type[q] == 0 ? 2.0 * bc.value[q] / (h * h) : (bc.type[q] == 1 ? bc.value[q] / h : 0.0);
     wt.field[q] = bc.field[q];
     wt.type[q] = bc.type[q];
   }

@@ -225,22 +225,6 @@ __device__ __forceinline__ double f64_of_scaled(float e, int p) {
   return ldexp_rne_general((double)e, p);  // subnormals, infinities, NaN, range ends
 }
 
-// Sum of the six neighbours (in the order -x,+x,-y,+y,-z,+z; absent ones are zero) of the cell at
-// index m of row `row` in colour c, where y points at the other colour's array.
-template <typename T>
-__device__ __forceinline__ T nbsum_packed(const T* __restrict__ y, const Geom& G, long long row, int m, int s, int j,
-                                          int k) {
-  const long long plane = (long long)G.ny * G.hx;
-  const T* yr = y + row;
-  const T xm = (m == 0 && s == 0) ? T(0) : __ldg(yr + m + s - 1);
-  const T xp = (m == G.hx - 1 && s == 1) ? T(0) : __ldg(yr + m + s);
-  const T ym = (j > 0) ? __ldg(yr + m - G.hx) : T(0);
-  const T yp = (j < G.ny - 1) ? __ldg(yr + m + G.hx) : T(0);
-  const T zm = (k > 0) ? __ldg(yr + m - plane) : T(0);
-  const T zp = (k < G.nz - 1) ? __ldg(yr + m + plane) : T(0);
-  return ((((xm + xp) + ym) + yp) + zm) + zp;
-}
-
 // 16-byte vector loads and stores (4 floats or 2 doubles).
 __device__ __forceinline__ void load_vec(const float* p, float (&o)[4]) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
@@ -257,12 +241,62 @@ __device__ __forceinline__ void store_vec(double* p, const double (&o)[2]) {
   *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
 }
 
+// Neighbour row Q (0: -y, 1: +y, 2: -z, 3: +z) of packed row (j, k): whether it exists (inside
+// the level, or across a periodic axis, where it is the row at the opposite side: Sec. 2.4), and
+// its offset within a colour array (the same row serves the cells of either colour). PER = false
+// compiles the plain wall tests of a level without periodic axes.
+template <int Q, bool PER>
+__device__ __forceinline__ bool nb_inside(const Geom& G, int j, int k) {
+  return Q == 0 ? j > 0 : (Q == 1 ? j < G.ny - 1 : (Q == 2 ? k > 0 : k < G.nz - 1));
+}
+template <int Q, bool PER>
+__device__ __forceinline__ bool nb_has(const Geom& G, int j, int k) {
+  return nb_inside<Q, PER>(G, j, k) || (PER && (G.per & (Q < 2 ? 2 : 4)) != 0);
+}
+template <int Q, bool PER>
+__device__ __forceinline__ long long nb_off(const Geom& G, int j, int k) {
+  if (!PER || nb_inside<Q, PER>(G, j, k)) {
+    if constexpr (Q < 2) return (Q & 1) ? G.hx : -G.hx;
+    else return (Q & 1) ? (long long)G.ny * G.hx : -((long long)G.ny * G.hx);
+  }
+  if constexpr (Q < 2) return (Q & 1) ? -(long long)(G.ny - 1) * G.hx : (long long)(G.ny - 1) * G.hx;
+  else return (Q & 1) ? -(long long)(G.nz - 1) * G.ny * G.hx : (long long)(G.nz - 1) * G.ny * G.hx;
+}
+
+// Sum of the six neighbours (in the order -x,+x,-y,+y,-z,+z; absent ones are zero) of the cell at
+// index m of row `row` in colour c, where y points at the other colour's array. Across a periodic
+// x axis the neighbour of cell 0 (index 0, s = 0) is cell nx-1 (index hx-1 of the other colour)
+// and the other way round.
+template <typename T, bool PER = true>
+__device__ __forceinline__ T nbsum_packed(const T* __restrict__ y, const Geom& G, long long row, int m, int s, int j,
+                                          int k) {
+  const T* yr = y + row;
+  const bool px = PER && (G.per & 1) != 0;
+  const T xm = (m == 0 && s == 0) ? (px ? __ldg(yr + G.hx - 1) : T(0)) : __ldg(yr + m + s - 1);
+  const T xp = (m == G.hx - 1 && s == 1) ? (px ? __ldg(yr) : T(0)) : __ldg(yr + m + s);
+  const T ym = nb_has<0, PER>(G, j, k) ? __ldg(yr + m + nb_off<0, PER>(G, j, k)) : T(0);
+  const T yp = nb_has<1, PER>(G, j, k) ? __ldg(yr + m + nb_off<1, PER>(G, j, k)) : T(0);
+  const T zm = nb_has<2, PER>(G, j, k) ? __ldg(yr + m + nb_off<2, PER>(G, j, k)) : T(0);
+  const T zp = nb_has<3, PER>(G, j, k) ? __ldg(yr + m + nb_off<3, PER>(G, j, k)) : T(0);
+  return ((((xm + xp) + ym) + yp) + zm) + zp;
+}
+
+// The V-vector of neighbour row Q at m0, or zeros where the row does not exist.
+template <int Q, bool PER, typename T, int V>
+__device__ __forceinline__ void load_nb_vec(const T* __restrict__ yr, const Geom& G, int m0, int j, int k,
+                                            T (&o)[V]) {
+  if (nb_has<Q, PER>(G, j, k)) load_vec(yr + m0 + nb_off<Q, PER>(G, j, k), o);
+  else
+#pragma unroll
+    for (int i = 0; i < V; ++i) o[i] = T(0);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Red-black Gauss-Seidel half-sweep (Sec. 5.3): every cell of `colour` becomes the solution of
 // its own row, phi = (g + sum of neighbours) / (6 + d). ZERO: the level's current iterate is
 // zero (first sweep after restriction), so the neighbour sum is exactly zero and is not read.
 // Cell (m, j, k) of the colour's array; caller guarantees m < hx, j < ny, k < nz.
-template <typename T, bool ZERO>
+template <typename T, bool ZERO, bool PER = true>
 __device__ __forceinline__ void smooth_cell(T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                             const InvDiag<T>& inv, int colour, int m, int j, int k) {
   const int s = (j + k + colour) & 1;
@@ -270,7 +304,7 @@ __device__ __forceinline__ void smooth_cell(T* __restrict__ x, const T* __restri
   const long long own = (long long)colour * G.csz + row + m;
   const int d = diag_shift_packed(G, m, s, j, k);
   T S = T(0);
-  if (!ZERO) S = nbsum_packed(x + (long long)(1 - colour) * G.csz, G, row, m, s, j, k);
+  if (!ZERO) S = nbsum_packed<T, PER>(x + (long long)(1 - colour) * G.csz, G, row, m, s, j, k);
   x[own] = (__ldg(g + own) + S) * inv_of(inv, d);
 }
 
@@ -278,7 +312,7 @@ __device__ __forceinline__ void smooth_cell(T* __restrict__ x, const T* __restri
 // length is a multiple of V). The other colour's row segment m0..m0+V-1 supplies one x-neighbour
 // of every cell; the remaining one is the scalar just before (s = 0) or just after (s = 1) the
 // segment. Each cell's sum is formed in the same order as in smooth_cell: identical results.
-template <typename T, int V, bool ZERO>
+template <typename T, int V, bool ZERO, bool PER = true>
 __device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                            const InvDiag<T>& inv, int colour, int mv, int j, int k) {
   const int m0 = mv * V;
@@ -293,28 +327,17 @@ __device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restric
     for (int i = 0; i < V; ++i) out[i] = (gv[i] + T(0)) * invd[i];
   } else {
     const T* yr = x + (long long)(1 - colour) * G.csz + row;
-    const long long plane = (long long)G.ny * G.hx;
     T yc[V], ym[V], yp[V], zm[V], zp[V];
     load_vec(yr + m0, yc);
-    if (j > 0) load_vec(yr + m0 - G.hx, ym);
-    else
-#pragma unroll
-      for (int i = 0; i < V; ++i) ym[i] = T(0);
-    if (j < G.ny - 1) load_vec(yr + m0 + G.hx, yp);
-    else
-#pragma unroll
-      for (int i = 0; i < V; ++i) yp[i] = T(0);
-    if (k > 0) load_vec(yr + m0 - plane, zm);
-    else
-#pragma unroll
-      for (int i = 0; i < V; ++i) zm[i] = T(0);
-    if (k < G.nz - 1) load_vec(yr + m0 + plane, zp);
-    else
-#pragma unroll
-      for (int i = 0; i < V; ++i) zp[i] = T(0);
+    load_nb_vec<0, PER>(yr, G, m0, j, k, ym);
+    load_nb_vec<1, PER>(yr, G, m0, j, k, yp);
+    load_nb_vec<2, PER>(yr, G, m0, j, k, zm);
+    load_nb_vec<3, PER>(yr, G, m0, j, k, zp);
+    // the x-neighbour beyond the segment (the row's other end across a periodic x axis)
+    const bool px = PER && (G.per & 1) != 0;
     T extra;
-    if (s == 0) extra = (m0 > 0) ? __ldg(yr + m0 - 1) : T(0);
-    else extra = (m0 + V < G.hx) ? __ldg(yr + m0 + V) : T(0);
+    if (s == 0) extra = (m0 > 0) ? __ldg(yr + m0 - 1) : (px ? __ldg(yr + G.hx - 1) : T(0));
+    else extra = (m0 + V < G.hx) ? __ldg(yr + m0 + V) : (px ? __ldg(yr) : T(0));
 #pragma unroll
     for (int i = 0; i < V; ++i) {
       T xm, xp;
@@ -371,63 +394,76 @@ __device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, 
 // its parent at coarse (m, j'/2, k'/2). The red cells themselves are left uncorrected: the red
 // half-sweep that follows overwrites them without reading them. Same arithmetic as prolongation
 // followed by smooth_vec, hence identical results.
-template <typename T, int V>
+// PER = false: compiled without periodic support (the kernels choose by the level's walls).
+template <typename T, int V, bool PER = true>
 __device__ __forceinline__ void smooth_vec_prolong(T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                    const InvDiag<T>& inv, const T* __restrict__ ec, const Geom& Gc,
                                                    T omega, int mv, int j, int k) {
+  const int per = PER ? G.per : 0;
   const int colour = 1;
   const int m0 = mv * V;
   const int s = (j + k + colour) & 1;
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)colour * G.csz + row + m0;
   const T* yr = x + row;  // red array, row (j,k)
-  const long long plane = (long long)G.ny * G.hx;
   const int J = j >> 1, K = k >> 1;
   T gv[V], out[V], yc[V], ym[V], yp[V], zm[V], zp[V], wc[V], wy[V], wz[V], invd[V];
   inv_diag_vec<T, V>(G, inv, m0, s, j, k, invd);
   load_vec(g + own, gv);
   load_vec(yr + m0, yc);
   // coarse parents: row (J, K) serves the row itself and the y- and z-neighbour rows inside the
-  // same coarse cell; the other y (z) neighbour row has its parent in row J -+ 1 (K -+ 1)
+  // same coarse cell; the other y (z) neighbour row has its parent in row J -+ 1 (K -+ 1), which
+  // across a periodic axis is the coarse row at the opposite side
   coarse_row_w<T, V>(ec, Gc, m0, J, K, omega, wc);
-  const bool jy = (j & 1) ? (j < G.ny - 1) : (j > 0), kz = (k & 1) ? (k < G.nz - 1) : (k > 0);
-  if (jy) coarse_row_w<T, V>(ec, Gc, m0, (j & 1) ? J + 1 : J - 1, K, omega, wy);
-  if (kz) coarse_row_w<T, V>(ec, Gc, m0, J, (k & 1) ? K + 1 : K - 1, omega, wz);
+  const bool jy = (j & 1) ? nb_has<1, PER>(G, j, k) : nb_has<0, PER>(G, j, k);
+  const bool kz = (k & 1) ? nb_has<3, PER>(G, j, k) : nb_has<2, PER>(G, j, k);
+  int Jo = (j & 1) ? J + 1 : J - 1, Ko = (k & 1) ? K + 1 : K - 1;
+  if (PER) {
+    Jo = Jo == Gc.ny ? 0 : (Jo < 0 ? Gc.ny - 1 : Jo);
+    Ko = Ko == Gc.nz ? 0 : (Ko < 0 ? Gc.nz - 1 : Ko);
+  }
+  if (jy) coarse_row_w<T, V>(ec, Gc, m0, Jo, K, omega, wy);
+  if (kz) coarse_row_w<T, V>(ec, Gc, m0, J, Ko, omega, wz);
 #pragma unroll
   for (int v = 0; v < V; ++v) yc[v] = add_rn(yc[v], wc[v]);
+  // the x-neighbour beyond the segment; across a periodic x axis the red cell at the row's
+  // other end, whose parent is coarse cell (hx-1, J, K) or (0, J, K)
+  const bool px = (per & 1) != 0;
   T extra = T(0);
   if (s == 0) {
     if (m0 > 0) extra = add_rn(__ldg(yr + m0 - 1), mul_rn(omega, __ldg(ec + coarse_index(Gc, m0 - 1, J, K))));
+    else if (px) extra = add_rn(__ldg(yr + G.hx - 1), mul_rn(omega, __ldg(ec + coarse_index(Gc, G.hx - 1, J, K))));
   } else {
     if (m0 + V < G.hx) extra = add_rn(__ldg(yr + m0 + V), mul_rn(omega, __ldg(ec + coarse_index(Gc, m0 + V, J, K))));
+    else if (px) extra = add_rn(__ldg(yr), mul_rn(omega, __ldg(ec + coarse_index(Gc, 0, J, K))));
   }
   // (j-1)>>1 is J-1 for even j and J for odd j; (j+1)>>1 is J for even j and J+1 for odd j
-  if (j > 0) {
-    load_vec(yr + m0 - G.hx, ym);
+  if (nb_has<0, PER>(G, j, k)) {
+    load_vec(yr + m0 + nb_off<0, PER>(G, j, k), ym);
 #pragma unroll
     for (int v = 0; v < V; ++v) ym[v] = add_rn(ym[v], (j & 1) ? wc[v] : wy[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) ym[v] = T(0);
   }
-  if (j < G.ny - 1) {
-    load_vec(yr + m0 + G.hx, yp);
+  if (nb_has<1, PER>(G, j, k)) {
+    load_vec(yr + m0 + nb_off<1, PER>(G, j, k), yp);
 #pragma unroll
     for (int v = 0; v < V; ++v) yp[v] = add_rn(yp[v], (j & 1) ? wy[v] : wc[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) yp[v] = T(0);
   }
-  if (k > 0) {
-    load_vec(yr + m0 - plane, zm);
+  if (nb_has<2, PER>(G, j, k)) {
+    load_vec(yr + m0 + nb_off<2, PER>(G, j, k), zm);
 #pragma unroll
     for (int v = 0; v < V; ++v) zm[v] = add_rn(zm[v], (k & 1) ? wc[v] : wz[v]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) zm[v] = T(0);
   }
-  if (k < G.nz - 1) {
-    load_vec(yr + m0 + plane, zp);
+  if (nb_has<3, PER>(G, j, k)) {
+    load_vec(yr + m0 + nb_off<3, PER>(G, j, k), zp);
 #pragma unroll
     for (int v = 0; v < V; ++v) zp[v] = add_rn(zp[v], (k & 1) ? wz[v] : wc[v]);
   } else {
@@ -464,7 +500,7 @@ __device__ __forceinline__ long long coarse_index(const Geom& Gc, int I, int J, 
 // times 1/4 give the coarse scaled right-hand side. RED_ONLY: the black cells were just updated
 // by a black half-sweep, so their residuals are zero up to rounding and only the 4 red children
 // are summed (same order otherwise).
-template <typename T, bool RED_ONLY = false>
+template <typename T, bool RED_ONLY = false, bool PER = true>
 __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                     T* __restrict__ gc, const Geom& Gc, int I, int J, int K) {
   T acc = T(0);
@@ -479,7 +515,7 @@ __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, con
         if (RED_ONLY && c == 1) continue;
         const long long row = ((long long)k * G.ny + j) * G.hx;
         const long long own = (long long)c * G.csz + row + I;
-        const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, I, di, j, k);
+        const T S = nbsum_packed<T, PER>(x + (long long)(1 - c) * G.csz, G, row, I, di, j, k);
         const int d = diag_shift_packed(G, I, di, j, k);
         const T r = fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
         acc = acc + r;
@@ -492,11 +528,11 @@ __device__ __forceinline__ void resid_restrict_cell(const T* __restrict__ x, con
 // consecutive entries I0.. of both colour arrays of that row, so every load is a 16-byte vector
 // plus one scalar per colour; each coarse value is summed in the (dk, dj, di) order of
 // resid_restrict_cell, so the results are identical.
-template <typename T, int V, bool RED_ONLY = false>
+template <typename T, int V, bool RED_ONLY = false, bool PER = true>
 __device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                    T* __restrict__ gc, const Geom& Gc, int iv, int J, int K) {
+  const int per = PER ? G.per : 0;
   const int I0 = iv * V;
-  const long long plane = (long long)G.ny * G.hx;
   T acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = T(0);
@@ -521,30 +557,20 @@ __device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, cons
       const bool need0 = !RED_ONLY || c0 == 0, need1 = !RED_ONLY || c1 == 0;  // children computed
       if (need0) load_vec(g + (long long)c0 * G.csz + row + I0, g0);
       if (need1) load_vec(g + (long long)c1 * G.csz + row + I0, g1);
-      // x-neighbour of child (I0, di=0) and of child (I0+V-1, di=1)
-      const T left = (need0 && I0 > 0) ? __ldg(r1 + I0 - 1) : T(0);
-      const T right = (need1 && I0 + V < G.hx) ? __ldg(r0 + I0 + V) : T(0);
+      // x-neighbour of child (I0, di=0) and of child (I0+V-1, di=1) (the row's other end across a
+      // periodic x axis)
+      const bool px = (per & 1) != 0;
+      const T left = !need0 ? T(0) : (I0 > 0 ? __ldg(r1 + I0 - 1) : (px ? __ldg(r1 + G.hx - 1) : T(0)));
+      const T right = !need1 ? T(0) : (I0 + V < G.hx ? __ldg(r0 + I0 + V) : (px ? __ldg(r0) : T(0)));
 #pragma unroll
       for (int di = 0; di < 2; ++di) {
         if (di == 0 ? !need0 : !need1) continue;
         const T* y = di == 0 ? r1 : r0;  // the other colour's row
         T ym[V], yp[V], zm[V], zp[V];
-        if (j > 0) load_vec(y + I0 - G.hx, ym);
-        else
-#pragma unroll
-          for (int v = 0; v < V; ++v) ym[v] = T(0);
-        if (j < G.ny - 1) load_vec(y + I0 + G.hx, yp);
-        else
-#pragma unroll
-          for (int v = 0; v < V; ++v) yp[v] = T(0);
-        if (k > 0) load_vec(y + I0 - plane, zm);
-        else
-#pragma unroll
-          for (int v = 0; v < V; ++v) zm[v] = T(0);
-        if (k < G.nz - 1) load_vec(y + I0 + plane, zp);
-        else
-#pragma unroll
-          for (int v = 0; v < V; ++v) zp[v] = T(0);
+        load_nb_vec<0, PER>(y, G, I0, j, k, ym);
+        load_nb_vec<1, PER>(y, G, I0, j, k, yp);
+        load_nb_vec<2, PER>(y, G, I0, j, k, zm);
+        load_nb_vec<3, PER>(y, G, I0, j, k, zp);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int I = I0 + v;
@@ -733,14 +759,14 @@ __host__ __device__ __forceinline__ double fx_residual(const FxOp (&op)[8], int 
 
 // Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x (single
 // precision: the direct formula; the FP64 levels use the tiled walk below).
-template <typename T>
+template <typename T, bool PER = true>
 __device__ __forceinline__ T resid_packed(const T* __restrict__ x, const T* __restrict__ g, const Geom& G, int c,
                                           int m, int j, int k) {
   const int s = (j + k + c) & 1;
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)c * G.csz + row + m;
   const int d = diag_shift_packed(G, m, s, j, k);
-  const T S = nbsum_packed(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
+  const T S = nbsum_packed<T, PER>(x + (long long)(1 - c) * G.csz, G, row, m, s, j, k);
   return fmat(neg_diag<T>(d), __ldg(x + own), __ldg(g + own) + S);
 }
 
@@ -805,18 +831,25 @@ __device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, con
     slot ^= 1;  // the next sum writes the other pair; its barrier follows every read of this one
     return sv;
   };
-  // the cell's neighbours (bits -x,+x,-y,+y,-z,+z) and -(6 + d)
+  // the cell's neighbours (bits -x,+x,-y,+y,-z,+z, and their offsets: across a periodic axis the
+  // cell at the opposite side) and -(6 + d)
   unsigned nbm = 0u;
+  int no[6] = {-1, 1, -nx, nx, -nx * ny, nx * ny};
   double nd = 0.0, xi = 0.0, ri = 0.0;
   if (own) {
     const int ix = t % nx, iy = (t / nx) % ny, iz = t / (nx * ny);
+    const int ext[3] = {nx, ny, nz}, pos[3] = {ix, iy, iz}, st[3] = {1, nx, nx * ny};
     int d = 0;
-    if (ix > 0) nbm |= 1u; else d += G.sh[0];
-    if (ix < nx - 1) nbm |= 2u; else d += G.sh[1];
-    if (iy > 0) nbm |= 4u; else d += G.sh[2];
-    if (iy < ny - 1) nbm |= 8u; else d += G.sh[3];
-    if (iz > 0) nbm |= 16u; else d += G.sh[4];
-    if (iz < nz - 1) nbm |= 32u; else d += G.sh[5];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const bool per = (G.per >> a) & 1;
+      if (pos[a] > 0) nbm |= 1u << (2 * a);
+      else if (per) { nbm |= 1u << (2 * a); no[2 * a] = (ext[a] - 1) * st[a]; }
+      else d += G.sh[2 * a];
+      if (pos[a] < ext[a] - 1) nbm |= 2u << (2 * a);
+      else if (per) { nbm |= 2u << (2 * a); no[2 * a + 1] = -(ext[a] - 1) * st[a]; }
+      else d += G.sh[2 * a + 1];
+    }
     nd = neg_diag<double>(d);
     ri = (double)bi[t];
     p[t] = ri;
@@ -832,12 +865,9 @@ __device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, con
       if (own) {
         pi = p[t];
         double S = 0.0;
-        if (nbm & 1u) S += p[t - 1];
-        if (nbm & 2u) S += p[t + 1];
-        if (nbm & 4u) S += p[t - nx];
-        if (nbm & 8u) S += p[t + nx];
-        if (nbm & 16u) S += p[t - nx * ny];
-        if (nbm & 32u) S += p[t + nx * ny];
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if (nbm & (1u << q)) S += p[t + no[q]];
         a = -nd * pi - S;
       }
       const double pap = psum(pi * a);  // after its barrier nobody reads p of this iteration again
@@ -887,15 +917,16 @@ __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, con
     while (it < maxit) {
       loc = 0.0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny), pl = nx * ny;
+        const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0, pz = (G.per & 4) != 0;
         int d = 0;
         double S = 0.0;
-        if (ix > 0) S += p[i - 1]; else d += G.sh[0];
-        if (ix < nx - 1) S += p[i + 1]; else d += G.sh[1];
-        if (iy > 0) S += p[i - nx]; else d += G.sh[2];
-        if (iy < ny - 1) S += p[i + nx]; else d += G.sh[3];
-        if (iz > 0) S += p[i - nx * ny]; else d += G.sh[4];
-        if (iz < nz - 1) S += p[i + nx * ny]; else d += G.sh[5];
+        if (ix > 0) S += p[i - 1]; else if (px) S += p[i + nx - 1]; else d += G.sh[0];
+        if (ix < nx - 1) S += p[i + 1]; else if (px) S += p[i - (nx - 1)]; else d += G.sh[1];
+        if (iy > 0) S += p[i - nx]; else if (py) S += p[i + (ny - 1) * nx]; else d += G.sh[2];
+        if (iy < ny - 1) S += p[i + nx]; else if (py) S += p[i - (ny - 1) * nx]; else d += G.sh[3];
+        if (iz > 0) S += p[i - pl]; else if (pz) S += p[i + (nz - 1) * pl]; else d += G.sh[4];
+        if (iz < nz - 1) S += p[i + pl]; else if (pz) S += p[i - (nz - 1) * pl]; else d += G.sh[5];
         const double a = -neg_diag<double>(d) * p[i] - S;
         ap[i] = a;
         loc += p[i] * a;
@@ -951,7 +982,7 @@ __host__ __device__ __forceinline__ long long resid_tile_count(const Geom& G, in
 // beyond each end of a row loaded by the edge lanes in the colour the row's parity needs there.
 constexpr int kResXR = kResTJ + 2, kResXC = kResTM + 2;
 
-template <int MODE>
+template <int MODE, bool PER>
 __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x, const double* __restrict__ g,
                                                     const Geom& G, long long lb, long long nb, double c0,
                                                     double* __restrict__ outn, float* __restrict__ outp, double isc,
@@ -997,9 +1028,20 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
     // tile (first and last warp); zero outside the level (the absent neighbours). Fetched one
     // plane ahead of their conversion into slot kk & 3.
     const long long col = (long long)j * hx + m;  // the column's offset within a colour plane
-    const bool hok = hside != 0 && m + hside >= 0 && m + hside < hx && j < ny;
+    // Across a periodic axis the values beyond the level's end are those at its other end: the
+    // lane just past the last column (or the warp just past the last row) of a ragged tile, and
+    // the halo column (row, plane) beyond a wall, load the wrapped column (row, plane) instead.
+    const bool px = PER && (G.per & 1) != 0, py = PER && (G.per & 2) != 0, pz = PER && (G.per & 4) != 0;
+    const int mw = (m == hx && px) ? 0 : m, jw = (j == ny && py) ? 0 : j;
+    const bool lok = mw < hx && jw < ny;  // the thread's own column holds values (live or wrapped)
+    const long long lcol = (long long)jw * hx + mw;
+    int mh = m + hside;
+    if (px) mh = mh < 0 ? hx - 1 : (mh >= hx ? mh - hx : mh);
+    const bool hok = hside != 0 && mh >= 0 && mh < hx && j < ny;
+    const long long hcoff = (long long)j * hx + mh;
     const bool edge = w == 0 || w == kResTJ - 1;
-    const int jr = w == 0 ? j - 1 : j + 1;
+    int jr = w == 0 ? j - 1 : j + 1;
+    if (py) jr = jr < 0 ? ny - 1 : (jr >= ny ? jr - ny : jr);
     const bool rok = edge && jr >= 0 && jr < ny && m < hx;
     const long long rcol = (long long)jr * hx + m;
     struct Raw {
@@ -1007,11 +1049,12 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
     };
     auto hcol = [&](int kk) { return (hside < 0) == (((j + kk) & 1) != 0) ? 0 : 1; };
     auto fetch = [&](int kk, Raw& r) {
-      const bool zin = kk >= 0 && kk < nz;
-      const long long po = (long long)kk * plane;
+      const int kw = pz ? (kk < 0 ? nz - 1 : (kk >= nz ? kk - nz : kk)) : kk;
+      const bool zin = kw >= 0 && kw < nz;
+      const long long po = (long long)kw * plane;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) r.own[c] = (live && zin) ? __ldg(x + c * G.csz + po + col) : 0.0;
-      r.halo = (hok && zin) ? __ldg(x + hcol(kk) * G.csz + po + col + hside) : 0.0;
+      for (int c = 0; c < 2; ++c) r.own[c] = (lok && zin) ? __ldg(x + c * G.csz + po + lcol) : 0.0;
+      r.halo = (hok && zin) ? __ldg(x + hcol(kk) * G.csz + po + hcoff) : 0.0;
       if (edge) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) r.row[c] = (rok && zin) ? __ldg(x + c * G.csz + po + rcol) : 0.0;
@@ -1072,7 +1115,7 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
   return acc;
 }
 
-template <typename T, int MODE, bool POW2 = false>
+template <typename T, int MODE, bool POW2 = false, bool PER = true>
 __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x, const T* __restrict__ g,
                                                         const Geom& G, long long lb, long long nb, double c0,
                                                         double* __restrict__ outn, float* __restrict__ outp,
@@ -1087,7 +1130,7 @@ __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x,
       const int s = (j + k + c) & 1;
       const long long row = ((long long)k * G.ny + j) * G.hx;
       for (int m = threadIdx.x; m < G.hx; m += kResBX) {
-        const double rd = (double)resid_packed<T>(x, g, G, c, m, j, k);
+        const double rd = (double)resid_packed<T, PER>(x, g, G, c, m, j, k);
         acc = fma(rd, rd, acc);
         if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)G.ny * k)] = rd * c0;
         if (MODE == 2) outp[(long long)c * G.csz + row + m] = POW2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);
@@ -1100,12 +1143,14 @@ __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x,
     for (long long i = lb * (kResBX * kResBY) + tid; i < n; i += nb * (kResBX * kResBY)) {
       const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
       int d = 0;
-      const T xm = ix > 0 ? x[i - 1] : T(0);
-      const T xp = ix < nx - 1 ? x[i + 1] : T(0);
-      const T ym = iy > 0 ? x[i - nx] : T(0);
-      const T yp = iy < ny - 1 ? x[i + nx] : T(0);
-      const T zm = iz > 0 ? x[i - (long long)nx * ny] : T(0);
-      const T zp = iz < nz - 1 ? x[i + (long long)nx * ny] : T(0);
+      const long long pl = (long long)nx * ny;
+      const bool px = PER && (G.per & 1) != 0, py = PER && (G.per & 2) != 0, pz = PER && (G.per & 4) != 0;
+      const T xm = ix > 0 ? x[i - 1] : (px ? x[i + (nx - 1)] : T(0));
+      const T xp = ix < nx - 1 ? x[i + 1] : (px ? x[i - (nx - 1)] : T(0));
+      const T ym = iy > 0 ? x[i - nx] : (py ? x[i + (long long)(ny - 1) * nx] : T(0));
+      const T yp = iy < ny - 1 ? x[i + nx] : (py ? x[i - (long long)(ny - 1) * nx] : T(0));
+      const T zm = iz > 0 ? x[i - pl] : (pz ? x[i + (nz - 1) * pl] : T(0));
+      const T zp = iz < nz - 1 ? x[i + pl] : (pz ? x[i - (nz - 1) * pl] : T(0));
       if (ix == 0) d += G.sh[0];
       if (ix == nx - 1) d += G.sh[1];
       if (iy == 0) d += G.sh[2];
@@ -1129,17 +1174,18 @@ __device__ __forceinline__ double resid_norm_accum_impl(const T* __restrict__ x,
 }
 
 // The residual walk; in MODE 2 the single-precision copy float(r~ isc) is formed by exponent
-// arithmetic when isc is a power of two (the branch is uniform over the launch).
-template <typename T, int MODE>
+// arithmetic when isc is a power of two (the branch is uniform over the launch). PER = false:
+// the tile walk compiled without periodic halos (levels without a periodic axis).
+template <typename T, int MODE, bool PER = true>
 __device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, const T* __restrict__ g, const Geom& G,
                                                    long long lb, long long nb, double c0, double* __restrict__ outn,
                                                    float* __restrict__ outp, double isc) {
   const int p2 = MODE == 2 ? pow2_exponent(isc) : kBadPow2;
   if constexpr (sizeof(T) == 8) {
-    if (G.packed) return resid_tiles_accum<MODE>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
+    if (G.packed) return resid_tiles_accum<MODE, PER>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
   }
-  if (p2 != kBadPow2) return resid_norm_accum_impl<T, MODE, true>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
-  return resid_norm_accum_impl<T, MODE, false>(x, g, G, lb, nb, c0, outn, outp, isc, kBadPow2);
+  if (p2 != kBadPow2) return resid_norm_accum_impl<T, MODE, true, PER>(x, g, G, lb, nb, c0, outn, outp, isc, p2);
+  return resid_norm_accum_impl<T, MODE, false, PER>(x, g, G, lb, nb, c0, outn, outp, isc, kBadPow2);
 }
 
 // The single-precision residual copy of a zero iterate (r~ = g exactly) over the same rows of

@@ -323,8 +323,9 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
 }  // namespace
 
 bool tma_sweep_applies(const Geom& G) {
-  // rows of whole 4-float vectors and enough planes to march
-  return G.packed && (G.hx % 4) == 0 && G.nz >= 8 && (long long)G.hx * G.ny * G.nz >= (1LL << 16);
+  // rows of whole 4-float vectors and enough planes to march; no periodic axis (the staged tiles
+  // take zero beyond the walls, where a periodic axis needs the opposite side's values)
+  return G.packed && G.per == 0 && (G.hx % 4) == 0 && G.nz >= 8 && (long long)G.hx * G.ny * G.nz >= (1LL << 16);
 }
 
 bool tma_sweep_pays(const Geom& G) {

@@ -29,7 +29,7 @@ std::mutex g_mu;
 double* g_scratch[kMaxDevices] = {};
 
 // One block per z-plane: r = f - A_0 phi in natural order (Sec. 2.4 stencil with the walls
-// folded in), partial sums of r^2 and f^2 for the plane, fixed reduction order.
+// folded in, periodic axes wrapping around), partial sums of r^2 and f^2 for the plane, fixed reduction order.
 __global__ void __launch_bounds__(256) k_plane_residual(const double* __restrict__ phi, const double* __restrict__ f,
                                                         int nx, int ny, int nz, double c0, int4 sh_lo, int4 sh_hi,
                                                         double* __restrict__ partials) {
@@ -37,18 +37,19 @@ __global__ void __launch_bounds__(256) k_plane_residual(const double* __restrict
   const int k = blockIdx.x;
   const long long plane = (long long)nx * ny;
   const int sh[6] = {sh_lo.x, sh_lo.y, sh_lo.z, sh_lo.w, sh_hi.x, sh_hi.y};
+  const int per = sh_hi.z;  // periodic axes (bit a: axis a wraps around)
   double rr = 0.0, ff = 0.0;
   for (long long t = threadIdx.x; t < plane; t += blockDim.x) {
     const int i = (int)(t % nx), j = (int)(t / nx);
     const long long p = t + plane * k;
     double S = 0.0;
     int d = 0;
-    if (i > 0) S += phi[p - 1]; else d += sh[0];
-    if (i < nx - 1) S += phi[p + 1]; else d += sh[1];
-    if (j > 0) S += phi[p - nx]; else d += sh[2];
-    if (j < ny - 1) S += phi[p + nx]; else d += sh[3];
-    if (k > 0) S += phi[p - plane]; else d += sh[4];
-    if (k < nz - 1) S += phi[p + plane]; else d += sh[5];
+    if (i > 0) S += phi[p - 1]; else if (per & 1) S += phi[p + (nx - 1)]; else d += sh[0];
+    if (i < nx - 1) S += phi[p + 1]; else if (per & 1) S += phi[p - (nx - 1)]; else d += sh[1];
+    if (j > 0) S += phi[p - nx]; else if (per & 2) S += phi[p + (long long)(ny - 1) * nx]; else d += sh[2];
+    if (j < ny - 1) S += phi[p + nx]; else if (per & 2) S += phi[p - (long long)(ny - 1) * nx]; else d += sh[3];
+    if (k > 0) S += phi[p - plane]; else if (per & 4) S += phi[p + (nz - 1) * plane]; else d += sh[4];
+    if (k < nz - 1) S += phi[p + plane]; else if (per & 4) S += phi[p - (nz - 1) * plane]; else d += sh[5];
     const double fv = f[p];
     const double r = fv - c0 * ((double)(6 + d) * phi[p] - S);
     rr = fma(r, r, rr);
@@ -114,17 +115,22 @@ mg_status mg_residual_norm_static(int nx, int ny, int nz, double h, const int* h
   if (nz > kStaticMaxPlanes) return MG_ERR_INVALID;
   if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0)) return MG_ERR_INVALID;
   if (!h_bc_type6 || !d_phi || !d_f || !d_out2) return MG_ERR_INVALID;
-  int sh[6];
+  int sh[6], per = 0;
   for (int q = 0; q < 6; ++q) {
-    if (h_bc_type6[q] != MG_BC_DIRICHLET && h_bc_type6[q] != MG_BC_NEUMANN) return MG_ERR_INVALID;
-    sh[q] = h_bc_type6[q] == MG_BC_DIRICHLET ? 1 : -1;
+    const int t = h_bc_type6[q];
+    if (t != MG_BC_DIRICHLET && t != MG_BC_NEUMANN && t != MG_BC_PERIODIC) return MG_ERR_INVALID;
+    sh[q] = t == MG_BC_DIRICHLET ? 1 : (t == MG_BC_NEUMANN ? -1 : 0);
+  }
+  for (int a = 0; a < 3; ++a) {
+    if ((h_bc_type6[2 * a] == MG_BC_PERIODIC) != (h_bc_type6[2 * a + 1] == MG_BC_PERIODIC)) return MG_ERR_INVALID;
+    if (h_bc_type6[2 * a] == MG_BC_PERIODIC) per |= 1 << a;
   }
   double* scratch = nullptr;
   const mg_status st = scratch_for_current_device(&scratch);
   if (st != MG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   k_plane_residual<<<nz, 256, 0, s>>>(d_phi, d_f, nx, ny, nz, 1.0 / (h * h), make_int4(sh[0], sh[1], sh[2], sh[3]),
-                                       make_int4(sh[4], sh[5], 0, 0), scratch);
+                                       make_int4(sh[4], sh[5], per, 0), scratch);
   k_plane_finalize<<<1, 32, 0, s>>>(scratch, nz, d_out2);
   return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DIRICHLET, NEUMANN, MG_FP64, MG_MIXED, MgError  # noqa: F401
+from ._lib import DIRICHLET, NEUMANN, PERIODIC, MG_FP64, MG_MIXED, MgError  # noqa: F401
 
 PRECISIONS = {"fp64": MG_FP64, "mixed": MG_MIXED}
 

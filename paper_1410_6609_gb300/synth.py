@@ -15,6 +15,7 @@ import numpy as np
 
 DIRICHLET = 0
 NEUMANN = 1
+PERIODIC = 2
 
 # Faces: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z.
 # Electrokinetic cell: phi = 0 at -z, phi = V at +z, zero-flux Neumann on the x and y walls.

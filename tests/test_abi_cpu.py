@@ -58,6 +58,8 @@ def _params(**kw):
 @pytest.mark.parametrize("bad", [
     dict(nx=31), dict(ny=2), dict(nz=0), dict(h=0.0), dict(h=-1.0), dict(eps=0.0),
     dict(bc_type=(1, 1, 1, 1, 1, 1)), dict(bc_type=(0, 0, 0, 0, 0, 7)), dict(nu1=-1), dict(nu2=0),
+    dict(bc_type=(2, 0, 0, 0, 0, 0)), dict(bc_type=(0, 0, 0, 2, 0, 0)),  # periodic faces unpaired
+    dict(bc_type=(2, 2, 2, 2, 2, 2)), dict(bc_type=(2, 2, 1, 1, 2, 2)),  # no Dirichlet face: singular
     dict(nu2=17), dict(prec=5), dict(bc_value=(0, 0, 0, 0, 0, float("nan"))),
     dict(nx=4 * 1024, ny=2 * 5 * 7, nz=2 * 5 * 7),  # coarsest grid too large
 ])
@@ -98,3 +100,12 @@ def test_batch_create_rejects_invalid_params():
     assert lib.mg_batch_create(2, arr, None, ctypes.byref(h)) == _lib.MG_ERR_INVALID
     assert b"even" in lib.mg_batch_last_error(None)
     assert lib.mg_batch_solve(None, 1e-9, 10, None, None) == _lib.MG_ERR_INVALID
+
+
+@needs_nvcc
+def test_static_residual_rejects_unpaired_periodic_faces():
+    lib = _lib.load()
+    bc = (ctypes.c_int * 6)(2, 0, 0, 0, 0, 0)
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the types are checked first
+    st = lib.mg_residual_norm_static(8, 8, 8, 1.0, bc, dummy, dummy, dummy, None)
+    assert st == _lib.MG_ERR_INVALID
