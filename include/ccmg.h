@@ -96,13 +96,14 @@ mg_status mg_set_bc_values(mg_ctx* ctx, const double* h_bc_value6);
  * the outward normal derivative (Neumann) of that cell's face, entering the right-hand side
  * (2 g / h^2 or g / h, Sec. 2.4) and the ghost values of mg_efield, mg_force_gather and their
  * adjoint. The array is copied (the call returns after the copy); NULL returns the face to its
- * uniform value. Takes effect like mg_set_bc_values. Errors: MG_ERR_INVALID for a bad face,
- * MG_ERR_OOM / MG_ERR_CUDA if the copy cannot be made. Batched solves have no per-cell values. */
+ * uniform value. Takes effect like mg_set_bc_values. Errors: MG_ERR_INVALID for a bad face or a
+ * periodic one, MG_ERR_OOM / MG_ERR_CUDA if the copy cannot be made. Batched solves have no
+ * per-cell values. */
 mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
 
 /* Right-hand side from a charge density: f = rho/eps, then adapted to the wall values once
  * on the finest grid (Sec. 2.4 and Sec. 5.3: Dirichlet face cells += 2 g / h^2, Neumann face
- * cells += g / h). d_rho: nx*ny*nz doubles. */
+ * cells += g / h; periodic faces add nothing). d_rho: nx*ny*nz doubles. */
 mg_status mg_set_rhs(mg_ctx* ctx, const double* d_rho);
 /* Right-hand side f of A phi = f taken as is (no 1/eps, no wall terms): used for adjoint
  * solves, whose wall conditions are homogeneous. d_f: nx*ny*nz doubles. */
@@ -128,7 +129,8 @@ mg_status mg_solve(mg_ctx* ctx, double rel_tol, int max_cycles, int* h_cycles, d
 mg_status mg_residual(mg_ctx* ctx, double* h_rel_res, double* d_r);
 
 /* E = -grad(phi) by central differences (D3Q7), with the wall ghost values
- * (Dirichlet 2 g - phi, Neumann phi + h g), or by the stencil mg_set_gradient_stencil chose.
+ * (Dirichlet 2 g - phi, Neumann phi + h g; across a periodic axis the cell at the opposite
+ * side), or by the stencil mg_set_gradient_stencil chose.
  * d_E: 3 arrays of nx*ny*nz doubles (Ex, Ey, Ez). */
 mg_status mg_efield(mg_ctx* ctx, double* d_E);
 
@@ -136,7 +138,7 @@ mg_status mg_efield(mg_ctx* ctx, double* d_E);
  *   7  (default) D3Q7 central differences everywhere, with the wall ghost values;
  *   19 the isotropy-preserving D3Q19 stencil, grad phi ~ (1/w_1) sum_q w_q phi(x + e_q) e_q / h^2
  *      (weights 1/3 rest, 1/18 faces, 1/36 edges), at every cell whose 18 neighbours lie in the
- *      domain, and D3Q7 with ghosts at the others.
+ *      domain or across periodic axes, and D3Q7 with ghosts at the others.
  * Other values return MG_ERR_INVALID and leave the setting unchanged. mg_force_gather_adjoint
  * is implemented for the D3Q7 gradient only and returns MG_ERR_INVALID while 19 is set.
  * mg_gradient_stencil returns the setting (-1 for a NULL context). */
@@ -145,13 +147,16 @@ int mg_gradient_stencil(const mg_ctx* ctx);
 
 /* Charge density of P spheres with subsampling factor sf (1..8): each cell is split into sf^3
  * sub-cells and rho(cell) = sum_s density_s * (sub-cells whose centre lies in sphere s) / sf^3
- * (Sec. 2.4, "Subsampling"). d_centers: P*3 doubles (x,y,z); d_radius, d_density: P doubles.
+ * (Sec. 2.4, "Subsampling"). Along a periodic axis a sphere that reaches across the wall puts
+ * its charge in the cells at the opposite side (its periodic image); elsewhere the part outside
+ * the domain is dropped. d_centers: P*3 doubles (x,y,z); d_radius, d_density: P doubles.
  * d_rho (nx*ny*nz doubles) is overwritten. */
 mg_status mg_sphere_density(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
                             const double* d_density, int sf, double* d_rho);
 
 /* Coulomb force on each sphere, F_s = h^3 sum_b w_{s,b} density_s E(x_b) (Eq. ElectrostatForce,
- * E by the gradient of mg_efield, w the subsampled overlap). d_forces: P*3 doubles. */
+ * E by the gradient of mg_efield, w the subsampled overlap; the cells b of mg_sphere_density,
+ * periodic images included). d_forces: P*3 doubles. */
 mg_status mg_force_gather(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
                           const double* d_density, int sf, double* d_forces);
 
@@ -160,7 +165,7 @@ mg_status mg_force_gather(mg_ctx* ctx, int P, const double* d_centers, const dou
  *     explicit density factor, d_gbc (6, device) = dJ/dbc_value through the ghost values.
  *   mg_sphere_density_adjoint: d_gdensity[s] = sum_b w_{s,b} d_gfield[b].
  *   mg_rhs_adjoint: given lambda = dJ/df, d_grho = lambda / eps and d_gbc (6, device) =
- *     sum over each face's cells of lambda * (2/h^2 Dirichlet, 1/h Neumann). */
+ *     sum over each face's cells of lambda * (2/h^2 Dirichlet, 1/h Neumann, 0 periodic). */
 mg_status mg_force_gather_adjoint(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
                                   const double* d_density, int sf, const double* d_wF, double* d_gphi,
                                   double* d_gdensity, double* d_gbc);
@@ -280,7 +285,8 @@ long long mg_batch_kernel_launches(const mg_batch* b);
  *
  * Computes, for caller-owned fields in natural order (nx*ny*nz doubles, x fastest), the
  * residual r = f - A phi of the operator of mg_create (cell size h, wall types h_bc_type6 folded
- * into the stencil; f must already contain the wall terms, as from mg_level_get(ctx, 0, 1, ...))
+ * into the stencil, periodic ones, in opposite pairs, wrapping around; f must already contain the
+ * wall terms, as from mg_level_get(ctx, 0, 1, ...))
  * and writes d_out2[0] = ||r||_2 / ||f||_2 (||r||_2 if f is zero) and d_out2[1] = ||r||_2 to
  * device memory, enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
  *
