@@ -86,6 +86,12 @@ def _load():
                 "ccmg_or_force_gather_stencil": (None, [P, I, I, I, D, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_field": (None, [P, I, I, I, D, P, P, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_adjoint": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P, P, P, P]),
+                "ccmg_or_var_coeffs": (None, [P, I, I, I, P, I, P, P, P, P]),
+                "ccmg_or_var_apply": (None, [P, P, P, I, I, I, D, P, I]),
+                "ccmg_or_var_rhs": (None, [P, P, P, I, I, I, D, P, P]),
+                "ccmg_or_var_vcycles": (None, [P, P, P, I, I, I, D, P, I, I, D, I]),
+                "ccmg_or_var_solve": (I, [P, P, P, I, I, I, D, P, I, I, D, D, I, P]),
+                "ccmg_or_var_rel_residual": (D, [P, P, P, I, I, I, D, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -413,3 +419,59 @@ def force_objective_and_grad(shape, h: float, bc_type, bc_value, centers, radius
     grho, gbc_rhs = rhs_adjoint(lam, h, bc_type, eps)
     gdens = gdens + sphere_density_adjoint(grho, h, centers, radius, sf, bc_type)
     return J, gdens, gbc + gbc_rhs, {"phi": phi, "lam": lam, "cycles": (k1, k2), "rel": (rel1, rel2)}
+
+
+# --------------------------------------------------------------------------------------------
+# Variable permittivity (Sec. 3: Galerkin coarsening with averaging restriction and constant
+# prolongation extends the solver to discontinuous dielectricity; -div(eps grad phi) = rho, face
+# weights the harmonic mean of the two cells' permittivities)
+
+def var_coeffs(eps, bc_type, level: int = 0):
+    """Scaled weights (D, wx, wy, wz) of level `level` of the hierarchy of eps ([nz, ny, nx])."""
+    eps = _f64(eps)
+    nx, ny, nz = _dims(eps)
+    d = levels(nx, ny, nz)[level]
+    shape = (d[2], d[1], d[0])
+    out = [np.empty(shape) for _ in range(4)]
+    _load().ccmg_or_var_coeffs(_p(eps), nx, ny, nz, _p(_bc(bc_type)), level, *[_p(a) for a in out])
+    return tuple(out)
+
+
+def var_apply(phi, eps, h: float, bc_type, level: int = 0) -> np.ndarray:
+    """A_l phi with the Galerkin operator of level `level` (phi of that level's shape)."""
+    eps = _f64(eps)
+    phi = _f64(phi)
+    out = np.empty_like(phi)
+    _load().ccmg_or_var_apply(_p(phi), _p(out), _p(eps), *_dims(eps), h, _p(_bc(bc_type)), level)
+    return out
+
+
+def var_rhs(rho, eps, h: float, bc_type, bc_value) -> np.ndarray:
+    """f = rho plus the wall terms 2 eps g / h^2 (Dirichlet), eps g / h (Neumann)."""
+    rho, eps = _f64(rho), _f64(eps)
+    f = np.empty_like(rho)
+    _load().ccmg_or_var_rhs(_p(rho), _p(eps), _p(f), *_dims(rho), h, _p(_bc(bc_type)), _p(_f64(bc_value)))
+    return f
+
+
+def var_vcycles(phi, f, eps, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2, omega: float = 2.0):
+    phi = _f64(phi).copy()
+    f, eps = _f64(f), _f64(eps)
+    _load().ccmg_or_var_vcycles(_p(phi), _p(f), _p(eps), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega, ncycles)
+    return phi
+
+
+def var_solve(f, eps, h: float, bc_type, tol: float = 1e-10, max_cycles: int = 100, nu1: int = 2, nu2: int = 2,
+              omega: float = 2.0, phi0=None):
+    """Algorithm 1 with the weighted operators. Returns (phi, cycles, relative residual)."""
+    f, eps = _f64(f), _f64(eps)
+    phi = np.zeros_like(f) if phi0 is None else _f64(phi0).copy()
+    rel = ctypes.c_double()
+    k = _load().ccmg_or_var_solve(_p(phi), _p(f), _p(eps), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega, tol,
+                                  max_cycles, ctypes.byref(rel))
+    return phi, k, rel.value
+
+
+def var_rel_residual(phi, f, eps, h: float, bc_type) -> float:
+    return _load().ccmg_or_var_rel_residual(_p(_f64(phi)), _p(_f64(f)), _p(_f64(eps)), *_dims(_f64(f)), h,
+                                            _p(_bc(bc_type)))

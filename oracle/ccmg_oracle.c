@@ -832,3 +832,344 @@ void ccmg_or_force_gather_adjoint(const double* phi, int nx, int ny, int nz, dou
     for (int a = 0; a < 3; ++a) gdens[s] = gdens[s] + wF[3 * s + a] * h3 * Fsum[a];
   }
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Variable permittivity (Sec. 3: the solver extends to discontinuous dielectricity by Galerkin
+ * coarsening with the averaging restriction and the nearest-neighbour prolongation, after
+ * Alcouffe et al.). The equation is -div(eps grad phi) = rho; the finite-volume flux between two
+ * cells has the weight of the harmonic mean of their permittivities (the flux-continuous choice
+ * for a jump at the face). Each level carries, in natural order and scaled like the constant
+ * case (A_l = c_l * (D phi - sum of w phi_neighbour), c_l = 1/(2^l h^2)):
+ *   wx[i,j,k]  weight of the face between cells i-1 and i (at i = 0: the -x wall face, or across
+ *              a periodic axis the face to cell nx-1); wy, wz likewise;
+ *   D[i,j,k]   the diagonal: the weights of the cell's six faces, a Dirichlet wall face counted
+ *              twice (ghost 2 g - phi), a Neumann wall face not at all (ghost phi + h g).
+ * The wall face of a cell has the weight of the cell's own permittivity. With eps = 1 the
+ * weights are 1 and D = 6 + d, the constant operator above.
+ * Galerkin: A_{l+1} = R A_l P with R = P^T / 8, so in scaled form (c_{l+1} = c_l / 2)
+ *   w_{l+1}(coarse face) = (1/4) * (sum of the 4 fine face weights on it),
+ *   D_{l+1}(I) = (1/4) * (sum of the 8 children's D - 2 * the 12 faces inside I),
+ * the entries of (1/4) P^T A~_l P written out (checked against the literal product by the tests). */
+
+typedef struct {
+  int n[3];
+  double *D, *wx, *wy, *wz;
+} var_level;
+
+static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+static void var_alloc(var_level* V, const int* d) {
+  const size_t n = (size_t)d[0] * d[1] * d[2];
+  for (int a = 0; a < 3; ++a) V->n[a] = d[a];
+  V->D = (double*)calloc(n, sizeof(double));
+  V->wx = (double*)calloc(n, sizeof(double));
+  V->wy = (double*)calloc(n, sizeof(double));
+  V->wz = (double*)calloc(n, sizeof(double));
+}
+
+static void var_free(var_level* V) {
+  free(V->D);
+  free(V->wx);
+  free(V->wy);
+  free(V->wz);
+}
+
+/* Level-0 weights from the cell permittivities. */
+static void var_fine(const double* eps, const int* bc, var_level* V) {
+  const int nx = V->n[0], ny = V->n[1], nz = V->n[2];
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        const double e = eps[p];
+        V->wx[p] = i > 0 ? harmonic(eps[idx3(i - 1, j, k, nx, ny)], e)
+                         : (bc[0] == BC_PERIODIC ? harmonic(eps[idx3(nx - 1, j, k, nx, ny)], e) : e);
+        V->wy[p] = j > 0 ? harmonic(eps[idx3(i, j - 1, k, nx, ny)], e)
+                         : (bc[2] == BC_PERIODIC ? harmonic(eps[idx3(i, ny - 1, k, nx, ny)], e) : e);
+        V->wz[p] = k > 0 ? harmonic(eps[idx3(i, j, k - 1, nx, ny)], e)
+                         : (bc[4] == BC_PERIODIC ? harmonic(eps[idx3(i, j, nz - 1, nx, ny)], e) : e);
+      }
+  /* the diagonal: six faces in the order -x,+x,-y,+y,-z,+z */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        const double e = eps[p];
+        const int pos[3] = {i, j, k};
+        const double* w[3] = {V->wx, V->wy, V->wz};
+        double D = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const int n = V->n[a];
+          /* minus face */
+          if (pos[a] > 0 || bc[2 * a] == BC_PERIODIC) D = D + w[a][p];
+          else if (bc[2 * a] == BC_DIRICHLET) D = D + 2.0 * e;
+          /* plus face: the minus face of the next cell (of cell 0 across a periodic axis) */
+          int q[3] = {i, j, k};
+          if (pos[a] < n - 1) {
+            q[a] += 1;
+            D = D + w[a][idx3(q[0], q[1], q[2], nx, ny)];
+          } else if (bc[2 * a + 1] == BC_PERIODIC) {
+            q[a] = 0;
+            D = D + w[a][idx3(q[0], q[1], q[2], nx, ny)];
+          } else if (bc[2 * a + 1] == BC_DIRICHLET) {
+            D = D + 2.0 * e;
+          }
+        }
+        V->D[p] = D;
+      }
+}
+
+/* Galerkin coarse weights (fine level F, coarse level C with half the dimensions). */
+static void var_coarsen(const var_level* F, var_level* C) {
+  const int nx = F->n[0], ny = F->n[1];
+  for (int K = 0; K < C->n[2]; ++K)
+    for (int J = 0; J < C->n[1]; ++J)
+      for (int I = 0; I < C->n[0]; ++I) {
+        double sx = 0.0, sy = 0.0, sz = 0.0, sd = 0.0, inner = 0.0;
+        for (int u = 0; u < 2; ++u)
+          for (int v = 0; v < 2; ++v) {
+            sx = sx + F->wx[idx3(2 * I, 2 * J + u, 2 * K + v, nx, ny)];
+            sy = sy + F->wy[idx3(2 * I + u, 2 * J, 2 * K + v, nx, ny)];
+            sz = sz + F->wz[idx3(2 * I + u, 2 * J + v, 2 * K, nx, ny)];
+          }
+        for (int dk = 0; dk < 2; ++dk)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) sd = sd + F->D[idx3(2 * I + di, 2 * J + dj, 2 * K + dk, nx, ny)];
+        for (int u = 0; u < 2; ++u)
+          for (int v = 0; v < 2; ++v) {
+            inner = inner + F->wx[idx3(2 * I + 1, 2 * J + u, 2 * K + v, nx, ny)];
+            inner = inner + F->wy[idx3(2 * I + u, 2 * J + 1, 2 * K + v, nx, ny)];
+            inner = inner + F->wz[idx3(2 * I + u, 2 * J + v, 2 * K + 1, nx, ny)];
+          }
+        const size_t p = idx3(I, J, K, C->n[0], C->n[1]);
+        C->wx[p] = sx / 4.0;
+        C->wy[p] = sy / 4.0;
+        C->wz[p] = sz / 4.0;
+        C->D[p] = (sd - 2.0 * inner) / 4.0;
+      }
+}
+
+/* Weighted sum of the neighbours, in the order -x,+x,-y,+y,-z,+z (walls: none). */
+static double var_nbsum(const double* phi, const var_level* V, const int* bc, int i, int j, int k) {
+  const int nx = V->n[0], ny = V->n[1], nz = V->n[2];
+  const size_t p = idx3(i, j, k, nx, ny);
+  double s = 0.0;
+  if (i > 0) s = s + V->wx[p] * phi[idx3(i - 1, j, k, nx, ny)];
+  else if (bc[0] == BC_PERIODIC) s = s + V->wx[p] * phi[idx3(nx - 1, j, k, nx, ny)];
+  if (i < nx - 1) s = s + V->wx[idx3(i + 1, j, k, nx, ny)] * phi[idx3(i + 1, j, k, nx, ny)];
+  else if (bc[1] == BC_PERIODIC) s = s + V->wx[idx3(0, j, k, nx, ny)] * phi[idx3(0, j, k, nx, ny)];
+  if (j > 0) s = s + V->wy[p] * phi[idx3(i, j - 1, k, nx, ny)];
+  else if (bc[2] == BC_PERIODIC) s = s + V->wy[p] * phi[idx3(i, ny - 1, k, nx, ny)];
+  if (j < ny - 1) s = s + V->wy[idx3(i, j + 1, k, nx, ny)] * phi[idx3(i, j + 1, k, nx, ny)];
+  else if (bc[3] == BC_PERIODIC) s = s + V->wy[idx3(i, 0, k, nx, ny)] * phi[idx3(i, 0, k, nx, ny)];
+  if (k > 0) s = s + V->wz[p] * phi[idx3(i, j, k - 1, nx, ny)];
+  else if (bc[4] == BC_PERIODIC) s = s + V->wz[p] * phi[idx3(i, j, nz - 1, nx, ny)];
+  if (k < nz - 1) s = s + V->wz[idx3(i, j, k + 1, nx, ny)] * phi[idx3(i, j, k + 1, nx, ny)];
+  else if (bc[5] == BC_PERIODIC) s = s + V->wz[idx3(i, j, 0, nx, ny)] * phi[idx3(i, j, 0, nx, ny)];
+  return s;
+}
+
+static void var_apply(const double* phi, double* out, const var_level* V, double c, const int* bc) {
+  for (int k = 0; k < V->n[2]; ++k)
+    for (int j = 0; j < V->n[1]; ++j)
+      for (int i = 0; i < V->n[0]; ++i) {
+        const size_t p = idx3(i, j, k, V->n[0], V->n[1]);
+        out[p] = c * (V->D[p] * phi[p] - var_nbsum(phi, V, bc, i, j, k));
+      }
+}
+
+static void var_residual(const double* phi, const double* f, double* r, const var_level* V, double c,
+                         const int* bc) {
+  for (int k = 0; k < V->n[2]; ++k)
+    for (int j = 0; j < V->n[1]; ++j)
+      for (int i = 0; i < V->n[0]; ++i) {
+        const size_t p = idx3(i, j, k, V->n[0], V->n[1]);
+        r[p] = f[p] - c * (V->D[p] * phi[p] - var_nbsum(phi, V, bc, i, j, k));
+      }
+}
+
+/* One colour of red-black Gauss-Seidel: phi_i = (f_i / c + weighted neighbours) / D_i. */
+static void var_rbgs_half(double* phi, const double* f, const var_level* V, double c, const int* bc, int colour) {
+  for (int k = 0; k < V->n[2]; ++k)
+    for (int j = 0; j < V->n[1]; ++j)
+      for (int i = 0; i < V->n[0]; ++i) {
+        if (((i + j + k) & 1) != colour) continue;
+        const size_t p = idx3(i, j, k, V->n[0], V->n[1]);
+        phi[p] = (f[p] / c + var_nbsum(phi, V, bc, i, j, k)) / V->D[p];
+      }
+}
+
+/* CG on the coarsest level, as ccmg_or_cg with the weighted operator. */
+static int var_cg(double* x, const double* b, const var_level* V, double c, const int* bc, double rtol, int maxit) {
+  const size_t n = (size_t)V->n[0] * V->n[1] * V->n[2];
+  double* r = (double*)malloc(n * sizeof(double));
+  double* p = (double*)malloc(n * sizeof(double));
+  double* ap = (double*)malloc(n * sizeof(double));
+  for (size_t q = 0; q < n; ++q) {
+    x[q] = 0.0;
+    r[q] = b[q];
+    p[q] = b[q];
+  }
+  const double bnorm = sqrt(dot_d(b, b, n));
+  double rr = dot_d(r, r, n);
+  int it = 0;
+  if (bnorm > 0.0) {
+    while (it < maxit) {
+      var_apply(p, ap, V, c, bc);
+      const double alpha = rr / dot_d(p, ap, n);
+      for (size_t q = 0; q < n; ++q) {
+        x[q] = x[q] + alpha * p[q];
+        r[q] = r[q] - alpha * ap[q];
+      }
+      ++it;
+      const double rr_new = dot_d(r, r, n);
+      if (sqrt(rr_new) <= rtol * bnorm) break;
+      const double beta = rr_new / rr;
+      for (size_t q = 0; q < n; ++q) p[q] = r[q] + beta * p[q];
+      rr = rr_new;
+    }
+  }
+  free(r);
+  free(p);
+  free(ap);
+  return it;
+}
+
+typedef struct {
+  hierarchy H;
+  var_level V[OR_MAX_LEVELS];
+} var_hierarchy;
+
+static void var_hier_init(var_hierarchy* G, const double* eps, int nx, int ny, int nz, const int* bc) {
+  hier_init(&G->H, nx, ny, nz, 0);
+  for (int l = 0; l < G->H.L; ++l) var_alloc(&G->V[l], G->H.dims[l]);
+  var_fine(eps, bc, &G->V[0]);
+  for (int l = 1; l < G->H.L; ++l) var_coarsen(&G->V[l - 1], &G->V[l]);
+}
+
+static void var_hier_free(var_hierarchy* G) {
+  for (int l = 0; l < G->H.L; ++l) var_free(&G->V[l]);
+  hier_free(&G->H);
+}
+
+static void var_vcycle(var_hierarchy* G, int l, double h, const int* bc, int nu1, int nu2, double omega) {
+  hierarchy* H = &G->H;
+  const var_level* V = &G->V[l];
+  const int* d = H->dims[l];
+  const double c = level_coeff(h, l);
+  if (l == H->L - 1) {
+    var_cg(H->phi[l], H->f[l], V, c, bc, CG_RTOL, 2 * (int)ncells(d));
+    return;
+  }
+  for (int s = 0; s < nu1; ++s) {
+    var_rbgs_half(H->phi[l], H->f[l], V, c, bc, 0);
+    var_rbgs_half(H->phi[l], H->f[l], V, c, bc, 1);
+  }
+  var_residual(H->phi[l], H->f[l], H->r, V, c, bc);
+  restrict_avg_d(H->r, H->f[l + 1], d[0], d[1], d[2]);
+  memset(H->phi[l + 1], 0, ncells(H->dims[l + 1]) * sizeof(double));
+  var_vcycle(G, l + 1, h, bc, nu1, nu2, omega);
+  prolong_correct_d(H->phi[l], H->phi[l + 1], d[0], d[1], d[2], omega);
+  for (int s = 0; s < nu2; ++s) {
+    var_rbgs_half(H->phi[l], H->f[l], V, c, bc, 1);
+    var_rbgs_half(H->phi[l], H->f[l], V, c, bc, 0);
+  }
+}
+
+/* The scaled weights of level `level` (D, wx, wy, wz, each of that level's cell count). */
+void ccmg_or_var_coeffs(const double* eps, int nx, int ny, int nz, const int* bc, int level, double* D, double* wx,
+                        double* wy, double* wz) {
+  var_hierarchy G;
+  var_hier_init(&G, eps, nx, ny, nz, bc);
+  const size_t n = ncells(G.H.dims[level]);
+  memcpy(D, G.V[level].D, n * sizeof(double));
+  memcpy(wx, G.V[level].wx, n * sizeof(double));
+  memcpy(wy, G.V[level].wy, n * sizeof(double));
+  memcpy(wz, G.V[level].wz, n * sizeof(double));
+  var_hier_free(&G);
+}
+
+/* out = A_l phi_l on level `level` of the hierarchy of eps (fine dimensions nx, ny, nz). */
+void ccmg_or_var_apply(const double* phi, double* out, const double* eps, int nx, int ny, int nz, double h,
+                       const int* bc, int level) {
+  var_hierarchy G;
+  var_hier_init(&G, eps, nx, ny, nz, bc);
+  var_apply(phi, out, &G.V[level], level_coeff(h, level), bc);
+  var_hier_free(&G);
+}
+
+/* Right-hand side of -div(eps grad phi) = rho with the walls folded in once on the finest grid:
+ * f = rho; Dirichlet face cells f += 2 eps g / h^2; Neumann face cells f += eps g / h (eps of the
+ * boundary cell, the weight of its wall face); periodic faces add nothing. */
+void ccmg_or_var_rhs(const double* rho, const double* eps, double* f, int nx, int ny, int nz, double h, const int* bc,
+                     const double* bcv) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        double v = rho[p];
+        const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
+        for (int q = 0; q < 6; ++q) {
+          if (!on_face[q] || bc[q] == BC_PERIODIC) continue;
+          if (bc[q] == BC_DIRICHLET)
+            v = v + 2.0 * eps[p] * bcv[q] / (h * h);
+          else
+            v = v + eps[p] * bcv[q] / h;
+        }
+        f[p] = v;
+      }
+}
+
+/* ncycles V-cycles (as ccmg_or_vcycles) with the weighted operators. */
+void ccmg_or_var_vcycles(double* phi, const double* f, const double* eps, int nx, int ny, int nz, double h,
+                         const int* bc, int nu1, int nu2, double omega, int ncycles) {
+  var_hierarchy G;
+  var_hier_init(&G, eps, nx, ny, nz, bc);
+  G.H.phi[0] = phi;
+  G.H.f[0] = (double*)f;
+  for (int k = 0; k < ncycles; ++k) var_vcycle(&G, 0, h, bc, nu1, nu2, omega);
+  G.H.phi[0] = NULL;
+  G.H.f[0] = NULL;
+  var_hier_free(&G);
+}
+
+/* Algorithm 1 with the weighted operators; returns the cycle count. */
+int ccmg_or_var_solve(double* phi, const double* f, const double* eps, int nx, int ny, int nz, double h,
+                      const int* bc, int nu1, int nu2, double omega, double tol, int max_cycles, double* rel_res_out) {
+  var_hierarchy G;
+  var_hier_init(&G, eps, nx, ny, nz, bc);
+  G.H.phi[0] = phi;
+  G.H.f[0] = (double*)f;
+  const size_t n = (size_t)nx * ny * nz;
+  const double fn = norm2_d(f, n);
+  int k = 0;
+  double rel;
+  for (;;) {
+    var_residual(phi, f, G.H.r, &G.V[0], level_coeff(h, 0), bc);
+    rel = fn > 0.0 ? norm2_d(G.H.r, n) / fn : norm2_d(G.H.r, n);
+    if (!(rel >= tol) || k >= max_cycles) break;
+    var_vcycle(&G, 0, h, bc, nu1, nu2, omega);
+    ++k;
+  }
+  if (rel_res_out) *rel_res_out = rel;
+  G.H.phi[0] = NULL;
+  G.H.f[0] = NULL;
+  var_hier_free(&G);
+  return k;
+}
+
+/* Relative residual ||f - A_0 phi|| / ||f|| with the weighted operator. */
+double ccmg_or_var_rel_residual(const double* phi, const double* f, const double* eps, int nx, int ny, int nz,
+                                double h, const int* bc) {
+  var_level V;
+  const int d[3] = {nx, ny, nz};
+  var_alloc(&V, d);
+  var_fine(eps, bc, &V);
+  const size_t n = (size_t)nx * ny * nz;
+  double* r = (double*)malloc(n * sizeof(double));
+  var_residual(phi, f, r, &V, level_coeff(h, 0), bc);
+  const double fn = norm2_d(f, n), rn = norm2_d(r, n);
+  free(r);
+  var_free(&V);
+  return fn > 0.0 ? rn / fn : rn;
+}

@@ -696,3 +696,93 @@ def test_periodic_adjoint_gradient_vs_finite_differences():
 def test_periodic_faces_must_pair():
     with pytest.raises(ValueError):
         oracle.apply(np.zeros((4, 4, 4)), 1.0, (PER, D, D, D, D, D))
+
+
+# ------------------------------------------------------------------------------------------
+# Variable permittivity (Sec. 3: Galerkin coarsening with averaging restriction and constant
+# prolongation extends the solver to discontinuous dielectricity): -div(eps grad phi) = rho
+
+def dense_var(eps, h, bc, level, dims):
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    for q in range(n):
+        e = np.zeros(n)
+        e[q] = 1.0
+        A[:, q] = oracle.var_apply(e.reshape(nz, ny, nx), eps, h, bc, level).ravel()
+    return A
+
+
+def _jumping_eps(dims, seed, lo=1.0, hi=80.0):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    return np.where(rng.random((nz, ny, nx)) < 0.4, hi, lo) * np.exp(0.1 * rng.standard_normal((nz, ny, nx)))
+
+
+@pytest.mark.parametrize("bc", [(D,) * 6, (N, N, N, N, D, D), (PER, PER, D, N, PER, PER)])
+def test_var_constant_permittivity_is_the_constant_operator(bc):
+    dims = (16, 12, 20)
+    nx, ny, nz = dims
+    rho = synth.random_field(dims, 1)
+    bcv = (0.1, -0.2, 0.3, 0.0, -1.0, 1.0)
+    eps = np.full((nz, ny, nx), 2.5)
+    f = oracle.var_rhs(rho, eps, 0.5, bc, bcv)
+    assert np.abs(f - 2.5 * oracle.rhs(rho, 0.5, bc, bcv, eps=2.5)).max() <= 1e-12 * np.abs(f).max()
+    phi, k, rel = oracle.var_solve(f, eps, 0.5, bc, tol=1e-13, max_cycles=100)
+    ref, k_ref, _ = oracle.solve(f / 2.5, 0.5, bc, tol=1e-13, max_cycles=100)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-12 and k == k_ref
+    Dw = oracle.var_coeffs(eps, bc, 1)
+    assert np.allclose(Dw[1:], 2.5, rtol=0, atol=1e-15)  # Galerkin keeps the scaled weights
+
+
+@pytest.mark.parametrize("bc", [(D, N, N, D, D, N), (PER, PER, D, D, N, D), (PER,) * 6])
+def test_var_galerkin_closed_form(bc):
+    """(1/8) P^T A_l P equals the level-(l+1) operator built from the coarsening formulas, for a
+    jumping permittivity (two levels)."""
+    fine = (12, 12, 12)
+    eps = _jumping_eps(fine, 4)
+    h = 0.5
+    A0 = dense_var(eps, h, bc, 0, fine)
+    assert np.abs(A0 - A0.T).max() <= 1e-12 * np.abs(A0).max()
+    Pm = injection(fine)
+    A1 = dense_var(eps, h, bc, 1, (6, 6, 6))
+    assert np.abs((Pm.T / 8.0) @ A0 @ Pm - A1).max() <= 1e-13 * np.abs(A1).max()
+    P2 = injection((6, 6, 6))
+    A2 = dense_var(eps, h, bc, 2, (3, 3, 3))
+    assert np.abs((P2.T / 8.0) @ A1 @ P2 - A2).max() <= 1e-13 * np.abs(A2).max()
+
+
+def test_var_dense_direct_solve():
+    dims = (8, 6, 10)
+    nx, ny, nz = dims
+    bc = (D, N, PER, PER, D, N)
+    eps = _jumping_eps(dims, 5)
+    A = dense_var(eps, 1.0, bc, 0, dims)
+    f = synth.random_field(dims, 3)
+    x = np.linalg.solve(A, f.ravel()).reshape(nz, ny, nx)
+    phi, k, rel = oracle.var_solve(f, eps, 1.0, bc, tol=1e-13, max_cycles=300)
+    assert np.linalg.norm(phi - x) / np.linalg.norm(x) < 1e-11
+
+
+@pytest.mark.parametrize("h", [1.0, 0.25])
+def test_var_layered_dielectric_between_plates(h):
+    """Two dielectric layers between plates at 0 and V (interface on a cell face): the flux is
+    constant, so the exact potential is linear in each layer with slopes q/eps1 and q/eps2,
+    V = q (L/2) (1/eps1 + 1/eps2). The harmonic-mean face weight and the wall folding reproduce
+    it exactly at the cell centres."""
+    nx, ny, nz = 6, 4, 16
+    e1, e2, V = 3.0, 40.0, 2.0
+    L = nz * h
+    eps = np.empty((nz, ny, nx))
+    eps[: nz // 2] = e1
+    eps[nz // 2:] = e2
+    bc = (N, N, PER, PER, D, D)
+    bcv = (0.0, 0.0, 0.0, 0.0, 0.0, V)
+    f = oracle.var_rhs(np.zeros((nz, ny, nx)), eps, h, bc, bcv)
+    phi, k, rel = oracle.var_solve(f, eps, h, bc, tol=1e-14, max_cycles=200)
+    q = V / ((L / 2) * (1 / e1 + 1 / e2))
+    z = (np.arange(nz) + 0.5) * h
+    exact = np.where(z < L / 2, q * z / e1, q * (L / 2) / e1 + q * (z - L / 2) / e2)
+    assert np.abs(phi - exact[:, None, None]).max() < 1e-12 * V
+    # the arithmetic mean at the interface would not reproduce it
+    assert abs((phi[nz // 2] - phi[nz // 2 - 1]).max() - q * h * (1 / e1 + 1 / e2) / 2) < 1e-12
