@@ -101,6 +101,22 @@ mg_status mg_set_bc_values(mg_ctx* ctx, const double* h_bc_value6);
  * per-cell values. */
 mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
 
+/* Variable permittivity (Sec. 3: the solver extends to discontinuous dielectricity by Galerkin
+ * coarsening with the averaging restriction and the nearest-neighbour prolongation). d_eps
+ * (device, nx*ny*nz doubles, natural order, positive and finite; not checked) gives the cell
+ * permittivities; the equation becomes -div(eps grad phi) = rho, the flux between two cells
+ * weighted by the harmonic mean of their permittivities and a wall face by its cell's (Dirichlet
+ * ghost 2 g - phi, Neumann phi + h g, as in the constant case), and every coarse level carries the
+ * Galerkin operator R A P of the finer one. The array is copied and the level coefficients are
+ * built before the call returns; mg_set_rhs then takes f = rho with the wall terms 2 eps g / h^2
+ * and eps g / h, and the cycle, the solve and the residual use the weighted operators. NULL
+ * returns to the constant permittivity of mg_params. Errors: MG_ERR_INVALID in MG_MIXED mode
+ * (FP64 only), MG_ERR_OOM if the coefficients (4 doubles per cell and level) cannot be allocated.
+ * mg_rhs_adjoint refuses a context with a variable permittivity (its adjoint differs). */
+mg_status mg_set_permittivity(mg_ctx* ctx, const double* d_eps);
+/* 1 if a variable permittivity is set, 0 otherwise (and for a NULL context). */
+int mg_has_permittivity(const mg_ctx* ctx);
+
 /* Right-hand side from a charge density: f = rho/eps, then adapted to the wall values once
  * on the finest grid (Sec. 2.4 and Sec. 5.3: Dirichlet face cells += 2 g / h^2, Neumann face
  * cells += g / h; periodic faces add nothing). d_rho: nx*ny*nz doubles. */
@@ -187,8 +203,11 @@ mg_status mg_step_host(mg_ctx* ctx, int P, const double* h_centers, const double
 /* ----------------------------------------------------------------------------------------- */
 /* Level-wise operations, for verifying each kernel on its own. level 0 is the finest.
  * Level fields are exchanged in natural (x-fastest) order, in double, whatever the internal
- * layout and precision. which: 0 = solution/correction phi_l, 1 = right-hand side f_l.
- * In MG_MIXED mode these address the single-precision hierarchy (values rounded to float). */
+ * layout and precision. which: 0 = solution/correction phi_l, 1 = right-hand side f_l; for
+ * mg_level_get with a variable permittivity set also 2 = the diagonal D_l, 3, 4, 5 = the weights
+ * of the cells' -x, -y, -z faces (scaled: A_l = (D_l phi - sum w phi_neighbour) / (2^l h^2)).
+ * In MG_MIXED mode these address the single-precision hierarchy (values rounded to float). The
+ * operations below use the weighted operators while a variable permittivity is set. */
 mg_status mg_level_set(mg_ctx* ctx, int level, int which, const double* d_in);
 mg_status mg_level_get(mg_ctx* ctx, int level, int which, double* d_out);
 /* One red (colour 0, i+j+k even) or black (colour 1) Gauss-Seidel half-sweep on level l. */

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB_PATH = os.path.join(HERE, "libccmg.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["level_kernels.cu", "smooth_tma.cu", "field_kernels.cu", "ccmg_api.cu", "static_scratch.cu",
+SOURCES = ["level_kernels.cu", "smooth_tma.cu", "field_kernels.cu", "ccmg_api.cu", "static_scratch.cu", "var_kernels.cu",
            "batch_kernels.cu", "batch_api.cu"]
 HEADERS = ["ccmg_internal.cuh", "level_ops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

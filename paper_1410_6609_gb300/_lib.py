@@ -82,6 +82,8 @@ SIGNATURES = {
     "mg_kernel_launches": (ctypes.c_longlong, [_P]),
     "mg_level_sweep_kind": (_I, [_P, _I]),
     "mg_selftest_wait_timeout": (_I, [_P, _I]),
+    "mg_set_permittivity": (_I, [_P, _P]),
+    "mg_has_permittivity": (_I, [_P]),
     "mg_residual_norm_static": (_I, [_I, _I, _I, _D, _P, _P, _P, _P, _P]),
     "mg_batch_create": (_I, [_I, _P, _P, _P]),
     "mg_batch_destroy": (_I, [_P]),

@@ -57,6 +57,8 @@ struct mg_ctx {
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
   double* d_bcf[6] = {};       // per-cell wall values of each face (allocated on first use)
+  double* d_eps = nullptr;     // variable permittivity (cell values), or null: the constant eps
+  double* vc[kMaxLevels]{};    // its coefficients per level (D, wx, wy, wz)
   std::string err;
 };
 
@@ -94,6 +96,8 @@ void free_all(mg_ctx* c) {
     cudaFree(c->g32[l]);
   }
   for (int q = 0; q < 6; ++q) cudaFree(c->d_bcf[q]);
+  cudaFree(c->d_eps);
+  for (int l = 0; l < kMaxLevels; ++l) cudaFree(c->vc[l]);
   cudaFree(c->partials);
   cudaFree(c->scal);
   cudaFree(c->d_iters);
@@ -115,6 +119,40 @@ cudaError_t sweep(mg_ctx* c, T* x, const T* g, const InvDiag<T>& inv, int l, int
     if (!zero && c->tma[l].ok && x == c->x32[l] && g == c->g32[l])
       return launch_smooth_tma(x, c->geo[l], inv, colour, c->tma[l], c->d_err, s);
   return launch_smooth<T>(x, g, c->geo[l], inv, colour, zero, s);
+}
+
+// The FP64 V-cycle with the variable-permittivity operators (the same steps, weighted kernels).
+cudaError_t enqueue_vcycle_var(mg_ctx* c, int l, bool zero, cudaStream_t s, long long* nk) {
+  const Geom& G = c->geo[l];
+  double* x = c->x64[l];
+  const double* g = c->g64[l];
+  cudaError_t e;
+  if (l == c->L - 1) {
+    ++*nk;
+    return launch_var_coarse_cg(x, g, c->vc[l], G, 1e-14, 2 * G.nx * G.ny * G.nz, c->d_iters, s);
+  }
+  if (zero && c->p.nu1 == 0) {
+    e = cudaMemsetAsync(x, 0, sizeof(double) * (size_t)cells(G), s);
+    if (e != cudaSuccess) return e;
+  }
+  for (int it = 0; it < c->p.nu1; ++it) {
+    if ((e = launch_var_smooth(x, g, c->vc[l], G, 0, zero && it == 0, s)) != cudaSuccess) return e;
+    if ((e = launch_var_smooth(x, g, c->vc[l], G, 1, false, s)) != cudaSuccess) return e;
+    *nk += 2;
+  }
+  if ((e = launch_var_resid_restrict(x, g, c->vc[l], G, c->g64[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
+  ++*nk;
+  if ((e = enqueue_vcycle_var(c, l + 1, true, s, nk)) != cudaSuccess) return e;
+  if ((e = launch_prolong<double>(x, G, c->x64[l + 1], c->geo[l + 1], c->p.cgc_weight, c->p.nu2 >= 1, s)) !=
+      cudaSuccess)
+    return e;
+  ++*nk;
+  for (int it = 0; it < c->p.nu2; ++it) {
+    if ((e = launch_var_smooth(x, g, c->vc[l], G, 1, false, s)) != cudaSuccess) return e;
+    if ((e = launch_var_smooth(x, g, c->vc[l], G, 0, false, s)) != cudaSuccess) return e;
+    *nk += 2;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -170,6 +208,7 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
 // residual that the residual graph left in g32[0] (the first from e = 0), followed by
 // phi += scale * e (phi = scale * e for a zero iterate, `first`) and the next scale.
 cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk, bool first) {
+  if (c->d_eps) return enqueue_vcycle_var(c, 0, false, s, nk);
   if (!mixed(c)) return enqueue_vcycle<double>(c, c->x64, c->g64, c->inv64, 0, false, s, nk);
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < c->p.mixed_inner; ++it)
@@ -186,6 +225,13 @@ cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk, bool first) 
 // single-precision residual for the next inner cycle.
 cudaError_t enqueue_resid(mg_ctx* c, int mode, double* out_natural, cudaStream_t s, long long* nk) {
   int np = 0;
+  if (c->d_eps) {
+    cudaError_t e = launch_var_resid_norm(c->x64[0], c->g64[0], c->vc[0], c->geo[0], level_coeff(c, 0), c->partials,
+                                          &np, mode == 1 ? out_natural : nullptr, s);
+    if (e != cudaSuccess) return e;
+    *nk += 2;
+    return launch_finalize(c->partials, np, c->scal, S_RSUM, S_REL, S_GSUM, s);
+  }
   cudaError_t e = launch_resid_norm<double>(c->x64[0], c->g64[0], c->geo[0], c->partials, &np, mode,
                                             level_coeff(c, 0), out_natural, mode == 2 ? c->g32[0] : nullptr,
                                             c->scal + S_INV_SCALE, s);
@@ -406,6 +452,7 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pin, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_coarse_cg();
+  if (e == cudaSuccess) e = prepare_var_coarse_cg();
   // TMA-staged half-sweeps on the single-precision levels where they are the faster kernel;
   // CCMG_SWEEP=vec keeps the direct-load kernel everywhere, CCMG_SWEEP=tma takes the TMA one on
   // every level it can run on (both for comparing and testing the two)
@@ -530,7 +577,10 @@ static mg_status set_rhs_impl(mg_ctx* c, const double* d_rho, int raw) {
   if (!c) return MG_ERR_INVALID;
   if (!d_rho) return fail(c, MG_ERR_INVALID, "null right-hand side");
   const Geom& G = c->geo[0];
-  CK(launch_set_rhs<double>(c->g64[0], G, d_rho, 1.0 / c->p.eps, c->p.h, c->bc, raw, c->stream), "set_rhs");
+  if (c->d_eps && !raw)
+    CK(launch_var_set_rhs(c->g64[0], G, d_rho, c->d_eps, c->p.h, c->bc, c->stream), "set_rhs");
+  else
+    CK(launch_set_rhs<double>(c->g64[0], G, d_rho, 1.0 / c->p.eps, c->p.h, c->bc, raw, c->stream), "set_rhs");
   int np = 0;
   CK(launch_sumsq<double>(c->g64[0], cells(G), c->partials, &np, c->stream), "set_rhs norm");
   CK(launch_finalize(c->partials, np, c->scal, S_GSUM, -1, 0, c->stream), "set_rhs norm");
@@ -538,6 +588,54 @@ static mg_status set_rhs_impl(mg_ctx* c, const double* d_rho, int raw) {
   c->launches += 4;
   return MG_OK;
 }
+
+mg_status mg_set_permittivity(mg_ctx* c, const double* d_eps) {
+  if (!c) return MG_ERR_INVALID;
+  if (d_eps && mixed(c)) return fail(c, MG_ERR_INVALID, "a variable permittivity needs MG_FP64");
+  // the cycle and residual graphs hold the operator's kernels: capture them again
+  for (cudaGraphExec_t* gx : {&c->g_cycle, &c->g_cycle0, &c->g_resid, &c->g_resid0})
+    if (*gx) {
+      cudaGraphExecDestroy(*gx);
+      *gx = nullptr;
+    }
+  if (!d_eps) {
+    CK(cudaStreamSynchronize(c->stream), "permittivity");
+    cudaFree(c->d_eps);
+    c->d_eps = nullptr;
+    for (int l = 0; l < c->L; ++l) {
+      cudaFree(c->vc[l]);
+      c->vc[l] = nullptr;
+    }
+    return MG_OK;
+  }
+  const Geom& G = c->geo[0];
+  const size_t n = (size_t)G.nx * G.ny * G.nz;
+  if (!c->d_eps) {
+    if (cudaMalloc((void**)&c->d_eps, n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_eps = nullptr;
+      return fail(c, MG_ERR_OOM, "permittivity");
+    }
+    for (int l = 0; l < c->L; ++l)
+      if (cudaMalloc((void**)&c->vc[l], 4 * (size_t)cells(c->geo[l]) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        for (int q = 0; q <= l; ++q) {
+          cudaFree(c->vc[q]);
+          c->vc[q] = nullptr;
+        }
+        cudaFree(c->d_eps);
+        c->d_eps = nullptr;
+        return fail(c, MG_ERR_OOM, "permittivity coefficients");
+      }
+  }
+  CK(cudaMemcpyAsync(c->d_eps, d_eps, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "permittivity");
+  CK(launch_var_setup(c->d_eps, c->geo, c->L, c->bc, c->vc, c->stream), "permittivity coefficients");
+  c->launches += c->L;
+  CK(cudaStreamSynchronize(c->stream), "permittivity");
+  return MG_OK;
+}
+
+int mg_has_permittivity(const mg_ctx* c) { return c && c->d_eps ? 1 : 0; }
 
 mg_status mg_set_rhs(mg_ctx* c, const double* d_rho) { return set_rhs_impl(c, d_rho, 0); }
 mg_status mg_set_rhs_f(mg_ctx* c, const double* d_f) { return set_rhs_impl(c, d_f, 1); }
@@ -701,6 +799,7 @@ mg_status mg_sphere_density_adjoint(mg_ctx* c, int P, const double* ctr, const d
 mg_status mg_rhs_adjoint(mg_ctx* c, const double* d_lam, double* d_grho, double* d_gbc) {
   if (!c) return MG_ERR_INVALID;
   if (!d_lam || !d_grho || !d_gbc) return fail(c, MG_ERR_INVALID, "null argument");
+  if (c->d_eps) return fail(c, MG_ERR_INVALID, "the right-hand-side adjoint is for a constant permittivity");
   CK(launch_rhs_adjoint(c->geo[0], c->p.h, 1.0 / c->p.eps, c->bc, d_lam, d_grho, d_gbc, c->stream), "rhs_adjoint");
   c->launches += 2;
   return MG_OK;
@@ -771,6 +870,14 @@ mg_status mg_level_set(mg_ctx* c, int level, int which, const double* d_in) {
 
 mg_status mg_level_get(mg_ctx* c, int level, int which, double* d_out) {
   if (!c) return MG_ERR_INVALID;
+  if (level >= 0 && level < c->L && which >= 2 && which <= 5 && d_out) {  // permittivity coefficients
+    if (!c->d_eps) return fail(c, MG_ERR_INVALID, "no variable permittivity is set");
+    CK(launch_unpack<double>(d_out, c->vc[level] + (which - 2) * cells(c->geo[level]), c->geo[level], 1.0,
+                             c->stream),
+       "level_get");
+    c->launches += 1;
+    return MG_OK;
+  }
   if (level < 0 || level >= c->L || (which != 0 && which != 1) || !d_out)
     return fail(c, MG_ERR_INVALID, "bad level, field or pointer");
   const double scale = which == 0 ? 1.0 : level_coeff(c, level);
@@ -789,7 +896,10 @@ mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1 || (colour != 0 && colour != 1))
     return fail(c, MG_ERR_INVALID, "smoothing needs a non-coarsest level and colour 0 or 1");
-  if (mixed(c))
+  if (c->d_eps)
+    CK(launch_var_smooth(c->x64[level], c->g64[level], c->vc[level], c->geo[level], colour, false, c->stream),
+       "smooth");
+  else if (mixed(c))
     CK(sweep<float>(c, c->x32[level], c->g32[level], c->inv32, level, colour, false, c->stream), "smooth");
   else
     CK(launch_smooth<double>(c->x64[level], c->g64[level], c->geo[level], c->inv64, colour, false, c->stream),
@@ -801,7 +911,12 @@ mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
 static mg_status residual_restrict_op(mg_ctx* c, int level, bool red_only) {
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "restriction needs a non-coarsest level");
-  if (mixed(c))
+  if (c->d_eps && red_only) return fail(c, MG_ERR_INVALID, "the red-only restriction is single precision");
+  if (c->d_eps)
+    CK(launch_var_resid_restrict(c->x64[level], c->g64[level], c->vc[level], c->geo[level], c->g64[level + 1],
+                                 c->geo[level + 1], c->stream),
+       "residual_restrict");
+  else if (mixed(c))
     CK(launch_resid_restrict<float>(c->x32[level], c->g32[level], c->geo[level], c->g32[level + 1],
                                     c->geo[level + 1], red_only, c->stream),
        "residual_restrict");
@@ -838,7 +953,9 @@ mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
   const Geom& G = c->geo[l];
   const int n = G.nx * G.ny * G.nz;
   if (!mixed(c) && l == 0) c->phi_zero = false;  // single-level grid: the CG writes the finest iterate
-  if (mixed(c))
+  if (c->d_eps)
+    CK(launch_var_coarse_cg(c->x64[l], c->g64[l], c->vc[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
+  else if (mixed(c))
     CK(launch_coarse_cg<float>(c->x32[l], c->g32[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
   else
     CK(launch_coarse_cg<double>(c->x64[l], c->g64[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");

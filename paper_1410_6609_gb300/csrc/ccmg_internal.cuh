@@ -96,6 +96,23 @@ __device__ __forceinline__ double face_value(const FaceBC& bc, int q, int i, int
   return f ? __ldg(f + face_index(q, i, j, k, nx, ny)) : bc.value[q];
 }
 
+// Variable permittivity (var_kernels.cu): four coefficient arrays per level (D, wx, wy, wz, each
+// of the level's cell count, in its storage order) at vc[l].
+long long var_cells(const Geom& G);
+cudaError_t launch_var_setup(const double* eps, const Geom* geo, int L, const FaceBC& bc, double* const* vc,
+                             cudaStream_t s);
+cudaError_t launch_var_smooth(double* x, const double* g, const double* vc, const Geom& G, int colour, bool zero,
+                              cudaStream_t s);
+cudaError_t launch_var_resid_restrict(const double* x, const double* g, const double* vc, const Geom& G, double* gc,
+                                      const Geom& Gc, cudaStream_t s);
+cudaError_t launch_var_resid_norm(const double* x, const double* g, const double* vc, const Geom& G, double c0,
+                                  double* partials, int* nparts, double* out_natural, cudaStream_t s);
+cudaError_t launch_var_coarse_cg(double* x, const double* b, const double* vc, const Geom& Gc, double rtol, int maxit,
+                                 int* d_iters, cudaStream_t s);
+cudaError_t prepare_var_coarse_cg();
+cudaError_t launch_var_set_rhs(double* g, const Geom& G, const double* rho, const double* eps, double h,
+                               const FaceBC& bc, cudaStream_t s);
+
 // Kernel launchers (all enqueue on `s`; return cudaGetLastError()).
 template <typename T>
 cudaError_t launch_smooth(T* x, const T* g, const Geom& G, const InvDiag<T>& inv, int colour, bool zero_start,

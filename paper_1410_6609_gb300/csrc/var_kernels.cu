@@ -1,0 +1,410 @@
+// var_kernels.cu -- the solver with a variable permittivity (sm_103a), FP64.
+//
+// Sec. 3 of the paper: the cell-centred solver extends to discontinuous dielectricity through
+// Galerkin coarsening with the averaging restriction and the nearest-neighbour prolongation (after
+// Alcouffe et al.). The equation becomes -div(eps grad phi) = rho; the flux through the face of
+// two cells has the weight of the harmonic mean of their permittivities, and a wall face the
+// weight of its cell's permittivity (Dirichlet: counted twice, ghost 2 g - phi; Neumann: not at
+// all, ghost phi + h g; periodic: the face to the cell at the opposite side). Every level stores,
+// in its own order (packed colours, or natural order on the coarsest level), four arrays of its
+// cell count: the diagonal D and the weights wx, wy, wz of each cell's -x, -y, -z faces, scaled as
+// in the constant case (A_l = c_l (D phi - sum w phi_neighbour), c_l = 1/(2^l h^2)). The +x face
+// of a cell is the -x face of its +x neighbour, so its weight sits at that neighbour's index:
+// the same index as the neighbour's potential. Galerkin coarsening, A_{l+1} = R A_l P with
+// R = P^T / 8, keeps this form:
+//   w_{l+1}(coarse face) = (1/4) (sum of the 4 fine face weights on it),
+//   D_{l+1}(I) = (1/4) (sum of the 8 children's D - 2 (sum of the 12 faces inside I)).
+// The setup kernels evaluate these in the oracle's order with rounded operations, so the
+// coefficients agree bit for bit; the cycle kernels are the FP64 cell-by-cell forms of the
+// smoother, the fused residual and restriction, the residual norm and the coarse CG.
+#include "ccmg_internal.cuh"
+#include "level_ops.cuh"
+
+namespace ccmg {
+namespace {
+
+using ops::block_sum;
+using ops::coarse_index;
+using ops::nb_has;
+using ops::nb_off;
+
+// The four coefficient arrays of a level at vc: D, wx, wy, wz, each of `n` entries.
+struct VarCoef {
+  const double* D;
+  const double* wx;
+  const double* wy;
+  const double* wz;
+};
+__device__ __forceinline__ VarCoef var_coef(const double* vc, long long n) {
+  return VarCoef{vc, vc + n, vc + 2 * n, vc + 3 * n};
+}
+
+__device__ __forceinline__ double harmonic(double a, double b) { return __ddiv_rn(__dmul_rn(2.0 * a, b), a + b); }
+
+__device__ __forceinline__ long long natural(const Geom& G, int i, int j, int k) {
+  return (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+}
+
+// Level-0 coefficients from the cell permittivities eps (natural order).
+__global__ void __launch_bounds__(256) k_var_fine(const double* __restrict__ eps, Geom G, FaceBC bc,
+                                                  double* __restrict__ vc, long long n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  const int nn[3] = {G.nx, G.ny, G.nz}, pos[3] = {i, j, k};
+  const double e = __ldg(eps + natural(G, i, j, k));
+  double w[3], D = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int q[3] = {i, j, k};
+    const bool per = (G.per >> a) & 1;
+    // the -a face
+    double wm;
+    if (pos[a] > 0 || per) {
+      q[a] = pos[a] > 0 ? pos[a] - 1 : nn[a] - 1;
+      wm = harmonic(__ldg(eps + natural(G, q[0], q[1], q[2])), e);
+    } else {
+      wm = e;
+    }
+    w[a] = wm;
+    if (pos[a] > 0 || per) D = __dadd_rn(D, wm);
+    else if (bc.type[2 * a] == 0) D = __dadd_rn(D, __dmul_rn(2.0, e));
+    // the +a face: the -a face of the next cell (of cell 0 across a periodic axis)
+    if (pos[a] < nn[a] - 1 || per) {
+      q[a] = pos[a] < nn[a] - 1 ? pos[a] + 1 : 0;
+      const double en = __ldg(eps + natural(G, q[0], q[1], q[2]));
+      D = __dadd_rn(D, harmonic(e, en));
+    } else if (bc.type[2 * a + 1] == 0) {
+      D = __dadd_rn(D, __dmul_rn(2.0, e));
+    }
+  }
+  const long long o = coarse_index(G, i, j, k);
+  vc[o] = D;
+  vc[n + o] = w[0];
+  vc[2 * n + o] = w[1];
+  vc[3 * n + o] = w[2];
+}
+
+// Galerkin coefficients of coarse level Gc from fine level Gf (the oracle's summation order).
+__global__ void __launch_bounds__(256) k_var_coarsen(const double* __restrict__ vf, Geom Gf, long long nf,
+                                                     double* __restrict__ vcc, Geom Gc, long long nc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= Gc.nx || J >= Gc.ny) return;
+  const VarCoef F = var_coef(vf, nf);
+  auto at = [&](const double* a, int i, int j, int k) { return __ldg(a + coarse_index(Gf, i, j, k)); };
+  double sx = 0.0, sy = 0.0, sz = 0.0, sd = 0.0, inner = 0.0;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      sx = __dadd_rn(sx, at(F.wx, 2 * I, 2 * J + u, 2 * K + v));
+      sy = __dadd_rn(sy, at(F.wy, 2 * I + u, 2 * J, 2 * K + v));
+      sz = __dadd_rn(sz, at(F.wz, 2 * I + u, 2 * J + v, 2 * K));
+    }
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) sd = __dadd_rn(sd, at(F.D, 2 * I + di, 2 * J + dj, 2 * K + dk));
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      inner = __dadd_rn(inner, at(F.wx, 2 * I + 1, 2 * J + u, 2 * K + v));
+      inner = __dadd_rn(inner, at(F.wy, 2 * I + u, 2 * J + 1, 2 * K + v));
+      inner = __dadd_rn(inner, at(F.wz, 2 * I + u, 2 * J + v, 2 * K + 1));
+    }
+  const long long o = coarse_index(Gc, I, J, K);
+  vcc[o] = __ddiv_rn(__dsub_rn(sd, __dmul_rn(2.0, inner)), 4.0);
+  vcc[nc + o] = __ddiv_rn(sx, 4.0);
+  vcc[2 * nc + o] = __ddiv_rn(sy, 4.0);
+  vcc[3 * nc + o] = __ddiv_rn(sz, 4.0);
+}
+
+// Weighted neighbour sum of cell m of colour c, row (j, k), on a packed level, in the order
+// -x,+x,-y,+y,-z,+z (walls: none; periodic axes wrap). The weight of a + face is read at the
+// neighbour's index, where its potential is.
+__device__ __forceinline__ double var_nbsum_packed(const double* __restrict__ x, const VarCoef& W, const Geom& G,
+                                                   int c, int m, int j, int k) {
+  const int s = (j + k + c) & 1;
+  const long long row = ((long long)k * G.ny + j) * G.hx;
+  const long long own = (long long)c * G.csz + row + m;
+  const long long oth = (long long)(1 - c) * G.csz + row;
+  const bool px = (G.per & 1) != 0;
+  double acc = 0.0;
+  if (!(m == 0 && s == 0)) acc = fma(__ldg(W.wx + own), __ldg(x + oth + m + s - 1), acc);
+  else if (px) acc = fma(__ldg(W.wx + own), __ldg(x + oth + G.hx - 1), acc);
+  if (!(m == G.hx - 1 && s == 1)) {
+    const long long q = oth + m + s;
+    acc = fma(__ldg(W.wx + q), __ldg(x + q), acc);
+  } else if (px) {
+    acc = fma(__ldg(W.wx + oth), __ldg(x + oth), acc);
+  }
+  if (nb_has<0, true>(G, j, k)) acc = fma(__ldg(W.wy + own), __ldg(x + oth + m + nb_off<0, true>(G, j, k)), acc);
+  if (nb_has<1, true>(G, j, k)) {
+    const long long q = oth + m + nb_off<1, true>(G, j, k);
+    acc = fma(__ldg(W.wy + q), __ldg(x + q), acc);
+  }
+  if (nb_has<2, true>(G, j, k)) acc = fma(__ldg(W.wz + own), __ldg(x + oth + m + nb_off<2, true>(G, j, k)), acc);
+  if (nb_has<3, true>(G, j, k)) {
+    const long long q = oth + m + nb_off<3, true>(G, j, k);
+    acc = fma(__ldg(W.wz + q), __ldg(x + q), acc);
+  }
+  return acc;
+}
+
+// The same on a natural-order level.
+__device__ __forceinline__ double var_nbsum_natural(const double* __restrict__ x, const VarCoef& W, const Geom& G,
+                                                    int i, int j, int k) {
+  const long long p = natural(G, i, j, k);
+  const long long sy = G.nx, sz = (long long)G.nx * G.ny;
+  const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0, pz = (G.per & 4) != 0;
+  double acc = 0.0;
+  if (i > 0) acc = fma(W.wx[p], x[p - 1], acc);
+  else if (px) acc = fma(W.wx[p], x[p + G.nx - 1], acc);
+  if (i < G.nx - 1) acc = fma(W.wx[p + 1], x[p + 1], acc);
+  else if (px) acc = fma(W.wx[p - (G.nx - 1)], x[p - (G.nx - 1)], acc);
+  if (j > 0) acc = fma(W.wy[p], x[p - sy], acc);
+  else if (py) acc = fma(W.wy[p], x[p + (G.ny - 1) * sy], acc);
+  if (j < G.ny - 1) acc = fma(W.wy[p + sy], x[p + sy], acc);
+  else if (py) acc = fma(W.wy[p - (G.ny - 1) * sy], x[p - (G.ny - 1) * sy], acc);
+  if (k > 0) acc = fma(W.wz[p], x[p - sz], acc);
+  else if (pz) acc = fma(W.wz[p], x[p + (G.nz - 1) * sz], acc);
+  if (k < G.nz - 1) acc = fma(W.wz[p + sz], x[p + sz], acc);
+  else if (pz) acc = fma(W.wz[p - (G.nz - 1) * sz], x[p - (G.nz - 1) * sz], acc);
+  return acc;
+}
+
+// Red-black Gauss-Seidel half-sweep: phi = (g + weighted neighbours) / D for the cells of
+// `colour` (ZERO: the iterate is zero, phi = g / D).
+template <bool ZERO>
+__global__ void __launch_bounds__(256) k_var_smooth(double* __restrict__ x, const double* __restrict__ g,
+                                                    const double* __restrict__ vc, Geom G, int colour) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (m >= G.hx || j >= G.ny) return;
+  const VarCoef W = var_coef(vc, 2 * G.csz);
+  const long long own = (long long)colour * G.csz + ((long long)k * G.ny + j) * G.hx + m;
+  const double S = ZERO ? 0.0 : var_nbsum_packed(x, W, G, colour, m, j, k);
+  x[own] = __ddiv_rn(__ldg(g + own) + S, __ldg(W.D + own));
+}
+
+// Fused residual and averaging restriction: gc(I,J,K) = (1/4) sum of the 8 children's scaled
+// residuals g + sum w phi - D phi, in the order (dk, dj, di).
+__global__ void __launch_bounds__(256) k_var_resid_restrict(const double* __restrict__ x,
+                                                            const double* __restrict__ g,
+                                                            const double* __restrict__ vc, Geom G,
+                                                            double* __restrict__ gc, Geom Gc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= Gc.nx || J >= Gc.ny) return;
+  const VarCoef W = var_coef(vc, 2 * G.csz);
+  double acc = 0.0;
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        const int j = 2 * J + dj, k = 2 * K + dk;
+        const int c = (di + dj + dk) & 1;
+        const long long own = (long long)c * G.csz + ((long long)k * G.ny + j) * G.hx + I;
+        const double S = var_nbsum_packed(x, W, G, c, I, j, k);
+        acc = acc + fma(-__ldg(W.D + own), __ldg(x + own), __ldg(g + own) + S);
+      }
+  gc[coarse_index(Gc, I, J, K)] = acc * 0.25;
+}
+
+// Scaled residual of every cell with per-block partial sums of its square; OUT: also the
+// residual field r = r~ c0 in natural order.
+template <bool OUT>
+__global__ void __launch_bounds__(256) k_var_resid_norm(const double* __restrict__ x, const double* __restrict__ g,
+                                                        const double* __restrict__ vc, Geom G, double c0,
+                                                        double* __restrict__ partials, double* __restrict__ outn) {
+  __shared__ double red[33];
+  const VarCoef W = var_coef(vc, G.packed ? 2 * G.csz : G.csz);
+  const long long n = G.packed ? 2 * G.csz : G.csz;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double rd;
+    long long nat;
+    if (G.packed) {
+      const int c = (int)(t / G.csz);
+      const long long r = t - (long long)c * G.csz;
+      const int m = (int)(r % G.hx);
+      const long long rw = r / G.hx;
+      const int j = (int)(rw % G.ny), k = (int)(rw / G.ny);
+      const double S = var_nbsum_packed(x, W, G, c, m, j, k);
+      rd = fma(-__ldg(W.D + t), __ldg(x + t), __ldg(g + t) + S);
+      nat = (long long)(2 * m + ((j + k + c) & 1)) + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+    } else {
+      const int i = (int)(t % G.nx), j = (int)((t / G.nx) % G.ny), k = (int)(t / ((long long)G.nx * G.ny));
+      const double S = var_nbsum_natural(x, W, G, i, j, k);
+      rd = fma(-W.D[t], x[t], g[t] + S);
+      nat = t;
+    }
+    acc = fma(rd, rd, acc);
+    if (OUT) outn[nat] = rd * c0;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// Unpreconditioned CG on the coarsest (natural-order) level with the weighted operator, one CTA,
+// vectors in shared memory (4 n doubles); stops at ||r|| <= rtol ||b|| or maxit iterations.
+__global__ void __launch_bounds__(256) k_var_coarse_cg(double* __restrict__ xo, const double* __restrict__ bi,
+                                                       const double* __restrict__ vc, Geom G, double rtol, int maxit,
+                                                       int* iters) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  const int n = G.nx * G.ny * G.nz;
+  const VarCoef W = var_coef(vc, n);
+  double* x = sm;
+  double* r = x + n;
+  double* p = r + n;
+  double* ap = p + n;
+  double loc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double b = bi[i];
+    x[i] = 0.0;
+    r[i] = b;
+    p[i] = b;
+    loc += b * b;
+  }
+  double rr = block_sum(loc, red);
+  const double bnorm = sqrt(rr);
+  int it = 0;
+  if (bnorm > 0.0) {
+    while (it < maxit) {
+      loc = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ix = i % G.nx, iy = (i / G.nx) % G.ny, iz = i / (G.nx * G.ny);
+        const double a = W.D[i] * p[i] - var_nbsum_natural(p, W, G, ix, iy, iz);
+        ap[i] = a;
+        loc += p[i] * a;
+      }
+      const double pap = block_sum(loc, red);
+      const double alpha = rr / pap;
+      loc = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        x[i] = x[i] + alpha * p[i];
+        const double ri = r[i] - alpha * ap[i];
+        r[i] = ri;
+        loc += ri * ri;
+      }
+      const double rrn = block_sum(loc, red);
+      ++it;
+      if (sqrt(rrn) <= rtol * bnorm) break;
+      const double beta = rrn / rr;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = r[i] + beta * p[i];
+      __syncthreads();
+      rr = rrn;
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xo[i] = x[i];
+  if (threadIdx.x == 0 && iters) *iters = it;
+}
+
+// Right-hand side of -div(eps grad phi) = rho, scaled g = f h^2: f = rho, Dirichlet face cells
+// += 2 eps g / h^2, Neumann face cells += eps g / h (the oracle's operations and face order).
+__global__ void __launch_bounds__(256) k_var_set_rhs(double* __restrict__ gout, Geom G,
+                                                     const double* __restrict__ rho,
+                                                     const double* __restrict__ eps, double h, FaceBC bc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  const long long p = natural(G, i, j, k);
+  double v = rho[p];
+  const bool on[6] = {i == 0, i == G.nx - 1, j == 0, j == G.ny - 1, k == 0, k == G.nz - 1};
+  const double e = eps[p];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (!on[q] || bc.type[q] == 2) continue;
+    const double gv = face_value(bc, q, i, j, k, G.nx, G.ny);
+    v = bc.type[q] == 0 ? __dadd_rn(v, __ddiv_rn(__dmul_rn(__dmul_rn(2.0, e), gv), __dmul_rn(h, h)))
+                        : __dadd_rn(v, __ddiv_rn(__dmul_rn(e, gv), h));
+  }
+  gout[coarse_index(G, i, j, k)] = __dmul_rn(v, __dmul_rn(h, h));
+}
+
+void shape2(int nx, int ny, int nz, dim3& b, dim3& g) {
+  const int bx = nx >= 64 ? 64 : (nx >= 32 ? 32 : 16);
+  b = dim3(bx, 256 / bx, 1);
+  g = dim3((nx + bx - 1) / bx, (ny + b.y - 1) / b.y, nz);
+}
+
+}  // namespace
+
+long long var_cells(const Geom& G) { return G.packed ? 2 * G.csz : G.csz; }
+
+cudaError_t launch_var_setup(const double* eps, const Geom* geo, int L, const FaceBC& bc, double* const* vc,
+                             cudaStream_t s) {
+  dim3 b, g;
+  shape2(geo[0].nx, geo[0].ny, geo[0].nz, b, g);
+  k_var_fine<<<g, b, 0, s>>>(eps, geo[0], bc, vc[0], var_cells(geo[0]));
+  for (int l = 1; l < L; ++l) {
+    shape2(geo[l].nx, geo[l].ny, geo[l].nz, b, g);
+    k_var_coarsen<<<g, b, 0, s>>>(vc[l - 1], geo[l - 1], var_cells(geo[l - 1]), vc[l], geo[l], var_cells(geo[l]));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_smooth(double* x, const double* g, const double* vc, const Geom& G, int colour, bool zero,
+                              cudaStream_t s) {
+  dim3 b, gr;
+  shape2(G.hx, G.ny, G.nz, b, gr);
+  if (zero) k_var_smooth<true><<<gr, b, 0, s>>>(x, g, vc, G, colour);
+  else k_var_smooth<false><<<gr, b, 0, s>>>(x, g, vc, G, colour);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_resid_restrict(const double* x, const double* g, const double* vc, const Geom& G, double* gc,
+                                      const Geom& Gc, cudaStream_t s) {
+  dim3 b, gr;
+  shape2(Gc.nx, Gc.ny, Gc.nz, b, gr);
+  k_var_resid_restrict<<<gr, b, 0, s>>>(x, g, vc, G, gc, Gc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_resid_norm(const double* x, const double* g, const double* vc, const Geom& G, double c0,
+                                  double* partials, int* nparts, double* out_natural, cudaStream_t s) {
+  const long long n = var_cells(G);
+  long long blocks = (n + 255) / 256;
+  if (blocks > kMaxPartials) blocks = kMaxPartials;
+  if (out_natural) k_var_resid_norm<true><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, out_natural);
+  else k_var_resid_norm<false><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, nullptr);
+  *nparts = (int)blocks;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_coarse_cg(double* x, const double* b, const double* vc, const Geom& Gc, double rtol, int maxit,
+                                 int* d_iters, cudaStream_t s) {
+  const int n = Gc.nx * Gc.ny * Gc.nz;
+  int threads = ((n + 31) / 32) * 32;
+  if (threads > 256) threads = 256;
+  const size_t smem = (size_t)4 * n * sizeof(double);
+  k_var_coarse_cg<<<1, threads, smem, s>>>(x, b, vc, Gc, rtol, maxit, d_iters);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_var_coarse_cg() {
+  const int bytes = (int)(4 * kMaxCoarseCells * sizeof(double));
+  return cudaFuncSetAttribute(k_var_coarse_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_var_set_rhs(double* g, const Geom& G, const double* rho, const double* eps, double h,
+                               const FaceBC& bc, cudaStream_t s) {
+  dim3 b, gr;
+  shape2(G.nx, G.ny, G.nz, b, gr);
+  k_var_set_rhs<<<gr, b, 0, s>>>(g, G, rho, eps, h, bc);
+  return cudaGetLastError();
+}
+
+}  // namespace ccmg

@@ -191,6 +191,20 @@ class Poisson:
         t = self._field(values, "bc field", shapes[int(face)] if 0 <= int(face) < 6 else (0,))
         self._check(self.lib.mg_set_bc_field(self.ctx, int(face), _ptr(t)), "mg_set_bc_field")
 
+    def set_permittivity(self, eps=None):
+        """Cell permittivities (float64 tensor [nz, ny, nx] on the device, positive) for
+        -div(eps grad phi) = rho with Galerkin coarse operators (see mg_set_permittivity); None
+        returns to the constant eps of the constructor."""
+        if eps is None:
+            self._check(self.lib.mg_set_permittivity(self.ctx, None), "mg_set_permittivity")
+            return
+        t = self._field(eps, "permittivity").contiguous()
+        self._check(self.lib.mg_set_permittivity(self.ctx, _ptr(t)), "mg_set_permittivity")
+
+    @property
+    def has_permittivity(self) -> bool:
+        return bool(self.lib.mg_has_permittivity(self.ctx))
+
     @property
     def gradient_stencil(self) -> int:
         """Gradient of efield / force_gather / step: 7 (D3Q7) or 19 (D3Q19 wherever it fits in the domain)."""
