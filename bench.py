@@ -486,6 +486,10 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     except Exception as e:
         out["time_loop"] = {"error": repr(e)}
     try:
+        out["permittivity"] = measure_permittivity(w, sp, t64, k64, hbm)
+    except Exception as e:
+        out["permittivity"] = {"error": repr(e)}
+    try:
         out["batched"] = measure_batched()
     except Exception as e:  # reported, never fatal for the main line
         out["batched"] = {"error": repr(e)}
@@ -529,6 +533,45 @@ def measure_time_loop(P, w, sp, r, q, stream, steps: int = 20, vel: float = 0.07
     return {"ms_per_step": ms, "mlups": N / ms / 1e3, "steps": steps, "cycles_per_step": 1,
             "first_step_cycles": 5, "sphere_velocity_cells_per_step": vel,
             "rel_residual_after_last_step": rel}
+
+
+def measure_permittivity(w, sp, t64_const, k64_const, hbm):
+    """The same spheres as dielectric particles (permittivity 2 in a fluid of 80, cells weighted
+    by their covered volume) with the workload's charges and walls: the FP64 solve of
+    -div(eps grad phi) = rho with Galerkin coarse operators to the workload's tolerance, beside
+    the constant-permittivity FP64 solve, and the weighted half-sweep's HBM throughput."""
+    import torch
+
+    from paper_1410_6609_gb300.solver import Poisson
+
+    nx, ny, nz = w.dims
+    N = nx * ny * nz
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="fp64")
+    c, r = dev(sp.centers), dev(sp.radius)
+    vol = P.sphere_density(c, r, torch.ones(sp.count, dtype=torch.float64, device="cuda"), w.subsample)
+    torch.cuda.synchronize()
+    eps = 80.0 - 78.0 * vol
+    torch.cuda.synchronize()
+    P.set_permittivity(eps)
+    rho = P.sphere_density(c, r, dev(sp.density), w.subsample)
+    P.set_rhs(rho)
+
+    def solve():
+        P.set_solution(None)
+        return P.solve(w.tol, 300)
+
+    k, rel = solve()
+    t = _time(solve, P.stream, 2)
+    t_sw = _time(lambda: P.op_smooth(0, 0), P.stream, 10)
+    # a half-sweep reads the other colour, its own right-hand side, 1/D and three weights, the
+    # other colour's three weights (the + faces), and writes its colour: 80 B per cell of it
+    bsw = 40.0 * N
+    P.close()
+    return {"tol": w.tol, "cycles": k, "rel_residual": rel, "ms": t, "solve_mlups": N / t / 1e3,
+            "constant_eps_fp64_ms": t64_const, "constant_eps_fp64_cycles": k64_const,
+            "half_sweep_ms": t_sw, "half_sweep_GB/s": bsw / t_sw / 1e6, "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm,
+            "half_sweep_bytes": int(bsw), "particle_eps": 2.0, "fluid_eps": 80.0}
 
 
 def measure_batched(tol: float = 1e-9):

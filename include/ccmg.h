@@ -111,7 +111,7 @@ mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
  * built before the call returns; mg_set_rhs then takes f = rho with the wall terms 2 eps g / h^2
  * and eps g / h, and the cycle, the solve and the residual use the weighted operators. NULL
  * returns to the constant permittivity of mg_params. Errors: MG_ERR_INVALID in MG_MIXED mode
- * (FP64 only), MG_ERR_OOM if the coefficients (4 doubles per cell and level) cannot be allocated.
+ * (FP64 only), MG_ERR_OOM if the coefficients (5 doubles per cell and level) cannot be allocated.
  * mg_rhs_adjoint refuses a context with a variable permittivity (its adjoint differs). */
 mg_status mg_set_permittivity(mg_ctx* ctx, const double* d_eps);
 /* 1 if a variable permittivity is set, 0 otherwise (and for a NULL context). */

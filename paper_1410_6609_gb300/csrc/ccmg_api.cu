@@ -58,7 +58,7 @@ struct mg_ctx {
   int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
   double* d_bcf[6] = {};       // per-cell wall values of each face (allocated on first use)
   double* d_eps = nullptr;     // variable permittivity (cell values), or null: the constant eps
-  double* vc[kMaxLevels]{};    // its coefficients per level (D, wx, wy, wz)
+  double* vc[kMaxLevels]{};    // its coefficients per level (D, wx, wy, wz, 1/D)
   std::string err;
 };
 
@@ -617,7 +617,7 @@ mg_status mg_set_permittivity(mg_ctx* c, const double* d_eps) {
       return fail(c, MG_ERR_OOM, "permittivity");
     }
     for (int l = 0; l < c->L; ++l)
-      if (cudaMalloc((void**)&c->vc[l], 4 * (size_t)cells(c->geo[l]) * sizeof(double)) != cudaSuccess) {
+      if (cudaMalloc((void**)&c->vc[l], 5 * (size_t)cells(c->geo[l]) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         for (int q = 0; q <= l; ++q) {
           cudaFree(c->vc[q]);

@@ -96,8 +96,8 @@ __device__ __forceinline__ double face_value(const FaceBC& bc, int q, int i, int
   return f ? __ldg(f + face_index(q, i, j, k, nx, ny)) : bc.value[q];
 }
 
-// Variable permittivity (var_kernels.cu): four coefficient arrays per level (D, wx, wy, wz, each
-// of the level's cell count, in its storage order) at vc[l].
+// Variable permittivity (var_kernels.cu): five coefficient arrays per level (D, wx, wy, wz, 1/D,
+// each of the level's cell count, in its storage order) at vc[l].
 long long var_cells(const Geom& G);
 cudaError_t launch_var_setup(const double* eps, const Geom* geo, int L, const FaceBC& bc, double* const* vc,
                              cudaStream_t s);

@@ -28,15 +28,18 @@ using ops::coarse_index;
 using ops::nb_has;
 using ops::nb_off;
 
-// The four coefficient arrays of a level at vc: D, wx, wy, wz, each of `n` entries.
+// The coefficient arrays of a level at vc: D, wx, wy, wz and 1/D, each of `n` entries (the
+// smoother multiplies by the stored reciprocal: FP64 division is many times slower than a
+// multiply on this GPU, and the half-sweep would be bound by it).
 struct VarCoef {
   const double* D;
   const double* wx;
   const double* wy;
   const double* wz;
+  const double* invD;
 };
 __device__ __forceinline__ VarCoef var_coef(const double* vc, long long n) {
-  return VarCoef{vc, vc + n, vc + 2 * n, vc + 3 * n};
+  return VarCoef{vc, vc + n, vc + 2 * n, vc + 3 * n, vc + 4 * n};
 }
 
 __device__ __forceinline__ double harmonic(double a, double b) { return __ddiv_rn(__dmul_rn(2.0 * a, b), a + b); }
@@ -84,6 +87,7 @@ __global__ void __launch_bounds__(256) k_var_fine(const double* __restrict__ eps
   vc[n + o] = w[0];
   vc[2 * n + o] = w[1];
   vc[3 * n + o] = w[2];
+  vc[4 * n + o] = __ddiv_rn(1.0, D);
 }
 
 // Galerkin coefficients of coarse level Gc from fine level Gf (the oracle's summation order).
@@ -119,7 +123,9 @@ __global__ void __launch_bounds__(256) k_var_coarsen(const double* __restrict__ 
       inner = __dadd_rn(inner, at(F.wz, 2 * I + u, 2 * J + v, 2 * K + 1));
     }
   const long long o = coarse_index(Gc, I, J, K);
-  vcc[o] = __ddiv_rn(__dsub_rn(sd, __dmul_rn(2.0, inner)), 4.0);
+  const double Dc = __ddiv_rn(__dsub_rn(sd, __dmul_rn(2.0, inner)), 4.0);
+  vcc[o] = Dc;
+  vcc[4 * nc + o] = __ddiv_rn(1.0, Dc);
   vcc[nc + o] = __ddiv_rn(sx, 4.0);
   vcc[2 * nc + o] = __ddiv_rn(sy, 4.0);
   vcc[3 * nc + o] = __ddiv_rn(sz, 4.0);
@@ -179,8 +185,8 @@ __device__ __forceinline__ double var_nbsum_natural(const double* __restrict__ x
   return acc;
 }
 
-// Red-black Gauss-Seidel half-sweep: phi = (g + weighted neighbours) / D for the cells of
-// `colour` (ZERO: the iterate is zero, phi = g / D).
+// Red-black Gauss-Seidel half-sweep: phi = (g + weighted neighbours) (1/D) for the cells of
+// `colour` (ZERO: the iterate is zero, phi = g (1/D)).
 template <bool ZERO>
 __global__ void __launch_bounds__(256) k_var_smooth(double* __restrict__ x, const double* __restrict__ g,
                                                     const double* __restrict__ vc, Geom G, int colour) {
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(256) k_var_smooth(double* __restrict__ x, cons
   const VarCoef W = var_coef(vc, 2 * G.csz);
   const long long own = (long long)colour * G.csz + ((long long)k * G.ny + j) * G.hx + m;
   const double S = ZERO ? 0.0 : var_nbsum_packed(x, W, G, colour, m, j, k);
-  x[own] = __ddiv_rn(__ldg(g + own) + S, __ldg(W.D + own));
+  x[own] = (__ldg(g + own) + S) * __ldg(W.invD + own);
 }
 
 // Fused residual and averaging restriction: gc(I,J,K) = (1/4) sum of the 8 children's scaled
