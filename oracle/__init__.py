@@ -86,12 +86,14 @@ def _load():
                 "ccmg_or_force_gather_stencil": (None, [P, I, I, I, D, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_field": (None, [P, I, I, I, D, P, P, P, P, I, P, P, P, I, I, P]),
                 "ccmg_or_force_gather_adjoint": (None, [P, I, I, I, D, P, P, I, P, P, P, I, P, P, P, P]),
-                "ccmg_or_var_coeffs": (None, [P, I, I, I, P, I, P, P, P, P]),
-                "ccmg_or_var_apply": (None, [P, P, P, I, I, I, D, P, I]),
+                "ccmg_or_var_coeffs": (None, [P, P, D, I, I, I, P, D, I, P, P, P, P]),
+                "ccmg_or_var_apply": (None, [P, P, P, P, I, I, I, D, P, D, I]),
                 "ccmg_or_var_rhs": (None, [P, P, P, I, I, I, D, P, P]),
-                "ccmg_or_var_vcycles": (None, [P, P, P, I, I, I, D, P, I, I, D, I]),
-                "ccmg_or_var_solve": (I, [P, P, P, I, I, I, D, P, I, I, D, D, I, P]),
-                "ccmg_or_var_rel_residual": (D, [P, P, P, I, I, I, D, P]),
+                "ccmg_or_var_vcycles": (None, [P, P, P, P, I, I, I, D, P, I, I, D, I]),
+                "ccmg_or_var_solve": (I, [P, P, P, P, I, I, I, D, P, I, I, D, D, I, P]),
+                "ccmg_or_var_rel_residual": (D, [P, P, P, P, I, I, I, D, P]),
+                "ccmg_or_pb_newton": (I, [P, P, P, P, I, I, I, D, P, I, I, D, D, I, D, I, P]),
+                "ccmg_or_pb_residual": (D, [P, P, P, P, I, I, I, D, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -424,25 +426,34 @@ def force_objective_and_grad(shape, h: float, bc_type, bc_value, centers, radius
 # --------------------------------------------------------------------------------------------
 # Variable permittivity (Sec. 3: Galerkin coarsening with averaging restriction and constant
 # prolongation extends the solver to discontinuous dielectricity; -div(eps grad phi) = rho, face
-# weights the harmonic mean of the two cells' permittivities)
+# weights the harmonic mean of the two cells' permittivities), with an optional reaction term
+# k2 phi (screened / linearised Poisson-Boltzmann operator; k2 >= 0 per cell, None: none). The
+# coarse levels carry the diffusion part divided by the correction factor omega (the coarse-grid
+# correction itself is not magnified) and the reaction part unmagnified.
 
-def var_coeffs(eps, bc_type, level: int = 0):
+def _k2(k2):
+    return None if k2 is None else _p(_f64(k2))
+
+
+def var_coeffs(eps, bc_type, level: int = 0, k2=None, h: float = 1.0, omega: float = 2.0):
     """Scaled weights (D, wx, wy, wz) of level `level` of the hierarchy of eps ([nz, ny, nx])."""
     eps = _f64(eps)
     nx, ny, nz = _dims(eps)
     d = levels(nx, ny, nz)[level]
-    shape = (d[2], d[1], d[0])
-    out = [np.empty(shape) for _ in range(4)]
-    _load().ccmg_or_var_coeffs(_p(eps), nx, ny, nz, _p(_bc(bc_type)), level, *[_p(a) for a in out])
+    out = [np.empty((d[2], d[1], d[0])) for _ in range(4)]
+    k2a = None if k2 is None else _f64(k2)
+    _load().ccmg_or_var_coeffs(_p(eps), None if k2a is None else _p(k2a), h, nx, ny, nz, _p(_bc(bc_type)), omega,
+                               level, *[_p(a) for a in out])
     return tuple(out)
 
 
-def var_apply(phi, eps, h: float, bc_type, level: int = 0) -> np.ndarray:
-    """A_l phi with the Galerkin operator of level `level` (phi of that level's shape)."""
-    eps = _f64(eps)
-    phi = _f64(phi)
+def var_apply(phi, eps, h: float, bc_type, level: int = 0, k2=None, omega: float = 2.0) -> np.ndarray:
+    """A_l phi with the coarse operator of level `level` (phi of that level's shape)."""
+    eps, phi = _f64(eps), _f64(phi)
+    k2a = None if k2 is None else _f64(k2)
     out = np.empty_like(phi)
-    _load().ccmg_or_var_apply(_p(phi), _p(out), _p(eps), *_dims(eps), h, _p(_bc(bc_type)), level)
+    _load().ccmg_or_var_apply(_p(phi), _p(out), _p(eps), None if k2a is None else _p(k2a), *_dims(eps), h,
+                              _p(_bc(bc_type)), omega, level)
     return out
 
 
@@ -454,24 +465,52 @@ def var_rhs(rho, eps, h: float, bc_type, bc_value) -> np.ndarray:
     return f
 
 
-def var_vcycles(phi, f, eps, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2, omega: float = 2.0):
+def var_vcycles(phi, f, eps, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2, omega: float = 2.0,
+                k2=None):
     phi = _f64(phi).copy()
     f, eps = _f64(f), _f64(eps)
-    _load().ccmg_or_var_vcycles(_p(phi), _p(f), _p(eps), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega, ncycles)
+    k2a = None if k2 is None else _f64(k2)
+    _load().ccmg_or_var_vcycles(_p(phi), _p(f), _p(eps), None if k2a is None else _p(k2a), *_dims(f), h,
+                                _p(_bc(bc_type)), nu1, nu2, omega, ncycles)
     return phi
 
 
 def var_solve(f, eps, h: float, bc_type, tol: float = 1e-10, max_cycles: int = 100, nu1: int = 2, nu2: int = 2,
-              omega: float = 2.0, phi0=None):
+              omega: float = 2.0, phi0=None, k2=None):
     """Algorithm 1 with the weighted operators. Returns (phi, cycles, relative residual)."""
     f, eps = _f64(f), _f64(eps)
+    k2a = None if k2 is None else _f64(k2)
     phi = np.zeros_like(f) if phi0 is None else _f64(phi0).copy()
     rel = ctypes.c_double()
-    k = _load().ccmg_or_var_solve(_p(phi), _p(f), _p(eps), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega, tol,
-                                  max_cycles, ctypes.byref(rel))
+    k = _load().ccmg_or_var_solve(_p(phi), _p(f), _p(eps), None if k2a is None else _p(k2a), *_dims(f), h,
+                                  _p(_bc(bc_type)), nu1, nu2, omega, tol, max_cycles, ctypes.byref(rel))
     return phi, k, rel.value
 
 
-def var_rel_residual(phi, f, eps, h: float, bc_type) -> float:
-    return _load().ccmg_or_var_rel_residual(_p(_f64(phi)), _p(_f64(f)), _p(_f64(eps)), *_dims(_f64(f)), h,
-                                            _p(_bc(bc_type)))
+def var_rel_residual(phi, f, eps, h: float, bc_type, k2=None) -> float:
+    k2a = None if k2 is None else _f64(k2)
+    return _load().ccmg_or_var_rel_residual(_p(_f64(phi)), _p(_f64(f)), _p(_f64(eps)),
+                                            None if k2a is None else _p(k2a), *_dims(_f64(f)), h, _p(_bc(bc_type)))
+
+
+# --------------------------------------------------------------------------------------------
+# Poisson-Boltzmann (the next application the paper names for the solver module):
+# -div(eps grad phi) + k2 sinh(phi) = rho by Newton's method
+
+def pb_newton(f, eps, k2, h: float, bc_type, tol: float = 1e-10, max_newton: int = 50, inner_tol: float = 1e-12,
+              max_cycles: int = 200, nu1: int = 2, nu2: int = 2, omega: float = 2.0, phi0=None):
+    """Newton's method for -div(eps grad phi) + k2 sinh(phi) = f. Returns (phi, steps, ||F||/||f||)."""
+    f, eps, k2 = _f64(f), _f64(eps), _f64(k2)
+    phi = np.zeros_like(f) if phi0 is None else _f64(phi0).copy()
+    rel = ctypes.c_double()
+    it = _load().ccmg_or_pb_newton(_p(phi), _p(f), _p(eps), _p(k2), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2,
+                                   omega, tol, max_newton, inner_tol, max_cycles, ctypes.byref(rel))
+    return phi, it, rel.value
+
+
+def pb_residual(phi, f, eps, k2, h: float, bc_type):
+    """(F, ||F||/||f||) with F = f - A_eps phi - k2 sinh(phi)."""
+    phi, f, eps, k2 = _f64(phi), _f64(f), _f64(eps), _f64(k2)
+    F = np.empty_like(phi)
+    r = _load().ccmg_or_pb_residual(_p(phi), _p(f), _p(eps), _p(k2), *_dims(f), h, _p(_bc(bc_type)), _p(F))
+    return F, r

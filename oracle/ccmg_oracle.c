@@ -854,6 +854,7 @@ void ccmg_or_force_gather_adjoint(const double* phi, int nx, int ny, int nz, dou
 typedef struct {
   int n[3];
   double *D, *wx, *wy, *wz;
+  double *Dw, *M; /* D = Dw + M: the diffusion part and the reaction (mass) part */
 } var_level;
 
 static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
@@ -865,6 +866,8 @@ static void var_alloc(var_level* V, const int* d) {
   V->wx = (double*)calloc(n, sizeof(double));
   V->wy = (double*)calloc(n, sizeof(double));
   V->wz = (double*)calloc(n, sizeof(double));
+  V->Dw = (double*)calloc(n, sizeof(double));
+  V->M = (double*)calloc(n, sizeof(double));
 }
 
 static void var_free(var_level* V) {
@@ -872,6 +875,8 @@ static void var_free(var_level* V) {
   free(V->wx);
   free(V->wy);
   free(V->wz);
+  free(V->Dw);
+  free(V->M);
 }
 
 /* Level-0 weights from the cell permittivities. */
@@ -915,17 +920,26 @@ static void var_fine(const double* eps, const int* bc, var_level* V) {
             D = D + 2.0 * e;
           }
         }
+        V->Dw[p] = D;
+        V->M[p] = 0.0;
         V->D[p] = D;
       }
 }
 
-/* Galerkin coarse weights (fine level F, coarse level C with half the dimensions). */
-static void var_coarsen(const var_level* F, var_level* C) {
+/* Coarse weights (fine level F, coarse level C with half the dimensions): the Galerkin product
+ * of the diffusion part divided by the correction factor omega, and that of the reaction part.
+ * The paper magnifies the coarse-grid correction of the Poisson operator by about two because
+ * the averaging restriction and constant prolongation are of too low order for a second-order
+ * operator; taking the factor into the coarse operator instead (A_c = R A_diff P / omega +
+ * R M P, correction weight 1) gives the same iterates for the Poisson operator (omega a power of
+ * two: bit for bit) and leaves the zeroth-order reaction term, which these transfers coarsen
+ * exactly, without magnification. */
+static void var_coarsen(const var_level* F, var_level* C, double omega) {
   const int nx = F->n[0], ny = F->n[1];
   for (int K = 0; K < C->n[2]; ++K)
     for (int J = 0; J < C->n[1]; ++J)
       for (int I = 0; I < C->n[0]; ++I) {
-        double sx = 0.0, sy = 0.0, sz = 0.0, sd = 0.0, inner = 0.0;
+        double sx = 0.0, sy = 0.0, sz = 0.0, sd = 0.0, sm = 0.0, inner = 0.0;
         for (int u = 0; u < 2; ++u)
           for (int v = 0; v < 2; ++v) {
             sx = sx + F->wx[idx3(2 * I, 2 * J + u, 2 * K + v, nx, ny)];
@@ -934,7 +948,10 @@ static void var_coarsen(const var_level* F, var_level* C) {
           }
         for (int dk = 0; dk < 2; ++dk)
           for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) sd = sd + F->D[idx3(2 * I + di, 2 * J + dj, 2 * K + dk, nx, ny)];
+            for (int di = 0; di < 2; ++di) {
+              sd = sd + F->Dw[idx3(2 * I + di, 2 * J + dj, 2 * K + dk, nx, ny)];
+              sm = sm + F->M[idx3(2 * I + di, 2 * J + dj, 2 * K + dk, nx, ny)];
+            }
         for (int u = 0; u < 2; ++u)
           for (int v = 0; v < 2; ++v) {
             inner = inner + F->wx[idx3(2 * I + 1, 2 * J + u, 2 * K + v, nx, ny)];
@@ -942,10 +959,12 @@ static void var_coarsen(const var_level* F, var_level* C) {
             inner = inner + F->wz[idx3(2 * I + u, 2 * J + v, 2 * K + 1, nx, ny)];
           }
         const size_t p = idx3(I, J, K, C->n[0], C->n[1]);
-        C->wx[p] = sx / 4.0;
-        C->wy[p] = sy / 4.0;
-        C->wz[p] = sz / 4.0;
-        C->D[p] = (sd - 2.0 * inner) / 4.0;
+        C->wx[p] = sx / 4.0 / omega;
+        C->wy[p] = sy / 4.0 / omega;
+        C->wz[p] = sz / 4.0 / omega;
+        C->Dw[p] = (sd - 2.0 * inner) / 4.0 / omega;
+        C->M[p] = sm / 4.0;
+        C->D[p] = C->Dw[p] + C->M[p];
       }
 }
 
@@ -1040,11 +1059,21 @@ typedef struct {
   var_level V[OR_MAX_LEVELS];
 } var_hierarchy;
 
-static void var_hier_init(var_hierarchy* G, const double* eps, int nx, int ny, int nz, const int* bc) {
+/* The weighted hierarchy of eps, with the reaction coefficient r (NULL: none) on level 0, coarse
+ * levels by var_coarsen with the correction factor omega. */
+static void var_hier_init_r(var_hierarchy* G, const double* eps, const double* r, double h, int nx, int ny, int nz,
+                            const int* bc, double omega) {
   hier_init(&G->H, nx, ny, nz, 0);
   for (int l = 0; l < G->H.L; ++l) var_alloc(&G->V[l], G->H.dims[l]);
   var_fine(eps, bc, &G->V[0]);
-  for (int l = 1; l < G->H.L; ++l) var_coarsen(&G->V[l - 1], &G->V[l]);
+  if (r) {
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t p = 0; p < n; ++p) {
+      G->V[0].M[p] = r[p] * (h * h);
+      G->V[0].D[p] = G->V[0].Dw[p] + G->V[0].M[p];
+    }
+  }
+  for (int l = 1; l < G->H.L; ++l) var_coarsen(&G->V[l - 1], &G->V[l], omega);
 }
 
 static void var_hier_free(var_hierarchy* G) {
@@ -1069,18 +1098,19 @@ static void var_vcycle(var_hierarchy* G, int l, double h, const int* bc, int nu1
   restrict_avg_d(H->r, H->f[l + 1], d[0], d[1], d[2]);
   memset(H->phi[l + 1], 0, ncells(H->dims[l + 1]) * sizeof(double));
   var_vcycle(G, l + 1, h, bc, nu1, nu2, omega);
-  prolong_correct_d(H->phi[l], H->phi[l + 1], d[0], d[1], d[2], omega);
+  prolong_correct_d(H->phi[l], H->phi[l + 1], d[0], d[1], d[2], 1.0); /* omega is in the coarse operator */
   for (int s = 0; s < nu2; ++s) {
     var_rbgs_half(H->phi[l], H->f[l], V, c, bc, 1);
     var_rbgs_half(H->phi[l], H->f[l], V, c, bc, 0);
   }
 }
 
-/* The scaled weights of level `level` (D, wx, wy, wz, each of that level's cell count). */
-void ccmg_or_var_coeffs(const double* eps, int nx, int ny, int nz, const int* bc, int level, double* D, double* wx,
-                        double* wy, double* wz) {
+/* The scaled weights of level `level` (D, wx, wy, wz, each of that level's cell count) of the
+ * hierarchy of eps with the reaction coefficient k2 (NULL: none) and correction factor omega. */
+void ccmg_or_var_coeffs(const double* eps, const double* k2, double h, int nx, int ny, int nz, const int* bc,
+                        double omega, int level, double* D, double* wx, double* wy, double* wz) {
   var_hierarchy G;
-  var_hier_init(&G, eps, nx, ny, nz, bc);
+  var_hier_init_r(&G, eps, k2, h, nx, ny, nz, bc, omega);
   const size_t n = ncells(G.H.dims[level]);
   memcpy(D, G.V[level].D, n * sizeof(double));
   memcpy(wx, G.V[level].wx, n * sizeof(double));
@@ -1089,18 +1119,18 @@ void ccmg_or_var_coeffs(const double* eps, int nx, int ny, int nz, const int* bc
   var_hier_free(&G);
 }
 
-/* out = A_l phi_l on level `level` of the hierarchy of eps (fine dimensions nx, ny, nz). */
-void ccmg_or_var_apply(const double* phi, double* out, const double* eps, int nx, int ny, int nz, double h,
-                       const int* bc, int level) {
+/* out = A_l phi_l on level `level` of that hierarchy (fine dimensions nx, ny, nz). */
+void ccmg_or_var_apply(const double* phi, double* out, const double* eps, const double* k2, int nx, int ny, int nz,
+                       double h, const int* bc, double omega, int level) {
   var_hierarchy G;
-  var_hier_init(&G, eps, nx, ny, nz, bc);
+  var_hier_init_r(&G, eps, k2, h, nx, ny, nz, bc, omega);
   var_apply(phi, out, &G.V[level], level_coeff(h, level), bc);
   var_hier_free(&G);
 }
 
-/* Right-hand side of -div(eps grad phi) = rho with the walls folded in once on the finest grid:
- * f = rho; Dirichlet face cells f += 2 eps g / h^2; Neumann face cells f += eps g / h (eps of the
- * boundary cell, the weight of its wall face); periodic faces add nothing. */
+/* Right-hand side of -div(eps grad phi) (+ reaction) = rho with the walls folded in once on the
+ * finest grid: f = rho; Dirichlet face cells f += 2 eps g / h^2; Neumann face cells f += eps g / h
+ * (eps of the boundary cell, the weight of its wall face); periodic faces add nothing. */
 void ccmg_or_var_rhs(const double* rho, const double* eps, double* f, int nx, int ny, int nz, double h, const int* bc,
                      const double* bcv) {
   for (int k = 0; k < nz; ++k)
@@ -1121,10 +1151,10 @@ void ccmg_or_var_rhs(const double* rho, const double* eps, double* f, int nx, in
 }
 
 /* ncycles V-cycles (as ccmg_or_vcycles) with the weighted operators. */
-void ccmg_or_var_vcycles(double* phi, const double* f, const double* eps, int nx, int ny, int nz, double h,
-                         const int* bc, int nu1, int nu2, double omega, int ncycles) {
+void ccmg_or_var_vcycles(double* phi, const double* f, const double* eps, const double* k2, int nx, int ny, int nz,
+                         double h, const int* bc, int nu1, int nu2, double omega, int ncycles) {
   var_hierarchy G;
-  var_hier_init(&G, eps, nx, ny, nz, bc);
+  var_hier_init_r(&G, eps, k2, h, nx, ny, nz, bc, omega);
   G.H.phi[0] = phi;
   G.H.f[0] = (double*)f;
   for (int k = 0; k < ncycles; ++k) var_vcycle(&G, 0, h, bc, nu1, nu2, omega);
@@ -1134,10 +1164,11 @@ void ccmg_or_var_vcycles(double* phi, const double* f, const double* eps, int nx
 }
 
 /* Algorithm 1 with the weighted operators; returns the cycle count. */
-int ccmg_or_var_solve(double* phi, const double* f, const double* eps, int nx, int ny, int nz, double h,
-                      const int* bc, int nu1, int nu2, double omega, double tol, int max_cycles, double* rel_res_out) {
+int ccmg_or_var_solve(double* phi, const double* f, const double* eps, const double* k2, int nx, int ny, int nz,
+                      double h, const int* bc, int nu1, int nu2, double omega, double tol, int max_cycles,
+                      double* rel_res_out) {
   var_hierarchy G;
-  var_hier_init(&G, eps, nx, ny, nz, bc);
+  var_hier_init_r(&G, eps, k2, h, nx, ny, nz, bc, omega);
   G.H.phi[0] = phi;
   G.H.f[0] = (double*)f;
   const size_t n = (size_t)nx * ny * nz;
@@ -1159,17 +1190,90 @@ int ccmg_or_var_solve(double* phi, const double* f, const double* eps, int nx, i
 }
 
 /* Relative residual ||f - A_0 phi|| / ||f|| with the weighted operator. */
-double ccmg_or_var_rel_residual(const double* phi, const double* f, const double* eps, int nx, int ny, int nz,
-                                double h, const int* bc) {
-  var_level V;
-  const int d[3] = {nx, ny, nz};
-  var_alloc(&V, d);
-  var_fine(eps, bc, &V);
+double ccmg_or_var_rel_residual(const double* phi, const double* f, const double* eps, const double* k2, int nx,
+                                int ny, int nz, double h, const int* bc) {
+  var_hierarchy G;
+  var_hier_init_r(&G, eps, k2, h, nx, ny, nz, bc, 2.0);
   const size_t n = (size_t)nx * ny * nz;
   double* r = (double*)malloc(n * sizeof(double));
-  var_residual(phi, f, r, &V, level_coeff(h, 0), bc);
+  var_residual(phi, f, r, &G.V[0], level_coeff(h, 0), bc);
   const double fn = norm2_d(f, n), rn = norm2_d(r, n);
   free(r);
-  var_free(&V);
+  var_hier_free(&G);
   return fn > 0.0 ? rn / fn : rn;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Screened and Poisson-Boltzmann operators (the paper names the Poisson-Boltzmann equation as
+ * the next application of the solver module, Sec. 9): with a reaction coefficient k2 >= 0 per
+ * cell (the squared inverse Debye length times the permittivity in the electrolyte, zero where
+ * ions are excluded) the equation is
+ *   -div(eps grad phi) + k2 phi = rho          (linear, Debye-Hueckel), or
+ *   -div(eps grad phi) + k2 sinh(phi) = rho    (nonlinear, symmetric 1:1 electrolyte, phi in
+ *                                                units of the thermal voltage).
+ * The reaction term is cell-local: it adds k2 h^2 to the scaled diagonal of level 0 (A_0 =
+ * c_0 (D phi - sum w phi) + k2 phi, c_0 = 1/h^2), and the Galerkin coarsening carries it to the
+ * coarse levels as part of D (R M P of a diagonal M is the diagonal of the children's means).
+ * The nonlinear equation is solved by Newton's method: F(phi) = f - A_eps phi - k2 sinh(phi);
+ * stop when ||F|| / ||f|| < tol; else solve (A_eps + k2 cosh(phi)) delta = F (homogeneous walls)
+ * to the inner tolerance with the multigrid of that linear operator, phi += delta. */
+
+/* F = f - A_eps phi - k2 sinh(phi) (the nonlinear residual); returns ||F||_2. */
+static double pb_residual(const double* phi, const double* f, const var_level* V0, const double* k2, double h,
+                          const int* bc, double* F) {
+  const size_t n = (size_t)V0->n[0] * V0->n[1] * V0->n[2];
+  var_residual(phi, f, F, V0, level_coeff(h, 0), bc);
+  for (size_t p = 0; p < n; ++p) F[p] = F[p] - k2[p] * sinh(phi[p]);
+  return norm2_d(F, n);
+}
+
+/* Newton's method for -div(eps grad phi) + k2 sinh(phi) = f (f with the wall terms, as from
+ * ccmg_or_var_rhs); phi is the start value and the result. Each step solves the linearised
+ * equation to inner_tol (relative) by V-cycles. Returns the number of Newton steps; the final
+ * ||F|| / ||f|| in rel_out. */
+int ccmg_or_pb_newton(double* phi, const double* f, const double* eps, const double* k2, int nx, int ny, int nz,
+                      double h, const int* bc, int nu1, int nu2, double omega, double tol, int max_newton,
+                      double inner_tol, int max_cycles, double* rel_out) {
+  const size_t n = (size_t)nx * ny * nz;
+  const int d[3] = {nx, ny, nz};
+  var_level V0;
+  var_alloc(&V0, d);
+  var_fine(eps, bc, &V0);
+  double* F = (double*)malloc(n * sizeof(double));
+  double* kl = (double*)malloc(n * sizeof(double));
+  double* delta = (double*)malloc(n * sizeof(double));
+  const double fn = norm2_d(f, n);
+  int it = 0;
+  double rel;
+  for (;;) {
+    const double Fn = pb_residual(phi, f, &V0, k2, h, bc, F);
+    rel = fn > 0.0 ? Fn / fn : Fn;
+    if (!(rel >= tol) || it >= max_newton) break;
+    for (size_t p = 0; p < n; ++p) {
+      kl[p] = k2[p] * cosh(phi[p]);
+      delta[p] = 0.0;
+    }
+    ccmg_or_var_solve(delta, F, eps, kl, nx, ny, nz, h, bc, nu1, nu2, omega, inner_tol, max_cycles, NULL);
+    for (size_t p = 0; p < n; ++p) phi[p] = phi[p] + delta[p];
+    ++it;
+  }
+  if (rel_out) *rel_out = rel;
+  free(F);
+  free(kl);
+  free(delta);
+  var_free(&V0);
+  return it;
+}
+
+/* The nonlinear residual F of phi (for checks), written to F_out; returns ||F|| / ||f||. */
+double ccmg_or_pb_residual(const double* phi, const double* f, const double* eps, const double* k2, int nx, int ny,
+                           int nz, double h, const int* bc, double* F_out) {
+  const int d[3] = {nx, ny, nz};
+  var_level V0;
+  var_alloc(&V0, d);
+  var_fine(eps, bc, &V0);
+  const double Fn = pb_residual(phi, f, &V0, k2, h, bc, F_out);
+  const double fn = norm2_d(f, (size_t)nx * ny * nz);
+  var_free(&V0);
+  return fn > 0.0 ? Fn / fn : Fn;
 }

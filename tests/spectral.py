@@ -48,8 +48,8 @@ def _axis_transform(lo: int, hi: int):
     raise ValueError((lo, hi))
 
 
-def solve(f: np.ndarray, h: float, bc_type) -> np.ndarray:
-    """Exact solution of A phi = f (homogeneous face BCs), f in [z, y, x] order."""
+def solve(f: np.ndarray, h: float, bc_type, shift: float = 0.0) -> np.ndarray:
+    """Exact solution of (A + shift) phi = f (homogeneous face BCs), f in [z, y, x] order."""
     nz, ny, nx = f.shape
     # array axis for x, y, z and the BC pair on that axis
     axes = [(2, nx, bc_type[0], bc_type[1]), (1, ny, bc_type[2], bc_type[3]),
@@ -67,6 +67,7 @@ def solve(f: np.ndarray, h: float, bc_type) -> np.ndarray:
         shape[ax] = n
         lam = lam + eig(n).reshape(shape) / (h * h)
         inv.append((ax, bwd, lo == P))
+    lam = lam + shift
     if np.any(lam == 0.0):
         raise ValueError("singular operator (no Dirichlet face)")
     g = g / lam

@@ -702,14 +702,14 @@ def test_periodic_faces_must_pair():
 # Variable permittivity (Sec. 3: Galerkin coarsening with averaging restriction and constant
 # prolongation extends the solver to discontinuous dielectricity): -div(eps grad phi) = rho
 
-def dense_var(eps, h, bc, level, dims):
+def dense_var(eps, h, bc, level, dims, k2=None):
     nx, ny, nz = dims
     n = nx * ny * nz
     A = np.zeros((n, n))
     for q in range(n):
         e = np.zeros(n)
         e[q] = 1.0
-        A[:, q] = oracle.var_apply(e.reshape(nz, ny, nx), eps, h, bc, level).ravel()
+        A[:, q] = oracle.var_apply(e.reshape(nz, ny, nx), eps, h, bc, level, k2=k2).ravel()
     return A
 
 
@@ -732,13 +732,15 @@ def test_var_constant_permittivity_is_the_constant_operator(bc):
     ref, k_ref, _ = oracle.solve(f / 2.5, 0.5, bc, tol=1e-13, max_cycles=100)
     assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-12 and k == k_ref
     Dw = oracle.var_coeffs(eps, bc, 1)
-    assert np.allclose(Dw[1:], 2.5, rtol=0, atol=1e-15)  # Galerkin keeps the scaled weights
+    assert np.all(np.stack(Dw[1:]) == 2.5 / 2.0)  # Galerkin weights, divided by the factor 2
 
 
 @pytest.mark.parametrize("bc", [(D, N, N, D, D, N), (PER, PER, D, D, N, D), (PER,) * 6])
 def test_var_galerkin_closed_form(bc):
-    """(1/8) P^T A_l P equals the level-(l+1) operator built from the coarsening formulas, for a
-    jumping permittivity (two levels)."""
+    """(1/8) P^T A_l P / omega equals the level-(l+1) operator built from the coarsening formulas
+    for a jumping permittivity (two levels; the correction factor omega = 2 sits in the coarse
+    diffusion operator); with a reaction term, the coarse reaction is the Galerkin product alone:
+    A_{l+1} = R A_diff P / omega + R M P."""
     fine = (12, 12, 12)
     eps = _jumping_eps(fine, 4)
     h = 0.5
@@ -746,10 +748,16 @@ def test_var_galerkin_closed_form(bc):
     assert np.abs(A0 - A0.T).max() <= 1e-12 * np.abs(A0).max()
     Pm = injection(fine)
     A1 = dense_var(eps, h, bc, 1, (6, 6, 6))
-    assert np.abs((Pm.T / 8.0) @ A0 @ Pm - A1).max() <= 1e-13 * np.abs(A1).max()
+    assert np.abs((Pm.T / 8.0) @ A0 @ Pm / 2.0 - A1).max() <= 1e-13 * np.abs(A1).max()
     P2 = injection((6, 6, 6))
     A2 = dense_var(eps, h, bc, 2, (3, 3, 3))
-    assert np.abs((P2.T / 8.0) @ A1 @ P2 - A2).max() <= 1e-13 * np.abs(A2).max()
+    assert np.abs((P2.T / 8.0) @ A1 @ P2 / 2.0 - A2).max() <= 1e-13 * np.abs(A2).max()
+    k2 = np.random.default_rng(6).random(eps.shape) * 3.0
+    M0 = np.diag(k2.ravel())
+    A1r = dense_var(eps, h, bc, 1, (6, 6, 6), k2=k2)
+    ref = (Pm.T / 8.0) @ A0 @ Pm / 2.0 + (Pm.T / 8.0) @ M0 @ Pm
+    assert np.abs(dense_var(eps, h, bc, 0, fine, k2=k2) - (A0 + M0)).max() <= 1e-13 * np.abs(A0).max()
+    assert np.abs(A1r - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
 def test_var_dense_direct_solve():
@@ -786,3 +794,97 @@ def test_var_layered_dielectric_between_plates(h):
     assert np.abs(phi - exact[:, None, None]).max() < 1e-12 * V
     # the arithmetic mean at the interface would not reproduce it
     assert abs((phi[nz // 2] - phi[nz // 2 - 1]).max() - q * h * (1 / e1 + 1 / e2) / 2) < 1e-12
+
+
+
+# ------------------------------------------------------------------------------------------
+# Screened and Poisson-Boltzmann operators (the next application the paper names for the solver
+# module): -div(eps grad phi) + k2 phi = rho and -div(eps grad phi) + k2 sinh(phi) = rho
+
+@pytest.mark.parametrize("bc", [(PER, PER, N, N, D, D), (D,) * 6, (N, D, PER, PER, D, N)])
+@pytest.mark.parametrize("kk", [0.05, 3.0])
+def test_screened_spectral(bc, kk):
+    """Constant eps and k2: the exact discrete solution by the sine/cosine/Fourier diagonalisation
+    with every eigenvalue shifted by k2 h^2."""
+    dims = (16, 12, 20)
+    nx, ny, nz = dims
+    f = synth.random_field(dims, 7)
+    eps = np.full((nz, ny, nx), 1.0)
+    k2 = np.full((nz, ny, nx), kk)
+    phi, k, rel = oracle.var_solve(f, eps, 0.5, bc, tol=1e-13, max_cycles=100, k2=k2)
+    ex = spectral.solve(f, 0.5, bc, shift=kk)
+    assert np.linalg.norm(phi - ex) / np.linalg.norm(ex) < 1e-11 and k < 20
+
+
+def _pb_residual_numpy(phi, f, h, bc, k2):
+    """F = f - (-lap_h phi with the homogeneous-wall ghosts folded in) - k2 sinh(phi) for eps = 1,
+    written independently of the oracle (ghost cells by padding)."""
+    p = np.pad(phi, 1)
+    for ax, q in ((2, 0), (1, 2), (0, 4)):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        src_lo = [slice(None)] * 3
+        src_hi = [slice(None)] * 3
+        lo[ax], hi[ax], src_lo[ax], src_hi[ax] = 0, -1, 1, -2
+        if bc[q] == PER:
+            src_lo[ax], src_hi[ax] = -2, 1
+            p[tuple(lo)] = p[tuple(src_lo)]
+            p[tuple(hi)] = p[tuple(src_hi)]
+        else:
+            sgn_lo = -1.0 if bc[q] == D else 1.0
+            sgn_hi = -1.0 if bc[q + 1] == D else 1.0
+            p[tuple(lo)] = sgn_lo * p[tuple(src_lo)]
+            p[tuple(hi)] = sgn_hi * p[tuple(src_hi)]
+    c = p[1:-1, 1:-1, 1:-1]
+    lap = (p[1:-1, 1:-1, :-2] + p[1:-1, 1:-1, 2:] + p[1:-1, :-2, 1:-1] + p[1:-1, 2:, 1:-1] + p[:-2, 1:-1, 1:-1]
+           + p[2:, 1:-1, 1:-1] - 6 * c) / h ** 2
+    return f + lap - k2 * np.sinh(phi)
+
+
+def test_pb_newton_satisfies_the_discrete_equation():
+    """Newton's result satisfies -lap phi + k2 sinh(phi) = f (homogeneous walls, eps = 1) by an
+    independent numpy evaluation, converges quadratically, and differs from the linearised
+    (Debye-Hueckel) solution at large potential but agrees with it at small potential to O(phi^3)."""
+    dims = (16, 12, 20)
+    nx, ny, nz = dims
+    bc = (PER, PER, N, N, D, D)
+    eps = np.ones((nz, ny, nx))
+    k2 = np.full((nz, ny, nx), 0.5)
+    rho = synth.random_field(dims, 3) * 4.0
+    f = oracle.var_rhs(rho, eps, 1.0, bc, (0.0,) * 6)
+    phi, it, rel = oracle.pb_newton(f, eps, k2, 1.0, bc, tol=1e-12)
+    F = _pb_residual_numpy(phi, f, 1.0, bc, k2)
+    assert np.linalg.norm(F) / np.linalg.norm(f) < 1e-11 and it <= 8
+    assert np.abs(phi).max() > 1.0  # nonlinear regime
+    lin, _, _ = oracle.var_solve(f, eps, 1.0, bc, tol=1e-13, k2=k2)
+    assert np.abs(phi - lin).max() > 0.05 * np.abs(lin).max()
+    small = f * 1e-3
+    phs, _, _ = oracle.pb_newton(small, eps, k2, 1.0, bc, tol=1e-13)
+    lns, _, _ = oracle.var_solve(small, eps, 1.0, bc, tol=1e-14, k2=k2)
+    assert np.abs(phs - lns).max() < 1e-5 * np.abs(lns).max()
+    # quadratic convergence: residual after step n+1 <= C * (after step n)^2
+    rels = [oracle.pb_newton(f, eps, k2, 1.0, bc, tol=0.0, max_newton=n)[2] for n in range(1, 5)]
+    assert rels[2] < 10 * rels[1] ** 2 * 1e0 + 1e-14 and rels[1] < rels[0]
+
+
+def test_pb_gouy_chapman_second_order():
+    """A charged wall at potential phi0 in a 1:1 electrolyte (planar double layer): the continuum
+    solution tanh(phi/4) = tanh(phi0/4) exp(-kappa z) (Gouy-Chapman); with the far wall at its
+    exact value the discrete Newton solution converges to it at second order in h."""
+    phi0, kappa, Lz = 2.0, 1.0, 12.0
+
+    def gc(z):
+        return 4.0 * np.arctanh(np.tanh(phi0 / 4.0) * np.exp(-kappa * z))
+
+    errs = []
+    for nz in (48, 96, 192):
+        h = Lz / nz
+        nx, ny = 4, 4
+        bc = (PER, PER, PER, PER, D, D)
+        eps = np.ones((nz, ny, nx))
+        k2 = np.full((nz, ny, nx), kappa ** 2)
+        f = oracle.var_rhs(np.zeros((nz, ny, nx)), eps, h, bc, (0.0, 0.0, 0.0, 0.0, phi0, gc(Lz)))
+        phi, it, rel = oracle.pb_newton(f, eps, k2, h, bc, tol=1e-12)
+        z = (np.arange(nz) + 0.5) * h
+        errs.append(np.abs(phi[:, 0, 0] - gc(z)).max())
+    assert errs[0] < 2e-2 and 3.0 < errs[0] / errs[1] < errs[1] / errs[2] < 4.2  # the rate approaches 4
