@@ -114,8 +114,36 @@ mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
  * (FP64 only), MG_ERR_OOM if the coefficients (5 doubles per cell and level) cannot be allocated.
  * mg_rhs_adjoint refuses a context with a variable permittivity (its adjoint differs). */
 mg_status mg_set_permittivity(mg_ctx* ctx, const double* d_eps);
-/* 1 if a variable permittivity is set, 0 otherwise (and for a NULL context). */
+/* 1 if the weighted operator is active (a variable permittivity or a reaction term is set), 0
+ * otherwise (and for a NULL context). */
 int mg_has_permittivity(const mg_ctx* ctx);
+
+/* Reaction term (the Poisson-Boltzmann equation, which the paper names as the next application
+ * of the solver module): d_k2 (device, nx*ny*nz doubles, natural order, >= 0; not checked) gives
+ * per cell k2 (the permittivity over the squared Debye length in the electrolyte, 0 where ions
+ * are excluded). The operator becomes -div(eps grad phi) + k2 phi (screened, linearised
+ * Poisson-Boltzmann / Debye-Hueckel), with the permittivities of mg_set_permittivity or the
+ * constant eps; the reaction term adds k2 h^2 to the level-0 diagonal and is carried to the coarse
+ * levels by its Galerkin product, while the diffusion part of every coarse operator carries the
+ * coarse-grid correction factor (1/cgc_weight times its Galerkin product, the correction itself
+ * unmagnified: the same iterates for the Poisson operator, no overshoot of the reaction part).
+ * The array is copied and the coefficients built before the call returns. NULL removes the term.
+ * MG_ERR_INVALID in MG_MIXED mode, MG_ERR_OOM if the buffers cannot be allocated. */
+mg_status mg_set_reaction(mg_ctx* ctx, const double* d_k2);
+int mg_has_reaction(const mg_ctx* ctx);
+
+/* Nonlinear Poisson-Boltzmann equation -div(eps grad phi) + k2 sinh(phi) = f for a symmetric 1:1
+ * electrolyte (phi in units of the thermal voltage), k2 from mg_set_reaction, f from mg_set_rhs
+ * (rho with the wall terms), by Newton's method from the current solution: F = f - A_eps phi -
+ * k2 sinh(phi); stop when ||F||_2 / ||f||_2 < rel_tol or after max_newton steps; else solve
+ * (A_eps + k2 cosh(phi)) delta = F with homogeneous walls by V-cycles to inner_tol (at most
+ * max_cycles; an inexact step is kept), phi += delta. Writes the step count and the final
+ * ||F|| / ||f|| (either pointer may be NULL); the potential is the context's solution afterwards,
+ * and the weighted operator holds the last linearisation (mg_set_reaction restores the linear
+ * one). Returns MG_ERR_NOT_CONVERGED if the tolerance is not reached, MG_ERR_INVALID without a
+ * reaction term or with negative arguments. Synchronises. */
+mg_status mg_solve_pb(mg_ctx* ctx, double rel_tol, int max_newton, double inner_tol, int max_cycles, int* h_newton,
+                      double* h_rel_res);
 
 /* Right-hand side from a charge density: f = rho/eps, then adapted to the wall values once
  * on the finest grid (Sec. 2.4 and Sec. 5.3: Dirichlet face cells += 2 g / h^2, Neumann face

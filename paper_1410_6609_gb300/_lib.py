@@ -84,6 +84,9 @@ SIGNATURES = {
     "mg_selftest_wait_timeout": (_I, [_P, _I]),
     "mg_set_permittivity": (_I, [_P, _P]),
     "mg_has_permittivity": (_I, [_P]),
+    "mg_set_reaction": (_I, [_P, _P]),
+    "mg_has_reaction": (_I, [_P]),
+    "mg_solve_pb": (_I, [_P, _D, _I, _D, _I, _P, _P]),
     "mg_residual_norm_static": (_I, [_I, _I, _I, _D, _P, _P, _P, _P, _P]),
     "mg_batch_create": (_I, [_I, _P, _P, _P]),
     "mg_batch_destroy": (_I, [_P]),

@@ -19,7 +19,7 @@ using namespace ccmg;
 
 namespace {
 
-enum Slot { S_GSUM = 0, S_RSUM = 1, S_REL = 2, S_SCALE = 3, S_INV_SCALE = 4, S_COUNT = 8 };
+enum Slot { S_GSUM = 0, S_RSUM = 1, S_REL = 2, S_SCALE = 3, S_INV_SCALE = 4, S_PB_REF = 5, S_PB_REL = 6, S_COUNT = 8 };
 
 thread_local std::string g_create_error;
 
@@ -57,8 +57,11 @@ struct mg_ctx {
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
   double* d_bcf[6] = {};       // per-cell wall values of each face (allocated on first use)
-  double* d_eps = nullptr;     // variable permittivity (cell values), or null: the constant eps
-  double* vc[kMaxLevels]{};    // its coefficients per level (D, wx, wy, wz, 1/D)
+  double* d_eps = nullptr;     // weighted operator: cell permittivities (null: the constant operator)
+  bool eps_set = false;        // d_eps came from mg_set_permittivity (else the constant eps)
+  double* d_k2 = nullptr;      // reaction coefficients (screened / Poisson-Boltzmann), or null
+  double* vc[kMaxLevels]{};    // weighted coefficients per level (D, wx, wy, wz, 1/D, Dw, M)
+  double* d_pb = nullptr;      // Newton state: base right-hand side and potential (2 finest fields)
   std::string err;
 };
 
@@ -97,6 +100,8 @@ void free_all(mg_ctx* c) {
   }
   for (int q = 0; q < 6; ++q) cudaFree(c->d_bcf[q]);
   cudaFree(c->d_eps);
+  cudaFree(c->d_k2);
+  cudaFree(c->d_pb);
   for (int l = 0; l < kMaxLevels; ++l) cudaFree(c->vc[l]);
   cudaFree(c->partials);
   cudaFree(c->scal);
@@ -143,8 +148,8 @@ cudaError_t enqueue_vcycle_var(mg_ctx* c, int l, bool zero, cudaStream_t s, long
   if ((e = launch_var_resid_restrict(x, g, c->vc[l], G, c->g64[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
   ++*nk;
   if ((e = enqueue_vcycle_var(c, l + 1, true, s, nk)) != cudaSuccess) return e;
-  if ((e = launch_prolong<double>(x, G, c->x64[l + 1], c->geo[l + 1], c->p.cgc_weight, c->p.nu2 >= 1, s)) !=
-      cudaSuccess)
+  // the correction factor is in the coarse operators (var_kernels.cu): weight 1 here
+  if ((e = launch_prolong<double>(x, G, c->x64[l + 1], c->geo[l + 1], 1.0, c->p.nu2 >= 1, s)) != cudaSuccess)
     return e;
   ++*nk;
   for (int it = 0; it < c->p.nu2; ++it) {
@@ -589,53 +594,171 @@ static mg_status set_rhs_impl(mg_ctx* c, const double* d_rho, int raw) {
   return MG_OK;
 }
 
-mg_status mg_set_permittivity(mg_ctx* c, const double* d_eps) {
-  if (!c) return MG_ERR_INVALID;
-  if (d_eps && mixed(c)) return fail(c, MG_ERR_INVALID, "a variable permittivity needs MG_FP64");
-  // the cycle and residual graphs hold the operator's kernels: capture them again
+}  // extern "C"
+
+namespace {
+
+// The cycle and residual graphs hold the operator's kernels: drop them to be captured again.
+void drop_graphs(mg_ctx* c) {
   for (cudaGraphExec_t* gx : {&c->g_cycle, &c->g_cycle0, &c->g_resid, &c->g_resid0})
     if (*gx) {
       cudaGraphExecDestroy(*gx);
       *gx = nullptr;
     }
-  if (!d_eps) {
-    CK(cudaStreamSynchronize(c->stream), "permittivity");
+}
+
+// Buffers of the weighted operator (permittivities and coefficients of every level); a new
+// permittivity array is filled with the constant eps of the parameters when `fill`.
+mg_status var_alloc(mg_ctx* c, bool fill) {
+  if (c->d_eps) return MG_OK;
+  const Geom& G = c->geo[0];
+  const size_t n = (size_t)G.nx * G.ny * G.nz;
+  bool ok = cudaMalloc((void**)&c->d_eps, n * sizeof(double)) == cudaSuccess;
+  for (int l = 0; l < c->L && ok; ++l)
+    ok = cudaMalloc((void**)&c->vc[l], (size_t)var_arrays() * cells(c->geo[l]) * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
     cudaFree(c->d_eps);
     c->d_eps = nullptr;
     for (int l = 0; l < c->L; ++l) {
       cudaFree(c->vc[l]);
       c->vc[l] = nullptr;
     }
-    return MG_OK;
+    return fail(c, MG_ERR_OOM, "weighted operator");
   }
+  if (fill) CK(launch_fill(c->d_eps, c->p.eps, (long long)n, c->stream), "permittivity");
+  return MG_OK;
+}
+
+void var_release(mg_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_eps);
+  c->d_eps = nullptr;
+  for (int l = 0; l < c->L; ++l) {
+    cudaFree(c->vc[l]);
+    c->vc[l] = nullptr;
+  }
+}
+
+// The coefficients of every level from the permittivities and the reaction coefficients.
+mg_status var_rebuild(mg_ctx* c) {
+  CK(launch_var_setup(c->d_eps, c->d_k2, c->p.h, c->p.cgc_weight, c->geo, c->L, c->bc, c->vc, c->stream),
+     "weighted coefficients");
+  c->launches += c->L;
+  CK(cudaStreamSynchronize(c->stream), "weighted coefficients");
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_set_permittivity(mg_ctx* c, const double* d_eps) {
+  if (!c) return MG_ERR_INVALID;
+  if (d_eps && mixed(c)) return fail(c, MG_ERR_INVALID, "a variable permittivity needs MG_FP64");
+  drop_graphs(c);
+  mg_status st;
+  c->eps_set = d_eps != nullptr;
+  if (!d_eps) {
+    if (!c->d_k2) {
+      var_release(c);
+      return MG_OK;
+    }
+    // the reaction term stays: the weighted operator with the constant permittivity
+    CK(launch_fill(c->d_eps, c->p.eps, (long long)c->geo[0].nx * c->geo[0].ny * c->geo[0].nz, c->stream),
+       "permittivity");
+    return var_rebuild(c);
+  }
+  if ((st = var_alloc(c, false)) != MG_OK) return st;
   const Geom& G = c->geo[0];
   const size_t n = (size_t)G.nx * G.ny * G.nz;
-  if (!c->d_eps) {
-    if (cudaMalloc((void**)&c->d_eps, n * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      c->d_eps = nullptr;
-      return fail(c, MG_ERR_OOM, "permittivity");
-    }
-    for (int l = 0; l < c->L; ++l)
-      if (cudaMalloc((void**)&c->vc[l], 5 * (size_t)cells(c->geo[l]) * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        for (int q = 0; q <= l; ++q) {
-          cudaFree(c->vc[q]);
-          c->vc[q] = nullptr;
-        }
-        cudaFree(c->d_eps);
-        c->d_eps = nullptr;
-        return fail(c, MG_ERR_OOM, "permittivity coefficients");
-      }
-  }
   CK(cudaMemcpyAsync(c->d_eps, d_eps, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "permittivity");
-  CK(launch_var_setup(c->d_eps, c->geo, c->L, c->bc, c->vc, c->stream), "permittivity coefficients");
-  c->launches += c->L;
-  CK(cudaStreamSynchronize(c->stream), "permittivity");
+  return var_rebuild(c);
+}
+
+mg_status mg_set_reaction(mg_ctx* c, const double* d_k2) {
+  if (!c) return MG_ERR_INVALID;
+  if (d_k2 && mixed(c)) return fail(c, MG_ERR_INVALID, "a reaction term needs MG_FP64");
+  drop_graphs(c);
+  const Geom& G = c->geo[0];
+  const size_t n = (size_t)G.nx * G.ny * G.nz;
+  if (!d_k2) {
+    CK(cudaStreamSynchronize(c->stream), "reaction");
+    cudaFree(c->d_k2);
+    c->d_k2 = nullptr;
+    if (c->d_eps && !c->eps_set) var_release(c);  // the constant operator again
+    return c->d_eps ? var_rebuild(c) : MG_OK;
+  }
+  mg_status st = var_alloc(c, true);
+  if (st != MG_OK) return st;
+  if (!c->d_k2 && cudaMalloc((void**)&c->d_k2, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_k2 = nullptr;
+    return fail(c, MG_ERR_OOM, "reaction");
+  }
+  CK(cudaMemcpyAsync(c->d_k2, d_k2, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "reaction");
+  return var_rebuild(c);
+}
+
+mg_status mg_solve_pb(mg_ctx* c, double tol, int max_newton, double inner_tol, int max_cycles, int* h_newton,
+                      double* h_rel) {
+  if (!c) return MG_ERR_INVALID;
+  if (!c->d_k2) return fail(c, MG_ERR_INVALID, "no reaction coefficients (mg_set_reaction)");
+  if (!(tol >= 0.0) || !(inner_tol >= 0.0) || max_newton < 0 || max_cycles < 0)
+    return fail(c, MG_ERR_INVALID, "need tolerances >= 0 and counts >= 0");
+  mg_status st = ensure_graphs(c);
+  if (st != MG_OK) return st;
+  const Geom& G = c->geo[0];
+  const long long n = cells(G);
+  if (!c->d_pb && cudaMalloc((void**)&c->d_pb, 2 * (size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_pb = nullptr;
+    return fail(c, MG_ERR_OOM, "Newton state");
+  }
+  double* g0 = c->d_pb;
+  double* phi = c->d_pb + n;
+  if ((st = materialize(c)) != MG_OK) return st;
+  CK(cudaMemcpyAsync(g0, c->g64[0], n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "Newton");
+  CK(cudaMemcpyAsync(phi, c->x64[0], n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "Newton");
+  int np = 0;
+  CK(launch_sumsq<double>(g0, n, c->partials, &np, c->stream), "Newton");
+  CK(launch_finalize(c->partials, np, c->scal, S_PB_REF, -1, 0, c->stream), "Newton");
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    // F = f - A_eps phi - k2 sinh(phi) into the right-hand side, and the linearised diagonal
+    CK(launch_pb_update(phi, g0, c->vc[0], G, c->d_k2, c->p.h, c->g64[0], c->partials, &np, c->stream), "Newton");
+    CK(launch_finalize(c->partials, np, c->scal, S_GSUM, S_PB_REL, S_PB_REF, c->stream), "Newton");
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->h_pin, c->scal + S_PB_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "Newton");
+    CK(cudaStreamSynchronize(c->stream), "Newton");
+    rel = c->h_pin[0];
+    if (!(rel >= tol) || it >= max_newton) break;
+    // (A_eps + k2 cosh(phi)) delta = F with homogeneous walls, from delta = 0
+    CK(launch_var_coarsen_all(c->geo, c->L, c->vc, c->p.cgc_weight, c->stream), "Newton");
+    c->launches += c->L - 1;
+    CK(cudaMemsetAsync(c->x64[0], 0, n * sizeof(double), c->stream), "Newton");
+    c->phi_zero = true;
+    st = mg_solve(c, inner_tol, max_cycles, nullptr, nullptr);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;  // an inexact step is still a step
+    CK(launch_axpy(phi, c->x64[0], n, c->stream), "Newton");
+    c->launches += 1;
+    ++it;
+  }
+  // the potential into the iterate; the right-hand side back to f
+  CK(cudaMemcpyAsync(c->x64[0], phi, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "Newton");
+  CK(cudaMemcpyAsync(c->g64[0], g0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "Newton");
+  CK(cudaStreamSynchronize(c->stream), "Newton");
+  c->phi_zero = false;
+  if (h_newton) *h_newton = it;
+  if (h_rel) *h_rel = rel;
+  if (!std::isfinite(rel)) return fail(c, MG_ERR_NOT_CONVERGED, "Newton residual is not finite");
+  if (rel >= tol) return fail(c, MG_ERR_NOT_CONVERGED, "Newton did not reach the tolerance");
   return MG_OK;
 }
 
 int mg_has_permittivity(const mg_ctx* c) { return c && c->d_eps ? 1 : 0; }
+int mg_has_reaction(const mg_ctx* c) { return c && c->d_k2 ? 1 : 0; }
 
 mg_status mg_set_rhs(mg_ctx* c, const double* d_rho) { return set_rhs_impl(c, d_rho, 0); }
 mg_status mg_set_rhs_f(mg_ctx* c, const double* d_f) { return set_rhs_impl(c, d_f, 1); }

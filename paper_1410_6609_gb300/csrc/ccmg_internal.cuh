@@ -96,11 +96,17 @@ __device__ __forceinline__ double face_value(const FaceBC& bc, int q, int i, int
   return f ? __ldg(f + face_index(q, i, j, k, nx, ny)) : bc.value[q];
 }
 
-// Variable permittivity (var_kernels.cu): five coefficient arrays per level (D, wx, wy, wz, 1/D,
-// each of the level's cell count, in its storage order) at vc[l].
+// Variable permittivity and reaction term (var_kernels.cu): var_arrays() coefficient arrays per
+// level (D, wx, wy, wz, 1/D, Dw, M, each of the level's cell count, in its storage order) at vc[l].
 long long var_cells(const Geom& G);
-cudaError_t launch_var_setup(const double* eps, const Geom* geo, int L, const FaceBC& bc, double* const* vc,
-                             cudaStream_t s);
+int var_arrays();
+cudaError_t launch_var_setup(const double* eps, const double* react, double h, double omega, const Geom* geo, int L,
+                             const FaceBC& bc, double* const* vc, cudaStream_t s);
+cudaError_t launch_var_coarsen_all(const Geom* geo, int L, double* const* vc, double omega, cudaStream_t s);
+cudaError_t launch_pb_update(const double* x, const double* g0, double* vc, const Geom& G, const double* k2, double h,
+                             double* f, double* partials, int* nparts, cudaStream_t s);
+cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s);
+cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s);
 cudaError_t launch_var_smooth(double* x, const double* g, const double* vc, const Geom& G, int colour, bool zero,
                               cudaStream_t s);
 cudaError_t launch_var_resid_restrict(const double* x, const double* g, const double* vc, const Geom& G, double* gc,

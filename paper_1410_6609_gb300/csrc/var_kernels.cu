@@ -14,9 +14,17 @@
 // R = P^T / 8, keeps this form:
 //   w_{l+1}(coarse face) = (1/4) (sum of the 4 fine face weights on it),
 //   D_{l+1}(I) = (1/4) (sum of the 8 children's D - 2 (sum of the 12 faces inside I)).
+// A reaction term k2 phi (screened and Poisson-Boltzmann operators) adds M = k2 h^2 to the
+// level-0 diagonal; the coarse levels carry the diffusion part divided by the coarse-grid
+// correction factor omega (the factor of Sec. 3 taken into the operator, so the correction
+// itself is not magnified: the same iterates for the Poisson operator) and the reaction part,
+// which these transfers coarsen exactly, as its plain Galerkin product (1/4) (sum of the 8
+// children's M). D = Dw + M is kept with its parts Dw and M.
 // The setup kernels evaluate these in the oracle's order with rounded operations, so the
 // coefficients agree bit for bit; the cycle kernels are the FP64 cell-by-cell forms of the
 // smoother, the fused residual and restriction, the residual norm and the coarse CG.
+#include <algorithm>
+
 #include "ccmg_internal.cuh"
 #include "level_ops.cuh"
 
@@ -28,18 +36,21 @@ using ops::coarse_index;
 using ops::nb_has;
 using ops::nb_off;
 
-// The coefficient arrays of a level at vc: D, wx, wy, wz and 1/D, each of `n` entries (the
-// smoother multiplies by the stored reciprocal: FP64 division is many times slower than a
+// The coefficient arrays of a level at vc: D, wx, wy, wz, 1/D, Dw and M, each of `n` entries
+// (the smoother multiplies by the stored reciprocal: FP64 division is many times slower than a
 // multiply on this GPU, and the half-sweep would be bound by it).
+constexpr int kVarArrays = 7;
 struct VarCoef {
   const double* D;
   const double* wx;
   const double* wy;
   const double* wz;
   const double* invD;
+  const double* Dw;
+  const double* M;
 };
 __device__ __forceinline__ VarCoef var_coef(const double* vc, long long n) {
-  return VarCoef{vc, vc + n, vc + 2 * n, vc + 3 * n, vc + 4 * n};
+  return VarCoef{vc, vc + n, vc + 2 * n, vc + 3 * n, vc + 4 * n, vc + 5 * n, vc + 6 * n};
 }
 
 __device__ __forceinline__ double harmonic(double a, double b) { return __ddiv_rn(__dmul_rn(2.0 * a, b), a + b); }
@@ -48,9 +59,10 @@ __device__ __forceinline__ long long natural(const Geom& G, int i, int j, int k)
   return (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
 }
 
-// Level-0 coefficients from the cell permittivities eps (natural order).
-__global__ void __launch_bounds__(256) k_var_fine(const double* __restrict__ eps, Geom G, FaceBC bc,
-                                                  double* __restrict__ vc, long long n) {
+// Level-0 coefficients from the cell permittivities eps and the reaction coefficients react
+// (natural order; react null: none).
+__global__ void __launch_bounds__(256) k_var_fine(const double* __restrict__ eps, const double* __restrict__ react,
+                                                  double h2, Geom G, FaceBC bc, double* __restrict__ vc, long long n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -83,23 +95,28 @@ __global__ void __launch_bounds__(256) k_var_fine(const double* __restrict__ eps
     }
   }
   const long long o = coarse_index(G, i, j, k);
-  vc[o] = D;
+  const double M = react ? __dmul_rn(__ldg(react + natural(G, i, j, k)), h2) : 0.0;
+  const double Dt = __dadd_rn(D, M);
+  vc[o] = Dt;
   vc[n + o] = w[0];
   vc[2 * n + o] = w[1];
   vc[3 * n + o] = w[2];
-  vc[4 * n + o] = __ddiv_rn(1.0, D);
+  vc[4 * n + o] = __ddiv_rn(1.0, Dt);
+  vc[5 * n + o] = D;
+  vc[6 * n + o] = M;
 }
 
-// Galerkin coefficients of coarse level Gc from fine level Gf (the oracle's summation order).
+// Coefficients of coarse level Gc from fine level Gf (the oracle's summation order): the Galerkin
+// product of the diffusion part divided by omega, that of the reaction part as it is.
 __global__ void __launch_bounds__(256) k_var_coarsen(const double* __restrict__ vf, Geom Gf, long long nf,
-                                                     double* __restrict__ vcc, Geom Gc, long long nc) {
+                                                     double* __restrict__ vcc, Geom Gc, long long nc, double omega) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= Gc.nx || J >= Gc.ny) return;
   const VarCoef F = var_coef(vf, nf);
   auto at = [&](const double* a, int i, int j, int k) { return __ldg(a + coarse_index(Gf, i, j, k)); };
-  double sx = 0.0, sy = 0.0, sz = 0.0, sd = 0.0, inner = 0.0;
+  double sx = 0.0, sy = 0.0, sz = 0.0, sd = 0.0, sm = 0.0, inner = 0.0;
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -113,7 +130,10 @@ __global__ void __launch_bounds__(256) k_var_coarsen(const double* __restrict__ 
 #pragma unroll
     for (int dj = 0; dj < 2; ++dj)
 #pragma unroll
-      for (int di = 0; di < 2; ++di) sd = __dadd_rn(sd, at(F.D, 2 * I + di, 2 * J + dj, 2 * K + dk));
+      for (int di = 0; di < 2; ++di) {
+        sd = __dadd_rn(sd, at(F.Dw, 2 * I + di, 2 * J + dj, 2 * K + dk));
+        sm = __dadd_rn(sm, at(F.M, 2 * I + di, 2 * J + dj, 2 * K + dk));
+      }
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -123,13 +143,18 @@ __global__ void __launch_bounds__(256) k_var_coarsen(const double* __restrict__ 
       inner = __dadd_rn(inner, at(F.wz, 2 * I + u, 2 * J + v, 2 * K + 1));
     }
   const long long o = coarse_index(Gc, I, J, K);
-  const double Dc = __ddiv_rn(__dsub_rn(sd, __dmul_rn(2.0, inner)), 4.0);
+  const double Dw = __ddiv_rn(__ddiv_rn(__dsub_rn(sd, __dmul_rn(2.0, inner)), 4.0), omega);
+  const double M = __ddiv_rn(sm, 4.0);
+  const double Dc = __dadd_rn(Dw, M);
   vcc[o] = Dc;
+  vcc[nc + o] = __ddiv_rn(__ddiv_rn(sx, 4.0), omega);
+  vcc[2 * nc + o] = __ddiv_rn(__ddiv_rn(sy, 4.0), omega);
+  vcc[3 * nc + o] = __ddiv_rn(__ddiv_rn(sz, 4.0), omega);
   vcc[4 * nc + o] = __ddiv_rn(1.0, Dc);
-  vcc[nc + o] = __ddiv_rn(sx, 4.0);
-  vcc[2 * nc + o] = __ddiv_rn(sy, 4.0);
-  vcc[3 * nc + o] = __ddiv_rn(sz, 4.0);
+  vcc[5 * nc + o] = Dw;
+  vcc[6 * nc + o] = M;
 }
+
 
 // Weighted neighbour sum of cell m of colour c, row (j, k), on a packed level, in the order
 // -x,+x,-y,+y,-z,+z (walls: none; periodic axes wrap). The weight of a + face is read at the
@@ -340,6 +365,51 @@ __global__ void __launch_bounds__(256) k_var_set_rhs(double* __restrict__ gout, 
   gout[coarse_index(G, i, j, k)] = __dmul_rn(v, __dmul_rn(h, h));
 }
 
+// Newton step of the Poisson-Boltzmann equation on the (packed) finest level: the scaled
+// nonlinear residual F~ = g0 + sum w phi - Dw phi - k2 h^2 sinh(phi) into f (the right-hand side
+// of the correction equation), partial sums of F~^2, and the linearised diagonal
+// M = k2 h^2 cosh(phi), D = Dw + M, 1/D for the next coarsening.
+__global__ void __launch_bounds__(256) k_pb_update(const double* __restrict__ x, const double* __restrict__ g0,
+                                                   double* __restrict__ vc, Geom G, const double* __restrict__ k2,
+                                                   double h2, double* __restrict__ f,
+                                                   double* __restrict__ partials) {
+  __shared__ double red[33];
+  const long long n = 2 * G.csz;
+  const VarCoef W = var_coef(vc, n);
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / G.csz);
+    const long long r = t - (long long)c * G.csz;
+    const int m = (int)(r % G.hx);
+    const long long rw = r / G.hx;
+    const int j = (int)(rw % G.ny), k = (int)(rw / G.ny);
+    const long long nat = (long long)(2 * m + ((j + k + c) & 1)) + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+    const double S = var_nbsum_packed(x, W, G, c, m, j, k);
+    const double p = x[t];
+    const double kh = __dmul_rn(__ldg(k2 + nat), h2);
+    const double F = fma(-kh, sinh(p), fma(-W.Dw[t], p, g0[t] + S));
+    f[t] = F;
+    acc = fma(F, F, acc);
+    const double M = __dmul_rn(kh, cosh(p));
+    const double D = __dadd_rn(W.Dw[t], M);
+    vc[6 * n + t] = M;
+    vc[t] = D;
+    vc[4 * n + t] = __ddiv_rn(1.0, D);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_axpy(double* __restrict__ y, const double* __restrict__ x, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = y[t] + x[t];
+}
+
+__global__ void __launch_bounds__(256) k_fill(double* __restrict__ y, double v, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = v;
+}
+
 void shape2(int nx, int ny, int nz, dim3& b, dim3& g) {
   const int bx = nx >= 64 ? 64 : (nx >= 32 ? 32 : 16);
   b = dim3(bx, 256 / bx, 1);
@@ -350,15 +420,47 @@ void shape2(int nx, int ny, int nz, dim3& b, dim3& g) {
 
 long long var_cells(const Geom& G) { return G.packed ? 2 * G.csz : G.csz; }
 
-cudaError_t launch_var_setup(const double* eps, const Geom* geo, int L, const FaceBC& bc, double* const* vc,
-                             cudaStream_t s) {
+int var_arrays() { return kVarArrays; }
+
+cudaError_t launch_var_coarsen_all(const Geom* geo, int L, double* const* vc, double omega, cudaStream_t s) {
   dim3 b, g;
-  shape2(geo[0].nx, geo[0].ny, geo[0].nz, b, g);
-  k_var_fine<<<g, b, 0, s>>>(eps, geo[0], bc, vc[0], var_cells(geo[0]));
   for (int l = 1; l < L; ++l) {
     shape2(geo[l].nx, geo[l].ny, geo[l].nz, b, g);
-    k_var_coarsen<<<g, b, 0, s>>>(vc[l - 1], geo[l - 1], var_cells(geo[l - 1]), vc[l], geo[l], var_cells(geo[l]));
+    k_var_coarsen<<<g, b, 0, s>>>(vc[l - 1], geo[l - 1], var_cells(geo[l - 1]), vc[l], geo[l], var_cells(geo[l]),
+                                  omega);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_setup(const double* eps, const double* react, double h, double omega, const Geom* geo, int L,
+                             const FaceBC& bc, double* const* vc, cudaStream_t s) {
+  dim3 b, g;
+  shape2(geo[0].nx, geo[0].ny, geo[0].nz, b, g);
+  k_var_fine<<<g, b, 0, s>>>(eps, react, h * h, geo[0], bc, vc[0], var_cells(geo[0]));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_var_coarsen_all(geo, L, vc, omega, s);
+}
+
+cudaError_t launch_pb_update(const double* x, const double* g0, double* vc, const Geom& G, const double* k2, double h,
+                             double* f, double* partials, int* nparts, cudaStream_t s) {
+  const long long n = var_cells(G);
+  long long blocks = (n + 255) / 256;
+  if (blocks > kMaxPartials) blocks = kMaxPartials;
+  k_pb_update<<<(int)blocks, 256, 0, s>>>(x, g0, vc, G, k2, h * h, f, partials);
+  *nparts = (int)blocks;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s) {
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_axpy<<<(int)blocks, 256, 0, s>>>(y, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s) {
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_fill<<<(int)blocks, 256, 0, s>>>(y, v, n);
   return cudaGetLastError();
 }
 

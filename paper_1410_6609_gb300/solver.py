@@ -205,6 +205,27 @@ class Poisson:
     def has_permittivity(self) -> bool:
         return bool(self.lib.mg_has_permittivity(self.ctx))
 
+    def set_reaction(self, k2=None):
+        """Reaction coefficients k2 >= 0 per cell (float64 tensor [nz, ny, nx] on the device) for
+        -div(eps grad phi) + k2 phi (see mg_set_reaction); None removes the term."""
+        if k2 is None:
+            self._check(self.lib.mg_set_reaction(self.ctx, None), "mg_set_reaction")
+            return
+        t = self._field(k2, "reaction").contiguous()
+        self._check(self.lib.mg_set_reaction(self.ctx, _ptr(t)), "mg_set_reaction")
+
+    def solve_pb(self, tol: float = 1e-10, max_newton: int = 30, inner_tol: float = 1e-3, max_cycles: int = 30,
+                 raise_on_fail: bool = True):
+        """Newton's method for -div(eps grad phi) + k2 sinh(phi) = f (see mg_solve_pb); returns
+        (Newton steps, ||F|| / ||f||)."""
+        k = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = self.lib.mg_solve_pb(self.ctx, float(tol), int(max_newton), float(inner_tol), int(max_cycles),
+                                  ctypes.byref(k), ctypes.byref(rel))
+        if st != 0 and (raise_on_fail or st != _lib.MG_ERR_NOT_CONVERGED):
+            self._check(st, "mg_solve_pb")
+        return k.value, rel.value
+
     @property
     def gradient_stencil(self) -> int:
         """Gradient of efield / force_gather / step: 7 (D3Q7) or 19 (D3Q19 wherever it fits in the domain)."""
