@@ -490,6 +490,10 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     except Exception as e:
         out["permittivity"] = {"error": repr(e)}
     try:
+        out["poisson_boltzmann"] = measure_pb(w, sp)
+    except Exception as e:
+        out["poisson_boltzmann"] = {"error": repr(e)}
+    try:
         out["batched"] = measure_batched()
     except Exception as e:  # reported, never fatal for the main line
         out["batched"] = {"error": repr(e)}
@@ -572,6 +576,43 @@ def measure_permittivity(w, sp, t64_const, k64_const, hbm):
             "constant_eps_fp64_ms": t64_const, "constant_eps_fp64_cycles": k64_const,
             "half_sweep_ms": t_sw, "half_sweep_GB/s": bsw / t_sw / 1e6, "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm,
             "half_sweep_bytes": int(bsw), "particle_eps": 2.0, "fluid_eps": 80.0}
+
+
+def measure_pb(w, sp, debye: float = 4.0, charge: float = 4.0):
+    """Charged dielectric spheres (permittivity 2, no ions inside) in a 1:1 electrolyte
+    (permittivity 80, Debye length `debye` cells) at the workload's size and walls: Newton's
+    method for the nonlinear Poisson-Boltzmann equation from zero to the workload's tolerance
+    (linearised steps to 1e-3 by V-cycles), with the sphere densities scaled so that the
+    potential reaches the nonlinear regime."""
+    import torch
+
+    from paper_1410_6609_gb300.solver import Poisson
+
+    nx, ny, nz = w.dims
+    N = nx * ny * nz
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="fp64")
+    c, r = dev(sp.centers), dev(sp.radius)
+    vol = P.sphere_density(c, r, torch.ones(sp.count, dtype=torch.float64, device="cuda"), w.subsample)
+    torch.cuda.synchronize()
+    eps = 80.0 - 78.0 * vol
+    k2 = (1.0 - vol) * (80.0 / debye ** 2)
+    torch.cuda.synchronize()
+    P.set_permittivity(eps)
+    P.set_reaction(k2)
+    rho = P.sphere_density(c, r, dev(sp.density * charge), w.subsample)
+
+    def solve():
+        P.set_rhs(rho)
+        P.set_solution(None)
+        return P.solve_pb(w.tol, 40, 1e-3, 30)
+
+    it, rel = solve()
+    t = _time(solve, P.stream, 1)
+    phimax = float(P.solution().abs().max())
+    P.close()
+    return {"tol": w.tol, "newton_steps": it, "rel_residual": rel, "ms": t, "mlups_per_solve": N / t / 1e3,
+            "max_abs_phi_thermal_units": phimax, "debye_length_cells": debye, "charge_scale": charge}
 
 
 def measure_batched(tol: float = 1e-9):
