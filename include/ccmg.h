@@ -109,10 +109,12 @@ mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
  * ghost 2 g - phi, Neumann phi + h g, as in the constant case), and every coarse level carries the
  * Galerkin operator R A P of the finer one. The array is copied and the level coefficients are
  * built before the call returns; mg_set_rhs then takes f = rho with the wall terms 2 eps g / h^2
- * and eps g / h, and the cycle, the solve and the residual use the weighted operators. NULL
- * returns to the constant permittivity of mg_params. Errors: MG_ERR_INVALID in MG_MIXED mode
- * (FP64 only), MG_ERR_OOM if the coefficients (5 doubles per cell and level) cannot be allocated.
- * mg_rhs_adjoint refuses a context with a variable permittivity (its adjoint differs). */
+ * and eps g / h, and the cycle, the solve and the residual use the weighted operators (in
+ * MG_MIXED mode the inner cycle uses single-precision copies of the coefficients, the outer
+ * residual and update stay FP64). NULL returns to the constant permittivity of mg_params.
+ * Errors: MG_ERR_OOM if the coefficients (7 doubles, and 5 floats in MG_MIXED mode, per cell and
+ * level) cannot be allocated. mg_rhs_adjoint refuses a context with a variable permittivity
+ * (its adjoint differs). */
 mg_status mg_set_permittivity(mg_ctx* ctx, const double* d_eps);
 /* 1 if the weighted operator is active (a variable permittivity or a reaction term is set), 0
  * otherwise (and for a NULL context). */
@@ -128,7 +130,7 @@ int mg_has_permittivity(const mg_ctx* ctx);
  * coarse-grid correction factor (1/cgc_weight times its Galerkin product, the correction itself
  * unmagnified: the same iterates for the Poisson operator, no overshoot of the reaction part).
  * The array is copied and the coefficients built before the call returns. NULL removes the term.
- * MG_ERR_INVALID in MG_MIXED mode, MG_ERR_OOM if the buffers cannot be allocated. */
+ * MG_ERR_OOM if the buffers cannot be allocated. */
 mg_status mg_set_reaction(mg_ctx* ctx, const double* d_k2);
 int mg_has_reaction(const mg_ctx* ctx);
 

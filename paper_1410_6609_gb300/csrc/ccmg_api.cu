@@ -61,6 +61,7 @@ struct mg_ctx {
   bool eps_set = false;        // d_eps came from mg_set_permittivity (else the constant eps)
   double* d_k2 = nullptr;      // reaction coefficients (screened / Poisson-Boltzmann), or null
   double* vc[kMaxLevels]{};    // weighted coefficients per level (D, wx, wy, wz, 1/D, Dw, M)
+  float* vc32[kMaxLevels]{};   // MG_MIXED: their single-precision copies (D, wx, wy, wz, 1/D)
   double* d_pb = nullptr;      // Newton state: base right-hand side and potential (2 finest fields)
   std::string err;
 };
@@ -102,7 +103,10 @@ void free_all(mg_ctx* c) {
   cudaFree(c->d_eps);
   cudaFree(c->d_k2);
   cudaFree(c->d_pb);
-  for (int l = 0; l < kMaxLevels; ++l) cudaFree(c->vc[l]);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    cudaFree(c->vc[l]);
+    cudaFree(c->vc32[l]);
+  }
   cudaFree(c->partials);
   cudaFree(c->scal);
   cudaFree(c->d_iters);
@@ -126,35 +130,37 @@ cudaError_t sweep(mg_ctx* c, T* x, const T* g, const InvDiag<T>& inv, int l, int
   return launch_smooth<T>(x, g, c->geo[l], inv, colour, zero, s);
 }
 
-// The FP64 V-cycle with the variable-permittivity operators (the same steps, weighted kernels).
-cudaError_t enqueue_vcycle_var(mg_ctx* c, int l, bool zero, cudaStream_t s, long long* nk) {
+// The V-cycle with the weighted operators (the same steps, weighted kernels), in double on the
+// FP64 hierarchy or in single precision on the inner-cycle hierarchy of MG_MIXED.
+template <typename T>
+cudaError_t enqueue_vcycle_var(mg_ctx* c, T* const* xs, T* const* gs, const T* const* vcs, int l, bool zero,
+                               cudaStream_t s, long long* nk) {
   const Geom& G = c->geo[l];
-  double* x = c->x64[l];
-  const double* g = c->g64[l];
+  T* x = xs[l];
+  const T* g = gs[l];
   cudaError_t e;
   if (l == c->L - 1) {
     ++*nk;
-    return launch_var_coarse_cg(x, g, c->vc[l], G, 1e-14, 2 * G.nx * G.ny * G.nz, c->d_iters, s);
+    return launch_var_coarse_cg<T>(x, g, vcs[l], G, 1e-14, 2 * G.nx * G.ny * G.nz, c->d_iters, s);
   }
   if (zero && c->p.nu1 == 0) {
-    e = cudaMemsetAsync(x, 0, sizeof(double) * (size_t)cells(G), s);
+    e = cudaMemsetAsync(x, 0, sizeof(T) * (size_t)cells(G), s);
     if (e != cudaSuccess) return e;
   }
   for (int it = 0; it < c->p.nu1; ++it) {
-    if ((e = launch_var_smooth(x, g, c->vc[l], G, 0, zero && it == 0, s)) != cudaSuccess) return e;
-    if ((e = launch_var_smooth(x, g, c->vc[l], G, 1, false, s)) != cudaSuccess) return e;
+    if ((e = launch_var_smooth<T>(x, g, vcs[l], G, 0, zero && it == 0, s)) != cudaSuccess) return e;
+    if ((e = launch_var_smooth<T>(x, g, vcs[l], G, 1, false, s)) != cudaSuccess) return e;
     *nk += 2;
   }
-  if ((e = launch_var_resid_restrict(x, g, c->vc[l], G, c->g64[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
+  if ((e = launch_var_resid_restrict<T>(x, g, vcs[l], G, gs[l + 1], c->geo[l + 1], s)) != cudaSuccess) return e;
   ++*nk;
-  if ((e = enqueue_vcycle_var(c, l + 1, true, s, nk)) != cudaSuccess) return e;
+  if ((e = enqueue_vcycle_var<T>(c, xs, gs, vcs, l + 1, true, s, nk)) != cudaSuccess) return e;
   // the correction factor is in the coarse operators (var_kernels.cu): weight 1 here
-  if ((e = launch_prolong<double>(x, G, c->x64[l + 1], c->geo[l + 1], 1.0, c->p.nu2 >= 1, s)) != cudaSuccess)
-    return e;
+  if ((e = launch_prolong<T>(x, G, xs[l + 1], c->geo[l + 1], T(1), c->p.nu2 >= 1, s)) != cudaSuccess) return e;
   ++*nk;
   for (int it = 0; it < c->p.nu2; ++it) {
-    if ((e = launch_var_smooth(x, g, c->vc[l], G, 1, false, s)) != cudaSuccess) return e;
-    if ((e = launch_var_smooth(x, g, c->vc[l], G, 0, false, s)) != cudaSuccess) return e;
+    if ((e = launch_var_smooth<T>(x, g, vcs[l], G, 1, false, s)) != cudaSuccess) return e;
+    if ((e = launch_var_smooth<T>(x, g, vcs[l], G, 0, false, s)) != cudaSuccess) return e;
     *nk += 2;
   }
   return cudaSuccess;
@@ -213,11 +219,14 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
 // residual that the residual graph left in g32[0] (the first from e = 0), followed by
 // phi += scale * e (phi = scale * e for a zero iterate, `first`) and the next scale.
 cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk, bool first) {
-  if (c->d_eps) return enqueue_vcycle_var(c, 0, false, s, nk);
+  if (c->d_eps && !mixed(c)) return enqueue_vcycle_var<double>(c, c->x64, c->g64, c->vc, 0, false, s, nk);
   if (!mixed(c)) return enqueue_vcycle<double>(c, c->x64, c->g64, c->inv64, 0, false, s, nk);
   cudaError_t e = cudaSuccess;
-  for (int it = 0; it < c->p.mixed_inner; ++it)
-    if ((e = enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, it == 0, s, nk)) != cudaSuccess) return e;
+  for (int it = 0; it < c->p.mixed_inner; ++it) {
+    e = c->d_eps ? enqueue_vcycle_var<float>(c, c->x32, c->g32, c->vc32, 0, it == 0, s, nk)
+                 : enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, it == 0, s, nk);
+    if (e != cudaSuccess) return e;
+  }
   e = first ? launch_set_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s)
             : launch_update_mixed(c->x64[0], c->x32[0], cells(c->geo[0]), c->scal, S_SCALE, s);
   if (e != cudaSuccess) return e;
@@ -232,7 +241,8 @@ cudaError_t enqueue_resid(mg_ctx* c, int mode, double* out_natural, cudaStream_t
   int np = 0;
   if (c->d_eps) {
     cudaError_t e = launch_var_resid_norm(c->x64[0], c->g64[0], c->vc[0], c->geo[0], level_coeff(c, 0), c->partials,
-                                          &np, mode == 1 ? out_natural : nullptr, s);
+                                          &np, mode, out_natural, mode == 2 ? c->g32[0] : nullptr,
+                                          c->scal + S_INV_SCALE, s);
     if (e != cudaSuccess) return e;
     *nk += 2;
     return launch_finalize(c->partials, np, c->scal, S_RSUM, S_REL, S_GSUM, s);
@@ -614,15 +624,20 @@ mg_status var_alloc(mg_ctx* c, bool fill) {
   const Geom& G = c->geo[0];
   const size_t n = (size_t)G.nx * G.ny * G.nz;
   bool ok = cudaMalloc((void**)&c->d_eps, n * sizeof(double)) == cudaSuccess;
-  for (int l = 0; l < c->L && ok; ++l)
+  for (int l = 0; l < c->L && ok; ++l) {
     ok = cudaMalloc((void**)&c->vc[l], (size_t)var_arrays() * cells(c->geo[l]) * sizeof(double)) == cudaSuccess;
+    if (ok && mixed(c))
+      ok = cudaMalloc((void**)&c->vc32[l], (size_t)var_arrays32() * cells(c->geo[l]) * sizeof(float)) == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     cudaFree(c->d_eps);
     c->d_eps = nullptr;
     for (int l = 0; l < c->L; ++l) {
       cudaFree(c->vc[l]);
+      cudaFree(c->vc32[l]);
       c->vc[l] = nullptr;
+      c->vc32[l] = nullptr;
     }
     return fail(c, MG_ERR_OOM, "weighted operator");
   }
@@ -636,15 +651,22 @@ void var_release(mg_ctx* c) {
   c->d_eps = nullptr;
   for (int l = 0; l < c->L; ++l) {
     cudaFree(c->vc[l]);
+    cudaFree(c->vc32[l]);
     c->vc[l] = nullptr;
+    c->vc32[l] = nullptr;
   }
 }
 
-// The coefficients of every level from the permittivities and the reaction coefficients.
+// The coefficients of every level from the permittivities and the reaction coefficients (and
+// their single-precision copies for the inner cycle of MG_MIXED).
 mg_status var_rebuild(mg_ctx* c) {
   CK(launch_var_setup(c->d_eps, c->d_k2, c->p.h, c->p.cgc_weight, c->geo, c->L, c->bc, c->vc, c->stream),
      "weighted coefficients");
   c->launches += c->L;
+  if (mixed(c)) {
+    CK(launch_var_to_f32(c->vc, c->vc32, c->geo, c->L, c->stream), "weighted coefficients");
+    c->launches += c->L;
+  }
   CK(cudaStreamSynchronize(c->stream), "weighted coefficients");
   return MG_OK;
 }
@@ -655,7 +677,6 @@ extern "C" {
 
 mg_status mg_set_permittivity(mg_ctx* c, const double* d_eps) {
   if (!c) return MG_ERR_INVALID;
-  if (d_eps && mixed(c)) return fail(c, MG_ERR_INVALID, "a variable permittivity needs MG_FP64");
   drop_graphs(c);
   mg_status st;
   c->eps_set = d_eps != nullptr;
@@ -678,7 +699,6 @@ mg_status mg_set_permittivity(mg_ctx* c, const double* d_eps) {
 
 mg_status mg_set_reaction(mg_ctx* c, const double* d_k2) {
   if (!c) return MG_ERR_INVALID;
-  if (d_k2 && mixed(c)) return fail(c, MG_ERR_INVALID, "a reaction term needs MG_FP64");
   drop_graphs(c);
   const Geom& G = c->geo[0];
   const size_t n = (size_t)G.nx * G.ny * G.nz;
@@ -737,6 +757,11 @@ mg_status mg_solve_pb(mg_ctx* c, double tol, int max_newton, double inner_tol, i
     // (A_eps + k2 cosh(phi)) delta = F with homogeneous walls, from delta = 0
     CK(launch_var_coarsen_all(c->geo, c->L, c->vc, c->p.cgc_weight, c->stream), "Newton");
     c->launches += c->L - 1;
+    if (mixed(c)) {  // the inner cycle's coefficients and the scale of its first defect-correction step
+      CK(launch_var_to_f32(c->vc, c->vc32, c->geo, c->L, c->stream), "Newton");
+      CK(launch_set_scale(c->scal, S_GSUM, S_SCALE, (double)n, c->stream), "Newton");
+      c->launches += c->L + 1;
+    }
     CK(cudaMemsetAsync(c->x64[0], 0, n * sizeof(double), c->stream), "Newton");
     c->phi_zero = true;
     st = mg_solve(c, inner_tol, max_cycles, nullptr, nullptr);
@@ -1019,8 +1044,12 @@ mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1 || (colour != 0 && colour != 1))
     return fail(c, MG_ERR_INVALID, "smoothing needs a non-coarsest level and colour 0 or 1");
-  if (c->d_eps)
-    CK(launch_var_smooth(c->x64[level], c->g64[level], c->vc[level], c->geo[level], colour, false, c->stream),
+  if (c->d_eps && mixed(c))
+    CK(launch_var_smooth<float>(c->x32[level], c->g32[level], c->vc32[level], c->geo[level], colour, false,
+                                c->stream),
+       "smooth");
+  else if (c->d_eps)
+    CK(launch_var_smooth<double>(c->x64[level], c->g64[level], c->vc[level], c->geo[level], colour, false, c->stream),
        "smooth");
   else if (mixed(c))
     CK(sweep<float>(c, c->x32[level], c->g32[level], c->inv32, level, colour, false, c->stream), "smooth");
@@ -1035,9 +1064,13 @@ static mg_status residual_restrict_op(mg_ctx* c, int level, bool red_only) {
   if (!c) return MG_ERR_INVALID;
   if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "restriction needs a non-coarsest level");
   if (c->d_eps && red_only) return fail(c, MG_ERR_INVALID, "the red-only restriction is single precision");
-  if (c->d_eps)
-    CK(launch_var_resid_restrict(c->x64[level], c->g64[level], c->vc[level], c->geo[level], c->g64[level + 1],
-                                 c->geo[level + 1], c->stream),
+  if (c->d_eps && mixed(c))
+    CK(launch_var_resid_restrict<float>(c->x32[level], c->g32[level], c->vc32[level], c->geo[level],
+                                        c->g32[level + 1], c->geo[level + 1], c->stream),
+       "residual_restrict");
+  else if (c->d_eps)
+    CK(launch_var_resid_restrict<double>(c->x64[level], c->g64[level], c->vc[level], c->geo[level],
+                                         c->g64[level + 1], c->geo[level + 1], c->stream),
        "residual_restrict");
   else if (mixed(c))
     CK(launch_resid_restrict<float>(c->x32[level], c->g32[level], c->geo[level], c->g32[level + 1],
@@ -1076,8 +1109,12 @@ mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
   const Geom& G = c->geo[l];
   const int n = G.nx * G.ny * G.nz;
   if (!mixed(c) && l == 0) c->phi_zero = false;  // single-level grid: the CG writes the finest iterate
-  if (c->d_eps)
-    CK(launch_var_coarse_cg(c->x64[l], c->g64[l], c->vc[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
+  if (c->d_eps && mixed(c))
+    CK(launch_var_coarse_cg<float>(c->x32[l], c->g32[l], c->vc32[l], G, 1e-14, 2 * n, c->d_iters, c->stream),
+       "coarse_solve");
+  else if (c->d_eps)
+    CK(launch_var_coarse_cg<double>(c->x64[l], c->g64[l], c->vc[l], G, 1e-14, 2 * n, c->d_iters, c->stream),
+       "coarse_solve");
   else if (mixed(c))
     CK(launch_coarse_cg<float>(c->x32[l], c->g32[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
   else

@@ -107,14 +107,21 @@ cudaError_t launch_pb_update(const double* x, const double* g0, double* vc, cons
                              double* f, double* partials, int* nparts, cudaStream_t s);
 cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s);
 cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s);
-cudaError_t launch_var_smooth(double* x, const double* g, const double* vc, const Geom& G, int colour, bool zero,
-                              cudaStream_t s);
-cudaError_t launch_var_resid_restrict(const double* x, const double* g, const double* vc, const Geom& G, double* gc,
-                                      const Geom& Gc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_var_smooth(T* x, const T* g, const T* vc, const Geom& G, int colour, bool zero, cudaStream_t s);
+template <typename T>
+cudaError_t launch_var_resid_restrict(const T* x, const T* g, const T* vc, const Geom& G, T* gc, const Geom& Gc,
+                                      cudaStream_t s);
+// mode 0: partial sums; 1: also the natural-order residual; 2: also the float copy float(r~ isc)
 cudaError_t launch_var_resid_norm(const double* x, const double* g, const double* vc, const Geom& G, double c0,
-                                  double* partials, int* nparts, double* out_natural, cudaStream_t s);
-cudaError_t launch_var_coarse_cg(double* x, const double* b, const double* vc, const Geom& Gc, double rtol, int maxit,
-                                 int* d_iters, cudaStream_t s);
+                                  double* partials, int* nparts, int mode, double* out_natural, float* out_packed,
+                                  const double* inv_scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_var_coarse_cg(T* x, const T* b, const T* vc, const Geom& Gc, double rtol, int maxit, int* d_iters,
+                                 cudaStream_t s);
+// single-precision copies of the cycle's coefficients (var_arrays32() arrays per level)
+int var_arrays32();
+cudaError_t launch_var_to_f32(const double* const* vc, float* const* v32, const Geom* geo, int L, cudaStream_t s);
 cudaError_t prepare_var_coarse_cg();
 cudaError_t launch_var_set_rhs(double* g, const Geom& G, const double* rho, const double* eps, double h,
                                const FaceBC& bc, cudaStream_t s);

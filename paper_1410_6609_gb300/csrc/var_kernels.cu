@@ -53,6 +53,25 @@ __device__ __forceinline__ VarCoef var_coef(const double* vc, long long n) {
   return VarCoef{vc, vc + n, vc + 2 * n, vc + 3 * n, vc + 4 * n, vc + 5 * n, vc + 6 * n};
 }
 
+// The cycle's view of a level's coefficients in precision T (the first five arrays: D, wx, wy,
+// wz, 1/D); the single-precision copies (kVarArrays32 arrays) serve the inner cycle of the
+// mixed-precision defect correction.
+constexpr int kVarArrays32 = 5;
+template <typename T>
+struct VarW {
+  const T* D;
+  const T* wx;
+  const T* wy;
+  const T* wz;
+  const T* invD;
+};
+template <typename T>
+__device__ __forceinline__ VarW<T> var_w(const T* vc, long long n) {
+  return VarW<T>{vc, vc + n, vc + 2 * n, vc + 3 * n, vc + 4 * n};
+}
+__device__ __forceinline__ VarW<double> var_w(const VarCoef& W) { return VarW<double>{W.D, W.wx, W.wy, W.wz, W.invD}; }
+using ops::fmat;
+
 __device__ __forceinline__ double harmonic(double a, double b) { return __ddiv_rn(__dmul_rn(2.0 * a, b), a + b); }
 
 __device__ __forceinline__ long long natural(const Geom& G, int i, int j, int k) {
@@ -159,84 +178,86 @@ __global__ void __launch_bounds__(256) k_var_coarsen(const double* __restrict__ 
 // Weighted neighbour sum of cell m of colour c, row (j, k), on a packed level, in the order
 // -x,+x,-y,+y,-z,+z (walls: none; periodic axes wrap). The weight of a + face is read at the
 // neighbour's index, where its potential is.
-__device__ __forceinline__ double var_nbsum_packed(const double* __restrict__ x, const VarCoef& W, const Geom& G,
-                                                   int c, int m, int j, int k) {
+template <typename T>
+__device__ __forceinline__ T var_nbsum_packed(const T* __restrict__ x, const VarW<T>& W, const Geom& G, int c, int m,
+                                              int j, int k) {
   const int s = (j + k + c) & 1;
   const long long row = ((long long)k * G.ny + j) * G.hx;
   const long long own = (long long)c * G.csz + row + m;
   const long long oth = (long long)(1 - c) * G.csz + row;
   const bool px = (G.per & 1) != 0;
-  double acc = 0.0;
-  if (!(m == 0 && s == 0)) acc = fma(__ldg(W.wx + own), __ldg(x + oth + m + s - 1), acc);
-  else if (px) acc = fma(__ldg(W.wx + own), __ldg(x + oth + G.hx - 1), acc);
+  T acc = T(0);
+  if (!(m == 0 && s == 0)) acc = fmat(__ldg(W.wx + own), __ldg(x + oth + m + s - 1), acc);
+  else if (px) acc = fmat(__ldg(W.wx + own), __ldg(x + oth + G.hx - 1), acc);
   if (!(m == G.hx - 1 && s == 1)) {
     const long long q = oth + m + s;
-    acc = fma(__ldg(W.wx + q), __ldg(x + q), acc);
+    acc = fmat(__ldg(W.wx + q), __ldg(x + q), acc);
   } else if (px) {
-    acc = fma(__ldg(W.wx + oth), __ldg(x + oth), acc);
+    acc = fmat(__ldg(W.wx + oth), __ldg(x + oth), acc);
   }
-  if (nb_has<0, true>(G, j, k)) acc = fma(__ldg(W.wy + own), __ldg(x + oth + m + nb_off<0, true>(G, j, k)), acc);
+  if (nb_has<0, true>(G, j, k)) acc = fmat(__ldg(W.wy + own), __ldg(x + oth + m + nb_off<0, true>(G, j, k)), acc);
   if (nb_has<1, true>(G, j, k)) {
     const long long q = oth + m + nb_off<1, true>(G, j, k);
-    acc = fma(__ldg(W.wy + q), __ldg(x + q), acc);
+    acc = fmat(__ldg(W.wy + q), __ldg(x + q), acc);
   }
-  if (nb_has<2, true>(G, j, k)) acc = fma(__ldg(W.wz + own), __ldg(x + oth + m + nb_off<2, true>(G, j, k)), acc);
+  if (nb_has<2, true>(G, j, k)) acc = fmat(__ldg(W.wz + own), __ldg(x + oth + m + nb_off<2, true>(G, j, k)), acc);
   if (nb_has<3, true>(G, j, k)) {
     const long long q = oth + m + nb_off<3, true>(G, j, k);
-    acc = fma(__ldg(W.wz + q), __ldg(x + q), acc);
+    acc = fmat(__ldg(W.wz + q), __ldg(x + q), acc);
   }
   return acc;
 }
 
-// The same on a natural-order level.
-__device__ __forceinline__ double var_nbsum_natural(const double* __restrict__ x, const VarCoef& W, const Geom& G,
-                                                    int i, int j, int k) {
+// The same on a natural-order level, values of type V and weights of type C, summed in V.
+template <typename V, typename C>
+__device__ __forceinline__ V var_nbsum_natural(const V* __restrict__ x, const VarW<C>& W, const Geom& G, int i, int j,
+                                               int k) {
   const long long p = natural(G, i, j, k);
   const long long sy = G.nx, sz = (long long)G.nx * G.ny;
   const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0, pz = (G.per & 4) != 0;
-  double acc = 0.0;
-  if (i > 0) acc = fma(W.wx[p], x[p - 1], acc);
-  else if (px) acc = fma(W.wx[p], x[p + G.nx - 1], acc);
-  if (i < G.nx - 1) acc = fma(W.wx[p + 1], x[p + 1], acc);
-  else if (px) acc = fma(W.wx[p - (G.nx - 1)], x[p - (G.nx - 1)], acc);
-  if (j > 0) acc = fma(W.wy[p], x[p - sy], acc);
-  else if (py) acc = fma(W.wy[p], x[p + (G.ny - 1) * sy], acc);
-  if (j < G.ny - 1) acc = fma(W.wy[p + sy], x[p + sy], acc);
-  else if (py) acc = fma(W.wy[p - (G.ny - 1) * sy], x[p - (G.ny - 1) * sy], acc);
-  if (k > 0) acc = fma(W.wz[p], x[p - sz], acc);
-  else if (pz) acc = fma(W.wz[p], x[p + (G.nz - 1) * sz], acc);
-  if (k < G.nz - 1) acc = fma(W.wz[p + sz], x[p + sz], acc);
-  else if (pz) acc = fma(W.wz[p - (G.nz - 1) * sz], x[p - (G.nz - 1) * sz], acc);
+  V acc = V(0);
+  if (i > 0) acc = fmat(V(W.wx[p]), x[p - 1], acc);
+  else if (px) acc = fmat(V(W.wx[p]), x[p + G.nx - 1], acc);
+  if (i < G.nx - 1) acc = fmat(V(W.wx[p + 1]), x[p + 1], acc);
+  else if (px) acc = fmat(V(W.wx[p - (G.nx - 1)]), x[p - (G.nx - 1)], acc);
+  if (j > 0) acc = fmat(V(W.wy[p]), x[p - sy], acc);
+  else if (py) acc = fmat(V(W.wy[p]), x[p + (G.ny - 1) * sy], acc);
+  if (j < G.ny - 1) acc = fmat(V(W.wy[p + sy]), x[p + sy], acc);
+  else if (py) acc = fmat(V(W.wy[p - (G.ny - 1) * sy]), x[p - (G.ny - 1) * sy], acc);
+  if (k > 0) acc = fmat(V(W.wz[p]), x[p - sz], acc);
+  else if (pz) acc = fmat(V(W.wz[p]), x[p + (G.nz - 1) * sz], acc);
+  if (k < G.nz - 1) acc = fmat(V(W.wz[p + sz]), x[p + sz], acc);
+  else if (pz) acc = fmat(V(W.wz[p - (G.nz - 1) * sz]), x[p - (G.nz - 1) * sz], acc);
   return acc;
 }
 
 // Red-black Gauss-Seidel half-sweep: phi = (g + weighted neighbours) (1/D) for the cells of
 // `colour` (ZERO: the iterate is zero, phi = g (1/D)).
-template <bool ZERO>
-__global__ void __launch_bounds__(256) k_var_smooth(double* __restrict__ x, const double* __restrict__ g,
-                                                    const double* __restrict__ vc, Geom G, int colour) {
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(256) k_var_smooth(T* __restrict__ x, const T* __restrict__ g,
+                                                    const T* __restrict__ vc, Geom G, int colour) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (m >= G.hx || j >= G.ny) return;
-  const VarCoef W = var_coef(vc, 2 * G.csz);
+  const VarW<T> W = var_w(vc, 2 * G.csz);
   const long long own = (long long)colour * G.csz + ((long long)k * G.ny + j) * G.hx + m;
-  const double S = ZERO ? 0.0 : var_nbsum_packed(x, W, G, colour, m, j, k);
+  const T S = ZERO ? T(0) : var_nbsum_packed<T>(x, W, G, colour, m, j, k);
   x[own] = (__ldg(g + own) + S) * __ldg(W.invD + own);
 }
 
 // Fused residual and averaging restriction: gc(I,J,K) = (1/4) sum of the 8 children's scaled
 // residuals g + sum w phi - D phi, in the order (dk, dj, di).
-__global__ void __launch_bounds__(256) k_var_resid_restrict(const double* __restrict__ x,
-                                                            const double* __restrict__ g,
-                                                            const double* __restrict__ vc, Geom G,
-                                                            double* __restrict__ gc, Geom Gc) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_var_resid_restrict(const T* __restrict__ x, const T* __restrict__ g,
+                                                            const T* __restrict__ vc, Geom G, T* __restrict__ gc,
+                                                            Geom Gc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= Gc.nx || J >= Gc.ny) return;
-  const VarCoef W = var_coef(vc, 2 * G.csz);
-  double acc = 0.0;
+  const VarW<T> W = var_w(vc, 2 * G.csz);
+  T acc = T(0);
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
@@ -246,21 +267,26 @@ __global__ void __launch_bounds__(256) k_var_resid_restrict(const double* __rest
         const int j = 2 * J + dj, k = 2 * K + dk;
         const int c = (di + dj + dk) & 1;
         const long long own = (long long)c * G.csz + ((long long)k * G.ny + j) * G.hx + I;
-        const double S = var_nbsum_packed(x, W, G, c, I, j, k);
-        acc = acc + fma(-__ldg(W.D + own), __ldg(x + own), __ldg(g + own) + S);
+        const T S = var_nbsum_packed<T>(x, W, G, c, I, j, k);
+        acc = acc + fmat(-__ldg(W.D + own), __ldg(x + own), __ldg(g + own) + S);
       }
-  gc[coarse_index(Gc, I, J, K)] = acc * 0.25;
+  gc[coarse_index(Gc, I, J, K)] = acc * T(0.25);
 }
 
-// Scaled residual of every cell with per-block partial sums of its square; OUT: also the
-// residual field r = r~ c0 in natural order.
-template <bool OUT>
+// Scaled residual of every cell with per-block partial sums of its square; MODE 1: also the
+// residual field r = r~ c0 in natural order; MODE 2: also float(r~ isc) in the level's order (the
+// right-hand side of the single-precision inner cycle, by exponent arithmetic when isc is a power
+// of two).
+template <int MODE>
 __global__ void __launch_bounds__(256) k_var_resid_norm(const double* __restrict__ x, const double* __restrict__ g,
                                                         const double* __restrict__ vc, Geom G, double c0,
-                                                        double* __restrict__ partials, double* __restrict__ outn) {
+                                                        double* __restrict__ partials, double* __restrict__ outn,
+                                                        float* __restrict__ outp, const double* __restrict__ inv_scale) {
   __shared__ double red[33];
-  const VarCoef W = var_coef(vc, G.packed ? 2 * G.csz : G.csz);
+  const VarW<double> W = var_w(vc, G.packed ? 2 * G.csz : G.csz);
   const long long n = G.packed ? 2 * G.csz : G.csz;
+  const double isc = MODE == 2 ? inv_scale[0] : 0.0;
+  const int p2 = MODE == 2 ? ops::pow2_exponent(isc) : ops::kBadPow2;
   double acc = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     double rd;
@@ -271,38 +297,41 @@ __global__ void __launch_bounds__(256) k_var_resid_norm(const double* __restrict
       const int m = (int)(r % G.hx);
       const long long rw = r / G.hx;
       const int j = (int)(rw % G.ny), k = (int)(rw / G.ny);
-      const double S = var_nbsum_packed(x, W, G, c, m, j, k);
+      const double S = var_nbsum_packed<double>(x, W, G, c, m, j, k);
       rd = fma(-__ldg(W.D + t), __ldg(x + t), __ldg(g + t) + S);
       nat = (long long)(2 * m + ((j + k + c) & 1)) + (long long)G.nx * ((long long)j + (long long)G.ny * k);
     } else {
       const int i = (int)(t % G.nx), j = (int)((t / G.nx) % G.ny), k = (int)(t / ((long long)G.nx * G.ny));
-      const double S = var_nbsum_natural(x, W, G, i, j, k);
+      const double S = var_nbsum_natural<double, double>(x, W, G, i, j, k);
       rd = fma(-W.D[t], x[t], g[t] + S);
       nat = t;
     }
     acc = fma(rd, rd, acc);
-    if (OUT) outn[nat] = rd * c0;
+    if (MODE == 1) outn[nat] = rd * c0;
+    if (MODE == 2) outp[t] = p2 != ops::kBadPow2 ? ops::f32_of_scaled(rd, p2) : (float)(rd * isc);
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 // Unpreconditioned CG on the coarsest (natural-order) level with the weighted operator, one CTA,
-// vectors in shared memory (4 n doubles); stops at ||r|| <= rtol ||b|| or maxit iterations.
-__global__ void __launch_bounds__(256) k_var_coarse_cg(double* __restrict__ xo, const double* __restrict__ bi,
-                                                       const double* __restrict__ vc, Geom G, double rtol, int maxit,
+// in double whatever T (the level's precision), vectors in shared memory (4 n doubles); stops at
+// ||r|| <= rtol ||b|| or maxit iterations.
+template <typename T>
+__global__ void __launch_bounds__(256) k_var_coarse_cg(T* __restrict__ xo, const T* __restrict__ bi,
+                                                       const T* __restrict__ vc, Geom G, double rtol, int maxit,
                                                        int* iters) {
   extern __shared__ double sm[];
   __shared__ double red[33];
   const int n = G.nx * G.ny * G.nz;
-  const VarCoef W = var_coef(vc, n);
+  const VarW<T> W = var_w(vc, n);
   double* x = sm;
   double* r = x + n;
   double* p = r + n;
   double* ap = p + n;
   double loc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double b = bi[i];
+    const double b = (double)bi[i];
     x[i] = 0.0;
     r[i] = b;
     p[i] = b;
@@ -316,7 +345,7 @@ __global__ void __launch_bounds__(256) k_var_coarse_cg(double* __restrict__ xo, 
       loc = 0.0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int ix = i % G.nx, iy = (i / G.nx) % G.ny, iz = i / (G.nx * G.ny);
-        const double a = W.D[i] * p[i] - var_nbsum_natural(p, W, G, ix, iy, iz);
+        const double a = (double)W.D[i] * p[i] - var_nbsum_natural<double, T>(p, W, G, ix, iy, iz);
         ap[i] = a;
         loc += p[i] * a;
       }
@@ -338,8 +367,16 @@ __global__ void __launch_bounds__(256) k_var_coarse_cg(double* __restrict__ xo, 
       rr = rrn;
     }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xo[i] = x[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xo[i] = (T)x[i];
   if (threadIdx.x == 0 && iters) *iters = it;
+}
+
+// Single-precision copies of the cycle's coefficient arrays of one level.
+__global__ void __launch_bounds__(256) k_var_to_f32(const double* __restrict__ vc, float* __restrict__ v32,
+                                                   long long n) {
+  const long long total = (long long)kVarArrays32 * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+    v32[t] = (float)vc[t];
 }
 
 // Right-hand side of -div(eps grad phi) = rho, scaled g = f h^2: f = rho, Dirichlet face cells
@@ -384,7 +421,7 @@ __global__ void __launch_bounds__(256) k_pb_update(const double* __restrict__ x,
     const long long rw = r / G.hx;
     const int j = (int)(rw % G.ny), k = (int)(rw / G.ny);
     const long long nat = (long long)(2 * m + ((j + k + c) & 1)) + (long long)G.nx * ((long long)j + (long long)G.ny * k);
-    const double S = var_nbsum_packed(x, W, G, c, m, j, k);
+    const double S = var_nbsum_packed<double>(x, var_w(W), G, c, m, j, k);
     const double p = x[t];
     const double kh = __dmul_rn(__ldg(k2 + nat), h2);
     const double F = fma(-kh, sinh(p), fma(-W.Dw[t], p, g0[t] + S));
@@ -464,48 +501,78 @@ cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_var_smooth(double* x, const double* g, const double* vc, const Geom& G, int colour, bool zero,
-                              cudaStream_t s) {
+template <typename T>
+cudaError_t launch_var_smooth(T* x, const T* g, const T* vc, const Geom& G, int colour, bool zero, cudaStream_t s) {
   dim3 b, gr;
   shape2(G.hx, G.ny, G.nz, b, gr);
-  if (zero) k_var_smooth<true><<<gr, b, 0, s>>>(x, g, vc, G, colour);
-  else k_var_smooth<false><<<gr, b, 0, s>>>(x, g, vc, G, colour);
+  if (zero) k_var_smooth<T, true><<<gr, b, 0, s>>>(x, g, vc, G, colour);
+  else k_var_smooth<T, false><<<gr, b, 0, s>>>(x, g, vc, G, colour);
   return cudaGetLastError();
 }
 
-cudaError_t launch_var_resid_restrict(const double* x, const double* g, const double* vc, const Geom& G, double* gc,
-                                      const Geom& Gc, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_var_resid_restrict(const T* x, const T* g, const T* vc, const Geom& G, T* gc, const Geom& Gc,
+                                      cudaStream_t s) {
   dim3 b, gr;
   shape2(Gc.nx, Gc.ny, Gc.nz, b, gr);
-  k_var_resid_restrict<<<gr, b, 0, s>>>(x, g, vc, G, gc, Gc);
+  k_var_resid_restrict<T><<<gr, b, 0, s>>>(x, g, vc, G, gc, Gc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_var_resid_norm(const double* x, const double* g, const double* vc, const Geom& G, double c0,
-                                  double* partials, int* nparts, double* out_natural, cudaStream_t s) {
+                                  double* partials, int* nparts, int mode, double* out_natural, float* out_packed,
+                                  const double* inv_scale, cudaStream_t s) {
   const long long n = var_cells(G);
   long long blocks = (n + 255) / 256;
   if (blocks > kMaxPartials) blocks = kMaxPartials;
-  if (out_natural) k_var_resid_norm<true><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, out_natural);
-  else k_var_resid_norm<false><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, nullptr);
+  if (mode == 1) k_var_resid_norm<1><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, out_natural, nullptr, nullptr);
+  else if (mode == 2)
+    k_var_resid_norm<2><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, nullptr, out_packed, inv_scale);
+  else k_var_resid_norm<0><<<(int)blocks, 256, 0, s>>>(x, g, vc, G, c0, partials, nullptr, nullptr, nullptr);
   *nparts = (int)blocks;
   return cudaGetLastError();
 }
 
-cudaError_t launch_var_coarse_cg(double* x, const double* b, const double* vc, const Geom& Gc, double rtol, int maxit,
-                                 int* d_iters, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_var_coarse_cg(T* x, const T* b, const T* vc, const Geom& Gc, double rtol, int maxit, int* d_iters,
+                                 cudaStream_t s) {
   const int n = Gc.nx * Gc.ny * Gc.nz;
   int threads = ((n + 31) / 32) * 32;
   if (threads > 256) threads = 256;
   const size_t smem = (size_t)4 * n * sizeof(double);
-  k_var_coarse_cg<<<1, threads, smem, s>>>(x, b, vc, Gc, rtol, maxit, d_iters);
+  k_var_coarse_cg<T><<<1, threads, smem, s>>>(x, b, vc, Gc, rtol, maxit, d_iters);
   return cudaGetLastError();
 }
 
 cudaError_t prepare_var_coarse_cg() {
   const int bytes = (int)(4 * kMaxCoarseCells * sizeof(double));
-  return cudaFuncSetAttribute(k_var_coarse_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_var_coarse_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_var_coarse_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
+
+int var_arrays32() { return kVarArrays32; }
+
+cudaError_t launch_var_to_f32(const double* const* vc, float* const* v32, const Geom* geo, int L, cudaStream_t s) {
+  for (int l = 0; l < L; ++l) {
+    const long long n = var_cells(geo[l]);
+    const long long blocks = std::min<long long>((kVarArrays32 * n + 255) / 256, 152LL * 16);
+    k_var_to_f32<<<(int)blocks, 256, 0, s>>>(vc[l], v32[l], n);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_var_smooth<double>(double*, const double*, const double*, const Geom&, int, bool,
+                                               cudaStream_t);
+template cudaError_t launch_var_smooth<float>(float*, const float*, const float*, const Geom&, int, bool, cudaStream_t);
+template cudaError_t launch_var_resid_restrict<double>(const double*, const double*, const double*, const Geom&,
+                                                       double*, const Geom&, cudaStream_t);
+template cudaError_t launch_var_resid_restrict<float>(const float*, const float*, const float*, const Geom&, float*,
+                                                      const Geom&, cudaStream_t);
+template cudaError_t launch_var_coarse_cg<double>(double*, const double*, const double*, const Geom&, double, int, int*,
+                                                  cudaStream_t);
+template cudaError_t launch_var_coarse_cg<float>(float*, const float*, const float*, const Geom&, double, int, int*,
+                                                 cudaStream_t);
 
 cudaError_t launch_var_set_rhs(double* g, const Geom& G, const double* rho, const double* eps, double h,
                                const FaceBC& bc, cudaStream_t s) {

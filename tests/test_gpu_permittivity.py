@@ -174,13 +174,47 @@ def test_charged_dielectric_spheres_between_plates():
     Pz.close()
 
 
+def test_mixed_precision_weighted_operator():
+    """The single-precision inner cycle on float copies of the weighted coefficients inside the
+    FP64 defect correction: the dielectric-sphere problem reaches 1e-9 by the oracle's residual,
+    the float half-sweep satisfies its rows to float rounding, and the coefficients kept for the
+    outer residual are the FP64 ones."""
+    dims = (64, 48, 56)
+    nx, ny, nz = dims
+    bc = synth.WALL_BC_TYPE
+    bcv = synth.wall_bc_value(1.0)
+    sp = synth.random_spheres(dims, 12, 4.0, 9)
+    vol = oracle.sphere_density((nz, ny, nx), 1.0, sp.centers, sp.radius, np.ones(sp.count), 2)
+    eps = 80.0 - 78.0 * vol
+    rho = oracle.sphere_density((nz, ny, nx), 1.0, sp.centers, sp.radius, sp.density, 2)
+    M = Poisson(dims, bc_type=bc, bc_value=bcv, precision="mixed")
+    M.set_permittivity(gpu(eps))
+    for which in range(4):
+        assert np.array_equal(cpu(M.level_get(1, 2 + which)), oracle.var_coeffs(eps, bc, 1)[which])
+    M.set_rhs(gpu(rho))
+    k, r = M.solve(1e-9, 60)
+    f = oracle.var_rhs(rho, eps, 1.0, bc, bcv)
+    assert r < 1e-9 and oracle.var_rel_residual(cpu(M.solution()), f, eps, 1.0, bc) < 1.0001e-9 and k < 15
+    # a float half-sweep on level 1
+    rng = np.random.default_rng(5)
+    l = 1
+    lx, ly, lz = M.level_dims(l)
+    c = oracle.level_coeff(1.0, l)
+    phi = rng.standard_normal((lz, ly, lx)).astype(np.float32).astype(np.float64)
+    g = (rng.standard_normal((lz, ly, lx)) * c * 40).astype(np.float32).astype(np.float64)
+    M.level_set(l, 0, gpu(phi))
+    M.level_set(l, 1, gpu(g))
+    M.op_smooth(l, 0)
+    got = cpu(M.level_get(l, 0))
+    kk, jj, ii = np.indices(got.shape)
+    res = g - oracle.var_apply(got, eps, 1.0, bc, l)
+    assert np.abs(res[(ii + jj + kk) % 2 == 0]).max() < 1e-5 * np.abs(g).max()
+    M.close()
+
+
 def test_refusals():
     dims = (16, 16, 16)
     eps = gpu(_eps(dims, 3))
-    M = Poisson(dims, precision="mixed")
-    with pytest.raises(MgError):
-        M.set_permittivity(eps)
-    M.close()
     Pz = Poisson(dims)
     Pz.set_permittivity(eps)
     with pytest.raises(MgError):
