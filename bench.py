@@ -551,31 +551,44 @@ def measure_permittivity(w, sp, t64_const, k64_const, hbm):
     nx, ny, nz = w.dims
     N = nx * ny * nz
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="fp64")
-    c, r = dev(sp.centers), dev(sp.radius)
-    vol = P.sphere_density(c, r, torch.ones(sp.count, dtype=torch.float64, device="cuda"), w.subsample)
-    torch.cuda.synchronize()
-    eps = 80.0 - 78.0 * vol
-    torch.cuda.synchronize()
-    P.set_permittivity(eps)
-    rho = P.sphere_density(c, r, dev(sp.density), w.subsample)
-    P.set_rhs(rho)
+    out = {"tol": w.tol, "particle_eps": 2.0, "fluid_eps": 80.0, "constant_eps_fp64_ms": t64_const,
+           "constant_eps_fp64_cycles": k64_const}
+    for prec in ("fp64", "mixed"):
+        P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision=prec)
+        c, r = dev(sp.centers), dev(sp.radius)
+        vol = P.sphere_density(c, r, torch.ones(sp.count, dtype=torch.float64, device="cuda"), w.subsample)
+        torch.cuda.synchronize()
+        eps = 80.0 - 78.0 * vol
+        torch.cuda.synchronize()
+        P.set_permittivity(eps)
+        rho = P.sphere_density(c, r, dev(sp.density), w.subsample)
+        P.set_rhs(rho)
 
-    def solve():
-        P.set_solution(None)
-        return P.solve(w.tol, 300)
+        def solve():
+            P.set_solution(None)
+            return P.solve(w.tol, 300)
 
-    k, rel = solve()
-    t = _time(solve, P.stream, 2)
-    t_sw = _time(lambda: P.op_smooth(0, 0), P.stream, 10)
-    # a half-sweep reads the other colour, its own right-hand side, 1/D and three weights, the
-    # other colour's three weights (the + faces), and writes its colour: 80 B per cell of it
-    bsw = 40.0 * N
-    P.close()
-    return {"tol": w.tol, "cycles": k, "rel_residual": rel, "ms": t, "solve_mlups": N / t / 1e3,
-            "constant_eps_fp64_ms": t64_const, "constant_eps_fp64_cycles": k64_const,
-            "half_sweep_ms": t_sw, "half_sweep_GB/s": bsw / t_sw / 1e6, "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm,
-            "half_sweep_bytes": int(bsw), "particle_eps": 2.0, "fluid_eps": 80.0}
+        k, rel = solve()
+        t = _time(solve, P.stream, 2)
+        d = {"cycles": k, "rel_residual": rel, "ms": t, "solve_mlups": N / t / 1e3}
+        if prec == "fp64":
+            t_sw = _time(lambda: P.op_smooth(0, 0), P.stream, 10)
+            # a half-sweep reads the other colour, its own right-hand side, 1/D and three weights,
+            # the other colour's three weights (the + faces), and writes its colour: 80 B per cell
+            # of it in FP64, 40 B in single precision
+            bsw = 40.0 * N
+            d.update({"half_sweep_ms": t_sw, "half_sweep_GB/s": bsw / t_sw / 1e6,
+                      "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm, "half_sweep_bytes": int(bsw),
+                      "half_sweep_bound": "FP64 pipe (profiles/k_var_smooth_fp64_spheres256.md)"})
+        else:
+            t_sw = _time(lambda: P.op_smooth(0, 0), P.stream, 10)
+            bsw = 20.0 * N
+            d.update({"half_sweep_ms": t_sw, "half_sweep_GB/s": bsw / t_sw / 1e6,
+                      "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm, "half_sweep_bytes": int(bsw)})
+        out[prec] = d
+        P.close()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    return out
 
 
 def measure_pb(w, sp, debye: float = 4.0, charge: float = 4.0):
@@ -591,28 +604,31 @@ def measure_pb(w, sp, debye: float = 4.0, charge: float = 4.0):
     nx, ny, nz = w.dims
     N = nx * ny * nz
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="fp64")
-    c, r = dev(sp.centers), dev(sp.radius)
-    vol = P.sphere_density(c, r, torch.ones(sp.count, dtype=torch.float64, device="cuda"), w.subsample)
-    torch.cuda.synchronize()
-    eps = 80.0 - 78.0 * vol
-    k2 = (1.0 - vol) * (80.0 / debye ** 2)
-    torch.cuda.synchronize()
-    P.set_permittivity(eps)
-    P.set_reaction(k2)
-    rho = P.sphere_density(c, r, dev(sp.density * charge), w.subsample)
+    out = {"tol": w.tol, "debye_length_cells": debye, "charge_scale": charge}
+    for prec in ("fp64", "mixed"):
+        P = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision=prec)
+        c, r = dev(sp.centers), dev(sp.radius)
+        vol = P.sphere_density(c, r, torch.ones(sp.count, dtype=torch.float64, device="cuda"), w.subsample)
+        torch.cuda.synchronize()
+        eps = 80.0 - 78.0 * vol
+        k2 = (1.0 - vol) * (80.0 / debye ** 2)
+        torch.cuda.synchronize()
+        P.set_permittivity(eps)
+        P.set_reaction(k2)
+        rho = P.sphere_density(c, r, dev(sp.density * charge), w.subsample)
 
-    def solve():
-        P.set_rhs(rho)
-        P.set_solution(None)
-        return P.solve_pb(w.tol, 40, 1e-3, 30)
+        def solve():
+            P.set_rhs(rho)
+            P.set_solution(None)
+            return P.solve_pb(w.tol, 40, 1e-3, 30)
 
-    it, rel = solve()
-    t = _time(solve, P.stream, 1)
-    phimax = float(P.solution().abs().max())
-    P.close()
-    return {"tol": w.tol, "newton_steps": it, "rel_residual": rel, "ms": t, "mlups_per_solve": N / t / 1e3,
-            "max_abs_phi_thermal_units": phimax, "debye_length_cells": debye, "charge_scale": charge}
+        it, rel = solve()
+        t = _time(solve, P.stream, 1)
+        out[prec] = {"newton_steps": it, "rel_residual": rel, "ms": t, "mlups_per_solve": N / t / 1e3,
+                     "max_abs_phi_thermal_units": float(P.solution().abs().max())}
+        P.close()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    return out
 
 
 def measure_batched(tol: float = 1e-9):
