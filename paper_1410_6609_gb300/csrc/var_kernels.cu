@@ -24,6 +24,8 @@
 // coefficients agree bit for bit; the cycle kernels are the FP64 cell-by-cell forms of the
 // smoother, the fused residual and restriction, the residual norm and the coarse CG.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "ccmg_internal.cuh"
 #include "level_ops.cuh"
@@ -590,8 +592,13 @@ cudaError_t launch_var_smooth(T* x, const T* g, const T* vc, const Geom& G, int 
   constexpr int V = 16 / sizeof(T);
   dim3 b, gr;
   // single precision: the vector sweep (HBM-bound); double: the per-cell sweep, which the FP64
-  // pipe bounds either way and which keeps more warps resident (measured 1.08 vs 1.17 ms at 512^3)
-  if (sizeof(T) == 4 && G.hx % V == 0) {
+  // pipe bounds either way and which keeps more warps resident (measured 1.08 vs 1.17 ms at 512^3).
+  // CCMG_VAR_SWEEP=cell keeps the per-cell sweep everywhere (for comparing the two).
+  static const bool cell_only = [] {
+    const char* e = std::getenv("CCMG_VAR_SWEEP");
+    return e && std::strcmp(e, "cell") == 0;
+  }();
+  if (sizeof(T) == 4 && G.hx % V == 0 && !cell_only) {
     const int nvec = G.hx / V;
     int bx = 1;
     while (bx < nvec && bx < 128) bx *= 2;

@@ -226,3 +226,34 @@ def test_refusals():
     with pytest.raises(MgError):
         C.level_get(0, 2)  # no permittivity set
     C.close()
+
+
+def test_vector_and_per_cell_float_sweeps_are_bit_identical():
+    """The vectorised single-precision weighted half-sweep against the per-cell one (the process
+    environment selects the per-cell kernel for a child process): identical iterates."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_1410_6609_gb300 import synth\n"
+        "from paper_1410_6609_gb300.solver import Poisson\n"
+        "dims = (64, 48, 40)\n"
+        "rng = np.random.default_rng(8)\n"
+        "eps = np.where(rng.random((40, 48, 64)) < 0.4, 80.0, 1.0)\n"
+        "M = Poisson(dims, bc_type=(2, 2, 1, 1, 0, 0), bc_value=(0, 0, 0, 0, 0, 1), precision='mixed')\n"
+        "M.set_permittivity(torch.from_numpy(eps).cuda())\n"
+        "M.set_rhs(torch.from_numpy(synth.random_field(dims, 3)).cuda())\n"
+        "M.set_solution(None)\n"
+        "M.vcycle(2)\n"
+        "np.save(__import__('sys').argv[1], M.solution().cpu().numpy())\n")
+    import os
+    import tempfile
+    out = []
+    with tempfile.TemporaryDirectory() as d:
+        for mode in ("", "cell"):
+            env = dict(os.environ, CCMG_VAR_SWEEP=mode)
+            path = os.path.join(d, f"phi{mode}.npy")
+            subprocess.run([sys.executable, "-c", code, path], check=True, env=env,
+                           cwd=os.path.dirname(os.path.dirname(__file__)))
+            out.append(np.load(path))
+    assert np.array_equal(out[0], out[1])
