@@ -121,7 +121,7 @@ mg_status mg_set_permittivity(mg_ctx* ctx, const double* d_eps);
 int mg_has_permittivity(const mg_ctx* ctx);
 
 /* Reaction term (the Poisson-Boltzmann equation, which the paper names as the next application
- * of the solver module): d_k2 (device, nx*ny*nz doubles, natural order, >= 0; not checked) gives
+ * of the solver module, Sec. 9): d_k2 (device, nx*ny*nz doubles, natural order, >= 0; not checked) gives
  * per cell k2 (the permittivity over the squared Debye length in the electrolyte, 0 where ions
  * are excluded). The operator becomes -div(eps grad phi) + k2 phi (screened, linearised
  * Poisson-Boltzmann / Debye-Hueckel), with the permittivities of mg_set_permittivity or the
