@@ -19,6 +19,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -81,7 +82,9 @@ class ClockSampler:
         self.proc = None
         self.gpu_index = gpu_index
         self.window = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples (CCMG_CLOCKS_DIR, else the temporary directory); the JSON line carries the summary
+        d = os.environ.get("CCMG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
