@@ -586,8 +586,14 @@ def measure_permittivity(w, sp, t64_const, k64_const, hbm):
         else:
             t_sw = _time(lambda: P.op_smooth(0, 0), P.stream, 10)
             bsw = 20.0 * N
+            # the fused residual and restriction reads both colours' potentials, right-hand
+            # sides, D and three weights (24 B per fine cell) and writes the coarse right-hand side
+            t_rr = _time(lambda: P.op_residual_restrict(0), P.stream, 10)
+            brr = 24.5 * N
             d.update({"half_sweep_ms": t_sw, "half_sweep_GB/s": bsw / t_sw / 1e6,
-                      "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm, "half_sweep_bytes": int(bsw)})
+                      "half_sweep_hbm_frac": bsw / t_sw / 1e6 / hbm, "half_sweep_bytes": int(bsw),
+                      "resid_restrict_ms": t_rr, "resid_restrict_GB/s": brr / t_rr / 1e6,
+                      "resid_restrict_hbm_frac": brr / t_rr / 1e6 / hbm})
         out[prec] = d
         P.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]

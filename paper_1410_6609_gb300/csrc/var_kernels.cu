@@ -359,6 +359,117 @@ __global__ void __launch_bounds__(256) k_var_resid_restrict(const T* __restrict_
   gc[coarse_index(Gc, I, J, K)] = acc * T(0.25);
 }
 
+// The fused residual and restriction for V consecutive coarse cells I0 = V iv .. I0+V-1 of coarse
+// row (J, K) (fine rows of whole vectors): their children in fine row (j, k) are entries I0.. of both
+// colour arrays, so every array is read as one vector per row segment (the x-neighbours beyond
+// the segment as scalars); each child's residual is formed in var_nbsum_packed's order and the
+// 8 summed in the order (dk, dj, di) of k_var_resid_restrict: identical results.
+template <typename T>
+__global__ void __launch_bounds__(256) k_var_resid_restrict_vec(const T* __restrict__ x, const T* __restrict__ g,
+                                                                const T* __restrict__ vc, Geom G,
+                                                                T* __restrict__ gc, Geom Gc) {
+  constexpr int V = 16 / sizeof(T);
+  const int iv = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (iv >= Gc.nx / V || J >= Gc.ny) return;
+  const int I0 = iv * V;
+  const VarW<T> W = var_w(vc, 2 * G.csz);
+  const bool px = (G.per & 1) != 0;
+  T acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = T(0);
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+      const int j = 2 * J + dj, k = 2 * K + dk;
+      const long long row = ((long long)k * G.ny + j) * G.hx;
+      const int c0 = (dj + dk) & 1, c1 = c0 ^ 1;  // colours of the children di = 0 (s = 0) and di = 1 (s = 1)
+      const long long r0 = (long long)c0 * G.csz + row, r1 = (long long)c1 * G.csz + row;
+      T x0[V], x1[V], g0[V], g1[V], D0[V], D1[V], wx0[V], wx1[V], wy0[V], wy1[V], wz0[V], wz1[V];
+      ops::load_vec(x + r0 + I0, x0);
+      ops::load_vec(x + r1 + I0, x1);
+      ops::load_vec(g + r0 + I0, g0);
+      ops::load_vec(g + r1 + I0, g1);
+      ops::load_vec(W.D + r0 + I0, D0);
+      ops::load_vec(W.D + r1 + I0, D1);
+      ops::load_vec(W.wx + r0 + I0, wx0);
+      ops::load_vec(W.wx + r1 + I0, wx1);
+      ops::load_vec(W.wy + r0 + I0, wy0);
+      ops::load_vec(W.wy + r1 + I0, wy1);
+      ops::load_vec(W.wz + r0 + I0, wz0);
+      ops::load_vec(W.wz + r1 + I0, wz1);
+      // x-neighbours beyond the segment: cell 2 I0 - 1 (colour c1, index I0 - 1) and cell 2 (I0+V)
+      // (colour c0, index I0 + V) with the weight of its face
+      T left = T(0), right = T(0), wright = T(0);
+      const bool hl = I0 > 0 || px, hr = I0 + V < G.hx || px;
+      if (I0 > 0) left = __ldg(x + r1 + I0 - 1);
+      else if (px) left = __ldg(x + r1 + G.hx - 1);
+      if (I0 + V < G.hx) {
+        right = __ldg(x + r0 + I0 + V);
+        wright = __ldg(W.wx + r0 + I0 + V);
+      } else if (px) {
+        right = __ldg(x + r0);
+        wright = __ldg(W.wx + r0);
+      }
+      const bool hym = nb_has<0, true>(G, j, k), hyp = nb_has<1, true>(G, j, k);
+      const bool hzm = nb_has<2, true>(G, j, k), hzp = nb_has<3, true>(G, j, k);
+      // neighbour rows of both colours (child di = 0 reads colour c1's, di = 1 colour c0's), and
+      // the + face weights stored there
+      T ym0[V], ym1[V], yp0[V], yp1[V], zm0[V], zm1[V], zp0[V], zp1[V], wyp0[V], wyp1[V], wzp0[V], wzp1[V];
+      if (hym) {
+        const long long o = nb_off<0, true>(G, j, k);
+        ops::load_vec(x + r0 + I0 + o, ym0);
+        ops::load_vec(x + r1 + I0 + o, ym1);
+      }
+      if (hyp) {
+        const long long o = nb_off<1, true>(G, j, k);
+        ops::load_vec(x + r0 + I0 + o, yp0);
+        ops::load_vec(x + r1 + I0 + o, yp1);
+        ops::load_vec(W.wy + r0 + I0 + o, wyp0);
+        ops::load_vec(W.wy + r1 + I0 + o, wyp1);
+      }
+      if (hzm) {
+        const long long o = nb_off<2, true>(G, j, k);
+        ops::load_vec(x + r0 + I0 + o, zm0);
+        ops::load_vec(x + r1 + I0 + o, zm1);
+      }
+      if (hzp) {
+        const long long o = nb_off<3, true>(G, j, k);
+        ops::load_vec(x + r0 + I0 + o, zp0);
+        ops::load_vec(x + r1 + I0 + o, zp1);
+        ops::load_vec(W.wz + r0 + I0 + o, wzp0);
+        ops::load_vec(W.wz + r1 + I0 + o, wzp1);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        // child di = 0 (colour c0, s = 0): -x at index m-1 of c1, +x at index m of c1
+        T S = T(0);
+        if (v > 0) S = fmat(wx0[v], x1[v - 1], S);
+        else if (hl) S = fmat(wx0[v], left, S);
+        S = fmat(wx1[v], x1[v], S);
+        if (hym) S = fmat(wy0[v], ym1[v], S);
+        if (hyp) S = fmat(wyp1[v], yp1[v], S);
+        if (hzm) S = fmat(wz0[v], zm1[v], S);
+        if (hzp) S = fmat(wzp1[v], zp1[v], S);
+        acc[v] = acc[v] + fmat(-D0[v], x0[v], g0[v] + S);
+        // child di = 1 (colour c1, s = 1): -x at index m of c0, +x at index m+1 of c0
+        S = T(0);
+        S = fmat(wx1[v], x0[v], S);
+        if (v < V - 1) S = fmat(wx0[v + 1], x0[v + 1], S);
+        else if (hr) S = fmat(wright, right, S);
+        if (hym) S = fmat(wy1[v], ym0[v], S);
+        if (hyp) S = fmat(wyp0[v], yp0[v], S);
+        if (hzm) S = fmat(wz1[v], zm0[v], S);
+        if (hzp) S = fmat(wzp0[v], zp0[v], S);
+        acc[v] = acc[v] + fmat(-D1[v], x1[v], g1[v] + S);
+      }
+    }
+#pragma unroll
+  for (int v = 0; v < V; ++v) gc[coarse_index(Gc, I0 + v, J, K)] = acc[v] * T(0.25);
+}
+
 // Scaled residual of every cell with per-block partial sums of its square; MODE 1: also the
 // residual field r = r~ c0 in natural order; MODE 2: also float(r~ isc) in the level's order (the
 // right-hand side of the single-precision inner cycle, by exponent arithmetic when isc is a power
@@ -617,7 +728,21 @@ cudaError_t launch_var_smooth(T* x, const T* g, const T* vc, const Geom& G, int 
 template <typename T>
 cudaError_t launch_var_resid_restrict(const T* x, const T* g, const T* vc, const Geom& G, T* gc, const Geom& Gc,
                                       cudaStream_t s) {
+  constexpr int V = 16 / sizeof(T);
   dim3 b, gr;
+  static const bool cell_only = [] {
+    const char* e = std::getenv("CCMG_VAR_SWEEP");
+    return e && std::strcmp(e, "cell") == 0;
+  }();
+  if (sizeof(T) == 4 && G.hx % V == 0 && !cell_only) {  // single precision: the vector form
+    const int nvec = Gc.nx / V;
+    int bx = 1;
+    while (bx < nvec && bx < 64) bx *= 2;
+    b = dim3(bx, 256 / bx, 1);
+    gr = dim3((nvec + bx - 1) / bx, (Gc.ny + b.y - 1) / b.y, Gc.nz);
+    k_var_resid_restrict_vec<T><<<gr, b, 0, s>>>(x, g, vc, G, gc, Gc);
+    return cudaGetLastError();
+  }
   shape2(Gc.nx, Gc.ny, Gc.nz, b, gr);
   k_var_resid_restrict<T><<<gr, b, 0, s>>>(x, g, vc, G, gc, Gc);
   return cudaGetLastError();
