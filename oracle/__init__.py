@@ -89,6 +89,7 @@ def _load():
                 "ccmg_or_var_coeffs": (None, [P, P, D, I, I, I, P, D, I, P, P, P, P]),
                 "ccmg_or_var_apply": (None, [P, P, P, P, I, I, I, D, P, D, I]),
                 "ccmg_or_var_rhs": (None, [P, P, P, I, I, I, D, P, P]),
+                "ccmg_or_var_rhs_adjoint": (None, [P, P, P, P, I, I, I, D, P]),
                 "ccmg_or_var_vcycles": (None, [P, P, P, P, I, I, I, D, P, I, I, D, I]),
                 "ccmg_or_var_solve": (I, [P, P, P, P, I, I, I, D, P, I, I, D, D, I, P]),
                 "ccmg_or_var_rel_residual": (D, [P, P, P, P, I, I, I, D, P]),
@@ -463,6 +464,15 @@ def var_rhs(rho, eps, h: float, bc_type, bc_value) -> np.ndarray:
     f = np.empty_like(rho)
     _load().ccmg_or_var_rhs(_p(rho), _p(eps), _p(f), *_dims(rho), h, _p(_bc(bc_type)), _p(_f64(bc_value)))
     return f
+
+
+def var_rhs_adjoint(lam, eps, h: float, bc_type):
+    """Adjoint of var_rhs: (dJ/drho = lambda, dJ/dbc_value per face)."""
+    lam, eps = _f64(lam), _f64(eps)
+    grho = np.empty_like(lam)
+    gbc = np.zeros(6)
+    _load().ccmg_or_var_rhs_adjoint(_p(lam), _p(eps), _p(grho), _p(gbc), *_dims(lam), h, _p(_bc(bc_type)))
+    return grho, gbc
 
 
 def var_vcycles(phi, f, eps, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2, omega: float = 2.0,

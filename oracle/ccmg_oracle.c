@@ -1277,3 +1277,21 @@ double ccmg_or_pb_residual(const double* phi, const double* f, const double* eps
   var_free(&V0);
   return fn > 0.0 ? Fn / fn : Fn;
 }
+
+/* Adjoint of ccmg_or_var_rhs: given lambda = dJ/df, dJ/drho = lambda and dJ/dbc_value[q] = the sum
+ * over the face-q cells of lambda * (2 eps / h^2 Dirichlet, eps / h Neumann; periodic: none). */
+void ccmg_or_var_rhs_adjoint(const double* lam, const double* eps, double* grho, double* gbc, int nx, int ny, int nz,
+                             double h, const int* bc) {
+  for (int q = 0; q < 6; ++q) gbc[q] = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t p = idx3(i, j, k, nx, ny);
+        grho[p] = lam[p];
+        const int on_face[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, k == 0, k == nz - 1};
+        for (int q = 0; q < 6; ++q) {
+          if (!on_face[q] || bc[q] == BC_PERIODIC) continue;
+          gbc[q] = gbc[q] + lam[p] * (bc[q] == BC_DIRICHLET ? 2.0 * eps[p] / (h * h) : eps[p] / h);
+        }
+      }
+}

@@ -888,3 +888,21 @@ def test_pb_gouy_chapman_second_order():
         z = (np.arange(nz) + 0.5) * h
         errs.append(np.abs(phi[:, 0, 0] - gc(z)).max())
     assert errs[0] < 2e-2 and 3.0 < errs[0] / errs[1] < errs[1] / errs[2] < 4.2  # the rate approaches 4
+
+
+def test_var_rhs_adjoint_is_the_transpose():
+    """<lambda, var_rhs(rho, g)> is linear in (rho, g): its gradient by var_rhs_adjoint equals the
+    explicit derivatives (random directions, exact in floating point up to rounding)."""
+    dims = (8, 6, 10)
+    nx, ny, nz = dims
+    bc = (D, N, PER, PER, N, D)
+    rng = np.random.default_rng(4)
+    eps = 1.0 + rng.random((nz, ny, nx)) * 5.0
+    lam = rng.standard_normal((nz, ny, nx))
+    h = 0.5
+    grho, gbc = oracle.var_rhs_adjoint(lam, eps, h, bc)
+    rho = rng.standard_normal((nz, ny, nx))
+    g = rng.standard_normal(6)
+    J = lambda r, v: float(np.sum(lam * oracle.var_rhs(r, eps, h, bc, v)))  # noqa: E731
+    assert abs(J(rho, g) - (np.sum(grho * rho) + np.dot(gbc, g))) < 1e-10 * max(1.0, abs(J(rho, g)))
+    assert np.all(gbc[2:4] == 0.0)  # periodic faces have no value
