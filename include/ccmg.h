@@ -113,8 +113,7 @@ mg_status mg_set_bc_field(mg_ctx* ctx, int face, const double* d_values);
  * MG_MIXED mode the inner cycle uses single-precision copies of the coefficients, the outer
  * residual and update stay FP64). NULL returns to the constant permittivity of mg_params.
  * Errors: MG_ERR_OOM if the coefficients (7 doubles, and 5 floats in MG_MIXED mode, per cell and
- * level) cannot be allocated. mg_rhs_adjoint refuses a context with a variable permittivity
- * (its adjoint differs). */
+ * level) cannot be allocated. */
 mg_status mg_set_permittivity(mg_ctx* ctx, const double* d_eps);
 /* 1 if the weighted operator is active (a variable permittivity or a reaction term is set), 0
  * otherwise (and for a NULL context). */
@@ -211,7 +210,9 @@ mg_status mg_force_gather(mg_ctx* ctx, int P, const double* d_centers, const dou
  *     explicit density factor, d_gbc (6, device) = dJ/dbc_value through the ghost values.
  *   mg_sphere_density_adjoint: d_gdensity[s] = sum_b w_{s,b} d_gfield[b].
  *   mg_rhs_adjoint: given lambda = dJ/df, d_grho = lambda / eps and d_gbc (6, device) =
- *     sum over each face's cells of lambda * (2/h^2 Dirichlet, 1/h Neumann, 0 periodic). */
+ *     sum over each face's cells of lambda * (2/h^2 Dirichlet, 1/h Neumann, 0 periodic); with the
+ *     weighted operator (mg_set_permittivity / mg_set_reaction), f = rho plus eps-weighted wall
+ *     terms, so d_grho = lambda and the face sums take lambda * (2 eps/h^2 or eps/h). */
 mg_status mg_force_gather_adjoint(mg_ctx* ctx, int P, const double* d_centers, const double* d_radius,
                                   const double* d_density, int sf, const double* d_wF, double* d_gphi,
                                   double* d_gdensity, double* d_gbc);

@@ -947,8 +947,8 @@ mg_status mg_sphere_density_adjoint(mg_ctx* c, int P, const double* ctr, const d
 mg_status mg_rhs_adjoint(mg_ctx* c, const double* d_lam, double* d_grho, double* d_gbc) {
   if (!c) return MG_ERR_INVALID;
   if (!d_lam || !d_grho || !d_gbc) return fail(c, MG_ERR_INVALID, "null argument");
-  if (c->d_eps) return fail(c, MG_ERR_INVALID, "the right-hand-side adjoint is for a constant permittivity");
-  CK(launch_rhs_adjoint(c->geo[0], c->p.h, 1.0 / c->p.eps, c->bc, d_lam, d_grho, d_gbc, c->stream), "rhs_adjoint");
+  CK(launch_rhs_adjoint(c->geo[0], c->p.h, 1.0 / c->p.eps, c->bc, c->d_eps, d_lam, d_grho, d_gbc, c->stream),
+     "rhs_adjoint");
   c->launches += 2;
   return MG_OK;
 }

@@ -236,8 +236,8 @@ cudaError_t launch_force_adjoint(const double* x, const Geom& G, double h, const
                                  const double* wF, double* gphi, double* gdens, double* gbc, cudaStream_t s);
 cudaError_t launch_density_adjoint(const Geom& G, double h, const Spheres& sp, int sf, const double* gfield,
                                    double* gdens, cudaStream_t s);
-cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* lam,
-                               double* grho, double* gbc, cudaStream_t s);
+cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* eps,
+                               const double* lam, double* grho, double* gbc, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------------
 // Batched launches over many independent systems of different sizes. One entry describes one

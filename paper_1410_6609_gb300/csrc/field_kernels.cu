@@ -470,8 +470,9 @@ __global__ void __launch_bounds__(256) k_scale_copy(const double* __restrict__ a
 
 // Six CTAs, one per wall: gbc[q] = sum over the wall's cells of lambda * (2/h^2 or 1/h); a
 // periodic face has no value (0).
+// With cell permittivities eps (the weighted operator): the sum of lambda * (2 eps/h^2 or eps/h).
 __global__ void __launch_bounds__(256) k_face_sums(Geom G, double h, FaceBC bc, const double* __restrict__ lam,
-                                                   double* __restrict__ gbc) {
+                                                   const double* __restrict__ eps, double* __restrict__ gbc) {
   __shared__ double red[32][3];
   const int q = blockIdx.x;
   const int a = q >> 1;
@@ -485,10 +486,13 @@ __global__ void __launch_bounds__(256) k_face_sums(Geom G, double h, FaceBC bc, 
     p[a] = fix;
     p[u] = (int)(t % n[u]);
     p[v] = (int)(t / n[u]);
-    acc[0] = acc[0] + lam[nat(G, p[0], p[1], p[2])];
+    const long long o = nat(G, p[0], p[1], p[2]);
+    if (eps) acc[0] = acc[0] + lam[o] * (bc.type[q] == 0 ? 2.0 * eps[o] / (h * h) : eps[o] / h);
+    else acc[0] = acc[0] + lam[o];
   }
   block_sum3(acc, red);
-  if (threadIdx.x == 0) gbc[q] = bc.type[q] == 2 ? 0.0 : acc[0] * (bc.type[q] == 0 ? 2.0 / (h * h) : 1.0 / h);
+  if (threadIdx.x == 0)
+    gbc[q] = bc.type[q] == 2 ? 0.0 : (eps ? acc[0] : acc[0] * (bc.type[q] == 0 ? 2.0 / (h * h) : 1.0 / h));
 }
 
 SubOff make_suboff(int sf) {
@@ -582,15 +586,15 @@ cudaError_t launch_density_adjoint(const Geom& G, double h, const Spheres& sp, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* lam,
-                               double* grho, double* gbc, cudaStream_t s) {
+cudaError_t launch_rhs_adjoint(const Geom& G, double h, double inv_eps, const FaceBC& bc, const double* eps,
+                               const double* lam, double* grho, double* gbc, cudaStream_t s) {
   const long long N = (long long)G.nx * G.ny * G.nz;
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_scale_copy<<<(int)blocks, 256, 0, s>>>(lam, grho, N, inv_eps);
+  k_scale_copy<<<(int)blocks, 256, 0, s>>>(lam, grho, N, eps ? 1.0 : inv_eps);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_face_sums<<<6, 256, 0, s>>>(G, h, bc, lam, gbc);
+  k_face_sums<<<6, 256, 0, s>>>(G, h, bc, lam, eps, gbc);
   return cudaGetLastError();
 }
 
