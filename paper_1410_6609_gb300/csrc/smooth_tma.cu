@@ -37,11 +37,12 @@ __host__ __device__ constexpr int round128(int b) { return ((b + 127) / 128) * 1
 // Tile of TY rows (one per thread row), ring of SLOTS plane slots. PRO: the black sweep fused
 // with the prolongation; each slot then also holds the coarse-correction rows (both coarse
 // colour arrays) under the other-colour box.
-template <int TY, int SLOTS, bool PRO = false>
+template <int TY, int SLOTS, bool PRO = false, bool PER = false>
 struct Cfg {
   static constexpr int kTY = TY;
   static constexpr int kSlots = SLOTS;
   static constexpr bool kPro = PRO;
+  static constexpr bool kPer = PER;  // levels with periodic axes: wrapped halos (the walls-only build keeps its registers)
   static constexpr int kBoxY = TY + 2;
   static constexpr int kBoxBytes = kBoxX * kBoxY * 4;                  // other-colour box
   static constexpr int kGBoxBytes = 4 * kTX * TY * 4;                  // right-hand-side box
@@ -59,6 +60,7 @@ struct Cfg {
   static_assert(TY % 2 == 0, "tiles cover whole coarse rows");
 };
 using Product = Cfg<8, 6>;           // 9600-byte slots, 57.6 KB per CTA, 3 CTAs per SM
+using ProductPer = Cfg<8, 6, false, true>;  // the same on levels with a periodic axis
 using ProductPro = Cfg<8, 5, true>;  // 13184-byte slots, 65.9 KB per CTA, 3 CTAs per SM (6 slots: 2 per SM, slower)
 // the fused sweep reads the other colour through the plain sweep's tensor maps, whose boxes are
 // Product::kBoxY rows high: the expected transaction bytes must match them
@@ -172,7 +174,9 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
       const unsigned dst = ring0 + (unsigned)(q * kSlotBytes);
       const bool with_rhs = i >= 2;
       mbar_expect_tx(bar, kBoxBytes + (with_rhs ? kGBoxBytes : 0) + (C::kPro ? 2 * kCBoxBytes : 0));
-      tma_load_box(dst, &other, t.x0 - kHaloX, t.y0 - 1, t.k0 - 1 + i, bar);
+      int kp = t.k0 - 1 + i;  // other-colour plane; across a periodic z axis the opposite one
+      if (C::kPer && (G.per & 4)) kp = kp < 0 ? G.nz - 1 : (kp >= G.nz ? kp - G.nz : kp);
+      tma_load_box(dst, &other, t.x0 - kHaloX, t.y0 - 1, kp, bar);
       if (with_rhs) tma_load_box(dst + kGOff, &rhs, t.x0, t.y0, t.k0 - 2 + i, bar);
       if (C::kPro) {
         const int kc = (t.k0 - 1 + i + 2) / 2 - 1;  // floor(p / 2) for red plane p >= -1
@@ -197,6 +201,7 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
     // walls touched by this thread's cells in every plane but the first and last (x and y);
     // without any, every cell's diagonal is 6
     const bool xy_wall = j == 0 || j == G.ny - 1 || (m0 == 0) || (m0 + 4 >= G.hx);
+    const int hxe_col = (G.hx - t.x0 + kHaloX < kBoxX) ? G.hx - t.x0 + kHaloX : -1;
     // PRO: red plane p in slot q becomes red + omega e_c(parent) in place. The parent of the red
     // cell at packed index m of fine row (j', p) is coarse cell (m, j'/2, p/2), of colour
     // (m + j'/2 + p/2) & 1 at packed index m >> 1; its coarse row sits in box row
@@ -224,6 +229,50 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
         *v = r;
       }
     };
+    // Periodic x / y axes: the copy engine fills the box beyond the level with zeros; the halo
+    // values the sweep reads there (the row beyond each end of the tile's rows, and the rows
+    // beyond the level's first and last row) are the other colour's values at the opposite side,
+    // loaded here into the landed plane before the barrier that publishes it. p: the plane.
+    auto patch = [&](int q, int p) {
+      float* slot = ring + q * (kSlotBytes / 4);
+      int pw = p;
+      if (G.per & 4) pw = pw < 0 ? G.nz - 1 : (pw >= G.nz ? pw - G.nz : pw);
+      if (pw < 0 || pw >= G.nz) return;  // a wall plane: zeros are right
+      const float* src = x + (long long)(1 - colour) * G.csz + (long long)pw * G.ny * G.hx;
+      const int nt = kTX * kTY, tid = ty * kTX + tx;
+      const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0;
+      // the rows beyond the level's first and last row: box row 0 holds row y0-1 (row -1 for the
+      // first tile), box row ny-y0+1 holds row ny when it lies in the box (the last tile, ragged
+      // or not)
+      if (py) {
+        const int rlo = t.y0 == 0 ? 0 : -1, rhi = G.ny - t.y0 + 1 < C::kBoxY ? G.ny - t.y0 + 1 : -1;
+        for (int f = tid; f < 2 * kBoxX; f += nt) {
+          const int r = f < kBoxX ? rlo : rhi;
+          if (r < 0) continue;
+          const int col = f < kBoxX ? f : f - kBoxX;
+          const int sy = f < kBoxX ? G.ny - 1 : 0;
+          int gx = t.x0 - kHaloX + col;
+          if (px) gx = gx < 0 ? gx + G.hx : (gx >= G.hx ? gx - G.hx : gx);
+          slot[r * kBoxX + col] = (gx >= 0 && gx < G.hx) ? __ldg(src + (long long)sy * G.hx + gx) : 0.0f;
+        }
+      }
+      // the column beyond each end of the tile's rows (box columns kHaloX-1 and hx-x0+kHaloX), in
+      // the rows of the level the box holds (the wrapped rows above need only their own columns)
+      if (px) {
+        const int rc = hxe_col;  // box column of global column hx, or -1 outside the box
+        for (int f = tid; f < 2 * C::kBoxY; f += nt) {
+          const int r = f % C::kBoxY;
+          const bool left = f < C::kBoxY;
+          const int gy = t.y0 - 1 + r;
+          if (gy < 0 || gy >= G.ny) continue;
+          if (left) {
+            if (t.x0 == 0) slot[r * kBoxX + kHaloX - 1] = __ldg(src + (long long)gy * G.hx + G.hx - 1);
+          } else if (rc >= 0) {
+            slot[r * kBoxX + rc] = __ldg(src + (long long)gy * G.hx);
+          }
+        }
+      }
+    };
     for (int k = t.k0; k < t.k1; ++k) {
       const int i = k - t.k0 + 1;  // load index of plane k (k-1 is i-1; k+1 and g(k) are i+1)
       bool ok = true;
@@ -232,6 +281,15 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
         ok = ok && mbar_wait(bar0 + 8u * (unsigned)qk, (unsigned)(((seq + 1) / kSlots) & 1), budget);
       }
       ok = ok && mbar_wait(bar0 + 8u * (unsigned)qp, php, budget);
+      if constexpr (C::kPer) {  // the fused sweep (PRO) is not run on periodic levels
+        if (ok && (G.per & 3)) {
+          if (k == t.k0) {
+            patch(qm, k - 1);
+            patch(qk, k);
+          }
+          patch(qp, k + 1);
+        }
+      }
       if constexpr (C::kPro) {
         // red planes k-1 and k arrived with the item's first plane, k+1 just now: add the
         // prolongated correction to them in place, once, before any cell reads them
@@ -323,9 +381,9 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
 }  // namespace
 
 bool tma_sweep_applies(const Geom& G) {
-  // rows of whole 4-float vectors and enough planes to march; no periodic axis (the staged tiles
-  // take zero beyond the walls, where a periodic axis needs the opposite side's values)
-  return G.packed && G.per == 0 && (G.hx % 4) == 0 && G.nz >= 8 && (long long)G.hx * G.ny * G.nz >= (1LL << 16);
+  // rows of whole 4-float vectors and enough planes to march (periodic axes: the kernel loads the
+  // wrapped halos itself)
+  return G.packed && (G.hx % 4) == 0 && G.nz >= 8 && (long long)G.hx * G.ny * G.nz >= (1LL << 16);
 }
 
 bool tma_sweep_pays(const Geom& G) {
@@ -412,7 +470,10 @@ cudaError_t prepare_tma_sweep_cfg(TmaSweep& t, float* x, const float* g, const G
 template <class C>
 cudaError_t prepare_tma_prolong_cfg(TmaSweep& t, const float* ec, const Geom& Gc, const Geom& G, int device) {
   t.ok_pro = 0;
-  if (!t.ok || !Gc.packed || (Gc.hx % 4) != 0 || Gc.hx * 2 != G.hx || Gc.ny * 2 != G.ny || Gc.nz * 2 != G.nz)
+  // the fused prolongation sweep takes the plain sweep's zero halos; periodic levels keep the
+  // separate direct-load fused sweep
+  if (!t.ok || G.per != 0 || !Gc.packed || (Gc.hx % 4) != 0 || Gc.hx * 2 != G.hx || Gc.ny * 2 != G.ny ||
+      Gc.nz * 2 != G.nz)
     return cudaSuccess;
   EncodeFn encode = nullptr;
   cudaError_t e = encoder(&encode);
@@ -440,7 +501,8 @@ cudaError_t launch_smooth_tma_cfg(float* x, const Geom& G, const InvDiag<float>&
 }  // namespace
 
 cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom& G, int device) {
-  return prepare_tma_sweep_cfg<Product>(t, x, g, G, device);
+  return G.per ? prepare_tma_sweep_cfg<ProductPer>(t, x, g, G, device)
+               : prepare_tma_sweep_cfg<Product>(t, x, g, G, device);
 }
 
 cudaError_t prepare_tma_prolong(TmaSweep& t, const float* ec, const Geom& Gc, const Geom& G, int device) {
@@ -449,7 +511,8 @@ cudaError_t prepare_tma_prolong(TmaSweep& t, const float* ec, const Geom& Gc, co
 
 cudaError_t launch_smooth_tma(float* x, const Geom& G, const InvDiag<float>& inv, int colour, const TmaSweep& t,
                               int* err, cudaStream_t s) {
-  return launch_smooth_tma_cfg<Product>(x, G, inv, colour, t, err, kWaitCycles, -1, s);
+  return G.per ? launch_smooth_tma_cfg<ProductPer>(x, G, inv, colour, t, err, kWaitCycles, -1, s)
+               : launch_smooth_tma_cfg<Product>(x, G, inv, colour, t, err, kWaitCycles, -1, s);
 }
 
 cudaError_t launch_smooth_prolong_tma(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t,

@@ -163,15 +163,17 @@ def test_periodic_adjoint_kernels_match_oracle():
     Pz.close()
 
 
-def test_periodic_mixed_precision_reaches_tolerance_and_skips_the_staged_sweep():
-    """Mixed precision to 1e-9 (checked by the oracle's residual); with the staged half-sweep
-    requested on every level, the periodic levels keep the direct-load kernel and give the same
-    result."""
-    dims = (64, 64, 64)
-    bc = (P, P, P, P, D, D)
-    bcv = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+@pytest.mark.parametrize("dims,bc", [((64, 64, 64), (P, P, P, P, D, D)), ((64, 60, 64), (D, N, P, P, P, P)),
+                                     ((72, 40, 48), (P, P, D, N, P, P))])
+def test_periodic_mixed_precision_and_the_staged_sweep(dims, bc):
+    """Mixed precision to 1e-9 (checked by the oracle's residual); with the TMA-staged half-sweep
+    requested on every level it can run on, the periodic levels take it (wrapped halo rows, columns
+    and planes loaded into the staged tiles; ragged tiles in y for 60 rows) and give the same
+    iterates as the direct-load sweep."""
+    nx, ny, nz = dims
+    bcv = (0.0, 0.0, 0.0, 0.0, 0.0, 1.0) if bc[5] == D else (0.0, 0.5, 0.0, 0.2, 0.0, 0.0)
     sp = synth.random_spheres(dims, 20, 4.0, 17)
-    rho = oracle.sphere_density((64, 64, 64), 1.0, sp.centers, sp.radius, sp.density, 2, bc)
+    rho = oracle.sphere_density((nz, ny, nx), 1.0, sp.centers, sp.radius, sp.density, 2, bc)
     f = oracle.rhs(rho, 1.0, bc, bcv)
     Pz = Poisson(dims, bc_type=bc, bc_value=bcv, precision="mixed")
     Pz.set_rhs(gpu(rho))
@@ -181,6 +183,7 @@ def test_periodic_mixed_precision_reaches_tolerance_and_skips_the_staged_sweep()
     assert oracle.rel_residual(phi, f, 1.0, bc) < 1.0001e-9
     ref64, _, _ = oracle.solve(f, 1.0, bc, tol=1e-12)
     assert rel(phi, ref64) < 1e-7
+    assert Pz.level_sweep_kind(0) == "vec"  # too small for the staged sweep by default
     old = os.environ.get("CCMG_SWEEP")
     os.environ["CCMG_SWEEP"] = "tma"
     try:
@@ -191,10 +194,21 @@ def test_periodic_mixed_precision_reaches_tolerance_and_skips_the_staged_sweep()
             del os.environ["CCMG_SWEEP"]
         else:
             os.environ["CCMG_SWEEP"] = old
-    assert Pt.level_sweep_kind(0) == "vec" and Pw.level_sweep_kind(0) == "tma"
+    assert Pt.level_sweep_kind(0) == "tma" and Pw.level_sweep_kind(0) == "tma"
     Pt.set_rhs(gpu(rho))
     assert Pt.solve(1e-9, 50) == (k, r)
     assert torch.equal(Pt.solution(), Pz.solution())
+    # the staged half-sweep on its own against the direct-load one, both colours
+    phi0 = synth.random_field(dims, 5).astype(np.float32).astype(np.float64)
+    g0 = (synth.random_field(dims, 6) * 0.1).astype(np.float32).astype(np.float64)
+    for colour in (0, 1):
+        outs = []
+        for ctx in (Pt, Pz):
+            ctx.level_set(0, 0, gpu(phi0))
+            ctx.level_set(0, 1, gpu(g0))
+            ctx.op_smooth(0, colour)
+            outs.append(cpu(ctx.level_get(0, 0)))
+        assert np.array_equal(outs[0], outs[1]), colour
     for ctx in (Pz, Pt, Pw):
         ctx.close()
 
