@@ -230,48 +230,63 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
       }
     };
     // Periodic x / y axes: the copy engine fills the box beyond the level with zeros; the halo
-    // values the sweep reads there (the row beyond each end of the tile's rows, and the rows
-    // beyond the level's first and last row) are the other colour's values at the opposite side,
-    // loaded here into the landed plane before the barrier that publishes it. p: the plane.
-    auto patch = [&](int q, int p) {
-      float* slot = ring + q * (kSlotBytes / 4);
-      int pw = p;
-      if (G.per & 4) pw = pw < 0 ? G.nz - 1 : (pw >= G.nz ? pw - G.nz : pw);
-      if (pw < 0 || pw >= G.nz) return;  // a wall plane: zeros are right
-      const float* src = x + (long long)(1 - colour) * G.csz + (long long)pw * G.ny * G.hx;
+    // values the sweep reads there (the column beyond each end of the tile's rows, and the rows
+    // beyond the level's first and last row) are the other colour's values at the opposite side.
+    // Each thread owns at most three of them (two of the wrapped rows, one of the columns): their
+    // box positions (hidx) and offsets within a plane (hoff, -1: zero) are fixed for the tile, the
+    // values of plane k+2 are loaded while plane k is computed and written into its slot after it
+    // lands, before the barrier that publishes it.
+    int hidx[3] = {-1, -1, -1};
+    int hoff[3] = {-1, -1, -1};  // within a plane: ny * hx entries
+    float hval[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (C::kPer) {
       const int nt = kTX * kTY, tid = ty * kTX + tx;
       const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0;
-      // the rows beyond the level's first and last row: box row 0 holds row y0-1 (row -1 for the
-      // first tile), box row ny-y0+1 holds row ny when it lies in the box (the last tile, ragged
-      // or not)
-      if (py) {
+      if (py) {  // box row 0 holds row -1 for the first tile, box row ny-y0+1 holds row ny
         const int rlo = t.y0 == 0 ? 0 : -1, rhi = G.ny - t.y0 + 1 < C::kBoxY ? G.ny - t.y0 + 1 : -1;
-        for (int f = tid; f < 2 * kBoxX; f += nt) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int f = tid + u * nt;
+          if (f >= 2 * kBoxX) continue;
           const int r = f < kBoxX ? rlo : rhi;
           if (r < 0) continue;
           const int col = f < kBoxX ? f : f - kBoxX;
           const int sy = f < kBoxX ? G.ny - 1 : 0;
           int gx = t.x0 - kHaloX + col;
           if (px) gx = gx < 0 ? gx + G.hx : (gx >= G.hx ? gx - G.hx : gx);
-          slot[r * kBoxX + col] = (gx >= 0 && gx < G.hx) ? __ldg(src + (long long)sy * G.hx + gx) : 0.0f;
+          hidx[u] = r * kBoxX + col;
+          hoff[u] = (gx >= 0 && gx < G.hx) ? sy * G.hx + gx : -1;
         }
       }
-      // the column beyond each end of the tile's rows (box columns kHaloX-1 and hx-x0+kHaloX), in
-      // the rows of the level the box holds (the wrapped rows above need only their own columns)
-      if (px) {
-        const int rc = hxe_col;  // box column of global column hx, or -1 outside the box
-        for (int f = tid; f < 2 * C::kBoxY; f += nt) {
-          const int r = f % C::kBoxY;
-          const bool left = f < C::kBoxY;
-          const int gy = t.y0 - 1 + r;
-          if (gy < 0 || gy >= G.ny) continue;
-          if (left) {
-            if (t.x0 == 0) slot[r * kBoxX + kHaloX - 1] = __ldg(src + (long long)gy * G.hx + G.hx - 1);
-          } else if (rc >= 0) {
-            slot[r * kBoxX + rc] = __ldg(src + (long long)gy * G.hx);
+      if (px && tid < 2 * C::kBoxY) {  // box columns kHaloX-1 (x0 = 0) and hx-x0+kHaloX (in the box)
+        const int r = tid % C::kBoxY;
+        const bool left = tid < C::kBoxY;
+        const int gy = t.y0 - 1 + r;
+        if (gy >= 0 && gy < G.ny) {
+          if (left && t.x0 == 0) {
+            hidx[2] = r * kBoxX + kHaloX - 1;
+            hoff[2] = gy * G.hx + G.hx - 1;
+          } else if (!left && hxe_col >= 0) {
+            hidx[2] = r * kBoxX + hxe_col;
+            hoff[2] = gy * G.hx;
           }
         }
       }
+    }
+    const float* const oth_base = x + (long long)(1 - colour) * G.csz;
+    auto gather = [&](int p) {  // the halo values of plane p (zeros for a wall plane)
+      int pw = p;
+      if (G.per & 4) pw = pw < 0 ? G.nz - 1 : (pw >= G.nz ? pw - G.nz : pw);
+      const bool in = pw >= 0 && pw < G.nz;
+      const float* src = oth_base + (long long)(in ? pw : 0) * G.ny * G.hx;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) hval[u] = (hidx[u] >= 0 && hoff[u] >= 0 && in) ? __ldg(src + hoff[u]) : 0.0f;
+    };
+    auto scatter = [&](int q) {
+      float* slot = ring + q * (kSlotBytes / 4);
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (hidx[u] >= 0) slot[hidx[u]] = hval[u];
     };
     for (int k = t.k0; k < t.k1; ++k) {
       const int i = k - t.k0 + 1;  // load index of plane k (k-1 is i-1; k+1 and g(k) are i+1)
@@ -283,11 +298,15 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
       ok = ok && mbar_wait(bar0 + 8u * (unsigned)qp, php, budget);
       if constexpr (C::kPer) {  // the fused sweep (PRO) is not run on periodic levels
         if (ok && (G.per & 3)) {
-          if (k == t.k0) {
-            patch(qm, k - 1);
-            patch(qk, k);
+          if (k == t.k0) {  // the item's first three planes: loaded here
+            gather(k - 1);
+            scatter(qm);
+            gather(k);
+            scatter(qk);
+            gather(k + 1);
           }
-          patch(qp, k + 1);
+          scatter(qp);                     // plane k+1 (loaded during the previous plane)
+          if (k + 1 < t.k1) gather(k + 2);  // in flight while plane k is computed
         }
       }
       if constexpr (C::kPro) {
@@ -389,8 +408,9 @@ bool tma_sweep_applies(const Geom& G) {
 bool tma_sweep_pays(const Geom& G) {
   // measured on GB300: ahead of the direct-load kernel at 512^3 (2^25 cells per colour), even at
   // 256^3, behind below that (too few tiles to keep every SM's copies in flight). Not on periodic
-  // levels: their wrapped halos are global loads whose latency each plane's barrier exposes (the
-  // periodic 512^3 time step took 17.9 ms with it against 13.7 ms with the direct-load sweep)
+  // levels: with their wrapped halo values (loaded a plane ahead) the kernel holds 88 registers
+  // and two CTAs per SM, and the periodic 512^3 time step took 14.9 ms with it against 13.7 ms
+  // with the direct-load sweep
   return tma_sweep_applies(G) && G.per == 0 && (long long)G.hx * G.ny * G.nz >= (1LL << 24);
 }
 
