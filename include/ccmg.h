@@ -344,7 +344,9 @@ long long mg_batch_kernel_launches(const mg_batch* b);
  * sums per z-plane. Every GPU that loads the library holds it until the process exits. Limits:
  * nz <= 4096 (larger nz returns MG_ERR_INVALID before anything is enqueued), nx, ny >= 1, h > 0.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current) and caches it; make that first call before any stream capture. Every
+ * that device current) and caches it with the current CUDA context; a later call under another
+ * context of the device (after cudaDeviceReset, or a driver-API context) looks it up again. Make
+ * the first call under each context before any stream capture. Every
  * call shares the one array: each call overwrites the partials of its own planes before
  * reading them (nothing needs to start at zero), but calls whose kernels overlap on the GPU
  * (different streams, or different host threads on one device) race on it and give wrong

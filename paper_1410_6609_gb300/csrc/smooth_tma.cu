@@ -95,6 +95,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long lo
     if (clock64() - t0 > budget) return false;
   }
 }
+// Orders this thread's earlier generic-proxy writes to shared memory before later accesses by the
+// async proxy (the tensor copies that refill the same ring slots). Without it a late plain store
+// of a slot could land after the copy that reuses the slot.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tma_load_box(unsigned dst, const CUtensorMap* map, int x, int y, int z,
                                              unsigned bar) {
   asm volatile(
@@ -240,6 +244,9 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
     int hoff[3] = {-1, -1, -1};  // within a plane: ny * hx entries
     float hval[3] = {0.0f, 0.0f, 0.0f};
     if constexpr (C::kPer) {
+      // every wrapped halo row value has a slot (two per thread) and every column value a thread
+      static_assert(kBoxX <= kTX * C::kTY, "two wrapped halo rows need kBoxX <= threads per CTA");
+      static_assert(2 * C::kBoxY <= kTX * C::kTY, "the wrapped halo columns need 2 kBoxY <= threads per CTA");
       const int nt = kTX * kTY, tid = ty * kTX + tx;
       const bool px = (G.per & 1) != 0, py = (G.per & 2) != 0;
       if (py) {  // box row 0 holds row -1 for the first tile, box row ny-y0+1 holds row ny
@@ -320,6 +327,11 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
           correct(qp, k + 1);
         }
       }
+      // plain stores into ring slots (wrapped halos, corrected planes) are ordered before the
+      // tensor copies that will refill those slots
+      if constexpr (C::kPro) fence_proxy_async_smem();
+      else if constexpr (C::kPer)
+        if (G.per & 3) fence_proxy_async_smem();
       // the barrier also retires iteration k-1 (and publishes the corrected planes), freeing the
       // slot of load i-2 for load i+kSlots-2
       if (__syncthreads_or(!ok)) {

@@ -11,8 +11,13 @@
 // The array below is part of the module: every GPU that loads libccmg holds it (64 KiB) until
 // the process exits, whether or not this entry point is called. Host code cannot use the
 // array's name as a device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it.
+// cudaGetSymbolAddress (with that device current) and caches it together with the CUDA context
+// it belongs to: the address is a property of the context, so a call made under another context
+// of the same device (after cudaDeviceReset, or under a context the caller created with the
+// driver API) looks it up again instead of using a stale address.
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/ccmg.h"
 
@@ -26,7 +31,11 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) double g_plane_partials[2 * kStaticMaxPlanes];
 
 std::mutex g_mu;
-double* g_scratch[kMaxDevices] = {};
+struct ScratchAddr {
+  CUcontext ctx;   // context the address was looked up in
+  double* ptr;     // device address of g_plane_partials there
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
 // One block per z-plane: r = f - A_0 phi in natural order (Sec. 2.4 stencil with the walls
 // folded in, periodic axes wrapping around), partial sums of r^2 and f^2 for the plane, fixed reduction order.
@@ -89,19 +98,44 @@ __global__ void k_plane_finalize(const double* __restrict__ partials, int nz, do
   out[1] = rn;
 }
 
-// Device address of g_plane_partials on the current device, looked up once per device.
+// The current CUDA context (cuCtxGetCurrent, fetched from the driver at run time so that the
+// library does not link against libcuda).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+mg_status current_context(CUcontext* out) {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return MG_ERR_CUDA;
+    fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  *out = nullptr;
+  return fn(out) == CUDA_SUCCESS && *out ? MG_OK : MG_ERR_CUDA;  // null: no context current
+}
+
+// Device address of g_plane_partials on the current device, looked up once per device and
+// context (set-up on the first call, with that device current).
 mg_status scratch_for_current_device(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MG_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return MG_ERR_INVALID;
+  CUcontext ctx = nullptr;
+  mg_status st = current_context(&ctx);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_plane_partials);
-    if (e != cudaSuccess || !ptr) return MG_ERR_CUDA;
-    g_scratch[dev] = (double*)ptr;
+  if (st == MG_OK && g_scratch[dev].ptr && g_scratch[dev].ctx == ctx) {
+    *out = g_scratch[dev].ptr;
+    return MG_OK;
   }
-  *out = g_scratch[dev];
+  // first call under this context (or no context current yet: the lookup initialises the
+  // runtime's primary context of the device, which is then the current one)
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_plane_partials);
+  if (e != cudaSuccess || !ptr) return MG_ERR_CUDA;
+  if ((st = current_context(&ctx)) != MG_OK) return st;
+  g_scratch[dev] = ScratchAddr{ctx, (double*)ptr};
+  *out = (double*)ptr;
   return MG_OK;
 }
 
