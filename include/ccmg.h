@@ -220,6 +220,22 @@ mg_status mg_sphere_density_adjoint(mg_ctx* ctx, int P, const double* d_centers,
                                     int sf, const double* d_gfield, double* d_gdensity);
 mg_status mg_rhs_adjoint(mg_ctx* ctx, const double* d_lambda, double* d_grho, double* d_gbc);
 
+/* Adjoint solve (not in the paper; derived from Eq. ElectrostatForce and the wall terms of
+ * Sec. 2.4): for J depending on phi = A^-1 f, dJ/df = lambda with A^T lambda = dJ/dphi. The
+ * operator is symmetric (the folded 7-point stencil, its Galerkin coarse operators, and the
+ * weighted operator of mg_set_permittivity / mg_set_reaction alike), so lambda solves
+ * A lambda = g with homogeneous walls by the same multigrid: d_g (device, nx*ny*nz doubles,
+ * natural order) is taken as the right-hand side as it is (no 1/eps, no wall terms), the
+ * iteration starts from zero and runs Algorithm 1 to rel_tol (at most max_cycles cycles), and
+ * lambda is written to d_lambda (device, nx*ny*nz doubles). The wall values of the forward
+ * problem are neither read nor changed; the context's right-hand side and solution are replaced
+ * (they hold g and lambda afterwards). Feed lambda to mg_rhs_adjoint for dJ/drho and dJ/dwall.
+ * h_cycles / h_rel_res (host, may be NULL) receive the cycle count and final relative residual.
+ * Returns the status of the solve (MG_ERR_NOT_CONVERGED with lambda written if the tolerance was
+ * missed), MG_ERR_INVALID for null pointers, a negative tolerance or max_cycles. Synchronises. */
+mg_status mg_adjoint_solve(mg_ctx* ctx, const double* d_g, double* d_lambda, double rel_tol, int max_cycles,
+                           int* h_cycles, double* h_rel_res);
+
 /* One electrostatics step with HOST buffers (Algorithm 1, the potential part): copy the
  * spheres in, set the right-hand side from their subsampled charge, solve to rel_tol from the
  * current solution (warm start), compute the force on every sphere and copy it out.
@@ -251,6 +267,17 @@ mg_status mg_op_residual_restrict(mg_ctx* ctx, int level);
 mg_status mg_op_residual_restrict_red(mg_ctx* ctx, int level);
 /* phi_l += cgc_weight * constant prolongation of phi_{l+1}. */
 mg_status mg_op_prolong_correct(mg_ctx* ctx, int level);
+/* The first black post-smoothing half-sweep of the single-precision cycle, fused with the
+ * prolongation of the coarse correction (Sec. 3): every black cell of level l becomes the
+ * half-sweep value computed from the red neighbours corrected by cgc_weight * phi_{l+1}(parent),
+ * i.e. the black cells of mg_op_prolong_correct followed by mg_op_smooth(level, 1). The red cells
+ * are left as they were, uncorrected (the cycle's next red half-sweep recomputes every one of
+ * them). Available where the cycle runs it: MG_MIXED, constant permittivity, levels with rows of
+ * whole 4-float vectors (nx a multiple of 8); MG_ERR_INVALID elsewhere.
+ * mg_level_prolong_sweep_kind tells which kernel runs it: 1 the TMA-staged one, 0 the
+ * direct-load one, -1 where the operation is not available. */
+mg_status mg_op_prolong_smooth(mg_ctx* ctx, int level);
+int mg_level_prolong_sweep_kind(const mg_ctx* ctx, int level);
 /* CG on the coarsest level: phi_L = A_L^-1 f_L (rtol 1e-14, at most 2 N_L iterations);
  * h_iters (may be NULL) receives the iteration count. Synchronises. */
 mg_status mg_op_coarse_solve(mg_ctx* ctx, int* h_iters);

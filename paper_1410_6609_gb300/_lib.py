@@ -69,6 +69,7 @@ SIGNATURES = {
     "mg_force_gather_adjoint": (_I, [_P, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
     "mg_sphere_density_adjoint": (_I, [_P, _I, _P, _P, _I, _P, _P]),
     "mg_rhs_adjoint": (_I, [_P, _P, _P, _P]),
+    "mg_adjoint_solve": (_I, [_P, _P, _P, _D, _I, _P, _P]),
     "mg_step_host": (_I, [_P, _I, _P, _P, _P, _I, _D, _I, _P, _P, _P]),
     "mg_level_set": (_I, [_P, _I, _I, _P]),
     "mg_level_get": (_I, [_P, _I, _I, _P]),
@@ -76,6 +77,8 @@ SIGNATURES = {
     "mg_op_residual_restrict": (_I, [_P, _I]),
     "mg_op_residual_restrict_red": (_I, [_P, _I]),
     "mg_op_prolong_correct": (_I, [_P, _I]),
+    "mg_op_prolong_smooth": (_I, [_P, _I]),
+    "mg_level_prolong_sweep_kind": (_I, [_P, _I]),
     "mg_op_coarse_solve": (_I, [_P, _P]),
     "mg_op_residual_norm": (_I, [_P]),
     "mg_op_scale_convert": (_I, [_P, _P, _P, ctypes.c_longlong, _D, _P, _P, _P, _P]),

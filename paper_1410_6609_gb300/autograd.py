@@ -49,10 +49,7 @@ class PoissonSolve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gphi):
         P = ctx.solver
-        P.set_rhs_f(gphi.contiguous())
-        P.set_solution(None)
-        P.solve(ctx.tol, ctx.max_cycles)
-        lam = P.solution()
+        lam, _, _ = P.adjoint_solve(gphi.contiguous(), ctx.tol, ctx.max_cycles)
         grho, gbc = P.rhs_adjoint(lam)
         return grho, gbc, None, None, None
 

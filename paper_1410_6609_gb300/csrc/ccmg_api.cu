@@ -953,6 +953,22 @@ mg_status mg_rhs_adjoint(mg_ctx* c, const double* d_lam, double* d_grho, double*
   return MG_OK;
 }
 
+mg_status mg_adjoint_solve(mg_ctx* c, const double* d_g, double* d_lambda, double tol, int max_cycles, int* h_cycles,
+                           double* h_rel) {
+  if (!c) return MG_ERR_INVALID;
+  if (!d_g || !d_lambda) return fail(c, MG_ERR_INVALID, "null argument");
+  if (!(tol >= 0.0) || max_cycles < 0) return fail(c, MG_ERR_INVALID, "need tol >= 0 and max_cycles >= 0");
+  // the adjoint system has homogeneous walls: g is the right-hand side as it is (the wall values
+  // of the forward problem are neither read nor changed)
+  mg_status st = mg_set_rhs_f(c, d_g);
+  if (st != MG_OK) return st;
+  if ((st = mg_set_solution(c, nullptr)) != MG_OK) return st;
+  const mg_status solve_st = mg_solve(c, tol, max_cycles, h_cycles, h_rel);
+  if (solve_st != MG_OK && solve_st != MG_ERR_NOT_CONVERGED) return solve_st;
+  if ((st = mg_get_solution(c, d_lambda)) != MG_OK) return st;
+  return solve_st;
+}
+
 mg_status mg_step_host(mg_ctx* c, int P, const double* h_ctr, const double* h_rad, const double* h_dens, int sf,
                        double tol, int max_cycles, double* h_F, int* h_cycles, double* h_rel) {
   if (!c) return MG_ERR_INVALID;
@@ -1086,6 +1102,33 @@ static mg_status residual_restrict_op(mg_ctx* c, int level, bool red_only) {
 
 mg_status mg_op_residual_restrict(mg_ctx* c, int level) { return residual_restrict_op(c, level, false); }
 mg_status mg_op_residual_restrict_red(mg_ctx* c, int level) { return residual_restrict_op(c, level, true); }
+
+mg_status mg_op_prolong_smooth(mg_ctx* c, int level) {
+  if (!c) return MG_ERR_INVALID;
+  if (level < 0 || level >= c->L - 1) return fail(c, MG_ERR_INVALID, "prolongation needs a non-coarsest level");
+  const Geom& G = c->geo[level];
+  if (!mixed(c) || c->d_eps || !G.packed || G.hx % 4 != 0)
+    return fail(c, MG_ERR_INVALID,
+                "the fused prolongation sweep runs on single-precision levels of the constant operator with rows of "
+                "whole 4-float vectors");
+  if (c->tma[level].ok_pro)
+    CK(launch_smooth_prolong_tma(c->x32[level], G, c->inv32, c->tma[level], (float)c->p.cgc_weight, c->d_err,
+                                 c->stream),
+       "prolong_smooth");
+  else
+    CK(launch_smooth_prolong(c->x32[level], c->g32[level], G, c->inv32, c->x32[level + 1], c->geo[level + 1],
+                             (float)c->p.cgc_weight, c->stream),
+       "prolong_smooth");
+  c->launches += 1;
+  return MG_OK;
+}
+
+int mg_level_prolong_sweep_kind(const mg_ctx* c, int level) {
+  if (!c || level < 0 || level >= c->L - 1) return -1;
+  const Geom& G = c->geo[level];
+  if (!mixed(c) || c->d_eps || !G.packed || G.hx % 4 != 0) return -1;
+  return c->tma[level].ok_pro ? 1 : 0;
+}
 
 mg_status mg_op_prolong_correct(mg_ctx* c, int level) {
   if (c && !mixed(c) && level == 0) c->phi_zero = false;

@@ -281,6 +281,19 @@ class Poisson:
         self._check(self.lib.mg_rhs_adjoint(self.ctx, _ptr(lam), _ptr(grho), _ptr(gbc)), "mg_rhs_adjoint")
         return grho, gbc
 
+    def adjoint_solve(self, g, tol: float = 1e-10, max_cycles: int = 100, out=None, raise_on_fail: bool = True):
+        """lambda with A lambda = g, homogeneous walls, from zero (mg_adjoint_solve). Returns
+        (lambda, cycles, relative residual); the context then holds g and lambda."""
+        g = self._field(g, "g")
+        out = self.new_field() if out is None else out
+        k = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = self.lib.mg_adjoint_solve(self.ctx, _ptr(g), _ptr(out), float(tol), int(max_cycles), ctypes.byref(k),
+                                       ctypes.byref(rel))
+        if raise_on_fail:
+            self._check(st, "mg_adjoint_solve")
+        return out, k.value, rel.value
+
     def step_host(self, centers: np.ndarray, radius: np.ndarray, density: np.ndarray, sf: int = 2,
                   tol: float = 1e-10, max_cycles: int = 100, forces: np.ndarray | None = None):
         """One electrostatics step through host buffers (see mg_step_host); tol < 0 runs exactly
@@ -322,6 +335,18 @@ class Poisson:
 
     def op_prolong_correct(self, level: int):
         self._check(self.lib.mg_op_prolong_correct(self.ctx, level), "mg_op_prolong_correct")
+
+    def op_prolong_smooth(self, level: int):
+        """The cycle's first black post-sweep fused with the prolongation (mg_op_prolong_smooth):
+        black cells swept from the corrected red values, red cells left uncorrected."""
+        self._check(self.lib.mg_op_prolong_smooth(self.ctx, level), "mg_op_prolong_smooth")
+
+    def prolong_sweep_kind(self, level: int) -> str:
+        """'tma' or 'vec': the kernel of the fused prolongation sweep (mg_level_prolong_sweep_kind)."""
+        k = self.lib.mg_level_prolong_sweep_kind(self.ctx, level)
+        if k < 0:
+            raise ValueError(f"no fused prolongation sweep on level {level}")
+        return "tma" if k == 1 else "vec"
 
     def op_residual_norm(self):
         self._check(self.lib.mg_op_residual_norm(self.ctx), "mg_op_residual_norm")

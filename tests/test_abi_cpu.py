@@ -77,6 +77,7 @@ def test_null_context_is_invalid():
     lib = _lib.load()
     assert lib.mg_vcycle(None, 1) == _lib.MG_ERR_INVALID
     assert lib.mg_solve(None, 1e-10, 10, None, None) == _lib.MG_ERR_INVALID
+    assert lib.mg_adjoint_solve(None, None, None, 1e-10, 10, None, None) == _lib.MG_ERR_INVALID
     assert lib.mg_destroy(None) == _lib.MG_ERR_INVALID
     assert lib.mg_num_levels(None) == 0
 

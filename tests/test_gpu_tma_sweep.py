@@ -1,4 +1,5 @@
-"""The TMA-staged single-precision half-sweep against the vectorised direct-load half-sweep.
+"""The TMA-staged single-precision half-sweep against the vectorised direct-load half-sweep and
+against the oracle.
 
 Both evaluate phi_i = (g_i + sum of neighbours) / (6 + d_i) with the same operands in the same
 order, so they must agree bit for bit. The TMA kernel marches tiles of 128 x 8 cells through
@@ -6,8 +7,8 @@ z-slabs, with the other colour's planes copied into shared memory by tensor-map 
 out-of-range elements (the walls) arrive as zeros. The grids here make every edge case of that
 scheme occur: rows shorter than a tile and not a multiple of it, row counts that leave a partial
 tile, plane counts that leave a partial slab, and mixed Dirichlet/Neumann walls (every diagonal
-shift). The vectorised kernel is itself checked against the oracle's single-precision sweep in
-test_gpu_parity.py.
+shift). Both kernels are also checked against the oracle's single-precision sweep, the TMA one
+below at the sizes where the cycle runs it (plain, periodic and fused with the prolongation).
 """
 from __future__ import annotations
 
@@ -17,6 +18,8 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -138,3 +141,121 @@ def test_tma_solve_bit_identical(dims, tma_levels):
     assert torch.equal(out[0][2], out[1][2])
     a.close()
     b.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# The TMA-staged sweeps against the oracle directly (Sec. 5.3: red-black Gauss-Seidel), at sizes
+# where they are the kernel the cycle runs. Both sides round in float; the GPU multiplies by
+# 1/(6+d) where the oracle divides, so they agree to a few float ulps (1e-6 relative, the bound of
+# the direct-load sweep's oracle test in test_gpu_parity.py).
+
+F32_TOL = 1e-6
+PER = 2
+
+
+def _maxrel(a, b):
+    m = np.abs(b).max()
+    return np.abs(a - b).max() / (m if m > 0 else 1.0)
+
+
+def _f32_fields(dims, seed, fscale=3.0):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    phi = rng.standard_normal((nz, ny, nx), dtype=np.float32)
+    f = rng.standard_normal((nz, ny, nx), dtype=np.float32) * np.float32(fscale)
+    return phi, f
+
+
+def _check_sweeps_against_oracle(P, phi, f, bc, colours):
+    """Each half-sweep from the same state, then the whole sequence from the oracle's own states."""
+    dev = lambda a: torch.from_numpy(a.astype(np.float64)).cuda()  # noqa: E731
+    c = oracle.level_coeff(1.0, 0)
+    for colour in (0, 1):
+        P.level_set(0, 0, dev(phi))
+        P.level_set(0, 1, dev(f))
+        P.op_smooth(0, colour)
+        err = _maxrel(P.level_get(0, 0).cpu().numpy(), oracle.rbgs_half_f32(phi, f, c, bc, colour))
+        assert err < F32_TOL, (colour, err)
+    P.level_set(0, 0, dev(phi))
+    ref = phi
+    for colour in colours:
+        P.op_smooth(0, colour)
+        ref = oracle.rbgs_half_f32(ref, f, c, bc, colour)
+    err = _maxrel(P.level_get(0, 0).cpu().numpy(), ref)
+    assert err < 4 * F32_TOL, err
+
+
+def test_tma_sweep_against_oracle_where_the_cycle_uses_it():
+    """512 x 256 x 256: 2^24 cells per colour, the size from which the default policy stages the
+    finest level's sweeps by TMA (the headline workload's finest-level kernel)."""
+    from paper_1410_6609_gb300.solver import Poisson
+
+    dims = (512, 256, 256)
+    P = Poisson(dims, precision="mixed", bc_type=BC_MIX, bc_value=(0.0, 1.0, -0.5, 0.25, 0.0, 2.0))
+    assert P.level_sweep_kind(0) == "tma"
+    phi, f = _f32_fields(dims, 41)
+    _check_sweeps_against_oracle(P, phi, f, BC_MIX, (0, 1, 1, 0))
+    P.close()
+
+
+@pytest.mark.parametrize("dims,bc", [
+    ((520, 16, 16), (PER, PER, PER, PER, D, D)),    # three x tiles, the last one ragged
+    ((528, 12, 40), (PER, PER, N, D, D, N)),        # three x tiles, a partial tile in y
+    ((264, 40, 72), (N, D, PER, PER, PER, PER)),    # periodic y and z, a partial slab
+])
+def test_periodic_tma_sweep_against_oracle(dims, bc):
+    """The staged sweep on periodic levels (selected by CCMG_SWEEP=tma): wrapped halo rows,
+    columns and planes loaded by the threads, with tiles starting beyond x = 0 so that the left
+    halo comes through the tensor copy and the wrapped column sits at the last tile's end. Also
+    bit-identical to the direct-load sweep."""
+    a, b = _pair(dims, bc_type=bc)
+    assert a.level_sweep_kind(0) == "tma" and b.level_sweep_kind(0) == "vec"
+    phi, f = _f32_fields(dims, sum(dims))
+    _check_sweeps_against_oracle(a, phi, f, bc, (0, 1, 0, 1))
+    dev = lambda v: torch.from_numpy(v.astype(np.float64)).cuda()  # noqa: E731
+    for P in (a, b):
+        P.level_set(0, 0, dev(phi))
+        P.level_set(0, 1, dev(f))
+    for colour in (0, 1, 1, 0):
+        a.op_smooth(0, colour)
+        b.op_smooth(0, colour)
+        assert torch.equal(a.level_get(0, 0), b.level_get(0, 0)), colour
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("dims,policy", [((512, 256, 256), None), ((272, 48, 40), "tma")])
+def test_fused_prolongation_sweep_against_oracle(dims, policy):
+    """The first black post-sweep fused with the prolongation (Sec. 3: phi += 2 P e_c, then the
+    black half-sweep), on the TMA-staged kernel: its black cells against the oracle's
+    prolong_correct_f32 followed by rbgs_half_f32, its red cells untouched."""
+    from paper_1410_6609_gb300.solver import Poisson
+
+    bc = (N, N, N, N, D, D)
+    P = _with_sweep(policy, dims, bc_type=bc) if policy else Poisson(dims, precision="mixed", bc_type=bc)
+    assert P.prolong_sweep_kind(0) == "tma"
+    nx, ny, nz = dims
+    phi, f = _f32_fields(dims, 43)
+    rng = np.random.default_rng(44)
+    ec = rng.standard_normal((nz // 2, ny // 2, nx // 2), dtype=np.float32) * np.float32(0.1)
+    dev = lambda v: torch.from_numpy(v.astype(np.float64)).cuda()  # noqa: E731
+    P.level_set(0, 0, dev(phi))
+    P.level_set(0, 1, dev(f))
+    P.level_set(1, 0, dev(ec))
+    P.op_prolong_smooth(0)
+    out = P.level_get(0, 0).cpu().numpy()
+    ref = oracle.rbgs_half_f32(oracle.prolong_correct_f32(phi, ec, 2.0), f, 1.0, bc, 1)
+    kk, jj, ii = np.indices(phi.shape)
+    black = (ii + jj + kk) % 2 == 1
+    assert _maxrel(out[black], ref[black]) < F32_TOL
+    assert np.array_equal(out[~black], phi[~black].astype(np.float64))
+    # the direct-load fused sweep gives the same bits
+    Q = _with_sweep("vec", dims, bc_type=bc)
+    assert Q.prolong_sweep_kind(0) == "vec"
+    Q.level_set(0, 0, dev(phi))
+    Q.level_set(0, 1, dev(f))
+    Q.level_set(1, 0, dev(ec))
+    Q.op_prolong_smooth(0)
+    assert np.array_equal(Q.level_get(0, 0).cpu().numpy()[black], out[black])
+    P.close()
+    Q.close()
