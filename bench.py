@@ -49,11 +49,15 @@ def parse():
 
 
 def workload_config(w, rank_seed_offset=0):
+    if w.sphere_count:
+        source = (f"{w.sphere_count} spheres R={w.sphere_radius:g} (N(0,1) charge, zero sum, subsampling "
+                  f"{w.subsample}), phi=0/1 on z walls, Neumann 0 on x/y")
+    else:
+        source = "f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) on the unit cube, homogeneous Dirichlet walls"
     return {
-        "workload": f"{w.name}: {w.dims[0]}x{w.dims[1]}x{w.dims[2]} cells, {w.sphere_count} spheres R={w.sphere_radius:g} "
-                    f"(N(0,1) charge, zero sum, subsampling {w.subsample}), phi=0/1 on z walls, Neumann 0 on x/y, "
+        "workload": f"{w.name}: {w.dims[0]}x{w.dims[1]}x{w.dims[2]} cells, {source}, "
                     f"{'FP32 V(2,2) inside FP64 defect correction' if w.precision == 'mixed' else 'FP64 V(2,2)'} "
-                    f"to {w.tol:g} relative residual from zero, then E-field and forces",
+                    f"to {w.tol:g} relative residual from zero, then E-field{' and forces' if w.sphere_count else ''}",
         "grid": list(w.dims),
         "spheres": w.sphere_count,
         "tol": w.tol,
@@ -152,47 +156,75 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-# CPU oracle timings (bounded samples)
+# CPU oracle timings (whole steps on the host cores)
 
-def oracle_sample(w, cycles_needed: int):
-    """Time the oracle on a bounded sample of the workload: density, RHS, one outer cycle, one
-    residual, forces; project the time of the whole step with the cycle count of the solve."""
+def host_threads() -> int:
+    return os.cpu_count() or 1
+
+
+def oracle_step(w, sp, threads: int):
+    """One whole step of the oracle on workload w, the same work as one GPU step: subsampled
+    sphere density, right-hand side with the wall terms, solve from zero to the workload's
+    tolerance in its precision (FP32 V(2,2)-cycles inside FP64 defect correction for 'mixed'),
+    E-field and forces. Returns (seconds, details, phi, f)."""
     import oracle
+    used = oracle.set_threads(threads)
     nx, ny, nz = w.dims
-    sp = w.spheres()
     t0 = time.perf_counter()
-    rho = oracle.sphere_density((nz, ny, nx), w.h, sp.centers, sp.radius, sp.density, w.subsample)
-    f = oracle.rhs(rho, w.h, w.bc_type, w.bc_value)
-    t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    rel = oracle.rel_residual(np.zeros_like(f), f, w.h, w.bc_type)
-    t_res = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    if w.precision == "mixed":
-        phi, k, _ = oracle.solve_mixed(f, w.h, w.bc_type, tol=0.0, max_cycles=1)
-    else:
-        phi, k, _ = oracle.solve(f, w.h, w.bc_type, tol=0.0, max_cycles=1)
-    t_one = time.perf_counter() - t0  # 2 residuals + 1 cycle
-    t_cycle = max(t_one - 2 * t_res, 0.0)
-    t0 = time.perf_counter()
-    oracle.force_gather(phi, w.h, w.bc_type, w.bc_value, sp.centers, sp.radius, sp.density, w.subsample)
-    t_force = time.perf_counter() - t0
-    t_step = t_setup + (cycles_needed + 1) * t_res + cycles_needed * t_cycle + t_force
-    N = nx * ny * nz
-    return {
-        "value": N / t_step / 1e6,
-        "unit": "MLUP/s",
-        "cores": 1,
-        "kind": "oracle",
-        "sample": (f"oracle (plain C, 1 thread) on the full {nx}x{ny}x{nz} workload: density+RHS {t_setup:.2f}s, "
-                   f"one residual {t_res:.2f}s, one {'outer mixed' if w.precision == 'mixed' else 'V(2,2)'} cycle "
-                   f"{t_cycle:.2f}s, forces {t_force:.2f}s; step time projected with the GPU solve's "
-                   f"{cycles_needed} cycles = {t_step:.1f}s"),
-        "t_step_s": t_step,
-        "rel0": rel,
-    }
+    if w.sphere_count:
+        rho = oracle.sphere_density((nz, ny, nx), w.h, sp.centers, sp.radius, sp.density, w.subsample, w.bc_type)
+        f = oracle.rhs(rho, w.h, w.bc_type, w.bc_value)
+    else:  # the manufactured solution: the analytic right-hand side, homogeneous walls
+        f = synth.manufactured_rhs(nx)[0]
+    t1 = time.perf_counter()
+    solve = oracle.solve_mixed if w.precision == "mixed" else oracle.solve
+    phi, k, rel = solve(f, w.h, w.bc_type, tol=w.tol, max_cycles=100)
+    t2 = time.perf_counter()
+    oracle.efield(phi, w.h, w.bc_type, w.bc_value)
+    if w.sphere_count:
+        oracle.force_gather(phi, w.h, w.bc_type, w.bc_value, sp.centers, sp.radius, sp.density, w.subsample)
+    t3 = time.perf_counter()
+    info = {"threads": used, "density_rhs_s": round(t1 - t0, 3), "solve_s": round(t2 - t1, 3),
+            "efield_forces_s": round(t3 - t2, 3), "cycles": k, "rel_residual": rel}
+    return t3 - t0, info, phi, f
 
 
+def oracle_adjoint_step(w, sp, threads: int):
+    """The adjoint workload on the oracle: J = sum of z-forces and its gradient with respect to
+    the sphere densities and the wall values (forward solve, force adjoint, one adjoint solve)."""
+    import oracle
+    used = oracle.set_threads(threads)
+    nx, ny, nz = w.dims
+    wF = np.zeros((sp.count, 3))
+    wF[:, 2] = 1.0
+    t0 = time.perf_counter()
+    J, gq, gv, info = oracle.force_objective_and_grad((nz, ny, nx), w.h, w.bc_type, w.bc_value, sp.centers,
+                                                      sp.radius, sp.density, wF, w.subsample, tol=w.tol)
+    return time.perf_counter() - t0, {"threads": used, "cycles": list(info["cycles"]), "dJ_dV_top": float(gv[5])}
+
+
+def oracle_baseline(w, sp, steps: int = 2):
+    """cpu_baseline of the GPU arm: whole oracle steps of the bench workload on all host cores
+    (a bounded sample of `steps` steps), the last step's potential and right-hand side kept for
+    comparing the GPU solution with."""
+    threads = host_threads()
+    times, info, phi, f = [], None, None, None
+    for _ in range(steps):
+        t, info, phi, f = oracle_step(w, sp, threads)
+        times.append(t)
+    t_step = statistics.mean(times)
+    N = int(np.prod(w.dims))
+    nx, ny, nz = w.dims
+    cb = {"value": N / t_step / 1e6, "unit": "MLUP/s", "cores": info["threads"], "kind": "oracle",
+          "sample": (f"{steps} whole oracle steps (plain C, OpenMP over z-planes, {info['threads']} threads) on the "
+                     f"full {nx}x{ny}x{nz} workload: density+RHS, {w.precision} solve from zero to {w.tol:g} "
+                     f"({info['cycles']} {'outer steps' if w.precision == 'mixed' else 'cycles'}), E-field, forces; "
+                     f"{t_step:.2f} s per step"),
+          "ms_per_step": t_step * 1e3, "last_step": info}
+    return cb, phi, f
+
+
+# ------------------------------------------------------------------------------------------
 # ------------------------------------------------------------------------------------------
 
 def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
@@ -211,34 +243,70 @@ def whole_job_mlups(cells_per_rank: int, world: int, ms: float) -> float:
     return world * cells_per_rank / (ms / 1e3) / 1e6
 
 
+def parallelism(world: int) -> str:
+    return "single" if world <= 1 else f"replicas{world}"
+
+
 def run_reference(args):
-    """The oracle on the host cores, on the same workload and metric (bounded per-step sample)."""
+    """The oracle on the host cores: the same workload, metric and config as the GPU arm, each
+    step one whole oracle step (density, RHS, solve to the tolerance, E-field, forces) on all host
+    threads; warm-up steps run the same work untimed. Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     w = workload(args)
-    # cycles of the solve to tolerance measured on the GPU (mixed: outer steps of mixed_inner = 4 cycles)
-    cycles = {"spheres512": 3, "spheres384": 3, "spheres256": 11, "adjoint256": 11, "manufactured32": 11}.get(w.name, 10)
-    for _ in range(min(args.warmup, 1)):
-        pass
-    samples = []
+    sp = w.spheres()
+    threads = host_threads()
+    for _ in range(args.warmup):
+        oracle_step(w, sp, threads)
+    times = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        samples.append(oracle_sample(w, cycles))
+        t, info, _, _ = oracle_step(w, sp, threads)
+        times.append(t)
     wall = time.perf_counter() - t_all
-    t_step = statistics.mean(s["t_step_s"] for s in samples)
+    t_step = statistics.mean(times)
     N = int(np.prod(w.dims))
     value = N / t_step / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f64+f32",
-        "data": "synthetic", "config": workload_config(w),
-        "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
-                         "sample": samples[0]["sample"] + f"; {args.steps} samples in {wall:.1f}s"},
+        "data": "synthetic", "config": {**workload_config(w), "parallelism": parallelism(world)},
+        "cycles_per_step": info["cycles"], "final_rel_residual": info["rel_residual"],
+        "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": info["threads"], "kind": "oracle",
+                         "sample": (f"{args.steps} whole oracle steps (after {args.warmup} untimed) on all "
+                                    f"{info['threads']} host threads in {wall:.1f} s; last step {info}")},
         "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if not args.no_extras:
+        line["oracle_extras"] = reference_extras(w, sp, threads)
     print(json.dumps(line), flush=True)
+
+
+def reference_extras(w, sp, threads):
+    """The oracle on the other configurations of the method (manufactured 32^3, 256^3 FP64, the
+    adjoint at 256^3) at all host threads, and the headline workload and the 256^3 one at one
+    thread: one whole step each."""
+    out = {"host_threads": threads}
+    for name in ("manufactured32", "spheres256"):
+        wx = synth.WORKLOADS[name]
+        spx = wx.spheres() if wx.sphere_count else None
+        t, info, phi, _ = oracle_step(wx, spx, threads)
+        d = {"ms_per_step": t * 1e3, "mlups": int(np.prod(wx.dims)) / t / 1e6, **info}
+        if name == "manufactured32":
+            ex = synth.manufactured_exact(wx.dims[0])
+            d["rel_error_vs_exact"] = float(np.linalg.norm(phi - ex) / np.linalg.norm(ex))
+        out[name] = d
+        t1, info1, _, _ = oracle_step(wx, spx, 1)
+        out[name]["one_thread"] = {"ms_per_step": t1 * 1e3, "mlups": int(np.prod(wx.dims)) / t1 / 1e6}
+    wa = synth.WORKLOADS["adjoint256"]
+    t, info = oracle_adjoint_step(wa, wa.spheres(), threads)
+    out["adjoint256"] = {"ms_forward_and_gradient": t * 1e3, **info}
+    t1, info1, _, _ = oracle_step(w, sp, 1)
+    out[w.name + "_one_thread"] = {"ms_per_step": t1 * 1e3, "mlups": int(np.prod(w.dims)) / t1 / 1e6, **info1}
+    return out
 
 
 def workload(args):
@@ -312,6 +380,8 @@ def run_ours(args):
     value = whole_job_mlups(N, world, ms_all)
     k_step = cycles_seen[-1][0]
     rel_final = max(v for _, v in cycles_seen)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    phi_gpu = P.solution().cpu().numpy() if want_cpu else None  # the last timed step's potential
 
     extras = {}
     if not args.no_extras:
@@ -332,19 +402,24 @@ def run_ours(args):
            "h2d_bytes_per_step": int(sp.centers.nbytes + sp.radius.nbytes + sp.density.nbytes),
            "d2h_bytes_per_step": int(Fh.nbytes)}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(w, k_step)
-        cpu.pop("t_step_s", None)
-        cpu.pop("rel0", None)
+    cpu = vs_oracle = None
+    if want_cpu:
+        import oracle
+        cpu, phi_or, f_or = oracle_baseline(w, sp)
+        # the GPU step's potential against the oracle: the oracle's own FP64 residual of it, and
+        # its distance from the oracle's solution of the same step
+        vs_oracle = {"oracle_rel_residual_of_gpu_solution": oracle.rel_residual(phi_gpu, f_or, w.h, w.bc_type),
+                     "rel_error_vs_oracle_solution": float(np.linalg.norm(phi_gpu - phi_or) / np.linalg.norm(phi_or)),
+                     "oracle_precision": w.precision, "tol": w.tol}
+        del phi_or, f_or, phi_gpu
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f64+f32", "data": "synthetic",
-            "config": {**workload_config(w), "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
-                       "cycles_per_step": k_step, "final_rel_residual": rel_final},
+            "config": {**workload_config(w), "parallelism": parallelism(world)},
+            "cycles_per_step": k_step, "final_rel_residual": rel_final,
             "gpu_launches": int(launches),
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -352,6 +427,7 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+            line["vs_oracle"] = vs_oracle
         print(json.dumps(line), flush=True)
     P.close()
     if world > 1:

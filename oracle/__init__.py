@@ -33,16 +33,26 @@ CG_RTOL = 1e-14
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (plain C11, no FMA contraction)."""
+    """Compile the oracle shared library with gcc (plain C11, no FMA contraction), with OpenMP
+    across z-planes where the compiler has it (the results do not depend on the thread count;
+    without OpenMP the same loops run serially)."""
     newest = max(os.path.getmtime(p) for p in _SRC)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           "-o", tmp, _SRC[0], "-lm"]
-    subprocess.check_call(cmd, cwd=_HERE)
+    base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", "-o", tmp, _SRC[0]]
+    try:
+        subprocess.check_call(base + ["-fopenmp", "-lm"], cwd=_HERE, stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + ["-Wno-unknown-pragmas", "-lm"], cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's plane loops (n < 1 keeps the current setting); returns the count in
+    effect (1 when the library was built without OpenMP)."""
+    return int(_load().ccmg_or_set_threads(int(n)))
 
 
 def _load():
@@ -57,6 +67,7 @@ def _load():
             F = ctypes.c_float
             sig = {
                 "ccmg_or_levels": (I, [I, I, I, P]),
+                "ccmg_or_set_threads": (I, [I]),
                 "ccmg_or_apply": (None, [P, P, I, I, I, D, P]),
                 "ccmg_or_apply_f": (None, [P, P, I, I, I, F, P]),
                 "ccmg_or_rbgs_half_f": (None, [P, P, I, I, I, F, P, I]),

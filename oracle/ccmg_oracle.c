@@ -34,6 +34,29 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Threads: with OpenMP the loops over the z-planes of a field are shared among threads (within
+ * one colour for the Gauss-Seidel half-sweeps, whose cells of one colour do not depend on each
+ * other); every cell is computed by the same operations as in a serial run, and every sum over
+ * a field is taken in a fixed order (blocks of 2^16 values), so the results do not depend on the
+ * number of threads. Without OpenMP the pragmas are ignored. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#define OR_PRAGMA(x) _Pragma(#x)
+#define OR_PAR_FOR OR_PRAGMA(omp parallel for schedule(static))
+#define OR_PAR_FOR_IF(cond) OR_PRAGMA(omp parallel for schedule(static) if(cond))
+
+/* Number of threads of the loops above (1 without OpenMP); n < 1 leaves the setting. */
+int ccmg_or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 #define BC_DIRICHLET 0
 #define BC_NEUMANN 1
 #define BC_PERIODIC 2
@@ -146,6 +169,7 @@ void ccmg_or_prolong_correct_f(float* phi, const float* ec, int nx, int ny, int 
  * Edge and corner cells receive the term of every face they touch. */
 void ccmg_or_rhs(const double* rho, double* f, int nx, int ny, int nz, double h, double eps,
                  const int* bc, const double* bcv) {
+  OR_PAR_FOR
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -183,6 +207,7 @@ static double bc_at(int q, int i, int j, int k, int nx, int ny, int nz, const do
 /* ccmg_or_rhs with per-cell boundary values (bc_at): the same terms in the same order. */
 void ccmg_or_rhs_field(const double* rho, double* f, int nx, int ny, int nz, double h, double eps, const int* bc,
                        const double* bcv, const double* bcf, const int* bcf_on) {
+  OR_PAR_FOR
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -374,7 +399,24 @@ static void vcycle_f(hierarchy* H, int l, double h, const int* bc, int nu1, int 
   }
 }
 
-static double norm2_d(const double* a, size_t n) { return sqrt(dot_d(a, a, n)); }
+/* Euclidean norm of a field (Algorithm 1's L2 norm): blocks of 2^16 values summed in index order,
+ * the block sums added in block order. */
+#define OR_NORM_BLOCK ((size_t)1 << 16)
+static double norm2_d(const double* a, size_t n) {
+  const size_t nb = (n + OR_NORM_BLOCK - 1) / OR_NORM_BLOCK;
+  double* part = (double*)malloc((nb ? nb : 1) * sizeof(double));
+  OR_PAR_FOR
+  for (size_t b = 0; b < nb; ++b) {
+    const size_t e = (b + 1) * OR_NORM_BLOCK < n ? (b + 1) * OR_NORM_BLOCK : n;
+    double t = 0.0;
+    for (size_t p = b * OR_NORM_BLOCK; p < e; ++p) t = t + a[p] * a[p];
+    part[b] = t;
+  }
+  double s = 0.0;
+  for (size_t b = 0; b < nb; ++b) s = s + part[b];
+  free(part);
+  return sqrt(s);
+}
 
 /* ncycles V-cycles on A_0 phi = f (f already BC-adapted), phi updated in place. Returns the
  * CG iteration count of the last coarse solve. */
@@ -465,11 +507,13 @@ int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, do
     const double rn = norm2_d(H.r, n);
     rel = fn > 0.0 ? rn / fn : rn;
     if (!(rel >= tol) || k >= max_cycles) break;
+    OR_PAR_FOR
     for (size_t q = 0; q < n; ++q) {
       H.ff[0][q] = (float)(H.r[q] / scale);
       H.phif[0][q] = 0.0f;
     }
     for (int it = 0; it < inner; ++it) vcycle_f(&H, 0, h, bc, nu1, nu2, (float)omega, NULL);
+    OR_PAR_FOR
     for (size_t q = 0; q < n; ++q) phi[q] = phi[q] + scale * (double)H.phif[0][q];
     ++k;
     const double next = rn / sqrt((double)n);
@@ -527,6 +571,7 @@ static double phi_nb_f(const double* phi, int i, int j, int k, int nx, int ny, i
 void ccmg_or_efield(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
                     const double* bcv) {
   const size_t n = (size_t)nx * ny * nz;
+  OR_PAR_FOR
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -576,6 +621,7 @@ static void efield_d3q19_at(const double* phi, int i, int j, int k, int nx, int 
 void ccmg_or_efield_field(const double* phi, double* E, int nx, int ny, int nz, double h, const int* bc,
                           const double* bcv, const double* bcf, const int* bcf_on, int stencil) {
   const size_t n = (size_t)nx * ny * nz;
+  OR_PAR_FOR
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -587,6 +633,7 @@ void ccmg_or_efield_field(const double* phi, double* E, int nx, int ny, int nz, 
         }
       }
   if (stencil != 19) return;
+  OR_PAR_FOR
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -716,6 +763,7 @@ void ccmg_or_force_gather_field(const double* phi, int nx, int ny, int nz, doubl
                                 int stencil, double* forces) {
   const double h3 = h * h * h;
   const int n[3] = {nx, ny, nz};
+  OR_PAR_FOR
   for (int s = 0; s < P; ++s) {
     const double* c = centers + 3 * s;
     int lo[3], hi[3];

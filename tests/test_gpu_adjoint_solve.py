@@ -48,7 +48,7 @@ def test_adjoint_solve_fp64_matches_oracle_solve(dims, h, bc_type, bcv):
     assert k == k_ref, (k, k_ref)
     lg = lam.cpu().numpy()
     assert np.linalg.norm(lg - ref) <= 1e-12 * np.linalg.norm(ref)
-    assert abs(rel - rel_ref) <= 1e-9 * rel_ref
+    assert abs(rel - rel_ref) <= 1e-12  # residuals relative to ||g||: the same state's residual to rounding
     # homogeneous walls: the forward problem's wall values were neither read nor changed, so a
     # forward solve afterwards equals one before
     rho = torch.from_numpy(synth.random_field(dims, 32)).cuda()

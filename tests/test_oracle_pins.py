@@ -906,3 +906,31 @@ def test_var_rhs_adjoint_is_the_transpose():
     J = lambda r, v: float(np.sum(lam * oracle.var_rhs(r, eps, h, bc, v)))  # noqa: E731
     assert abs(J(rho, g) - (np.sum(grho * rho) + np.dot(gbc, g))) < 1e-10 * max(1.0, abs(J(rho, g)))
     assert np.all(gbc[2:4] == 0.0)  # periodic faces have no value
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """The plane loops run on several threads; every cell takes the same operations and every
+    field norm a fixed summation order, so solves, fields and forces are bit-identical for any
+    thread count (also for a periodic axis of odd length, where the sweep stays serial)."""
+    dims = (40, 36, 28)
+    nx, ny, nz = dims
+    sp = synth.random_spheres(dims, 5, 3.0, 9)
+    bc, bcv = (1, 1, 2, 2, 0, 0), (0.1, -0.2, 0.0, 0.0, 0.0, 1.0)
+    out = []
+    n0 = oracle.set_threads(0)
+    try:
+        for t in (1, 3, 8):
+            oracle.set_threads(t)
+            rho = oracle.sphere_density((nz, ny, nx), 1.0, sp.centers, sp.radius, sp.density, 2, bc_type=bc)
+            f = oracle.rhs(rho, 1.0, bc, bcv)
+            phi, k, rel = oracle.solve(f, 1.0, bc, tol=1e-10)
+            pm, km, relm = oracle.solve_mixed(f, 1.0, bc, tol=1e-9)
+            E = oracle.efield(phi, 1.0, bc, bcv)
+            F = oracle.force_gather(phi, 1.0, bc, bcv, sp.centers, sp.radius, sp.density, 2)
+            odd = oracle.rbgs_half(phi[:, :, :39], f[:, :, :39], 1.0, (2, 2, 0, 0, 0, 0), 0)
+            out.append((f, phi, k, rel, pm, km, relm, E, F, odd))
+    finally:
+        oracle.set_threads(n0)
+    for o in out[1:]:
+        for a, b in zip(out[0], o):
+            assert np.array_equal(a, b)
