@@ -60,15 +60,23 @@ def test_single_rank_is_identity():
 
 
 def test_reference_arm_prints_one_json_line():
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--workload", "manufactured32"], capture_output=True, text=True,
-                         timeout=300, cwd=ROOT)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--workload", "manufactured32", "--no-extras"], capture_output=True,
+                         text=True, timeout=300, cwd=ROOT)
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["unit"] == "MLUP/s" and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["h2d_bytes_per_step"] == 0
+    assert rec["cpu_baseline"]["cores"] == (os.cpu_count() or 1) or rec["cpu_baseline"]["cores"] == 1
+    assert rec["steps"] == 2 and rec["warmup"] == 1
+    assert rec["cycles_per_step"] == 11 and rec["final_rel_residual"] < 1e-10
+    # the same config dict as the GPU arm prints for this workload
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1410_6609_gb300 import synth
+    assert rec["config"] == {**bench.workload_config(synth.WORKLOADS["manufactured32"]), "parallelism": "single"}
 
 
 def test_reference_arm_other_ranks_exit_quietly():
