@@ -13,7 +13,7 @@ from paper_1410_6609_gb300.solver import Poisson
 
 pytestmark = pytest.mark.gpu
 
-D, N = 0, 1
+D, N, PER = 0, 1, 2
 TOL = 1e-12
 
 
@@ -446,6 +446,57 @@ def test_fp64_residual_against_exact_arithmetic(dims, bc):
         bound = Fraction(np.spacing(max(abs(v) for v in ops))) / 2 + Fraction(np.spacing(abs(r[idx]))) / 2
         err = abs(Fraction(float(r[idx])) - exact)
         worst = max(worst, float(err / bound))
+    assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("bc", [(D, N, N, D, D, N), (PER, PER, N, D, PER, PER)])
+def test_fp64_residual_against_exact_arithmetic_many_tiles(bc):
+    """The same bound on a grid of several tiles of the residual walk in every direction, with
+    ragged tiles in x, y and z (80 x 20 x 72: packed rows of 40 = 32 + 8 columns, rows 8 + 8 + 4,
+    planes 64 + 8), walls and periodic axes (the halo columns, rows and planes of the walk then
+    come from the opposite side). The exact residual of each cell is summed by math.fsum, which
+    rounds it once, so the bound gains half an ulp of that rounded value."""
+    import math
+    rng = np.random.default_rng(12)
+    nx, ny, nz = 80, 20, 72
+    shape = (nz, ny, nx)
+    phi = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
+    phi[rng.random(shape) < 0.1] = 0.0
+    sh = {D: 1, N: -1, PER: 0}
+    diag = np.full(shape, 6, dtype=np.int64)
+    diag[:, :, 0] += sh[bc[0]]
+    diag[:, :, -1] += sh[bc[1]]
+    diag[:, 0, :] += sh[bc[2]]
+    diag[:, -1, :] += sh[bc[3]]
+    diag[0] += sh[bc[4]]
+    diag[-1] += sh[bc[5]]
+    p = phi
+    for ax, q in ((2, 0), (1, 2), (0, 4)):  # axis 2 is x, 1 is y, 0 is z
+        widths = [(0, 0)] * 3
+        widths[ax] = (1, 1)
+        p = np.pad(p, widths, mode="wrap" if bc[q] == PER else "constant")
+    nbs = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
+           p[2:, 1:-1, 1:-1]]
+    g = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
+    g[rng.random(shape) < 0.05] = 0.0
+    cancel = rng.random(shape) < 0.5
+    g[cancel] = (diag * phi - sum(nbs))[cancel]
+    P_ = Poisson((nx, ny, nz), h=1.0, bc_type=bc)
+    P_.level_set(0, 0, gpu(phi))
+    P_.level_set(0, 1, gpu(g))
+    _, r = P_.residual(field=True)
+    r = cpu(r)
+    P_.close()
+    vals = [g] + nbs + [-phi]
+    big = np.max(np.abs(np.stack(vals)), axis=0)
+    worst = 0.0
+    flat = [v.reshape(-1) for v in vals]
+    dflat, rflat, bflat = diag.reshape(-1), r.reshape(-1), big.reshape(-1)
+    for i in range(rflat.size):
+        terms = [float(v[i]) for v in flat[:-1]] + [float(flat[-1][i])] * int(dflat[i])
+        ex = math.fsum(terms)
+        bound = np.spacing(bflat[i]) / 2 + np.spacing(abs(rflat[i])) / 2 + np.spacing(abs(ex)) / 2
+        worst = max(worst, abs(rflat[i] - ex) / bound)
     assert worst <= 1.0, worst
 
 
