@@ -1124,7 +1124,9 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
                 p2 != kBadPow2 ? f32_of_scaled(rd, p2) : (float)(rd * isc);
         }
       };
-      const bool g0 = __all_sync(0xffffffffu, gv[0] == 0.0 && gv[1] == 0.0);  // non-live lanes hold 0
+      // zero tests on the bits (+-0; an FP64 compare would take the 1/64-rate FP64 pipe); non-live
+      // lanes hold 0
+      const bool g0 = __all_sync(0xffffffffu, ((fx_bits(gv[0]) | fx_bits(gv[1])) << 1) == 0ULL);
       if (live) {
         if (g0) cells(std::true_type{});
         else cells(std::false_type{});

@@ -211,20 +211,36 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
     // (m + j'/2 + p/2) & 1 at packed index m >> 1; its coarse row sits in box row
     // j'/2 - (y0/2 - 1), column (m >> 1) - (x0/2 - kCHalo). Out-of-range red values and parents
     // arrived as zeros, so walls stay zero.
+    // The box positions a thread corrects (vectors f = tid and tid + 256 of the box) are fixed for
+    // the tile: the red vector's offset in a slot, its parents' row offset in a coarse box, and the
+    // parity of m + J; only the coarse plane's parity changes from plane to plane.
+    constexpr int kVecs = kBoxX / 4 * C::kBoxY;
+    constexpr int kNT = kTX * C::kTY;
+    constexpr int kPerThr = (kVecs + kNT - 1) / kNT;
+    int cvo[kPerThr], cco[kPerThr], cpar[kPerThr];
+    if constexpr (C::kPro) {
+#pragma unroll
+      for (int u = 0; u < kPerThr; ++u) {
+        const int f = ty * kTX + tx + u * kNT;
+        const int by = f / (kBoxX / 4), bx = 4 * (f - by * (kBoxX / 4));
+        const int m = t.x0 - kHaloX + bx, J = (t.y0 - 1 + by) >> 1;
+        cvo[u] = f < kVecs ? by * kBoxX + bx : -1;
+        cco[u] = (J - (t.y0 / 2 - 1)) * kCBoxX + (bx >> 1) + (kCHalo - kHaloX / 2);
+        cpar[u] = (m + J) & 1;
+      }
+    }
     auto correct = [&](int q, int p) {
       float* slot = ring + q * (kSlotBytes / 4);
       const int K = (p + 2) / 2 - 1;  // floor(p / 2) for p >= -1
-      constexpr int kVecs = kBoxX / 4 * C::kBoxY;
-      for (int f = ty * kTX + tx; f < kVecs; f += kTX * kTY) {
-        const int by = f / (kBoxX / 4), bx = 4 * (f - by * (kBoxX / 4));
-        const int m = t.x0 - kHaloX + bx, J = (t.y0 - 1 + by) >> 1;
-        const int rowb = (J - (t.y0 / 2 - 1)) * kCBoxX + (bx >> 1) + (kCHalo - kHaloX / 2);
-        const bool even0 = ((m + J + K) & 1) == 0;  // parent I = m has colour 0
-        const float* ca = slot + (even0 ? C::kC0Off : C::kC1Off) / 4 + rowb;
-        const float* cb = slot + (even0 ? C::kC1Off : C::kC0Off) / 4 + rowb;
+#pragma unroll
+      for (int u = 0; u < kPerThr; ++u) {
+        if (cvo[u] < 0) continue;
+        const bool even0 = ((cpar[u] + K) & 1) == 0;  // parent I = m has colour 0
+        const float* ca = slot + (even0 ? C::kC0Off : C::kC1Off) / 4 + cco[u];
+        const float* cb = slot + (even0 ? C::kC1Off : C::kC0Off) / 4 + cco[u];
         const float2 pa = *reinterpret_cast<const float2*>(ca);
         const float2 pb = *reinterpret_cast<const float2*>(cb);
-        float4* v = reinterpret_cast<float4*>(slot + by * kBoxX + bx);
+        float4* v = reinterpret_cast<float4*>(slot + cvo[u]);
         float4 r = *v;
         r.x = __fadd_rn(r.x, __fmul_rn(omega, pa.x));
         r.y = __fadd_rn(r.y, __fmul_rn(omega, pb.x));
