@@ -293,6 +293,179 @@ __device__ __forceinline__ void load_nb_vec(const T* __restrict__ yr, const Geom
 }
 
 // ---------------------------------------------------------------------------------------------
+// The FP64 scaled residual r~ = g + (x_-x + x_+x + x_-y + x_+y + x_-z + x_+z) - D x_c of one cell
+// (D = 6 + d), evaluated in 64-bit fixed point. Each operand is first put in a form that does not
+// depend on the cell (FxOp: its 53-bit significand times 2^5 with its sign applied, and its biased
+// exponent), so the tiled kernel below converts every value once and reuses it for the seven
+// cells it enters. A cell then aligns its operands to the largest biased exponent E among them,
+// rounding each down to the unit 2^(E-1080) (an arithmetic shift), adds them as integers (the
+// magnitudes stay below 2^58 each, so the sum of at most 16 of them fits), and rounds the sum
+// once to the nearest double. Each operand loses less than one unit (the centre's loss is scaled
+// by D), so the result lies within 16 units, i.e. half an ulp of the largest operand, plus half
+// an ulp of itself, of the exact residual: closer than the seven rounded FP64 operations of the
+// direct formula. All of it is integer work: on GB300 the FP64 pipe, which the direct formula
+// occupies, runs at 1/64 of the FP32 rate. Subnormal operands count as zero (they lie below one
+// unit unless every operand is that small); a cell with an infinite or NaN operand takes the
+// direct formula.
+struct FxOp {
+  unsigned lo, hi;  // two's complement of +-significand * 2^5 (0 for zero and subnormal operands)
+  unsigned pk;      // biased exponent e in bits 0..15, and (e ? 2047 - e : 0) in bits 16..31
+};
+
+__host__ __device__ __forceinline__ unsigned long long fx_bits(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long u;
+  memcpy(&u, &v, sizeof(u));
+  return u;
+#endif
+}
+
+__host__ __device__ __forceinline__ double fx_double(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  memcpy(&v, &u, sizeof(v));
+  return v;
+#endif
+}
+
+__host__ __device__ __forceinline__ FxOp fx_op(double v) {
+  const unsigned long long u = fx_bits(v);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned keep = e ? 0xffffffffu : 0u;
+  const unsigned mh = (hi & 0xfffffu) | 0x100000u;
+  const unsigned long long mag = ((unsigned long long)(((mh << 5) | (lo >> 27)) & keep) << 32) | ((lo << 5) & keep);
+  const unsigned long long neg = (unsigned long long)(long long)((int)hi >> 31);
+  const unsigned long long S = (mag ^ neg) - neg;
+  FxOp o;
+  o.lo = (unsigned)S;
+  o.hi = (unsigned)(S >> 32);
+  o.pk = e | ((e ? 2047u - e : 0u) << 16);
+  return o;
+}
+
+// Lane-wise maximum of two pairs of 16-bit fields.
+__host__ __device__ __forceinline__ unsigned fx_max2(unsigned a, unsigned b) {
+#ifdef __CUDA_ARCH__
+  unsigned d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+#else
+  const unsigned l = (a & 0xffffu) > (b & 0xffffu) ? (a & 0xffffu) : (b & 0xffffu);
+  const unsigned h = (a >> 16) > (b >> 16) ? (a >> 16) : (b >> 16);
+  return l | (h << 16);
+#endif
+}
+
+// floor(S / 2^(E - e)) for an operand with E - e <= 31 (or S = 0): a funnel shift of the two words.
+__host__ __device__ __forceinline__ unsigned long long fx_align31(const FxOp& o, int E) {
+  const unsigned d = ((unsigned)E - o.pk) & 31u;  // the upper field of pk drops out of the low 5 bits
+#ifdef __CUDA_ARCH__
+  const unsigned lo = __funnelshift_r(o.lo, o.hi, d);
+  const unsigned hi = (unsigned)((int)o.hi >> d);
+  return ((unsigned long long)hi << 32) | lo;
+#else
+  return (unsigned long long)((long long)(((unsigned long long)o.hi << 32) | o.lo) >> d);
+#endif
+}
+
+// The same for any exponent gap (shifts of 63 and more leave 0 or -1).
+__host__ __device__ __forceinline__ unsigned long long fx_align(const FxOp& o, int E) {
+  int d = E - (int)(o.pk & 0xffffu);
+  d = d < 63 ? d : 63;
+  return (unsigned long long)((long long)(((unsigned long long)o.hi << 32) | o.lo) >> d);
+}
+
+// The signed sum S in units 2^(E-1080) as a double: the integer rounded to nearest (ties to even)
+// by the conversion instruction, then scaled by the power of two, which is exact unless the result
+// leaves the normal range (then it is rounded once more, or overflows to infinity, as ldexp does).
+__host__ __device__ __forceinline__ double fx_to_double(unsigned long long S, int E) {
+#ifdef __CUDA_ARCH__
+  return ldexp_rne(__ll2double_rn((long long)S), E - 1080);
+#else
+  return ldexp((double)(long long)S, E - 1080);
+#endif
+}
+
+// The operand back as a double (exact for normal values, infinities and NaN; subnormals give 0).
+__host__ __device__ __forceinline__ double fx_value(const FxOp& o) {
+  const unsigned long long S = ((unsigned long long)o.hi << 32) | o.lo;
+  const unsigned e = o.pk & 0xffffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long sgn = S & 0x8000000000000000ULL;
+  const unsigned long long mag = (sgn ? (0ULL - S) : S) >> 5;
+  return fx_double(sgn | ((unsigned long long)e << 52) | (mag & 0xfffffffffffffULL));
+}
+
+// The direct FP64 formula, for cells with an infinite or NaN operand.
+__host__ __device__ __forceinline__ double fx_direct(const FxOp (&op)[8], int D) {
+  const double S = ((((fx_value(op[1]) + fx_value(op[2])) + fx_value(op[3])) + fx_value(op[4])) + fx_value(op[5])) +
+                   fx_value(op[6]);
+  return fma(-(double)D, fx_value(op[7]), fx_value(op[0]) + S);
+}
+
+// r~ of one cell from op[0] = g, op[1..6] = the six neighbours (absent ones as fx_op(0.0)) and
+// op[7] = the centre, with D = 6 + d. G0: the right-hand side is zero and op[0] is not read (the
+// same exact sum without its zero term, hence the same result).
+template <bool G0 = false>
+__host__ __device__ __forceinline__ double fx_residual(const FxOp (&op)[8], int D) {
+  constexpr int i0 = G0 ? 1 : 0;
+  unsigned P = op[7].pk;
+#pragma unroll
+  for (int i = i0; i < 7; ++i) P = fx_max2(P, op[i].pk);
+  const int E = (int)(P & 0xffffu);
+  if (E == 0) return 0.0;  // every operand zero or subnormal
+  if (E == 2047) {
+    if (G0) {
+      const FxOp o[8] = {fx_op(0.0), op[1], op[2], op[3], op[4], op[5], op[6], op[7]};
+      return fx_direct(o, D);
+    }
+    return fx_direct(op, D);
+  }
+  const int emin = 2047 - (int)(P >> 16);  // smallest exponent among the nonzero operands
+  unsigned long long acc = 0ULL;
+  if (E - emin <= 31) {
+#pragma unroll
+    for (int i = i0; i < 7; ++i) acc += fx_align31(op[i], E);
+    acc -= fx_align31(op[7], E) * (unsigned long long)D;
+  } else {
+#pragma unroll
+    for (int i = i0; i < 7; ++i) acc += fx_align(op[i], E);
+    acc -= fx_align(op[7], E) * (unsigned long long)D;
+  }
+  return fx_to_double(acc, E);
+}
+
+// The sum of a cell's six neighbours (absent ones as fx_op(0.0)) in the same fixed point, rounded
+// once: within half an ulp of the largest neighbour plus half an ulp of itself of the exact sum
+// (closer than five rounded FP64 additions). The FP64 half-sweep takes it so that two of its
+// operations stay on the FP64 pipe instead of six.
+__host__ __device__ __forceinline__ double fx_sum6(const FxOp (&op)[6]) {
+  unsigned P = op[0].pk;
+#pragma unroll
+  for (int i = 1; i < 6; ++i) P = fx_max2(P, op[i].pk);
+  const int E = (int)(P & 0xffffu);
+  if (E == 0) return 0.0;  // every operand zero or subnormal
+  if (E == 2047)           // an infinite or NaN operand: the direct sum
+    return ((((fx_value(op[0]) + fx_value(op[1])) + fx_value(op[2])) + fx_value(op[3])) + fx_value(op[4])) +
+           fx_value(op[5]);
+  const int emin = 2047 - (int)(P >> 16);
+  unsigned long long acc = 0ULL;
+  if (E - emin <= 31) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc += fx_align31(op[i], E);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc += fx_align(op[i], E);
+  }
+  return fx_to_double(acc, E);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Red-black Gauss-Seidel half-sweep (Sec. 5.3): every cell of `colour` becomes the solution of
 // its own row, phi = (g + sum of neighbours) / (6 + d). ZERO: the level's current iterate is
 // zero (first sweep after restriction), so the neighbour sum is exactly zero and is not read.
@@ -339,18 +512,39 @@ __device__ __forceinline__ void smooth_vec(T* __restrict__ x, const T* __restric
     T extra;
     if (s == 0) extra = (m0 > 0) ? __ldg(yr + m0 - 1) : (px ? __ldg(yr + G.hx - 1) : T(0));
     else extra = (m0 + V < G.hx) ? __ldg(yr + m0 + V) : (px ? __ldg(yr) : T(0));
+    if constexpr (sizeof(T) == 8) {
+      // FP64: the neighbour sum exactly in fixed point, each loaded value converted once (fx_sum6)
+      FxOp fc[V], fym[V], fyp[V], fzm[V], fzp[V];
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-      T xm, xp;
-      if (s == 0) {
-        xm = (i == 0) ? extra : yc[(i + V - 1) % V];
-        xp = yc[i];
-      } else {
-        xm = yc[i];
-        xp = (i == V - 1) ? extra : yc[(i + 1) % V];
+      for (int i = 0; i < V; ++i) {
+        fc[i] = fx_op(yc[i]);
+        fym[i] = fx_op(ym[i]);
+        fyp[i] = fx_op(yp[i]);
+        fzm[i] = fx_op(zm[i]);
+        fzp[i] = fx_op(zp[i]);
       }
-      const T S = ((((xm + xp) + ym[i]) + yp[i]) + zm[i]) + zp[i];
-      out[i] = (gv[i] + S) * invd[i];
+      const FxOp fe = fx_op(extra);
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const FxOp xm = s == 0 ? (i == 0 ? fe : fc[(i + V - 1) % V]) : fc[i];
+        const FxOp xp = s == 0 ? fc[i] : (i == V - 1 ? fe : fc[(i + 1) % V]);
+        const FxOp op[6] = {xm, xp, fym[i], fyp[i], fzm[i], fzp[i]};
+        out[i] = (gv[i] + fx_sum6(op)) * invd[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        T xm, xp;
+        if (s == 0) {
+          xm = (i == 0) ? extra : yc[(i + V - 1) % V];
+          xp = yc[i];
+        } else {
+          xm = yc[i];
+          xp = (i == V - 1) ? extra : yc[(i + 1) % V];
+        }
+        const T S = ((((xm + xp) + ym[i]) + yp[i]) + zm[i]) + zp[i];
+        out[i] = (gv[i] + S) * invd[i];
+      }
     }
   }
   store_vec(x + own, out);
@@ -572,26 +766,52 @@ __device__ __forceinline__ void resid_restrict_vec(const T* __restrict__ x, cons
         load_nb_vec<1, PER>(y, G, I0, j, k, yp);
         load_nb_vec<2, PER>(y, G, I0, j, k, zm);
         load_nb_vec<3, PER>(y, G, I0, j, k, zp);
+        if constexpr (sizeof(T) == 8) {
+          // FP64: the neighbour sum exactly in fixed point (fx_sum6), as in the FP64 half-sweep
+          FxOp fo[V], fym[V], fyp[V], fzm[V], fzp[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int I = I0 + v;
-          T xm, xp, xv, gv;
-          if (di == 0) {  // cell i = 2I: x-neighbours 2I-1 (other colour, index I-1) and 2I+1 (index I)
-            xm = (v == 0) ? left : x1[(v + V - 1) % V];
-            xp = x1[v];
-            xv = x0[v];
-            gv = g0[v];
-          } else {  // cell i = 2I+1: x-neighbours 2I (index I) and 2I+2 (index I+1)
-            xm = x0[v];
-            xp = (v == V - 1) ? right : x0[(v + 1) % V];
-            xv = x1[v];
-            gv = g1[v];
+          for (int v = 0; v < V; ++v) {
+            fo[v] = fx_op(di == 0 ? x1[v] : x0[v]);  // the other colour's row segment
+            fym[v] = fx_op(ym[v]);
+            fyp[v] = fx_op(yp[v]);
+            fzm[v] = fx_op(zm[v]);
+            fzp[v] = fx_op(zp[v]);
           }
-          const T S = ((((xm + xp) + ym[v]) + yp[v]) + zm[v]) + zp[v];
-          int d = dyz;
-          if (I == 0 && di == 0) d += G.sh[0];
-          if (I == G.hx - 1 && di == 1) d += G.sh[1];
-          acc[v] = acc[v] + fmat(neg_diag<T>(d), xv, gv + S);
+          const FxOp fe = fx_op(di == 0 ? left : right);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int I = I0 + v;
+            const FxOp xm = di == 0 ? (v == 0 ? fe : fo[(v + V - 1) % V]) : fo[v];
+            const FxOp xp = di == 0 ? fo[v] : (v == V - 1 ? fe : fo[(v + 1) % V]);
+            const FxOp op[6] = {xm, xp, fym[v], fyp[v], fzm[v], fzp[v]};
+            const T xv = di == 0 ? x0[v] : x1[v], gv = di == 0 ? g0[v] : g1[v];
+            int d = dyz;
+            if (I == 0 && di == 0) d += G.sh[0];
+            if (I == G.hx - 1 && di == 1) d += G.sh[1];
+            acc[v] = acc[v] + fmat(neg_diag<T>(d), xv, gv + fx_sum6(op));
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int I = I0 + v;
+            T xm, xp, xv, gv;
+            if (di == 0) {  // cell i = 2I: x-neighbours 2I-1 (other colour, index I-1) and 2I+1 (index I)
+              xm = (v == 0) ? left : x1[(v + V - 1) % V];
+              xp = x1[v];
+              xv = x0[v];
+              gv = g0[v];
+            } else {  // cell i = 2I+1: x-neighbours 2I (index I) and 2I+2 (index I+1)
+              xm = x0[v];
+              xp = (v == V - 1) ? right : x0[(v + 1) % V];
+              xv = x1[v];
+              gv = g1[v];
+            }
+            const T S = ((((xm + xp) + ym[v]) + yp[v]) + zm[v]) + zp[v];
+            int d = dyz;
+            if (I == 0 && di == 0) d += G.sh[0];
+            if (I == G.hx - 1 && di == 1) d += G.sh[1];
+            acc[v] = acc[v] + fmat(neg_diag<T>(d), xv, gv + S);
+          }
         }
       }
     }
@@ -617,154 +837,6 @@ __device__ __forceinline__ void prolong_cell(T* __restrict__ x, const Geom& G, c
         const long long idx = (long long)c * G.csz + ((long long)(2 * K + dk) * G.ny + (2 * J + dj)) * G.hx + I;
         x[idx] = add_rn(x[idx], w);
       }
-}
-
-// ---------------------------------------------------------------------------------------------
-// The FP64 scaled residual r~ = g + (x_-x + x_+x + x_-y + x_+y + x_-z + x_+z) - D x_c of one cell
-// (D = 6 + d), evaluated in 64-bit fixed point. Each operand is first put in a form that does not
-// depend on the cell (FxOp: its 53-bit significand times 2^5 with its sign applied, and its biased
-// exponent), so the tiled kernel below converts every value once and reuses it for the seven
-// cells it enters. A cell then aligns its operands to the largest biased exponent E among them,
-// rounding each down to the unit 2^(E-1080) (an arithmetic shift), adds them as integers (the
-// magnitudes stay below 2^58 each, so the sum of at most 16 of them fits), and rounds the sum
-// once to the nearest double. Each operand loses less than one unit (the centre's loss is scaled
-// by D), so the result lies within 16 units, i.e. half an ulp of the largest operand, plus half
-// an ulp of itself, of the exact residual: closer than the seven rounded FP64 operations of the
-// direct formula. All of it is integer work: on GB300 the FP64 pipe, which the direct formula
-// occupies, runs at 1/64 of the FP32 rate. Subnormal operands count as zero (they lie below one
-// unit unless every operand is that small); a cell with an infinite or NaN operand takes the
-// direct formula.
-struct FxOp {
-  unsigned lo, hi;  // two's complement of +-significand * 2^5 (0 for zero and subnormal operands)
-  unsigned pk;      // biased exponent e in bits 0..15, and (e ? 2047 - e : 0) in bits 16..31
-};
-
-__host__ __device__ __forceinline__ unsigned long long fx_bits(double v) {
-#ifdef __CUDA_ARCH__
-  return (unsigned long long)__double_as_longlong(v);
-#else
-  unsigned long long u;
-  memcpy(&u, &v, sizeof(u));
-  return u;
-#endif
-}
-
-__host__ __device__ __forceinline__ double fx_double(unsigned long long u) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)u);
-#else
-  double v;
-  memcpy(&v, &u, sizeof(v));
-  return v;
-#endif
-}
-
-__host__ __device__ __forceinline__ FxOp fx_op(double v) {
-  const unsigned long long u = fx_bits(v);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const unsigned e = (hi >> 20) & 0x7ffu;
-  const unsigned keep = e ? 0xffffffffu : 0u;
-  const unsigned mh = (hi & 0xfffffu) | 0x100000u;
-  const unsigned long long mag = ((unsigned long long)(((mh << 5) | (lo >> 27)) & keep) << 32) | ((lo << 5) & keep);
-  const unsigned long long neg = (unsigned long long)(long long)((int)hi >> 31);
-  const unsigned long long S = (mag ^ neg) - neg;
-  FxOp o;
-  o.lo = (unsigned)S;
-  o.hi = (unsigned)(S >> 32);
-  o.pk = e | ((e ? 2047u - e : 0u) << 16);
-  return o;
-}
-
-// Lane-wise maximum of two pairs of 16-bit fields.
-__host__ __device__ __forceinline__ unsigned fx_max2(unsigned a, unsigned b) {
-#ifdef __CUDA_ARCH__
-  unsigned d;
-  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-  return d;
-#else
-  const unsigned l = (a & 0xffffu) > (b & 0xffffu) ? (a & 0xffffu) : (b & 0xffffu);
-  const unsigned h = (a >> 16) > (b >> 16) ? (a >> 16) : (b >> 16);
-  return l | (h << 16);
-#endif
-}
-
-// floor(S / 2^(E - e)) for an operand with E - e <= 31 (or S = 0): a funnel shift of the two words.
-__host__ __device__ __forceinline__ unsigned long long fx_align31(const FxOp& o, int E) {
-  const unsigned d = ((unsigned)E - o.pk) & 31u;  // the upper field of pk drops out of the low 5 bits
-#ifdef __CUDA_ARCH__
-  const unsigned lo = __funnelshift_r(o.lo, o.hi, d);
-  const unsigned hi = (unsigned)((int)o.hi >> d);
-  return ((unsigned long long)hi << 32) | lo;
-#else
-  return (unsigned long long)((long long)(((unsigned long long)o.hi << 32) | o.lo) >> d);
-#endif
-}
-
-// The same for any exponent gap (shifts of 63 and more leave 0 or -1).
-__host__ __device__ __forceinline__ unsigned long long fx_align(const FxOp& o, int E) {
-  int d = E - (int)(o.pk & 0xffffu);
-  d = d < 63 ? d : 63;
-  return (unsigned long long)((long long)(((unsigned long long)o.hi << 32) | o.lo) >> d);
-}
-
-// The signed sum S in units 2^(E-1080) as a double: the integer rounded to nearest (ties to even)
-// by the conversion instruction, then scaled by the power of two, which is exact unless the result
-// leaves the normal range (then it is rounded once more, or overflows to infinity, as ldexp does).
-__host__ __device__ __forceinline__ double fx_to_double(unsigned long long S, int E) {
-#ifdef __CUDA_ARCH__
-  return ldexp_rne(__ll2double_rn((long long)S), E - 1080);
-#else
-  return ldexp((double)(long long)S, E - 1080);
-#endif
-}
-
-// The operand back as a double (exact for normal values, infinities and NaN; subnormals give 0).
-__host__ __device__ __forceinline__ double fx_value(const FxOp& o) {
-  const unsigned long long S = ((unsigned long long)o.hi << 32) | o.lo;
-  const unsigned e = o.pk & 0xffffu;
-  if (e == 0u) return 0.0;
-  const unsigned long long sgn = S & 0x8000000000000000ULL;
-  const unsigned long long mag = (sgn ? (0ULL - S) : S) >> 5;
-  return fx_double(sgn | ((unsigned long long)e << 52) | (mag & 0xfffffffffffffULL));
-}
-
-// The direct FP64 formula, for cells with an infinite or NaN operand.
-__host__ __device__ __forceinline__ double fx_direct(const FxOp (&op)[8], int D) {
-  const double S = ((((fx_value(op[1]) + fx_value(op[2])) + fx_value(op[3])) + fx_value(op[4])) + fx_value(op[5])) +
-                   fx_value(op[6]);
-  return fma(-(double)D, fx_value(op[7]), fx_value(op[0]) + S);
-}
-
-// r~ of one cell from op[0] = g, op[1..6] = the six neighbours (absent ones as fx_op(0.0)) and
-// op[7] = the centre, with D = 6 + d. G0: the right-hand side is zero and op[0] is not read (the
-// same exact sum without its zero term, hence the same result).
-template <bool G0 = false>
-__host__ __device__ __forceinline__ double fx_residual(const FxOp (&op)[8], int D) {
-  constexpr int i0 = G0 ? 1 : 0;
-  unsigned P = op[7].pk;
-#pragma unroll
-  for (int i = i0; i < 7; ++i) P = fx_max2(P, op[i].pk);
-  const int E = (int)(P & 0xffffu);
-  if (E == 0) return 0.0;  // every operand zero or subnormal
-  if (E == 2047) {
-    if (G0) {
-      const FxOp o[8] = {fx_op(0.0), op[1], op[2], op[3], op[4], op[5], op[6], op[7]};
-      return fx_direct(o, D);
-    }
-    return fx_direct(op, D);
-  }
-  const int emin = 2047 - (int)(P >> 16);  // smallest exponent among the nonzero operands
-  unsigned long long acc = 0ULL;
-  if (E - emin <= 31) {
-#pragma unroll
-    for (int i = i0; i < 7; ++i) acc += fx_align31(op[i], E);
-    acc -= fx_align31(op[7], E) * (unsigned long long)D;
-  } else {
-#pragma unroll
-    for (int i = i0; i < 7; ++i) acc += fx_align(op[i], E);
-    acc -= fx_align(op[7], E) * (unsigned long long)D;
-  }
-  return fx_to_double(acc, E);
 }
 
 // Scaled residual of cell m of packed row (c, j, k); returns r~ = g + sum - (6+d) x (single
