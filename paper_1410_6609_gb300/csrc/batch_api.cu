@@ -8,6 +8,7 @@
 // let converged systems drop out of the same captured graphs. The smoother and transfer tile
 // shapes are chosen by mg_batch_autotune, which times the whole batched cycle per candidate.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -86,6 +87,14 @@ struct mg_batch {
   cudaGraphExec_t g_cycle = nullptr, g_resid = nullptr;
   long long n_cycle = 0, n_resid = 0;
   long long launches = 0;
+  // single precision: the finest levels' half-sweeps TMA-staged (one table entry per system), when
+  // every system's finest level qualifies
+  BTmaSys* d_tma = nullptr;
+  long long tma_total = 0;
+  int tma_grid = 0;
+  bool tma_ok = false;
+  int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
+  int* h_err = nullptr;
   std::string err;
 };
 
@@ -286,9 +295,16 @@ cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cuda
     const BLaunch Ls = bl(b, b->smooth[d]);
     if (Ls.count == 0) continue;
     const bool zero = (d > 0) || zero0;
+    // the finest levels' sweeps TMA-staged (single precision; not from a zero iterate)
+    auto sweep = [&](int colour, bool z) -> cudaError_t {
+      if constexpr (sizeof(T) == sizeof(float))
+        if (d == 0 && !z && b->tma_ok)
+          return launch_b_smooth_tma(b->d_tma, b->B, b->tma_total, b->tma_grid, act, inv, colour, b->d_err, s);
+      return launch_b_smooth<T>(Ls, act, inv, colour, z, s);
+    };
     for (int it = 0; it < b->nu1; ++it) {
-      if ((e = launch_b_smooth<T>(Ls, act, inv, 0, zero && it == 0, s)) != cudaSuccess) return e;
-      if ((e = launch_b_smooth<T>(Ls, act, inv, 1, false, s)) != cudaSuccess) return e;
+      if ((e = sweep(0, zero && it == 0)) != cudaSuccess) return e;
+      if ((e = sweep(1, false)) != cudaSuccess) return e;
       *nk += 2;
     }
     // as the single-system cycle: red-only restriction in single precision only
@@ -307,13 +323,23 @@ cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cuda
     const BLaunch Lp = bl(b, fuse ? b->xfer_nv[d] : b->xfer[d]);
     if ((e = launch_b_prolong<T>(Lp, act, (T)b->omega, b->nu2 >= 1, s)) != cudaSuccess) return e;
     *nk += Lp.count > 0 ? 1 : 0;
+    const bool tma = sizeof(T) == sizeof(float) && d == 0 && b->tma_ok;
     for (int it = 0; it < b->nu2; ++it) {
-      if (fuse && it == 0)
+      if (fuse && it == 0 && tma)
+        e = launch_b_smooth_prolong_tma(b->d_tma, b->B, b->tma_total, b->tma_grid, act, b->inv32, (float)b->omega,
+                                        b->d_err, s);
+      else if (fuse && it == 0)
         e = launch_b_smooth_prolong(Ls, act, b->inv32, (float)b->omega, s);
+      else if (tma)
+        e = launch_b_smooth_tma(b->d_tma, b->B, b->tma_total, b->tma_grid, act, b->inv32, 1, b->d_err, s);
       else
         e = launch_b_smooth<T>(Ls, act, inv, 1, false, s);
       if (e != cudaSuccess) return e;
-      if ((e = launch_b_smooth<T>(Ls, act, inv, 0, false, s)) != cudaSuccess) return e;
+      if (tma)
+        e = launch_b_smooth_tma(b->d_tma, b->B, b->tma_total, b->tma_grid, act, b->inv32, 0, b->d_err, s);
+      else
+        e = launch_b_smooth<T>(Ls, act, inv, 0, false, s);
+      if (e != cudaSuccess) return e;
       *nk += 2;
     }
   }
@@ -418,6 +444,9 @@ mg_status materialize(mg_batch* b, int s) {
 
 void free_batch(mg_batch* b) {
   destroy_graphs(b);
+  cudaFree(b->d_tma);
+  cudaFree(b->d_err);
+  if (b->h_err) cudaFreeHost(b->h_err);
   cudaFree(b->arena);
   cudaFree(b->d_entries);
   cudaFree(b->d_starts);
@@ -432,6 +461,42 @@ void free_batch(mg_batch* b) {
     if (b->flag_ev[k]) cudaEventDestroy(b->flag_ev[k]);
   if (b->h_scal) cudaFreeHost(b->h_scal);
   if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+// The TMA-staged half-sweeps of the systems' finest single-precision levels (as a single context
+// stages its largest levels): one table entry per system, made when every system qualifies
+// (packed finest level with whole 4-float rows and at least 8 planes, no periodic axis, a packed
+// next level of half the size). CCMG_SWEEP=vec keeps the direct-load sweeps (as for a context).
+mg_status prepare_batch_tma(mg_batch* b) {
+  b->tma_ok = false;
+  if (!bmixed(b)) return MG_OK;
+  const char* env = std::getenv("CCMG_SWEEP");
+  if (env && std::strcmp(env, "vec") == 0) return MG_OK;
+  std::vector<float*> x(b->B);
+  std::vector<const float*> g(b->B), xc(b->B);
+  std::vector<Geom> G(b->B), Gc(b->B);
+  std::vector<int> idx(b->B);
+  for (int s = 0; s < b->B; ++s) {
+    const BSys& S = b->sys[s];
+    if (S.L < 2) return MG_OK;
+    x[s] = S.x32[0];
+    g[s] = S.g32[0];
+    xc[s] = S.x32[1];
+    G[s] = S.geo[0];
+    Gc[s] = S.geo[1];
+    idx[s] = s;
+  }
+  std::vector<BTmaSys> tab(b->B);
+  int ok = 0, dev = 0;
+  BCK(cudaGetDevice(&dev), "batch TMA maps");
+  BCK(prepare_tma_batch(tab.data(), b->B, x.data(), g.data(), G.data(), xc.data(), Gc.data(), idx.data(),
+                        &b->tma_total, &b->tma_grid, &ok, dev),
+      "batch TMA maps");
+  if (!ok) return MG_OK;
+  BCK(cudaMalloc((void**)&b->d_tma, tab.size() * sizeof(BTmaSys)), "batch TMA maps");
+  BCK(cudaMemcpy(b->d_tma, tab.data(), tab.size() * sizeof(BTmaSys), cudaMemcpyHostToDevice), "batch TMA maps");
+  b->tma_ok = true;
+  return MG_OK;
 }
 
 mg_status check_sys(mg_batch* b, int s) {
@@ -554,6 +619,9 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_scal, (size_t)B * kScalStride * sizeof(double));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_b_coarse_cg();
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->arena, 0, bytes, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scal, 0, (size_t)B * kScalStride * sizeof(double), b->stream);
   if (e != cudaSuccess) {
@@ -579,7 +647,8 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
     }
   }
   for (int s = 0; s < B; ++s) b->h_zero[s] = 1;  // the arena starts zeroed
-  mg_status st = plan(b);
+  mg_status st = prepare_batch_tma(b);
+  if (st == MG_OK) st = plan(b);
   if (st == MG_OK) st = set_all_active(b, 1);
   if (st == MG_OK) st = upload_zero(b);
   if (st != MG_OK) {
@@ -667,7 +736,13 @@ mg_status mg_batch_solve(mg_batch* b, double tol, int max_cycles, int* h_cycles,
     BCK(cudaMemcpyAsync(b->h_scal, b->d_scal, (size_t)b->B * kScalStride * sizeof(double), cudaMemcpyDeviceToHost,
                         b->stream),
         "batch residual");
+    BCK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "batch residual");
     BCK(cudaStreamSynchronize(b->stream), "batch residual");
+    if (*b->h_err) {  // a staged sweep's bounded wait ran out: the iterates are incomplete
+      cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+      set_all_active(b, 1);
+      return bfail(b, MG_ERR_TIMEOUT, "a kernel's bounded wait for its staged copies ran out; the result is incomplete");
+    }
     bool any = false;
     for (int s = 0; s < b->B; ++s) {
       if (!b->h_active[s]) continue;

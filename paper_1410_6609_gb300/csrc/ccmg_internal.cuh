@@ -146,6 +146,20 @@ struct TmaSweep {
   int ok;                      // 1 when the level uses this path
   int ok_pro;                  // 1 when its first black post-sweep runs fused with the prolongation
 };
+// The finest level of one system of a batch, for the batched TMA-staged half-sweep: its tensor
+// maps (other[c], rhs[c] as in TmaSweep; coarse[] the next level's correction, for the fused
+// prolongation), geometry, iterate, slab length and its first work item in the launch.
+struct BTmaSys {  // aligned as its CUtensorMap members
+  CUtensorMap other[2];
+  CUtensorMap rhs[2];
+  CUtensorMap coarse[2];
+  Geom G;
+  float* x;
+  int sys;
+  int kz;
+  long long w0;     // first work item (items of one system are consecutive)
+  long long nwork;  // tiles x slabs
+};
 bool tma_sweep_applies(const Geom& G);  // the kernel can run on this level
 bool tma_sweep_pays(const Geom& G);     // ... and is the faster of the two here
 // Encode the tensor maps of level arrays x and g (both colours) and size the launch; t.ok = 0
@@ -160,6 +174,20 @@ cudaError_t launch_smooth_tma(float* x, const Geom& G, const InvDiag<float>& inv
 cudaError_t prepare_tma_prolong(TmaSweep& t, const float* ec, const Geom& Gc, const Geom& G, int device);
 cudaError_t launch_smooth_prolong_tma(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t,
                                       float omega, int* err, cudaStream_t s);
+// Batched systems: fills sys (one entry per system: finest level x, g of geometry G, next level xc,
+// Gc packed with whole 4-float rows) with tensor maps, slab lengths and work offsets; returns in
+// *total the number of work items and in *grid the persistent grid of the launches below; *ok = 0
+// when some system does not qualify (then nothing else is written).
+cudaError_t prepare_tma_batch(BTmaSys* sys, int n, float* const* x, const float* const* g, const Geom* G,
+                              const float* const* xc, const Geom* Gc, const int* sys_index, long long* total,
+                              int* grid, int* ok, int device);
+// The batched half-sweep of colour `colour` over the finest levels in the device table d_sys (n
+// entries, total work items), systems with active[sys] == 0 skipped; same results as the
+// single-system sweep of each. The fused prolongation variant: first black post-sweep.
+cudaError_t launch_b_smooth_tma(const BTmaSys* d_sys, int n, long long total, int grid, const int* active,
+                                const InvDiag<float>& inv, int colour, int* err, cudaStream_t s);
+cudaError_t launch_b_smooth_prolong_tma(const BTmaSys* d_sys, int n, long long total, int grid, const int* active,
+                                        const InvDiag<float>& inv, float omega, int* err, cudaStream_t s);
 // Failure-path self-test: the same red half-sweep with one plane copy of every CTA's first item
 // never issued, and a wait budget of budget_cycles; every CTA then sets *err and returns.
 cudaError_t launch_smooth_tma_withheld(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t, int* err,

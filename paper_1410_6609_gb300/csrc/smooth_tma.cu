@@ -16,6 +16,8 @@
 //
 // Every wait on an mbarrier is bounded (clock64 budget); a CTA that runs out sets the context's
 // error flag, waits (bounded) for the copies it has in flight and returns.
+#include <cstring>
+
 #include "ccmg_internal.cuh"
 #include "level_ops.cuh"
 
@@ -24,28 +26,28 @@ namespace {
 
 using ops::inv_of;
 
-constexpr int kTX = 32;    // 4-float vectors per tile row (threads in x)
 constexpr int kHaloX = 4;  // floats on each side of the tile row (16-byte aligned box start)
-constexpr int kBoxX = 4 * kTX + 2 * kHaloX;  // 136
 constexpr long long kWaitCycles = 4000000000LL;  // wait budget, about 2 s at 2 GHz
 
 constexpr int kCHalo = 4;  // coarse floats on each side of a tile's parents (16-byte aligned box start)
-constexpr int kCBoxX = 2 * kTX + 2 * kCHalo;  // 72: parents of the other-colour box, per coarse colour
 
 __host__ __device__ constexpr int round128(int b) { return ((b + 127) / 128) * 128; }
 
-// Tile of TY rows (one per thread row), ring of SLOTS plane slots. PRO: the black sweep fused
-// with the prolongation; each slot then also holds the coarse-correction rows (both coarse
-// colour arrays) under the other-colour box.
-template <int TY, int SLOTS, bool PRO = false, bool PER = false>
+// Tile of TX 4-float vectors (one per thread column) by TY rows (one per thread row), ring of
+// SLOTS plane slots. PRO: the black sweep fused with the prolongation; each slot then also holds
+// the coarse-correction rows (both coarse colour arrays) under the other-colour box.
+template <int TX, int TY, int SLOTS, bool PRO = false, bool PER = false>
 struct Cfg {
+  static constexpr int kTX = TX;
+  static constexpr int kBoxX = 4 * TX + 2 * kHaloX;    // other-colour box width (floats)
+  static constexpr int kCBoxX = 2 * TX + 2 * kCHalo;   // parents of the other-colour box, per coarse colour
   static constexpr int kTY = TY;
   static constexpr int kSlots = SLOTS;
   static constexpr bool kPro = PRO;
   static constexpr bool kPer = PER;  // levels with periodic axes: wrapped halos (the walls-only build keeps its registers)
   static constexpr int kBoxY = TY + 2;
   static constexpr int kBoxBytes = kBoxX * kBoxY * 4;                  // other-colour box
-  static constexpr int kGBoxBytes = 4 * kTX * TY * 4;                  // right-hand-side box
+  static constexpr int kGBoxBytes = 4 * TX * TY * 4;                   // right-hand-side box
   static constexpr int kCBoxY = TY / 2 + 2;                            // coarse rows of the parents
   static constexpr int kCBoxBytes = kCBoxX * kCBoxY * 4;               // one coarse colour's box
   static constexpr int kGOff = round128(kBoxBytes);                    // rhs box within a slot
@@ -59,9 +61,13 @@ struct Cfg {
   static_assert(SLOTS >= 4, "planes k-1, k, k+1 and at least one copy in flight");
   static_assert(TY % 2 == 0, "tiles cover whole coarse rows");
 };
-using Product = Cfg<8, 6>;           // 9600-byte slots, 57.6 KB per CTA, 3 CTAs per SM
-using ProductPer = Cfg<8, 6, false, true>;  // the same on levels with a periodic axis
-using ProductPro = Cfg<8, 5, true>;  // 13184-byte slots, 65.9 KB per CTA, 3 CTAs per SM (6 slots: 2 per SM, slower)
+using Product = Cfg<32, 8, 6>;           // 9600-byte slots, 57.6 KB per CTA, 3 CTAs per SM
+using ProductPer = Cfg<32, 8, 6, false, true>;  // the same on levels with a periodic axis
+using ProductPro = Cfg<32, 8, 5, true>;  // 13184-byte slots, 65.9 KB per CTA, 3 CTAs per SM (6 slots: 2 per SM, slower)
+// Batched systems (rows of 32 to 96 packed values): tiles of 32 packed columns by 32 rows, the
+// same slot sizes (a 40 x 34-float box is 1360 floats, as 136 x 10).
+using BatchCfg = Cfg<8, 32, 6>;
+using BatchPro = Cfg<8, 32, 5, true>;
 // the fused sweep reads the other colour through the plain sweep's tensor maps, whose boxes are
 // Product::kBoxY rows high: the expected transaction bytes must match them
 static_assert(ProductPro::kTY == Product::kTY, "the fused sweep shares the plain sweep's other-colour boxes");
@@ -111,8 +117,9 @@ __device__ __forceinline__ void tma_load_box(unsigned dst, const CUtensorMap* ma
 struct Work {
   int x0, y0, k0, k1;  // tile origin (colour-array index, row) and planes [k0, k1)
 };
-template <int kTY>
+template <class C>
 __device__ __forceinline__ Work work_item(const Geom& G, int kz, long long w) {
+  constexpr int kTX = C::kTX, kTY = C::kTY;
   const int tiles_x = (G.hx + 4 * kTX - 1) / (4 * kTX);
   const int tiles_y = (G.ny + kTY - 1) / kTY;
   const long long per_slab = (long long)tiles_x * tiles_y;
@@ -138,14 +145,21 @@ __device__ __forceinline__ Work work_item(const Geom& G, int kz, long long w) {
 // operations rounded separately as in ops::smooth_vec_prolong; the coarse rows arrive with each
 // red plane (coarse plane floor(p/2) for red plane p), out-of-range parents as zeros, and each
 // landed red plane is corrected once in shared memory before the cells read it.
-template <class C>
-__global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ x, Geom G, InvDiag<float> inv,
-                                                           int colour, int kz, long long nwork,
-                                                           const __grid_constant__ CUtensorMap other,
-                                                           const __grid_constant__ CUtensorMap rhs,
-                                                           const __grid_constant__ CUtensorMap coarse0,
-                                                           const __grid_constant__ CUtensorMap coarse1, float omega,
-                                                           int* err, long long budget, int withhold) {
+// BATCH: the work items of many systems' finest levels (table `bsys` of nbsys systems, items
+// numbered consecutively system by system); each item takes its system's geometry, iterate and
+// tensor maps from the table, and the items of systems whose active flag is 0 are skipped. The
+// arguments x, G, kz and the four maps are then unused.
+template <class C, bool BATCH = false>
+__global__ void __launch_bounds__(C::kTX* C::kTY) k_smooth_tma(float* __restrict__ x0, Geom G0, InvDiag<float> inv,
+                                                              int colour, int kz0, long long nwork,
+                                                              const __grid_constant__ CUtensorMap other,
+                                                              const __grid_constant__ CUtensorMap rhs,
+                                                              const __grid_constant__ CUtensorMap coarse0,
+                                                              const __grid_constant__ CUtensorMap coarse1, float omega,
+                                                              int* err, long long budget, int withhold,
+                                                              const BTmaSys* __restrict__ bsys, int nbsys,
+                                                              const int* __restrict__ active) {
+  constexpr int kTX = C::kTX, kBoxX = C::kBoxX, kCBoxX = C::kCBoxX;
   constexpr int kTY = C::kTY, kSlots = C::kSlots, kBoxBytes = C::kBoxBytes, kGBoxBytes = C::kGBoxBytes;
   constexpr int kGOff = C::kGOff, kSlotBytes = C::kSlotBytes, kCBoxBytes = C::kCBoxBytes;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -161,13 +175,32 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
 
   const unsigned ring0 = smem_addr(ring);
   const unsigned bar0 = smem_addr(bars);
-  float* const xo = x + (long long)colour * G.csz;
   int seq = 0;     // loads issued by this CTA before the current item
   int issued = 0;  // loads issued so far (leader)
   bool failed = false;
+  int sb = 0;      // BATCH: the table entry of the current item (items ascend per CTA)
 
   for (long long w = blockIdx.x; w < nwork && !failed; w += gridDim.x) {
-    const Work t = work_item<kTY>(G, kz, w);
+    // the item's level: the launch's one, or (BATCH) its system's from the table
+    Geom G = G0;
+    float* x = x0;
+    int kz = kz0;
+    long long wl = w;
+    const CUtensorMap *mo = &other, *mr = &rhs, *mc0 = &coarse0, *mc1 = &coarse1;
+    if constexpr (BATCH) {
+      while (sb + 1 < nbsys && bsys[sb + 1].w0 <= w) ++sb;
+      if (!__ldg(active + bsys[sb].sys)) continue;  // uniform over the CTA
+      G = bsys[sb].G;
+      x = bsys[sb].x;
+      kz = bsys[sb].kz;
+      wl = w - bsys[sb].w0;
+      mo = &bsys[sb].other[colour];
+      mr = &bsys[sb].rhs[colour];
+      mc0 = &bsys[sb].coarse[0];
+      mc1 = &bsys[sb].coarse[1];
+    }
+    float* const xo = x + (long long)colour * G.csz;
+    const Work t = work_item<C>(G, kz, wl);
     const int np = (t.k1 - t.k0) + 2;  // other-colour planes k0-1 .. k1
     // load i of the item into slot (seq+i) % kSlots
     auto issue = [&](int i) {
@@ -180,12 +213,12 @@ __global__ void __launch_bounds__(kTX* C::kTY) k_smooth_tma(float* __restrict__ 
       mbar_expect_tx(bar, kBoxBytes + (with_rhs ? kGBoxBytes : 0) + (C::kPro ? 2 * kCBoxBytes : 0));
       int kp = t.k0 - 1 + i;  // other-colour plane; across a periodic z axis the opposite one
       if (C::kPer && (G.per & 4)) kp = kp < 0 ? G.nz - 1 : (kp >= G.nz ? kp - G.nz : kp);
-      tma_load_box(dst, &other, t.x0 - kHaloX, t.y0 - 1, kp, bar);
-      if (with_rhs) tma_load_box(dst + kGOff, &rhs, t.x0, t.y0, t.k0 - 2 + i, bar);
+      tma_load_box(dst, mo, t.x0 - kHaloX, t.y0 - 1, kp, bar);
+      if (with_rhs) tma_load_box(dst + kGOff, mr, t.x0, t.y0, t.k0 - 2 + i, bar);
       if (C::kPro) {
         const int kc = (t.k0 - 1 + i + 2) / 2 - 1;  // floor(p / 2) for red plane p >= -1
-        tma_load_box(dst + C::kC0Off, &coarse0, t.x0 / 2 - kCHalo, t.y0 / 2 - 1, kc, bar);
-        tma_load_box(dst + C::kC1Off, &coarse1, t.x0 / 2 - kCHalo, t.y0 / 2 - 1, kc, bar);
+        tma_load_box(dst + C::kC0Off, mc0, t.x0 / 2 - kCHalo, t.y0 / 2 - 1, kc, bar);
+        tma_load_box(dst + C::kC1Off, mc1, t.x0 / 2 - kCHalo, t.y0 / 2 - 1, kc, bar);
       }
       issued = n + 1;
     };
@@ -480,12 +513,12 @@ cudaError_t size_launch(const Geom& G, int device, int& kz, long long& nwork, in
   cudaError_t e = cudaFuncSetAttribute(k_smooth_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_tma<C>, kTX * C::kTY, C::kSmemBytes)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_tma<C>, C::kTX * C::kTY, C::kSmemBytes)) !=
       cudaSuccess)
     return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const long long tiles = (long long)((G.hx + 4 * kTX - 1) / (4 * kTX)) * ((G.ny + C::kTY - 1) / C::kTY);
+  const long long tiles = (long long)((G.hx + 4 * C::kTX - 1) / (4 * C::kTX)) * ((G.ny + C::kTY - 1) / C::kTY);
   const long long slots = (long long)per_sm * sms;
   // planes per item: long slabs (each starts by loading two extra planes), but at least two
   // items per resident CTA; 64 planes measured best at 512^3
@@ -508,8 +541,8 @@ cudaError_t prepare_tma_sweep_cfg(TmaSweep& t, float* x, const float* g, const G
     const float* gbase = g + (long long)c * G.csz;       // and its own right-hand side
     if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || reinterpret_cast<uintptr_t>(gbase) % 16 != 0)
       return cudaSuccess;
-    if ((e = colour_map(encode, &t.other[c], base, G, kBoxX, C::kBoxY)) != cudaSuccess) return e;
-    if ((e = colour_map(encode, &t.rhs[c], gbase, G, 4 * kTX, C::kTY)) != cudaSuccess) return e;
+    if ((e = colour_map(encode, &t.other[c], base, G, C::kBoxX, C::kBoxY)) != cudaSuccess) return e;
+    if ((e = colour_map(encode, &t.rhs[c], gbase, G, 4 * C::kTX, C::kTY)) != cudaSuccess) return e;
   }
   if ((e = size_launch<C>(G, device, t.kz, t.nwork, t.grid)) != cudaSuccess) return e;
   t.ok = 1;
@@ -531,7 +564,7 @@ cudaError_t prepare_tma_prolong_cfg(TmaSweep& t, const float* ec, const Geom& Gc
   for (int c = 0; c < 2; ++c) {
     const float* base = ec + (long long)c * Gc.csz;
     if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return cudaSuccess;
-    if ((e = colour_map(encode, &t.coarse[c], base, Gc, kCBoxX, C::kCBoxY)) != cudaSuccess) return e;
+    if ((e = colour_map(encode, &t.coarse[c], base, Gc, C::kCBoxX, C::kCBoxY)) != cudaSuccess) return e;
   }
   if ((e = size_launch<C>(G, device, t.kz_pro, t.nwork_pro, t.grid_pro)) != cudaSuccess) return e;
   t.ok_pro = 1;
@@ -542,9 +575,9 @@ template <class C>
 cudaError_t launch_smooth_tma_cfg(float* x, const Geom& G, const InvDiag<float>& inv, int colour, const TmaSweep& t,
                                   int* err, long long budget, int withhold, cudaStream_t s) {
   if (!t.ok) return cudaErrorInvalidValue;
-  k_smooth_tma<C><<<t.grid, dim3(kTX, C::kTY, 1), C::kSmemBytes, s>>>(
+  k_smooth_tma<C><<<t.grid, dim3(C::kTX, C::kTY, 1), C::kSmemBytes, s>>>(
       x, G, inv, colour, t.kz, t.nwork, t.other[colour], t.rhs[colour], t.other[colour], t.other[colour], 0.0f, err,
-      budget, withhold);
+      budget, withhold, nullptr, 0, nullptr);
   return cudaGetLastError();
 }
 
@@ -568,9 +601,94 @@ cudaError_t launch_smooth_tma(float* x, const Geom& G, const InvDiag<float>& inv
 cudaError_t launch_smooth_prolong_tma(float* x, const Geom& G, const InvDiag<float>& inv, const TmaSweep& t,
                                       float omega, int* err, cudaStream_t s) {
   if (!t.ok_pro) return cudaErrorInvalidValue;
-  k_smooth_tma<ProductPro><<<t.grid_pro, dim3(kTX, ProductPro::kTY, 1), ProductPro::kSmemBytes, s>>>(
+  k_smooth_tma<ProductPro><<<t.grid_pro, dim3(ProductPro::kTX, ProductPro::kTY, 1), ProductPro::kSmemBytes, s>>>(
       x, G, inv, 1, t.kz_pro, t.nwork_pro, t.other[1], t.rhs[1], t.coarse[0], t.coarse[1], omega, err, kWaitCycles,
-      -1);
+      -1, nullptr, 0, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_tma_batch(BTmaSys* sys, int n, float* const* x, const float* const* g, const Geom* G,
+                              const float* const* xc, const Geom* Gc, const int* sys_index, long long* total,
+                              int* grid, int* ok, int device) {
+  *ok = 0;
+  for (int i = 0; i < n; ++i) {
+    const Geom &F = G[i], &C = Gc[i];
+    const bool halves = C.nx * 2 == F.nx && C.ny * 2 == F.ny && C.nz * 2 == F.nz;
+    if (!F.packed || F.per || F.hx % 4 != 0 || F.nz < 8 || !C.packed || C.hx % 4 != 0 || !halves) return cudaSuccess;
+    for (int c = 0; c < 2; ++c)
+      if (reinterpret_cast<uintptr_t>(x[i] + c * F.csz) % 16 || reinterpret_cast<uintptr_t>(g[i] + c * F.csz) % 16 ||
+          reinterpret_cast<uintptr_t>(xc[i] + c * C.csz) % 16)
+        return cudaSuccess;
+  }
+  EncodeFn encode = nullptr;
+  cudaError_t e = encoder(&encode);
+  if (e != cudaSuccess) return e;
+  static_assert(BatchPro::kBoxX == BatchCfg::kBoxX && BatchPro::kBoxY == BatchCfg::kBoxY,
+                "the fused batched sweep reads the other colour through the plain sweep's maps");
+  long long w = 0;
+  for (int i = 0; i < n; ++i) {
+    BTmaSys& d = sys[i];
+    std::memset(&d, 0, sizeof(d));
+    const Geom &F = G[i], &C = Gc[i];
+    for (int c = 0; c < 2; ++c) {
+      if ((e = colour_map(encode, &d.other[c], x[i] + (long long)(1 - c) * F.csz, F, BatchCfg::kBoxX,
+                          BatchCfg::kBoxY)) != cudaSuccess)
+        return e;
+      if ((e = colour_map(encode, &d.rhs[c], g[i] + (long long)c * F.csz, F, 4 * BatchCfg::kTX, BatchCfg::kTY)) !=
+          cudaSuccess)
+        return e;
+      if ((e = colour_map(encode, &d.coarse[c], xc[i] + (long long)c * C.csz, C, BatchPro::kCBoxX,
+                          BatchPro::kCBoxY)) != cudaSuccess)
+        return e;
+    }
+    d.G = F;
+    d.x = x[i];
+    d.sys = sys_index[i];
+    d.kz = F.nz < 64 ? F.nz : 64;  // slabs of up to 64 planes
+    const long long tiles =
+        (long long)((F.hx + 4 * BatchCfg::kTX - 1) / (4 * BatchCfg::kTX)) * ((F.ny + BatchCfg::kTY - 1) / BatchCfg::kTY);
+    d.nwork = tiles * ((F.nz + d.kz - 1) / d.kz);
+    d.w0 = w;
+    w += d.nwork;
+  }
+  // persistent grid: the smaller of the two kernels' resident CTAs
+  int per_a = 0, per_b = 0, sms = 0;
+  if ((e = cudaFuncSetAttribute(k_smooth_tma<BatchCfg, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                BatchCfg::kSmemBytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_smooth_tma<BatchPro, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                BatchPro::kSmemBytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, k_smooth_tma<BatchCfg, true>,
+                                                         BatchCfg::kTX * BatchCfg::kTY, BatchCfg::kSmemBytes)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, k_smooth_tma<BatchPro, true>,
+                                                         BatchPro::kTX * BatchPro::kTY, BatchPro::kSmemBytes)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+  const long long slots = (long long)(per_a < per_b ? per_a : per_b) * sms;
+  if (slots < 1) return cudaErrorInvalidConfiguration;
+  *total = w;
+  *grid = (int)(w < slots ? w : slots);
+  *ok = 1;
+  return cudaSuccess;
+}
+
+cudaError_t launch_b_smooth_tma(const BTmaSys* d_sys, int n, long long total, int grid, const int* active,
+                                const InvDiag<float>& inv, int colour, int* err, cudaStream_t s) {
+  CUtensorMap none{};
+  k_smooth_tma<BatchCfg, true><<<grid, dim3(BatchCfg::kTX, BatchCfg::kTY, 1), BatchCfg::kSmemBytes, s>>>(
+      nullptr, Geom{}, inv, colour, 0, total, none, none, none, none, 0.0f, err, kWaitCycles, -1, d_sys, n, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_smooth_prolong_tma(const BTmaSys* d_sys, int n, long long total, int grid, const int* active,
+                                        const InvDiag<float>& inv, float omega, int* err, cudaStream_t s) {
+  CUtensorMap none{};
+  k_smooth_tma<BatchPro, true><<<grid, dim3(BatchPro::kTX, BatchPro::kTY, 1), BatchPro::kSmemBytes, s>>>(
+      nullptr, Geom{}, inv, 1, 0, total, none, none, none, none, omega, err, kWaitCycles, -1, d_sys, n, active);
   return cudaGetLastError();
 }
 

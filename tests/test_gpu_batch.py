@@ -135,3 +135,57 @@ def test_zero_start_without_writing_and_flag_uploads_in_order():
         assert torch.equal(P.solution(), Bt.solution(b)), b
         P.close()
     Bt.close()
+
+
+# Systems whose finest levels all qualify for the TMA-staged batched sweep (packed rows of whole
+# 4-float vectors, next level of half the size with whole vectors), with tiles of 32 packed
+# columns x 32 rows left ragged in x (hx 48, 40), in y (80, 40) and in the slabs (136 planes),
+# and one system with a zero right-hand side (converged before its first cycle: its work items
+# are skipped and its iterate stays zero).
+TMA_SYSTEMS = [
+    dict(dims=(64, 64, 64), h=1.0, bc_type=synth.WALL_BC_TYPE, bc_value=synth.wall_bc_value(1.0)),
+    dict(dims=(96, 80, 48), h=1.0, bc_type=(D, N, N, D, D, N), bc_value=(0.2, 0.0, -0.1, 0.0, 0.0, 0.3)),
+    dict(dims=(80, 40, 136), h=0.5, bc_type=(D,) * 6, bc_value=(0.0, 0.1, 0.0, 0.0, 0.0, 1.0)),
+    dict(dims=(128, 32, 16), h=1.0, bc_type=synth.WALL_BC_TYPE, bc_value=synth.wall_bc_value(-0.5)),
+    dict(dims=(64, 48, 32), h=1.0, bc_type=(D,) * 6, bc_value=(0.0,) * 6),
+]
+
+
+def _solve_batch(systems, rho, sweep):
+    import os
+    old = os.environ.get("CCMG_SWEEP")
+    if sweep:
+        os.environ["CCMG_SWEEP"] = sweep
+    try:
+        Bt = BatchPoisson(systems, precision="mixed")
+    finally:
+        if old is None:
+            os.environ.pop("CCMG_SWEEP", None)
+        else:
+            os.environ["CCMG_SWEEP"] = old
+    for b, r in enumerate(rho):
+        Bt.set_rhs(b, r)
+    cyc, rel = Bt.solve(1e-9, 50)
+    sols = [Bt.solution(b) for b in range(len(systems))]
+    Bt.close()
+    return cyc, rel, sols
+
+
+def test_tma_staged_batch_equals_direct_load_batch_and_single_contexts():
+    rho = [torch.from_numpy(synth.random_field(s["dims"], 60 + i)).cuda() for i, s in enumerate(TMA_SYSTEMS)]
+    rho[-1].zero_()
+    ct, rt, st = _solve_batch(TMA_SYSTEMS, rho, None)   # TMA-staged finest-level sweeps
+    cv, rv, sv = _solve_batch(TMA_SYSTEMS, rho, "vec")  # direct-load sweeps everywhere
+    assert ct == cv and rt == rv
+    assert ct[-1] == 0 and not torch.any(st[-1] != 0)
+    for b, s in enumerate(TMA_SYSTEMS):
+        assert torch.equal(st[b], sv[b]), b
+        P = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision="mixed")
+        P.set_rhs(rho[b])
+        k, r = P.solve(1e-9, 50)
+        assert (k, r) == (ct[b], rt[b]), b
+        assert torch.equal(P.solution(), st[b]), b
+        P.close()
+        if b < len(TMA_SYSTEMS) - 1:
+            f = oracle.rhs(rho[b].cpu().numpy(), s["h"], s["bc_type"], s["bc_value"])
+            assert oracle.rel_residual(st[b].cpu().numpy(), f, s["h"], s["bc_type"]) < 1.0001e-9, b
