@@ -304,12 +304,15 @@ long long mg_kernel_launches(const mg_ctx* ctx);
 /* Which kernel performs the half-sweeps of a non-coarsest level: 1 = the TMA-staged z-slab
  * kernel, 0 = the vectorised direct-load kernel; -1 for an invalid context or level. Both give
  * bit-identical results. MG_MIXED takes the TMA kernel on single-precision levels with rows of
- * whole 4-float vectors, at least 8 planes and 2^24 cells per colour (where it measured faster).
- * The environment variable CCMG_SWEEP, read by mg_create, overrides this: "vec" never uses it,
- * "tma" uses it on every level it can run on (2^16 cells per colour and up). */
+ * whole 4-float vectors, at least 8 planes and 2^24 cells per colour (where it measured faster);
+ * MG_FP64 takes its FP64 counterpart on levels without a periodic axis, with rows of whole
+ * 2-double vectors, at least 8 planes and 2^22 cells per colour. The environment variable
+ * CCMG_SWEEP, read by mg_create, overrides this: "vec" never uses them, "tma" uses them on every
+ * level they can run on (2^16 cells per colour and up). */
 int mg_level_sweep_kind(const mg_ctx* ctx, int level);
 /* Self-test of the device-side failure path (not in the paper): runs one TMA-staged red
- * half-sweep of `level` in which every CTA leaves one of its plane copies unissued, with a wait
+ * half-sweep of `level` (single precision in MG_MIXED, FP64 in MG_FP64) in which every CTA leaves
+ * one of its plane copies unissued, with a wait
  * budget of 2e7 clock cycles (about 10 ms). Each CTA's wait for that copy runs out; it sets the
  * context's error flag, waits for the copies it did issue and returns without writing the level.
  * Returns MG_ERR_TIMEOUT when the flag came back as expected (and clears it; later calls work

@@ -54,6 +54,7 @@ struct mg_ctx {
   double* d_sph = nullptr;  // step_host scratch: 8*P doubles (centres, radius, density, forces)
   int sph_cap = 0;
   TmaSweep tma[kMaxLevels]{};  // TMA-staged single-precision half-sweeps, per level
+  TmaSweep tma64[kMaxLevels]{};  // TMA-staged FP64 half-sweeps (FP64 mode), per level
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
   double* d_bcf[6] = {};       // per-cell wall values of each face (allocated on first use)
@@ -124,9 +125,13 @@ void free_all(mg_ctx* c) {
 // not from a zero iterate), else the vectorised one; identical results.
 template <typename T>
 cudaError_t sweep(mg_ctx* c, T* x, const T* g, const InvDiag<T>& inv, int l, int colour, bool zero, cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value)
+  if constexpr (std::is_same<T, float>::value) {
     if (!zero && c->tma[l].ok && x == c->x32[l] && g == c->g32[l])
       return launch_smooth_tma(x, c->geo[l], inv, colour, c->tma[l], c->d_err, s);
+  } else {
+    if (!zero && c->tma64[l].ok && x == c->x64[l] && g == c->g64[l])
+      return launch_smooth_tma64(x, c->geo[l], inv, colour, c->tma64[l], c->d_err, s);
+  }
   return launch_smooth<T>(x, g, c->geo[l], inv, colour, zero, s);
 }
 
@@ -483,6 +488,13 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
         if (e == cudaSuccess) e = prepare_tma_prolong(c->tma[l], c->x32[l + 1], c->geo[l + 1], c->geo[l], dev);
       }
   }
+  if (!mixed(c) && !no_tma) {  // FP64 mode: the FP64 half-sweeps of the large levels staged the same way
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    for (int l = 0; l + 1 < c->L && e == cudaSuccess; ++l)
+      if (all_tma ? tma_sweep64_applies(c->geo[l]) : tma_sweep64_pays(c->geo[l]))
+        e = prepare_tma_sweep64(c->tma64[l], c->x64[l], c->g64[l], c->geo[l], dev);
+  }
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     std::string msg = std::string("mg_create: ") + cudaGetErrorString(e);
@@ -535,11 +547,16 @@ long long mg_kernel_launches(const mg_ctx* c) { return c ? c->launches : 0; }
 
 mg_status mg_selftest_wait_timeout(mg_ctx* c, int level) {
   if (!c) return MG_ERR_INVALID;
-  if (level < 0 || level >= c->L - 1 || !c->tma[level].ok)
+  if (level < 0 || level >= c->L - 1 || !(c->tma[level].ok || c->tma64[level].ok))
     return fail(c, MG_ERR_INVALID, "the level has no TMA-staged half-sweep");
-  CK(launch_smooth_tma_withheld(c->x32[level], c->geo[level], c->inv32, c->tma[level], c->d_err, 20000000LL,
-                                c->stream),
-     "wait-timeout self-test");
+  if (c->tma[level].ok)
+    CK(launch_smooth_tma_withheld(c->x32[level], c->geo[level], c->inv32, c->tma[level], c->d_err, 20000000LL,
+                                  c->stream),
+       "wait-timeout self-test");
+  else
+    CK(launch_smooth_tma64_withheld(c->x64[level], c->geo[level], c->inv64, c->tma64[level], c->d_err, 20000000LL,
+                                    c->stream),
+       "wait-timeout self-test");
   c->launches += 1;
   CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "self-test flag");
   CK(cudaStreamSynchronize(c->stream), "self-test sync");
@@ -548,7 +565,7 @@ mg_status mg_selftest_wait_timeout(mg_ctx* c, int level) {
 
 int mg_level_sweep_kind(const mg_ctx* c, int level) {
   if (!c || level < 0 || level >= c->L - 1) return -1;
-  return c->tma[level].ok ? 1 : 0;
+  return (c->tma[level].ok || c->tma64[level].ok) ? 1 : 0;
 }
 
 mg_status mg_set_bc_values(mg_ctx* c, const double* v) {
@@ -1070,8 +1087,7 @@ mg_status mg_op_smooth(mg_ctx* c, int level, int colour) {
   else if (mixed(c))
     CK(sweep<float>(c, c->x32[level], c->g32[level], c->inv32, level, colour, false, c->stream), "smooth");
   else
-    CK(launch_smooth<double>(c->x64[level], c->g64[level], c->geo[level], c->inv64, colour, false, c->stream),
-       "smooth");
+    CK(sweep<double>(c, c->x64[level], c->g64[level], c->inv64, level, colour, false, c->stream), "smooth");
   c->launches += 1;
   return MG_OK;
 }

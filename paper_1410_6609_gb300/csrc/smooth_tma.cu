@@ -24,6 +24,9 @@
 namespace ccmg {
 namespace {
 
+using ops::FxOp;
+using ops::fx_op;
+using ops::fx_sum6;
 using ops::inv_of;
 
 constexpr int kHaloX = 4;  // floats on each side of the tile row (16-byte aligned box start)
@@ -458,6 +461,168 @@ __global__ void __launch_bounds__(C::kTX* C::kTY) k_smooth_tma(float* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP64 half-sweep with TMA z-slab staging (FP64 mode, levels without a periodic axis). The
+// arithmetic is that of ops::smooth_vec<double>: the six-neighbour sum in exact fixed point
+// (fx_sum6), then (g + S) / (6 + d) by the stored reciprocal, so the results are bit-identical.
+// The direct-load kernel converts each neighbour every time a cell reads it (about 5.5
+// conversions per cell); here every value of a landed other-colour plane is converted once into a
+// ring of four converted planes (FxOp, 12 bytes per value) and the cells read their operands from
+// there. A CTA of 32 x 8 threads owns a tile of 64 x 8 cells of the colour (two per thread, a
+// 16-byte vector) and marches it through a slab of planes; the other colour's planes arrive as
+// 68 x 10-double boxes (tile plus a one-row and a 2-double x halo, 16-byte aligned start), with
+// the tile's right-hand side one plane behind, in four raw slots. Load i (other-colour plane
+// k0-1+i, right-hand-side plane k0-2+i for i >= 2) goes to raw slot and converted plane
+// (seq + i) % 4. At plane k (load i+1 just landed and converted) one barrier publishes the
+// conversion and retires plane k-1, whose raw slot (load i) is refilled with load i+4; the
+// converted plane overwritten by load i+1 was last read at plane k-2.
+constexpr int k64TX = 32, k64TY = 8;
+constexpr int k64Halo = 2;                              // doubles on each side of a tile row
+constexpr int k64BoxX = 2 * k64TX + 2 * k64Halo;        // 68
+constexpr int k64BoxY = k64TY + 2;                      // 10
+constexpr int k64BoxN = k64BoxX * k64BoxY;              // values per converted plane
+constexpr int k64BoxBytes = k64BoxN * 8;                // 5440
+constexpr int k64GBoxBytes = 2 * k64TX * k64TY * 8;     // 4096
+constexpr int k64GOff = round128(k64BoxBytes);
+constexpr int k64SlotBytes = round128(k64GOff + k64GBoxBytes);  // 9600
+constexpr int k64Slots = 4;
+constexpr int k64Fx = 4;  // converted planes
+constexpr int k64SmemBytes = k64Slots * k64SlotBytes + k64Fx * k64BoxN * (8 + 4) + 8 * k64Slots;
+static_assert(k64GOff % 128 == 0 && k64SlotBytes % 128 == 0, "TMA destinations need 128-byte alignment");
+static_assert((k64Slots * k64SlotBytes) % 8 == 0 && (k64Fx * k64BoxN * 8) % 8 == 0, "ring alignment");
+
+__global__ void __launch_bounds__(k64TX* k64TY) k_smooth_tma64(double* __restrict__ x, Geom G, InvDiag<double> inv,
+                                                              int colour, int kz, long long nwork,
+                                                              const __grid_constant__ CUtensorMap other,
+                                                              const __grid_constant__ CUtensorMap rhs, int* err,
+                                                              long long budget, int withhold) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* raw = smem;
+  unsigned long long* fS = reinterpret_cast<unsigned long long*>(smem + k64Slots * k64SlotBytes);
+  unsigned* fP = reinterpret_cast<unsigned*>(fS + k64Fx * k64BoxN);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(fP + k64Fx * k64BoxN);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * k64TX + tx;
+  const bool leader = tid == 0;
+  if (leader) {
+    for (int q = 0; q < k64Slots; ++q) mbar_init(smem_addr(bars + q), 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const unsigned raw0 = smem_addr(raw), bar0 = smem_addr(bars);
+  double* const xo = x + (long long)colour * G.csz;
+  int seq = 0, issued = 0;
+  bool failed = false;
+  for (long long w = blockIdx.x; w < nwork && !failed; w += gridDim.x) {
+    const int tiles_x = (G.hx + 2 * k64TX - 1) / (2 * k64TX), tiles_y = (G.ny + k64TY - 1) / k64TY;
+    const long long per_slab = (long long)tiles_x * tiles_y;
+    const int slab = (int)(w / per_slab), rem = (int)(w - per_slab * slab);
+    const int x0 = (rem % tiles_x) * 2 * k64TX, y0 = (rem / tiles_x) * k64TY;
+    const int k0 = slab * kz, k1 = min(k0 + kz, G.nz);
+    const int np = (k1 - k0) + 2;
+    auto issue = [&](int i) {
+      if (seq == 0 && i == withhold) return;  // the failure-path self-test only
+      const int n = seq + i, q = n % k64Slots;
+      const unsigned bar = bar0 + 8u * q, dst = raw0 + (unsigned)(q * k64SlotBytes);
+      mbar_expect_tx(bar, k64BoxBytes + (i >= 2 ? k64GBoxBytes : 0));
+      tma_load_box(dst, &other, x0 - k64Halo, y0 - 1, k0 - 1 + i, bar);
+      if (i >= 2) tma_load_box(dst + k64GOff, &rhs, x0, y0, k0 - 2 + i, bar);
+      issued = n + 1;
+    };
+    auto wait = [&](int i) {
+      const int n = seq + i;
+      return mbar_wait(bar0 + 8u * (unsigned)(n % k64Slots), (unsigned)((n / k64Slots) & 1), budget);
+    };
+    // load i's other-colour plane into converted plane (seq + i) % k64Fx
+    auto convert = [&](int i) {
+      const int n = seq + i;
+      const double* src = reinterpret_cast<const double*>(raw + (n % k64Slots) * k64SlotBytes);
+      unsigned long long* dS = fS + (n % k64Fx) * k64BoxN;
+      unsigned* dP = fP + (n % k64Fx) * k64BoxN;
+      for (int f = tid; f < k64BoxN; f += k64TX * k64TY) {
+        const FxOp o = fx_op(src[f]);
+        dS[f] = ((unsigned long long)o.hi << 32) | o.lo;
+        dP[f] = o.pk;
+      }
+    };
+    auto get = [&](int plane_slot, int idx) -> FxOp {
+      const unsigned long long v = fS[plane_slot * k64BoxN + idx];
+      FxOp o;
+      o.lo = (unsigned)v;
+      o.hi = (unsigned)(v >> 32);
+      o.pk = fP[plane_slot * k64BoxN + idx];
+      return o;
+    };
+    __syncthreads();  // every thread is done with the previous item's slots
+    if (leader)
+      for (int i = 0; i < np && i < k64Slots; ++i) issue(i);
+    bool ok = wait(0) && wait(1);
+    const int m0 = x0 + 2 * tx, j = y0 + ty;
+    const bool mine = m0 < G.hx && j < G.ny;
+    const bool xy_wall = j == 0 || j == G.ny - 1 || m0 == 0 || m0 + 2 >= G.hx;
+    const int c0 = (ty + 1) * k64BoxX + k64Halo + 2 * tx;  // box position of m0 in row j
+    if (ok) {
+      convert(0);
+      convert(1);
+    }
+    double* xrow = xo + ((long long)k0 * G.ny + j) * G.hx + m0;
+    const long long plane_stride = (long long)G.ny * G.hx;
+    for (int k = k0; k < k1; ++k) {
+      const int i = k - k0 + 1;  // load index of plane k
+      ok = ok && wait(i + 1);
+      if (ok) convert(i + 1);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      if (leader) {  // raw slots whose planes are converted and right-hand sides used
+        if (i == 1 && k64Slots < np) issue(k64Slots);
+        if (i + k64Slots < np) issue(i + k64Slots);
+      }
+      if (mine) {
+        const int fm = (seq + i - 1) % k64Fx, fk = (seq + i) % k64Fx, fp = (seq + i + 1) % k64Fx;
+        const int s = (j + k + colour) & 1;
+        // x-neighbours: other colour at m + s - 1 and m + s for cells m0 and m0 + 1
+        const FxOp xa = get(fk, c0 + s - 1), xb = get(fk, c0 + s), xc = get(fk, c0 + s + 1);
+        const FxOp ym0 = get(fk, c0 - k64BoxX), ym1 = get(fk, c0 - k64BoxX + 1);
+        const FxOp yp0 = get(fk, c0 + k64BoxX), yp1 = get(fk, c0 + k64BoxX + 1);
+        const FxOp zm0 = get(fm, c0), zm1 = get(fm, c0 + 1), zp0 = get(fp, c0), zp1 = get(fp, c0 + 1);
+        const double2 gv = *reinterpret_cast<const double2*>(
+            raw + ((seq + i + 1) % k64Slots) * k64SlotBytes + k64GOff + (ty * 2 * k64TX + 2 * tx) * 8);
+        double invd[2];
+        if (xy_wall || k == 0 || k == G.nz - 1) {
+          int dbase = 0;
+          if (j == 0) dbase += G.sh[2];
+          if (j == G.ny - 1) dbase += G.sh[3];
+          if (k == 0) dbase += G.sh[4];
+          if (k == G.nz - 1) dbase += G.sh[5];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            int d = dbase;
+            if (m0 + e == 0 && s == 0) d += G.sh[0];
+            if (m0 + e == G.hx - 1 && s == 1) d += G.sh[1];
+            invd[e] = inv_of(inv, d);
+          }
+        } else {
+          invd[0] = invd[1] = inv.v[3];
+        }
+        const FxOp op0[6] = {xa, xb, ym0, yp0, zm0, zp0};
+        const FxOp op1[6] = {xb, xc, ym1, yp1, zm1, zp1};
+        const double o0 = (gv.x + fx_sum6(op0)) * invd[0];
+        const double o1 = (gv.y + fx_sum6(op1)) * invd[1];
+        *reinterpret_cast<double2*>(xrow) = make_double2(o0, o1);
+      }
+      xrow += plane_stride;
+    }
+    seq += np;
+  }
+  if (failed && leader) {
+    atomicExch(err, 1);
+    for (int n = issued > k64Slots ? issued - k64Slots : 0; n < issued; ++n)
+      if (!(seq == 0 && n == withhold))
+        mbar_wait(bar0 + 8u * (unsigned)(n % k64Slots), (unsigned)((n / k64Slots) & 1), budget);
+  }
+}
+
 }  // namespace
 
 bool tma_sweep_applies(const Geom& G) {
@@ -581,7 +746,76 @@ cudaError_t launch_smooth_tma_cfg(float* x, const Geom& G, const InvDiag<float>&
   return cudaGetLastError();
 }
 
+// The FP64 sweep: 3D double map of one colour array of level G.
+cudaError_t colour_map64(EncodeFn encode, CUtensorMap* map, const double* base, const Geom& G, int box_x, int box_y) {
+  const cuuint64_t dims[3] = {(cuuint64_t)G.hx, (cuuint64_t)G.ny, (cuuint64_t)G.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)G.hx * 8, (cuuint64_t)G.hx * G.ny * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+bool tma_sweep64_applies(const Geom& G) {
+  // rows of whole 16-byte vectors, enough planes to march, walls only (no periodic axis)
+  return G.packed && (G.hx % 2) == 0 && G.nz >= 8 && G.per == 0 && (long long)G.hx * G.ny * G.nz >= (1LL << 16);
+}
+
+bool tma_sweep64_pays(const Geom& G) { return tma_sweep64_applies(G) && (long long)G.hx * G.ny * G.nz >= (1LL << 22); }
+
+cudaError_t prepare_tma_sweep64(TmaSweep& t, double* x, const double* g, const Geom& G, int device) {
+  t.ok = 0;
+  if (!tma_sweep64_applies(G)) return cudaSuccess;
+  EncodeFn encode = nullptr;
+  cudaError_t e = encoder(&encode);
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < 2; ++c) {
+    const double* base = x + (long long)(1 - c) * G.csz;
+    const double* gbase = g + (long long)c * G.csz;
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || reinterpret_cast<uintptr_t>(gbase) % 16 != 0)
+      return cudaSuccess;
+    if ((e = colour_map64(encode, &t.other[c], base, G, k64BoxX, k64BoxY)) != cudaSuccess) return e;
+    if ((e = colour_map64(encode, &t.rhs[c], gbase, G, 2 * k64TX, k64TY)) != cudaSuccess) return e;
+  }
+  if ((e = cudaFuncSetAttribute(k_smooth_tma64, cudaFuncAttributeMaxDynamicSharedMemorySize, k64SmemBytes)) !=
+      cudaSuccess)
+    return e;
+  int per_sm = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_tma64, k64TX * k64TY, k64SmemBytes)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long tiles = (long long)((G.hx + 2 * k64TX - 1) / (2 * k64TX)) * ((G.ny + k64TY - 1) / k64TY);
+  const long long slots = (long long)per_sm * sms;
+  int kz = 64;
+  while (kz > 8 && tiles * ((G.nz + kz - 1) / kz) < 2 * slots) kz /= 2;
+  t.kz = kz;
+  t.nwork = tiles * ((G.nz + kz - 1) / kz);
+  t.grid = (int)(t.nwork < slots ? t.nwork : slots);
+  t.ok = 1;
+  return cudaSuccess;
+}
+
+cudaError_t launch_smooth_tma64(double* x, const Geom& G, const InvDiag<double>& inv, int colour, const TmaSweep& t,
+                                int* err, cudaStream_t s) {
+  if (!t.ok) return cudaErrorInvalidValue;
+  k_smooth_tma64<<<t.grid, dim3(k64TX, k64TY, 1), k64SmemBytes, s>>>(
+      x, G, inv, colour, t.kz, t.nwork, t.other[colour], t.rhs[colour], err, kWaitCycles, -1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_tma64_withheld(double* x, const Geom& G, const InvDiag<double>& inv, const TmaSweep& t,
+                                         int* err, long long budget_cycles, cudaStream_t s) {
+  if (!t.ok) return cudaErrorInvalidValue;
+  k_smooth_tma64<<<t.grid, dim3(k64TX, k64TY, 1), k64SmemBytes, s>>>(x, G, inv, 0, t.kz, t.nwork, t.other[0],
+                                                                    t.rhs[0], err, budget_cycles, 2);
+  return cudaGetLastError();
+}
 
 cudaError_t prepare_tma_sweep(TmaSweep& t, float* x, const float* g, const Geom& G, int device) {
   return G.per ? prepare_tma_sweep_cfg<ProductPer>(t, x, g, G, device)

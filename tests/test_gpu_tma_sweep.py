@@ -259,3 +259,98 @@ def test_fused_prolongation_sweep_against_oracle(dims, policy):
     assert np.array_equal(Q.level_get(0, 0).cpu().numpy()[black], out[black])
     P.close()
     Q.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# The FP64 half-sweep staged the same way (FP64 mode): the neighbour sum in exact fixed point from
+# planes converted once, against the direct-load FP64 sweep (same operands, same exact sum: the
+# same bits) and the oracle's FP64 half-sweep. Tiles of 64 x 8 cells of a colour, ragged in x
+# (hx 100, 68), in y (88, 40) and in the slabs.
+
+def _fp64_pair(dims, **kw):
+    from paper_1410_6609_gb300.solver import Poisson
+
+    out = []
+    for kind in ("tma", "vec"):
+        old = os.environ.get("CCMG_SWEEP")
+        os.environ["CCMG_SWEEP"] = kind
+        try:
+            out.append(Poisson(dims, precision="fp64", **kw))
+        finally:
+            if old is None:
+                del os.environ["CCMG_SWEEP"]
+            else:
+                os.environ["CCMG_SWEEP"] = old
+    return out
+
+
+@pytest.mark.parametrize("dims", [(200, 88, 72), (256, 64, 96), (136, 40, 32), (512, 24, 48)])
+def test_fp64_tma_half_sweeps_bit_identical_and_match_oracle(dims):
+    a, b = _fp64_pair(dims, bc_type=BC_MIX, bc_value=(0.0, 1.0, -0.5, 0.25, 0.0, 2.0))
+    assert a.level_sweep_kind(0) == "tma" and b.level_sweep_kind(0) == "vec"
+    nx, ny, nz = dims
+    rng = np.random.default_rng(sum(dims) + 1)
+    phi = rng.standard_normal((nz, ny, nx))
+    f = rng.standard_normal((nz, ny, nx)) * 3.0
+    for colour in (0, 1):
+        for P in (a, b):
+            P.level_set(0, 0, torch.from_numpy(phi).cuda())
+            P.level_set(0, 1, torch.from_numpy(f).cuda())
+            P.op_smooth(0, colour)
+        xa = a.level_get(0, 0)
+        assert torch.equal(xa, b.level_get(0, 0)), colour
+        ref = oracle.rbgs_half(phi, f, 1.0, BC_MIX, colour)
+        assert _maxrel(xa.cpu().numpy(), ref) < 1e-14
+    for colour in (0, 1, 1, 0, 1, 0):  # from the state left above
+        a.op_smooth(0, colour)
+        b.op_smooth(0, colour)
+        assert torch.equal(a.level_get(0, 0), b.level_get(0, 0)), colour
+    a.close()
+    b.close()
+
+
+def test_fp64_tma_default_policy_and_solve_bit_identical():
+    """By default FP64 levels of 2^22 cells per colour and more take the staged sweep; a whole FP64
+    solve with it equals the direct-load one bit for bit."""
+    from paper_1410_6609_gb300 import synth
+    from paper_1410_6609_gb300.solver import Poisson
+
+    dims = (256, 256, 128)
+    P = Poisson(dims, precision="fp64")
+    assert [P.level_sweep_kind(l) for l in range(2)] == ["tma", "vec"]
+    P.close()
+    a, b = _fp64_pair(dims, bc_type=(N, N, N, N, D, D), bc_value=(0, 0, 0, 0, 0.0, 1.0))
+    rho = torch.from_numpy(synth.random_field(dims, 77)).cuda()
+    out = []
+    for P in (a, b):
+        P.set_rhs(rho)
+        P.set_solution(None)
+        k, rel = P.solve(1e-10, 40)
+        out.append((k, rel, P.solution()))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and out[0][1] < 1e-10
+    assert torch.equal(out[0][2], out[1][2])
+    a.close()
+    b.close()
+
+
+def test_fp64_tma_wait_timeout_reported_and_context_usable():
+    from paper_1410_6609_gb300 import _lib
+
+    dims = (128, 64, 64)
+    a, b = _fp64_pair(dims)
+    assert a.level_sweep_kind(0) == "tma"
+    rng = np.random.default_rng(5)
+    phi = torch.from_numpy(rng.standard_normal((64, 64, 128))).cuda()
+    f = torch.from_numpy(rng.standard_normal((64, 64, 128))).cuda()
+    for P in (a, b):
+        P.level_set(0, 0, phi)
+        P.level_set(0, 1, f)
+    before = a.level_get(0, 0)
+    assert a.lib.mg_selftest_wait_timeout(a.ctx, 0) == _lib.MG_ERR_TIMEOUT
+    assert torch.equal(a.level_get(0, 0), before)
+    for colour in (0, 1):
+        a.op_smooth(0, colour)
+        b.op_smooth(0, colour)
+    assert torch.equal(a.level_get(0, 0), b.level_get(0, 0))
+    a.close()
+    b.close()
