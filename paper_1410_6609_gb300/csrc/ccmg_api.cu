@@ -130,7 +130,7 @@ cudaError_t sweep(mg_ctx* c, T* x, const T* g, const InvDiag<T>& inv, int l, int
       return launch_smooth_tma(x, c->geo[l], inv, colour, c->tma[l], c->d_err, s);
   } else {
     if (!zero && c->tma64[l].ok && x == c->x64[l] && g == c->g64[l])
-      return launch_smooth_tma64(x, c->geo[l], inv, colour, c->tma64[l], c->d_err, s);
+      return launch_smooth_tma64(x, g, c->geo[l], inv, colour, c->tma64[l], c->d_err, s);
   }
   return launch_smooth<T>(x, g, c->geo[l], inv, colour, zero, s);
 }
@@ -554,7 +554,7 @@ mg_status mg_selftest_wait_timeout(mg_ctx* c, int level) {
                                   c->stream),
        "wait-timeout self-test");
   else
-    CK(launch_smooth_tma64_withheld(c->x64[level], c->geo[level], c->inv64, c->tma64[level], c->d_err, 20000000LL,
+    CK(launch_smooth_tma64_withheld(c->x64[level], c->g64[level], c->geo[level], c->inv64, c->tma64[level], c->d_err, 20000000LL,
                                     c->stream),
        "wait-timeout self-test");
   c->launches += 1;

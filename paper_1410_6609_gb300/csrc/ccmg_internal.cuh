@@ -165,9 +165,9 @@ struct BTmaSys {  // aligned as its CUtensorMap members
 bool tma_sweep64_applies(const Geom& G);
 bool tma_sweep64_pays(const Geom& G);
 cudaError_t prepare_tma_sweep64(TmaSweep& t, double* x, const double* g, const Geom& G, int device);
-cudaError_t launch_smooth_tma64(double* x, const Geom& G, const InvDiag<double>& inv, int colour, const TmaSweep& t,
+cudaError_t launch_smooth_tma64(double* x, const double* g, const Geom& G, const InvDiag<double>& inv, int colour, const TmaSweep& t,
                                 int* err, cudaStream_t s);
-cudaError_t launch_smooth_tma64_withheld(double* x, const Geom& G, const InvDiag<double>& inv, const TmaSweep& t,
+cudaError_t launch_smooth_tma64_withheld(double* x, const double* g, const Geom& G, const InvDiag<double>& inv, const TmaSweep& t,
                                          int* err, long long budget_cycles, cudaStream_t s);
 bool tma_sweep_applies(const Geom& G);  // the kernel can run on this level
 bool tma_sweep_pays(const Geom& G);     // ... and is the faster of the two here

@@ -470,32 +470,30 @@ __global__ void __launch_bounds__(C::kTX* C::kTY) k_smooth_tma(float* __restrict
 // ring of four converted planes (FxOp, 12 bytes per value) and the cells read their operands from
 // there. A CTA of 32 x 8 threads owns a tile of 64 x 8 cells of the colour (two per thread, a
 // 16-byte vector) and marches it through a slab of planes; the other colour's planes arrive as
-// 68 x 10-double boxes (tile plus a one-row and a 2-double x halo, 16-byte aligned start), with
-// the tile's right-hand side one plane behind, in four raw slots. Load i (other-colour plane
-// k0-1+i, right-hand-side plane k0-2+i for i >= 2) goes to raw slot and converted plane
-// (seq + i) % 4. At plane k (load i+1 just landed and converted) one barrier publishes the
-// conversion and retires plane k-1, whose raw slot (load i) is refilled with load i+4; the
-// converted plane overwritten by load i+1 was last read at plane k-2.
+// 68 x 10-double boxes (tile plus a one-row and a 2-double x halo, 16-byte aligned start) in
+// four raw slots; the right-hand side, read once, comes by a plain vector load issued before the
+// plane's wait, which keeps the shared memory at 54.7 KB and four CTAs on an SM (with it in the
+// ring: 71 KB, three CTAs, 6 % slower at 512^3). Load i (other-colour plane k0-1+i) goes to raw
+// slot and converted plane (seq + i) % 4. At plane k (load i+1 just landed and converted) one
+// barrier publishes the conversion and retires plane k-1, whose raw slot (load i) is refilled
+// with load i+4; the converted plane overwritten by load i+1 was last read at plane k-2.
 constexpr int k64TX = 32, k64TY = 8;
 constexpr int k64Halo = 2;                              // doubles on each side of a tile row
 constexpr int k64BoxX = 2 * k64TX + 2 * k64Halo;        // 68
 constexpr int k64BoxY = k64TY + 2;                      // 10
 constexpr int k64BoxN = k64BoxX * k64BoxY;              // values per converted plane
 constexpr int k64BoxBytes = k64BoxN * 8;                // 5440
-constexpr int k64GBoxBytes = 2 * k64TX * k64TY * 8;     // 4096
-constexpr int k64GOff = round128(k64BoxBytes);
-constexpr int k64SlotBytes = round128(k64GOff + k64GBoxBytes);  // 9600
+constexpr int k64SlotBytes = round128(k64BoxBytes);    // 5504
 constexpr int k64Slots = 4;
 constexpr int k64Fx = 4;  // converted planes
 constexpr int k64SmemBytes = k64Slots * k64SlotBytes + k64Fx * k64BoxN * (8 + 4) + 8 * k64Slots;
-static_assert(k64GOff % 128 == 0 && k64SlotBytes % 128 == 0, "TMA destinations need 128-byte alignment");
+static_assert(k64SlotBytes % 128 == 0, "TMA destinations need 128-byte alignment");
 static_assert((k64Slots * k64SlotBytes) % 8 == 0 && (k64Fx * k64BoxN * 8) % 8 == 0, "ring alignment");
 
-__global__ void __launch_bounds__(k64TX* k64TY) k_smooth_tma64(double* __restrict__ x, Geom G, InvDiag<double> inv,
-                                                              int colour, int kz, long long nwork,
-                                                              const __grid_constant__ CUtensorMap other,
-                                                              const __grid_constant__ CUtensorMap rhs, int* err,
-                                                              long long budget, int withhold) {
+__global__ void __launch_bounds__(k64TX* k64TY, 4)
+    k_smooth_tma64(double* __restrict__ x, const double* __restrict__ g, Geom G, InvDiag<double> inv, int colour, int kz,
+                   long long nwork, const __grid_constant__ CUtensorMap other, int* err, long long budget,
+                   int withhold) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* raw = smem;
   unsigned long long* fS = reinterpret_cast<unsigned long long*>(smem + k64Slots * k64SlotBytes);
@@ -523,9 +521,8 @@ __global__ void __launch_bounds__(k64TX* k64TY) k_smooth_tma64(double* __restric
       if (seq == 0 && i == withhold) return;  // the failure-path self-test only
       const int n = seq + i, q = n % k64Slots;
       const unsigned bar = bar0 + 8u * q, dst = raw0 + (unsigned)(q * k64SlotBytes);
-      mbar_expect_tx(bar, k64BoxBytes + (i >= 2 ? k64GBoxBytes : 0));
+      mbar_expect_tx(bar, k64BoxBytes);
       tma_load_box(dst, &other, x0 - k64Halo, y0 - 1, k0 - 1 + i, bar);
-      if (i >= 2) tma_load_box(dst + k64GOff, &rhs, x0, y0, k0 - 2 + i, bar);
       issued = n + 1;
     };
     auto wait = [&](int i) {
@@ -565,9 +562,12 @@ __global__ void __launch_bounds__(k64TX* k64TY) k_smooth_tma64(double* __restric
       convert(1);
     }
     double* xrow = xo + ((long long)k0 * G.ny + j) * G.hx + m0;
+    const double* grow = g + (xrow - x);
     const long long plane_stride = (long long)G.ny * G.hx;
     for (int k = k0; k < k1; ++k) {
       const int i = k - k0 + 1;  // load index of plane k
+      // the cell pair's right-hand side, read while the plane's copy lands and is converted
+      const double2 gv = mine ? __ldg(reinterpret_cast<const double2*>(grow)) : make_double2(0.0, 0.0);
       ok = ok && wait(i + 1);
       if (ok) convert(i + 1);
       if (__syncthreads_or(!ok)) {
@@ -586,8 +586,6 @@ __global__ void __launch_bounds__(k64TX* k64TY) k_smooth_tma64(double* __restric
         const FxOp ym0 = get(fk, c0 - k64BoxX), ym1 = get(fk, c0 - k64BoxX + 1);
         const FxOp yp0 = get(fk, c0 + k64BoxX), yp1 = get(fk, c0 + k64BoxX + 1);
         const FxOp zm0 = get(fm, c0), zm1 = get(fm, c0 + 1), zp0 = get(fp, c0), zp1 = get(fp, c0 + 1);
-        const double2 gv = *reinterpret_cast<const double2*>(
-            raw + ((seq + i + 1) % k64Slots) * k64SlotBytes + k64GOff + (ty * 2 * k64TX + 2 * tx) * 8);
         double invd[2];
         if (xy_wall || k == 0 || k == G.nz - 1) {
           int dbase = 0;
@@ -612,6 +610,7 @@ __global__ void __launch_bounds__(k64TX* k64TY) k_smooth_tma64(double* __restric
         *reinterpret_cast<double2*>(xrow) = make_double2(o0, o1);
       }
       xrow += plane_stride;
+      grow += plane_stride;
     }
     seq += np;
   }
@@ -779,7 +778,6 @@ cudaError_t prepare_tma_sweep64(TmaSweep& t, double* x, const double* g, const G
     if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || reinterpret_cast<uintptr_t>(gbase) % 16 != 0)
       return cudaSuccess;
     if ((e = colour_map64(encode, &t.other[c], base, G, k64BoxX, k64BoxY)) != cudaSuccess) return e;
-    if ((e = colour_map64(encode, &t.rhs[c], gbase, G, 2 * k64TX, k64TY)) != cudaSuccess) return e;
   }
   if ((e = cudaFuncSetAttribute(k_smooth_tma64, cudaFuncAttributeMaxDynamicSharedMemorySize, k64SmemBytes)) !=
       cudaSuccess)
@@ -801,19 +799,19 @@ cudaError_t prepare_tma_sweep64(TmaSweep& t, double* x, const double* g, const G
   return cudaSuccess;
 }
 
-cudaError_t launch_smooth_tma64(double* x, const Geom& G, const InvDiag<double>& inv, int colour, const TmaSweep& t,
-                                int* err, cudaStream_t s) {
+cudaError_t launch_smooth_tma64(double* x, const double* g, const Geom& G, const InvDiag<double>& inv, int colour,
+                                const TmaSweep& t, int* err, cudaStream_t s) {
   if (!t.ok) return cudaErrorInvalidValue;
-  k_smooth_tma64<<<t.grid, dim3(k64TX, k64TY, 1), k64SmemBytes, s>>>(
-      x, G, inv, colour, t.kz, t.nwork, t.other[colour], t.rhs[colour], err, kWaitCycles, -1);
+  k_smooth_tma64<<<t.grid, dim3(k64TX, k64TY, 1), k64SmemBytes, s>>>(x, g, G, inv, colour, t.kz, t.nwork,
+                                                                    t.other[colour], err, kWaitCycles, -1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_smooth_tma64_withheld(double* x, const Geom& G, const InvDiag<double>& inv, const TmaSweep& t,
-                                         int* err, long long budget_cycles, cudaStream_t s) {
+cudaError_t launch_smooth_tma64_withheld(double* x, const double* g, const Geom& G, const InvDiag<double>& inv,
+                                         const TmaSweep& t, int* err, long long budget_cycles, cudaStream_t s) {
   if (!t.ok) return cudaErrorInvalidValue;
-  k_smooth_tma64<<<t.grid, dim3(k64TX, k64TY, 1), k64SmemBytes, s>>>(x, G, inv, 0, t.kz, t.nwork, t.other[0],
-                                                                    t.rhs[0], err, budget_cycles, 2);
+  k_smooth_tma64<<<t.grid, dim3(k64TX, k64TY, 1), k64SmemBytes, s>>>(x, g, G, inv, 0, t.kz, t.nwork, t.other[0],
+                                                                    err, budget_cycles, 2);
   return cudaGetLastError();
 }
 
