@@ -464,10 +464,10 @@ FP64_OPS_PEAK = 0.625  # Tops/s
 # same workload (profiles/); None where no capture of the current kernel exists.
 MEASURED_TRAFFIC = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one finest-level FP32 half-sweep of the
-    # 512^3 mixed step (TMA kernel as of commit db4ad4e): 545.2 MB read + 234.7 MB written, mean
-    # of the 12 captured launches; the algorithmic figure is 805.3 MB (the rest of the writes are
-    # still in L2 when the launch ends)
-    ("spheres512", "k_smooth_tma"): 779_880_000,
+    # 512^3 mixed step (one-pass capture of that kernel alone, TMA kernel as of commit d5485bd):
+    # 545.2 MB read + 234.7 MB written, mean of two launches; the algorithmic figure is 805.3 MB
+    # (the rest of the writes are still in L2 when the launch ends)
+    ("spheres512", "k_smooth_tma"): 779_890_000,
 }
 
 
