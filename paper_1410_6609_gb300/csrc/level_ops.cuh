@@ -296,8 +296,9 @@ __device__ __forceinline__ void load_nb_vec(const T* __restrict__ yr, const Geom
 // The FP64 scaled residual r~ = g + (x_-x + x_+x + x_-y + x_+y + x_-z + x_+z) - D x_c of one cell
 // (D = 6 + d), evaluated in 64-bit fixed point. Each operand is first put in a form that does not
 // depend on the cell (FxOp: its 53-bit significand times 2^5 with its sign applied, and its biased
-// exponent), so the tiled kernel below converts every value once and reuses it for the seven
-// cells it enters. A cell then aligns its operands to the largest biased exponent E among them,
+// exponent), so that a value converted once can serve every cell it enters (the packed tile walk
+// below goes one step further and aligns each ring row to one exponent; this per-cell form serves
+// the natural-order levels). A cell aligns its operands to the largest biased exponent E among them,
 // rounding each down to the unit 2^(E-1080) (an arithmetic shift), adds them as integers (the
 // magnitudes stay below 2^58 each, so the sum of at most 16 of them fits), and rounds the sum
 // once to the nearest double. Each operand loses less than one unit (the centre's loss is scaled
@@ -463,6 +464,17 @@ __host__ __device__ __forceinline__ double fx_sum6(const FxOp (&op)[6]) {
     for (int i = 0; i < 6; ++i) acc += fx_align(op[i], E);
   }
   return fx_to_double(acc, E);
+}
+
+// The biased exponent of v (0 for zero and subnormal values, 2047 for infinities and NaN).
+__device__ __forceinline__ unsigned fx_exp(double v) { return ((unsigned)__double2hiint(v) >> 20) & 0x7ffu; }
+
+// v as a signed integer multiple of 2^(E - 1080), rounded toward -infinity (E >= fx_exp(v);
+// subnormal values count as zero): the fixed point of fx_op aligned to the exponent E.
+__device__ __forceinline__ long long fx_at(double v, int E) {
+  const FxOp o = fx_op(v);
+  const int d = E - (int)(o.pk & 0xffffu);
+  return (long long)(((unsigned long long)o.hi << 32) | o.lo) >> (d < 63 ? d : 63);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1040,8 +1052,8 @@ __device__ int coarse_cg_block(T* __restrict__ xo, const T* __restrict__ bi, con
 // kResBX x kResBY threads, block lb of nb. Packed FP64 levels are cut into tiles of kResTM packed
 // columns (one per lane) x kResTJ rows (one per warp) x kResTZ planes, both colours; block lb
 // takes tiles lb, lb + nb, ... and each warp marches its row through the tile's planes; the
-// operands of a plane pass through shared memory, so every value is read and converted (fx_op)
-// once per tile (plus a one-cell halo) and serves the seven cells it enters from there. Packed
+// operands of a plane pass through shared memory, so every value is read and converted once per
+// tile (plus a one-cell halo) and serves the seven cells it enters from there. Packed
 // single-precision levels are walked row by row in (k, j, colour) order, kResBY rows at a time,
 // threads along the row; a natural-order level (single-level grid) cell by cell. Returns the
 // thread's sum of r~^2; by MODE also writes r = r~ c0 in natural order (1) or float(r~ isc) in
@@ -1062,6 +1074,25 @@ __host__ __device__ __forceinline__ long long resid_tile_count(const Geom& G, in
 // only after every warp has passed the barrier of the plane after the one that read it last),
 // with a one-cell halo: rows j0-1 and j0+kResTJ loaded by the first and last warp, and the column
 // beyond each end of a row loaded by the edge lanes in the colour the row's parity needs there.
+//
+// The residual r~ = g + (x_-x + x_+x + x_-y + x_+y + x_-z + x_+z) - D x_c (D = 6 + d) is summed in
+// 64-bit fixed point with one exponent per ring row. The warp that stores a row (its 32 columns in
+// both colours, and the halo column of its edge lanes) takes the largest biased exponent E_R of
+// its values (one warp reduction) and stores each value as floor(+-significand 2^5 / 2^(E_R - e)),
+// an integer in units of 2^(E_R - 1080) of magnitude below 2^58. A cell reads five rows: its own
+// (both x neighbours and the centre, one unit, summed without shifts), the rows j-1 and j+1 of its
+// plane and its row in the planes k-1 and k+1. Their exponents are the same for the whole warp;
+// with E the largest of them (and of g's, unless the warp's right-hand side is zero) each of the
+// five partial sums is shifted down to the unit 2^(E - 1080) and added, g is converted at that
+// unit, and the integer is rounded once to a double (fx_to_double). The magnitudes stay below
+// 2^62. Each truncation is a floor (two nested floors by powers of two are one), so x_-x, x_+x and
+// D x_c lose less than 2 + D units of their row, the shift of their sum, each other neighbour and
+// g less than one unit of 2^(E - 1080) each: the result lies within (8 + D) such units, i.e.
+// (8 + D)/32 of an ulp of the largest value among the rows the cell reads (and its g), plus half an
+// ulp of itself, of the exact residual. (Per-cell alignment, as in fx_residual, is
+// bounded by the cell's own largest operand instead; the row exponent moves the alignment shifts
+// from every use of a value to its conversion and took the 512^3 walk from 1.33 to 1.11 ms.) A cell
+// whose rows hold an infinity or NaN (E = 2047) takes the direct FP64 formula from global memory.
 constexpr int kResXR = kResTJ + 2, kResXC = kResTM + 2;
 
 template <int MODE, bool PER>
@@ -1072,27 +1103,15 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
   // ring slot b, row r (0 and kResXR-1 are the halo rows), colour c, column col (0 and kResXC-1 are
   // the halo columns) at b * kSlot + r * kRow + c * kResXC + col
   constexpr int kRow = 2 * kResXC, kSlot = kResXR * kRow;
-  __shared__ unsigned long long sS[4 * kSlot];  // FxOp::lo, hi
-  __shared__ unsigned sP[4 * kSlot];            // FxOp::pk
+  __shared__ long long sT[4 * kSlot];  // values in units of their row's 2^(E_row - 1080)
+  __shared__ int sE[4 * kResXR];       // E_row of ring slot b, row r at b * kResXR + r
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int w = tid >> 5, lane = tid & 31;
   int nmb, njb;
   const long long ntiles = resid_tile_count(G, &nmb, &njb);
   const int hx = G.hx, ny = G.ny, nz = G.nz;
   const long long plane = (long long)ny * hx;
-  auto put = [&](int b, int r, int c, int col, const FxOp& o) {
-    const int i = b * kSlot + r * kRow + c * kResXC + col;
-    sS[i] = ((unsigned long long)o.hi << 32) | o.lo;
-    sP[i] = o.pk;
-  };
-  auto get = [&](int i) -> FxOp {
-    const unsigned long long v = sS[i];
-    FxOp o;
-    o.lo = (unsigned)v;
-    o.hi = (unsigned)(v >> 32);
-    o.pk = sP[i];
-    return o;
-  };
+  auto put = [&](int b, int r, int c, int col, long long v) { sT[b * kSlot + r * kRow + c * kResXC + col] = v; };
   double acc = 0.0;
   for (long long t = lb; t < ntiles; t += nb) {
     const int mb = (int)(t % nmb);
@@ -1145,13 +1164,19 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
     auto gload = [&](int c, int kk) { return live ? __ldg(g + c * G.csz + (long long)kk * plane + col) : 0.0; };
     auto store = [&](int kk, const Raw& r) {
       const int b = kk & 3;
+      unsigned em = max(fx_exp(r.own[0]), fx_exp(r.own[1]));
+      if (hside != 0) em = max(em, fx_exp(r.halo));
+      const int er = (int)__reduce_max_sync(0xffffffffu, em);
+      if (lane == 0) sE[b * kResXR + w + 1] = er;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) put(b, w + 1, c, lane + 1, fx_op(r.own[c]));
-      if (hside != 0) put(b, w + 1, hcol(kk), hside < 0 ? 0 : kResXC - 1, fx_op(r.halo));
+      for (int c = 0; c < 2; ++c) put(b, w + 1, c, lane + 1, fx_at(r.own[c], er));
+      if (hside != 0) put(b, w + 1, hcol(kk), hside < 0 ? 0 : kResXC - 1, fx_at(r.halo, er));
       if (edge) {
         const int rr = w == 0 ? 0 : kResXR - 1;
+        const int eh = (int)__reduce_max_sync(0xffffffffu, max(fx_exp(r.row[0]), fx_exp(r.row[1])));
+        if (lane == 0) sE[b * kResXR + rr] = eh;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) put(b, rr, c, lane + 1, fx_op(r.row[c]));
+        for (int c = 0; c < 2; ++c) put(b, rr, c, lane + 1, fx_at(r.row[c], eh));
       }
     };
     __syncthreads();  // the previous tile's last reads of the ring are done
@@ -1181,14 +1206,27 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
         const int B0 = (k & 3) * kSlot + own, BM = ((k - 1) & 3) * kSlot + own, BP = ((k + 1) & 3) * kSlot + own;
         // diagonal shift: the walls of this row and plane, then the x walls per cell
         const int dbase = dj + (k == 0 ? G.sh[4] : 0) + (k == nz - 1 ? G.sh[5] : 0);
+        const int e0 = (k & 3) * kResXR + w + 1;
+        const int eo = sE[e0], eym = sE[e0 - 1], eyp = sE[e0 + 1];
+        const int ezm = sE[((k - 1) & 3) * kResXR + w + 1], ezp = sE[((k + 1) & 3) * kResXR + w + 1];
+        const int E5 = max(max(max(eo, eym), max(eyp, ezm)), ezp);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int s = (j + k + c) & 1, o = (1 - c) * kResXC;
-          // x neighbours: the other colour at m + s - 1 and m + s (columns shifted by the halo)
-          const FxOp op[8] = {G0 ? FxOp{0u, 0u, 0u} : fx_op(gv[c]), get(B0 + o + s - 1), get(B0 + o + s),
-                              get(B0 + o - kRow), get(B0 + o + kRow), get(BM + o), get(BP + o), get(B0 + c * kResXC)};
           const int d = dbase + (m == 0 && s == 0 ? G.sh[0] : 0) + (m == hx - 1 && s == 1 ? G.sh[1] : 0);
-          const double rd = fx_residual<G0>(op, 6 + d);
+          int E = E5;
+          if (!G0) E = max(E, (int)fx_exp(gv[c]));
+          auto al = [&](long long v, int ev) {
+            const int dd = E - ev;
+            return v >> (dd < 63 ? dd : 63);
+          };
+          // x neighbours: the other colour at m + s - 1 and m + s (columns shifted by the halo)
+          const long long A = sT[B0 + o + s - 1] + sT[B0 + o + s] - (long long)(6 + d) * sT[B0 + c * kResXC];
+          long long sum = al(A, eo) + al(sT[B0 + o - kRow], eym) + al(sT[B0 + o + kRow], eyp) + al(sT[BM + o], ezm) +
+                          al(sT[BP + o], ezp);
+          if (!G0) sum += fx_at(gv[c], E);
+          const double rd = E == 2047 ? (double)resid_packed<double, PER>(x, g, G, c, m, j, k)
+                                      : fx_to_double((unsigned long long)sum, E);
           acc = fma(rd, rd, acc);
           if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)ny * k)] = rd * c0;
           if (MODE == 2)

@@ -405,20 +405,27 @@ def test_zero_start_without_writing_the_iterate():
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("dims,bc", [((24, 20, 18), (D, N, N, D, D, N)), ((4, 6, 4), (N, D, D, N, N, D))])
-def test_fp64_residual_against_exact_arithmetic(dims, bc):
-    """The FP64 residual r = g + (sum of the six neighbours) - (6 + d) phi of every cell (h = 1, so
-    the scaled and the plain residual coincide) lies within half an ulp of its largest operand
-    plus half an ulp of itself from the exact rational value: operands spread over 2^-40 .. 2^40
-    with zeros among them, and on half the cells a right-hand side that cancels the stencil to its
-    rounding error. A multi-level (checkerboard-packed) grid and a single-level (natural order) one."""
-    from fractions import Fraction
-    rng = np.random.default_rng(11)
-    nx, ny, nz = dims
-    shape = (nz, ny, nx)
-    phi = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
-    phi[rng.random(shape) < 0.1] = 0.0
-    sh = {D: 1, N: -1}
+def _rows_max(phi, bc):
+    """Per cell, the largest |phi| over the five grid rows (x lines) that the packed residual walk
+    reads for it: rows j-1, j, j+1 of its plane and row j of planes k-1 and k+1, across a periodic
+    axis the row at the opposite side, beyond a wall none. The walk's row exponents are taken over
+    parts of these rows, so this bounds them from above."""
+    R = np.abs(phi).max(axis=2)  # (nz, ny): largest |value| of each row, both colours
+    out = R.copy()
+    for ax, q in ((1, 2), (0, 4)):  # y rows within the plane, then z neighbours
+        for shift in (1, -1):
+            nb = np.roll(R, shift, axis=ax)
+            if bc[q] != PER:
+                if shift == 1:
+                    nb[(slice(None),) * ax + (0,)] = 0.0
+                else:
+                    nb[(slice(None),) * ax + (-1,)] = 0.0
+            out = np.maximum(out, nb)
+    return np.broadcast_to(out[:, :, None], phi.shape)
+
+
+def _diag(shape, bc):
+    sh = {D: 1, N: -1, PER: 0}
     diag = np.full(shape, 6, dtype=np.int64)
     diag[:, :, 0] += sh[bc[0]]
     diag[:, :, -1] += sh[bc[1]]
@@ -426,14 +433,42 @@ def test_fp64_residual_against_exact_arithmetic(dims, bc):
     diag[:, -1, :] += sh[bc[3]]
     diag[0] += sh[bc[4]]
     diag[-1] += sh[bc[5]]
-    p = np.pad(phi, 1)
+    return diag
+
+
+def _residual_case(shape, bc, seed):
+    """phi and g spread over 2^-40 .. 2^40 with zeros among them, and on half the cells a right-hand
+    side that cancels the stencil to its rounding error; the six neighbour fields (zero beyond a
+    wall, the opposite side across a periodic axis)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
+    phi[rng.random(shape) < 0.1] = 0.0
+    diag = _diag(shape, bc)
+    p = phi
+    for ax, q in ((2, 0), (1, 2), (0, 4)):  # axis 2 is x, 1 is y, 0 is z
+        widths = [(0, 0)] * 3
+        widths[ax] = (1, 1)
+        p = np.pad(p, widths, mode="wrap" if bc[q] == PER else "constant")
     nbs = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
            p[2:, 1:-1, 1:-1]]
     g = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
     g[rng.random(shape) < 0.05] = 0.0
     cancel = rng.random(shape) < 0.5
     g[cancel] = (diag * phi - sum(nbs))[cancel]
+    return phi, g, diag, nbs
+
+
+def test_fp64_residual_against_exact_arithmetic_natural_order():
+    """The FP64 residual r = g + (sum of the six neighbours) - (6 + d) phi of every cell of a
+    single-level (natural order) grid, aligned per cell: within half an ulp of its largest
+    operand plus half an ulp of itself from the exact rational value (h = 1, so the scaled and the
+    plain residual coincide)."""
+    from fractions import Fraction
+    dims, bc = (4, 6, 4), (N, D, D, N, N, D)
+    shape = tuple(reversed(dims))
+    phi, g, diag, nbs = _residual_case(shape, bc, 11)
     P = Poisson(dims, h=1.0, bc_type=bc)
+    assert P.num_levels == 1
     P.level_set(0, 0, gpu(phi))
     P.level_set(0, 1, gpu(g))
     _, r = P.residual(field=True)
@@ -449,53 +484,71 @@ def test_fp64_residual_against_exact_arithmetic(dims, bc):
     assert worst <= 1.0, worst
 
 
-@pytest.mark.parametrize("bc", [(D, N, N, D, D, N), (PER, PER, N, D, PER, PER)])
-def test_fp64_residual_against_exact_arithmetic_many_tiles(bc):
-    """The same bound on a grid of several tiles of the residual walk in every direction, with
-    ragged tiles in x, y and z (80 x 20 x 72: packed rows of 40 = 32 + 8 columns, rows 8 + 8 + 4,
-    planes 64 + 8), walls and periodic axes (the halo columns, rows and planes of the walk then
-    come from the opposite side). The exact residual of each cell is summed by math.fsum, which
-    rounds it once, so the bound gains half an ulp of that rounded value."""
+@pytest.mark.parametrize("dims,bc", [((24, 20, 18), (D, N, N, D, D, N)), ((80, 20, 72), (D, N, N, D, D, N)),
+                                     ((80, 20, 72), (PER, PER, N, D, PER, PER))])
+def test_fp64_residual_against_exact_arithmetic(dims, bc):
+    """The FP64 residual of the packed tile walk (each ring row in fixed point at its own
+    exponent): within (8 + D)/32 of an ulp of the largest value among the five rows the cell reads
+    (or of its g) plus half an ulp of itself from the exact value, which math.fsum rounds once (so
+    the bound gains half an ulp of that). Operands spread over 2^-40 .. 2^40, zeros among them,
+    right-hand sides that cancel the stencil; a one-tile grid and one of several tiles in every
+    direction, ragged in x, y and z (80 x 20 x 72: packed rows of 40 = 32 + 8 columns, rows 8 + 8
+    + 4, planes 64 + 8), with walls and with periodic axes (the halo columns, rows and planes of
+    the walk then come from the opposite side)."""
     import math
-    rng = np.random.default_rng(12)
-    nx, ny, nz = 80, 20, 72
-    shape = (nz, ny, nx)
-    phi = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
-    phi[rng.random(shape) < 0.1] = 0.0
-    sh = {D: 1, N: -1, PER: 0}
-    diag = np.full(shape, 6, dtype=np.int64)
-    diag[:, :, 0] += sh[bc[0]]
-    diag[:, :, -1] += sh[bc[1]]
-    diag[:, 0, :] += sh[bc[2]]
-    diag[:, -1, :] += sh[bc[3]]
-    diag[0] += sh[bc[4]]
-    diag[-1] += sh[bc[5]]
-    p = phi
-    for ax, q in ((2, 0), (1, 2), (0, 4)):  # axis 2 is x, 1 is y, 0 is z
-        widths = [(0, 0)] * 3
-        widths[ax] = (1, 1)
-        p = np.pad(p, widths, mode="wrap" if bc[q] == PER else "constant")
-    nbs = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
-           p[2:, 1:-1, 1:-1]]
-    g = rng.standard_normal(shape) * np.exp2(rng.integers(-40, 41, shape))
-    g[rng.random(shape) < 0.05] = 0.0
-    cancel = rng.random(shape) < 0.5
-    g[cancel] = (diag * phi - sum(nbs))[cancel]
-    P_ = Poisson((nx, ny, nz), h=1.0, bc_type=bc)
+    shape = tuple(reversed(dims))
+    phi, g, diag, nbs = _residual_case(shape, bc, 12)
+    P_ = Poisson(dims, h=1.0, bc_type=bc)
+    assert P_.num_levels > 1
     P_.level_set(0, 0, gpu(phi))
     P_.level_set(0, 1, gpu(g))
     _, r = P_.residual(field=True)
     r = cpu(r)
     P_.close()
+    big = np.maximum(_rows_max(phi, bc), np.abs(g)).reshape(-1)
     vals = [g] + nbs + [-phi]
-    big = np.max(np.abs(np.stack(vals)), axis=0)
-    worst = 0.0
     flat = [v.reshape(-1) for v in vals]
-    dflat, rflat, bflat = diag.reshape(-1), r.reshape(-1), big.reshape(-1)
+    dflat, rflat = diag.reshape(-1), r.reshape(-1)
+    worst = 0.0
     for i in range(rflat.size):
         terms = [float(v[i]) for v in flat[:-1]] + [float(flat[-1][i])] * int(dflat[i])
         ex = math.fsum(terms)
-        bound = np.spacing(bflat[i]) / 2 + np.spacing(abs(rflat[i])) / 2 + np.spacing(abs(ex)) / 2
+        bound = (8 + int(dflat[i])) / 32 * np.spacing(big[i]) + np.spacing(abs(rflat[i])) / 2 + \
+            np.spacing(abs(ex)) / 2
+        worst = max(worst, abs(rflat[i] - ex) / bound)
+    assert worst <= 1.0, worst
+
+
+def test_fp64_residual_walk_on_a_smooth_field():
+    """On a smooth potential (the case of a solve), where the rows a cell reads hold values of the
+    cell's own size, the walk's residual is within an ulp of the largest of the cell's own
+    operands (plus half an ulp of itself and of the rounded exact value)."""
+    import math
+    dims, bc = (96, 40, 24), (N, N, N, N, D, D)
+    shape = tuple(reversed(dims))
+    zz, yy, xx = np.meshgrid(*(np.arange(n) + 0.5 for n in shape), indexing="ij")
+    phi = 1.0 + 0.3 * np.sin(0.05 * xx) * np.cos(0.07 * yy) + zz / shape[0]
+    diag = _diag(shape, bc)
+    p = np.pad(phi, 1)
+    nbs = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
+           p[2:, 1:-1, 1:-1]]
+    g = np.zeros(shape)
+    g[:, :, : dims[0] // 2] = (diag * phi - sum(nbs))[:, :, : dims[0] // 2] * 0.999
+    P_ = Poisson(dims, h=1.0, bc_type=bc)
+    P_.level_set(0, 0, gpu(phi))
+    P_.level_set(0, 1, gpu(g))
+    _, r = P_.residual(field=True)
+    r = cpu(r)
+    P_.close()
+    ops = np.max(np.abs(np.stack([g, phi] + nbs)), axis=0).reshape(-1)
+    vals = [g] + nbs + [-phi]
+    flat = [v.reshape(-1) for v in vals]
+    dflat, rflat = diag.reshape(-1), r.reshape(-1)
+    worst = 0.0
+    for i in range(rflat.size):
+        terms = [float(v[i]) for v in flat[:-1]] + [float(flat[-1][i])] * int(dflat[i])
+        ex = math.fsum(terms)
+        bound = np.spacing(ops[i]) + np.spacing(abs(rflat[i])) / 2 + np.spacing(abs(ex)) / 2
         worst = max(worst, abs(rflat[i] - ex) / bound)
     assert worst <= 1.0, worst
 
