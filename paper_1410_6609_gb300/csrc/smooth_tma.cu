@@ -27,6 +27,9 @@ namespace {
 using ops::FxOp;
 using ops::fx_op;
 using ops::fx_sum6;
+using ops::fx_exp;
+using ops::fx_at;
+using ops::fx_to_double;
 using ops::inv_of;
 
 constexpr int kHaloX = 4;  // floats on each side of the tile row (16-byte aligned box start)
@@ -462,21 +465,29 @@ __global__ void __launch_bounds__(C::kTX* C::kTY) k_smooth_tma(float* __restrict
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP64 half-sweep with TMA z-slab staging (FP64 mode, levels without a periodic axis). The
-// arithmetic is that of ops::smooth_vec<double>: the six-neighbour sum in exact fixed point
-// (fx_sum6), then (g + S) / (6 + d) by the stored reciprocal, so the results are bit-identical.
-// The direct-load kernel converts each neighbour every time a cell reads it (about 5.5
-// conversions per cell); here every value of a landed other-colour plane is converted once into a
-// ring of four converted planes (FxOp, 12 bytes per value) and the cells read their operands from
-// there. A CTA of 32 x 8 threads owns a tile of 64 x 8 cells of the colour (two per thread, a
-// 16-byte vector) and marches it through a slab of planes; the other colour's planes arrive as
-// 68 x 10-double boxes (tile plus a one-row and a 2-double x halo, 16-byte aligned start) in
-// four raw slots; the right-hand side, read once, comes by a plain vector load issued before the
-// plane's wait, which keeps the shared memory at 54.7 KB and four CTAs on an SM (with it in the
-// ring: 71 KB, three CTAs, 6 % slower at 512^3). Load i (other-colour plane k0-1+i) goes to raw
-// slot and converted plane (seq + i) % 4. At plane k (load i+1 just landed and converted) one
-// barrier publishes the conversion and retires plane k-1, whose raw slot (load i) is refilled
-// with load i+4; the converted plane overwritten by load i+1 was last read at plane k-2.
+// FP64 half-sweep with TMA z-slab staging (FP64 mode, levels without a periodic axis):
+// phi = (g + S) / (6 + d) with the six-neighbour sum S formed exactly in 64-bit fixed point. A CTA
+// of 32 x 8 threads owns a tile of 64 x 8 cells of the colour (two per thread, a 16-byte vector)
+// and marches it through a slab of planes; the other colour's planes arrive as 68 x 10-double
+// boxes (tile plus a one-row and a 2-double x halo, 16-byte aligned start) in four raw slots.
+// Every landed plane gets one exponent, the largest biased exponent E_p among its box values
+// (each warp reduces its share, the CTA takes the maximum of the eight), and every value is
+// converted once, as floor(+-significand 2^5 / 2^(E_p - e)), an integer in units of 2^(E_p - 1080)
+// of magnitude below 2^58, into a ring of four converted planes. A cell's four in-plane neighbours
+// share one unit and are added without shifts; with E the largest of the three planes' exponents
+// the in-plane sum and the two z neighbours are shifted to the unit 2^(E - 1080) (shifts the same
+// for the whole CTA), added and rounded once to a double. Each floor loses less than one unit, so
+// S lies within 7 units of 2^(E - 1080), 7/32 of an ulp of the largest value in the three boxes,
+// plus half an ulp of itself, of the exact sum; then + g and x 1/(6 + d) as in the direct-load
+// sweep, whose per-cell alignment (fx_sum6) is bounded by the cell's own largest neighbour instead.
+// A tile plane next to an infinity or NaN takes the direct FP64 sum from global memory.
+// The right-hand side, read once, comes by a plain vector load issued before the plane's wait.
+// Load i (other-colour plane k0-1+i) goes to raw slot and converted plane (seq + i) % 4. The
+// exponent of a plane must be known before its values are converted, so the pipeline runs one
+// plane deeper than the copies: at plane k (load index i) the threads take the exponents of load
+// i+2, convert load i+1 with the exponent published at the previous barrier, and one barrier
+// publishes both; then the raw slot of load i+1 takes load i+5 and the cells read loads i-1, i,
+// i+1. A converted plane is rewritten two barriers after its last read.
 constexpr int k64TX = 32, k64TY = 8;
 constexpr int k64Halo = 2;                              // doubles on each side of a tile row
 constexpr int k64BoxX = 2 * k64TX + 2 * k64Halo;        // 68
@@ -486,9 +497,12 @@ constexpr int k64BoxBytes = k64BoxN * 8;                // 5440
 constexpr int k64SlotBytes = round128(k64BoxBytes);    // 5504
 constexpr int k64Slots = 4;
 constexpr int k64Fx = 4;  // converted planes
-constexpr int k64SmemBytes = k64Slots * k64SlotBytes + k64Fx * k64BoxN * (8 + 4) + 8 * k64Slots;
+constexpr int k64Warps = k64TX * k64TY / 32;
+constexpr int k64SmemBytes = k64Slots * k64SlotBytes + k64Fx * k64BoxN * 8 + k64Slots * k64Warps * 4 + 8 * k64Slots;
 static_assert(k64SlotBytes % 128 == 0, "TMA destinations need 128-byte alignment");
-static_assert((k64Slots * k64SlotBytes) % 8 == 0 && (k64Fx * k64BoxN * 8) % 8 == 0, "ring alignment");
+static_assert((k64Slots * k64SlotBytes) % 8 == 0 && (k64Fx * k64BoxN * 8) % 8 == 0 && (k64Slots * k64Warps * 4) % 8 == 0,
+              "ring alignment");
+static_assert(k64BoxN <= 3 * k64TX * k64TY, "three box values per thread at most");
 
 __global__ void __launch_bounds__(k64TX* k64TY, 4)
     k_smooth_tma64(double* __restrict__ x, const double* __restrict__ g, Geom G, InvDiag<double> inv, int colour, int kz,
@@ -496,10 +510,10 @@ __global__ void __launch_bounds__(k64TX* k64TY, 4)
                    int withhold) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* raw = smem;
-  unsigned long long* fS = reinterpret_cast<unsigned long long*>(smem + k64Slots * k64SlotBytes);
-  unsigned* fP = reinterpret_cast<unsigned*>(fS + k64Fx * k64BoxN);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(fP + k64Fx * k64BoxN);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * k64TX + tx;
+  long long* fT = reinterpret_cast<long long*>(smem + k64Slots * k64SlotBytes);  // converted planes
+  int* pexp = reinterpret_cast<int*>(fT + k64Fx * k64BoxN);  // per raw slot, each warp's largest exponent
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(pexp + k64Slots * k64Warps);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * k64TX + tx, wid = tid >> 5;
   const bool leader = tid == 0;
   if (leader) {
     for (int q = 0; q < k64Slots; ++q) mbar_init(smem_addr(bars + q), 1);
@@ -508,6 +522,7 @@ __global__ void __launch_bounds__(k64TX* k64TY, 4)
   __syncthreads();
   const unsigned raw0 = smem_addr(raw), bar0 = smem_addr(bars);
   double* const xo = x + (long long)colour * G.csz;
+  const double* const xoth = x + (long long)(1 - colour) * G.csz;
   int seq = 0, issued = 0;
   bool failed = false;
   for (long long w = blockIdx.x; w < nwork && !failed; w += gridDim.x) {
@@ -529,63 +544,80 @@ __global__ void __launch_bounds__(k64TX* k64TY, 4)
       const int n = seq + i;
       return mbar_wait(bar0 + 8u * (unsigned)(n % k64Slots), (unsigned)((n / k64Slots) & 1), budget);
     };
-    // load i's other-colour plane into converted plane (seq + i) % k64Fx
-    auto convert = [&](int i) {
-      const int n = seq + i;
-      const double* src = reinterpret_cast<const double*>(raw + (n % k64Slots) * k64SlotBytes);
-      unsigned long long* dS = fS + (n % k64Fx) * k64BoxN;
-      unsigned* dP = fP + (n % k64Fx) * k64BoxN;
-      for (int f = tid; f < k64BoxN; f += k64TX * k64TY) {
-        const FxOp o = fx_op(src[f]);
-        dS[f] = ((unsigned long long)o.hi << 32) | o.lo;
-        dP[f] = o.pk;
+    auto rawp = [&](int i) { return reinterpret_cast<const double*>(raw + ((seq + i) % k64Slots) * k64SlotBytes); };
+    // the largest exponent among this warp's share of load i's box, for the plane's exponent
+    auto scan = [&](int i) {
+      const double* src = rawp(i);
+      unsigned e = 0u;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int f = tid + u * k64TX * k64TY;
+        if (f < k64BoxN) e = max(e, fx_exp(src[f]));
       }
+      e = __reduce_max_sync(0xffffffffu, e);
+      if ((tid & 31) == 0) pexp[((seq + i) % k64Slots) * k64Warps + wid] = (int)e;
     };
-    auto get = [&](int plane_slot, int idx) -> FxOp {
-      const unsigned long long v = fS[plane_slot * k64BoxN + idx];
-      FxOp o;
-      o.lo = (unsigned)v;
-      o.hi = (unsigned)(v >> 32);
-      o.pk = fP[plane_slot * k64BoxN + idx];
-      return o;
+    auto plane_exp = [&](int i) {
+      const int* pe = pexp + ((seq + i) % k64Slots) * k64Warps;
+      int e = pe[0];
+#pragma unroll
+      for (int q = 1; q < k64Warps; ++q) e = max(e, pe[q]);
+      return e;
+    };
+    // load i's box into converted plane (seq + i) % k64Fx at the plane's exponent E
+    auto convert = [&](int i, int E) {
+      const double* src = rawp(i);
+      long long* dT = fT + ((seq + i) % k64Fx) * k64BoxN;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int f = tid + u * k64TX * k64TY;
+        if (f < k64BoxN) dT[f] = fx_at(src[f], E);
+      }
     };
     __syncthreads();  // every thread is done with the previous item's slots
     if (leader)
       for (int i = 0; i < np && i < k64Slots; ++i) issue(i);
-    bool ok = wait(0) && wait(1);
+    bool ok = wait(0) && wait(1) && wait(2);
+    if (ok) {
+      scan(0);
+      scan(1);
+      scan(2);
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    int Em = plane_exp(0), Ek = plane_exp(1);  // exponents of loads i-1 and i at plane k
+    convert(0, Em);
+    convert(1, Ek);
     const int m0 = x0 + 2 * tx, j = y0 + ty;
     const bool mine = m0 < G.hx && j < G.ny;
     const bool xy_wall = j == 0 || j == G.ny - 1 || m0 == 0 || m0 + 2 >= G.hx;
     const int c0 = (ty + 1) * k64BoxX + k64Halo + 2 * tx;  // box position of m0 in row j
-    if (ok) {
-      convert(0);
-      convert(1);
-    }
     double* xrow = xo + ((long long)k0 * G.ny + j) * G.hx + m0;
     const double* grow = g + (xrow - x);
     const long long plane_stride = (long long)G.ny * G.hx;
     for (int k = k0; k < k1; ++k) {
       const int i = k - k0 + 1;  // load index of plane k
-      // the cell pair's right-hand side, read while the plane's copy lands and is converted
+      // the cell pair's right-hand side, read while the copies land and are converted
       const double2 gv = mine ? __ldg(reinterpret_cast<const double2*>(grow)) : make_double2(0.0, 0.0);
-      ok = ok && wait(i + 1);
-      if (ok) convert(i + 1);
+      const int Ep = plane_exp(i + 1);  // published by the previous barrier
+      if (i + 2 < np) {
+        ok = ok && wait(i + 2);
+        if (ok) scan(i + 2);
+      }
+      convert(i + 1, Ep);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
-      if (leader) {  // raw slots whose planes are converted and right-hand sides used
-        if (i == 1 && k64Slots < np) issue(k64Slots);
-        if (i + k64Slots < np) issue(i + k64Slots);
+      if (leader) {  // raw slots whose planes are converted: loads 0..2 at the first plane, then i+1
+        if (i == 1)
+          for (int n = k64Slots; n < k64Slots + 2 && n < np; ++n) issue(n);
+        if (i + k64Slots + 1 < np) issue(i + k64Slots + 1);
       }
       if (mine) {
-        const int fm = (seq + i - 1) % k64Fx, fk = (seq + i) % k64Fx, fp = (seq + i + 1) % k64Fx;
         const int s = (j + k + colour) & 1;
-        // x-neighbours: other colour at m + s - 1 and m + s for cells m0 and m0 + 1
-        const FxOp xa = get(fk, c0 + s - 1), xb = get(fk, c0 + s), xc = get(fk, c0 + s + 1);
-        const FxOp ym0 = get(fk, c0 - k64BoxX), ym1 = get(fk, c0 - k64BoxX + 1);
-        const FxOp yp0 = get(fk, c0 + k64BoxX), yp1 = get(fk, c0 + k64BoxX + 1);
-        const FxOp zm0 = get(fm, c0), zm1 = get(fm, c0 + 1), zp0 = get(fp, c0), zp1 = get(fp, c0 + 1);
         double invd[2];
         if (xy_wall || k == 0 || k == G.nz - 1) {
           int dbase = 0;
@@ -603,12 +635,37 @@ __global__ void __launch_bounds__(k64TX* k64TY, 4)
         } else {
           invd[0] = invd[1] = inv.v[3];
         }
-        const FxOp op0[6] = {xa, xb, ym0, yp0, zm0, zp0};
-        const FxOp op1[6] = {xb, xc, ym1, yp1, zm1, zp1};
-        const double o0 = (gv.x + fx_sum6(op0)) * invd[0];
-        const double o1 = (gv.y + fx_sum6(op1)) * invd[1];
-        *reinterpret_cast<double2*>(xrow) = make_double2(o0, o1);
+        const int E = max(max(Em, Ek), Ep);
+        double S[2];
+        if (E != 2047) {
+          const long long* pm = fT + ((seq + i - 1) % k64Fx) * k64BoxN;
+          const long long* pk = fT + ((seq + i) % k64Fx) * k64BoxN;
+          const long long* pp = fT + ((seq + i + 1) % k64Fx) * k64BoxN;
+          const int dk = min(E - Ek, 63), dm = min(E - Em, 63), dp = min(E - Ep, 63);
+          // x-neighbours: other colour at m + s - 1 and m + s for cells m0 and m0 + 1
+          const long long xa = pk[c0 + s - 1], xb = pk[c0 + s], xc = pk[c0 + s + 1];
+          const long long in0 = xa + xb + pk[c0 - k64BoxX] + pk[c0 + k64BoxX];
+          const long long in1 = xb + xc + pk[c0 - k64BoxX + 1] + pk[c0 + k64BoxX + 1];
+          S[0] = fx_to_double((unsigned long long)((in0 >> dk) + (pm[c0] >> dm) + (pp[c0] >> dp)), E);
+          S[1] = fx_to_double((unsigned long long)((in1 >> dk) + (pm[c0 + 1] >> dm) + (pp[c0 + 1] >> dp)), E);
+        } else {  // an infinity or NaN in the three planes: the direct sum of the values
+          auto nb = [&](int mm, int jj, int kk) {
+            return (mm >= 0 && mm < G.hx && jj >= 0 && jj < G.ny && kk >= 0 && kk < G.nz)
+                       ? __ldg(xoth + ((long long)kk * G.ny + jj) * G.hx + mm)
+                       : 0.0;
+          };
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int mm = m0 + e;
+            S[e] = ((((nb(mm + s - 1, j, k) + nb(mm + s, j, k)) + nb(mm, j - 1, k)) + nb(mm, j + 1, k)) +
+                    nb(mm, j, k - 1)) +
+                   nb(mm, j, k + 1);
+          }
+        }
+        *reinterpret_cast<double2*>(xrow) = make_double2((gv.x + S[0]) * invd[0], (gv.y + S[1]) * invd[1]);
       }
+      Em = Ek;
+      Ek = Ep;
       xrow += plane_stride;
       grow += plane_stride;
     }

@@ -262,10 +262,11 @@ def test_fused_prolongation_sweep_against_oracle(dims, policy):
 
 
 # ------------------------------------------------------------------------------------------------
-# The FP64 half-sweep staged the same way (FP64 mode): the neighbour sum in exact fixed point from
-# planes converted once, against the direct-load FP64 sweep (same operands, same exact sum: the
-# same bits) and the oracle's FP64 half-sweep. Tiles of 64 x 8 cells of a colour, ragged in x
-# (hx 100, 68), in y (88, 40) and in the slabs.
+# The FP64 half-sweep staged the same way (FP64 mode): every landed plane converted once into 64-bit
+# fixed point at the plane's largest exponent, the six-neighbour sum formed exactly from there and
+# rounded once, then + g and x 1/(6 + d). Against the oracle's FP64 half-sweep, the direct-load FP64
+# sweep (which aligns per cell: the two agree to rounding, not bit for bit) and exact arithmetic.
+# Tiles of 64 x 8 cells of a colour, ragged in x (hx 100, 68), in y (88, 40) and in the slabs.
 
 def _fp64_pair(dims, **kw):
     from paper_1410_6609_gb300.solver import Poisson
@@ -285,7 +286,7 @@ def _fp64_pair(dims, **kw):
 
 
 @pytest.mark.parametrize("dims", [(200, 88, 72), (256, 64, 96), (136, 40, 32), (512, 24, 48)])
-def test_fp64_tma_half_sweeps_bit_identical_and_match_oracle(dims):
+def test_fp64_tma_half_sweeps_match_oracle(dims):
     a, b = _fp64_pair(dims, bc_type=BC_MIX, bc_value=(0.0, 1.0, -0.5, 0.25, 0.0, 2.0))
     assert a.level_sweep_kind(0) == "tma" and b.level_sweep_kind(0) == "vec"
     nx, ny, nz = dims
@@ -297,21 +298,77 @@ def test_fp64_tma_half_sweeps_bit_identical_and_match_oracle(dims):
             P.level_set(0, 0, torch.from_numpy(phi).cuda())
             P.level_set(0, 1, torch.from_numpy(f).cuda())
             P.op_smooth(0, colour)
-        xa = a.level_get(0, 0)
-        assert torch.equal(xa, b.level_get(0, 0)), colour
+        xa, xb = a.level_get(0, 0).cpu().numpy(), b.level_get(0, 0).cpu().numpy()
         ref = oracle.rbgs_half(phi, f, 1.0, BC_MIX, colour)
-        assert _maxrel(xa.cpu().numpy(), ref) < 1e-14
-    for colour in (0, 1, 1, 0, 1, 0):  # from the state left above
+        assert _maxrel(xa, ref) < 1e-14 and _maxrel(xa, xb) < 1e-14
+        kk, jj, ii = np.indices(phi.shape)
+        assert np.array_equal(xa[(ii + jj + kk) % 2 != colour], phi[(ii + jj + kk) % 2 != colour])
+    a.level_set(0, 0, torch.from_numpy(phi).cuda())
+    ref = phi
+    for colour in (0, 1, 1, 0, 1, 0):  # the same sequence on both sides
         a.op_smooth(0, colour)
-        b.op_smooth(0, colour)
-        assert torch.equal(a.level_get(0, 0), b.level_get(0, 0)), colour
+        ref = oracle.rbgs_half(ref, f, 1.0, BC_MIX, colour)
+    assert _maxrel(a.level_get(0, 0).cpu().numpy(), ref) < 1e-13
     a.close()
     b.close()
 
 
-def test_fp64_tma_default_policy_and_solve_bit_identical():
+def test_fp64_tma_half_sweep_against_exact_arithmetic():
+    """Values spread over 2^-30 .. 2^30 with zeros: each updated cell within the sum's bound of the
+    exact (g + S)/(6 + d): S within 7/32 of an ulp of the largest other-colour value in the boxes of
+    planes k-1..k+1 the kernel aligns to (bounded here by whole rows: the tile's 8 rows of the cell
+    and the row beyond each side) plus half an ulp of itself, then three roundings (+ g,
+    1/(6 + d), the product)."""
+    import math
+    dims = (136, 40, 32)
+    bc = BC_MIX
+    a, b = _fp64_pair(dims, bc_type=bc)
+    b.close()
+    nx, ny, nz = dims
+    rng = np.random.default_rng(21)
+    phi = rng.standard_normal((nz, ny, nx)) * np.exp2(rng.integers(-30, 31, (nz, ny, nx)))
+    phi[rng.random(phi.shape) < 0.1] = 0.0
+    f = rng.standard_normal((nz, ny, nx)) * np.exp2(rng.integers(-30, 31, (nz, ny, nx)))
+    sh = {D: 1, N: -1}
+    diag = np.full(phi.shape, 6, dtype=np.int64)
+    diag[:, :, 0] += sh[bc[0]]
+    diag[:, :, -1] += sh[bc[1]]
+    diag[:, 0, :] += sh[bc[2]]
+    diag[:, -1, :] += sh[bc[3]]
+    diag[0] += sh[bc[4]]
+    diag[-1] += sh[bc[5]]
+    p = np.pad(phi, 1)
+    nbs = [p[1:-1, 1:-1, :-2], p[1:-1, 1:-1, 2:], p[1:-1, :-2, 1:-1], p[1:-1, 2:, 1:-1], p[:-2, 1:-1, 1:-1],
+           p[2:, 1:-1, 1:-1]]
+    kk, jj, ii = np.indices(phi.shape)
+    for colour in (0, 1):
+        a.level_set(0, 0, torch.from_numpy(phi).cuda())
+        a.level_set(0, 1, torch.from_numpy(f).cuda())
+        a.op_smooth(0, colour)
+        out = a.level_get(0, 0).cpu().numpy()
+        # the largest |value| of the other colour over rows j-1..j+1 of planes k-1..k+1
+        oth = np.where((ii + jj + kk) % 2 != colour, np.abs(phi), 0.0)
+        R = oth.max(axis=2)  # (nz, ny) row maxima
+        big = np.zeros((nz, ny))
+        for z in range(nz):
+            for y in range(ny):
+                y0 = (y // 8) * 8
+                big[z, y] = R[max(z - 1, 0):z + 2, max(y0 - 1, 0):y0 + 9].max()
+        worst = 0.0
+        for idx in zip(*np.nonzero((ii + jj + kk) % 2 == colour)):
+            S = math.fsum(float(n[idx]) for n in nbs)
+            D_ = int(diag[idx])
+            exact = (f[idx] + S) / D_
+            sbound = 7 / 32 * np.spacing(big[idx[0], idx[1]]) + np.spacing(abs(S))
+            bound = sbound / D_ + 4 * np.spacing(abs(exact)) + np.spacing(abs(f[idx] + S)) / D_
+            worst = max(worst, abs(out[idx] - exact) / bound)
+        assert worst <= 1.0, (colour, worst)
+    a.close()
+
+
+def test_fp64_tma_default_policy_and_solve():
     """By default FP64 levels of 2^22 cells per colour and more take the staged sweep; a whole FP64
-    solve with it equals the direct-load one bit for bit."""
+    solve with it takes the direct-load solve's cycles and reaches the same solution to rounding."""
     from paper_1410_6609_gb300 import synth
     from paper_1410_6609_gb300.solver import Poisson
 
@@ -326,9 +383,10 @@ def test_fp64_tma_default_policy_and_solve_bit_identical():
         P.set_rhs(rho)
         P.set_solution(None)
         k, rel = P.solve(1e-10, 40)
-        out.append((k, rel, P.solution()))
-    assert out[0][0] == out[1][0] and out[0][1] == out[1][1] and out[0][1] < 1e-10
-    assert torch.equal(out[0][2], out[1][2])
+        out.append((k, rel, P.solution().cpu().numpy()))
+    assert out[0][0] == out[1][0] and out[0][1] < 1e-10 and out[1][1] < 1e-10
+    assert abs(out[0][1] - out[1][1]) <= 1e-3 * out[1][1]
+    assert np.linalg.norm(out[0][2] - out[1][2]) <= 1e-9 * np.linalg.norm(out[1][2])
     a.close()
     b.close()
 
@@ -351,6 +409,6 @@ def test_fp64_tma_wait_timeout_reported_and_context_usable():
     for colour in (0, 1):
         a.op_smooth(0, colour)
         b.op_smooth(0, colour)
-    assert torch.equal(a.level_get(0, 0), b.level_get(0, 0))
+    assert _maxrel(a.level_get(0, 0).cpu().numpy(), b.level_get(0, 0).cpu().numpy()) < 1e-14
     a.close()
     b.close()
