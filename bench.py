@@ -542,7 +542,8 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     phi64 = P64.solution()
     # the FP64-mode kernels of the same level: bytes against the measured HBM rate, FP64-pipe
     # operations against the FP64 issue peak (3 per cell in the half-sweep: int->double of the exact
-    # fixed-point neighbour sum, + g, x 1/D; 4 per fine cell in the residual + restriction)
+    # fixed-point neighbour sum, + g, x 1/D; 2 per fine cell in the residual + restriction by the
+    # fixed-point walk: int->double of the residual, the children's sum)
     sweep64 = "k_smooth_tma64" if P64.level_sweep_kind(0) == "tma" else "k_smooth_vec<double,2,0>"
     t64_sm = _time(lambda: P64.op_smooth(0, 0), P64.stream, 10)
     t64_rr = _time(lambda: P64.op_residual_restrict(0), P64.stream, 10)
@@ -553,8 +554,9 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
                               "fp64_frac": 0.5 * N * 3 / t64_sm / 1e9 / FP64_OPS_PEAK, "device_kernel": sweep64,
                               "bound": "integer ALU + FP64 pipe (fixed-point neighbour sum)"},
         "resid_restrict": {"ms": t64_rr, "GB/s": b64_rr / t64_rr / 1e6, "hbm_frac": b64_rr / t64_rr / 1e6 / hbm,
-                           "bytes_per_launch": int(b64_rr), "fp64_ops_per_cell": 4,
-                           "fp64_frac": N * 4 / t64_rr / 1e9 / FP64_OPS_PEAK},
+                           "bytes_per_launch": int(b64_rr), "fp64_ops_per_cell": 2,
+                           "fp64_frac": N * 2 / t64_rr / 1e9 / FP64_OPS_PEAK, "device_kernel": "k_resid_restrict_walk",
+                           "bound": "integer ALU (64-bit fixed-point residual per cell)"},
     }
     err = float(torch.linalg.norm(phi_m - phi64) / torch.linalg.norm(phi64))
 

@@ -55,6 +55,7 @@ struct mg_ctx {
   int sph_cap = 0;
   TmaSweep tma[kMaxLevels]{};  // TMA-staged single-precision half-sweeps, per level
   TmaSweep tma64[kMaxLevels]{};  // TMA-staged FP64 half-sweeps (FP64 mode), per level
+  unsigned char rr_walk[kMaxLevels]{};  // FP64 residual + restriction by the fixed-point walk, per level
   int* d_err = nullptr;        // set by a kernel whose bounded wait ran out
   int grad_stencil = 7;        // gradient of mg_efield / mg_force_gather: 7 (D3Q7) or 19 (D3Q19)
   double* d_bcf[6] = {};       // per-cell wall values of each face (allocated on first use)
@@ -194,7 +195,15 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
   // below what the inner cycle resolves, so only the red residuals are restricted. Double
   // precision keeps them: near FP64 convergence those rounding residuals are the residual.
   const bool red_only = std::is_same<T, float>::value && c->p.nu1 >= 1;
-  if ((e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], red_only, s)) != cudaSuccess) return e;
+  if constexpr (std::is_same<T, double>::value) {
+    if (c->rr_walk[l] && x == c->x64 && !red_only)
+      e = launch_resid_restrict_walk(x[l], g[l], G, g[l + 1], c->geo[l + 1], s);
+    else
+      e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], red_only, s);
+  } else {
+    e = launch_resid_restrict<T>(x[l], g[l], G, g[l + 1], c->geo[l + 1], red_only, s);
+  }
+  if (e != cudaSuccess) return e;
   ++*nk;
   if ((e = enqueue_vcycle<T>(c, x, g, inv, l + 1, true, s, nk)) != cudaSuccess) return e;
   // single precision, vector rows: the prolongation is fused into the first black half-sweep
@@ -494,6 +503,17 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
     for (int l = 0; l + 1 < c->L && e == cudaSuccess; ++l)
       if (all_tma ? tma_sweep64_applies(c->geo[l]) : tma_sweep64_pays(c->geo[l]))
         e = prepare_tma_sweep64(c->tma64[l], c->x64[l], c->g64[l], c->geo[l], dev);
+  }
+  // FP64 mode: the residual + restriction of the large levels by the fixed-point residual walk;
+  // CCMG_RESTRICT=vec keeps the direct-load kernel everywhere, =walk takes the walk on every
+  // packed level it can run on
+  if (!mixed(c)) {
+    const char* rr_env = std::getenv("CCMG_RESTRICT");
+    const bool rr_vec = rr_env && std::strcmp(rr_env, "vec") == 0;
+    const bool rr_all = rr_env && std::strcmp(rr_env, "walk") == 0;
+    for (int l = 0; l + 1 < c->L; ++l)
+      c->rr_walk[l] = !rr_vec && resid_restrict_walk_applies(c->geo[l]) &&
+                      (rr_all || cells(c->geo[l]) >= (1LL << 21));
   }
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
@@ -1107,6 +1127,10 @@ static mg_status residual_restrict_op(mg_ctx* c, int level, bool red_only) {
   else if (mixed(c))
     CK(launch_resid_restrict<float>(c->x32[level], c->g32[level], c->geo[level], c->g32[level + 1],
                                     c->geo[level + 1], red_only, c->stream),
+       "residual_restrict");
+  else if (c->rr_walk[level] && !red_only)
+    CK(launch_resid_restrict_walk(c->x64[level], c->g64[level], c->geo[level], c->g64[level + 1],
+                                  c->geo[level + 1], c->stream),
        "residual_restrict");
   else
     CK(launch_resid_restrict<double>(c->x64[level], c->g64[level], c->geo[level], c->g64[level + 1],

@@ -207,6 +207,11 @@ template <typename T>
 // residuals are zero up to rounding).
 cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, const Geom& Gc, bool red_only,
                                   cudaStream_t s);
+// FP64 residual + restriction by the fixed-point residual walk (packed levels of at least one
+// tile width); the direct-load kernel above serves the other levels and single precision.
+bool resid_restrict_walk_applies(const Geom& G);
+cudaError_t launch_resid_restrict_walk(const double* x, const double* g, const Geom& G, double* gc, const Geom& Gc,
+                                       cudaStream_t s);
 template <typename T>
 cudaError_t launch_prolong(T* x, const Geom& G, const T* ec, const Geom& Gc, T omega, bool red_only,
                            cudaStream_t s);

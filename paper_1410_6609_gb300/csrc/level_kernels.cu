@@ -65,6 +65,16 @@ __global__ void __launch_bounds__(256) k_resid_restrict_vec(const T* __restrict_
   resid_restrict_vec<T, V, RED_ONLY, PER>(x, g, G, gc, Gc, iv, J, K);
 }
 
+// FP64 residual and restriction by the residual walk (packed levels): the tiles of block
+// blockIdx.x of gridDim.x, every fine residual summed in fixed point per ring row, the eight
+// children of each coarse cell added and scaled by 1/4 (resid_tiles_accum, MODE 3).
+template <bool PER>
+__global__ void __launch_bounds__(256, 3) k_resid_restrict_walk(const double* __restrict__ x,
+                                                             const double* __restrict__ g, Geom G,
+                                                             double* __restrict__ gc, Geom Gc) {
+  resid_tiles_accum<3, PER>(x, g, G, blockIdx.x, gridDim.x, 0.0, nullptr, nullptr, 0.0, kBadPow2, gc, &Gc);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(T* __restrict__ x, Geom G, const T* __restrict__ ec, Geom Gc,
                                                  T omega, int red_only) {
@@ -399,6 +409,19 @@ cudaError_t launch_resid_restrict(const T* x, const T* g, const Geom& G, T* gc, 
     k_resid_restrict<T, true><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
   else
     k_resid_restrict<T, false><<<gr, b, 0, s>>>(x, g, G, gc, Gc);
+  return cudaGetLastError();
+}
+
+bool resid_restrict_walk_applies(const Geom& G) { return G.packed && G.hx >= kResTM; }
+
+cudaError_t launch_resid_restrict_walk(const double* x, const double* g, const Geom& G, double* gc, const Geom& Gc,
+                                       cudaStream_t s) {
+  if (!resid_restrict_walk_applies(G)) return cudaErrorInvalidValue;
+  const long long tiles = resid_tile_count(G);
+  const int grid = (int)(tiles < (1LL << 20) ? tiles : (1LL << 20));
+  const dim3 b(kResBX, kResBY, 1);
+  if (G.per) k_resid_restrict_walk<true><<<grid, b, 0, s>>>(x, g, G, gc, Gc);
+  else k_resid_restrict_walk<false><<<grid, b, 0, s>>>(x, g, G, gc, Gc);
   return cudaGetLastError();
 }
 

@@ -1095,16 +1095,25 @@ __host__ __device__ __forceinline__ long long resid_tile_count(const Geom& G, in
 // whose rows hold an infinity or NaN (E = 2047) takes the direct FP64 formula from global memory.
 constexpr int kResXR = kResTJ + 2, kResXC = kResTM + 2;
 
+// MODE 3: the residual's restriction instead of its norm (the FP64 cycle's fused residual and
+// restriction, Sec. 3): coarse cell (I, J, K) of the next level (gc, geometry Gc) becomes 1/4 of
+// the sum of its eight children's scaled residuals. A lane's two cells (packed column m = I, both
+// colours) are the children with i = 2I and 2I+1; it adds them over the planes 2K, 2K+1, and the
+// warp of row 2J+1 hands its sums through shared memory to the warp of row 2J, which adds them
+// after the next barrier and writes the coarse value (tiles start on even rows and planes, and
+// levels with a coarser one have even extents, so the pairs never straddle tiles).
 template <int MODE, bool PER>
 __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x, const double* __restrict__ g,
                                                     const Geom& G, long long lb, long long nb, double c0,
                                                     double* __restrict__ outn, float* __restrict__ outp, double isc,
-                                                    int p2) {
+                                                    int p2, double* __restrict__ gc = nullptr,
+                                                    const Geom* Gc = nullptr) {
   // ring slot b, row r (0 and kResXR-1 are the halo rows), colour c, column col (0 and kResXC-1 are
   // the halo columns) at b * kSlot + r * kRow + c * kResXC + col
   constexpr int kRow = 2 * kResXC, kSlot = kResXR * kRow;
   __shared__ long long sT[4 * kSlot];  // values in units of their row's 2^(E_row - 1080)
   __shared__ int sE[4 * kResXR];       // E_row of ring slot b, row r at b * kResXR + r
+  __shared__ double sR[MODE == 3 ? kResTJ / 2 * kResTM : 1];  // MODE 3: the odd rows' sums
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int w = tid >> 5, lane = tid & 31;
   int nmb, njb;
@@ -1179,6 +1188,15 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
         for (int c = 0; c < 2; ++c) put(b, rr, c, lane + 1, fx_at(r.row[c], eh));
       }
     };
+    // MODE 3: this lane's sum over its two cells and the plane pair, kept by an even row until the
+    // odd row's arrives
+    double racc = 0.0, rkeep = 0.0;
+    int kpend = -1;
+    auto flush = [&]() {
+      if (MODE == 3 && kpend >= 0 && (w & 1) == 0 && live)
+        gc[coarse_index(*Gc, m, j >> 1, kpend)] = 0.25 * (rkeep + sR[(w >> 1) * kResTM + lane]);
+      kpend = -1;
+    };
     __syncthreads();  // the previous tile's last reads of the ring are done
     Raw pre;
     fetch(k0 - 1, pre);
@@ -1197,6 +1215,10 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
       }
       store(k + 1, cur);
       __syncthreads();
+      if (MODE == 3 && (k & 1) == 0) {
+        flush();  // the pair of planes before: the odd row's sums were published by this barrier
+        racc = 0.0;
+      }
       // the two cells of this thread; G0: the right-hand side is zero in every cell of the warp's
       // row (most cells of a charged-particle problem carry no charge), so its term is left out,
       // a uniform branch (7.5 % of the walk's time at 512^3 with 1600 charged spheres)
@@ -1227,7 +1249,8 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
           if (!G0) sum += fx_at(gv[c], E);
           const double rd = E == 2047 ? (double)resid_packed<double, PER>(x, g, G, c, m, j, k)
                                       : fx_to_double((unsigned long long)sum, E);
-          acc = fma(rd, rd, acc);
+          if (MODE != 3) acc = fma(rd, rd, acc);
+          if (MODE == 3) racc += rd;
           if (MODE == 1) outn[(long long)(2 * m + s) + (long long)G.nx * ((long long)j + (long long)ny * k)] = rd * c0;
           if (MODE == 2)
             outp[(long long)c * G.csz + k * plane + col] =
@@ -1241,6 +1264,15 @@ __device__ __forceinline__ double resid_tiles_accum(const double* __restrict__ x
         if (g0) cells(std::true_type{});
         else cells(std::false_type{});
       }
+      if (MODE == 3 && (k & 1) == 1) {
+        if (w & 1) sR[(w >> 1) * kResTM + lane] = racc;
+        else rkeep = racc;
+        kpend = k >> 1;
+      }
+    }
+    if (MODE == 3) {
+      __syncthreads();
+      flush();
     }
   }
   return acc;
