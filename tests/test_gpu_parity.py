@@ -168,6 +168,50 @@ def test_efield_and_forces_match_oracle():
     P2.close()
 
 
+@pytest.mark.parametrize("h", [0.5, 0.3])
+def test_efield_differences_bit_exact(h):
+    """The central differences of the E-field, E = (phi(x - 1) - phi(x + 1)) / (2h) per axis, bit for
+    bit against the IEEE double subtraction (numpy) on every interior cell, for potentials chosen
+    to exercise the rounding of the differences: magnitudes spread over 2^-600 .. 2^600 with zeros of both signs, subnormals, neighbours equal
+    or a few ulps apart (cancellation), values near the largest double (overflow to infinity), and
+    an infinity. With h = 0.5 the factor 1/(2h) is 1; with h = 0.3 it is a rounded FP64 product.
+    Rows of 128 packed columns, so that the warps away from the x walls take the interior path;
+    the sign of a zero difference is not compared (the wall path forms it as -(phi(x+1) - phi(x-1)))."""
+    dims = (256, 24, 16)
+    nx, ny, nz = dims
+    rng = np.random.default_rng(31)
+    phi = rng.standard_normal((nz, ny, nx)) * np.exp2(rng.integers(-600, 601, (nz, ny, nx)).astype(float))
+    u = rng.random(phi.shape)
+    phi[u < 0.05] = 0.0
+    phi[(u >= 0.05) & (u < 0.08)] = -0.0
+    phi[(u >= 0.08) & (u < 0.11)] = rng.integers(-50, 50, int(((u >= 0.08) & (u < 0.11)).sum())) * 5e-324
+    # x neighbours two apart equal, or a few ulps apart
+    sel = (u >= 0.11) & (u < 0.2)
+    kk, jj, ii = np.nonzero(sel)
+    ok = ii + 2 < nx
+    kk, jj, ii = kk[ok], jj[ok], ii[ok]
+    steps = rng.integers(-3, 4, kk.size)
+    phi[kk, jj, ii + 2] = phi[kk, jj, ii] + steps * np.spacing(phi[kk, jj, ii])
+    big = (u >= 0.2) & (u < 0.22)
+    phi[big] = np.sign(rng.standard_normal(int(big.sum()))) * 1.7e308
+    phi[nz // 2, ny // 2, nx // 2] = np.inf
+    P = Poisson(dims, h=h, bc_type=(D,) * 6)
+    P.set_solution(gpu(phi))
+    E = cpu(P.efield())
+    P.close()
+    inv2h = 1.0 / (2.0 * h)
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref = [(phi[1:-1, 1:-1, :-2] - phi[1:-1, 1:-1, 2:]), (phi[1:-1, :-2, 1:-1] - phi[1:-1, 2:, 1:-1]),
+               (phi[:-2, 1:-1, 1:-1] - phi[2:, 1:-1, 1:-1])]
+        ref = [r if h == 0.5 else r * inv2h for r in ref]
+    for a in range(3):
+        got, want = E[a][1:-1, 1:-1, 1:-1], ref[a]
+        nan = np.isnan(want)
+        assert np.array_equal(np.isnan(got), nan), a
+        g_, w_ = np.where(got == 0, 0.0, got)[~nan], np.where(want == 0, 0.0, want)[~nan]
+        assert np.array_equal(g_.view(np.uint64), w_.view(np.uint64)), (a, int((g_ != w_).sum()))
+
+
 @pytest.mark.parametrize("h", [1.0, 0.3])
 def test_d3q19_efield_and_forces_match_oracle(h):
     """The D3Q19 gradient (Sec. 2.4) where all 18 neighbours exist, D3Q7 elsewhere: the GPU repeats
