@@ -645,3 +645,31 @@ def test_per_cell_wall_values_match_oracle(h):
     with pytest.raises(Exception):
         P.set_bc_field(6, gpu(field[0]))
     P.close()
+
+
+def test_fp64_residual_walk_non_finite_values():
+    """Infinities and a NaN in the iterate: the cells whose rows hold them take the direct FP64
+    formula (the walk's fallback); the non-finite pattern equals the oracle's, and every finite
+    residual is within the walk's bound of the oracle's FP64 residual."""
+    dims, bc = (80, 20, 72), (D, N, N, D, D, N)
+    nx, ny, nz = dims
+    rng = np.random.default_rng(29)
+    phi = rng.standard_normal((nz, ny, nx))
+    phi[3, 4, 10] = np.inf
+    phi[40, 12, 60] = -np.inf
+    phi[66, 17, 33] = np.nan
+    g = rng.standard_normal((nz, ny, nx))
+    P = Poisson(dims, h=1.0, bc_type=bc)
+    assert P.num_levels > 1
+    P.level_set(0, 0, gpu(phi))
+    P.level_set(0, 1, gpu(g))
+    _, r = P.residual(field=True)
+    r = cpu(r)
+    P.close()
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = oracle.residual(phi, g, 1.0, bc)
+    assert np.array_equal(np.isnan(r), np.isnan(ref))
+    assert np.array_equal(np.isinf(r), np.isinf(ref)) and np.array_equal(r[np.isinf(r)], ref[np.isinf(ref)])
+    fin = np.isfinite(ref)
+    assert (~fin).sum() >= 3
+    assert np.abs(r[fin] - ref[fin]).max() <= 1e-14 * np.abs(ref[fin]).max()

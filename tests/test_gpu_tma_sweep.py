@@ -412,3 +412,30 @@ def test_fp64_tma_wait_timeout_reported_and_context_usable():
     assert _maxrel(a.level_get(0, 0).cpu().numpy(), b.level_get(0, 0).cpu().numpy()) < 1e-14
     a.close()
     b.close()
+
+
+def test_fp64_tma_half_sweep_non_finite_values():
+    """An infinity and a NaN in the iterate: the tile planes around them take the direct FP64 sum.
+    Infinite and NaN results where the direct-load sweep has them, finite cells within 1e-14."""
+    dims = (136, 40, 32)
+    a, b = _fp64_pair(dims, bc_type=BC_MIX)
+    nx, ny, nz = dims
+    rng = np.random.default_rng(23)
+    phi = rng.standard_normal((nz, ny, nx))
+    phi[10, 20, 32] = np.inf     # a red cell (i + j + k even)
+    phi[20, 5, 100] = -np.inf    # a black one
+    phi[25, 30, 71] = np.nan     # red
+    f = rng.standard_normal((nz, ny, nx))
+    for colour in (0, 1):
+        for P in (a, b):
+            P.level_set(0, 0, torch.from_numpy(phi).cuda())
+            P.level_set(0, 1, torch.from_numpy(f).cuda())
+            P.op_smooth(0, colour)
+        xa, xb = a.level_get(0, 0).cpu().numpy(), b.level_get(0, 0).cpu().numpy()
+        assert np.array_equal(np.isnan(xa), np.isnan(xb)) and np.array_equal(np.isinf(xa), np.isinf(xb))
+        fin = np.isfinite(xb)
+        assert np.array_equal(xa[np.isinf(xa)], xb[np.isinf(xb)])
+        assert np.abs(xa[fin] - xb[fin]).max() <= 1e-14 * np.abs(xb[fin]).max()
+        assert (~fin).sum() >= 3
+    a.close()
+    b.close()
