@@ -1352,27 +1352,31 @@ __device__ __forceinline__ double resid_norm_accum(const T* __restrict__ x, cons
 }
 
 // The single-precision residual copy of a zero iterate (r~ = g exactly) over the same rows of
-// block lb of nb as resid_norm_accum: float(g isc), without evaluating the stencil.
+// The single-precision residual copy of a zero iterate (r~ = g exactly) for block lb of nb of a
+// level: float(g isc) over the block's contiguous share of the level's values (both colour arrays
+// of a packed level are one contiguous range, a natural-order level is one too), two values per
+// thread and step with 16-byte loads where the arrays allow it. Every value is written once, the
+// same values as the stencil would give.
 __device__ __forceinline__ void resid_zero_rows(const double* __restrict__ g, const Geom& G, long long lb, long long nb,
                                                 float* __restrict__ outp, double isc) {
   const int p2 = pow2_exponent(isc);
-  if (G.packed) {
-    const long long rows = 2LL * G.nz * G.ny;
-    for (long long rw = lb * kResBY + threadIdx.y; rw < rows; rw += nb * kResBY) {
-      const int k = (int)(rw / (2LL * G.ny));
-      const int rem = (int)(rw - 2LL * G.ny * k);
-      const int j = rem >> 1, c = rem & 1;
-      const long long base = (long long)c * G.csz + ((long long)k * G.ny + j) * G.hx;
-      for (int m = threadIdx.x; m < G.hx; m += kResBX) {
-        const double v = g[base + m];
-        outp[base + m] = (p2 != kBadPow2) ? f32_of_scaled(v, p2) : (float)(v * isc);
+  auto cv = [&](double v) { return (p2 != kBadPow2) ? f32_of_scaled(v, p2) : (float)(v * isc); };
+  const long long n = G.packed ? 2LL * G.csz : (long long)G.nx * G.ny * G.nz;
+  const long long per = (((n + nb - 1) / nb) + 1) & ~1LL;  // an even share per block
+  const long long a = lb * per, b = a + per < n ? a + per : n;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const bool vec = ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(outp)) & 15) == 0;
+  if (vec) {
+    for (long long i = a + 2LL * tid; i < b; i += 2LL * nt) {
+      if (i + 1 < b) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(g + i));
+        *reinterpret_cast<float2*>(outp + i) = make_float2(cv(v.x), cv(v.y));
+      } else {
+        outp[i] = cv(g[i]);
       }
     }
   } else {
-    const long long n = (long long)G.nx * G.ny * G.nz;
-    const int tid = threadIdx.y * kResBX + threadIdx.x;
-    for (long long i = lb * (kResBX * kResBY) + tid; i < n; i += nb * (kResBX * kResBY))
-      outp[i] = (p2 != kBadPow2) ? f32_of_scaled(g[i], p2) : (float)(g[i] * isc);
+    for (long long i = a + tid; i < b; i += nt) outp[i] = cv(g[i]);
   }
 }
 
