@@ -807,8 +807,8 @@ def measure_batched(tol: float = 1e-9):
     stream = Bt.stream
 
     def run_batch():
+        Bt.set_rhs_all(rho)
         for b in range(len(ws)):
-            Bt.set_rhs(b, rho[b])
             Bt.set_solution(b, None)
         return Bt.solve(tol, 50)
 

@@ -335,6 +335,12 @@ mg_status mg_batch_destroy(mg_batch* b);
 const char* mg_batch_last_error(const mg_batch* b);
 int mg_batch_size(const mg_batch* b);
 mg_status mg_batch_set_rhs(mg_batch* b, int sys, const double* d_rho);        /* as mg_set_rhs */
+/* Every system's right-hand side at once: h_rho is a host array of B device pointers (system s's
+ * charge density, natural order, its own dimensions; none NULL). The same values, norms and
+ * first defect-correction scales as B calls of mg_batch_set_rhs, in three launches instead of
+ * 4 B. Stream-ordered; returns without waiting for the GPU (it may wait for the staging copy of
+ * the call before the previous one). MG_ERR_INVALID for a NULL array or entry. */
+mg_status mg_batch_set_rhs_all(mg_batch* b, const double* const* h_rho);
 mg_status mg_batch_set_solution(mg_batch* b, int sys, const double* d_phi);   /* NULL = zero */
 mg_status mg_batch_get_solution(mg_batch* b, int sys, double* d_phi);
 /* ncycles cycles of every system (MG_MIXED: outer defect-correction steps). No sync. */

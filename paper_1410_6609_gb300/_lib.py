@@ -96,6 +96,7 @@ SIGNATURES = {
     "mg_batch_last_error": (ctypes.c_char_p, [_P]),
     "mg_batch_size": (_I, [_P]),
     "mg_batch_set_rhs": (_I, [_P, _I, _P]),
+    "mg_batch_set_rhs_all": (_I, [_P, _P]),
     "mg_batch_set_solution": (_I, [_P, _I, _P]),
     "mg_batch_get_solution": (_I, [_P, _I, _P]),
     "mg_batch_vcycle": (_I, [_P, _I]),

@@ -91,6 +91,14 @@ class BatchPoisson:
         rho = self._field(b, rho)
         self._check(self.lib.mg_batch_set_rhs(self.h, b, _ptr(rho)), "mg_batch_set_rhs")
 
+    def set_rhs_all(self, rhos):
+        """Every system's right-hand side in one call (three launches): rhos[b] as for set_rhs(b)."""
+        if len(rhos) != self.B:
+            raise ValueError(f"need {self.B} right-hand sides, got {len(rhos)}")
+        fields = [self._field(b, r) for b, r in enumerate(rhos)]
+        arr = (ctypes.c_void_p * self.B)(*[t.data_ptr() for t in fields])
+        self._check(self.lib.mg_batch_set_rhs_all(self.h, arr), "mg_batch_set_rhs_all")
+
     def set_solution(self, b: int, phi=None):
         if phi is not None:
             phi = self._field(b, phi)

@@ -78,6 +78,14 @@ struct mg_batch {
   // last has run (its event), so a later host-side change never leaks into an earlier upload
   static constexpr int kFlagSlots = 16;
   int* h_flag_ring = nullptr;
+  // mg_batch_set_rhs_all: the job table on the device, its staging ring on the host (two slots,
+  // each reused once its copy has run), the sum-of-squares partials of all systems
+  RhsJob* d_rhs = nullptr;
+  RhsJob* h_rhs = nullptr;
+  cudaEvent_t rhs_ev[2]{};
+  int rhs_slot = 0;
+  int rhs_nsb = 0;
+  double* d_rhs_partials = nullptr;
   cudaEvent_t flag_ev[kFlagSlots]{};
   int flag_slot = 0;
   double* d_scal = nullptr;
@@ -460,6 +468,11 @@ void free_batch(mg_batch* b) {
   for (int k = 0; k < mg_batch::kFlagSlots; ++k)
     if (b->flag_ev[k]) cudaEventDestroy(b->flag_ev[k]);
   if (b->h_scal) cudaFreeHost(b->h_scal);
+  cudaFree(b->d_rhs);
+  cudaFree(b->d_rhs_partials);
+  if (b->h_rhs) cudaFreeHost(b->h_rhs);
+  for (int k = 0; k < 2; ++k)
+    if (b->rhs_ev[k]) cudaEventDestroy(b->rhs_ev[k]);
   if (b->cap) cudaStreamDestroy(b->cap);
 }
 
@@ -624,6 +637,19 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->arena, 0, bytes, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_scal, 0, (size_t)B * kScalStride * sizeof(double), b->stream);
+  if (e == cudaSuccess) {  // mg_batch_set_rhs_all: one sum-of-squares partial per block of each system
+    long long nsb = 0;
+    for (int s = 0; s < B; ++s) {
+      RhsJob j;
+      rhs_job_static(j, b->sys[s].geo[0], nullptr, 1.0, 1.0, b->sys[s].bc, nullptr);
+      nsb += j.sbn;
+    }
+    b->rhs_nsb = (int)nsb;
+    e = cudaMalloc((void**)&b->d_rhs_partials, (size_t)nsb * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_rhs, (size_t)B * sizeof(RhsJob));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_rhs, (size_t)2 * B * sizeof(RhsJob));
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->rhs_ev[k], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     const bool oom = (e == cudaErrorMemoryAllocation);
     std::string msg = std::string("mg_batch_create: ") + cudaGetErrorString(e);
@@ -684,6 +710,38 @@ mg_status mg_batch_set_rhs(mg_batch* b, int s, const double* d_rho) {
   BCK(launch_finalize(b->d_partials, np, sc, kSlotGsum, -1, 0, b->stream), "batch set_rhs");
   BCK(launch_set_scale(sc, kSlotGsum, kSlotScale, (double)cells(G), b->stream), "batch set_rhs");
   b->launches += 4;
+  return MG_OK;
+}
+
+mg_status mg_batch_set_rhs_all(mg_batch* b, const double* const* h_rho) {
+  if (!b) return MG_ERR_INVALID;
+  if (!h_rho) return bfail(b, MG_ERR_INVALID, "null array of right-hand sides");
+  for (int s = 0; s < b->B; ++s)
+    if (!h_rho[s]) return bfail(b, MG_ERR_INVALID, "null right-hand side in the array");
+  const int k = b->rhs_slot;
+  b->rhs_slot ^= 1;
+  BCK(cudaEventSynchronize(b->rhs_ev[k]), "batch set_rhs_all");  // the slot's previous copy has run
+  RhsJob* J = b->h_rhs + (size_t)k * b->B;
+  long long nb = 0;
+  int sb = 0;
+  for (int s = 0; s < b->B; ++s) {
+    BSys& S = b->sys[s];
+    const Geom& G = S.geo[0];
+    rhs_job_static(J[s], G, S.g64[0], 1.0 / S.p.eps, S.p.h, S.bc, b->d_scal + (size_t)kScalStride * s);
+    J[s].rho = h_rho[s];
+    J[s].pair = G.packed && reinterpret_cast<uintptr_t>(h_rho[s]) % 16 == 0;
+    J[s].b0 = nb;
+    J[s].sb0 = sb;
+    const long long items = J[s].pair ? (long long)G.hx * G.ny * G.nz : (long long)G.nx * G.ny * G.nz;
+    nb += (items + 255) / 256;
+    sb += J[s].sbn;
+  }
+  BCK(cudaMemcpyAsync(b->d_rhs, J, (size_t)b->B * sizeof(RhsJob), cudaMemcpyHostToDevice, b->stream),
+      "batch set_rhs_all");
+  BCK(cudaEventRecord(b->rhs_ev[k], b->stream), "batch set_rhs_all");
+  BCK(launch_set_rhs_all(b->d_rhs, b->B, nb, sb, b->d_rhs_partials, kSlotGsum, kSlotScale, b->stream),
+      "batch set_rhs_all");
+  b->launches += 3;
   return MG_OK;
 }
 

@@ -322,6 +322,40 @@ cudaError_t launch_b_smooth_prolong(const BLaunch& L, const int* active, const I
 template <typename T>
 cudaError_t launch_b_coarse_cg(const BLaunch& L, const int* active, size_t smem, double rtol, cudaStream_t s);
 cudaError_t prepare_b_coarse_cg();
+// The wall terms of a right-hand side (Sec. 2.4): t[q] = 2 value / h^2 (Dirichlet), value / h
+// (Neumann), 0 (periodic) for a face with one value; field[q] for a face with values per cell.
+struct WallTerms {
+  double t[6];
+  const double* field[6];
+  int type[6];
+  double h;
+};
+WallTerms make_wall_terms(const FaceBC& bc, double h);
+
+// One system of a batched right-hand-side setting (mg_batch_set_rhs_all): its finest level, the
+// factors and wall terms of its set_rhs, its scalars, and the block layout of its sum of squares
+// (the one launch_sumsq takes, so that the norms equal a single context's).
+struct RhsJob {
+  Geom G;
+  double* g;          // finest scaled right-hand side
+  const double* rho;  // this call's charge density, natural order
+  double inv_eps, hsq;
+  int qe, qh, pow2, fld;
+  WallTerms wt;
+  int pair;      // packed level and 16-byte aligned rho: two cells per thread
+  long long b0;  // first block of this system in the right-hand-side launch
+  int sb0, sbn;  // its sum-of-squares blocks: first, count
+  double* scal;  // its scalars
+  double n;      // its cells
+};
+// The parts of a job that do not change from call to call (all but rho, pair and b0).
+void rhs_job_static(RhsJob& j, const Geom& G, double* g, double inv_eps, double h, const FaceBC& bc, double* scal);
+// Right-hand sides, their sums of squares (partials: one per sum-of-squares block of all jobs),
+// norms into slot_gsum and the first defect-correction scale into slot_scale (and its
+// reciprocal) of every job's scalars: three launches for the whole batch.
+cudaError_t launch_set_rhs_all(const RhsJob* d_jobs, int B, long long nblocks, int nsblocks, double* partials,
+                               int slot_gsum, int slot_scale, cudaStream_t s);
+
 // Per-system scalars of a batch: kScalStride doubles per system, same slots as a single context.
 constexpr int kScalStride = 8;
 constexpr int kSlotGsum = 0, kSlotRsum = 1, kSlotRel = 2, kSlotScale = 3, kSlotInvScale = 4;

@@ -148,12 +148,6 @@ __global__ void k_set_scale(double* scal, int src, int dst, double n) {
 // the finest grid): f = rho/eps + wall terms, stored scaled, g = f * h^2. A face with one value
 // has its term precomputed (t[q]); a face with values per cell computes 2 g / h^2 (Dirichlet) or
 // g / h (Neumann) per cell with the same operations.
-struct WallTerms {
-  double t[6];
-  const double* field[6];
-  int type[6];
-  double h;
-};
 __device__ __forceinline__ double wall_term(const WallTerms& wt, int q, int i, int j, int k, const Geom& G) {
   if (!wt.field[q]) return wt.t[q];
   const double g = __ldg(wt.field[q] + face_index(q, i, j, k, G.nx, G.ny));
@@ -175,12 +169,9 @@ __device__ __forceinline__ double add_wall_terms(double v, int i, int j, int k, 
 }
 // POW2: 1/eps = 2^qe and h^2 = 2^qh (lattice units), the products are exponent shifts.
 template <typename T, bool POW2, bool FIELD>
-__global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
-                                                 double inv_eps, double hsq, int qe, int qh, WallTerms wt, int raw) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= G.nx || j >= G.ny) return;
+__device__ __forceinline__ void set_rhs_cell(T* __restrict__ gout, const Geom& G, const double* __restrict__ rho,
+                                             double inv_eps, double hsq, int qe, int qh, const WallTerms& wt, int raw,
+                                             int i, int j, int k) {
   const long long p = (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
   double v = rho[p];
   if (!raw) {
@@ -194,18 +185,23 @@ __global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, c
   if (G.packed) o = (long long)((i + j + k) & 1) * G.csz + ((long long)k * G.ny + j) * G.hx + (i >> 1);
   gout[o] = (T)(POW2 ? ldexp_rne(v, qh) : v * hsq);
 }
+template <typename T, bool POW2, bool FIELD>
+__global__ void __launch_bounds__(256) k_set_rhs(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
+                                                 double inv_eps, double hsq, int qe, int qh, WallTerms wt, int raw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  set_rhs_cell<T, POW2, FIELD>(gout, G, rho, inv_eps, hsq, qe, qh, wt, raw, i, j, k);
+}
 
 // The same for a packed level, two cells per thread: cells 2m and 2m+1 of row (j, k) are one
 // 16-byte load of rho and land at index m of the two colour arrays, so both the loads and the
 // stores of a warp are contiguous.
 template <typename T, bool POW2, bool FIELD>
-__global__ void __launch_bounds__(256) k_set_rhs_pair(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
-                                                      double inv_eps, double hsq, int qe, int qh, WallTerms wt,
-                                                      int raw) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (m >= G.hx || j >= G.ny) return;
+__device__ __forceinline__ void set_rhs_pair(T* __restrict__ gout, const Geom& G, const double* __restrict__ rho,
+                                             double inv_eps, double hsq, int qe, int qh, const WallTerms& wt, int raw,
+                                             int m, int j, int k) {
   const int i0 = 2 * m;
   const long long p = (long long)i0 + (long long)G.nx * ((long long)j + (long long)G.ny * k);
   const double2 r = __ldg(reinterpret_cast<const double2*>(rho + p));
@@ -223,6 +219,80 @@ __global__ void __launch_bounds__(256) k_set_rhs_pair(T* __restrict__ gout, Geom
   const long long o = ((long long)k * G.ny + j) * G.hx + m;
   gout[(long long)c0 * G.csz + o] = (T)(POW2 ? ldexp_rne(v0, qh) : v0 * hsq);
   gout[(long long)(c0 ^ 1) * G.csz + o] = (T)(POW2 ? ldexp_rne(v1, qh) : v1 * hsq);
+}
+template <typename T, bool POW2, bool FIELD>
+__global__ void __launch_bounds__(256) k_set_rhs_pair(T* __restrict__ gout, Geom G, const double* __restrict__ rho,
+                                                      double inv_eps, double hsq, int qe, int qh, WallTerms wt,
+                                                      int raw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (m >= G.hx || j >= G.ny) return;
+  set_rhs_pair<T, POW2, FIELD>(gout, G, rho, inv_eps, hsq, qe, qh, wt, raw, m, j, k);
+}
+
+// Batched right-hand sides (mg_batch_set_rhs_all): blocks of 256 items (cell pairs of a packed
+// level with aligned rho, else cells) of every system in turn, each item the same per-cell
+// operations as the single-system kernels above.
+template <bool POW2, bool FIELD>
+__device__ __forceinline__ void set_rhs_item(const RhsJob& J, long long q) {
+  const Geom& G = J.G;
+  if (J.pair) {
+    const long long row = q / G.hx;
+    const int m = (int)(q - row * G.hx), j = (int)(row % G.ny), k = (int)(row / G.ny);
+    if (k < G.nz) set_rhs_pair<double, POW2, FIELD>(J.g, G, J.rho, J.inv_eps, J.hsq, J.qe, J.qh, J.wt, 0, m, j, k);
+  } else {
+    const long long row = q / G.nx;
+    const int i = (int)(q - row * G.nx), j = (int)(row % G.ny), k = (int)(row / G.ny);
+    if (k < G.nz) set_rhs_cell<double, POW2, FIELD>(J.g, G, J.rho, J.inv_eps, J.hsq, J.qe, J.qh, J.wt, 0, i, j, k);
+  }
+}
+__global__ void __launch_bounds__(256) k_set_rhs_all(const RhsJob* __restrict__ jobs, int B, long long nblocks) {
+  int s = 0;
+  for (long long vb = blockIdx.x; vb < nblocks; vb += gridDim.x) {
+    while (s + 1 < B && jobs[s + 1].b0 <= vb) ++s;
+    const RhsJob& J = jobs[s];
+    const long long q = (vb - J.b0) * 256 + threadIdx.x;
+    if (J.pow2) {
+      if (J.fld) set_rhs_item<true, true>(J, q);
+      else set_rhs_item<true, false>(J, q);
+    } else {
+      if (J.fld) set_rhs_item<false, true>(J, q);
+      else set_rhs_item<false, false>(J, q);
+    }
+  }
+}
+// Each system's sum of squares of g in the block layout of k_sumsq with its own grid of J.sbn
+// blocks (the same partials, hence the same norm as a single context), then per system the fixed
+// order sum of its partials (k_finalize) and the scale (k_set_scale).
+__global__ void __launch_bounds__(256) k_sumsq_all(const RhsJob* __restrict__ jobs, int B, int nsblocks,
+                                                   double* __restrict__ partials) {
+  __shared__ double red[33];
+  int s = 0;
+  for (int vb = blockIdx.x; vb < nsblocks; vb += gridDim.x) {
+    while (s + 1 < B && jobs[s + 1].sb0 <= vb) ++s;
+    const RhsJob& J = jobs[s];
+    const long long n = (long long)J.n, lb = vb - J.sb0;
+    double acc = 0.0;
+    for (long long i = lb * 256 + threadIdx.x; i < n; i += (long long)J.sbn * 256) {
+      const double v = J.g[i];
+      acc = fma(v, v, acc);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[vb] = acc;
+  }
+}
+__global__ void __launch_bounds__(256) k_finalize_all(const RhsJob* __restrict__ jobs, const double* __restrict__ partials,
+                                                      int slot_gsum, int slot_scale) {
+  __shared__ double red[33];
+  const RhsJob& J = jobs[blockIdx.x];
+  const double acc = sum_partials(partials + J.sb0, J.sbn, red);
+  if (threadIdx.x == 0) {
+    J.scal[slot_gsum] = acc;
+    const double sc = pow2_floor(sqrt(J.scal[slot_gsum] / J.n));
+    J.scal[slot_scale] = sc;
+    J.scal[slot_scale + 1] = 1.0 / sc;
+  }
 }
 
 template <typename T>
@@ -493,9 +563,7 @@ cudaError_t launch_set_scale(double* scal, int src, int dst, double n, cudaStrea
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_eps, double h, const FaceBC& bc, int raw,
-                           cudaStream_t s) {
+WallTerms make_wall_terms(const FaceBC& bc, double h) {
   WallTerms wt;
   for (int q = 0; q < 6; ++q) {
     wt.t[q] = bc.type[q] == 0 ? 2.0 * bc.value[q] / (h * h) : (bc.type[q] == 1 ? bc.value[q] / h : 0.0);
@@ -503,6 +571,47 @@ cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_ep
     wt.type[q] = bc.type[q];
   }
   wt.h = h;
+  return wt;
+}
+
+void rhs_job_static(RhsJob& j, const Geom& G, double* g, double inv_eps, double h, const FaceBC& bc, double* scal) {
+  j.G = G;
+  j.g = g;
+  j.rho = nullptr;
+  j.inv_eps = inv_eps;
+  j.hsq = h * h;
+  j.qe = host_pow2_exponent(inv_eps);
+  j.qh = host_pow2_exponent(j.hsq);
+  j.pow2 = j.qe != kBadPow2 && j.qh != kBadPow2;
+  j.fld = has_field(bc) ? 1 : 0;
+  j.wt = make_wall_terms(bc, h);
+  j.pair = 0;
+  j.b0 = 0;
+  const long long n = (long long)G.nx * G.ny * G.nz;
+  long long blocks = (n + 255) / 256;  // as launch_sumsq
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  j.sb0 = 0;
+  j.sbn = (int)blocks;
+  j.scal = scal;
+  j.n = (double)n;
+}
+
+cudaError_t launch_set_rhs_all(const RhsJob* d_jobs, int B, long long nblocks, int nsblocks, double* partials,
+                               int slot_gsum, int slot_scale, cudaStream_t s) {
+  if (B < 1) return cudaSuccess;
+  const long long g1 = nblocks < 152 * 16 ? nblocks : 152 * 16;
+  k_set_rhs_all<<<(int)(g1 > 0 ? g1 : 1), 256, 0, s>>>(d_jobs, B, nblocks);
+  const int g2 = nsblocks < 152 * 8 ? nsblocks : 152 * 8;
+  k_sumsq_all<<<g2 > 0 ? g2 : 1, 256, 0, s>>>(d_jobs, B, nsblocks, partials);
+  k_finalize_all<<<B, 256, 0, s>>>(d_jobs, partials, slot_gsum, slot_scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_set_rhs(T* g, const Geom& G, const double* rho, double inv_eps, double h, const FaceBC& bc, int raw,
+                           cudaStream_t s) {
+  const WallTerms wt = make_wall_terms(bc, h);
   const bool fld = has_field(bc);
   dim3 b, gr;
   const double hsq = h * h;

@@ -101,6 +101,7 @@ def test_batch_create_rejects_invalid_params():
     assert lib.mg_batch_create(2, arr, None, ctypes.byref(h)) == _lib.MG_ERR_INVALID
     assert b"even" in lib.mg_batch_last_error(None)
     assert lib.mg_batch_solve(None, 1e-9, 10, None, None) == _lib.MG_ERR_INVALID
+    assert lib.mg_batch_set_rhs_all(None, None) == _lib.MG_ERR_INVALID
 
 
 @needs_nvcc

@@ -189,3 +189,40 @@ def test_tma_staged_batch_equals_direct_load_batch_and_single_contexts():
         if b < len(TMA_SYSTEMS) - 1:
             f = oracle.rhs(rho[b].cpu().numpy(), s["h"], s["bc_type"], s["bc_value"])
             assert oracle.rel_residual(st[b].cpu().numpy(), f, s["h"], s["bc_type"]) < 1.0001e-9, b
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_set_rhs_all_equals_per_system_calls(precision):
+    """mg_batch_set_rhs_all (three launches for every system) gives the same solves, bit for bit,
+    as set_rhs per system, whether a density sits on a 16-byte boundary (two cells per thread) or
+    not (one cell per thread); called twice in a row, the second call's values are the ones
+    solved; a wrong count is refused."""
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    rho = rhos()
+    shifted = []
+    for r in rho:  # the same values 8 bytes past a 16-byte boundary
+        buf = torch.empty(r.numel() + 1, dtype=torch.float64, device="cuda")
+        v = buf[1:].view(r.shape)
+        v.copy_(r)
+        shifted.append(v)
+    assert all(t.data_ptr() % 16 == 8 for t in shifted)
+    out = []
+    for mode in ("each", "all", "all_shifted"):
+        Bt = BatchPoisson(SYSTEMS, precision=precision)
+        if mode == "each":
+            for b, r in enumerate(rho):
+                Bt.set_rhs(b, r)
+        elif mode == "all":
+            Bt.set_rhs_all([r * 2.0 for r in rho])  # overwritten by the next call
+            Bt.set_rhs_all(rho)
+        else:
+            Bt.set_rhs_all(shifted)
+        cyc, rel = Bt.solve(tol, 50)
+        out.append((cyc, rel, [Bt.solution(b).clone() for b in range(len(SYSTEMS))]))
+        if mode == "all":
+            with pytest.raises(ValueError):
+                Bt.set_rhs_all(rho[:-1])
+        Bt.close()
+    for o in out[1:]:
+        assert o[0] == out[0][0] and o[1] == out[0][1]
+        assert all(torch.equal(a, b) for a, b in zip(o[2], out[0][2]))
