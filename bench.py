@@ -582,6 +582,14 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
         out["time_loop"] = measure_time_loop(P, w, sp, r, q, stream)
     except Exception as e:
         out["time_loop"] = {"error": repr(e)}
+    try:  # the same loop with one FP32 V(2,2) per outer step: one cycle per time step, as in Sec. 8.1
+        P1 = Poisson(w.dims, h=w.h, bc_type=w.bc_type, bc_value=w.bc_value, precision="mixed", mixed_inner=1)
+        d1 = measure_time_loop(P1, w, sp, r, q, P1.stream)
+        d1["fp32_cycles_per_outer_step"] = 1
+        out["time_loop_one_fp32_cycle"] = d1
+        P1.close()
+    except Exception as e:
+        out["time_loop_one_fp32_cycle"] = {"error": repr(e)}
     try:
         out["time_loop_periodic"] = measure_time_loop_periodic(w, sp)
     except Exception as e:
