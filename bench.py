@@ -364,6 +364,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         cycles_seen.clear()
         launches0 = P.kernel_launches
+        counts0 = P.outer_counts()
         barrier()
         torch.cuda.synchronize()
         t_wall0 = time.time()
@@ -376,6 +377,8 @@ def run_ours(args):
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = (P.kernel_launches - launches0) // args.steps
+    counts = [(b - a) / args.steps for a, b in zip(counts0, P.outer_counts())]
+    outer = {"cycles": counts[0], "by_recurrence": counts[1], "direct_residuals": counts[2]}
     ms_all = max_over_ranks(ms, world, "cuda")
     value = whole_job_mlups(N, world, ms_all)
     k_step = cycles_seen[-1][0]
@@ -385,7 +388,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras:
-        extras = measure_extras(P, w, sp, c, r, q, rho, stream, k_step)
+        extras = measure_extras(P, w, sp, c, r, q, rho, stream, k_step, outer)
 
     # e2e: the public host-buffer call (spheres in, forces out) plus the E-field, timed by wall clock
     P.set_solution(None)
@@ -419,7 +422,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f64+f32", "data": "synthetic",
             "config": {**workload_config(w), "parallelism": parallelism(world)},
-            "cycles_per_step": k_step, "final_rel_residual": rel_final,
+            "cycles_per_step": k_step, "final_rel_residual": rel_final, "outer_steps_per_step": outer,
             "gpu_launches": int(launches),
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -471,7 +474,7 @@ MEASURED_TRAFFIC = {
 }
 
 
-def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
+def measure_extras(P, w, sp, c, r, q, rho, stream, k_step, outer):
     """Kernel-level timings for the roofline, the FP64 GPU solve at the same tolerance, and the
     error of the mixed solution against it."""
     import torch
@@ -490,9 +493,18 @@ def measure_extras(P, w, sp, c, r, q, rho, stream, k_step):
     mixed = w.precision == "mixed"
     bytes_res = N * (8 + 8 + (4 if mixed else 0))
     kern["residual_fp64"] = {"ms": t_res, "GB/s": bytes_res / t_res / 1e6,
-                             "launches_per_step": k_step, "bytes_per_launch": int(bytes_res),
+                             "launches_per_step": outer["direct_residuals"], "bytes_per_launch": int(bytes_res),
                              "bound": "integer ALU (64-bit fixed-point sum per cell)",
                              "note": "plus one stencil-free residual of the zero start per step"}
+    if outer["by_recurrence"] > 0:
+        # the outer step that carries the residual by recurrence (phi += s e, residual pair - A e)
+        t_def = _time(P.op_defect_step, stream, 10)
+        bytes_def = N * 36
+        kern["defect_update"] = {"ms": t_def, "GB/s": bytes_def / t_def / 1e6,
+                                 "launches_per_step": outer["by_recurrence"], "bytes_per_launch": bytes_def,
+                                 "device_kernel": "k_defect_rec",
+                                 "note": "reads e (4 B), phi (8), the residual pair (8), writes phi and the pair; "
+                                         "the first step from zero reads g (8 B) and no phi: 28 B per cell"}
     # smoother half-sweep and fused residual+restriction on the finest level
     esz = 4 if mixed else 8
     inner = P.mixed_inner if mixed else 1  # finest-level V-cycles per outer step

@@ -166,8 +166,21 @@ mg_status mg_vcycle(mg_ctx* ctx, int ncycles);
 /* Algorithm 1: while ||f - A phi||_2 / ||f||_2 >= rel_tol and fewer than max_cycles cycles:
  * one cycle. Writes the cycle count and the final relative residual (host pointers, either
  * may be NULL). Returns MG_ERR_NOT_CONVERGED if max_cycles is reached first or the residual
- * is not finite, MG_ERR_DIVERGED if it grows above 1e3 times its starting value. */
+ * is not finite, MG_ERR_DIVERGED if it grows above 1e3 times its starting value.
+ * MG_MIXED with the constant operator, from the zero iterate of mg_set_solution(NULL) (not in
+ * the paper): an outer step may carry the residual by recurrence, r <- r - s A e (see
+ * mg_op_defect_update), instead of evaluating it from phi; it does so from the zero start and
+ * after another such step, unless the last contraction predicts that the step reaches rel_tol.
+ * The residual is evaluated directly before every decision that ends the solve (below rel_tol,
+ * not finite, diverged, max_cycles), and the relative residual written to h_rel_res is always
+ * that direct evaluation. Environment CCMG_DEFECT=walk (read at mg_create) evaluates it
+ * directly after every step. */
 mg_status mg_solve(mg_ctx* ctx, double rel_tol, int max_cycles, int* h_cycles, double* h_rel_res);
+/* Counts since mg_create (host array of 3): [0] outer cycles run by mg_solve, [1] those of them
+ * that carried the residual by recurrence, [2] direct evaluations of the finest-level residual
+ * (mg_solve's checks, mg_residual, mg_op_residual_norm; not the stencil-free residual of a zero
+ * iterate). */
+mg_status mg_outer_counts(const mg_ctx* ctx, long long* h_counts3);
 
 /* Relative residual ||f - A phi||_2 / ||f||_2 of the current solution (host scalar), and, if
  * d_r is not NULL, the residual field f - A phi itself (nx*ny*nz doubles). */
@@ -286,6 +299,34 @@ mg_status mg_op_coarse_solve(mg_ctx* ctx, int* h_iters);
  * reduction of its squared norm; in MG_MIXED mode also the scaled single-precision residual that
  * the next inner cycle solves for), without reading anything back. For timing that kernel. */
 mg_status mg_op_residual_norm(mg_ctx* ctx);
+
+/* One outer step of the MG_MIXED defect correction with the residual carried by recurrence
+ * (not in the paper), for verifying it: from the iterate phi_k (d_phi; ignored with zero_start,
+ * where phi_k = 0), a correction e (d_e, each value rounded to float) and the scaled residual
+ * r~_k = g + sum of the six neighbours - (6 + d) phi_k (d_r; the level's units, g = f / c_0),
+ * it forms phi_{k+1} = phi_k + sc e (one rounded FP64 addition; sc e exact) and
+ * r~_{k+1} = r~_k - sc A e, where A e = (6 + d) e - sum of e's six neighbours is the constant
+ * operator with the context's walls. The residual is carried in units of the scales as a pair of
+ * floats: r~_k / sc is split into hi + lo (hi rounded to nearest, lo the rounded remainder) and
+ * r~_{k+1} / sc_next is returned the same way (d_hi_out, d_lo_out: hi is the single-precision
+ * right-hand side of the next inner cycles); their sum lies within 2^-44 (|r~_k| / sc +
+ * |r~_{k+1}| / sc) + 2^-58 sum(|terms of A e|) of the exact value (A e is summed by three
+ * cascades of error-free additions). h_sumsq receives sum(hi^2) sc_next^2, the squared norm
+ * the solver takes for the next scale. All fields natural order, nx*ny*nz doubles of device
+ * memory, borrowed. sc, sc_next: powers of two in [2^-800, 2^800]. Overwrites the context's
+ * finest iterate, single-precision finest level and scalars (and with zero_start its finest
+ * right-hand side, which then holds r~_0). MG_ERR_INVALID unless MG_MIXED with finest rows of
+ * whole 4-float vectors (nx a multiple of 8), for bad scales or null pointers. Synchronises. */
+mg_status mg_op_defect_update(mg_ctx* ctx, int zero_start, double sc, double sc_next, const double* d_phi,
+                              const double* d_e, const double* d_r, double* d_phi_out, double* d_hi_out,
+                              double* d_lo_out, double* h_sumsq);
+
+/* Enqueue the recurrence step alone on the context's current state (the next scale from the
+ * last residual norm, then the update of the iterate and of the residual pair by the current
+ * single-precision finest correction, and the pair's norm), without reading anything back. For
+ * timing that kernel; the state it leaves is not a residual of the iterate. MG_ERR_INVALID where
+ * mg_op_defect_update is. */
+mg_status mg_op_defect_step(mg_ctx* ctx);
 
 /* The power-of-two products and precision conversions on caller data, for verifying them (not in
  * the paper): d_xf[i] = float(d_x[i] * (1/sc)) as MG_MIXED hands the outer residual to the inner

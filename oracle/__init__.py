@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-ba
 imports it and shares no code with it.
 
 The arithmetic lives in ``ccmg_oracle.c`` (plain scalar loops, FP64, ``-ffp-contract=off``);
-this module only compiles it with gcc, loads it with ctypes and marshals NumPy arrays.
+this module only compiles it with gcc, loads it with ctypes and marshals NumPy arrays. The one
+exception is ``defect_update`` (NumPy with an exactly rounded ``math.fsum`` per cell).
 Arrays are C-ordered ``[nz, ny, nx]`` (x fastest), matching the C layout ``i + nx*(j + ny*k)``.
 
 Every function cites the paper passage it follows (section / equation / algorithm).
@@ -14,6 +15,7 @@ Pins that tie the oracle to something other than itself are in ``tests/test_orac
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -316,6 +318,46 @@ def solve(f, h: float, bc_type, tol: float = 1e-10, max_cycles: int = 100, nu1: 
     k = _load().ccmg_or_solve(_p(phi), _p(f), *_dims(f), h, _p(_bc(bc_type)), nu1, nu2, omega, tol,
                               max_cycles, ctypes.byref(rel))
     return phi, k, rel.value
+
+
+def defect_update(phi, e, r, s: float, bc_type):
+    """One outer step of the mixed-precision defect correction with the residual carried by
+    recurrence (not in the paper; its operator is the folded stencil of Sec. 2.4 on a level of
+    Sec. 3). Adding s e to the iterate changes the residual by exactly -s A e, so
+
+        phi' = phi + s e                 (s a power of two: s e is exact, one FP64 rounding),
+        r'   = r - s A e = r + s (sum of e's six neighbours - (6 + d) e),
+
+    in the scaled units of the level (r = g + sum - D phi, g = f / c_l): a neighbour across a
+    periodic face is the cell at the opposite side, a Dirichlet face adds 1 to the diagonal and a
+    Neumann face takes 1 from it (the correction has homogeneous walls). e is rounded to float
+    first, as the single-precision inner cycles hold it. Every term of r' is then an exact double
+    (a float times a small integer times a power of two), and r' is their sum rounded once to the
+    nearest double (math.fsum, an exactly rounded summation). Pure-Python loop over the cells:
+    small grids only. Returns (phi', r')."""
+    phi, r = _f64(phi), _f64(r)
+    ev = np.ascontiguousarray(e, dtype=np.float32).astype(np.float64)
+    bc = _bc(bc_type)
+    nz, ny, nx = ev.shape
+    n = (nx, ny, nz)
+    terms = [r.copy()]
+    diag = np.full(ev.shape, 6.0)
+    for face in range(6):
+        axis, step = face // 2, (-1 if face % 2 == 0 else 1)
+        nb = np.roll(ev, -step, axis=2 - axis)  # nb[cell] = e[cell + step along the axis]
+        idx = np.arange(n[axis])
+        edge = (idx == 0) if step < 0 else (idx == n[axis] - 1)  # cells whose neighbour is outside
+        shape = [1, 1, 1]
+        shape[2 - axis] = n[axis]
+        edge = np.broadcast_to(edge.reshape(shape), ev.shape)
+        if bc[face] != PERIODIC:  # the wrapped value is no neighbour: a wall
+            nb = np.where(edge, 0.0, nb)
+            diag = diag + np.where(edge, 1.0 if bc[face] == DIRICHLET else -1.0, 0.0)
+        terms.append(s * nb)
+    terms.append(-s * (diag * ev))
+    stack = np.stack(terms, axis=-1).reshape(-1, len(terms))
+    r_new = np.array([math.fsum(row) for row in stack]).reshape(ev.shape)
+    return phi + s * ev, r_new
 
 
 def solve_mixed(f, h: float, bc_type, tol: float = 1e-9, max_cycles: int = 100, nu1: int = 2,

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 LIB_PATH = os.path.join(HERE, "libccmg.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["level_kernels.cu", "smooth_tma.cu", "field_kernels.cu", "ccmg_api.cu", "static_scratch.cu", "var_kernels.cu",
-           "batch_kernels.cu", "batch_api.cu"]
+           "batch_kernels.cu", "batch_api.cu", "defect_kernels.cu"]
 HEADERS = ["ccmg_internal.cuh", "level_ops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

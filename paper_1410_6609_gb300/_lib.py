@@ -82,6 +82,9 @@ SIGNATURES = {
     "mg_op_coarse_solve": (_I, [_P, _P]),
     "mg_op_residual_norm": (_I, [_P]),
     "mg_op_scale_convert": (_I, [_P, _P, _P, ctypes.c_longlong, _D, _P, _P, _P, _P]),
+    "mg_op_defect_update": (_I, [_P, _I, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
+    "mg_op_defect_step": (_I, [_P]),
+    "mg_outer_counts": (_I, [_P, _P]),
     "mg_kernel_launches": (ctypes.c_longlong, [_P]),
     "mg_level_sweep_kind": (_I, [_P, _I]),
     "mg_selftest_wait_timeout": (_I, [_P, _I]),

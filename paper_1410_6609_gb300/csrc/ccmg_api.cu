@@ -19,7 +19,11 @@ using namespace ccmg;
 
 namespace {
 
-enum Slot { S_GSUM = 0, S_RSUM = 1, S_REL = 2, S_SCALE = 3, S_INV_SCALE = 4, S_PB_REF = 5, S_PB_REL = 6, S_COUNT = 8 };
+enum Slot {
+  S_GSUM = 0, S_RSUM = 1, S_REL = 2, S_SCALE = 3, S_INV_SCALE = 4, S_PB_REF = 5, S_PB_REL = 6,
+  S_NEXT = 8,  // the next outer step's scale and its inverse (9) while a recurrence step runs
+  S_COUNT = 10
+};
 
 thread_local std::string g_create_error;
 
@@ -46,7 +50,12 @@ struct mg_ctx {
   cudaGraphExec_t g_cycle0 = nullptr;  // mixed: the first cycle from a zero iterate (phi = s e)
   cudaGraphExec_t g_resid = nullptr;
   cudaGraphExec_t g_resid0 = nullptr;  // the termination residual of a zero iterate (r = f)
-  long long n_cycle = 0, n_cycle0 = 0, n_resid = 0, n_resid0 = 0;  // kernel nodes per graph
+  cudaGraphExec_t g_rec = nullptr;   // mixed: a cycle whose update carries the residual by recurrence
+  cudaGraphExec_t g_rec0 = nullptr;  // the same from a zero iterate
+  long long n_cycle = 0, n_cycle0 = 0, n_resid = 0, n_resid0 = 0, n_rec = 0, n_rec0 = 0;  // kernel nodes per graph
+  float* q_lo = nullptr;     // mixed: low part of the residual pair whose high part is g32[0] (recurrence)
+  bool rec_on = false;       // mixed solves carry the residual by recurrence between direct checks
+  long long cnt_cycles = 0, cnt_rec = 0, cnt_direct = 0;  // outer cycles, those by recurrence, direct residuals
   bool phi_zero = true;                // the finest iterate is known to be exactly zero
   bool x_lazy = false;                 // mixed: x64[0] holds no data, its value is zero
   long long launches = 0;
@@ -95,6 +104,9 @@ void free_all(mg_ctx* c) {
   if (c->g_cycle0) cudaGraphExecDestroy(c->g_cycle0);
   if (c->g_resid) cudaGraphExecDestroy(c->g_resid);
   if (c->g_resid0) cudaGraphExecDestroy(c->g_resid0);
+  if (c->g_rec) cudaGraphExecDestroy(c->g_rec);
+  if (c->g_rec0) cudaGraphExecDestroy(c->g_rec0);
+  cudaFree(c->q_lo);
   for (int l = 0; l < kMaxLevels; ++l) {
     cudaFree(c->x64[l]);
     cudaFree(c->g64[l]);
@@ -249,6 +261,28 @@ cudaError_t enqueue_cycle(mg_ctx* c, cudaStream_t s, long long* nk, bool first) 
   return cudaSuccess;
 }
 
+// A mixed cycle whose update also carries the residual by recurrence: mixed_inner single-
+// precision V-cycles on the scaled residual's high part g32[0] (the first from e = 0), the next
+// scale from the residual's norm into scal[S_NEXT], then phi += s e (phi = s e from a zero
+// iterate, `first`) with the residual pair (g32[0], q_lo) updated to (r - s A e) / s_next, its
+// norm and relative norm (scal[S_RSUM], scal[S_REL]), and s_next made current. From a zero
+// iterate the pair is formed from g64[0] (r = f); otherwise it must hold the current residual
+// (rec_avail).
+cudaError_t enqueue_cycle_rec(mg_ctx* c, cudaStream_t s, long long* nk, bool first) {
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < c->p.mixed_inner; ++it)
+    if ((e = enqueue_vcycle<float>(c, c->x32, c->g32, c->inv32, 0, it == 0, s, nk)) != cudaSuccess) return e;
+  if ((e = launch_set_scale(c->scal, S_RSUM, S_NEXT, (double)cells(c->geo[0]), s)) != cudaSuccess) return e;
+  int np = 0;
+  e = launch_defect_rec(c->x64[0], c->x32[0], c->g32[0], c->q_lo, c->g64[0], c->geo[0], c->scal, S_SCALE, S_NEXT,
+                        first, c->partials, &np, s);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_defect_finalize(c->partials, np, c->scal, S_RSUM, S_REL, S_GSUM, S_SCALE, S_NEXT, s)) != cudaSuccess)
+    return e;
+  *nk += 3;
+  return cudaSuccess;
+}
+
 // Termination quantity ||r|| / ||f|| into scal[S_REL]; in mixed mode also the scaled
 // single-precision residual for the next inner cycle.
 cudaError_t enqueue_resid(mg_ctx* c, int mode, double* out_natural, cudaStream_t s, long long* nk) {
@@ -303,6 +337,14 @@ mg_status ensure_graphs(mg_ctx* c) {
                  [c](cudaStream_t s, long long* nk) { return enqueue_cycle(c, s, nk, true); }, "capture cycle");
     if (st != MG_OK) return st;
   }
+  if (c->rec_on && !c->d_eps) {
+    st = capture(c, &c->g_rec, &c->n_rec,
+                 [c](cudaStream_t s, long long* nk) { return enqueue_cycle_rec(c, s, nk, false); }, "capture cycle");
+    if (st != MG_OK) return st;
+    st = capture(c, &c->g_rec0, &c->n_rec0,
+                 [c](cudaStream_t s, long long* nk) { return enqueue_cycle_rec(c, s, nk, true); }, "capture cycle");
+    if (st != MG_OK) return st;
+  }
   const int mode = mixed(c) ? 2 : 0;
   st = capture(c, &c->g_resid, &c->n_resid,
                [c, mode](cudaStream_t s, long long* nk) { return enqueue_resid(c, mode, nullptr, s, nk); },
@@ -331,7 +373,27 @@ mg_status run_cycle(mg_ctx* c) {
   if (st != MG_OK) return st;
   c->x_lazy = false;
   c->phi_zero = false;
+  ++c->cnt_cycles;
   return MG_OK;
+}
+
+mg_status check_err_flag(mg_ctx* c);
+
+// A cycle that carries the residual by recurrence, then its relative residual (scal[S_REL]) read
+// back: an estimate that only a direct evaluation (read_rel) confirms.
+mg_status run_cycle_rec(mg_ctx* c, double* rel) {
+  mg_status st = c->x_lazy ? run_graph(c, c->g_rec0, c->n_rec0, "cycle")
+                           : run_graph(c, c->g_rec, c->n_rec, "cycle");
+  if (st != MG_OK) return st;
+  c->x_lazy = false;
+  c->phi_zero = false;
+  ++c->cnt_cycles;
+  ++c->cnt_rec;
+  CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read residual");
+  CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error flag");
+  CK(cudaStreamSynchronize(c->stream), "residual sync");
+  *rel = c->h_pin[0];
+  return check_err_flag(c);
 }
 
 // Write the zeros of a finest iterate that mg_set_solution(NULL) left unwritten, before a call
@@ -359,6 +421,7 @@ mg_status read_rel(mg_ctx* c, double* rel) {
   mg_status st = c->phi_zero ? run_graph(c, c->g_resid0, c->n_resid0, "residual")
                              : run_graph(c, c->g_resid, c->n_resid, "residual");
   if (st != MG_OK) return st;
+  if (!c->phi_zero) ++c->cnt_direct;
   CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read residual");
   CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error flag");
   CK(cudaStreamSynchronize(c->stream), "residual sync");
@@ -474,6 +537,11 @@ mg_status mg_create(const mg_params* p, void* stream, mg_ctx** out) {
       alloc((void**)&c->g32[l], n * sizeof(float));
     }
   }
+  // MG_MIXED: the outer steps carry the residual by recurrence (defect_kernels.cu) on finest levels
+  // of whole 4-float rows; CCMG_DEFECT=walk evaluates it directly after every step instead
+  const char* defect_env = std::getenv("CCMG_DEFECT");
+  c->rec_on = mixed(c) && defect_rec_applies(c->geo[0]) && !(defect_env && std::strcmp(defect_env, "walk") == 0);
+  if (c->rec_on) alloc((void**)&c->q_lo, (size_t)cells(c->geo[0]) * sizeof(float));
   alloc((void**)&c->partials, kMaxPartials * sizeof(double));
   alloc((void**)&c->scal, S_COUNT * sizeof(double));
   alloc((void**)&c->d_iters, sizeof(int));
@@ -648,7 +716,7 @@ namespace {
 
 // The cycle and residual graphs hold the operator's kernels: drop them to be captured again.
 void drop_graphs(mg_ctx* c) {
-  for (cudaGraphExec_t* gx : {&c->g_cycle, &c->g_cycle0, &c->g_resid, &c->g_resid0})
+  for (cudaGraphExec_t* gx : {&c->g_cycle, &c->g_cycle0, &c->g_resid, &c->g_resid0, &c->g_rec, &c->g_rec0})
     if (*gx) {
       cudaGraphExecDestroy(*gx);
       *gx = nullptr;
@@ -871,10 +939,22 @@ mg_status mg_solve(mg_ctx* c, double tol, int max_cycles, int* h_cycles, double*
   mg_status st = ensure_graphs(c);
   if (st != MG_OK) return st;
   int k = 0;
-  double rel = 0.0, rel0 = -1.0;
+  double rel = 0.0, rel0 = -1.0, rel_prev = -1.0;
   mg_status out = MG_OK;
+  // MG_MIXED with the constant operator: a cycle may carry the residual by recurrence (from a zero
+  // iterate, or after another such cycle), which leaves an estimate of the relative residual in
+  // place of its direct evaluation. The direct evaluation follows whenever the estimate would end
+  // the solve (below the tolerance, non-finite, diverged, or at max_cycles), so every result the
+  // solve returns is evaluated directly. The recurrence is skipped for a cycle that the last
+  // contraction predicts to reach the tolerance: that cycle is followed by the direct evaluation.
+  const bool use_rec = c->rec_on && !c->d_eps && !c->d_k2;
+  bool estimate = false;  // rel is the recurrence's estimate
   for (;;) {
-    if ((st = read_rel(c, &rel)) != MG_OK) return st;
+    if (!estimate ||
+        !(rel >= tol) || !std::isfinite(rel) || (rel0 >= 0.0 && rel > 1e3 * rel0) || k >= max_cycles) {
+      if ((st = read_rel(c, &rel)) != MG_OK) return st;
+      estimate = false;
+    }
     if (!std::isfinite(rel)) {
       out = fail(c, MG_ERR_NOT_CONVERGED, "residual is not finite");
       break;
@@ -889,7 +969,16 @@ mg_status mg_solve(mg_ctx* c, double tol, int max_cycles, int* h_cycles, double*
       out = fail(c, MG_ERR_NOT_CONVERGED, "max_cycles reached before the tolerance");
       break;
     }
-    if ((st = run_cycle(c)) != MG_OK) return st;
+    // the recurrence continues from a zero iterate or from its own last step
+    const bool rec_next = use_rec && (c->x_lazy || estimate) && !(rel_prev > 0.0 && rel * (rel / rel_prev) < tol);
+    rel_prev = rel;
+    if (rec_next) {
+      if ((st = run_cycle_rec(c, &rel)) != MG_OK) return st;
+      estimate = true;
+    } else {
+      if ((st = run_cycle(c)) != MG_OK) return st;
+      estimate = false;
+    }
     ++k;
   }
   if (h_cycles) *h_cycles = k;
@@ -904,6 +993,7 @@ mg_status mg_residual(mg_ctx* c, double* h_rel, double* d_r) {
   long long nk = 0;
   CK(enqueue_resid(c, d_r ? 1 : 0, d_r, c->stream, &nk), "residual");
   c->launches += nk;
+  ++c->cnt_direct;
   CK(cudaMemcpyAsync(c->h_pin, c->scal + S_REL, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "residual");
   CK(cudaMemcpyAsync(c->h_pin + 1, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "residual");
   CK(cudaStreamSynchronize(c->stream), "residual sync");
@@ -1219,6 +1309,76 @@ mg_status mg_op_residual_norm(mg_ctx* c) {
   long long nk = 0;
   CK(enqueue_resid(c, mixed(c) ? 2 : 0, nullptr, c->stream, &nk), "residual_norm");
   c->launches += nk;
+  ++c->cnt_direct;
+  return MG_OK;
+}
+
+mg_status mg_op_defect_update(mg_ctx* c, int zero_start, double sc, double sc_next, const double* d_phi,
+                              const double* d_e, const double* d_r, double* d_phi_out, double* d_hi_out,
+                              double* d_lo_out, double* h_sumsq) {
+  if (!c) return MG_ERR_INVALID;
+  if (!c->rec_on) return fail(c, MG_ERR_INVALID, "the recurrence step needs MG_MIXED and finest rows of whole 4-float vectors");
+  // both scales powers of two in [2^-800, 2^800], as the solver's are
+  int p = 0, pn = 0;
+  const bool ok = sc > 0.0 && sc_next > 0.0 && std::isfinite(sc) && std::isfinite(sc_next) &&
+                  std::frexp(sc, &p) == 0.5 && std::frexp(sc_next, &pn) == 0.5 && std::abs(p - 1) <= 800 &&
+                  std::abs(pn - 1) <= 800;
+  if (!ok) return fail(c, MG_ERR_INVALID, "scales must be powers of two in [2^-800, 2^800]");
+  p -= 1;
+  if (!d_e || !d_r || (!zero_start && !d_phi) || !d_phi_out || !d_hi_out || !d_lo_out || !h_sumsq)
+    return fail(c, MG_ERR_INVALID, "null argument");
+  const Geom& G = c->geo[0];
+  CK(launch_pack<float>(c->x32[0], G, d_e, 1.0, c->stream), "defect_update");
+  if (zero_start) {
+    CK(launch_pack<double>(c->g64[0], G, d_r, 1.0, c->stream), "defect_update");
+  } else {
+    CK(launch_pack<double>(c->x64[0], G, d_phi, 1.0, c->stream), "defect_update");
+    CK(launch_pack_pair(c->g32[0], c->q_lo, G, d_r, -p, c->stream), "defect_update");
+  }
+  const double sv[2] = {sc, 1.0 / sc}, nv[2] = {sc_next, 1.0 / sc_next};
+  CK(cudaMemcpyAsync(c->scal + S_SCALE, sv, sizeof(sv), cudaMemcpyHostToDevice, c->stream), "defect_update");
+  CK(cudaMemcpyAsync(c->scal + S_NEXT, nv, sizeof(nv), cudaMemcpyHostToDevice, c->stream), "defect_update");
+  int np = 0;
+  CK(launch_defect_rec(c->x64[0], c->x32[0], c->g32[0], c->q_lo, c->g64[0], G, c->scal, S_SCALE, S_NEXT,
+                       zero_start != 0, c->partials, &np, c->stream),
+     "defect_update");
+  CK(launch_defect_finalize(c->partials, np, c->scal, S_RSUM, S_REL, S_GSUM, S_SCALE, S_NEXT, c->stream),
+     "defect_update");
+  CK(launch_unpack<double>(d_phi_out, c->x64[0], G, 1.0, c->stream), "defect_update");
+  CK(launch_unpack<float>(d_hi_out, c->g32[0], G, 1.0, c->stream), "defect_update");
+  CK(launch_unpack<float>(d_lo_out, c->q_lo, G, 1.0, c->stream), "defect_update");
+  CK(cudaMemcpyAsync(c->h_pin, c->scal + S_RSUM, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "defect_update");
+  CK(cudaStreamSynchronize(c->stream), "defect_update");
+  *h_sumsq = c->h_pin[0];
+  c->x_lazy = false;
+  c->phi_zero = false;
+  c->launches += zero_start ? 8 : 9;
+  return MG_OK;
+}
+
+mg_status mg_outer_counts(const mg_ctx* c, long long* h_counts3) {
+  if (!c || !h_counts3) return MG_ERR_INVALID;
+  h_counts3[0] = c->cnt_cycles;
+  h_counts3[1] = c->cnt_rec;
+  h_counts3[2] = c->cnt_direct;
+  return MG_OK;
+}
+
+mg_status mg_op_defect_step(mg_ctx* c) {
+  if (!c) return MG_ERR_INVALID;
+  if (!c->rec_on) return fail(c, MG_ERR_INVALID, "the recurrence step needs MG_MIXED and finest rows of whole 4-float vectors");
+  mg_status st = materialize(c);
+  if (st != MG_OK) return st;
+  const Geom& G = c->geo[0];
+  int np = 0;
+  CK(launch_set_scale(c->scal, S_RSUM, S_NEXT, (double)cells(G), c->stream), "defect_step");
+  CK(launch_defect_rec(c->x64[0], c->x32[0], c->g32[0], c->q_lo, c->g64[0], G, c->scal, S_SCALE, S_NEXT, false,
+                       c->partials, &np, c->stream),
+     "defect_step");
+  CK(launch_defect_finalize(c->partials, np, c->scal, S_RSUM, S_REL, S_GSUM, S_SCALE, S_NEXT, c->stream),
+     "defect_step");
+  c->phi_zero = false;
+  c->launches += 3;
   return MG_OK;
 }
 

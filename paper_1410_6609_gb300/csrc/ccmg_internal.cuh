@@ -259,6 +259,21 @@ cudaError_t launch_scale_convert(const double* x, const float* e, const double* 
 // x = s e for an iterate that is zero (x is not read).
 cudaError_t launch_set_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
 cudaError_t launch_update_mixed(double* x, const float* e, long long n, const double* scal, int slot, cudaStream_t s);
+// The outer step with the residual carried by recurrence (defect_kernels.cu): x += s e (x = s e
+// for a zero, unwritten iterate: `zero`, the pair then formed from g / s), the residual pair
+// (qh, ql) in units of s = scal[slot] becomes (pair - A e) in units of scal[slot_next], and the
+// per-block sums of squares of the new qh go to partials (*nparts of them). Packed levels with
+// rows of whole 4-float vectors (defect_rec_applies).
+bool defect_rec_applies(const Geom& G);
+cudaError_t launch_defect_rec(double* x, const float* e, float* qh, float* ql, const double* g, const Geom& G,
+                              double* scal, int slot, int slot_next, bool zero, double* partials, int* nparts,
+                              cudaStream_t s);
+// scal[rsum] = sum(partials) scal[next]^2, scal[rel] = sqrt(rsum / scal[gsum]), then the next
+// scale and its inverse move into scal[scale], scal[scale + 1].
+cudaError_t launch_defect_finalize(const double* partials, int nparts, double* scal, int slot_rsum, int slot_rel,
+                                   int slot_gsum, int slot_scale, int slot_next, cudaStream_t s);
+// Natural-order double field times 2^q -> the packed float pair (qh, ql) (verification).
+cudaError_t launch_pack_pair(float* qh, float* ql, const Geom& G, const double* src, int q, cudaStream_t s);
 
 // Fields and forces (finest level, FP64 packed potential).
 struct Spheres {

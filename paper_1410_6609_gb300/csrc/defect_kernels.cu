@@ -1,0 +1,319 @@
+// defect_kernels.cu -- the outer step of the mixed-precision defect correction with its residual
+// updated by recurrence (not in the paper; the paper's solver is FP64 throughout).
+//
+// An outer step adds s e (e: the single-precision inner cycles' correction, s: a power of two) to
+// the FP64 iterate, so its residual changes by exactly -s A e: r~' = r~ + s (sum of e's six
+// neighbours - (6 + d) e_c) in the scaled units of the level (r~ = g + sum - D x, Sec. 2.4 and
+// Sec. 3). This file forms that change exactly enough to carry the residual from step to step
+// without reading the iterate's stencil:
+//  - A e of seven floats with small integer weights is summed by three cascades of error-free
+//    additions (Knuth's TwoSum, the product by Dekker's method with one FMA): the terms, their
+//    rounding errors, and those errors' errors, so that only the last, third-order sum rounds
+//    (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005, the K = 3 case of SumK). Its
+//    error is below 2^-60 of the sum of the terms' magnitudes.
+//  - The residual is held as a pair of floats hi + lo in units of the current scale s: hi is the
+//    single-precision right-hand side the next inner cycles solve for, lo (|lo| <= ulp(hi)/2) the
+//    rest, so the pair carries about 48 bits. New pair = old pair + A e in error-free steps, one
+//    rounding of the small remainders (below 2^-45 of the old and new residuals), then a
+//    power-of-two rescaling to the next step's scale (exact).
+//  - The iterate update phi' = phi + s e is the single rounded FP64 add of the plain update.
+// Single precision is the right tool here: the error-free transformations run on the FP32 pipe,
+// the whole step reads e, phi and the pair once and writes phi and the pair once (36 B per cell,
+// against 40 B for the plain update followed by the FP64 residual walk, which is bound by its
+// integer work), and only the iterate update uses the FP64 pipe. The solver still evaluates the
+// residual directly (the fixed-point walk) before it accepts convergence.
+#include "level_ops.cuh"
+
+namespace ccmg {
+namespace {
+
+using namespace ops;
+
+// a + b = s + t exactly (round to nearest; no overflow).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The three leading components of xm + xp + ym + yp + zm + zp + nd c (nd = -(6 + d)): the
+// exact value minus the rounding of the third component, which is below 2^-60 of the terms'
+// magnitudes.
+struct F3 {
+  float a, b, c;
+};
+__device__ __forceinline__ F3 stencil_sum(float xm, float xp, float ym, float yp, float zm, float zp, float nd,
+                                          float c) {
+  const float p = __fmul_rn(nd, c);
+  const float q = __fmaf_rn(nd, c, -p);  // nd c = p + q exactly
+  float s, e1, e2, e3, e4, e5, e6;
+  two_sum(xm, xp, s, e1);
+  two_sum(s, ym, s, e2);
+  two_sum(s, yp, s, e3);
+  two_sum(s, zm, s, e4);
+  two_sum(s, zp, s, e5);
+  two_sum(s, p, s, e6);
+  float t, f1, f2, f3, f4, f5, f6;
+  two_sum(e1, e2, t, f1);
+  two_sum(t, e3, t, f2);
+  two_sum(t, e4, t, f3);
+  two_sum(t, e5, t, f4);
+  two_sum(t, e6, t, f5);
+  two_sum(t, q, t, f6);
+  const float u = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(f1, f2), f3), f4), f5), f6);
+  return {s, t, u};
+}
+
+// (hi, lo) = (qh + ql) + (T.a + T.b + T.c) as a normalised float pair (hi = the sum rounded to
+// float, |lo| <= ulp(hi)/2): the leading parts cancel without error, the rest is rounded once.
+__device__ __forceinline__ void add_pair(float qh, float ql, const F3& T, float& hi, float& lo) {
+  float u, eu, v, ev, h1, e1;
+  two_sum(qh, T.a, u, eu);
+  two_sum(ql, T.b, v, ev);
+  two_sum(u, v, h1, e1);
+  const float rest = __fadd_rn(__fadd_rn(__fadd_rn(eu, ev), e1), T.c);
+  two_sum(h1, rest, hi, lo);
+}
+
+// x 2^q as a float pair: hi = float(x 2^q) rounded to nearest even, lo = the remainder rounded to
+// nearest (x's 53-bit significand split into its top 24 bits and the 29 below). The common case
+// (normal x, hi and lo both normal floats) in integer operations; the rest by FP64 arithmetic.
+__device__ __forceinline__ void split_scaled(double x, int q, float& hi, float& lo) {
+  const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
+  const int E = (int)((xh >> 20) & 0x7ffu);
+  const int eL = E - 1023 + q;  // x 2^q lies in [2^eL, 2^(eL+1))
+  if (E != 0 && E != 0x7ff && eL >= -74 && eL <= 126) {
+    const unsigned m23 = ((xh & 0xfffffu) << 3) | (xl >> 29);
+    const unsigned rest = xl & 0x1fffffffu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+    hi = __uint_as_float((xh & 0x80000000u) | ((((unsigned)(eL + 127) << 23) | m23) + up));
+    // remainder (rest - up 2^29) 2^(eL - 52), |rest - up 2^29| <= 2^28, with x's sign
+    const float r = __fmul_rn(__int2float_rn((int)rest - (int)(up << 29)), __uint_as_float((unsigned)(eL + 75) << 23));
+    lo = (xh & 0x80000000u) ? -r : r;
+    return;
+  }
+  hi = f32_of_scaled(x, q);
+  const double xs = ldexp_rne(x, q);
+  lo = (isfinite(hi) && hi != 0.0f) ? __double2float_rn(__dsub_rn(xs, (double)hi)) : 0.0f;
+}
+
+// Division of n < 2^31 by an invariant d >= 1 as a multiply-high, an add and a shift (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(m, n) + n) >> l; the sum stays below 2^32.
+struct FastDiv {
+  unsigned m;
+  int l;
+};
+FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  return {(unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) { return (__umulhi(f.m, n) + n) >> f.l; }
+
+// v 2^k for the rescaling of the pair; f = 2^k when it is a normal float (the common case).
+__device__ __forceinline__ float scale_by(float v, float f, bool f_ok, int k) {
+  return f_ok ? __fmul_rn(v, f) : ldexpf(v, k);
+}
+
+// One outer step over the finest level (packed, rows of whole 4-float vectors), four packed
+// columns of one colour's row per item (the other colour's segment is read for the x-neighbours;
+// both colours of a row in one item held twice the registers, two CTAs per SM instead of three,
+// and took 1.04 against 0.93 ms at 512^3). ZERO: the iterate is zero and unwritten (the
+// first step of a solve from zero): phi' = s e, and the residual pair is formed from g.
+// Otherwise phi' = phi + s e and the pair is read from (qh, ql). Writes phi', the new pair in
+// units of the next scale, and per block the sum of squares of the new hi values.
+template <bool ZERO, bool PER>
+__global__ void __launch_bounds__(256) k_defect_rec(double* __restrict__ x, const float* __restrict__ e,
+                                                    float* __restrict__ qh, float* __restrict__ ql,
+                                                    const double* __restrict__ g, Geom G, FastDiv by_nvec,
+                                                    FastDiv by_ny, const double* __restrict__ scal, int slot,
+                                                    int slot_next, double* __restrict__ partials) {
+  __shared__ double red[33];
+  const double sc = scal[slot];
+  const int p = pow2_exponent(sc), pn = pow2_exponent(scal[slot_next]);
+  const int dk = p - pn;  // new pair = (pair + A e) 2^(p - pn)
+  const bool f_ok = dk >= -126 && dk <= 127;
+  const float fac = f_ok ? __uint_as_float((unsigned)(dk + 127) << 23) : 1.0f;
+  const bool p_ok = p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit;
+  const int per = PER ? G.per : 0;
+  const bool px = (per & 1) != 0;
+  const unsigned nvec = (unsigned)G.hx >> 2;
+  const unsigned items = nvec * (unsigned)G.ny * (unsigned)G.nz;  // < 2^31 (checked at launch)
+  double acc = 0.0;
+  const unsigned items2 = 2u * items;
+  for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items2; it += gridDim.x * blockDim.x) {
+    const unsigned rowc = fdiv(it, by_nvec);
+    const int iv = (int)(it - rowc * nvec);
+    const int c = (int)(rowc & 1u);
+    const unsigned rowi = rowc >> 1;
+    const int k = (int)fdiv(rowi, by_ny), j = (int)rowi - k * G.ny;
+    const long long row = (long long)rowi * G.hx;
+    const int m0 = iv * 4;
+    int dyz = 0;
+    if (j == 0) dyz += G.sh[2];
+    if (j == G.ny - 1) dyz += G.sh[3];
+    if (k == 0) dyz += G.sh[4];
+    if (k == G.nz - 1) dyz += G.sh[5];
+    float own[4], oth[4];
+    load_vec(e + (long long)c * G.csz + row + m0, own);
+    const float* yr = e + (long long)(1 - c) * G.csz + row;  // the other colour's row
+    load_vec(yr + m0, oth);
+    float sq = 0.0f;
+    {
+      const int s = (c + j + k) & 1;
+      float edge;
+      if (s == 0) edge = m0 > 0 ? __ldg(yr + m0 - 1) : (px ? __ldg(yr + G.hx - 1) : 0.0f);
+      else edge = m0 + 4 < G.hx ? __ldg(yr + m0 + 4) : (px ? __ldg(yr) : 0.0f);
+      float ym[4], yp[4], zm[4], zp[4];
+      load_nb_vec<0, PER>(yr, G, m0, j, k, ym);
+      load_nb_vec<1, PER>(yr, G, m0, j, k, yp);
+      load_nb_vec<2, PER>(yr, G, m0, j, k, zm);
+      load_nb_vec<3, PER>(yr, G, m0, j, k, zp);
+      const long long o = (long long)c * G.csz + row + m0;
+      float hv[4], lv[4];
+      double xv[4];
+      if constexpr (ZERO) {
+        double g2[2];
+        load_vec(g + o, g2);
+        split_scaled(g2[0], -p, hv[0], lv[0]);
+        split_scaled(g2[1], -p, hv[1], lv[1]);
+        load_vec(g + o + 2, g2);
+        split_scaled(g2[0], -p, hv[2], lv[2]);
+        split_scaled(g2[1], -p, hv[3], lv[3]);
+      } else {
+        load_vec(qh + o, hv);
+        load_vec(ql + o, lv);
+        double x2[2];
+        load_vec(x + o, x2);
+        xv[0] = x2[0];
+        xv[1] = x2[1];
+        load_vec(x + o + 2, x2);
+        xv[2] = x2[0];
+        xv[3] = x2[1];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float xm = s == 0 ? (v == 0 ? edge : oth[(v + 3) & 3]) : oth[v];
+        const float xp = s == 0 ? oth[v] : (v == 3 ? edge : oth[(v + 1) & 3]);
+        int d = dyz;
+        if (m0 + v == 0 && s == 0) d += G.sh[0];
+        if (m0 + v == G.hx - 1 && s == 1) d += G.sh[1];
+        const F3 T = stencil_sum(xm, xp, ym[v], yp[v], zm[v], zp[v], neg_diag<float>(d), own[v]);
+        float hi, lo;
+        add_pair(hv[v], lv[v], T, hi, lo);
+        hv[v] = scale_by(hi, fac, f_ok, dk);
+        lv[v] = scale_by(lo, fac, f_ok, dk);
+        sq = __fmaf_rn(hv[v], hv[v], sq);
+        if constexpr (ZERO) {
+          if (p_ok) {
+            const double w = f64_of_scaled(own[v], p);
+            xv[v] = (__double_as_longlong(w) == (long long)0x8000000000000000ULL) ? 0.0 : w;
+          } else {
+            xv[v] = fma(sc, (double)own[v], 0.0);
+          }
+        } else {
+          xv[v] = p_ok ? xv[v] + f64_of_scaled(own[v], p) : fma(sc, (double)own[v], xv[v]);
+        }
+      }
+      store_vec(qh + o, hv);
+      store_vec(ql + o, lv);
+      double x2[2] = {xv[0], xv[1]};
+      store_vec(x + o, x2);
+      x2[0] = xv[2];
+      x2[1] = xv[3];
+      store_vec(x + o + 2, x2);
+    }
+    acc += (double)sq;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// The step's scalars: ||r~'||^2 = (fixed-order sum of the partials) s'^2 into scal[slot_rsum],
+// ||r~'|| / ||g|| into scal[slot_rel], and the next scale (scal[slot_next], its inverse) becomes
+// the current one (scal[slot_scale], scal[slot_scale + 1]).
+__global__ void __launch_bounds__(256) k_defect_finalize(const double* __restrict__ partials, int n, double* scal,
+                                                         int slot_rsum, int slot_rel, int slot_gsum, int slot_scale,
+                                                         int slot_next) {
+  __shared__ double red[33];
+  const double acc = sum_partials(partials, n, red);
+  if (threadIdx.x == 0) {
+    const double sn = scal[slot_next];
+    const double rs = (acc * sn) * sn;
+    scal[slot_rsum] = rs;
+    const double gs = scal[slot_gsum];
+    scal[slot_rel] = gs > 0.0 ? sqrt(rs) / sqrt(gs) : sqrt(rs);
+    scal[slot_scale] = sn;
+    scal[slot_scale + 1] = scal[slot_next + 1];
+  }
+}
+
+// Natural-order double field -> the packed residual pair in units of 2^-q (for verification).
+__global__ void __launch_bounds__(256) k_pack_pair(float* __restrict__ qh, float* __restrict__ ql, Geom G,
+                                                   const double* __restrict__ src, int q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= G.nx || j >= G.ny) return;
+  const long long pidx = (long long)i + (long long)G.nx * ((long long)j + (long long)G.ny * k);
+  const long long o = (long long)((i + j + k) & 1) * G.csz + ((long long)k * G.ny + j) * G.hx + (i >> 1);
+  float hi, lo;
+  split_scaled(src[pidx], q, hi, lo);
+  qh[o] = hi;
+  ql[o] = lo;
+}
+
+int g_defect_grid = 0;  // CTAs of the step kernel: the SMs times the CTAs resident per SM
+
+}  // namespace
+
+bool defect_rec_applies(const Geom& G) { return G.packed && G.hx >= 4 && (G.hx & 3) == 0; }
+
+cudaError_t launch_defect_rec(double* x, const float* e, float* qh, float* ql, const double* g, const Geom& G,
+                              double* scal, int slot, int slot_next, bool zero, double* partials, int* nparts,
+                              cudaStream_t s) {
+  if (!defect_rec_applies(G)) return cudaErrorInvalidValue;
+  if (g_defect_grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess)
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_defect_rec<false, true>, 256, 0);
+    if (err != cudaSuccess) return err;
+    g_defect_grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (g_defect_grid > kMaxPartials) g_defect_grid = kMaxPartials;
+  }
+  const long long items = 2LL * (G.hx / 4) * G.ny * G.nz;
+  if (items >= (1LL << 31) - 256LL * kMaxPartials) return cudaErrorInvalidValue;  // 32-bit item indices
+  const FastDiv by_nvec = make_fastdiv((unsigned)(G.hx / 4)), by_ny = make_fastdiv((unsigned)G.ny);
+  long long blocks = (items + 255) / 256;
+  if (blocks > g_defect_grid) blocks = g_defect_grid;
+  if (blocks < 1) blocks = 1;
+  const bool per = G.per != 0;
+  if (zero) {
+    if (per) k_defect_rec<true, true><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
+    else k_defect_rec<true, false><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
+  } else {
+    if (per) k_defect_rec<false, true><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
+    else k_defect_rec<false, false><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
+  }
+  *nparts = (int)blocks;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defect_finalize(const double* partials, int nparts, double* scal, int slot_rsum, int slot_rel,
+                                   int slot_gsum, int slot_scale, int slot_next, cudaStream_t s) {
+  k_defect_finalize<<<1, 256, 0, s>>>(partials, nparts, scal, slot_rsum, slot_rel, slot_gsum, slot_scale, slot_next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_pair(float* qh, float* ql, const Geom& G, const double* src, int q, cudaStream_t s) {
+  const int bx = G.nx >= 128 ? 128 : (G.nx >= 64 ? 64 : 32);
+  const int by = 256 / bx;
+  dim3 b(bx, by, 1), gr((G.nx + bx - 1) / bx, (G.ny + by - 1) / by, G.nz);
+  k_pack_pair<<<gr, b, 0, s>>>(qh, ql, G, src, q);
+  return cudaGetLastError();
+}
+
+}  // namespace ccmg

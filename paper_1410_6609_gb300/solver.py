@@ -168,6 +168,13 @@ class Poisson:
             self._check(st, "mg_solve")
         return k.value, rel.value
 
+    def outer_counts(self) -> tuple[int, int, int]:
+        """(outer cycles run by solve, those that carried the residual by recurrence, direct
+        finest-level residual evaluations) since creation (mg_outer_counts)."""
+        a = (ctypes.c_longlong * 3)()
+        self._check(self.lib.mg_outer_counts(self.ctx, a), "mg_outer_counts")
+        return int(a[0]), int(a[1]), int(a[2])
+
     def residual(self, field: bool = False):
         rel = ctypes.c_double()
         r = self.new_field() if field else None
@@ -347,6 +354,32 @@ class Poisson:
         if k < 0:
             raise ValueError(f"no fused prolongation sweep on level {level}")
         return "tma" if k == 1 else "vec"
+
+    def op_defect_update(self, phi, e, r, sc: float, sc_next: float, zero_start: bool = False):
+        """One outer mixed-precision step with the residual carried by recurrence
+        (mg_op_defect_update): from phi (ignored with zero_start), the correction e and the scaled
+        residual r (natural order [nz, ny, nx] float64 CUDA tensors) returns phi + sc e, the new
+        scaled residual over sc_next as the float pair (hi, lo) in float64 tensors, and the
+        squared norm sum(hi^2) sc_next^2."""
+        nx, ny, nz = self.dims
+        shape = (nz, ny, nx)
+        for t in (e, r) if zero_start else (phi, e, r):
+            if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != shape:
+                raise ValueError(f"fields must be float64 CUDA tensors of shape {shape}")
+        e, r = e.contiguous(), r.contiguous()
+        phi = phi.contiguous() if not zero_start else None
+        phi_out = torch.empty(shape, dtype=torch.float64, device=e.device)
+        hi = torch.empty_like(phi_out)
+        lo = torch.empty_like(phi_out)
+        ss = ctypes.c_double()
+        self._check(self.lib.mg_op_defect_update(self.ctx, 1 if zero_start else 0, float(sc), float(sc_next),
+                                                 _ptr(phi), _ptr(e), _ptr(r), _ptr(phi_out), _ptr(hi), _ptr(lo),
+                                                 ctypes.byref(ss)), "mg_op_defect_update")
+        return phi_out, hi, lo, ss.value
+
+    def op_defect_step(self):
+        """Enqueue the recurrence step alone on the current state (mg_op_defect_step; timing)."""
+        self._check(self.lib.mg_op_defect_step(self.ctx), "mg_op_defect_step")
 
     def op_residual_norm(self):
         self._check(self.lib.mg_op_residual_norm(self.ctx), "mg_op_residual_norm")

@@ -79,6 +79,9 @@ def test_null_context_is_invalid():
     assert lib.mg_solve(None, 1e-10, 10, None, None) == _lib.MG_ERR_INVALID
     assert lib.mg_adjoint_solve(None, None, None, 1e-10, 10, None, None) == _lib.MG_ERR_INVALID
     assert lib.mg_destroy(None) == _lib.MG_ERR_INVALID
+    assert lib.mg_op_defect_update(None, 0, 1.0, 1.0, None, None, None, None, None, None, None) == _lib.MG_ERR_INVALID
+    assert lib.mg_op_defect_step(None) == _lib.MG_ERR_INVALID
+    assert lib.mg_outer_counts(None, None) == _lib.MG_ERR_INVALID
     assert lib.mg_num_levels(None) == 0
 
 

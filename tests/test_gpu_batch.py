@@ -24,6 +24,22 @@ SYSTEMS = [
 ]
 
 
+def _single(s, precision="mixed"):
+    """A single context of system s whose mixed-precision outer steps evaluate every residual
+    directly (CCMG_DEFECT=walk), as the batched outer steps do; by default a single solve from
+    zero carries the residual by recurrence between direct checks, which rounds differently."""
+    import os
+    old = os.environ.get("CCMG_DEFECT")
+    os.environ["CCMG_DEFECT"] = "walk"
+    try:
+        return Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision=precision)
+    finally:
+        if old is None:
+            del os.environ["CCMG_DEFECT"]
+        else:
+            os.environ["CCMG_DEFECT"] = old
+
+
 def rhos():
     return [torch.from_numpy(synth.random_field(s["dims"], 30 + i)).cuda() for i, s in enumerate(SYSTEMS)]
 
@@ -37,7 +53,7 @@ def test_batch_is_bit_identical_to_single_contexts(precision):
         Bt.set_rhs(b, r)
     cyc, rel = Bt.solve(tol, 50)
     for b, s in enumerate(SYSTEMS):
-        P = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision=precision)
+        P = _single(s, precision)
         P.set_rhs(rho[b])
         k, r = P.solve(tol, 50)
         assert (k, r) == (cyc[b], rel[b]), (b, k, cyc[b], r, rel[b])
@@ -128,7 +144,7 @@ def test_zero_start_without_writing_and_flag_uploads_in_order():
     Bt.reset_solutions()
     Bt.vcycle(2)
     for b, s in enumerate(SYSTEMS):
-        P = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision="mixed")
+        P = _single(s)
         P.set_rhs(rho[b])
         P.set_solution(None)
         P.vcycle(2)
@@ -180,7 +196,7 @@ def test_tma_staged_batch_equals_direct_load_batch_and_single_contexts():
     assert ct[-1] == 0 and not torch.any(st[-1] != 0)
     for b, s in enumerate(TMA_SYSTEMS):
         assert torch.equal(st[b], sv[b]), b
-        P = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision="mixed")
+        P = _single(s)
         P.set_rhs(rho[b])
         k, r = P.solve(1e-9, 50)
         assert (k, r) == (ct[b], rt[b]), b

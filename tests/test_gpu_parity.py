@@ -424,15 +424,32 @@ def test_warm_start_continues_the_iteration():
     P.close()
 
 
-def test_zero_start_without_writing_the_iterate():
+@pytest.mark.parametrize("defect", ["walk", None])
+def test_zero_start_without_writing_the_iterate(defect):
     """In mixed precision mg_set_solution(NULL) writes nothing (the first cycle stores phi = s e);
-    the solve, and every call that reads phi before it, equal those of an explicit zero field."""
+    every call that reads phi before the solve equals that of an explicit zero field, and so does
+    the solve where every outer step evaluates its residual directly (CCMG_DEFECT=walk). By
+    default a solve from the unwritten zero carries the residual by recurrence (an explicit zero
+    field is an iterate like any other and does not), so there the two solves take the same steps
+    and agree to rounding."""
+    import os
+
     dims = (64, 48, 32)
     bc = synth.WALL_BC_TYPE
     rho = synth.random_field(dims, seed=8)
     outs = []
     for explicit in (False, True):
-        P = Poisson(dims, bc_type=bc, bc_value=synth.wall_bc_value(1.0), precision="mixed")
+        old = os.environ.get("CCMG_DEFECT")
+        if defect:
+            os.environ["CCMG_DEFECT"] = defect
+        try:
+            P = Poisson(dims, bc_type=bc, bc_value=synth.wall_bc_value(1.0), precision="mixed")
+        finally:
+            if defect:
+                if old is None:
+                    del os.environ["CCMG_DEFECT"]
+                else:
+                    os.environ["CCMG_DEFECT"] = old
         P.set_rhs(gpu(rho))
         zeros = torch.zeros(tuple(reversed(dims)), dtype=torch.float64, device="cuda")
         P.set_solution(zeros if explicit else None)
@@ -445,8 +462,11 @@ def test_zero_start_without_writing_the_iterate():
     (a0, ra0, ka, rela, a), (b0, rb0, kb, relb, b) = outs
     assert torch.equal(a0, b0) and not torch.any(a0 != 0)
     assert ra0 == rb0 and abs(ra0 - 1.0) < 1e-12
-    assert ka == kb and rela == relb and rela < 1e-9
-    assert torch.equal(a, b)
+    assert ka == kb and rela < 1e-9 and relb < 1e-9
+    if defect == "walk":
+        assert rela == relb and torch.equal(a, b)
+    else:
+        assert torch.linalg.norm(a - b) <= 1e-8 * torch.linalg.norm(b)
 
 
 def _rows_max(phi, bc):

@@ -934,3 +934,59 @@ def test_oracle_results_do_not_depend_on_the_thread_count():
     for o in out[1:]:
         for a, b in zip(out[0], o):
             assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------------------------
+# The mixed-precision outer step with its residual carried by recurrence (the folded operator of
+# Sec. 2.4): pinned to the residual's definition. With dyadic data of few bits every FP64
+# operation of oracle.residual is exact, so the recurrence must land exactly on the residual of
+# the updated iterate; a wrong sign, a dropped or misplaced neighbour or a wrong wall shift of the
+# diagonal breaks the equality.
+
+@pytest.mark.parametrize("bc", [(0, 1, 1, 0, 0, 1), (2, 2, 0, 1, 2, 2), (1, 1, 2, 2, 0, 1), (0, 0, 0, 0, 0, 0)])
+def test_defect_update_is_the_residual_of_the_updated_iterate(bc):
+    rng = np.random.default_rng(sum(bc) + 7)
+    shape = (6, 5, 8)
+    phi = rng.integers(-64, 64, shape) / 8.0
+    f = rng.integers(-100, 100, shape).astype(np.float64)
+    e = rng.integers(-32, 32, shape) / 4.0
+    for s in (0.125, 2.0):
+        r = oracle.residual(phi, f, 1.0, bc)  # h = 1, level 0: c = 1, scaled = natural units
+        phi2, r2 = oracle.defect_update(phi, e, r, s, bc)
+        assert np.array_equal(phi2, phi + s * e)
+        assert np.array_equal(r2, oracle.residual(phi2, f, 1.0, bc))
+
+
+def test_defect_update_rounds_once():
+    """Non-dyadic data: r' is the exactly rounded value of r + s (sum - D e), checked against
+    rational arithmetic cell by cell; a zero correction leaves everything unchanged."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(3)
+    shape = (3, 4, 4)
+    bc = (0, 1, 2, 2, 1, 0)
+    phi = rng.standard_normal(shape)
+    e = rng.standard_normal(shape).astype(np.float32)
+    r = rng.standard_normal(shape) * 1e-3
+    s = 2.0 ** -5
+    _, r2 = oracle.defect_update(phi, e, r, s, bc)
+    nz, ny, nx = shape
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                acc = Fraction(float(r[k, j, i]))
+                d = 6
+                for axis, n in ((0, nx), (1, ny), (2, nz)):
+                    for step in (-1, 1):
+                        q = [i, j, k]
+                        q[axis] += step
+                        face = 2 * axis + (0 if step < 0 else 1)
+                        if 0 <= q[axis] < n or bc[face] == 2:
+                            q[axis] %= n
+                            acc += Fraction(s) * Fraction(float(e[q[2], q[1], q[0]]))
+                        else:
+                            d += 1 if bc[face] == 0 else -1
+                acc -= Fraction(s) * d * Fraction(float(e[k, j, i]))
+                assert r2[k, j, i] == float(acc)
+    phi3, r3 = oracle.defect_update(phi, np.zeros(shape), r, s, bc)
+    assert np.array_equal(phi3, phi) and np.array_equal(r3, r)
