@@ -75,9 +75,18 @@ __device__ __forceinline__ void add_pair(float qh, float ql, const F3& T, float&
   two_sum(h1, rest, hi, lo);
 }
 
+// split_scaled for the rare operands (subnormal, infinite or NaN x, or x 2^q outside the range
+// where hi and lo are normal floats), out of line so that its FP64 operations are never issued
+// for the common ones.
+static __device__ __noinline__ float2 split_scaled_general(double x, int q) {
+  const float hi = f32_of_scaled(x, q);
+  const double xs = ldexp_rne(x, q);
+  return make_float2(hi, (isfinite(hi) && hi != 0.0f) ? __double2float_rn(__dsub_rn(xs, (double)hi)) : 0.0f);
+}
+
 // x 2^q as a float pair: hi = float(x 2^q) rounded to nearest even, lo = the remainder rounded to
-// nearest (x's 53-bit significand split into its top 24 bits and the 29 below). The common case
-// (normal x, hi and lo both normal floats) in integer operations; the rest by FP64 arithmetic.
+// nearest (x's 53-bit significand split into its top 24 bits and the 29 below). Zeros and the
+// common case (normal x, hi and lo both normal floats) in integer operations.
 __device__ __forceinline__ void split_scaled(double x, int q, float& hi, float& lo) {
   const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
   const int E = (int)((xh >> 20) & 0x7ffu);
@@ -92,9 +101,14 @@ __device__ __forceinline__ void split_scaled(double x, int q, float& hi, float& 
     lo = (xh & 0x80000000u) ? -r : r;
     return;
   }
-  hi = f32_of_scaled(x, q);
-  const double xs = ldexp_rne(x, q);
-  lo = (isfinite(hi) && hi != 0.0f) ? __double2float_rn(__dsub_rn(xs, (double)hi)) : 0.0f;
+  if (((xh & 0x7fffffffu) | xl) == 0u) {  // +-0
+    hi = __uint_as_float(xh & 0x80000000u);
+    lo = 0.0f;
+    return;
+  }
+  const float2 hl = split_scaled_general(x, q);
+  hi = hl.x;
+  lo = hl.y;
 }
 
 // Division of n < 2^31 by an invariant d >= 1 as a multiply-high, an add and a shift (Granlund and
@@ -111,10 +125,6 @@ FastDiv make_fastdiv(unsigned d) {
 }
 __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) { return (__umulhi(f.m, n) + n) >> f.l; }
 
-// v 2^k for the rescaling of the pair; f = 2^k when it is a normal float (the common case).
-__device__ __forceinline__ float scale_by(float v, float f, bool f_ok, int k) {
-  return f_ok ? __fmul_rn(v, f) : ldexpf(v, k);
-}
 
 // One outer step over the finest level (packed, rows of whole 4-float vectors), four packed
 // columns of one colour's row per item (the other colour's segment is read for the x-neighbours;
@@ -122,26 +132,22 @@ __device__ __forceinline__ float scale_by(float v, float f, bool f_ok, int k) {
 // and took 1.04 against 0.93 ms at 512^3). ZERO: the iterate is zero and unwritten (the
 // first step of a solve from zero): phi' = s e, and the residual pair is formed from g.
 // Otherwise phi' = phi + s e and the pair is read from (qh, ql). Writes phi', the new pair in
-// units of the next scale, and per block the sum of squares of the new hi values.
-template <bool ZERO, bool PER>
-__global__ void __launch_bounds__(256) k_defect_rec(double* __restrict__ x, const float* __restrict__ e,
-                                                    float* __restrict__ qh, float* __restrict__ ql,
-                                                    const double* __restrict__ g, Geom G, FastDiv by_nvec,
-                                                    FastDiv by_ny, const double* __restrict__ scal, int slot,
-                                                    int slot_next, double* __restrict__ partials) {
-  __shared__ double red[33];
-  const double sc = scal[slot];
-  const int p = pow2_exponent(sc), pn = pow2_exponent(scal[slot_next]);
-  const int dk = p - pn;  // new pair = (pair + A e) 2^(p - pn)
-  const bool f_ok = dk >= -126 && dk <= 127;
-  const float fac = f_ok ? __uint_as_float((unsigned)(dk + 127) << 23) : 1.0f;
-  const bool p_ok = p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit;
+// units of the next scale, and adds the squares of the new hi values to the thread's compensated
+// float sum (ss, sc2). FAST: the scale is a power of two with s e exact and the rescaling factor a
+// normal float (always, for the solver's scales); the other case takes ldexpf and the FMA. The
+// choice is uniform over the launch and made outside the loop, so that the FP64 operations of the
+// rare case are never issued for the common one (if-converted, they kept the FP64 pipe 70-84 %
+// busy).
+template <bool ZERO, bool PER, bool FAST>
+__device__ __forceinline__ void rec_items(double* __restrict__ x, const float* __restrict__ e,
+                                          float* __restrict__ qh, float* __restrict__ ql,
+                                          const double* __restrict__ g, const Geom& G, const FastDiv& by_nvec,
+                                          const FastDiv& by_ny, double sc, int p, int dk, float fac, float& ss,
+                                          float& sc2) {
   const int per = PER ? G.per : 0;
   const bool px = (per & 1) != 0;
   const unsigned nvec = (unsigned)G.hx >> 2;
-  const unsigned items = nvec * (unsigned)G.ny * (unsigned)G.nz;  // < 2^31 (checked at launch)
-  double acc = 0.0;
-  const unsigned items2 = 2u * items;
+  const unsigned items2 = 2u * nvec * (unsigned)G.ny * (unsigned)G.nz;  // < 2^31 (checked at launch)
   for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items2; it += gridDim.x * blockDim.x) {
     const unsigned rowc = fdiv(it, by_nvec);
     const int iv = (int)(it - rowc * nvec);
@@ -202,18 +208,18 @@ __global__ void __launch_bounds__(256) k_defect_rec(double* __restrict__ x, cons
         const F3 T = stencil_sum(xm, xp, ym[v], yp[v], zm[v], zp[v], neg_diag<float>(d), own[v]);
         float hi, lo;
         add_pair(hv[v], lv[v], T, hi, lo);
-        hv[v] = scale_by(hi, fac, f_ok, dk);
-        lv[v] = scale_by(lo, fac, f_ok, dk);
+        hv[v] = FAST ? __fmul_rn(hi, fac) : ldexpf(hi, dk);
+        lv[v] = FAST ? __fmul_rn(lo, fac) : ldexpf(lo, dk);
         sq = __fmaf_rn(hv[v], hv[v], sq);
         if constexpr (ZERO) {
-          if (p_ok) {
+          if constexpr (FAST) {
             const double w = f64_of_scaled(own[v], p);
             xv[v] = (__double_as_longlong(w) == (long long)0x8000000000000000ULL) ? 0.0 : w;
           } else {
             xv[v] = fma(sc, (double)own[v], 0.0);
           }
         } else {
-          xv[v] = p_ok ? xv[v] + f64_of_scaled(own[v], p) : fma(sc, (double)own[v], xv[v]);
+          xv[v] = FAST ? xv[v] + f64_of_scaled(own[v], p) : fma(sc, (double)own[v], xv[v]);
         }
       }
       store_vec(qh + o, hv);
@@ -224,9 +230,29 @@ __global__ void __launch_bounds__(256) k_defect_rec(double* __restrict__ x, cons
       x2[1] = xv[3];
       store_vec(x + o + 2, x2);
     }
-    acc += (double)sq;
+    float t;
+    two_sum(ss, sq, ss, t);
+    sc2 = __fadd_rn(sc2, t);
   }
-  acc = block_sum(acc, red);
+}
+
+template <bool ZERO, bool PER>
+__global__ void __launch_bounds__(256) k_defect_rec(double* __restrict__ x, const float* __restrict__ e,
+                                                    float* __restrict__ qh, float* __restrict__ ql,
+                                                    const double* __restrict__ g, Geom G, FastDiv by_nvec,
+                                                    FastDiv by_ny, const double* __restrict__ scal, int slot,
+                                                    int slot_next, double* __restrict__ partials) {
+  __shared__ double red[33];
+  const double sc = scal[slot];
+  const int p = pow2_exponent(sc), pn = pow2_exponent(scal[slot_next]);
+  const int dk = p - pn;  // new pair = (pair + A e) 2^(p - pn)
+  const bool f_ok = dk >= -126 && dk <= 127;
+  const float fac = f_ok ? __uint_as_float((unsigned)(dk + 127) << 23) : 1.0f;
+  const bool p_ok = p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit;
+  float ss = 0.0f, sc2 = 0.0f;
+  if (p_ok && f_ok) rec_items<ZERO, PER, true>(x, e, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, ss, sc2);
+  else rec_items<ZERO, PER, false>(x, e, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, ss, sc2);
+  const double acc = block_sum((double)ss + (double)sc2, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
@@ -264,7 +290,41 @@ __global__ void __launch_bounds__(256) k_pack_pair(float* __restrict__ qh, float
   ql[o] = lo;
 }
 
-int g_defect_grid = 0;  // CTAs of the step kernel: the SMs times the CTAs resident per SM
+// CTAs of the step kernel: the SMs times the CTAs of its largest variant (72-76 registers) that
+// fit on one; the same grid for every variant (four CTAs per SM for the 64-register ones took
+// 0.88 against 0.87 ms at 512^3)
+int g_defect_grid = 0;
+
+cudaError_t defect_grid(int* out) {
+  if (g_defect_grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_defect_rec<true, true>, 256, 0);
+    if (err != cudaSuccess) return err;
+    g_defect_grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (g_defect_grid > kMaxPartials) g_defect_grid = kMaxPartials;
+  }
+  *out = g_defect_grid;
+  return cudaSuccess;
+}
+
+template <bool ZERO, bool PER>
+cudaError_t launch_rec(double* x, const float* e, float* qh, float* ql, const double* g, const Geom& G,
+                       const double* scal, int slot, int slot_next, double* partials, long long items, int* nparts,
+                       cudaStream_t s) {
+  int grid = 0;
+  cudaError_t err = defect_grid(&grid);
+  if (err != cudaSuccess) return err;
+  long long blocks = (items + 255) / 256;
+  if (blocks > grid) blocks = grid;
+  if (blocks < 1) blocks = 1;
+  const FastDiv by_nvec = make_fastdiv((unsigned)(G.hx / 4)), by_ny = make_fastdiv((unsigned)G.ny);
+  k_defect_rec<ZERO, PER><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next,
+                                                      partials);
+  *nparts = (int)blocks;
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -274,32 +334,14 @@ cudaError_t launch_defect_rec(double* x, const float* e, float* qh, float* ql, c
                               double* scal, int slot, int slot_next, bool zero, double* partials, int* nparts,
                               cudaStream_t s) {
   if (!defect_rec_applies(G)) return cudaErrorInvalidValue;
-  if (g_defect_grid == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (err == cudaSuccess)
-      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_defect_rec<false, true>, 256, 0);
-    if (err != cudaSuccess) return err;
-    g_defect_grid = sms * (per_sm > 0 ? per_sm : 1);
-    if (g_defect_grid > kMaxPartials) g_defect_grid = kMaxPartials;
-  }
   const long long items = 2LL * (G.hx / 4) * G.ny * G.nz;
   if (items >= (1LL << 31) - 256LL * kMaxPartials) return cudaErrorInvalidValue;  // 32-bit item indices
-  const FastDiv by_nvec = make_fastdiv((unsigned)(G.hx / 4)), by_ny = make_fastdiv((unsigned)G.ny);
-  long long blocks = (items + 255) / 256;
-  if (blocks > g_defect_grid) blocks = g_defect_grid;
-  if (blocks < 1) blocks = 1;
   const bool per = G.per != 0;
-  if (zero) {
-    if (per) k_defect_rec<true, true><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
-    else k_defect_rec<true, false><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
-  } else {
-    if (per) k_defect_rec<false, true><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
-    else k_defect_rec<false, false><<<(int)blocks, 256, 0, s>>>(x, e, qh, ql, g, G, by_nvec, by_ny, scal, slot, slot_next, partials);
-  }
-  *nparts = (int)blocks;
-  return cudaGetLastError();
+  if (zero)
+    return per ? launch_rec<true, true>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s)
+               : launch_rec<true, false>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s);
+  return per ? launch_rec<false, true>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s)
+             : launch_rec<false, false>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s);
 }
 
 cudaError_t launch_defect_finalize(const double* partials, int nparts, double* scal, int slot_rsum, int slot_rel,
