@@ -29,6 +29,7 @@ struct BSys {
   double* g64[kMaxLevels]{};
   float* x32[kMaxLevels]{};
   float* g32[kMaxLevels]{};
+  float* q_lo = nullptr;  // mixed: low part of the residual pair whose high part is g32[0] (recurrence)
   FaceBC bc{};
 };
 
@@ -67,6 +68,10 @@ struct mg_batch {
   int* d_starts = nullptr;
   size_t cap_entries = 0, cap_starts = 0;
   Plan smooth[kMaxLevels], xfer[kMaxLevels], restr[kMaxLevels], cg, resid, update;
+  Plan defect;  // finest levels of the systems that can step by recurrence (q_lo set)
+  bool rec_on = false;  // mixed solves carry residuals by recurrence (CCMG_DEFECT=walk: never)
+  int* d_rec = nullptr;  // per system: this cycle steps by recurrence (all zero outside mg_batch_solve)
+  int* h_rec = nullptr;
   Plan xfer_nv[kMaxLevels];  // prolongation entries of the systems whose rows are not whole vectors
   size_t cg_smem = 0;
   int* d_active = nullptr;
@@ -263,6 +268,26 @@ mg_status plan(mg_batch* b) {
     add_plan(b, b->resid, er, dim3(ops::kResBX, ops::kResBY, 1));
     add_plan(b, b->update, eu, dim3(256, 1, 1));
   }
+  {  // the recurrence step: each system as many virtual blocks as its single-system launch has CTAs
+    std::vector<BEntry> ed;
+    for (int s = 0; s < b->B; ++s) {
+      BSys& S = b->sys[s];
+      if (!S.q_lo) continue;
+      BEntry e{};
+      e.G = S.geo[0];
+      e.x = S.x64[0];
+      e.g = S.g64[0];
+      e.xc = S.x32[0];
+      e.gc = S.g32[0];
+      e.aux = S.q_lo;
+      e.sys = s;
+      e.gx = defect_rec_blocks(S.geo[0]);
+      e.gy = e.gz = 1;
+      if (e.gx < 1) return bfail(b, MG_ERR_CUDA, "batch plan: no occupancy for the recurrence step");
+      ed.push_back(e);
+    }
+    add_plan(b, b->defect, ed, dim3(256, 1, 1));
+  }
   if (b->h_entries.size() > b->cap_entries) {
     cudaFree(b->d_entries);
     b->d_entries = nullptr;
@@ -277,7 +302,7 @@ mg_status plan(mg_batch* b) {
     BCK(cudaMalloc((void**)&b->d_starts, b->h_starts.size() * sizeof(int)), "batch plan");
     b->cap_starts = b->h_starts.size();
   }
-  const size_t np = std::max((size_t)b->resid.blocks, (size_t)kMaxPartials);
+  const size_t np = std::max({(size_t)b->resid.blocks, (size_t)b->defect.blocks, (size_t)kMaxPartials});
   if (np > b->cap_partials) {
     cudaFree(b->d_partials);
     b->d_partials = nullptr;
@@ -359,8 +384,16 @@ cudaError_t enqueue_bcycle(mg_batch* b, cudaStream_t s, long long* nk) {
   cudaError_t e;
   for (int it = 0; it < b->inner; ++it)
     if ((e = enqueue_bvcycle<float>(b, b->inv32, it == 0, s, nk)) != cudaSuccess) return e;
-  if ((e = launch_b_update(bl(b, b->update), b->d_active, b->d_zero, b->d_scal, s)) != cudaSuccess) return e;
-  if ((e = launch_b_set_scale(bl(b, b->resid), b->d_active, b->d_scal, s)) != cudaSuccess) return e;
+  // phi += s e and the next scale for the systems that evaluate their residual directly; the
+  // recurrence step (with its own next scale and norm) for those with rec[sys]
+  if ((e = launch_b_update(bl(b, b->update), b->d_active, b->d_rec, b->d_zero, b->d_scal, s)) != cudaSuccess) return e;
+  if (b->defect.count > 0) {
+    if ((e = launch_b_defect_step(bl(b, b->defect), b->d_active, b->d_rec, b->d_zero, b->d_scal, b->d_partials, s)) !=
+        cudaSuccess)
+      return e;
+    *nk += 4;
+  }
+  if ((e = launch_b_set_scale(bl(b, b->resid), b->d_active, b->d_rec, b->d_scal, s)) != cudaSuccess) return e;
   *nk += 2;
   return cudaSuccess;
 }
@@ -460,6 +493,8 @@ void free_batch(mg_batch* b) {
   cudaFree(b->d_starts);
   cudaFree(b->d_active);
   cudaFree(b->d_zero);
+  cudaFree(b->d_rec);
+  if (b->h_rec) cudaFreeHost(b->h_rec);
   cudaFree(b->d_scal);
   cudaFree(b->d_partials);
   if (b->h_active) cudaFreeHost(b->h_active);
@@ -558,6 +593,11 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
   b->nu2 = p0.nu2;
   b->inner = p0.mixed_inner;
   b->omega = p0.cgc_weight;
+  // mixed solves carry each system's residual by recurrence between direct checks where its
+  // finest level has rows of whole 4-float vectors, as single contexts do; CCMG_DEFECT=walk
+  // evaluates it directly after every step
+  const char* defect_env = std::getenv("CCMG_DEFECT");
+  b->rec_on = bmixed(b) && !(defect_env && std::strcmp(defect_env, "walk") == 0);
   b->stream = (cudaStream_t)stream;
   b->sys.resize(B);
   for (int d6 = -3; d6 <= 3; ++d6) {
@@ -618,9 +658,14 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
         offs[s].push_back(reserve(n * sizeof(float)));
       }
     }
+    if (b->rec_on && defect_rec_applies(S.geo[0]))
+      offs[s].push_back(reserve((size_t)cells(S.geo[0]) * sizeof(float)));  // q_lo
   }
   cudaError_t e = cudaMalloc((void**)&b->arena, bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_active, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_rec, B * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_rec, 0, B * sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_rec, B * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_zero, B * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_zero, B * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_scal, (size_t)B * kScalStride * sizeof(double));
@@ -671,6 +716,7 @@ mg_status mg_batch_create(int B, const mg_params* params, void* stream, mg_batch
         S.g32[l] = (float*)(b->arena + offs[s][k++]);
       }
     }
+    if (b->rec_on && defect_rec_applies(S.geo[0])) S.q_lo = (float*)(b->arena + offs[s][k++]);
   }
   for (int s = 0; s < B; ++s) b->h_zero[s] = 1;  // the arena starts zeroed
   mg_status st = prepare_batch_tma(b);
@@ -787,48 +833,95 @@ mg_status mg_batch_solve(mg_batch* b, double tol, int max_cycles, int* h_cycles,
   if (!(tol >= 0.0) || max_cycles < 0) return bfail(b, MG_ERR_INVALID, "need tol >= 0 and max_cycles >= 0");
   mg_status st = bgraphs(b);
   if (st != MG_OK) return st;
-  if ((st = set_all_active(b, 1)) != MG_OK) return st;
-  std::vector<int> cyc(b->B, 0), conv(b->B, 0);
-  for (;;) {
-    if ((st = brun(b, b->g_resid, b->n_resid, "batch residual")) != MG_OK) return st;
-    BCK(cudaMemcpyAsync(b->h_scal, b->d_scal, (size_t)b->B * kScalStride * sizeof(double), cudaMemcpyDeviceToHost,
+  const int B = b->B;
+  // per system, as mg_solve: a cycle from a never-written zero iterate, or after another such
+  // cycle, carries the residual by recurrence unless the last contraction predicts that it reaches
+  // the tolerance; its estimate is replaced by the direct residual before it ends the solve
+  std::vector<int> cyc(B, 0), conv(B, 0), run(B, 1), est(B, 0);
+  std::vector<double> rel(B, 0.0), relp(B, -1.0);
+  auto finish = [&](mg_status out) {
+    for (int s = 0; s < B; ++s) b->h_rec[s] = 0;  // the recurrence flags stay zero outside a solve
+    mg_status u = upload_flags(b, b->d_rec, b->h_rec);
+    if (u == MG_OK) u = set_all_active(b, 1);
+    return out != MG_OK ? out : u;
+  };
+  auto read_scal = [&](const char* what) -> mg_status {
+    BCK(cudaMemcpyAsync(b->h_scal, b->d_scal, (size_t)B * kScalStride * sizeof(double), cudaMemcpyDeviceToHost,
                         b->stream),
-        "batch residual");
-    BCK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "batch residual");
-    BCK(cudaStreamSynchronize(b->stream), "batch residual");
+        what);
+    BCK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), what);
+    BCK(cudaStreamSynchronize(b->stream), what);
     if (*b->h_err) {  // a staged sweep's bounded wait ran out: the iterates are incomplete
       cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
-      set_all_active(b, 1);
       return bfail(b, MG_ERR_TIMEOUT, "a kernel's bounded wait for its staged copies ran out; the result is incomplete");
     }
+    return MG_OK;
+  };
+  for (;;) {
+    // direct residuals of the running systems whose value is not an estimate, or whose estimate
+    // would end their solve
+    bool anyd = false;
+    for (int s = 0; s < B; ++s) {
+      b->h_active[s] = run[s] && (!est[s] || !(rel[s] >= tol) || !std::isfinite(rel[s]) || cyc[s] >= max_cycles);
+      anyd = anyd || b->h_active[s];
+    }
+    if (anyd) {
+      if ((st = upload_flags(b, b->d_active, b->h_active)) != MG_OK) return finish(st);
+      if ((st = brun(b, b->g_resid, b->n_resid, "batch residual")) != MG_OK) return finish(st);
+      if ((st = read_scal("batch residual")) != MG_OK) return finish(st);
+      for (int s = 0; s < B; ++s)
+        if (b->h_active[s]) {
+          rel[s] = b->h_scal[(size_t)kScalStride * s + kSlotRel];
+          est[s] = 0;
+        }
+    }
     bool any = false;
-    for (int s = 0; s < b->B; ++s) {
-      if (!b->h_active[s]) continue;
-      const double rel = b->h_scal[(size_t)kScalStride * s + kSlotRel];
-      if (!std::isfinite(rel)) {
-        b->h_active[s] = 0;
-      } else if (!(rel >= tol)) {
-        b->h_active[s] = 0;
+    for (int s = 0; s < B; ++s) {
+      if (!run[s]) continue;
+      if (!std::isfinite(rel[s])) {
+        run[s] = 0;
+      } else if (!(rel[s] >= tol)) {
+        run[s] = 0;
         conv[s] = 1;
       } else if (cyc[s] >= max_cycles) {
-        b->h_active[s] = 0;
+        run[s] = 0;
       } else {
         any = true;
       }
     }
     if (!any) break;
-    if ((st = upload_flags(b, b->d_active, b->h_active)) != MG_OK) return st;
-    if ((st = brun(b, b->g_cycle, b->n_cycle, "batch cycle")) != MG_OK) return st;
-    if ((st = clear_zero_of_active(b)) != MG_OK) return st;
-    for (int s = 0; s < b->B; ++s) cyc[s] += b->h_active[s];
+    bool anyrec = false;
+    for (int s = 0; s < B; ++s) {
+      b->h_active[s] = run[s];
+      b->h_rec[s] = run[s] && b->sys[s].q_lo && (b->lazy[s] || est[s]) &&
+                    !(relp[s] > 0.0 && rel[s] * (rel[s] / relp[s]) < tol);
+      if (run[s]) relp[s] = rel[s];
+      anyrec = anyrec || b->h_rec[s];
+    }
+    if ((st = upload_flags(b, b->d_active, b->h_active)) != MG_OK) return finish(st);
+    if ((st = upload_flags(b, b->d_rec, b->h_rec)) != MG_OK) return finish(st);
+    if ((st = brun(b, b->g_cycle, b->n_cycle, "batch cycle")) != MG_OK) return finish(st);
+    if ((st = clear_zero_of_active(b)) != MG_OK) return finish(st);
+    for (int s = 0; s < B; ++s) {
+      cyc[s] += b->h_active[s];
+      if (b->h_active[s] && !b->h_rec[s]) est[s] = 0;
+    }
+    if (anyrec) {  // the estimates of the systems that stepped by recurrence
+      if ((st = read_scal("batch cycle")) != MG_OK) return finish(st);
+      for (int s = 0; s < B; ++s)
+        if (b->h_rec[s]) {
+          rel[s] = b->h_scal[(size_t)kScalStride * s + kSlotRel];
+          est[s] = 1;
+        }
+    }
   }
   bool all = true;
-  for (int s = 0; s < b->B; ++s) {
+  for (int s = 0; s < B; ++s) {
     if (h_cycles) h_cycles[s] = cyc[s];
-    if (h_rel) h_rel[s] = b->h_scal[(size_t)kScalStride * s + kSlotRel];
+    if (h_rel) h_rel[s] = rel[s];
     if (!conv[s]) all = false;
   }
-  if ((st = set_all_active(b, 1)) != MG_OK) return st;
+  if ((st = finish(MG_OK)) != MG_OK) return st;
   if (!all) return bfail(b, MG_ERR_NOT_CONVERGED, "some systems did not reach the tolerance");
   return MG_OK;
 }

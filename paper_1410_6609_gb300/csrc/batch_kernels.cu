@@ -184,11 +184,13 @@ __global__ void __launch_bounds__(256) kb_finalize(const BEntry* __restrict__ E,
 }
 
 // phi += s e; for a system whose iterate is zero (possibly never written) phi = fma(s, e, +0),
-// without reading phi (as k_set_mixed).
+// without reading phi (as k_set_mixed). Systems stepping by recurrence (rec[sys]) are left to
+// kb_defect_rec.
 __global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, const int* __restrict__ start, int count,
-                                                 int total, const int* __restrict__ active,
+                                                 int total, const int* __restrict__ active, const int* __restrict__ rec,
                                                  const int* __restrict__ zero, const double* __restrict__ scal) {
   for_vblocks(E, start, count, total, active, [&](const BEntry& en, int e, int lb) {
+    if (rec && rec[en.sys]) return;
     const long long nb = __ldg(start + e + 1) - __ldg(start + e);
     const Geom G = en.G;
     const long long n = G.packed ? 2 * G.csz : G.csz;
@@ -215,11 +217,11 @@ __global__ void __launch_bounds__(256) kb_update(const BEntry* __restrict__ E, c
 }
 
 __global__ void kb_set_scale(const BEntry* __restrict__ E, int count, const int* __restrict__ active,
-                             double* __restrict__ scal) {
+                             const int* __restrict__ rec, double* __restrict__ scal) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= count) return;
   const int sys = E[e].sys;
-  if (!active[sys]) return;
+  if (!active[sys] || (rec && rec[sys])) return;
   const Geom G = E[e].G;
   const double n = (double)(G.packed ? 2 * G.csz : G.csz);
   double* sc = scal + kScalStride * sys;
@@ -318,15 +320,16 @@ cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_update(const BLaunch& L, const int* active, const int* zero, const double* scal, cudaStream_t s) {
+cudaError_t launch_b_update(const BLaunch& L, const int* active, const int* rec, const int* zero, const double* scal,
+                            cudaStream_t s) {
   if (L.count == 0 || L.blocks == 0) return cudaSuccess;
-  kb_update<<<persist(L), 256, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, zero, scal);
+  kb_update<<<persist(L), 256, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, rec, zero, scal);
   return cudaGetLastError();
 }
 
-cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, double* scal, cudaStream_t s) {
+cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, const int* rec, double* scal, cudaStream_t s) {
   if (L.count == 0) return cudaSuccess;
-  kb_set_scale<<<(L.count + 63) / 64, 64, 0, s>>>(L.entries, L.count, active, scal);
+  kb_set_scale<<<(L.count + 63) / 64, 64, 0, s>>>(L.entries, L.count, active, rec, scal);
   return cudaGetLastError();
 }
 

@@ -374,14 +374,24 @@ cudaError_t launch_set_rhs_all(const RhsJob* d_jobs, int B, long long nblocks, i
 // Per-system scalars of a batch: kScalStride doubles per system, same slots as a single context.
 constexpr int kScalStride = 8;
 constexpr int kSlotGsum = 0, kSlotRsum = 1, kSlotRel = 2, kSlotScale = 3, kSlotInvScale = 4;
+constexpr int kSlotNext = 5;  // the next scale (and its inverse at 6) while a recurrence step runs
 // FP64 residual of every system's finest level (mode 0 or 2, as launch_resid_norm), per-block
 // partials, then one finalize block per system: rsum, rel = sqrt(rsum / gsum) in its slots.
 // zero[s] != 0: system s's iterate is exactly zero, its norm is taken from the gsum slot.
 cudaError_t launch_b_resid_norm(const BLaunch& L, const int* active, const int* zero, int mode, double* scal,
                                 double* partials, cudaStream_t s);
-// x64 += scale * double(e32) on every active system's finest level (update entries).
-cudaError_t launch_b_update(const BLaunch& L, const int* active, const int* zero, const double* scal, cudaStream_t s);
-// scale = sqrt(rsum / n) (1 if not positive and finite), inv_scale = 1 / scale, per system.
-cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, double* scal, cudaStream_t s);
+// x64 += scale * double(e32) on every active system's finest level (update entries), except the
+// systems that step by recurrence (rec[sys]; rec may be null).
+cudaError_t launch_b_update(const BLaunch& L, const int* active, const int* rec, const int* zero, const double* scal,
+                            cudaStream_t s);
+// scale = sqrt(rsum / n) (1 if not positive and finite), inv_scale = 1 / scale, per system (not
+// those with rec[sys]; rec may be null).
+cudaError_t launch_b_set_scale(const BLaunch& L, const int* active, const int* rec, double* scal, cudaStream_t s);
+// The recurrence step over the active systems with rec[sys] (defect_kernels.cu): per system the
+// next scale, the step (bit-identical to its single-system launch, entries of defect_rec_blocks
+// virtual blocks: x phi, g g, xc e, gc the pair's hi, aux its lo), the norm and scale update.
+int defect_rec_blocks(const Geom& G);
+cudaError_t launch_b_defect_step(const BLaunch& L, const int* active, const int* rec, const int* zero, double* scal,
+                                 double* partials, cudaStream_t s);
 
 }  // namespace ccmg

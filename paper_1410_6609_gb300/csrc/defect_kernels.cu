@@ -118,7 +118,7 @@ struct FastDiv {
   unsigned m;
   int l;
 };
-FastDiv make_fastdiv(unsigned d) {
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
   int l = 0;
   while ((1ull << l) < d) ++l;
   return {(unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
@@ -142,13 +142,13 @@ template <bool ZERO, bool PER, bool FAST>
 __device__ __forceinline__ void rec_items(double* __restrict__ x, const float* __restrict__ e,
                                           float* __restrict__ qh, float* __restrict__ ql,
                                           const double* __restrict__ g, const Geom& G, const FastDiv& by_nvec,
-                                          const FastDiv& by_ny, double sc, int p, int dk, float fac, float& ss,
-                                          float& sc2) {
+                                          const FastDiv& by_ny, double sc, int p, int dk, float fac, unsigned blk,
+                                          unsigned nblk, float& ss, float& sc2) {
   const int per = PER ? G.per : 0;
   const bool px = (per & 1) != 0;
   const unsigned nvec = (unsigned)G.hx >> 2;
   const unsigned items2 = 2u * nvec * (unsigned)G.ny * (unsigned)G.nz;  // < 2^31 (checked at launch)
-  for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items2; it += gridDim.x * blockDim.x) {
+  for (unsigned it = blk * blockDim.x + threadIdx.x; it < items2; it += nblk * blockDim.x) {
     const unsigned rowc = fdiv(it, by_nvec);
     const int iv = (int)(it - rowc * nvec);
     const int c = (int)(rowc & 1u);
@@ -250,8 +250,10 @@ __global__ void __launch_bounds__(256) k_defect_rec(double* __restrict__ x, cons
   const float fac = f_ok ? __uint_as_float((unsigned)(dk + 127) << 23) : 1.0f;
   const bool p_ok = p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit;
   float ss = 0.0f, sc2 = 0.0f;
-  if (p_ok && f_ok) rec_items<ZERO, PER, true>(x, e, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, ss, sc2);
-  else rec_items<ZERO, PER, false>(x, e, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, ss, sc2);
+  if (p_ok && f_ok)
+    rec_items<ZERO, PER, true>(x, e, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, blockIdx.x, gridDim.x, ss, sc2);
+  else
+    rec_items<ZERO, PER, false>(x, e, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, blockIdx.x, gridDim.x, ss, sc2);
   const double acc = block_sum((double)ss + (double)sc2, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -288,6 +290,97 @@ __global__ void __launch_bounds__(256) k_pack_pair(float* __restrict__ qh, float
   split_scaled(src[pidx], q, hi, lo);
   qh[o] = hi;
   ql[o] = lo;
+}
+
+// The same step over the finest levels of many systems (batched solves). Entry e of the table is
+// one system's level 0 (x: phi, g: g, xc: the correction e, gc: the pair's hi, aux: its lo), split
+// into exactly the gx CTAs that the single-system launch takes for it; virtual block lb runs that
+// CTA's grid-stride items and writes its partial at the same position, so every system's values
+// and norm are bit-identical to those of its single-system step. Systems that are not active, or
+// do not step by recurrence this cycle (rec[sys] == 0), are skipped, a whole entry at a time. ZERO:
+// the launch for the systems whose iterate is zero and unwritten (zero[sys], the first-step form);
+// the other launch takes the rest (one kernel for both held 117 registers, two CTAs per SM, and
+// took 2.3 ms for the 64-system batch). A persistent grid walks the virtual blocks in order.
+template <bool PER, bool ZERO>
+__global__ void __launch_bounds__(256, 3) kb_defect_rec(const BEntry* __restrict__ E, const int* __restrict__ start,
+                                                     int count, int total, const int* __restrict__ active,
+                                                     const int* __restrict__ rec, const int* __restrict__ zero,
+                                                     const double* __restrict__ scal, double* __restrict__ partials) {
+  __shared__ double red[33];
+  if ((int)blockIdx.x >= total) return;
+  int lo = 0, hi = count - 1;  // the entry of the first virtual block (offsets ascend)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  int e = lo;
+  for (int b = blockIdx.x; b < total; b += gridDim.x) {
+    while (__ldg(start + e + 1) <= b) ++e;
+    const BEntry& en = E[e];
+    const int sys = en.sys;
+    if (!active[sys] || !rec[sys] || (zero[sys] != 0) != ZERO) {  // to this CTA's first block of the next entry
+      const int next = __ldg(start + e + 1);
+      if (next > b) b += ((next - b - 1) / (int)gridDim.x) * (int)gridDim.x;
+      continue;
+    }
+    const unsigned lb = (unsigned)(b - __ldg(start + e)), nb = (unsigned)(__ldg(start + e + 1) - __ldg(start + e));
+    const Geom G = en.G;
+    const double* sp = scal + kScalStride * sys;
+    const double sc = sp[kSlotScale];
+    const int p = pow2_exponent(sc), pn = pow2_exponent(sp[kSlotNext]);
+    const int dk = p - pn;
+    const bool f_ok = dk >= -126 && dk <= 127;
+    const float fac = f_ok ? __uint_as_float((unsigned)(dk + 127) << 23) : 1.0f;
+    const bool fast = f_ok && p != kBadPow2 && p >= -kScaleExpLimit && p <= kScaleExpLimit;
+    const FastDiv by_nvec = make_fastdiv((unsigned)(G.hx / 4)), by_ny = make_fastdiv((unsigned)G.ny);
+    double* x = (double*)en.x;
+    const float* ev = (const float*)en.xc;
+    float* qh = (float*)en.gc;
+    float* ql = (float*)en.aux;
+    const double* g = (const double*)en.g;
+    float ss = 0.0f, sc2 = 0.0f;
+    if (fast) rec_items<ZERO, PER, true>(x, ev, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, lb, nb, ss, sc2);
+    else rec_items<ZERO, PER, false>(x, ev, qh, ql, g, G, by_nvec, by_ny, sc, p, dk, fac, lb, nb, ss, sc2);
+    const double acc = block_sum((double)ss + (double)sc2, red);
+    if (threadIdx.x == 0) partials[b] = acc;
+  }
+}
+
+// Per stepping system: the next scale from the last residual norm, as k_set_scale computes it.
+__global__ void kb_defect_set_next(const BEntry* __restrict__ E, int count, const int* __restrict__ active,
+                                   const int* __restrict__ rec, double* __restrict__ scal) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const int sys = E[e].sys;
+  if (!active[sys] || !rec[sys]) return;
+  const Geom G = E[e].G;
+  double* sp = scal + kScalStride * sys;
+  const double s = pow2_floor(sqrt(sp[kSlotRsum] / (double)(2 * G.csz)));
+  sp[kSlotNext] = s;
+  sp[kSlotNext + 1] = 1.0 / s;
+}
+
+// Per stepping system (one CTA each): k_defect_finalize over its partials.
+__global__ void __launch_bounds__(256) kb_defect_finalize(const BEntry* __restrict__ E, const int* __restrict__ start,
+                                                          const int* __restrict__ active, const int* __restrict__ rec,
+                                                          const double* __restrict__ partials,
+                                                          double* __restrict__ scal) {
+  __shared__ double red[33];
+  const int e = blockIdx.x;
+  const int sys = E[e].sys;
+  if (!active[sys] || !rec[sys]) return;
+  const double acc = sum_partials(partials + start[e], start[e + 1] - start[e], red);
+  if (threadIdx.x == 0) {
+    double* sp = scal + kScalStride * sys;
+    const double sn = sp[kSlotNext];
+    const double rs = (acc * sn) * sn;
+    sp[kSlotRsum] = rs;
+    const double gs = sp[kSlotGsum];
+    sp[kSlotRel] = gs > 0.0 ? sqrt(rs) / sqrt(gs) : sqrt(rs);
+    sp[kSlotScale] = sn;
+    sp[kSlotInvScale] = sp[kSlotNext + 1];
+  }
 }
 
 // CTAs of the step kernel: the SMs times the CTAs of its largest variant (72-76 registers) that
@@ -342,6 +435,50 @@ cudaError_t launch_defect_rec(double* x, const float* e, float* qh, float* ql, c
                : launch_rec<true, false>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s);
   return per ? launch_rec<false, true>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s)
              : launch_rec<false, false>(x, e, qh, ql, g, G, scal, slot, slot_next, partials, items, nparts, s);
+}
+
+// One batched launch: a persistent grid of the SMs times the CTAs of this variant that fit on one,
+// at most one per virtual block.
+template <bool PER, bool ZERO>
+cudaError_t launch_kb_rec(const BLaunch& L, const int* active, const int* rec, const int* zero, double* scal,
+                          double* partials, cudaStream_t s) {
+  static int ctas_max = 0;
+  if (ctas_max == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_defect_rec<PER, ZERO>, 256, 0);
+    if (err != cudaSuccess) return err;
+    ctas_max = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int ctas = L.blocks < ctas_max ? L.blocks : ctas_max;
+  kb_defect_rec<PER, ZERO><<<ctas, 256, 0, s>>>(L.entries, L.start, L.count, L.blocks, active, rec, zero, scal, partials);
+  return cudaGetLastError();
+}
+
+int defect_rec_blocks(const Geom& G) {
+  int grid = 0;
+  if (defect_grid(&grid) != cudaSuccess || grid < 1) return 0;
+  const long long items = 2LL * (G.hx / 4) * G.ny * G.nz;
+  long long blocks = (items + 255) / 256;
+  if (blocks > grid) blocks = grid;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+cudaError_t launch_b_defect_step(const BLaunch& L, const int* active, const int* rec, const int* zero, double* scal,
+                                 double* partials, cudaStream_t s) {
+  if (L.count == 0) return cudaSuccess;
+  kb_defect_set_next<<<(L.count + 63) / 64, 64, 0, s>>>(L.entries, L.count, active, rec, scal);
+  cudaError_t err = cudaSuccess;
+  if (L.per) {
+    if ((err = launch_kb_rec<true, true>(L, active, rec, zero, scal, partials, s)) != cudaSuccess) return err;
+    if ((err = launch_kb_rec<true, false>(L, active, rec, zero, scal, partials, s)) != cudaSuccess) return err;
+  } else {
+    if ((err = launch_kb_rec<false, true>(L, active, rec, zero, scal, partials, s)) != cudaSuccess) return err;
+    if ((err = launch_kb_rec<false, false>(L, active, rec, zero, scal, partials, s)) != cudaSuccess) return err;
+  }
+  kb_defect_finalize<<<L.count, 256, 0, s>>>(L.entries, L.start, active, rec, partials, scal);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_defect_finalize(const double* partials, int nparts, double* scal, int slot_rsum, int slot_rel,

@@ -24,15 +24,15 @@ SYSTEMS = [
 ]
 
 
-def _single(s, precision="mixed"):
-    """A single context of system s whose mixed-precision outer steps evaluate every residual
-    directly (CCMG_DEFECT=walk), as the batched outer steps do; by default a single solve from
-    zero carries the residual by recurrence between direct checks, which rounds differently."""
+def _with_defect(defect, make):
+    """make() with CCMG_DEFECT=defect in the environment (None: as it is)."""
     import os
+    if defect is None:
+        return make()
     old = os.environ.get("CCMG_DEFECT")
-    os.environ["CCMG_DEFECT"] = "walk"
+    os.environ["CCMG_DEFECT"] = defect
     try:
-        return Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision=precision)
+        return make()
     finally:
         if old is None:
             del os.environ["CCMG_DEFECT"]
@@ -40,8 +40,49 @@ def _single(s, precision="mixed"):
             os.environ["CCMG_DEFECT"] = old
 
 
+def _single(s, precision="mixed", defect=None):
+    return _with_defect(defect, lambda: Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"],
+                                                precision=precision))
+
+
 def rhos():
     return [torch.from_numpy(synth.random_field(s["dims"], 30 + i)).cuda() for i, s in enumerate(SYSTEMS)]
+
+
+@pytest.mark.parametrize("defect", [None, "walk"])
+def test_zero_start_batch_is_bit_identical_to_single_contexts(defect):
+    """Solves from the never-written zero iterate (mixed precision): the systems whose finest rows
+    are whole 4-float vectors carry their residuals by recurrence (CCMG_DEFECT unset) exactly as
+    single contexts do, the others (and all, with CCMG_DEFECT=walk) evaluate them directly; every
+    system's cycles, relative residual and iterate equal those of its single context, bit for bit."""
+    rho = rhos()
+    Bt = _with_defect(defect, lambda: BatchPoisson(SYSTEMS, precision="mixed"))
+    for b, r in enumerate(rho):
+        Bt.set_rhs(b, r)
+    for rep in range(2):  # the second solve after the first left non-zero iterates and flags behind
+        Bt.reset_solutions()
+        cyc, rel = Bt.solve(1e-9, 50)
+    for b, s in enumerate(SYSTEMS):
+        P = _single(s, "mixed", defect)
+        P.set_rhs(rho[b])
+        P.set_solution(None)
+        k, r = P.solve(1e-9, 50)
+        assert (k, r) == (cyc[b], rel[b]), (b, k, cyc[b], r, rel[b])
+        assert torch.equal(P.solution(), Bt.solution(b)), b
+        counts = P.outer_counts()
+        assert (counts[1] > 0) == (defect is None and s["dims"][0] % 8 == 0 and min(s["dims"]) >= 6), (b, counts)
+        P.close()
+    # a later fixed number of cycles takes no recurrence step (the flags were reset)
+    Bt.reset_solutions()
+    Bt.vcycle(2)
+    for b, s in enumerate(SYSTEMS[:2]):
+        P = _single(s, "mixed", defect)
+        P.set_rhs(rho[b])
+        P.set_solution(None)
+        P.vcycle(2)
+        assert torch.equal(P.solution(), Bt.solution(b)), b
+        P.close()
+    Bt.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
