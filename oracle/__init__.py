@@ -83,6 +83,7 @@ def _load():
                 "ccmg_or_rhs": (None, [P, P, I, I, I, D, D, P, P]),
                 "ccmg_or_rhs_adjoint": (None, [P, P, P, I, I, I, D, D, P]),
                 "ccmg_or_cg": (I, [P, P, I, I, I, D, P, D, I]),
+                "ccmg_or_cg_f": (I, [P, P, I, I, I, ctypes.c_float, P, D, I]),
                 "ccmg_or_vcycles": (I, [P, P, I, I, I, D, P, I, I, D, I]),
                 "ccmg_or_rel_residual": (D, [P, P, I, I, I, D, P]),
                 "ccmg_or_solve": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
@@ -287,6 +288,20 @@ def cg(b, c: float, bc_type, rtol: float = CG_RTOL, maxit: int | None = None):
     if maxit is None:
         maxit = 2 * b.size
     it = _load().ccmg_or_cg(_p(x), _p(b), *_dims(b), c, _p(_bc(bc_type)), rtol, maxit)
+    return x, it
+
+
+CG_RTOL_F32 = 1e-5
+
+
+def cg_f32(b, c: float, bc_type, rtol: float = CG_RTOL_F32, maxit: int | None = None):
+    """The same CG in single precision (the coarsest grid of the mixed solver's single-precision
+    inner cycles; not in the paper). Returns (x as float32, iters)."""
+    b = _f32(b)
+    x = np.empty_like(b)
+    if maxit is None:
+        maxit = 2 * b.size
+    it = _load().ccmg_or_cg_f(_p(x), _p(b), *_dims(b), c, _p(_bc(bc_type)), rtol, maxit)
     return x, it
 
 

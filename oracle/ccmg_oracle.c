@@ -289,6 +289,50 @@ int ccmg_or_cg(double* x, const double* b, int nx, int ny, int nz, double c, con
   return it;
 }
 
+static float dot_f(const float* a, const float* b, size_t n) {
+  float s = 0.0f;
+  for (size_t p = 0; p < n; ++p) s = s + a[p] * b[p];
+  return s;
+}
+
+/* The same iteration in single precision, for the coarsest grid of the single-precision inner
+ * cycles of the mixed-precision solver (not in the paper); rtol there is CG_RTOL_F32. */
+int ccmg_or_cg_f(float* x, const float* b, int nx, int ny, int nz, float c, const int* bc, double rtol,
+                 int maxit) {
+  const size_t n = (size_t)nx * ny * nz;
+  float* r = (float*)malloc(n * sizeof(float));
+  float* p = (float*)malloc(n * sizeof(float));
+  float* ap = (float*)malloc(n * sizeof(float));
+  for (size_t q = 0; q < n; ++q) {
+    x[q] = 0.0f;
+    r[q] = b[q];
+    p[q] = b[q];
+  }
+  const float bnorm = sqrtf(dot_f(b, b, n));
+  float rr = dot_f(r, r, n);
+  int it = 0;
+  if (bnorm > 0.0f) {
+    while (it < maxit) {
+      apply_f(p, ap, nx, ny, nz, c, bc);
+      const float alpha = rr / dot_f(p, ap, n);
+      for (size_t q = 0; q < n; ++q) {
+        x[q] = x[q] + alpha * p[q];
+        r[q] = r[q] - alpha * ap[q];
+      }
+      ++it;
+      const float rr_new = dot_f(r, r, n);
+      if (sqrtf(rr_new) <= (float)rtol * bnorm) break;
+      const float beta = rr_new / rr;
+      for (size_t q = 0; q < n; ++q) p[q] = r[q] + beta * p[q];
+      rr = rr_new;
+    }
+  }
+  free(r);
+  free(p);
+  free(ap);
+  return it;
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* V-cycle (Sec. 3, Sec. 5.3): at level l < L-1:
  *   nu1 x (red, black);  r = f - A phi;  f_{l+1} = R r;  phi_{l+1} = 0;  V at l+1;
@@ -342,6 +386,7 @@ static void hier_free(hierarchy* H) {
 }
 
 #define CG_RTOL 1e-14
+#define CG_RTOL_F32 1e-5 /* the single-precision inner cycles' coarsest CG (float cannot reach 1e-14) */
 
 static void vcycle_d(hierarchy* H, int l, double h, const int* bc, int nu1, int nu2, double omega,
                      int* cg_iters) {
@@ -373,14 +418,9 @@ static void vcycle_f(hierarchy* H, int l, double h, const int* bc, int nu1, int 
   const int* d = H->dims[l];
   const size_t n = ncells(d);
   if (l == H->L - 1) {
-    double* b = (double*)malloc(n * sizeof(double));
-    double* x = (double*)malloc(n * sizeof(double));
-    for (size_t q = 0; q < n; ++q) b[q] = (double)H->ff[l][q];
-    const int it = ccmg_or_cg(x, b, d[0], d[1], d[2], level_coeff(h, l), bc, CG_RTOL, 2 * (int)n);
-    for (size_t q = 0; q < n; ++q) H->phif[l][q] = (float)x[q];
+    const int it = ccmg_or_cg_f(H->phif[l], H->ff[l], d[0], d[1], d[2], (float)level_coeff(h, l), bc, CG_RTOL_F32,
+                                2 * (int)n);
     if (cg_iters) *cg_iters = it;
-    free(b);
-    free(x);
     return;
   }
   const float c = (float)level_coeff(h, l);

@@ -345,7 +345,7 @@ cudaError_t enqueue_bvcycle(mg_batch* b, const InvDiag<T>& inv, bool zero0, cuda
     if ((e = launch_b_resid_restrict<T>(bl(b, b->restr[d]), act, red_only, s)) != cudaSuccess) return e;
     ++*nk;
   }
-  if ((e = launch_b_coarse_cg<T>(bl(b, b->cg), act, b->cg_smem, 1e-14, s)) != cudaSuccess) return e;
+  if ((e = launch_b_coarse_cg<T>(bl(b, b->cg), act, b->cg_smem, coarse_rtol<T>(), s)) != cudaSuccess) return e;
   ++*nk;
   // single precision, as the single-system cycle: the prolongation is fused into the first black
   // sweep of the systems whose rows are whole vectors; the others prolong first

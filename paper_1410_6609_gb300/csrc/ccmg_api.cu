@@ -192,7 +192,7 @@ cudaError_t enqueue_vcycle(mg_ctx* c, T* const* x, T* const* g, const InvDiag<T>
   if (l == c->L - 1) {
     const int n = G.nx * G.ny * G.nz;
     ++*nk;
-    return launch_coarse_cg<T>(x[l], g[l], G, 1e-14, 2 * n, c->d_iters, s);
+    return launch_coarse_cg<T>(x[l], g[l], G, coarse_rtol<T>(), 2 * n, c->d_iters, s);
   }
   if (zero && c->p.nu1 == 0) {
     e = cudaMemsetAsync(x[l], 0, sizeof(T) * (size_t)cells(G), s);
@@ -1290,7 +1290,7 @@ mg_status mg_op_coarse_solve(mg_ctx* c, int* h_iters) {
     CK(launch_var_coarse_cg<double>(c->x64[l], c->g64[l], c->vc[l], G, 1e-14, 2 * n, c->d_iters, c->stream),
        "coarse_solve");
   else if (mixed(c))
-    CK(launch_coarse_cg<float>(c->x32[l], c->g32[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
+    CK(launch_coarse_cg<float>(c->x32[l], c->g32[l], G, kCoarseRtolF32, 2 * n, c->d_iters, c->stream), "coarse_solve");
   else
     CK(launch_coarse_cg<double>(c->x64[l], c->g64[l], G, 1e-14, 2 * n, c->d_iters, c->stream), "coarse_solve");
   c->launches += 1;

@@ -26,6 +26,12 @@ namespace ccmg {
 
 constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarseCells = 4096;
+// Relative residuals at which the coarsest CG stops: FP64 levels 1e-14; the single-precision
+// levels of the mixed solver's inner cycles 1e-5 (float cannot reach 1e-14, and the inner
+// cycles' correction needs no more on the coarsest grid).
+constexpr double kCoarseRtol = 1e-14, kCoarseRtolF32 = 1e-5;
+template <typename T>
+constexpr double coarse_rtol() { return sizeof(T) == sizeof(float) ? kCoarseRtolF32 : kCoarseRtol; }
 
 struct Geom {
   int nx, ny, nz;  // cells per axis

@@ -872,6 +872,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubles of shared memory */) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
@@ -898,12 +903,17 @@ __device__ __forceinline__ double block_sum(double v, double* red /* >= 33 doubl
 // and r in registers, only p (which the neighbours read) lives in shared memory, and the dot
 // products are warp_sum reductions, added over the two warps in a fixed order. On GB300 an FP64
 // warp instruction takes 64 cycles of its sub-partition's FP64 pipe, so one cell per lane on two
-// sub-partitions halves the issue time of the former two-cells-per-lane warp.
+// sub-partitions halves the issue time of the former two-cells-per-lane warp. It computes in the
+// level's own precision: double for the FP64 cycle, float for the single-precision inner cycle of
+// the mixed solver (stopping at kCoarseRtolF32; in double its FP64 operations took 37 us of
+// 64-cycle issue per coarsest solve).
 constexpr int kCoarseSmallCells = 64;
 
 template <typename T>
 __device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, const Geom& G, double rtol, int maxit,
-                               double* __restrict__ p, double* __restrict__ red) {
+                               double* __restrict__ sm, double* __restrict__ red_d) {
+  T* p = reinterpret_cast<T*>(sm);
+  T* red = reinterpret_cast<T*>(red_d);
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = nx * ny * nz;
   const int W = n > 32 ? 2 : 1;  // warps taking part (uniform)
@@ -916,12 +926,12 @@ __device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, con
   };
   int slot = 0;
   // sum of one value per thread over the W warps, in a fixed order
-  auto psum = [&](double v) -> double {
+  auto psum = [&](T v) -> T {
     v = warp_sum(v);
     if (W == 1) return v;
     if (lane == 0) red[2 * slot + w] = v;
     sync();
-    const double sv = red[2 * slot] + red[2 * slot + 1];
+    const T sv = red[2 * slot] + red[2 * slot + 1];
     slot ^= 1;  // the next sum writes the other pair; its barrier follows every read of this one
     return sv;
   };
@@ -929,7 +939,7 @@ __device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, con
   // cell at the opposite side) and -(6 + d)
   unsigned nbm = 0u;
   int no[6] = {-1, 1, -nx, nx, -nx * ny, nx * ny};
-  double nd = 0.0, xi = 0.0, ri = 0.0;
+  T nd = T(0), xi = T(0), ri = T(0);
   if (own) {
     const int ix = t % nx, iy = (t / nx) % ny, iz = t / (nx * ny);
     const int ext[3] = {nx, ny, nz}, pos[3] = {ix, iy, iz}, st[3] = {1, nx, nx * ny};
@@ -944,36 +954,36 @@ __device__ int coarse_cg_small(T* __restrict__ xo, const T* __restrict__ bi, con
       else if (per) { nbm |= 2u << (2 * a); no[2 * a + 1] = -(ext[a] - 1) * st[a]; }
       else d += G.sh[2 * a + 1];
     }
-    nd = neg_diag<double>(d);
-    ri = (double)bi[t];
+    nd = neg_diag<T>(d);
+    ri = bi[t];
     p[t] = ri;
   }
-  double rr = psum(ri * ri);  // its barrier also publishes p
-  const double bnorm = sqrt(rr);
-  const double stop = rtol * bnorm;
-  const double stop2 = stop * stop;  // ||r|| <= stop as ||r||^2 <= stop^2: no square root per iteration
+  T rr = psum(ri * ri);  // its barrier also publishes p
+  const T bnorm = sqrt(rr);
+  const T stop = (T)rtol * bnorm;
+  const T stop2 = stop * stop;  // ||r|| <= stop as ||r||^2 <= stop^2: no square root per iteration
   int it = 0;
-  if (bnorm > 0.0) {
+  if (bnorm > T(0)) {
     while (it < maxit) {
-      double a = 0.0, pi = 0.0;
+      T a = T(0), pi = T(0);
       if (own) {
         pi = p[t];
-        double S = 0.0;
+        T S = T(0);
 #pragma unroll
         for (int q = 0; q < 6; ++q)
           if (nbm & (1u << q)) S += p[t + no[q]];
         a = -nd * pi - S;
       }
-      const double pap = psum(pi * a);  // after its barrier nobody reads p of this iteration again
-      const double alpha = rr / pap;
+      const T pap = psum(pi * a);  // after its barrier nobody reads p of this iteration again
+      const T alpha = rr / pap;
       if (own) {
         xi = xi + alpha * pi;
         ri = ri - alpha * a;
       }
-      const double rrn = psum(ri * ri);
+      const T rrn = psum(ri * ri);
       ++it;
       if (rrn <= stop2) break;
-      const double beta = rrn / rr;
+      const T beta = rrn / rr;
       if (own) p[t] = ri + beta * pi;
       sync();  // p complete before the next product reads its neighbours
       rr = rrn;

@@ -379,6 +379,19 @@ def test_single_precision_level_operations_match_oracle(dims, bc):
         P.level_set(l + 1, 0, gpu(ec))
         P.op_prolong_correct(l)
         assert maxrel(cpu(P.level_get(l, 0)), oracle.prolong_correct_f32(phi, ec, 2.0)) == 0.0
+    # the coarsest CG of the single-precision cycle: in float, to 1e-5 (the GPU reduces in a
+    # different order, so the iterates agree to the tolerance, not bit for bit)
+    L = P.num_levels
+    nx, ny, nz = P.level_dims(L - 1)
+    cL = oracle.level_coeff(h, L - 1)
+    b = (rng.standard_normal((nz, ny, nx)) * cL).astype(np.float32).astype(np.float64)
+    P.level_set(L - 1, 1, gpu(b))
+    its = P.op_coarse_solve()
+    x = cpu(P.level_get(L - 1, 0))
+    x_ref, it_ref = oracle.cg_f32(b, cL, bc)
+    x64, _ = oracle.cg(b, cL, bc)
+    assert abs(its - it_ref) <= 3, (its, it_ref)
+    assert rel(x, x64) < 1e-4 and rel(x_ref.astype(np.float64), x64) < 1e-4
     P.close()
 
 
