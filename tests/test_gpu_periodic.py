@@ -214,8 +214,11 @@ def test_periodic_mixed_precision_and_the_staged_sweep(dims, bc):
         ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_periodic_batch_is_bit_identical_to_single_contexts(precision):
+@pytest.mark.parametrize("precision,zero_start", [("fp64", False), ("mixed", False), ("mixed", True)])
+def test_periodic_batch_is_bit_identical_to_single_contexts(precision, zero_start):
+    """Batched solves with periodic axes (and one system without) equal single contexts bit for bit;
+    from the never-written zero the mixed solves carry their residuals by recurrence (the batched
+    step's periodic variant serving the system without periodic axes too)."""
     systems = [
         dict(dims=(32, 32, 32), h=1.0, bc_type=(P, P, P, P, D, D), bc_value=(0.0, 0.0, 0.0, 0.0, 0.0, 1.0)),
         dict(dims=(48, 40, 24), h=0.5, bc_type=(D, N, P, P, P, P), bc_value=(0.2, -0.1, 0.0, 0.0, 0.0, 0.0)),
@@ -227,12 +230,18 @@ def test_periodic_batch_is_bit_identical_to_single_contexts(precision):
     Bt = BatchPoisson(systems, precision=precision)
     for b, r in enumerate(rho):
         Bt.set_rhs(b, r)
+    if zero_start:
+        Bt.reset_solutions()
     cyc, rels = Bt.solve(tol, 50)
     for b, s in enumerate(systems):
         Pz = Poisson(s["dims"], h=s["h"], bc_type=s["bc_type"], bc_value=s["bc_value"], precision=precision)
         Pz.set_rhs(rho[b])
+        if zero_start:
+            Pz.set_solution(None)
         k, r = Pz.solve(tol, 50)
         assert (k, r) == (cyc[b], rels[b]), b
+        if zero_start:
+            assert Pz.outer_counts()[1] >= 1, b  # the recurrence ran
         assert torch.equal(Pz.solution(), Bt.solution(b)), b
         f = oracle.rhs(rho[b].cpu().numpy(), s["h"], s["bc_type"], s["bc_value"])
         assert oracle.rel_residual(cpu(Pz.solution()), f, s["h"], s["bc_type"]) < tol * 1.0001, b
