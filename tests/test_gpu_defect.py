@@ -151,11 +151,13 @@ def _solve_pair(dims, bc, bcv, rho, tol):
         k, rel = P.solve(tol, 40)
         cyc, rec, direct = P.outer_counts()
         assert cyc == k
+        # a direct evaluation after every step that is not by recurrence (two where a step
+        # predicted to end the solve did not: its check leaves out the single-precision copy that
+        # the next step then needs), and one before the solve stops after a step by recurrence
         if defect == "walk":
-            assert rec == 0 and direct == k
-        else:  # the first step from zero by recurrence; a direct evaluation after every other
-            # step and before the solve stops
-            assert rec >= 1 and direct >= 1 and k - rec <= direct <= k - rec + 1
+            assert rec == 0 and k <= direct <= 2 * k
+        else:  # the first step from zero is by recurrence
+            assert rec >= 1 and direct >= 1 and k - rec <= direct <= 2 * (k - rec) + 1
         rel_direct = P.residual()
         out.append((k, rel, rel_direct, P.solution().cpu().numpy()))
         P.close()
