@@ -88,6 +88,7 @@ def _load():
                 "ccmg_or_rel_residual": (D, [P, P, I, I, I, D, P]),
                 "ccmg_or_solve": (I, [P, P, I, I, I, D, P, I, I, D, D, I, P]),
                 "ccmg_or_solve_mixed": (I, [P, P, I, I, I, D, P, I, I, D, D, I, I, P]),
+                "ccmg_or_vcycles_f": (I, [P, P, I, I, I, D, P, I, I, D, I]),
                 "ccmg_or_efield": (None, [P, P, I, I, I, D, P, P]),
                 "ccmg_or_efield_stencil": (None, [P, P, I, I, I, D, P, P, I]),
                 "ccmg_or_efield_field": (None, [P, P, I, I, I, D, P, P, P, P, I]),
@@ -373,6 +374,14 @@ def defect_update(phi, e, r, s: float, bc_type):
     stack = np.stack(terms, axis=-1).reshape(-1, len(terms))
     r_new = np.array([math.fsum(row) for row in stack]).reshape(ev.shape)
     return phi + s * ev, r_new
+
+
+def vcycles_f32(phi, f, h: float, bc_type, ncycles: int, nu1: int = 2, nu2: int = 2, omega: float = 2.0):
+    """ncycles single-precision V-cycles on A phi = f (the mixed solver's inner cycles; not in the
+    paper). Returns phi as float32."""
+    phi = _f32(phi).copy()
+    _load().ccmg_or_vcycles_f(_p(phi), _p(_f32(f)), *_dims(phi), h, _p(_bc(bc_type)), nu1, nu2, omega, ncycles)
+    return phi
 
 
 def solve_mixed(f, h: float, bc_type, tol: float = 1e-9, max_cycles: int = 100, nu1: int = 2,

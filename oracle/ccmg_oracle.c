@@ -532,6 +532,21 @@ static double pow2_floor(double v) {
  *         at the bottom);
  *         phi += s * e (double).
  * Returns the number of outer iterations. */
+/* ncycles single-precision V-cycles (the mixed solver's inner cycles, its coarsest CG in float) on
+ * A phi = f at the finest level, from phi as given; float arrays in natural order. */
+int ccmg_or_vcycles_f(float* phi, const float* f, int nx, int ny, int nz, double h, const int* bc, int nu1,
+                      int nu2, double omega, int ncycles) {
+  hierarchy H;
+  hier_init(&H, nx, ny, nz, 1);
+  const size_t n = ncells(H.dims[0]);
+  memcpy(H.ff[0], f, n * sizeof(float));
+  memcpy(H.phif[0], phi, n * sizeof(float));
+  for (int it = 0; it < ncycles; ++it) vcycle_f(&H, 0, h, bc, nu1, nu2, (float)omega, NULL);
+  memcpy(phi, H.phif[0], n * sizeof(float));
+  hier_free(&H);
+  return ncycles;
+}
+
 int ccmg_or_solve_mixed(double* phi, const double* f, int nx, int ny, int nz, double h, const int* bc,
                         int nu1, int nu2, double omega, double tol, int max_cycles, int inner,
                         double* rel_res_out) {

@@ -4,6 +4,7 @@ Each test ties one part of the oracle to something other than the oracle itself:
 discrete solution, an exact spectral solver, a dense direct solve, a literal Galerkin triple
 product, a symmetry, a table of the paper, or brute force on tiny inputs.
 """
+import math
 import os
 
 import numpy as np
@@ -1008,3 +1009,45 @@ def test_defect_update_rounds_once():
                 assert r2[k, j, i] == float(acc)
     phi3, r3 = oracle.defect_update(phi, np.zeros(shape), r, s, bc)
     assert np.array_equal(phi3, phi) and np.array_equal(r3, r)
+
+
+@pytest.mark.parametrize("bc", [(N, N, N, N, D, D), (2, 2, N, D, D, N)])
+def test_defect_recurrence_loop_takes_the_direct_loops_steps(bc):
+    """The mixed solver's outer loop with the residual carried by recurrence (oracle.defect_update
+    after the oracle's single-precision inner cycles, the residual evaluated directly only before
+    the loop stops) against the oracle's loop with the direct FP64 residual after every step: the
+    same outer steps, both below the tolerance by the direct residual, solutions equal to the inner
+    cycles' single precision. The scale rule is the solver's: the largest power of two not above
+    the RMS of the previous residual (of f first)."""
+    dims = (24, 20, 16)
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    rho = synth.random_field(dims, 21)
+    f = oracle.rhs(rho, 1.0, bc, (0.0, 0.0, 0.0, 0.0, 0.0, 1.0))  # h = 1: scaled = natural units
+    tol, inner = 1e-9, 4
+
+    def pow2_floor(v):
+        m, e = math.frexp(v)  # v = m 2^e, 0.5 <= m < 1
+        return math.ldexp(1.0, e - 1)
+
+    phi_d, k_d, rel_d = oracle.solve_mixed(f, 1.0, bc, tol=tol, inner=inner)
+    fn = np.linalg.norm(f)
+    phi = np.zeros_like(f)
+    r = f.copy()
+    scale = pow2_floor(fn / math.sqrt(n))
+    k = 0
+    while True:
+        rel = np.linalg.norm(r) / fn  # the recurrence's estimate
+        if rel < tol and oracle.rel_residual(phi, f, 1.0, bc) < tol:
+            break
+        assert k < 20
+        e = oracle.vcycles_f32(np.zeros_like(f), (r / scale).astype(np.float32), 1.0, bc, inner)
+        r_used = r
+        phi, r = oracle.defect_update(phi, e, r, scale, bc)
+        scale = pow2_floor(np.linalg.norm(r_used) / math.sqrt(n))
+        k += 1
+    assert k == k_d and rel_d < tol
+    assert oracle.rel_residual(phi, f, 1.0, bc) < tol
+    # the carried residual stays the residual of the carried iterate (to FP64 rounding)
+    assert np.linalg.norm(r - oracle.residual(phi, f, 1.0, bc)) <= 1e-13 * fn
+    assert np.linalg.norm(phi - phi_d) <= 1e-6 * np.linalg.norm(phi_d)
