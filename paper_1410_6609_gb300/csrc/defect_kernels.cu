@@ -7,13 +7,13 @@
 // Sec. 3). This file forms that change exactly enough to carry the residual from step to step
 // without reading the iterate's stencil:
 //  - A e of seven floats with small integer weights is summed by three cascades of error-free
-//    additions (Knuth's TwoSum, the product by Dekker's method with one FMA): the terms, their
+//    additions (Knuth's TwoSum; the diagonal product's rounding error recovered by one FMA): the terms, their
 //    rounding errors, and those errors' errors, so that only the last, third-order sum rounds
 //    (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005, the K = 3 case of SumK). Its
 //    error is below 2^-60 of the sum of the terms' magnitudes.
 //  - The residual is held as a pair of floats hi + lo in units of the current scale s: hi is the
 //    single-precision right-hand side the next inner cycles solve for, lo (|lo| <= ulp(hi)/2) the
-//    rest, so the pair carries about 48 bits. New pair = old pair + A e in error-free steps, one
+//    rest, so the pair carries about 48 bits. New pair = old pair - A e in error-free steps, one
 //    rounding of the small remainders (below 2^-45 of the old and new residuals), then a
 //    power-of-two rescaling to the next step's scale (exact).
 //  - The iterate update phi' = phi + s e is the single rounded FP64 add of the plain update.
@@ -21,7 +21,8 @@
 // the whole step reads e, phi and the pair once and writes phi and the pair once (36 B per cell,
 // against 40 B for the plain update followed by the FP64 residual walk, which is bound by its
 // integer work), and only the iterate update uses the FP64 pipe. The solver still evaluates the
-// residual directly (the fixed-point walk) before it accepts convergence.
+// residual directly (the fixed-point walk) before it accepts convergence. The batched launch runs
+// the same per-item body over many systems, each exactly as its single-system launch would.
 #include "level_ops.cuh"
 
 namespace ccmg {
