@@ -7,10 +7,10 @@
 // Sec. 3). This file forms that change exactly enough to carry the residual from step to step
 // without reading the iterate's stencil:
 //  - A e of seven floats with small integer weights is summed by three cascades of error-free
-//    additions (Knuth's TwoSum; the diagonal product's rounding error recovered by one FMA): the terms, their
-//    rounding errors, and those errors' errors, so that only the last, third-order sum rounds
-//    (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005, the K = 3 case of SumK). Its
-//    error is below 2^-60 of the sum of the terms' magnitudes.
+//    additions (Knuth's TwoSum; the diagonal product's rounding error recovered by one FMA): the
+//    terms, their rounding errors, and those errors' errors, so that only the last, third-order
+//    sum rounds (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005, the K = 3 case of
+//    SumK). Its error is below 2^-60 of the sum of the terms' magnitudes.
 //  - The residual is held as a pair of floats hi + lo in units of the current scale s: hi is the
 //    single-precision right-hand side the next inner cycles solve for, lo (|lo| <= ulp(hi)/2) the
 //    rest, so the pair carries about 48 bits. New pair = old pair - A e in error-free steps, one
